@@ -1,0 +1,154 @@
+/*
+ * oracle.h -- FP64 CPU oracle of the immersed-boundary lattice-Boltzmann
+ * finite-element (IB-LBM-FEM) time step of Krueger, Varnik and Raabe,
+ * "Efficient and accurate simulations of deformable particles immersed in a
+ * fluid using a combined immersed boundary lattice Boltzmann finite element
+ * method" (arXiv:1004.2416).
+ *
+ * THIS IS TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load it.  The CUDA library never calls
+ * it, includes it or links it, and the two share no source: no kernel, header,
+ * helper, table or constant generator.
+ *
+ * Every routine is the paper's definition written out in plain double
+ * precision, in the paper's order and notation, with no blocking, fusion or
+ * reordering.  Where the paper is silent or ambiguous the reading taken is
+ * stated beside the code.  All functions are single-threaded.
+ *
+ * Conventions shared with the paper (Sec. II, Sec. IV):
+ *   lattice units dx = dt = 1, c_s^2 = 1/3, rest density rho0 = 1;
+ *   lattice cell (x, y, z), 0 <= x < nx etc., linear index x + nx*(y + ny*z);
+ *   population arrays are [19][nz][ny][nx] (direction slowest);
+ *   vector fields are [3][nz][ny][nx];
+ *   membrane node arrays are [n][3] (x, y, z per node).
+ *
+ * Parity status of each function is listed in the header comment of the .c
+ * file that defines it.  Return codes: 0 ok, -1 bad argument, -5 a stencil
+ * cell lies outside the walls (z < 0 or z >= nz), -2 out of memory.
+ */
+#ifndef IBLBM_ORACLE_H
+#define IBLBM_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- lattice.c : Sec. II.A -------------------------------------------- */
+
+/* D3Q19 velocity set in the numbering of Fig. d3q19, the standard D3Q19
+ * weights (cited to Qian et al. in Sec. II.A, values not printed) and the
+ * index of the opposite direction. */
+void orc_d3q19(int c[19][3], double w[19], int opp[19]);
+
+/* Eq. (equilibrium): f_i^eq = w_i rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u). */
+double orc_feq(int i, double rho, const double u[3]);
+
+/* Eq. (latticeforce), Guo forcing term F_i for body force density f. */
+double orc_guo(int i, double tau, const double u[3], const double f[3]);
+
+/* Eqs. (lbmmomenta0), (lbmmomenta1): rho = sum f_i,
+ * rho u = sum c_i f_i + f/2 (dt = 1). */
+void orc_moments(const double fi[19], const double force[3], double *rho,
+                 double u[3]);
+
+/* One step of Eq. (lbequation) on the whole lattice: BGK collision with the
+ * Guo term, streaming periodic in x and y, moving-wall bounce-back at the
+ * half-way planes z = -1/2 (velocity -u_wall along x) and z = nz - 1/2
+ * (velocity +u_wall).  f, f_out: [19][cells]; force: [3][cells] or NULL. */
+int orc_lbm_step(int nx, int ny, int nz, double tau, double u_wall,
+                 const double *f, const double *force, double *f_out);
+
+/* Equilibrium populations of the linear Couette profile
+ * u_x(z) = (2 u_wall / nz) (z - (nz - 1)/2), rho = 1. */
+void orc_init_couette(int nx, int ny, int nz, double u_wall, double *f);
+
+/* ---- ibm.c : Sec. II.C -------------------------------------------------- */
+
+/* Eqs. (2point), (3point), (4point): phi_n(r), n = 2, 3, 4. */
+double orc_phi(int n, double r);
+
+/* First lattice index of the n-point stencil around coordinate x. */
+int orc_stencil_base(int n, double x);
+
+/* Eq. (forcespreading): force_out[3][cells] = sum_i F_i delta(X - x_i).
+ * force_out is overwritten (zeroed first). */
+int orc_spread(int nx, int ny, int nz, int n, int n_nodes, const double *x,
+               const double *F, double *force_out);
+
+/* Eq. (velocityinterpolation): u_out[i] = sum_X u(X) delta(X - x_i),
+ * u_field [3][cells]. */
+int orc_interpolate(int nx, int ny, int nz, int n, int n_nodes,
+                    const double *x, const double *u_field, double *u_out);
+
+/* ---- membrane.c : Sec. II.B ---------------------------------------------- */
+
+/* Energy A0 w^S of one face, Eqs. (constitutivelaw) and (c)-(lambda1);
+ * X0, x: the three corners [3][3] in the reference and current state. */
+double orc_face_energy(const double X0[9], const double x[9], double ks,
+                       double ka);
+
+/* Same energy and the corner forces F = -dW/dx (Eq. forcefromenergy). */
+double orc_face_forces(const double X0[9], const double x[9], double ks,
+                       double ka, double F[9]);
+
+/* Total energy and node forces of one membrane; F [n][3] is overwritten. */
+double orc_membrane_forces(int n_nodes, const double *X0, const double *x,
+                           int n_tri, const int *tri, double ks, double ka,
+                           double *F);
+
+/* Invariants (I1, I2) of one face, from the a, b, c route. */
+void orc_face_invariants(const double X0[9], const double x[9], double *I1,
+                         double *I2);
+
+/* ---- mesh.c : Sec. II.D --------------------------------------------------- */
+
+/* Icosahedron subdivided m times, radius r, centre c.  nodes: room for
+ * 10*4^m + 2 nodes [n][3]; tri: room for 20*4^m faces [f][3].
+ * Returns the node count. */
+int orc_icosphere(int m, double r, const double c[3], double *nodes, int *tri);
+
+/* ---- taylor.c : Sec. III ------------------------------------------------- */
+
+/* Volume, area, centroid and inertia tensor of a closed membrane, and the
+ * Taylor deformation and inclination derived from them.  out[16] =
+ * {D, theta, r_a, r_b, r_c, V, A, c_x, c_y, c_z,
+ *  I_xx, I_yy, I_zz, I_xy, I_xz, I_yz}. */
+int orc_taylor(int n_nodes, const double *x, int n_tri, const int *tri,
+               double out[16]);
+
+/* Symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations: eigenvalues
+ * ascending, eigenvectors in the columns of vec. */
+void orc_eig3(const double A[9], double eval[3], double vec[9]);
+
+/* ---- sim.c : Sec. II.C sub-step list ------------------------------------- */
+
+typedef struct orc_sim orc_sim;
+
+orc_sim *orc_sim_create(int nx, int ny, int nz, double tau, int delta_n,
+                        double u_wall);
+void orc_sim_destroy(orc_sim *s);
+/* Adds a membrane; the current shape starts equal to the reference shape.
+ * Returns the capsule id (>= 0) or a negative error. */
+int orc_sim_add_capsule(orc_sim *s, int n_nodes, const double *X0, int n_tri,
+                        const int *tri, double ks, double ka);
+int orc_sim_n_nodes(const orc_sim *s);
+void orc_sim_init_couette(orc_sim *s);
+/* n_steps of the sub-step list: forces, spread, LBM, interpolate, advect. */
+int orc_sim_step(orc_sim *s, int n_steps);
+void orc_sim_get_f(const orc_sim *s, double *f);
+void orc_sim_set_f(orc_sim *s, const double *f);
+void orc_sim_get_nodes(const orc_sim *s, double *x);
+void orc_sim_set_nodes(orc_sim *s, const double *x);
+/* Last spread force density f(X, t) [3][cells]. */
+void orc_sim_get_force_field(const orc_sim *s, double *force);
+/* Node forces F_i(t) and interpolated velocities u_i(t+1) of the last step. */
+void orc_sim_get_node_forces(const orc_sim *s, double *F);
+void orc_sim_get_node_velocities(const orc_sim *s, double *u);
+/* rho and u = (sum c f + f_last/2)/rho of the current populations. */
+void orc_sim_get_density(const orc_sim *s, double *rho);
+void orc_sim_get_velocity(const orc_sim *s, double *u);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
