@@ -1,0 +1,212 @@
+/*
+ * iblbm.h -- C ABI of the GB300 (sm_103a) implementation of the combined
+ * immersed-boundary lattice-Boltzmann finite-element (IB-LBM-FEM) time step of
+ * Krueger, Varnik and Raabe (arXiv:1004.2416), used to simulate deformable
+ * capsules in simple shear flow.
+ *
+ * One simulation object holds a D3Q19 lattice of nx*ny*nz fluid cells
+ * (periodic in x and y, bounded by half-way bounce-back walls at
+ * z = -1/2 and z = nz - 1/2 that move along x with -u_wall and +u_wall) and
+ * any number of closed triangulated membranes (capsules).  All state lives in
+ * the memory of the CUDA device that was current when the object was created.
+ *
+ * General conventions
+ *   - Every call returns an iblbm_status (0 = success).  On failure
+ *     iblbm_last_error() gives a message.  No call traps, aborts or throws.
+ *   - Calls are asynchronous on the stream given to iblbm_create() except the
+ *     getters, setters and iblbm_sync(), which synchronise that stream.
+ *     Errors raised inside kernels (a stencil crossing a wall, a non-finite or
+ *     runaway density) are recorded in a device status word and returned by
+ *     the next synchronising call.
+ *   - Lattice cell (x, y, z) has linear index x + nx*(y + ny*z).  Scalar
+ *     fields are [nz][ny][nx], vector fields [3][nz][ny][nx], population
+ *     fields [19][nz][ny][nx], all double precision on the host side.
+ *   - Membrane node arrays are [n][3] doubles (x, y, z per node), node
+ *     coordinates are unwrapped (not reduced modulo the periodic box).
+ *   - Lattice units: dx = dt = 1, c_s^2 = 1/3, rest density 1.
+ *   - The library owns all device memory it allocates; the caller owns every
+ *     host buffer passed in.  Host buffers are only accessed during the call.
+ *   - Objects are not thread-safe: one thread at a time per object.
+ */
+#ifndef IBLBM_H
+#define IBLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct iblbm_sim iblbm_sim;
+
+typedef enum {
+    IBLBM_OK = 0,
+    IBLBM_ERR_ARG = -1,      /* invalid argument or size */
+    IBLBM_ERR_OOM = -2,      /* device or host allocation failed */
+    IBLBM_ERR_CUDA = -3,     /* a CUDA runtime call failed */
+    IBLBM_ERR_UNSTABLE = -4, /* density left (0.5, 2) or became NaN */
+    IBLBM_ERR_STENCIL = -5,  /* an IBM stencil cell lies beyond a wall */
+    IBLBM_ERR_TIMEOUT = -6,  /* a bounded device wait gave up */
+    IBLBM_ERR_STATE = -7     /* call not valid in the current state */
+} iblbm_status;
+
+/* Storage precision of the populations.
+ *   IBLBM_FP64: populations, arithmetic and node positions in double.
+ *   IBLBM_FP32: populations stored as float deviations from the rest
+ *               equilibrium f_i - w_i, float arithmetic, node positions as
+ *               unevaluated float pairs (hi + lo).
+ *   IBLBM_FP16: as IBLBM_FP32 but the deviations stored as scaled halves. */
+typedef enum { IBLBM_FP64 = 0, IBLBM_FP32 = 1, IBLBM_FP16 = 2 } iblbm_precision;
+
+/* Optional device allocator (for instance a caching allocator of the
+ * caller's framework).  alloc returns device memory of at least `bytes`
+ * bytes usable on `stream`, or NULL; free releases it. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *ctx);
+    void (*free)(void *ptr, void *stream, void *ctx);
+    void *ctx;
+} iblbm_allocator;
+
+typedef struct {
+    int nx, ny, nz;
+    int precision;     /* iblbm_precision */
+    int delta_points;  /* 2, 3 or 4 */
+    int n_capsules;
+    int n_nodes;       /* all capsules */
+    int n_faces;       /* all capsules */
+    int64_t step;      /* completed time steps */
+    double tau;
+    double u_wall;
+} iblbm_info;
+
+/* ---- life cycle ---------------------------------------------------------- */
+
+/* Creates a lattice of nx*ny*nz cells with BGK relaxation time tau
+ * (Eq. lbequation, Sec. II.A; tau > 1/2), the given population precision and
+ * the n-point discrete delta function of Eqs. (2point)-(4point) (Sec. II.C,
+ * delta_points = 2, 3 or 4).  stream: a cudaStream_t (NULL = legacy default
+ * stream); alloc: NULL for cudaMalloc.  The fluid starts at rest at
+ * density 1 with resting walls.  Limits: 1 <= nx, ny, nz and
+ * nx*ny*nz <= 2^31 - 1.  *out is NULL on failure. */
+int iblbm_create(iblbm_sim **out, int nx, int ny, int nz, double tau,
+                 int precision, int delta_points, void *stream,
+                 const iblbm_allocator *alloc);
+
+/* Frees all device and host memory of the object (NULL is accepted). */
+int iblbm_destroy(iblbm_sim *sim);
+
+/* Message of the last failure on this object ("" if none).  With sim ==
+ * NULL, the message of the last failed iblbm_create in this thread. */
+const char *iblbm_last_error(const iblbm_sim *sim);
+
+/* Static name of a status code. */
+const char *iblbm_status_string(int status);
+
+int iblbm_get_info(const iblbm_sim *sim, iblbm_info *out);
+
+/* ---- configuration ------------------------------------------------------- */
+
+/* Simple shear by moving walls (Sec. II.A, after Eq. lbmmomenta1): the wall
+ * at z = nz - 1/2 moves with +u_wall along x, the wall at z = -1/2 with
+ * -u_wall, so the shear rate is 2 u_wall / nz.  Uses Ladd's moving-wall
+ * bounce-back with the rest density 1. */
+int iblbm_set_shear_walls(iblbm_sim *sim, double u_wall);
+
+/* Adds a spherical capsule meshed by icosahedron subdivision (Sec. II.D,
+ * Fig. subdivision): 20*4^m faces and 10*4^m + 2 nodes, 0 <= m <= 7, on a
+ * sphere of the given radius around (cx, cy, cz).  The node and face order is
+ * the library's canonical order (documented with the design).  The reference
+ * shape is the initial shape, with k_s = k_alpha = 0 until iblbm_set_skalak.
+ * *capsule_id receives the new id (0, 1, ...). */
+int iblbm_add_capsule_icosphere(iblbm_sim *sim, double cx, double cy,
+                                double cz, double radius, int subdivisions,
+                                int *capsule_id);
+
+/* Adds a capsule from a closed triangle mesh: ref_xyz [n_nodes][3] is both
+ * the reference and the initial shape, tri [n_tri][3] node indices
+ * (0-based, counter-clockwise seen from outside).  A node may belong to at
+ * most 32 faces. */
+int iblbm_add_capsule_mesh(iblbm_sim *sim, const double *ref_xyz, int n_nodes,
+                           const int32_t *tri, int n_tri, int *capsule_id);
+
+/* Skalak law, Eq. (constitutivelaw) (Sec. II.B): shear modulus k_s and
+ * area-dilation modulus k_alpha = C k_s.  capsule_id = -1 sets every capsule.
+ * The reduced shear rate of Sec. III is G = shear_rate * eta * r / k_s with
+ * eta = (tau - 1/2)/3. */
+int iblbm_set_skalak(iblbm_sim *sim, int capsule_id, double k_s, double C);
+
+/* Initial fluid state.  mode 0: rest (f_i = w_i).  mode 1: equilibrium of the
+ * linear Couette profile u_x(z) = (2 u_wall / nz)(z - (nz - 1)/2) at density
+ * 1 (the state reached by simple shear between the walls).  Also clears the
+ * force density and the step counter. */
+int iblbm_init_fluid(iblbm_sim *sim, int mode);
+
+/* ---- time stepping --------------------------------------------------------- */
+
+/* Advances n_steps >= 0 time steps, each the sub-step list at the end of
+ * Sec. II.C: membrane forces from the current node positions (Sec. II.B,
+ * Eq. forcefromenergy), spreading (Eq. forcespreading), one collide-and-stream
+ * step with Guo forcing (Eqs. lbequation, equilibrium, latticeforce,
+ * lbmmomenta0/1), interpolation of the new lattice velocity at the old node
+ * positions (Eq. velocityinterpolation) and Euler advection
+ * (Eq. positionupdate).  The lattice velocity that is interpolated is
+ * (sum_i c_i f_i(t+1) + f(t)/2) / rho(t+1).  Asynchronous. */
+int iblbm_step(iblbm_sim *sim, int64_t n_steps);
+
+/* Waits for the stream and returns the first device error recorded since the
+ * last call that returned it (then clears it). */
+int iblbm_sync(iblbm_sim *sim);
+
+/* Host-only utility, needs no device: the canonical icosphere used by
+ * iblbm_add_capsule_icosphere (Sec. II.D) -- node coordinates nodes_out
+ * [10*4^m + 2][3] and faces tri_out [20*4^m][3] (either may be NULL). */
+int iblbm_icosphere(int subdivisions, double radius, const double center[3],
+                    double *nodes_out, int32_t *tri_out);
+
+/* ---- read-back and state access (synchronising) ------------------------------ */
+
+/* Lattice velocity u = (sum_i c_i f_i + f/2)/rho of the current populations
+ * with the force density of the last step (Eq. lbmmomenta1), [3][nz][ny][nx]. */
+int iblbm_get_velocity(iblbm_sim *sim, double *host_out);
+
+/* Density rho = sum_i f_i (Eq. lbmmomenta0), [nz][ny][nx]. */
+int iblbm_get_density(iblbm_sim *sim, double *host_out);
+
+/* Full populations f_i (not deviations), [19][nz][ny][nx], velocity i as in
+ * Fig. d3q19. */
+int iblbm_get_populations(iblbm_sim *sim, double *host_out);
+int iblbm_set_populations(iblbm_sim *sim, const double *host_in);
+
+/* Force density f(X, t) spread in the last step (Eq. forcespreading),
+ * [3][nz][ny][nx]; zero before the first step. */
+int iblbm_get_force_field(iblbm_sim *sim, double *host_out);
+
+/* Node positions [n][3] of one capsule (capsule_id >= 0) or of all capsules
+ * in id order (capsule_id = -1). */
+int iblbm_get_nodes(iblbm_sim *sim, int capsule_id, double *host_out);
+int iblbm_set_nodes(iblbm_sim *sim, int capsule_id, const double *host_in);
+
+/* Node forces F_i(t) of the last step (Eq. forcefromenergy) and node
+ * velocities u_i(t+1) of the last step (Eq. velocityinterpolation), [n][3]. */
+int iblbm_get_node_forces(iblbm_sim *sim, int capsule_id, double *host_out);
+int iblbm_get_node_velocities(iblbm_sim *sim, int capsule_id, double *host_out);
+
+/* Node and face counts of one capsule and its faces [n_tri][3]
+ * (tri_out may be NULL). */
+int iblbm_get_mesh(iblbm_sim *sim, int capsule_id, int *n_nodes, int *n_tri,
+                   int32_t *tri_out);
+
+/* Shape of one capsule (Sec. III): out[16] = {D, theta, r_a, r_b, r_c, V, A,
+ * c_x, c_y, c_z, I_xx, I_yy, I_zz, I_xy, I_xz, I_yz}.  V, A, centroid c and
+ * the inertia tensor I of the paper's face sum about c are reduced in double
+ * precision on the device; I/V is diagonalised on the host; r_a >= r_b >= r_c
+ * are the semi-axes of the ellipsoid with the same tensor,
+ * D = (r_a - r_c)/(r_a + r_c) the Taylor deformation, theta the angle of the
+ * major axis in the xz plane, from +x toward +z. */
+int iblbm_get_taylor(iblbm_sim *sim, int capsule_id, double out[16]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

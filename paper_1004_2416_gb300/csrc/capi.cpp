@@ -1,0 +1,807 @@
+// capi.cpp -- the C ABI of include/iblbm.h: simulation object, device memory,
+// membrane tables, the time-step sequence (captured in CUDA graphs) and the
+// read-back paths.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "iblbm.h"
+#include "internal.h"
+
+using namespace iblbm;
+
+namespace {
+
+struct Capsule {
+    int node0, n_nodes, face0, n_faces;
+    double ks, ka;
+    double origin[3];  // reference centre (mean of the reference nodes)
+};
+
+constexpr int kGraphSteps = 16;  // steps per captured graph (even)
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct iblbm_sim {
+    Lattice L{};
+    int prec = 1;
+    int delta = 3;
+    double tau = 1.0;
+    double u_wall = 0.0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    iblbm_allocator alloc{};
+    bool has_alloc = false;
+    size_t pop_bytes = 0;  // one population buffer
+    size_t vec_bytes = 0;  // one force buffer
+    void *pop[2] = {nullptr, nullptr};
+    int cur = 0;  // pop[cur] holds f(t); force[cur] the last spread force
+    void *force[2] = {nullptr, nullptr};
+    uint8_t *flags[2] = {nullptr, nullptr};
+    int *d_status = nullptr;
+
+    std::vector<Capsule> caps;
+    std::vector<double> X0;  // reference nodes [n][3]
+    std::vector<int> tri;    // faces [f][3], global node indices
+    bool mesh_dirty = false;
+    int dev_nodes = 0;  // nodes present in the device arrays
+    MeshDev mesh{};
+    std::vector<void *> mesh_allocs;
+    TaylorPlan plan{};
+    std::vector<void *> plan_allocs;
+
+    double *d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t steps = 0;
+    std::string err;
+};
+
+namespace {
+
+int fail(iblbm_sim *s, int code, const std::string &msg) {
+    if (s) s->err = msg;
+    return code;
+}
+
+int cuda_fail(iblbm_sim *s, cudaError_t e, const char *what) {
+    return fail(s, IBLBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail(s, e_, #call);     \
+    } while (0)
+
+void *dev_alloc(iblbm_sim *s, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (s->has_alloc) {
+        p = s->alloc.alloc(bytes, (void *)s->stream, s->alloc.ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+void dev_free(iblbm_sim *s, void *p) {
+    if (!p) return;
+    if (s->has_alloc) s->alloc.free(p, (void *)s->stream, s->alloc.ctx);
+    else cudaFree(p);
+}
+
+void drop_graphs(iblbm_sim *s) {
+    for (int k = 0; k < 2; ++k)
+        if (s->graph[k]) {
+            cudaGraphExecDestroy(s->graph[k]);
+            s->graph[k] = nullptr;
+        }
+}
+
+int ensure_scratch(iblbm_sim *s, size_t bytes) {
+    if (s->scratch_bytes >= bytes) return IBLBM_OK;
+    dev_free(s, s->d_scratch);
+    s->d_scratch = (double *)dev_alloc(s, bytes);
+    s->scratch_bytes = s->d_scratch ? bytes : 0;
+    if (!s->d_scratch) return fail(s, IBLBM_ERR_OOM, "scratch allocation failed");
+    return IBLBM_OK;
+}
+
+size_t real_bytes(const iblbm_sim *s) { return s->prec == kF64 ? 8 : 4; }
+
+// (Re)builds the device membrane tables after capsules were added.  Current
+// node positions of existing capsules are kept.
+int ensure_mesh(iblbm_sim *s) {
+    if (!s->mesh_dirty) return IBLBM_OK;
+    const int nn = (int)(s->X0.size() / 3), nf = (int)(s->tri.size() / 3), nc = (int)s->caps.size();
+    std::vector<double> xcur(s->X0);
+    if (s->dev_nodes > 0) {
+        int rc = ensure_scratch(s, sizeof(double) * 3 * s->dev_nodes);
+        if (rc) return rc;
+        launch_nodes_to_f64(s->prec, s->mesh, 0, 0, s->dev_nodes, s->d_scratch, s->stream);
+        CK(cudaMemcpyAsync(xcur.data(), s->d_scratch, sizeof(double) * 3 * s->dev_nodes,
+                           cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+    }
+    for (void *p : s->mesh_allocs) dev_free(s, p);
+    s->mesh_allocs.clear();
+    for (void *p : s->plan_allocs) dev_free(s, p);
+    s->plan_allocs.clear();
+    drop_graphs(s);
+
+    const size_t rb = real_bytes(s);
+    const size_t v4 = 4 * rb;
+    auto A = [&](size_t bytes) {
+        void *p = dev_alloc(s, bytes);
+        if (p) s->mesh_allocs.push_back(p);
+        return p;
+    };
+    MeshDev m{};
+    m.n_nodes = nn;
+    m.n_faces = nf;
+    m.n_caps = nc;
+    m.x = A(v4 * nn);
+    m.x_lo = s->prec == kF64 ? nullptr : A(v4 * nn);
+    m.F = A(v4 * nn);
+    m.u = A(v4 * nn);
+    void *adj_off = A(sizeof(int) * (nn + 1));
+    void *adj = A(sizeof(int) * 3 * nf);
+    void *tri4 = A(sizeof(int) * 4 * nf);
+    void *fconst = A(v4 * nf);
+    void *A0 = A(rb * nf);
+    void *capmod = A(v4 * nc);
+    if (!m.x || (s->prec != kF64 && !m.x_lo) || !m.F || !m.u || !adj_off || !adj || !tri4 ||
+        !fconst || !A0 || !capmod)
+        return fail(s, IBLBM_ERR_OOM, "membrane table allocation failed");
+
+    // node -> (face, corner) lists in ascending face order
+    std::vector<int> off(nn + 1, 0), ent(3 * (size_t)nf);
+    for (int f = 0; f < nf; ++f)
+        for (int k = 0; k < 3; ++k) off[s->tri[3 * f + k] + 1]++;
+    for (int n = 0; n < nn; ++n) {
+        if (off[n + 1] > 32) return fail(s, IBLBM_ERR_ARG, "a node belongs to more than 32 faces");
+        off[n + 1] += off[n];
+    }
+    {
+        std::vector<int> fill(off.begin(), off.end() - 1);
+        for (int f = 0; f < nf; ++f)
+            for (int k = 0; k < 3; ++k) ent[fill[s->tri[3 * f + k]]++] = 4 * f + k;
+    }
+    std::vector<int> t4(4 * (size_t)nf);
+    std::vector<double> fc(4 * (size_t)nf), a0(nf), cm(4 * (size_t)nc, 0.0);
+    for (int c = 0; c < nc; ++c) {
+        const Capsule &cp = s->caps[c];
+        cm[4 * c] = cp.ks / 6.0;
+        cm[4 * c + 1] = cp.ka / 6.0;
+        for (int f = cp.face0; f < cp.face0 + cp.n_faces; ++f) t4[4 * f + 3] = c;
+    }
+    for (int f = 0; f < nf; ++f) {
+        const int a = s->tri[3 * f], b = s->tri[3 * f + 1], c = s->tri[3 * f + 2];
+        t4[4 * f] = a;
+        t4[4 * f + 1] = b;
+        t4[4 * f + 2] = c;
+        double U[3], V[3];
+        for (int k = 0; k < 3; ++k) {
+            U[k] = s->X0[3 * b + k] - s->X0[3 * a + k];
+            V[k] = s->X0[3 * c + k] - s->X0[3 * a + k];
+        }
+        const double G11 = U[0] * U[0] + U[1] * U[1] + U[2] * U[2];
+        const double G12 = U[0] * V[0] + U[1] * V[1] + U[2] * V[2];
+        const double G22 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
+        const double det = G11 * G22 - G12 * G12;
+        if (!(det > 0.0)) return fail(s, IBLBM_ERR_ARG, "degenerate reference face");
+        fc[4 * f] = G22 / det;      // alpha
+        fc[4 * f + 1] = G12 / det;  // beta
+        fc[4 * f + 2] = G11 / det;  // gamma
+        fc[4 * f + 3] = 1.0 / det;  // kappa
+        a0[f] = 0.5 * std::sqrt(det);
+    }
+    auto up_real = [&](void *dst, const std::vector<double> &v) -> cudaError_t {
+        if (s->prec == kF64)
+            return cudaMemcpyAsync(dst, v.data(), v.size() * 8, cudaMemcpyHostToDevice, s->stream);
+        std::vector<float> f(v.begin(), v.end());
+        cudaError_t e = cudaMemcpyAsync(dst, f.data(), f.size() * 4, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        return e;
+    };
+    CK(cudaMemcpyAsync(adj_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(adj, ent.data(), sizeof(int) * ent.size(), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(tri4, t4.data(), sizeof(int) * t4.size(), cudaMemcpyHostToDevice, s->stream));
+    CK(up_real(fconst, fc));
+    CK(up_real(A0, a0));
+    CK(up_real(capmod, cm));
+    CK(cudaMemsetAsync(m.F, 0, v4 * nn, s->stream));
+    CK(cudaMemsetAsync(m.u, 0, v4 * nn, s->stream));
+    m.adj_off = (const int *)adj_off;
+    m.adj = (const int *)adj;
+    m.tri = (const int *)tri4;
+    m.fconst = fconst;
+    m.A0 = A0;
+    m.capmod = capmod;
+    s->mesh = m;
+    // positions
+    {
+        int rc = ensure_scratch(s, sizeof(double) * 3 * std::max(nn, 1));
+        if (rc) return rc;
+        CK(cudaMemcpyAsync(s->d_scratch, xcur.data(), sizeof(double) * 3 * nn, cudaMemcpyHostToDevice,
+                           s->stream));
+        launch_f64_to_nodes(s->prec, s->mesh, 0, nn, s->d_scratch, s->stream);
+        CK(cudaGetLastError());
+    }
+    // Taylor plan: kTaylorFacesPerBlock faces per block
+    {
+        std::vector<int> bcap, bf0, bnf, cb0(nc + 1, 0);
+        std::vector<double> org(3 * (size_t)nc);
+        for (int c = 0; c < nc; ++c) {
+            const Capsule &cp = s->caps[c];
+            cb0[c] = (int)bcap.size();
+            for (int f = 0; f < cp.n_faces; f += kTaylorFacesPerBlock) {
+                bcap.push_back(c);
+                bf0.push_back(cp.face0 + f);
+                bnf.push_back(std::min(kTaylorFacesPerBlock, cp.n_faces - f));
+            }
+            for (int k = 0; k < 3; ++k) org[3 * c + k] = cp.origin[k];
+        }
+        cb0[nc] = (int)bcap.size();
+        const int nb = (int)bcap.size();
+        auto P = [&](size_t bytes) {
+            void *p = dev_alloc(s, bytes);
+            if (p) s->plan_allocs.push_back(p);
+            return p;
+        };
+        TaylorPlan p{};
+        p.n_caps = nc;
+        p.total_blocks = nb;
+        p.blk_cap = (const int *)P(sizeof(int) * nb);
+        p.blk_face0 = (const int *)P(sizeof(int) * nb);
+        p.blk_nface = (const int *)P(sizeof(int) * nb);
+        p.cap_blk0 = (const int *)P(sizeof(int) * (nc + 1));
+        p.origin = (const double *)P(sizeof(double) * 3 * nc);
+        p.partial = (double *)P(sizeof(double) * 16 * nb);
+        p.out = (double *)P(sizeof(double) * 12 * nc);
+        if (!p.blk_cap || !p.blk_face0 || !p.blk_nface || !p.cap_blk0 || !p.origin || !p.partial || !p.out)
+            return fail(s, IBLBM_ERR_OOM, "Taylor plan allocation failed");
+        CK(cudaMemcpyAsync((void *)p.blk_cap, bcap.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s->stream));
+        CK(cudaMemcpyAsync((void *)p.blk_face0, bf0.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s->stream));
+        CK(cudaMemcpyAsync((void *)p.blk_nface, bnf.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s->stream));
+        CK(cudaMemcpyAsync((void *)p.cap_blk0, cb0.data(), sizeof(int) * (nc + 1), cudaMemcpyHostToDevice, s->stream));
+        CK(cudaMemcpyAsync((void *)p.origin, org.data(), sizeof(double) * 3 * nc, cudaMemcpyHostToDevice, s->stream));
+        s->plan = p;
+    }
+    CK(cudaStreamSynchronize(s->stream));
+    s->dev_nodes = nn;
+    s->mesh_dirty = false;
+    return IBLBM_OK;
+}
+
+// One time step (sub-step list of Sec. II.C) enqueued on the stream.
+void enqueue_step(iblbm_sim *s) {
+    const int c = s->cur, n = 1 - s->cur;
+    launch_force_spread(s->prec, s->delta, s->L, s->mesh, s->force[n], s->flags[n], s->d_status,
+                        s->stream);
+    CollideArgs a;
+    a.src = s->pop[c];
+    a.dst = s->pop[n];
+    a.fcur = s->force[n];
+    a.flag_cur = s->flags[n];
+    a.fold = s->force[c];
+    a.flag_old = s->flags[c];
+    a.tau = s->tau;
+    a.u_wall = s->u_wall;
+    a.status = s->d_status;
+    launch_collide_stream(s->prec, s->L, a, s->stream);
+    launch_interp_advect(s->prec, s->delta, s->L, s->mesh, s->pop[n], s->force[n], s->stream);
+    s->cur = n;
+}
+
+int check_sim(const iblbm_sim *s) { return s ? IBLBM_OK : IBLBM_ERR_ARG; }
+
+int status_from_bits(int bits) {
+    if (bits & 1) return IBLBM_ERR_UNSTABLE;
+    if (bits & 2) return IBLBM_ERR_STENCIL;
+    return IBLBM_OK;
+}
+
+int sync_status(iblbm_sim *s) {
+    CK(cudaSetDevice(s->device));
+    CK(cudaStreamSynchronize(s->stream));
+    int bits = 0;
+    CK(cudaMemcpy(&bits, s->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (bits) {
+        CK(cudaMemset(s->d_status, 0, sizeof(int)));
+        int rc = status_from_bits(bits);
+        return fail(s, rc, rc == IBLBM_ERR_UNSTABLE
+                               ? "density left (0.5, 2) or became non-finite"
+                               : "an IBM stencil cell lies beyond a wall (z < 0 or z >= nz)");
+    }
+    return IBLBM_OK;
+}
+
+int capsule_range(iblbm_sim *s, int id, int *first, int *count) {
+    if (id == -1) {
+        *first = 0;
+        *count = (int)(s->X0.size() / 3);
+        return IBLBM_OK;
+    }
+    if (id < 0 || id >= (int)s->caps.size()) return fail(s, IBLBM_ERR_ARG, "no such capsule");
+    *first = s->caps[id].node0;
+    *count = s->caps[id].n_nodes;
+    return IBLBM_OK;
+}
+
+int add_capsule(iblbm_sim *s, const double *xyz, int n_nodes, const int *tri, int n_tri, int *id) {
+    if (n_nodes < 4 || n_tri < 4 || !xyz || !tri) return fail(s, IBLBM_ERR_ARG, "bad mesh arguments");
+    for (int k = 0; k < 3 * n_tri; ++k)
+        if (tri[k] < 0 || tri[k] >= n_nodes) return fail(s, IBLBM_ERR_ARG, "face index out of range");
+    for (int k = 0; k < 3 * n_nodes; ++k)
+        if (!std::isfinite(xyz[k])) return fail(s, IBLBM_ERR_ARG, "non-finite node coordinate");
+    Capsule c{};
+    c.node0 = (int)(s->X0.size() / 3);
+    c.n_nodes = n_nodes;
+    c.face0 = (int)(s->tri.size() / 3);
+    c.n_faces = n_tri;
+    c.ks = 0.0;
+    c.ka = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        double m = 0.0;
+        for (int n = 0; n < n_nodes; ++n) m += xyz[3 * n + k];
+        c.origin[k] = m / n_nodes;
+    }
+    s->X0.insert(s->X0.end(), xyz, xyz + 3 * (size_t)n_nodes);
+    for (int k = 0; k < 3 * n_tri; ++k) s->tri.push_back(tri[k] + c.node0);
+    s->caps.push_back(c);
+    s->mesh_dirty = true;
+    if (id) *id = (int)s->caps.size() - 1;
+    return IBLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *iblbm_status_string(int status) {
+    switch (status) {
+        case IBLBM_OK: return "IBLBM_OK";
+        case IBLBM_ERR_ARG: return "IBLBM_ERR_ARG";
+        case IBLBM_ERR_OOM: return "IBLBM_ERR_OOM";
+        case IBLBM_ERR_CUDA: return "IBLBM_ERR_CUDA";
+        case IBLBM_ERR_UNSTABLE: return "IBLBM_ERR_UNSTABLE";
+        case IBLBM_ERR_STENCIL: return "IBLBM_ERR_STENCIL";
+        case IBLBM_ERR_TIMEOUT: return "IBLBM_ERR_TIMEOUT";
+        case IBLBM_ERR_STATE: return "IBLBM_ERR_STATE";
+        default: return "IBLBM_ERR_UNKNOWN";
+    }
+}
+
+const char *iblbm_last_error(const iblbm_sim *s) {
+    return s ? s->err.c_str() : g_create_error.c_str();
+}
+
+int iblbm_create(iblbm_sim **out, int nx, int ny, int nz, double tau, int precision,
+                 int delta_points, void *stream, const iblbm_allocator *alloc) {
+    if (!out) return IBLBM_ERR_ARG;
+    *out = nullptr;
+    g_create_error.clear();
+    if (nx < 1 || ny < 1 || nz < 1 || (long long)nx * ny * nz > 2147483647LL) {
+        g_create_error = "lattice dimensions out of range";
+        return IBLBM_ERR_ARG;
+    }
+    if (!(tau > 0.5) || !std::isfinite(tau)) {
+        g_create_error = "tau must exceed 1/2";
+        return IBLBM_ERR_ARG;
+    }
+    if (precision < 0 || precision > 2 || delta_points < 2 || delta_points > 4) {
+        g_create_error = "precision must be 0..2 and delta_points 2..4";
+        return IBLBM_ERR_ARG;
+    }
+    if (alloc && (!alloc->alloc || !alloc->free)) {
+        g_create_error = "allocator needs both alloc and free";
+        return IBLBM_ERR_ARG;
+    }
+    iblbm_sim *s = new (std::nothrow) iblbm_sim();
+    if (!s) return IBLBM_ERR_OOM;
+    s->L = make_lattice(nx, ny, nz);
+    s->prec = precision;
+    s->delta = delta_points;
+    s->tau = tau;
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        cudaGetLastError();
+        g_create_error = "no CUDA device";
+        delete s;
+        return IBLBM_ERR_CUDA;
+    }
+    if (alloc) {
+        s->alloc = *alloc;
+        s->has_alloc = true;
+    }
+    if (stream) {
+        s->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            g_create_error = "cudaStreamCreate failed";
+            delete s;
+            return IBLBM_ERR_CUDA;
+        }
+        s->own_stream = true;
+    }
+    const size_t el = precision == kF64 ? 8 : (precision == kF32 ? 4 : 2);
+    s->pop_bytes = 19 * el * (size_t)s->L.ncell;
+    s->vec_bytes = 4 * real_bytes(s) * (size_t)s->L.ncell;
+    bool ok = true;
+    for (int k = 0; k < 2 && ok; ++k) {
+        s->pop[k] = dev_alloc(s, s->pop_bytes);
+        s->force[k] = dev_alloc(s, s->vec_bytes);
+        s->flags[k] = (uint8_t *)dev_alloc(s, (size_t)s->L.ntiles);
+        ok = s->pop[k] && s->force[k] && s->flags[k];
+    }
+    s->d_status = (int *)dev_alloc(s, sizeof(int));
+    ok = ok && s->d_status;
+    if (!ok) {
+        g_create_error = "device allocation failed";
+        iblbm_destroy(s);
+        return IBLBM_ERR_OOM;
+    }
+    for (int k = 0; k < 2; ++k) {
+        cudaMemsetAsync(s->force[k], 0, s->vec_bytes, s->stream);
+        cudaMemsetAsync(s->flags[k], 0, (size_t)s->L.ntiles, s->stream);
+    }
+    cudaMemsetAsync(s->d_status, 0, sizeof(int), s->stream);
+    launch_init_fluid(s->prec, s->L, s->pop[0], 0, 0.0, s->stream);
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        g_create_error = std::string("initialisation failed: ") + cudaGetErrorString(e);
+        iblbm_destroy(s);
+        return IBLBM_ERR_CUDA;
+    }
+    *out = s;
+    return IBLBM_OK;
+}
+
+int iblbm_destroy(iblbm_sim *s) {
+    if (!s) return IBLBM_OK;
+    cudaSetDevice(s->device);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    drop_graphs(s);
+    for (int k = 0; k < 2; ++k) {
+        dev_free(s, s->pop[k]);
+        dev_free(s, s->force[k]);
+        dev_free(s, s->flags[k]);
+    }
+    dev_free(s, s->d_status);
+    dev_free(s, s->d_scratch);
+    for (void *p : s->mesh_allocs) dev_free(s, p);
+    for (void *p : s->plan_allocs) dev_free(s, p);
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+    return IBLBM_OK;
+}
+
+int iblbm_get_info(const iblbm_sim *s, iblbm_info *out) {
+    if (!s || !out) return IBLBM_ERR_ARG;
+    out->nx = s->L.nx;
+    out->ny = s->L.ny;
+    out->nz = s->L.nz;
+    out->precision = s->prec;
+    out->delta_points = s->delta;
+    out->n_capsules = (int)s->caps.size();
+    out->n_nodes = (int)(s->X0.size() / 3);
+    out->n_faces = (int)(s->tri.size() / 3);
+    out->step = s->steps;
+    out->tau = s->tau;
+    out->u_wall = s->u_wall;
+    return IBLBM_OK;
+}
+
+int iblbm_set_shear_walls(iblbm_sim *s, double u_wall) {
+    if (!s) return IBLBM_ERR_ARG;
+    if (!std::isfinite(u_wall) || std::fabs(u_wall) > 0.3)
+        return fail(s, IBLBM_ERR_ARG, "wall speed must be finite and |u_wall| <= 0.3");
+    s->u_wall = u_wall;
+    drop_graphs(s);
+    return IBLBM_OK;
+}
+
+int iblbm_add_capsule_icosphere(iblbm_sim *s, double cx, double cy, double cz, double radius,
+                                int subdivisions, int *capsule_id) {
+    if (!s) return IBLBM_ERR_ARG;
+    if (subdivisions < 0 || subdivisions > 7 || !(radius > 0.0) || !std::isfinite(radius))
+        return fail(s, IBLBM_ERR_ARG, "subdivisions must be 0..7 and radius positive");
+    std::vector<double> nodes;
+    std::vector<int> tri;
+    const double c[3] = {cx, cy, cz};
+    icosphere(subdivisions, radius, c, nodes, tri);
+    return add_capsule(s, nodes.data(), (int)(nodes.size() / 3), tri.data(), (int)(tri.size() / 3),
+                       capsule_id);
+}
+
+int iblbm_icosphere(int subdivisions, double radius, const double center[3], double *nodes_out,
+                    int32_t *tri_out) {
+    if (subdivisions < 0 || subdivisions > 7 || !(radius > 0.0) || !std::isfinite(radius) || !center)
+        return IBLBM_ERR_ARG;
+    std::vector<double> nodes;
+    std::vector<int> tri;
+    icosphere(subdivisions, radius, center, nodes, tri);
+    if (nodes_out) std::memcpy(nodes_out, nodes.data(), sizeof(double) * nodes.size());
+    if (tri_out)
+        for (size_t k = 0; k < tri.size(); ++k) tri_out[k] = tri[k];
+    return IBLBM_OK;
+}
+
+int iblbm_add_capsule_mesh(iblbm_sim *s, const double *ref_xyz, int n_nodes, const int32_t *tri,
+                           int n_tri, int *capsule_id) {
+    if (!s) return IBLBM_ERR_ARG;
+    return add_capsule(s, ref_xyz, n_nodes, (const int *)tri, n_tri, capsule_id);
+}
+
+int iblbm_set_skalak(iblbm_sim *s, int capsule_id, double k_s, double C) {
+    if (!s) return IBLBM_ERR_ARG;
+    if (!(k_s >= 0.0) || !(C >= 0.0) || !std::isfinite(k_s) || !std::isfinite(C))
+        return fail(s, IBLBM_ERR_ARG, "moduli must be finite and non-negative");
+    if (capsule_id < -1 || capsule_id >= (int)s->caps.size())
+        return fail(s, IBLBM_ERR_ARG, "no such capsule");
+    for (int c = 0; c < (int)s->caps.size(); ++c)
+        if (capsule_id == -1 || capsule_id == c) {
+            s->caps[c].ks = k_s;
+            s->caps[c].ka = C * k_s;
+        }
+    if (s->mesh_dirty) return IBLBM_OK;  // uploaded with the tables
+    CK(cudaSetDevice(s->device));
+    const int nc = (int)s->caps.size();
+    if (s->prec == kF64) {
+        std::vector<double> cm(4 * (size_t)nc, 0.0);
+        for (int c = 0; c < nc; ++c) {
+            cm[4 * c] = s->caps[c].ks / 6.0;
+            cm[4 * c + 1] = s->caps[c].ka / 6.0;
+        }
+        CK(cudaMemcpyAsync((void *)s->mesh.capmod, cm.data(), cm.size() * 8, cudaMemcpyHostToDevice, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+    } else {
+        std::vector<float> cm(4 * (size_t)nc, 0.0f);
+        for (int c = 0; c < nc; ++c) {
+            cm[4 * c] = (float)(s->caps[c].ks / 6.0);
+            cm[4 * c + 1] = (float)(s->caps[c].ka / 6.0);
+        }
+        CK(cudaMemcpyAsync((void *)s->mesh.capmod, cm.data(), cm.size() * 4, cudaMemcpyHostToDevice, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+    }
+    return IBLBM_OK;
+}
+
+int iblbm_init_fluid(iblbm_sim *s, int mode) {
+    if (!s) return IBLBM_ERR_ARG;
+    if (mode != 0 && mode != 1) return fail(s, IBLBM_ERR_ARG, "mode must be 0 or 1");
+    CK(cudaSetDevice(s->device));
+    s->cur = 0;
+    launch_init_fluid(s->prec, s->L, s->pop[0], mode, s->u_wall, s->stream);
+    for (int k = 0; k < 2; ++k) {
+        CK(cudaMemsetAsync(s->force[k], 0, s->vec_bytes, s->stream));
+        CK(cudaMemsetAsync(s->flags[k], 0, (size_t)s->L.ntiles, s->stream));
+    }
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s->stream));
+    s->steps = 0;
+    return IBLBM_OK;
+}
+
+int iblbm_step(iblbm_sim *s, int64_t n_steps) {
+    if (!s) return IBLBM_ERR_ARG;
+    if (n_steps < 0) return fail(s, IBLBM_ERR_ARG, "negative step count");
+    CK(cudaSetDevice(s->device));
+    int rc = ensure_mesh(s);
+    if (rc) return rc;
+    int64_t left = n_steps;
+    while (left >= kGraphSteps) {
+        cudaGraphExec_t &g = s->graph[s->cur];
+        if (!g) {
+            cudaGraph_t graph = nullptr;
+            const int cur0 = s->cur;
+            CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+            for (int k = 0; k < kGraphSteps; ++k) enqueue_step(s);
+            cudaError_t e = cudaStreamEndCapture(s->stream, &graph);
+            s->cur = cur0;
+            if (e != cudaSuccess) return cuda_fail(s, e, "graph capture");
+            e = cudaGraphInstantiate(&g, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) {
+                g = nullptr;
+                return cuda_fail(s, e, "graph instantiation");
+            }
+        }
+        CK(cudaGraphLaunch(g, s->stream));
+        left -= kGraphSteps;  // kGraphSteps is even: parity unchanged
+        s->steps += kGraphSteps;
+    }
+    for (; left > 0; --left) {
+        enqueue_step(s);
+        s->steps++;
+    }
+    CK(cudaGetLastError());
+    return IBLBM_OK;
+}
+
+int iblbm_sync(iblbm_sim *s) {
+    if (!s) return IBLBM_ERR_ARG;
+    return sync_status(s);
+}
+
+int iblbm_get_velocity(iblbm_sim *s, double *host_out) {
+    if (!s || !host_out) return IBLBM_ERR_ARG;
+    int rc = sync_status(s);
+    if (rc) return rc;
+    const size_t n = (size_t)s->L.ncell;
+    rc = ensure_scratch(s, sizeof(double) * 3 * n);
+    if (rc) return rc;
+    launch_moments(s->prec, s->L, s->pop[s->cur], s->force[s->cur], nullptr, s->d_scratch, s->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(host_out, s->d_scratch, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return IBLBM_OK;
+}
+
+int iblbm_get_density(iblbm_sim *s, double *host_out) {
+    if (!s || !host_out) return IBLBM_ERR_ARG;
+    int rc = sync_status(s);
+    if (rc) return rc;
+    const size_t n = (size_t)s->L.ncell;
+    rc = ensure_scratch(s, sizeof(double) * n);
+    if (rc) return rc;
+    launch_moments(s->prec, s->L, s->pop[s->cur], s->force[s->cur], s->d_scratch, nullptr, s->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(host_out, s->d_scratch, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return IBLBM_OK;
+}
+
+int iblbm_get_populations(iblbm_sim *s, double *host_out) {
+    if (!s || !host_out) return IBLBM_ERR_ARG;
+    int rc = sync_status(s);
+    if (rc) return rc;
+    const size_t n = 19 * (size_t)s->L.ncell;
+    rc = ensure_scratch(s, sizeof(double) * n);
+    if (rc) return rc;
+    launch_pop_to_f64(s->prec, s->L, s->pop[s->cur], s->d_scratch, s->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(host_out, s->d_scratch, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return IBLBM_OK;
+}
+
+int iblbm_set_populations(iblbm_sim *s, const double *host_in) {
+    if (!s || !host_in) return IBLBM_ERR_ARG;
+    int rc = sync_status(s);
+    if (rc) return rc;
+    const size_t n = 19 * (size_t)s->L.ncell;
+    for (size_t k = 0; k < n; ++k)
+        if (!std::isfinite(host_in[k])) return fail(s, IBLBM_ERR_ARG, "non-finite population");
+    rc = ensure_scratch(s, sizeof(double) * n);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(s->d_scratch, host_in, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
+    launch_f64_to_pop(s->prec, s->L, s->d_scratch, s->pop[s->cur], s->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s->stream));
+    return IBLBM_OK;
+}
+
+int iblbm_get_force_field(iblbm_sim *s, double *host_out) {
+    if (!s || !host_out) return IBLBM_ERR_ARG;
+    int rc = sync_status(s);
+    if (rc) return rc;
+    const size_t n = (size_t)s->L.ncell;
+    rc = ensure_scratch(s, sizeof(double) * 3 * n);
+    if (rc) return rc;
+    launch_force_to_f64(s->prec, s->L, s->force[s->cur], s->d_scratch, s->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(host_out, s->d_scratch, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return IBLBM_OK;
+}
+
+static int node_get(iblbm_sim *s, int id, int which, double *host_out) {
+    if (!s || !host_out) return IBLBM_ERR_ARG;
+    int rc = sync_status(s);
+    if (rc) return rc;
+    int first, count;
+    rc = capsule_range(s, id, &first, &count);
+    if (rc) return rc;
+    rc = ensure_mesh(s);
+    if (rc) return rc;
+    if (count == 0) return IBLBM_OK;
+    rc = ensure_scratch(s, sizeof(double) * 3 * count);
+    if (rc) return rc;
+    launch_nodes_to_f64(s->prec, s->mesh, which, first, count, s->d_scratch, s->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(host_out, s->d_scratch, sizeof(double) * 3 * count, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return IBLBM_OK;
+}
+
+int iblbm_get_nodes(iblbm_sim *s, int id, double *out) { return node_get(s, id, 0, out); }
+int iblbm_get_node_forces(iblbm_sim *s, int id, double *out) { return node_get(s, id, 1, out); }
+int iblbm_get_node_velocities(iblbm_sim *s, int id, double *out) { return node_get(s, id, 2, out); }
+
+int iblbm_set_nodes(iblbm_sim *s, int id, const double *host_in) {
+    if (!s || !host_in) return IBLBM_ERR_ARG;
+    int rc = sync_status(s);
+    if (rc) return rc;
+    int first, count;
+    rc = capsule_range(s, id, &first, &count);
+    if (rc) return rc;
+    for (int k = 0; k < 3 * count; ++k)
+        if (!std::isfinite(host_in[k])) return fail(s, IBLBM_ERR_ARG, "non-finite node coordinate");
+    rc = ensure_mesh(s);
+    if (rc) return rc;
+    if (count == 0) return IBLBM_OK;
+    rc = ensure_scratch(s, sizeof(double) * 3 * count);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(s->d_scratch, host_in, sizeof(double) * 3 * count, cudaMemcpyHostToDevice, s->stream));
+    launch_f64_to_nodes(s->prec, s->mesh, first, count, s->d_scratch, s->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s->stream));
+    return IBLBM_OK;
+}
+
+int iblbm_get_mesh(iblbm_sim *s, int id, int *n_nodes, int *n_tri, int32_t *tri_out) {
+    if (!s) return IBLBM_ERR_ARG;
+    if (id < 0 || id >= (int)s->caps.size()) return fail(s, IBLBM_ERR_ARG, "no such capsule");
+    const Capsule &c = s->caps[id];
+    if (n_nodes) *n_nodes = c.n_nodes;
+    if (n_tri) *n_tri = c.n_faces;
+    if (tri_out)
+        for (int k = 0; k < 3 * c.n_faces; ++k) tri_out[k] = s->tri[3 * c.face0 + k] - c.node0;
+    return IBLBM_OK;
+}
+
+int iblbm_get_taylor(iblbm_sim *s, int id, double out[16]) {
+    if (!s || !out) return IBLBM_ERR_ARG;
+    if (id < 0 || id >= (int)s->caps.size()) return fail(s, IBLBM_ERR_ARG, "no such capsule");
+    int rc = sync_status(s);
+    if (rc) return rc;
+    rc = ensure_mesh(s);
+    if (rc) return rc;
+    launch_taylor(s->prec, s->mesh, s->plan, s->stream);
+    CK(cudaGetLastError());
+    double r[12];
+    CK(cudaMemcpyAsync(r, s->plan.out + 12 * id, sizeof(r), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    const double V = r[0];
+    const double I[9] = {r[5], r[8], r[9], r[8], r[6], r[10], r[9], r[10], r[7]};
+    double J[9], val[3], vec[9];
+    for (int k = 0; k < 9; ++k) J[k] = I[k] / V;
+    sym_eig3(J, val, vec);
+    const double ra = std::sqrt(std::max(0.0, 2.5 * (val[1] + val[2] - val[0])));
+    const double rb = std::sqrt(std::max(0.0, 2.5 * (val[0] + val[2] - val[1])));
+    const double rc2 = std::sqrt(std::max(0.0, 2.5 * (val[0] + val[1] - val[2])));
+    double vx = vec[0], vz = vec[6];
+    if (vx < 0.0) {
+        vx = -vx;
+        vz = -vz;
+    }
+    out[0] = (ra - rc2) / (ra + rc2);
+    out[1] = std::atan2(vz, vx);
+    out[2] = ra;
+    out[3] = rb;
+    out[4] = rc2;
+    out[5] = V;
+    out[6] = r[1];
+    out[7] = r[2];
+    out[8] = r[3];
+    out[9] = r[4];
+    for (int k = 0; k < 6; ++k) out[10 + k] = r[5 + k];
+    return IBLBM_OK;
+}
+
+}  // extern "C"

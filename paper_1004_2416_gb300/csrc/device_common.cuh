@@ -1,0 +1,140 @@
+// device_common.cuh -- device-side building blocks shared by the kernels of
+// the IB-LBM-FEM library: the D3Q19 velocity set, the discrete delta
+// functions, storage conversions and double-float node coordinates.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace iblbm {
+
+// Kernel-side error bits (OR-ed into the device status word).
+enum : int {
+    kStatusUnstable = 1,  // density out of (0.5, 2) or NaN
+    kStatusStencil = 2,   // an IBM stencil cell beyond a wall
+};
+
+// D3Q19 velocity set numbered as in Fig. d3q19 of the paper (the arrow i
+// points to twice (cx, cy, cz) in the figure's coordinates).
+#define IBLBM_D3Q19_CX {0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, -1, 1, 1, -1, 0, 0, 0, 0}
+#define IBLBM_D3Q19_CY {0, 0, 0, 1, -1, 0, 0, 0, 0, -1, 1, 0, 0, -1, 1, -1, 1, -1, 1}
+#define IBLBM_D3Q19_CZ {0, 0, 0, 0, 0, 1, -1, 1, -1, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1}
+// index of -c_i
+#define IBLBM_D3Q19_OPP {0, 2, 1, 4, 3, 6, 5, 8, 7, 10, 9, 12, 11, 14, 13, 16, 15, 18, 17}
+
+__host__ __device__ constexpr int q_cx(int i) {
+    constexpr int t[19] = IBLBM_D3Q19_CX;
+    return t[i];
+}
+__host__ __device__ constexpr int q_cy(int i) {
+    constexpr int t[19] = IBLBM_D3Q19_CY;
+    return t[i];
+}
+__host__ __device__ constexpr int q_cz(int i) {
+    constexpr int t[19] = IBLBM_D3Q19_CZ;
+    return t[i];
+}
+__host__ __device__ constexpr int q_opp(int i) {
+    constexpr int t[19] = IBLBM_D3Q19_OPP;
+    return t[i];
+}
+// Weight by speed class: |c|^2 = 0 -> 1/3, 1 -> 1/18, 2 -> 1/36.
+template <typename T>
+__host__ __device__ constexpr T q_w(int i) {
+    return (i == 0) ? T(1) / T(3) : (i <= 6 ? T(1) / T(18) : T(1) / T(36));
+}
+
+// Scale applied to the half-precision population deviations so that their
+// typical magnitude (1e-6 .. 1e-1) stays in the normal range of binary16.
+constexpr float kHalfScale = 4096.0f;
+constexpr float kHalfInvScale = 1.0f / 4096.0f;
+
+template <typename S, typename T>
+struct Store;
+template <>
+struct Store<double, double> {
+    static __device__ __forceinline__ double load(const double *p) { return __ldg(p); }
+    static __device__ __forceinline__ void store(double *p, double v) { *p = v; }
+};
+template <>
+struct Store<float, float> {
+    static __device__ __forceinline__ float load(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ void store(float *p, float v) { *p = v; }
+};
+template <>
+struct Store<__half, float> {
+    static __device__ __forceinline__ float load(const __half *p) {
+        return __half2float(__ldg(p)) * kHalfInvScale;
+    }
+    static __device__ __forceinline__ void store(__half *p, float v) {
+        *p = __float2half_rn(v * kHalfScale);
+    }
+};
+
+struct __align__(32) dvec4 {
+    double x, y, z, w;
+};
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+    using type = float4;
+};
+template <>
+struct Vec4<double> {
+    using type = dvec4;
+};
+
+// ---- discrete delta functions, Eqs. (2point), (3point), (4point) ----------
+template <int N, typename T>
+__device__ __forceinline__ T delta_phi(T r) {
+    T a = fabs(r);
+    if constexpr (N == 2) {
+        return a < T(1) ? T(1) - a : T(0);
+    } else if constexpr (N == 3) {
+        if (a <= T(0.5)) return (T(1) + sqrt(T(1) - T(3) * a * a)) * (T(1) / T(3));
+        if (a < T(1.5)) return (T(5) - T(3) * a - sqrt(fmax(T(0), T(6) * a - T(3) * a * a - T(2)))) * (T(1) / T(6));
+        return T(0);
+    } else {
+        if (a <= T(1)) return (T(3) - T(2) * a + sqrt(T(1) + T(4) * a - T(4) * a * a)) * T(0.125);
+        if (a < T(2)) return (T(5) - T(2) * a - sqrt(fmax(T(0), T(12) * a - T(4) * a * a - T(7)))) * T(0.125);
+        return T(0);
+    }
+}
+
+// First lattice index of the N-point stencil around coordinate x: the N
+// nodes i0 .. i0+N-1 with i0 = floor(x - N/2) + 1 contain every node where the
+// kernel is non-zero.
+template <int N, typename T>
+__device__ __forceinline__ int stencil_first(T x) {
+    return static_cast<int>(floor(x - T(0.5) * N)) + 1;
+}
+
+// ---- node coordinates -----------------------------------------------------
+// FP64 build: plain doubles.  Float builds: an unevaluated sum hi + lo of two
+// floats, advanced with an error-free two-sum, so that the ~1e-3 per-step
+// displacement of a node at coordinate ~100 keeps ~48 bits over 1e4+ steps.
+struct Coord2f {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum_add(float &hi, float &lo, float d) {
+    float s = hi + d;
+    float bb = s - hi;
+    float err = (hi - (s - bb)) + (d - bb);
+    float l = lo + err;
+    float t = s + l;
+    lo = l - (t - s);
+    hi = t;
+}
+
+__device__ __forceinline__ int wrap_index(int a, int n) {
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ void set_status(int *status, int bit) { atomicOr(status, bit); }
+
+}  // namespace iblbm

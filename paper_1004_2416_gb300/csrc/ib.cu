@@ -1,0 +1,394 @@
+// ib.cu -- immersed-boundary coupling and finite-element membrane forces.
+//
+//   k_force_spread   : node forces F_i = -dW/dx_i of the Skalak membrane
+//                      (Sec. II.B, Eqs. constitutivelaw, forcefromenergy)
+//                      and their spreading to the lattice (Eq. forcespreading)
+//   k_interp_advect  : interpolation of the new lattice velocity at the old
+//                      node positions (Eq. velocityinterpolation) and Euler
+//                      advection (Eq. positionupdate)
+//
+// Both kernels give one warp to one membrane node.  In k_force_spread the
+// lanes first take the faces around the node (one face each; a face's
+// contribution to this corner is recomputed by each of its three corner
+// warps, which keeps the assembly a deterministic warp reduction with no
+// atomics and no per-face scratch), then the lanes take the n^3 stencil cells
+// and add the spread force with one vector atomic per cell.  In
+// k_interp_advect the lanes take the stencil cells, each gathers the 19
+// populations of its cell (L2-resident: the stencils of all nodes cover a thin
+// shell of the lattice), and a warp reduction gives the node velocity.
+//
+// Face energy gradient.  With the current edge vectors u = x_b - x_a,
+// v = x_c - x_a, their Gram entries g11 = u.u, g12 = u.v, g22 = v.v and the
+// reference constants alpha, beta, gamma, kappa of the face (the entries of the
+// inverse reference Gram matrix and 1/det of it, prepared on the host), the
+// invariants of Sec. II.B are
+//     I1 = alpha g11 - 2 beta g12 + gamma g22 - 2,
+//     I2 = kappa (g11 g22 - g12^2) - 1,
+// and with w1 = dw/dI1 = k_s (I1 + 1)/6, w2 = dw/dI2 = (k_alpha I2 - k_s)/6
+//     dW/du = 2 A0 [(w1 alpha + w2 kappa g22) u - (w1 beta + w2 kappa g12) v],
+//     dW/dv = 2 A0 [(w1 gamma + w2 kappa g11) v - (w1 beta + w2 kappa g12) u];
+// the corner forces are F_b = -dW/du, F_c = -dW/dv, F_a = dW/du + dW/dv.
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace iblbm {
+
+template <typename T>
+struct PosView;
+
+// FP64 build: positions as double 4-vectors.
+template <>
+struct PosView<double> {
+    dvec4 *x;
+    __device__ __forceinline__ void edges(int a, int b, int c, double u[3], double v[3]) const {
+        dvec4 pa = x[a], pb = x[b], pc = x[c];
+        u[0] = pb.x - pa.x; u[1] = pb.y - pa.y; u[2] = pb.z - pa.z;
+        v[0] = pc.x - pa.x; v[1] = pc.y - pa.y; v[2] = pc.z - pa.z;
+    }
+    __device__ __forceinline__ void approx(int n, double p[3]) const {
+        dvec4 q = x[n];
+        p[0] = q.x; p[1] = q.y; p[2] = q.z;
+    }
+    // lattice node minus node position
+    __device__ __forceinline__ void rel(const double p[3], int X, int Y, int Z, double d[3]) const {
+        d[0] = X - p[0]; d[1] = Y - p[1]; d[2] = Z - p[2];
+    }
+    __device__ __forceinline__ void advance(int n, double dx, double dy, double dz) const {
+        dvec4 q = x[n];
+        q.x += dx; q.y += dy; q.z += dz;
+        x[n] = q;
+    }
+};
+
+// Float builds: positions as hi + lo float pairs.
+template <>
+struct PosView<float> {
+    float4 *hi;
+    float4 *lo;
+    __device__ __forceinline__ void edges(int a, int b, int c, float u[3], float v[3]) const {
+        float4 ha = hi[a], hb = hi[b], hc = hi[c];
+        float4 la = lo[a], lb = lo[b], lc = lo[c];
+        u[0] = (hb.x - ha.x) + (lb.x - la.x);
+        u[1] = (hb.y - ha.y) + (lb.y - la.y);
+        u[2] = (hb.z - ha.z) + (lb.z - la.z);
+        v[0] = (hc.x - ha.x) + (lc.x - la.x);
+        v[1] = (hc.y - ha.y) + (lc.y - la.y);
+        v[2] = (hc.z - ha.z) + (lc.z - la.z);
+    }
+    // p holds hi in [0..2] and lo in [3..5]
+    __device__ __forceinline__ void approx(int n, float p[6]) const {
+        float4 h = hi[n], l = lo[n];
+        p[0] = h.x; p[1] = h.y; p[2] = h.z;
+        p[3] = l.x; p[4] = l.y; p[5] = l.z;
+    }
+    __device__ __forceinline__ void rel(const float p[6], int X, int Y, int Z, float d[3]) const {
+        d[0] = ((float)X - p[0]) - p[3];
+        d[1] = ((float)Y - p[1]) - p[4];
+        d[2] = ((float)Z - p[2]) - p[5];
+    }
+    __device__ __forceinline__ void advance(int n, float dx, float dy, float dz) const {
+        float4 h = hi[n], l = lo[n];
+        two_sum_add(h.x, l.x, dx);
+        two_sum_add(h.y, l.y, dy);
+        two_sum_add(h.z, l.z, dz);
+        hi[n] = h;
+        lo[n] = l;
+    }
+};
+
+template <typename T>
+constexpr int kPosLen = 3;
+template <>
+constexpr int kPosLen<float> = 6;
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void add_force(float4 *f, float x, float y, float z) {
+    atomicAdd(f, make_float4(x, y, z, 0.0f));
+}
+__device__ __forceinline__ void add_force(dvec4 *f, double x, double y, double z) {
+    atomicAdd(&f->x, x);
+    atomicAdd(&f->y, y);
+    atomicAdd(&f->z, z);
+}
+
+template <int N, typename T>
+__global__ void __launch_bounds__(256)
+    k_force_spread(int n_nodes, PosView<T> pos, const int *__restrict__ adj_off,
+                   const int *__restrict__ adj, const int4 *__restrict__ tri,
+                   const typename Vec4<T>::type *__restrict__ fconst, const T *__restrict__ A0,
+                   const typename Vec4<T>::type *__restrict__ capmod,
+                   typename Vec4<T>::type *__restrict__ nodeF,
+                   typename Vec4<T>::type *__restrict__ force, uint8_t *__restrict__ flags, int nx,
+                   int ny, int nz, int ntx, int nty, int *status) {
+    using V4 = typename Vec4<T>::type;
+    const int lane = threadIdx.x & 31;
+    const int node = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    if (node >= n_nodes) return;
+
+    T fx = T(0), fy = T(0), fz = T(0);
+    const int e0 = adj_off[node], e1 = adj_off[node + 1];
+    for (int e = e0 + lane; e < e1; e += 32) {
+        const int ent = adj[e];
+        const int f = ent >> 2, corner = ent & 3;
+        const int4 t = tri[f];
+        T u[3], v[3];
+        pos.edges(t.x, t.y, t.z, u, v);
+        const V4 c = fconst[f];  // alpha, beta, gamma, kappa
+        const T a2 = T(2) * A0[f];
+        const V4 m = capmod[t.w];  // k_s/6, k_alpha/6
+        const T g11 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        const T g12 = u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
+        const T g22 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        const T I1 = c.x * g11 - T(2) * c.y * g12 + c.z * g22 - T(2);
+        const T I2 = c.w * (g11 * g22 - g12 * g12) - T(1);
+        const T w1 = m.x * (I1 + T(1));
+        const T w2 = m.y * I2 - m.x;
+        const T s_uu = a2 * (w1 * c.x + w2 * c.w * g22);
+        const T s_uv = -a2 * (w1 * c.y + w2 * c.w * g12);
+        const T s_vv = a2 * (w1 * c.z + w2 * c.w * g11);
+        T ku, kv;
+        if (corner == 0) {
+            ku = s_uu + s_uv;
+            kv = s_uv + s_vv;
+        } else if (corner == 1) {
+            ku = -s_uu;
+            kv = -s_uv;
+        } else {
+            ku = -s_uv;
+            kv = -s_vv;
+        }
+        fx += ku * u[0] + kv * v[0];
+        fy += ku * u[1] + kv * v[1];
+        fz += ku * u[2] + kv * v[2];
+    }
+    fx = warp_sum(fx);
+    fy = warp_sum(fy);
+    fz = warp_sum(fz);
+    if (lane == 0) nodeF[node] = V4{fx, fy, fz, T(0)};
+
+    T p[kPosLen<T>];
+    pos.approx(node, p);
+    T pc[3];
+    if constexpr (kPosLen<T> == 6) {
+        pc[0] = p[0] + p[3]; pc[1] = p[1] + p[4]; pc[2] = p[2] + p[5];
+    } else {
+        pc[0] = p[0]; pc[1] = p[1]; pc[2] = p[2];
+    }
+    const int bx = stencil_first<N>(pc[0]), by = stencil_first<N>(pc[1]), bz = stencil_first<N>(pc[2]);
+    constexpr int NC = N * N * N;
+    for (int k = lane; k < NC; k += 32) {
+        const int kx = k % N, ky = (k / N) % N, kz = k / (N * N);
+        const int X = bx + kx, Y = by + ky, Z = bz + kz;
+        if (Z < 0 || Z >= nz) {
+            set_status(status, kStatusStencil);
+            continue;
+        }
+        T d[3];
+        pos.rel(p, X, Y, Z, d);
+        const T w = delta_phi<N>(d[0]) * delta_phi<N>(d[1]) * delta_phi<N>(d[2]);
+        if (w == T(0)) continue;
+        const int xw = wrap_index(X, nx), yw = wrap_index(Y, ny);
+        const long long cell = xw + (long long)nx * (yw + (long long)ny * Z);
+        add_force(&force[cell], w * fx, w * fy, w * fz);
+        flags[((long long)Z * nty + yw / kTileY) * ntx + xw / kTileX] = 1;
+    }
+}
+
+template <int N, typename S, typename T>
+__global__ void __launch_bounds__(256)
+    k_interp_advect(int n_nodes, PosView<T> pos, const S *__restrict__ pop,
+                    const typename Vec4<T>::type *__restrict__ force,
+                    typename Vec4<T>::type *__restrict__ nodeU, int nx, int ny, int nz,
+                    long long ncell) {
+    using V4 = typename Vec4<T>::type;
+    const int lane = threadIdx.x & 31;
+    const int node = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    if (node >= n_nodes) return;
+    T p[kPosLen<T>];
+    pos.approx(node, p);
+    T pc[3];
+    if constexpr (kPosLen<T> == 6) {
+        pc[0] = p[0] + p[3]; pc[1] = p[1] + p[4]; pc[2] = p[2] + p[5];
+    } else {
+        pc[0] = p[0]; pc[1] = p[1]; pc[2] = p[2];
+    }
+    const int bx = stencil_first<N>(pc[0]), by = stencil_first<N>(pc[1]), bz = stencil_first<N>(pc[2]);
+    T ax = T(0), ay = T(0), az = T(0);
+    constexpr int NC = N * N * N;
+    for (int k = lane; k < NC; k += 32) {
+        const int kx = k % N, ky = (k / N) % N, kz = k / (N * N);
+        const int X = bx + kx, Y = by + ky, Z = bz + kz;
+        if (Z < 0 || Z >= nz) continue;  // reported by the spreading kernel
+        T d[3];
+        pos.rel(p, X, Y, Z, d);
+        const T w = delta_phi<N>(d[0]) * delta_phi<N>(d[1]) * delta_phi<N>(d[2]);
+        if (w == T(0)) continue;
+        const int xw = wrap_index(X, nx), yw = wrap_index(Y, ny);
+        const long long cell = xw + (long long)nx * (yw + (long long)ny * Z);
+        T g[19];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) g[i] = Store<S, T>::load(pop + i * ncell + cell);
+        T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            drho += g[i];
+            if (q_cx(i)) jx += q_cx(i) > 0 ? g[i] : -g[i];
+            if (q_cy(i)) jy += q_cy(i) > 0 ? g[i] : -g[i];
+            if (q_cz(i)) jz += q_cz(i) > 0 ? g[i] : -g[i];
+        }
+        const V4 f = force[cell];
+        const T inv_rho = T(1) / (T(1) + drho);
+        ax += w * ((jx + T(0.5) * f.x) * inv_rho);
+        ay += w * ((jy + T(0.5) * f.y) * inv_rho);
+        az += w * ((jz + T(0.5) * f.z) * inv_rho);
+    }
+    ax = warp_sum(ax);
+    ay = warp_sum(ay);
+    az = warp_sum(az);
+    if (lane == 0) {
+        nodeU[node] = V4{ax, ay, az, T(0)};
+        pos.advance(node, ax, ay, az);
+    }
+}
+
+// ---- node array conversions ---------------------------------------------------
+template <typename T>
+__global__ void k_nodes_to_f64(PosView<T> pos, const typename Vec4<T>::type *F,
+                               const typename Vec4<T>::type *U, int which, int first, int count,
+                               double *out) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    int n = first + k;
+    double r[3];
+    if (which == 0) {
+        T p[kPosLen<T>];
+        pos.approx(n, p);
+        if constexpr (kPosLen<T> == 6) {
+            for (int a = 0; a < 3; ++a) r[a] = (double)p[a] + (double)p[3 + a];
+        } else {
+            for (int a = 0; a < 3; ++a) r[a] = (double)p[a];
+        }
+    } else {
+        auto v = (which == 1) ? F[n] : U[n];
+        r[0] = (double)v.x; r[1] = (double)v.y; r[2] = (double)v.z;
+    }
+    out[3 * k] = r[0];
+    out[3 * k + 1] = r[1];
+    out[3 * k + 2] = r[2];
+}
+
+__global__ void k_f64_to_nodes_d(dvec4 *x, int first, int count, const double *in) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    x[first + k] = dvec4{in[3 * k], in[3 * k + 1], in[3 * k + 2], 0.0};
+}
+
+__global__ void k_f64_to_nodes_f(float4 *hi, float4 *lo, int first, int count, const double *in) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    float h[3], l[3];
+    for (int a = 0; a < 3; ++a) {
+        double v = in[3 * k + a];
+        h[a] = (float)v;
+        l[a] = (float)(v - (double)h[a]);
+    }
+    hi[first + k] = make_float4(h[0], h[1], h[2], 0.0f);
+    lo[first + k] = make_float4(l[0], l[1], l[2], 0.0f);
+}
+
+// ---- launchers ------------------------------------------------------------------
+template <typename T>
+static PosView<T> view(const MeshDev &m);
+template <>
+PosView<double> view<double>(const MeshDev &m) {
+    return PosView<double>{(dvec4 *)m.x};
+}
+template <>
+PosView<float> view<float>(const MeshDev &m) {
+    return PosView<float>{(float4 *)m.x, (float4 *)m.x_lo};
+}
+
+constexpr int kNodesPerBlock = 8;  // 8 warps of 32
+
+template <int N, typename T>
+static void force_spread_impl(const Lattice &L, const MeshDev &m, void *force, uint8_t *flags,
+                              int *status, cudaStream_t s) {
+    using V4 = typename Vec4<T>::type;
+    unsigned nb = (unsigned)((m.n_nodes + kNodesPerBlock - 1) / kNodesPerBlock);
+    k_force_spread<N, T><<<nb, 32 * kNodesPerBlock, 0, s>>>(
+        m.n_nodes, view<T>(m), m.adj_off, m.adj, (const int4 *)m.tri, (const V4 *)m.fconst,
+        (const T *)m.A0, (const V4 *)m.capmod, (V4 *)m.F, (V4 *)force, flags, L.nx, L.ny, L.nz,
+        L.ntx, L.nty, status);
+}
+
+template <int N, typename S, typename T>
+static void interp_impl(const Lattice &L, const MeshDev &m, const void *pop, const void *force,
+                        cudaStream_t s) {
+    using V4 = typename Vec4<T>::type;
+    unsigned nb = (unsigned)((m.n_nodes + kNodesPerBlock - 1) / kNodesPerBlock);
+    k_interp_advect<N, S, T><<<nb, 32 * kNodesPerBlock, 0, s>>>(
+        m.n_nodes, view<T>(m), (const S *)pop, (const V4 *)force, (V4 *)m.u, L.nx, L.ny, L.nz,
+        L.ncell);
+}
+
+void launch_force_spread(int prec, int delta, const Lattice &L, const MeshDev &m, void *force,
+                         uint8_t *flags, int *status, cudaStream_t s) {
+    if (m.n_nodes == 0) return;
+    if (prec == kF64) {
+        if (delta == 2) force_spread_impl<2, double>(L, m, force, flags, status, s);
+        else if (delta == 3) force_spread_impl<3, double>(L, m, force, flags, status, s);
+        else force_spread_impl<4, double>(L, m, force, flags, status, s);
+    } else {
+        if (delta == 2) force_spread_impl<2, float>(L, m, force, flags, status, s);
+        else if (delta == 3) force_spread_impl<3, float>(L, m, force, flags, status, s);
+        else force_spread_impl<4, float>(L, m, force, flags, status, s);
+    }
+}
+
+void launch_interp_advect(int prec, int delta, const Lattice &L, const MeshDev &m, const void *pop,
+                          const void *force, cudaStream_t s) {
+    if (m.n_nodes == 0) return;
+    if (prec == kF64) {
+        if (delta == 2) interp_impl<2, double, double>(L, m, pop, force, s);
+        else if (delta == 3) interp_impl<3, double, double>(L, m, pop, force, s);
+        else interp_impl<4, double, double>(L, m, pop, force, s);
+    } else if (prec == kF32) {
+        if (delta == 2) interp_impl<2, float, float>(L, m, pop, force, s);
+        else if (delta == 3) interp_impl<3, float, float>(L, m, pop, force, s);
+        else interp_impl<4, float, float>(L, m, pop, force, s);
+    } else {
+        if (delta == 2) interp_impl<2, __half, float>(L, m, pop, force, s);
+        else if (delta == 3) interp_impl<3, __half, float>(L, m, pop, force, s);
+        else interp_impl<4, __half, float>(L, m, pop, force, s);
+    }
+}
+
+void launch_nodes_to_f64(int prec, const MeshDev &m, int which, int first, int count, double *out,
+                         cudaStream_t s) {
+    if (count <= 0) return;
+    unsigned nb = (unsigned)((count + 255) / 256);
+    if (prec == kF64)
+        k_nodes_to_f64<double><<<nb, 256, 0, s>>>(view<double>(m), (const dvec4 *)m.F,
+                                                  (const dvec4 *)m.u, which, first, count, out);
+    else
+        k_nodes_to_f64<float><<<nb, 256, 0, s>>>(view<float>(m), (const float4 *)m.F,
+                                                 (const float4 *)m.u, which, first, count, out);
+}
+
+void launch_f64_to_nodes(int prec, const MeshDev &m, int first, int count, const double *in,
+                         cudaStream_t s) {
+    if (count <= 0) return;
+    unsigned nb = (unsigned)((count + 255) / 256);
+    if (prec == kF64)
+        k_f64_to_nodes_d<<<nb, 256, 0, s>>>((dvec4 *)m.x, first, count, in);
+    else
+        k_f64_to_nodes_f<<<nb, 256, 0, s>>>((float4 *)m.x, (float4 *)m.x_lo, first, count, in);
+}
+
+}  // namespace iblbm

@@ -1,0 +1,115 @@
+// internal.h -- interfaces between the host runtime (capi.cpp, mesh.cpp) and
+// the CUDA kernels (lbm.cu, ib.cu, taylor.cu) of the IB-LBM-FEM library.
+// Plain C++ (no CUDA syntax) so that host files compile with g++.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include <vector>
+
+namespace iblbm {
+
+// Lattice geometry.  Tiles of kTileX x kTileY x 1 cells are the unit of the
+// collide-stream thread block and of the sparse force-density bookkeeping.
+constexpr int kTileX = 32;
+constexpr int kTileY = 8;
+
+struct Lattice {
+    int nx, ny, nz;
+    int ntx, nty;  // tiles along x and y
+    long long ncell;
+    long long ntiles;
+};
+
+inline Lattice make_lattice(int nx, int ny, int nz) {
+    Lattice L;
+    L.nx = nx;
+    L.ny = ny;
+    L.nz = nz;
+    L.ntx = (nx + kTileX - 1) / kTileX;
+    L.nty = (ny + kTileY - 1) / kTileY;
+    L.ncell = (long long)nx * ny * nz;
+    L.ntiles = (long long)L.ntx * L.nty * nz;
+    return L;
+}
+
+enum Prec { kF64 = 0, kF32 = 1, kF16 = 2 };
+
+// Device views of the membrane data, all capsules concatenated.
+struct MeshDev {
+    int n_nodes;
+    int n_faces;
+    int n_caps;
+    // node coordinates: FP64 build double4[n]; float builds hi/lo float4[n]
+    void *x;      // double4* or float4* (hi)
+    void *x_lo;   // float4* (lo) or nullptr
+    void *F;      // node forces, double4* / float4*
+    void *u;      // node velocities, double4* / float4*
+    const int *adj_off;   // [n_nodes + 1]
+    const int *adj;       // [adj_off[n]] entries face*4 + corner
+    const int *tri;       // int4 [n_faces]: a, b, c, capsule
+    const void *fconst;   // Vec4 [n_faces]: alpha, beta, gamma, kappa
+    const void *A0;       // T [n_faces]
+    const void *capmod;   // Vec4 [n_caps]: k_s/6, k_alpha/6, 0, 0
+};
+
+// ---- lbm.cu -------------------------------------------------------------------
+struct CollideArgs {
+    const void *src;   // populations f(t) (deviations), storage type
+    void *dst;         // populations f(t+1)
+    const void *fcur;  // Vec4 force density of this step
+    const uint8_t *flag_cur;
+    void *fold;        // Vec4 force density of the previous step (cleared here)
+    uint8_t *flag_old;
+    double tau;
+    double u_wall;
+    int *status;
+};
+void launch_collide_stream(int prec, const Lattice &L, const CollideArgs &a, cudaStream_t s);
+// mode 0: rest; mode 1: linear Couette equilibrium
+void launch_init_fluid(int prec, const Lattice &L, void *pop, int mode, double u_wall, cudaStream_t s);
+// rho [ncell] and u [3][ncell] in double from populations + half the force
+void launch_moments(int prec, const Lattice &L, const void *pop, const void *force, double *rho,
+                    double *u, cudaStream_t s);
+void launch_pop_to_f64(int prec, const Lattice &L, const void *pop, double *out, cudaStream_t s);
+void launch_f64_to_pop(int prec, const Lattice &L, const double *in, void *pop, cudaStream_t s);
+void launch_force_to_f64(int prec, const Lattice &L, const void *force, double *out, cudaStream_t s);
+
+// ---- ib.cu ----------------------------------------------------------------------
+void launch_force_spread(int prec, int delta, const Lattice &L, const MeshDev &m, void *force,
+                         uint8_t *flags, int *status, cudaStream_t s);
+void launch_interp_advect(int prec, int delta, const Lattice &L, const MeshDev &m, const void *pop,
+                          const void *force, cudaStream_t s);
+// node data <-> host doubles [n][3]
+void launch_nodes_to_f64(int prec, const MeshDev &m, int which, int first, int count, double *out,
+                         cudaStream_t s);
+void launch_f64_to_nodes(int prec, const MeshDev &m, int first, int count, const double *in,
+                         cudaStream_t s);
+
+// ---- taylor.cu ----------------------------------------------------------------------
+// Per-capsule FP64 sums: out[c*12 + k] = {V, A, cx, cy, cz, Ixx, Iyy, Izz, Ixy, Ixz, Iyz, 0}
+struct TaylorPlan {
+    int n_caps;
+    int total_blocks;
+    const int *blk_cap;     // [total_blocks] capsule of each block
+    const int *blk_face0;   // [total_blocks] first face of each block
+    const int *blk_nface;   // [total_blocks]
+    const int *cap_blk0;    // [n_caps + 1] first block of each capsule
+    const double *origin;   // [n_caps][3]
+    double *partial;        // scratch [total_blocks][8]
+    double *out;            // [n_caps][12]
+};
+constexpr int kTaylorFacesPerBlock = 128;
+void launch_taylor(int prec, const MeshDev &m, const TaylorPlan &p, cudaStream_t s);
+
+// ---- mesh.cpp (host) -------------------------------------------------------------------
+// Canonical icosphere: nodes [n][3], faces [f][3]
+void icosphere(int m, double r, const double c[3], std::vector<double> &nodes,
+               std::vector<int> &tri);
+// Host eigen-decomposition of a symmetric 3x3 matrix: ascending values,
+// eigenvectors in columns of vec (row-major 3x3).
+void sym_eig3(const double A[9], double val[3], double vec[9]);
+
+}  // namespace iblbm

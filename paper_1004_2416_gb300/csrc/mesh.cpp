@@ -1,0 +1,213 @@
+// mesh.cpp -- host-side geometry of the IB-LBM-FEM library: the canonical
+// icosahedron-subdivision sphere (Sec. II.D, Fig. subdivision) and the
+// symmetric 3x3 eigen-decomposition behind the Taylor deformation (Sec. III).
+//
+// Canonical icosphere (the node and face order is part of the interface):
+//   base node k = 4 g + j (g = 0..2, j = 0..3), s1 = (j even ? +1 : -1),
+//   s2 = (j < 2 ? +1 : -1), t = golden ratio:
+//     g = 0 -> (0, s1, s2 t), g = 1 -> (s1, s2 t, 0), g = 2 -> (s2 t, 0, s1),
+//   each scaled by r / |v|;
+//   base faces = the mutually adjacent triples i < j < k in lexicographic
+//   order, stored (i, j, k) when det[v_i, v_j, v_k] > 0 (outward normal),
+//   otherwise (i, k, j);
+//   subdivision: faces in order, edges (a,b), (b,c), (c,a); an edge's midpoint
+//   (x_a + x_b)/2 projected to radius r becomes a new node at its first
+//   encounter; children (a,ab,ca), (ab,b,bc), (ca,bc,c), (ab,bc,ca);
+//   the centre is added last.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <unordered_map>
+#include <utility>
+#include <vector>
+
+#include "internal.h"
+
+namespace iblbm {
+
+namespace {
+
+struct V3 {
+    double x, y, z;
+};
+
+V3 project(const V3 &q, double r) {
+    double len = std::sqrt(q.x * q.x + q.y * q.y + q.z * q.z);
+    double s = r / len;
+    return V3{q.x * s, q.y * s, q.z * s};
+}
+
+double triple(const V3 &a, const V3 &b, const V3 &c) {
+    return a.x * (b.y * c.z - b.z * c.y) + a.y * (b.z * c.x - b.x * c.z) +
+           a.z * (b.x * c.y - b.y * c.x);
+}
+
+}  // namespace
+
+void icosphere(int m, double r, const double c[3], std::vector<double> &nodes,
+               std::vector<int> &tri) {
+    const double t = (1.0 + std::sqrt(5.0)) / 2.0;
+    std::vector<V3> base(12);
+    for (int k = 0; k < 12; ++k) {
+        const int g = k / 4, j = k % 4;
+        const double s1 = (j % 2 == 0) ? 1.0 : -1.0;
+        const double s2 = (j < 2) ? 1.0 : -1.0;
+        if (g == 0) base[k] = V3{0.0, s1, s2 * t};
+        else if (g == 1) base[k] = V3{s1, s2 * t, 0.0};
+        else base[k] = V3{s2 * t, 0.0, s1};
+    }
+    // adjacency of the unscaled icosahedron: edge length 2, next distance 2t
+    bool adj[12][12];
+    for (int i = 0; i < 12; ++i)
+        for (int j = 0; j < 12; ++j) {
+            const double dx = base[i].x - base[j].x, dy = base[i].y - base[j].y,
+                         dz = base[i].z - base[j].z;
+            adj[i][j] = (i != j) && (dx * dx + dy * dy + dz * dz < 5.0);
+        }
+    std::vector<int> faces;
+    for (int i = 0; i < 12; ++i)
+        for (int j = i + 1; j < 12; ++j) {
+            if (!adj[i][j]) continue;
+            for (int k = j + 1; k < 12; ++k) {
+                if (!adj[i][k] || !adj[j][k]) continue;
+                const bool out = triple(base[i], base[j], base[k]) > 0.0;
+                faces.push_back(i);
+                faces.push_back(out ? j : k);
+                faces.push_back(out ? k : j);
+            }
+        }
+    std::vector<V3> p;
+    p.reserve(10 * (size_t(1) << (2 * m)) + 2);
+    for (const V3 &v : base) p.push_back(project(v, r));
+
+    for (int level = 0; level < m; ++level) {
+        std::unordered_map<uint64_t, int> mid;
+        mid.reserve(faces.size());
+        auto midpoint = [&](int a, int b) {
+            const uint64_t key = (uint64_t)(uint32_t)std::min(a, b) << 32 | (uint32_t)std::max(a, b);
+            auto it = mid.find(key);
+            if (it != mid.end()) return it->second;
+            const V3 q{(p[a].x + p[b].x) * 0.5, (p[a].y + p[b].y) * 0.5, (p[a].z + p[b].z) * 0.5};
+            p.push_back(project(q, r));
+            const int id = (int)p.size() - 1;
+            mid.emplace(key, id);
+            return id;
+        };
+        std::vector<int> next;
+        next.reserve(faces.size() * 4);
+        for (size_t f = 0; f < faces.size(); f += 3) {
+            const int a = faces[f], b = faces[f + 1], cc = faces[f + 2];
+            const int ab = midpoint(a, b);
+            const int bc = midpoint(b, cc);
+            const int ca = midpoint(cc, a);
+            const int kids[12] = {a, ab, ca, ab, b, bc, ca, bc, cc, ab, bc, ca};
+            next.insert(next.end(), kids, kids + 12);
+        }
+        faces.swap(next);
+    }
+    nodes.resize(3 * p.size());
+    for (size_t n = 0; n < p.size(); ++n) {
+        nodes[3 * n] = c[0] + p[n].x;
+        nodes[3 * n + 1] = c[1] + p[n].y;
+        nodes[3 * n + 2] = c[2] + p[n].z;
+    }
+    tri = faces;
+}
+
+// Eigenvalues of a symmetric 3x3 matrix from the trigonometric solution of
+// its characteristic cubic (Smith, CACM 1961), each refined with an
+// eigenvector from a cross product of two rows of (A - lambda I) followed by
+// the Rayleigh quotient (twice), which makes the values accurate to rounding
+// even where the cubic's roots are ill-conditioned.
+namespace {
+
+void mat_vec(const double A[9], const double v[3], double out[3]) {
+    for (int i = 0; i < 3; ++i) out[i] = A[3 * i] * v[0] + A[3 * i + 1] * v[1] + A[3 * i + 2] * v[2];
+}
+
+bool null_vector(const double A[9], double lam, double v[3]) {
+    const double r0[3] = {A[0] - lam, A[1], A[2]};
+    const double r1[3] = {A[3], A[4] - lam, A[5]};
+    const double r2[3] = {A[6], A[7], A[8] - lam};
+    const double *rows[3] = {r0, r1, r2};
+    double best = -1.0;
+    for (int a = 0; a < 3; ++a) {
+        const double *p = rows[a], *q = rows[(a + 1) % 3];
+        double c[3] = {p[1] * q[2] - p[2] * q[1], p[2] * q[0] - p[0] * q[2], p[0] * q[1] - p[1] * q[0]};
+        double n = c[0] * c[0] + c[1] * c[1] + c[2] * c[2];
+        if (n > best) {
+            best = n;
+            for (int k = 0; k < 3; ++k) v[k] = c[k];
+        }
+    }
+    if (!(best > 0.0)) return false;
+    const double inv = 1.0 / std::sqrt(best);
+    for (int k = 0; k < 3; ++k) v[k] *= inv;
+    return true;
+}
+
+double rayleigh(const double A[9], const double v[3]) {
+    double Av[3];
+    mat_vec(A, v, Av);
+    return (v[0] * Av[0] + v[1] * Av[1] + v[2] * Av[2]) / (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+}
+
+}  // namespace
+
+void sym_eig3(const double A[9], double val[3], double vec[9]) {
+    const double a11 = A[0], a22 = A[4], a33 = A[8];
+    const double a12 = 0.5 * (A[1] + A[3]), a13 = 0.5 * (A[2] + A[6]), a23 = 0.5 * (A[5] + A[7]);
+    const double S[9] = {a11, a12, a13, a12, a22, a23, a13, a23, a33};
+    const double q = (a11 + a22 + a33) / 3.0;
+    const double p1 = a12 * a12 + a13 * a13 + a23 * a23;
+    const double p2 = (a11 - q) * (a11 - q) + (a22 - q) * (a22 - q) + (a33 - q) * (a33 - q) + 2.0 * p1;
+    const double p = std::sqrt(p2 / 6.0);
+    double lam[3];
+    double V[3][3];
+    if (!(p > 1e-300)) {
+        for (int k = 0; k < 3; ++k) {
+            val[k] = q;
+            for (int i = 0; i < 3; ++i) vec[3 * i + k] = (i == k) ? 1.0 : 0.0;
+        }
+        return;
+    }
+    const double B[9] = {(a11 - q) / p, a12 / p, a13 / p, a12 / p, (a22 - q) / p, a23 / p,
+                         a13 / p, a23 / p, (a33 - q) / p};
+    double detB = B[0] * (B[4] * B[8] - B[5] * B[7]) - B[1] * (B[3] * B[8] - B[5] * B[6]) +
+                  B[2] * (B[3] * B[7] - B[4] * B[6]);
+    double rr = 0.5 * detB;
+    rr = rr < -1.0 ? -1.0 : (rr > 1.0 ? 1.0 : rr);
+    const double phi = std::acos(rr) / 3.0;
+    const double two_pi_3 = 2.0943951023931954923;
+    lam[2] = q + 2.0 * p * std::cos(phi);               // largest
+    lam[0] = q + 2.0 * p * std::cos(phi + two_pi_3);    // smallest
+    lam[1] = 3.0 * q - lam[0] - lam[2];
+    // vectors of the outer eigenvalues, refined; the middle one completes
+    // the orthonormal frame.
+    for (int k : {0, 2}) {
+        double v[3] = {0, 0, 0};
+        for (int it = 0; it < 2; ++it) {
+            if (!null_vector(S, lam[k], v)) break;
+            lam[k] = rayleigh(S, v);
+        }
+        for (int i = 0; i < 3; ++i) V[i][k] = v[i];
+    }
+    {
+        double a[3] = {V[0][2], V[1][2], V[2][2]}, b[3] = {V[0][0], V[1][0], V[2][0]};
+        double c[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+        double n = std::sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+        if (n > 0.0)
+            for (int i = 0; i < 3; ++i) V[i][1] = c[i] / n;
+        lam[1] = n > 0.0 ? rayleigh(S, c) : lam[1];
+    }
+    int order[3] = {0, 1, 2};
+    for (int i = 0; i < 3; ++i)
+        for (int j = i + 1; j < 3; ++j)
+            if (lam[order[j]] < lam[order[i]]) std::swap(order[i], order[j]);
+    for (int k = 0; k < 3; ++k) {
+        val[k] = lam[order[k]];
+        for (int i = 0; i < 3; ++i) vec[3 * i + k] = V[i][order[k]];
+    }
+}
+
+}  // namespace iblbm

@@ -1,0 +1,296 @@
+"""ctypes binding of ``include/iblbm.h`` (the IB-LBM-FEM library for GB300).
+
+Argument marshalling only: every computation runs in ``lib/libiblbm.so``.
+The module raises ``ImportError`` at import time when the library is not
+built (there is no fallback path).  Functions keep the C names
+(``iblbm_create`` ...); :class:`Sim` wraps them with numpy arrays.
+
+Streams and device memory can come from PyTorch: pass
+``stream=torch.cuda.current_stream()`` to :class:`Sim`, or
+``allocator="torch"`` to let the library allocate through PyTorch's caching
+allocator.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libiblbm.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
+        "(nvcc, sm_103a); there is no non-CUDA fallback")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+IBLBM_OK = 0
+IBLBM_ERR_ARG = -1
+IBLBM_ERR_OOM = -2
+IBLBM_ERR_CUDA = -3
+IBLBM_ERR_UNSTABLE = -4
+IBLBM_ERR_STENCIL = -5
+IBLBM_ERR_TIMEOUT = -6
+IBLBM_ERR_STATE = -7
+
+IBLBM_FP64 = 0
+IBLBM_FP32 = 1
+IBLBM_FP16 = 2
+PRECISIONS = {"fp64": IBLBM_FP64, "fp32": IBLBM_FP32, "fp16": IBLBM_FP16}
+
+_vp = ctypes.c_void_p
+_int = ctypes.c_int
+_dbl = ctypes.c_double
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+
+ALLOC_FN = ctypes.CFUNCTYPE(_vp, ctypes.c_size_t, _vp, _vp)
+FREE_FN = ctypes.CFUNCTYPE(None, _vp, _vp, _vp)
+
+
+class iblbm_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", _vp)]
+
+
+class iblbm_info(ctypes.Structure):
+    _fields_ = [("nx", _int), ("ny", _int), ("nz", _int), ("precision", _int),
+                ("delta_points", _int), ("n_capsules", _int), ("n_nodes", _int),
+                ("n_faces", _int), ("step", ctypes.c_int64), ("tau", _dbl), ("u_wall", _dbl)]
+
+
+_SIGS = {
+    "iblbm_create": (_int, [ctypes.POINTER(_vp), _int, _int, _int, _dbl, _int, _int, _vp,
+                            ctypes.POINTER(iblbm_allocator)]),
+    "iblbm_destroy": (_int, [_vp]),
+    "iblbm_last_error": (ctypes.c_char_p, [_vp]),
+    "iblbm_status_string": (ctypes.c_char_p, [_int]),
+    "iblbm_get_info": (_int, [_vp, ctypes.POINTER(iblbm_info)]),
+    "iblbm_set_shear_walls": (_int, [_vp, _dbl]),
+    "iblbm_add_capsule_icosphere": (_int, [_vp, _dbl, _dbl, _dbl, _dbl, _int, _ip]),
+    "iblbm_add_capsule_mesh": (_int, [_vp, _dp, _int, _i32p, _int, _ip]),
+    "iblbm_set_skalak": (_int, [_vp, _int, _dbl, _dbl]),
+    "iblbm_init_fluid": (_int, [_vp, _int]),
+    "iblbm_step": (_int, [_vp, ctypes.c_int64]),
+    "iblbm_sync": (_int, [_vp]),
+    "iblbm_get_velocity": (_int, [_vp, _dp]),
+    "iblbm_get_density": (_int, [_vp, _dp]),
+    "iblbm_get_populations": (_int, [_vp, _dp]),
+    "iblbm_set_populations": (_int, [_vp, _dp]),
+    "iblbm_get_force_field": (_int, [_vp, _dp]),
+    "iblbm_get_nodes": (_int, [_vp, _int, _dp]),
+    "iblbm_set_nodes": (_int, [_vp, _int, _dp]),
+    "iblbm_get_node_forces": (_int, [_vp, _int, _dp]),
+    "iblbm_get_node_velocities": (_int, [_vp, _int, _dp]),
+    "iblbm_get_mesh": (_int, [_vp, _int, _ip, _ip, _i32p]),
+    "iblbm_get_taylor": (_int, [_vp, _int, _dp]),
+    "iblbm_icosphere": (_int, [_int, _dbl, _dp, _dp, _i32p]),
+}
+
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+    globals()[_name] = _f
+
+
+class IblbmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{iblbm_status_string(code).decode()} ({code}): {msg}")
+        self.code = code
+
+
+def _check(rc: int, handle=None):
+    if rc != IBLBM_OK:
+        msg = iblbm_last_error(handle).decode(errors="replace")
+        raise IblbmError(rc, msg)
+
+
+def _d(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def _torch_allocator():
+    import torch
+
+    live = {}
+
+    def _alloc(nbytes, stream, ctx):
+        t = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
+        live[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def _free(ptr, stream, ctx):
+        live.pop(ptr, None)
+
+    a = iblbm_allocator(ALLOC_FN(_alloc), FREE_FN(_free), None)
+    return a, live
+
+
+def icosphere(subdivisions: int, radius: float, center=(0.0, 0.0, 0.0)):
+    """The library's canonical icosphere (host only): nodes [n, 3], faces [f, 3]."""
+    nf = 20 * 4 ** subdivisions
+    nodes = np.empty((nf // 2 + 2, 3), np.float64)
+    tri = np.empty((nf, 3), np.int32)
+    c = np.ascontiguousarray(center, np.float64)
+    _check(iblbm_icosphere(subdivisions, radius, _d(c), _d(nodes), tri.ctypes.data_as(_i32p)))
+    return nodes, tri
+
+
+TAYLOR_KEYS = ("D", "theta", "r_a", "r_b", "r_c", "V", "A", "c_x", "c_y", "c_z",
+               "I_xx", "I_yy", "I_zz", "I_xy", "I_xz", "I_yz")
+
+
+class Sim:
+    """One lattice with its capsules (owns an ``iblbm_sim``)."""
+
+    def __init__(self, nx: int, ny: int, nz: int, tau: float = 1.0, precision="fp32",
+                 delta_points: int = 3, stream=None, allocator=None):
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self._keep = None
+        alloc_p = None
+        if allocator == "torch":
+            a, live = _torch_allocator()
+            self._keep = (a, live)
+            alloc_p = ctypes.pointer(a)
+        h = _vp()
+        rc = iblbm_create(ctypes.byref(h), nx, ny, nz, tau, prec, delta_points,
+                          _stream_handle(stream), alloc_p)
+        if rc != IBLBM_OK:
+            raise IblbmError(rc, iblbm_last_error(None).decode(errors="replace"))
+        self._h = h
+        self.shape = (nx, ny, nz)
+        self.ncell = nx * ny * nz
+        self._ncaps = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            iblbm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> iblbm_info:
+        out = iblbm_info()
+        _check(iblbm_get_info(self._h, ctypes.byref(out)), self._h)
+        return out
+
+    def set_shear_walls(self, u_wall: float):
+        _check(iblbm_set_shear_walls(self._h, u_wall), self._h)
+
+    def add_capsule_icosphere(self, center, radius: float, subdivisions: int) -> int:
+        cid = _int()
+        _check(iblbm_add_capsule_icosphere(self._h, *map(float, center), float(radius),
+                                           int(subdivisions), ctypes.byref(cid)), self._h)
+        self._ncaps += 1
+        return cid.value
+
+    def add_capsule_mesh(self, nodes, tri) -> int:
+        x = np.ascontiguousarray(nodes, np.float64)
+        t = np.ascontiguousarray(tri, np.int32)
+        cid = _int()
+        _check(iblbm_add_capsule_mesh(self._h, _d(x), x.shape[0], t.ctypes.data_as(_i32p),
+                                      t.shape[0], ctypes.byref(cid)), self._h)
+        self._ncaps += 1
+        return cid.value
+
+    def set_skalak(self, k_s: float, C: float = 1.0, capsule_id: int = -1):
+        _check(iblbm_set_skalak(self._h, capsule_id, k_s, C), self._h)
+
+    def init_fluid(self, mode: int = 1):
+        _check(iblbm_init_fluid(self._h, mode), self._h)
+
+    def step(self, n: int = 1):
+        _check(iblbm_step(self._h, int(n)), self._h)
+
+    def sync(self):
+        _check(iblbm_sync(self._h), self._h)
+
+    def _field(self, fn, shape):
+        out = np.empty(shape, np.float64)
+        _check(fn(self._h, _d(out)), self._h)
+        return out
+
+    def get_velocity(self):
+        nx, ny, nz = self.shape
+        return self._field(iblbm_get_velocity, (3, nz, ny, nx))
+
+    def get_density(self):
+        nx, ny, nz = self.shape
+        return self._field(iblbm_get_density, (nz, ny, nx))
+
+    def get_populations(self):
+        nx, ny, nz = self.shape
+        return self._field(iblbm_get_populations, (19, nz, ny, nx))
+
+    def set_populations(self, f):
+        nx, ny, nz = self.shape
+        f = np.ascontiguousarray(f, np.float64)
+        assert f.shape == (19, nz, ny, nx)
+        _check(iblbm_set_populations(self._h, _d(f)), self._h)
+
+    def get_force_field(self):
+        nx, ny, nz = self.shape
+        return self._field(iblbm_get_force_field, (3, nz, ny, nx))
+
+    def n_nodes(self, capsule_id: int = -1) -> int:
+        if capsule_id == -1:
+            return self.info().n_nodes
+        return self.mesh(capsule_id)[0]
+
+    def mesh(self, capsule_id: int):
+        nn, nt = _int(), _int()
+        _check(iblbm_get_mesh(self._h, capsule_id, ctypes.byref(nn), ctypes.byref(nt), None), self._h)
+        tri = np.empty((nt.value, 3), np.int32)
+        _check(iblbm_get_mesh(self._h, capsule_id, ctypes.byref(nn), ctypes.byref(nt),
+                              tri.ctypes.data_as(_i32p)), self._h)
+        return nn.value, tri
+
+    def _nodes(self, fn, capsule_id):
+        out = np.empty((self.n_nodes(capsule_id), 3), np.float64)
+        _check(fn(self._h, capsule_id, _d(out)), self._h)
+        return out
+
+    def get_nodes(self, capsule_id: int = -1):
+        return self._nodes(iblbm_get_nodes, capsule_id)
+
+    def set_nodes(self, x, capsule_id: int = -1):
+        x = np.ascontiguousarray(x, np.float64)
+        assert x.shape == (self.n_nodes(capsule_id), 3)
+        _check(iblbm_set_nodes(self._h, capsule_id, _d(x)), self._h)
+
+    def get_node_forces(self, capsule_id: int = -1):
+        return self._nodes(iblbm_get_node_forces, capsule_id)
+
+    def get_node_velocities(self, capsule_id: int = -1):
+        return self._nodes(iblbm_get_node_velocities, capsule_id)
+
+    def taylor(self, capsule_id: int = 0) -> dict:
+        out = np.empty(16, np.float64)
+        _check(iblbm_get_taylor(self._h, capsule_id, _d(out)), self._h)
+        return dict(zip(TAYLOR_KEYS, out.tolist()))

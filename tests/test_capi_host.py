@@ -1,0 +1,78 @@
+"""Host-side checks of the C ABI library that need no GPU: every function the
+header declares is exported, the host-only icosphere matches the oracle's bit
+for bit, and creating a simulation without a device fails cleanly."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "iblbm.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(iblbm_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for must in ("iblbm_create", "iblbm_destroy", "iblbm_step", "iblbm_set_shear_walls",
+                 "iblbm_set_skalak", "iblbm_add_capsule_icosphere", "iblbm_get_velocity",
+                 "iblbm_get_nodes", "iblbm_get_taylor"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1004_2416_gb300 import LIB_PATH
+
+    lib = ctypes.CDLL(LIB_PATH)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+@pytest.mark.parametrize("m", range(0, 6))
+def test_icosphere_bit_exact_with_oracle(m):
+    import oracle as O
+    from paper_1004_2416_gb300 import iblbm as B
+
+    c = (15.5, 63.5 - m, -2.25)
+    n1, t1 = B.icosphere(m, 4.0 + 3 * m, c)
+    n2, t2 = O.icosphere(m, 4.0 + 3 * m, c)
+    assert np.array_equal(t1, t2)
+    assert np.array_equal(n1.view(np.int64), n2.view(np.int64))
+
+
+def test_icosphere_rejects_bad_arguments():
+    from paper_1004_2416_gb300 import iblbm as B
+
+    with pytest.raises(B.IblbmError):
+        B.icosphere(8, 1.0)
+    with pytest.raises(B.IblbmError):
+        B.icosphere(2, -1.0)
+
+
+def test_status_strings():
+    from paper_1004_2416_gb300 import iblbm as B
+
+    assert B.iblbm_status_string(B.IBLBM_ERR_STENCIL) == b"IBLBM_ERR_STENCIL"
+    assert B.iblbm_status_string(0) == b"IBLBM_OK"
+
+
+def test_create_without_device_or_with_bad_args_fails_cleanly():
+    from paper_1004_2416_gb300 import iblbm as B
+
+    with pytest.raises(B.IblbmError) as e:
+        B.Sim(8, 8, 8, tau=0.4)
+    assert e.value.code == B.IBLBM_ERR_ARG
+    with pytest.raises(B.IblbmError) as e:
+        B.Sim(8, 8, 8, delta_points=5)
+    assert e.value.code == B.IBLBM_ERR_ARG
+    with pytest.raises(B.IblbmError) as e:
+        B.Sim(0, 8, 8)
+    assert e.value.code == B.IBLBM_ERR_ARG
