@@ -1,0 +1,389 @@
+#!/usr/bin/env python
+"""Benchmark of the fused IB-LBM-FEM time step on one GB300 per rank.
+
+Workload (config 2 of the paper-shaped set-ups): 128^3 D3Q19 lattice, tau = 1,
+wall-driven simple shear (shear rate 1e-3), one capsule of radius 16 on the
+5120-face icosphere, Skalak C = 1, reduced shear rate G = 0.0125, 4-point delta,
+FP32 populations.  One step = membrane forces + spreading, collide-and-stream,
+interpolation + advection, and the FP64 capsule reductions behind the Taylor
+deformation recorded on the device.  All of it runs in the library's CUDA
+kernels through the C ABI.
+
+Metric: MLUPS (lattice cell updates per second / 1e6) of the whole step,
+summed over ranks (independent replicas, weak scaling).  Also reported: the
+collide-and-stream kernel against the measured HBM bandwidth (152 algorithmic
+bytes per FP32 cell update), membrane nodes/s, an end-to-end figure through
+host buffers, the CPU oracle as a baseline, and SM clocks sampled during the
+timed region.
+
+`--impl reference` times the FP64 CPU oracle on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fused IB-LBM step MLUPS & % HBM roofline; adjoint/forward time at 1e-4 rel error"
+BYTES_PER_CELL = {"fp32": 152, "fp16": 76, "fp64": 304}
+KERNEL_LAUNCHES_PER_STEP = 3 + 3  # force+spread, collide, interp, 3 reduction stages
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20000)
+    p.add_argument("--warmup", type=int, default=200)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--delta", type=int, default=4)
+    p.add_argument("--G", type=float, default=0.0125)
+    p.add_argument("--precision", default="fp32")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-budget-s", type=float, default=20.0)
+    p.add_argument("--profile-steps", type=int, default=500)
+    return p.parse_args()
+
+
+def _workload(a):
+    from paper_1004_2416_gb300 import workloads as W
+
+    return W.config2(G=a.G, delta=a.delta, precision=a.precision)
+
+
+def _config(case, a):
+    c = case.capsules[0]
+    return {
+        "workload": case.name,
+        "lattice": list(case.shape),
+        "cells": case.ncell,
+        "capsules": len(case.capsules),
+        "membrane_nodes": case.n_nodes,
+        "faces": 20 * 4 ** c.subdivisions,
+        "radius": c.radius,
+        "delta_points": case.delta,
+        "reduced_shear_rate_G": a.G,
+        "k_s": c.k_s,
+        "u_wall": case.u_wall,
+        "tau": case.tau,
+        "storage": f"{case.precision} deviations from rest equilibrium",
+        "step": "forces+spread, collide-stream, interpolate+advect, FP64 Taylor reductions recorded",
+        "l2": "inputs larger than L2: two population buffers of 159 MB each",
+        "parallelism": "replicas (one independent simulation per rank)",
+    }
+
+
+# ---- distributed plumbing ------------------------------------------------------
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class _Group:
+    def __init__(self, backend):
+        self.ws, self.rank, self.local = _dist()
+        self.pg = None
+        if self.ws > 1:
+            import torch.distributed as dist
+
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+
+        dev = "cuda" if self.pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---- clocks -------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.p = None
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(gpu_index)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if not self.p:
+            return None
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        for line in out.splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(self.REASONS, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _gpu_index(local: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    parts = [v for v in vis.split(",") if v.strip()]
+    if parts and local < len(parts) and parts[local].strip().isdigit():
+        return int(parts[local])
+    return local
+
+
+# ---- roofline helpers --------------------------------------------------------------------
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def _kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("lbm.cu", "device_common.cuh", "internal.h"):
+        with open(os.path.join(ROOT, "paper_1004_2416_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(precision: str):
+    """DRAM bytes per collide-and-stream launch from the committed ncu summary,
+    or None when the summary is absent or was taken on other kernel source."""
+    path = os.path.join(ROOT, "profiles", f"collide_stream_config2_{precision}.txt")
+    try:
+        kv = {}
+        with open(path) as fh:
+            for line in fh:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha256_16") != _kernel_source_hash():
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# ---- CPU oracle ------------------------------------------------------------------------------
+
+def _oracle_run(case, budget_s: float, max_steps: int):
+    """Times the FP64 oracle on the full workload: one untimed step, then as many
+    timed steps as fit in the budget (at least one, at most max_steps)."""
+    import oracle as O
+
+    O.build()
+    nx, ny, nz = case.shape
+    o = O.Sim(nx, ny, nz, case.tau, case.delta, case.u_wall)
+    for c in case.capsules:
+        X0, tri = O.icosphere(c.subdivisions, c.radius, c.center)
+        o.add_capsule(X0, tri, c.k_s, c.C * c.k_s)
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter() - t0
+    n = int(max(1, min(max_steps, budget_s // max(t1, 1e-9))))
+    t0 = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t0
+    o.close()
+    return n, dt
+
+
+# ---- our arm ------------------------------------------------------------------------------------
+
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    from paper_1004_2416_gb300 import Sim, iblbm as B
+
+    grp = _Group("nccl")
+    torch.cuda.set_device(grp.local)
+    case = _workload(a)
+    nx, ny, nz = case.shape
+    stream = torch.cuda.Stream()
+    sim = Sim(nx, ny, nz, tau=case.tau, precision=case.precision, delta_points=case.delta, stream=stream)
+    sim.set_shear_walls(case.u_wall)
+    for c in case.capsules:
+        cid = sim.add_capsule_icosphere(c.center, c.radius, c.subdivisions)
+        sim.set_skalak(c.k_s, c.C, cid)
+    sim.init_fluid(1)
+    sim.set_taylor_recording(1, ring=a.steps + a.warmup + 4096)
+
+    sim.step(a.warmup)
+    sim.sync()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(_gpu_index(grp.local))
+    time.sleep(0.3)
+    grp.barrier()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    sim.step(a.steps)
+    end.record(stream)
+    end.synchronize()
+    torch.cuda.synchronize()
+    grp.barrier()
+    clocks = sampler.stop()
+    ms = start.elapsed_time(end)
+    sim.sync()  # raises on any device-side error of the timed region
+    ms_max = grp.max(ms)
+    cells = case.ncell
+    value = grp.ws * cells * a.steps / (ms_max * 1e-3) / 1e6
+    nodes_per_s = grp.ws * case.n_nodes * a.steps / (ms_max * 1e-3)
+    steps_rec, rec = sim.taylor_records(0, max_records=1)
+    D_last = float(rec[-1][0]) if len(rec) else None
+
+    # per-kernel device times with CUDA events on the launching stream
+    prof = sim.profile_kernels(a.profile_steps)
+    sim.sync()
+    peak, peak_kind = _peaks()
+    algo_bytes = BYTES_PER_CELL[case.precision] * cells
+    k_ms = prof["collide_stream"]
+    achieved = algo_bytes / (k_ms * 1e-3) / 1e9
+    traffic = _ncu_traffic(case.precision)
+    roofline = {"kernel": "k_collide_stream", "bound": "hbm", "achieved": round(achieved, 1),
+                "peak": peak, "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "algorithmic_bytes_per_launch": algo_bytes, "kernel_ms": round(k_ms, 5)}
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not a.no_e2e:
+        f_host = torch.empty(19 * cells, dtype=torch.float64, pin_memory=True).numpy().reshape(19, nz, ny, nx)
+        x_host = torch.empty(case.n_nodes * 3, dtype=torch.float64, pin_memory=True).numpy().reshape(-1, 3)
+        out_nodes = torch.empty(case.n_nodes * 3, dtype=torch.float64, pin_memory=True).numpy()
+        out_taylor = np.empty(16, np.float64)
+        f_host[...] = sim.get_populations()
+        x_host[...] = sim.get_nodes()
+        import ctypes
+
+        dp = ctypes.POINTER(ctypes.c_double)
+        h = sim.handle
+        k_e2e = a.steps
+        grp.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim.set_populations(f_host)
+        sim.set_nodes(x_host)
+        p_nodes = out_nodes.ctypes.data_as(dp)
+        p_tay = out_taylor.ctypes.data_as(dp)
+        for _ in range(k_e2e):
+            rc = B.iblbm_step(h, 1)
+            rc = rc or B.iblbm_get_taylor(h, 0, p_tay)
+            rc = rc or B.iblbm_get_nodes(h, -1, p_nodes)
+            if rc:
+                raise B.IblbmError(rc, B.iblbm_last_error(h).decode())
+        dt = time.perf_counter() - t0
+        dt_max = grp.max(dt)
+        e2e = {"value": round(grp.ws * cells * k_e2e / dt_max / 1e6, 2), "unit": "MLUPS",
+               "steps": k_e2e,
+               "h2d_bytes_per_step": int((19 * cells * 8 + case.n_nodes * 24) / k_e2e),
+               "d2h_bytes_per_step": case.n_nodes * 24 + 12 * 8,
+               "note": "timed region: upload of the state from pinned host memory, then per step "
+                       "iblbm_step(1) + Taylor read-back + node read-back to pinned host memory"}
+
+    cpu = None
+    if grp.rank == 0 and grp.ws == 1 and not a.no_cpu_baseline:
+        n, dt = _oracle_run(case, a.cpu_budget_s, a.steps)
+        cpu = {"value": round(cells * n / dt / 1e6, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+               "sample": f"{n} full oracle steps (FP64, single thread) of the same workload after one "
+                         f"untimed step, {dt:.1f} s"}
+
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": grp.ws,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms_max / a.steps, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if case.precision == "fp32" else ("f16-storage/f32" if case.precision == "fp16" else "f64"),
+        "data": "synthetic", "config": _config(case, a),
+        "membrane_nodes_per_s": round(nodes_per_s, 1),
+        "kernel_ms_per_step": {k: round(v, 5) for k, v in prof.items()},
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": KERNEL_LAUNCHES_PER_STEP * a.steps,
+        "final_D": D_last,
+    }
+    sim.close()
+    grp.close()
+    if grp.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_reference(a):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    case = _workload(a)
+    w = min(a.warmup, 1)
+    n, dt = _oracle_run(case, max(a.cpu_budget_s, 30.0), a.steps)
+    value = case.ncell * n / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MLUPS", "n_gpus": ws,
+        "steps": n, "warmup": w, "ms_per_step": round(dt / n * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(case, a),
+        "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"{n} full FP64 oracle steps of the workload (of {a.steps} requested; "
+                                   f"each oracle step of 2.1 M cells takes seconds), after 1 untimed step"},
+        "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -154,6 +154,29 @@ int iblbm_init_fluid(iblbm_sim *sim, int mode);
  * (sum_i c_i f_i(t+1) + f(t)/2) / rho(t+1).  Asynchronous. */
 int iblbm_step(iblbm_sim *sim, int64_t n_steps);
 
+/* Sub-step 6 of the step list of Sec. II.C, kept on the device: after every
+ * `every`-th step (counted from iblbm_init_fluid; every = 0 switches it off)
+ * the double-precision reductions behind iblbm_get_taylor (volume, area,
+ * centroid, inertia tensor of every capsule) are recorded into a device ring
+ * of `ring` records (1 <= ring <= 2^24), inside the same captured step
+ * sequence, without host synchronisation.  Resets earlier records. */
+int iblbm_set_taylor_recording(iblbm_sim *sim, int every, int ring);
+
+/* The most recent min(max_records, available) records of one capsule, oldest
+ * first: out [n][16] as in iblbm_get_taylor (may be NULL), steps_out [n] the
+ * step count after which each was taken (may be NULL), *n_records = n.
+ * Synchronising. */
+int iblbm_get_taylor_records(iblbm_sim *sim, int capsule_id, int max_records,
+                             double *out, int64_t *steps_out, int *n_records);
+
+/* Runs n_steps (1..100000) further time steps without graph capture, with
+ * CUDA events on the object's stream around each kernel group, and returns
+ * the mean device time per step in milliseconds of: ms_out[0] membrane
+ * forces + spreading, [1] collide-and-stream, [2] interpolation + advection,
+ * [3] Taylor recording (0 when off).  Advances the simulation like
+ * iblbm_step.  Synchronising. */
+int iblbm_profile_kernels(iblbm_sim *sim, int n_steps, double ms_out[4]);
+
 /* Waits for the stream and returns the first device error recorded since the
  * last call that returned it (then clears it). */
 int iblbm_sync(iblbm_sim *sim);

@@ -62,7 +62,16 @@ struct iblbm_sim {
     double *d_scratch = nullptr;
     size_t scratch_bytes = 0;
 
+    // Taylor recording: after every `rec_every`-th step (0 = off) the device
+    // reductions of all capsules go into a ring of `rec_ring` records.
+    int rec_every = 0;
+    int rec_ring = 0;
+    double *d_ring = nullptr;
+    unsigned long long *d_ring_count = nullptr;
+    std::vector<int64_t> rec_steps;  // step number of every record enqueued
+
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_len = 0;
     int64_t steps = 0;
     std::string err;
 };
@@ -121,6 +130,8 @@ int ensure_scratch(iblbm_sim *s, size_t bytes) {
 
 size_t real_bytes(const iblbm_sim *s) { return s->prec == kF64 ? 8 : 4; }
 
+void free_ring(iblbm_sim *s);
+
 // (Re)builds the device membrane tables after capsules were added.  Current
 // node positions of existing capsules are kept.
 int ensure_mesh(iblbm_sim *s) {
@@ -140,6 +151,7 @@ int ensure_mesh(iblbm_sim *s) {
     for (void *p : s->plan_allocs) dev_free(s, p);
     s->plan_allocs.clear();
     drop_graphs(s);
+    free_ring(s);
 
     const size_t rb = real_bytes(s);
     const size_t v4 = 4 * rb;
@@ -286,11 +298,51 @@ int ensure_mesh(iblbm_sim *s) {
     return IBLBM_OK;
 }
 
-// One time step (sub-step list of Sec. II.C) enqueued on the stream.
-void enqueue_step(iblbm_sim *s) {
+int graph_len_for(const iblbm_sim *s) {
+    const int e = s->rec_every;
+    if (e <= 0) return kGraphSteps;
+    int g = e * ((kGraphSteps + e - 1) / e);
+    if (g % 2) g *= 2;  // keep the buffer parity of a replay unchanged
+    return g;
+}
+
+bool record_after(const iblbm_sim *s, int64_t step_index) {
+    return s->rec_every > 0 && s->d_ring && (step_index + 1) % s->rec_every == 0;
+}
+
+int ensure_ring(iblbm_sim *s) {
+    if (s->rec_every <= 0 || s->d_ring || s->caps.empty()) return IBLBM_OK;
+    s->d_ring = (double *)dev_alloc(s, sizeof(double) * 12 * s->caps.size() * (size_t)s->rec_ring);
+    s->d_ring_count = (unsigned long long *)dev_alloc(s, sizeof(unsigned long long));
+    if (!s->d_ring || !s->d_ring_count) return fail(s, IBLBM_ERR_OOM, "record ring allocation failed");
+    CK(cudaMemsetAsync(s->d_ring_count, 0, sizeof(unsigned long long), s->stream));
+    s->rec_steps.clear();
+    s->plan.ring = s->d_ring;
+    s->plan.ring_len = s->rec_ring;
+    s->plan.ring_count = s->d_ring_count;
+    return IBLBM_OK;
+}
+
+void free_ring(iblbm_sim *s) {
+    dev_free(s, s->d_ring);
+    dev_free(s, s->d_ring_count);
+    s->d_ring = nullptr;
+    s->d_ring_count = nullptr;
+    s->plan.ring = nullptr;
+    s->plan.ring_count = nullptr;
+    s->rec_steps.clear();
+}
+
+// One time step (sub-step list of Sec. II.C) enqueued on the stream, with an
+// optional record of the capsule reductions (sub-step 6) at its end.  With
+// `ev` non-null, events are recorded around each kernel group:
+// ev[0] | spread | ev[1] | collide | ev[2] | interpolate | ev[3] | reductions | ev[4].
+void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) {
     const int c = s->cur, n = 1 - s->cur;
+    if (ev) cudaEventRecord(ev[0], s->stream);
     launch_force_spread(s->prec, s->delta, s->L, s->mesh, s->force[n], s->flags[n], s->d_status,
                         s->stream);
+    if (ev) cudaEventRecord(ev[1], s->stream);
     CollideArgs a;
     a.src = s->pop[c];
     a.dst = s->pop[n];
@@ -302,7 +354,11 @@ void enqueue_step(iblbm_sim *s) {
     a.u_wall = s->u_wall;
     a.status = s->d_status;
     launch_collide_stream(s->prec, s->L, a, s->stream);
+    if (ev) cudaEventRecord(ev[2], s->stream);
     launch_interp_advect(s->prec, s->delta, s->L, s->mesh, s->pop[n], s->force[n], s->stream);
+    if (ev) cudaEventRecord(ev[3], s->stream);
+    if (record) launch_taylor(s->prec, s->mesh, s->plan, true, s->stream);
+    if (ev) cudaEventRecord(ev[4], s->stream);
     s->cur = n;
 }
 
@@ -483,6 +539,7 @@ int iblbm_destroy(iblbm_sim *s) {
     }
     dev_free(s, s->d_status);
     dev_free(s, s->d_scratch);
+    free_ring(s);
     for (void *p : s->mesh_allocs) dev_free(s, p);
     for (void *p : s->plan_allocs) dev_free(s, p);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -594,6 +651,10 @@ int iblbm_init_fluid(iblbm_sim *s, int mode) {
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s->stream));
     s->steps = 0;
+    if (s->d_ring) {
+        CK(cudaMemset(s->d_ring_count, 0, sizeof(unsigned long long)));
+        s->rec_steps.clear();
+    }
     return IBLBM_OK;
 }
 
@@ -603,33 +664,116 @@ int iblbm_step(iblbm_sim *s, int64_t n_steps) {
     CK(cudaSetDevice(s->device));
     int rc = ensure_mesh(s);
     if (rc) return rc;
-    int64_t left = n_steps;
-    while (left >= kGraphSteps) {
-        cudaGraphExec_t &g = s->graph[s->cur];
-        if (!g) {
-            cudaGraph_t graph = nullptr;
-            const int cur0 = s->cur;
-            CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-            for (int k = 0; k < kGraphSteps; ++k) enqueue_step(s);
-            cudaError_t e = cudaStreamEndCapture(s->stream, &graph);
-            s->cur = cur0;
-            if (e != cudaSuccess) return cuda_fail(s, e, "graph capture");
-            e = cudaGraphInstantiate(&g, graph, 0);
-            cudaGraphDestroy(graph);
-            if (e != cudaSuccess) {
-                g = nullptr;
-                return cuda_fail(s, e, "graph instantiation");
-            }
-        }
-        CK(cudaGraphLaunch(g, s->stream));
-        left -= kGraphSteps;  // kGraphSteps is even: parity unchanged
-        s->steps += kGraphSteps;
+    rc = ensure_ring(s);
+    if (rc) return rc;
+    const int G = graph_len_for(s);
+    if (G != s->graph_len) {
+        drop_graphs(s);
+        s->graph_len = G;
     }
-    for (; left > 0; --left) {
-        enqueue_step(s);
-        s->steps++;
+    const int period = s->rec_every > 0 ? s->rec_every : 1;
+    int64_t left = n_steps;
+    while (left > 0) {
+        if (left >= G && s->steps % period == 0) {
+            cudaGraphExec_t &g = s->graph[s->cur];
+            if (!g) {
+                cudaGraph_t graph = nullptr;
+                const int cur0 = s->cur;
+                CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+                for (int k = 0; k < G; ++k) enqueue_step(s, record_after(s, k));
+                cudaError_t e = cudaStreamEndCapture(s->stream, &graph);
+                s->cur = cur0;
+                if (e != cudaSuccess) return cuda_fail(s, e, "graph capture");
+                e = cudaGraphInstantiate(&g, graph, 0);
+                cudaGraphDestroy(graph);
+                if (e != cudaSuccess) {
+                    g = nullptr;
+                    return cuda_fail(s, e, "graph instantiation");
+                }
+            }
+            CK(cudaGraphLaunch(g, s->stream));
+            for (int k = 0; k < G; ++k)
+                if (record_after(s, k)) s->rec_steps.push_back(s->steps + k + 1);
+            left -= G;  // G is even: buffer parity unchanged
+            s->steps += G;
+        } else {
+            const bool rec = record_after(s, s->steps);
+            enqueue_step(s, rec);
+            if (rec) s->rec_steps.push_back(s->steps + 1);
+            s->steps++;
+            left--;
+        }
     }
     CK(cudaGetLastError());
+    return IBLBM_OK;
+}
+
+int iblbm_set_taylor_recording(iblbm_sim *s, int every, int ring) {
+    if (!s) return IBLBM_ERR_ARG;
+    if (every < 0 || (every > 0 && (ring < 1 || ring > (1 << 24))))
+        return fail(s, IBLBM_ERR_ARG, "every must be >= 0 and ring in 1..2^24");
+    CK(cudaSetDevice(s->device));
+    CK(cudaStreamSynchronize(s->stream));
+    free_ring(s);
+    drop_graphs(s);
+    s->rec_every = every;
+    s->rec_ring = every > 0 ? ring : 0;
+    return IBLBM_OK;
+}
+
+static void taylor_from_sums(const double r[12], double out[16]);
+
+int iblbm_get_taylor_records(iblbm_sim *s, int capsule_id, int max_records, double *out,
+                             int64_t *steps_out, int *n_out) {
+    if (!s || !n_out || max_records < 0) return IBLBM_ERR_ARG;
+    if (capsule_id < 0 || capsule_id >= (int)s->caps.size()) return fail(s, IBLBM_ERR_ARG, "no such capsule");
+    int rc = sync_status(s);
+    if (rc) return rc;
+    *n_out = 0;
+    if (!s->d_ring) return IBLBM_OK;
+    unsigned long long count = 0;
+    CK(cudaMemcpy(&count, s->d_ring_count, sizeof(count), cudaMemcpyDeviceToHost));
+    const long long avail = std::min<long long>((long long)count, s->rec_ring);
+    const long long n = std::min<long long>(avail, max_records);
+    const int nc = (int)s->caps.size();
+    for (long long k = 0; k < n; ++k) {
+        const unsigned long long idx = count - n + k;  // oldest first
+        const size_t slot = (size_t)(idx % (unsigned long long)s->rec_ring);
+        double r[12];
+        CK(cudaMemcpy(r, s->d_ring + (slot * nc + capsule_id) * 12, sizeof(r), cudaMemcpyDeviceToHost));
+        if (out) taylor_from_sums(r, out + 16 * k);
+        if (steps_out) steps_out[k] = idx < s->rec_steps.size() ? s->rec_steps[idx] : -1;
+    }
+    *n_out = (int)n;
+    return IBLBM_OK;
+}
+
+int iblbm_profile_kernels(iblbm_sim *s, int n_steps, double ms_out[4]) {
+    if (!s || !ms_out || n_steps < 1 || n_steps > 100000) return IBLBM_ERR_ARG;
+    CK(cudaSetDevice(s->device));
+    int rc = ensure_mesh(s);
+    if (rc) return rc;
+    rc = ensure_ring(s);
+    if (rc) return rc;
+    std::vector<cudaEvent_t> ev(5 * (size_t)n_steps, nullptr);
+    for (auto &e : ev) CK(cudaEventCreate(&e));
+    for (int k = 0; k < n_steps; ++k) {
+        const bool rec = record_after(s, s->steps);
+        enqueue_step(s, rec, ev.data() + 5 * (size_t)k);
+        if (rec) s->rec_steps.push_back(s->steps + 1);
+        s->steps++;
+    }
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    double acc[4] = {0, 0, 0, 0};
+    for (int k = 0; k < n_steps && e == cudaSuccess; ++k)
+        for (int j = 0; j < 4; ++j) {
+            float ms = 0.0f;
+            e = cudaEventElapsedTime(&ms, ev[5 * k + j], ev[5 * k + j + 1]);
+            acc[j] += ms;
+        }
+    for (auto &x : ev) cudaEventDestroy(x);
+    if (e != cudaSuccess) return cuda_fail(s, e, "kernel timing");
+    for (int j = 0; j < 4; ++j) ms_out[j] = acc[j] / n_steps;
     return IBLBM_OK;
 }
 
@@ -772,11 +916,19 @@ int iblbm_get_taylor(iblbm_sim *s, int id, double out[16]) {
     if (rc) return rc;
     rc = ensure_mesh(s);
     if (rc) return rc;
-    launch_taylor(s->prec, s->mesh, s->plan, s->stream);
+    launch_taylor(s->prec, s->mesh, s->plan, false, s->stream);
     CK(cudaGetLastError());
     double r[12];
     CK(cudaMemcpyAsync(r, s->plan.out + 12 * id, sizeof(r), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
+    taylor_from_sums(r, out);
+    return IBLBM_OK;
+}
+
+}  // extern "C"
+
+// {V, A, c, I} of the device reductions -> the 16 outputs of iblbm_get_taylor.
+static void taylor_from_sums(const double r[12], double out[16]) {
     const double V = r[0];
     const double I[9] = {r[5], r[8], r[9], r[8], r[6], r[10], r[9], r[10], r[7]};
     double J[9], val[3], vec[9];
@@ -784,24 +936,21 @@ int iblbm_get_taylor(iblbm_sim *s, int id, double out[16]) {
     sym_eig3(J, val, vec);
     const double ra = std::sqrt(std::max(0.0, 2.5 * (val[1] + val[2] - val[0])));
     const double rb = std::sqrt(std::max(0.0, 2.5 * (val[0] + val[2] - val[1])));
-    const double rc2 = std::sqrt(std::max(0.0, 2.5 * (val[0] + val[1] - val[2])));
+    const double rc = std::sqrt(std::max(0.0, 2.5 * (val[0] + val[1] - val[2])));
     double vx = vec[0], vz = vec[6];
     if (vx < 0.0) {
         vx = -vx;
         vz = -vz;
     }
-    out[0] = (ra - rc2) / (ra + rc2);
+    out[0] = (ra - rc) / (ra + rc);
     out[1] = std::atan2(vz, vx);
     out[2] = ra;
     out[3] = rb;
-    out[4] = rc2;
+    out[4] = rc;
     out[5] = V;
     out[6] = r[1];
     out[7] = r[2];
     out[8] = r[3];
     out[9] = r[4];
     for (int k = 0; k < 6; ++k) out[10 + k] = r[5 + k];
-    return IBLBM_OK;
 }
-
-}  // extern "C"

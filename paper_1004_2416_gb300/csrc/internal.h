@@ -98,11 +98,15 @@ struct TaylorPlan {
     const int *blk_nface;   // [total_blocks]
     const int *cap_blk0;    // [n_caps + 1] first block of each capsule
     const double *origin;   // [n_caps][3]
-    double *partial;        // scratch [total_blocks][8]
-    double *out;            // [n_caps][12]
+    double *partial;        // scratch [total_blocks][16]
+    double *out;            // [n_caps][12] results of an immediate reduction
+    double *ring;           // [ring_len][n_caps][12] recorded results (or null)
+    int ring_len;
+    unsigned long long *ring_count;  // records written so far
 };
 constexpr int kTaylorFacesPerBlock = 128;
-void launch_taylor(int prec, const MeshDev &m, const TaylorPlan &p, cudaStream_t s);
+// record = false: results to p.out; record = true: to the next ring slot.
+void launch_taylor(int prec, const MeshDev &m, const TaylorPlan &p, bool record, cudaStream_t s);
 
 // ---- mesh.cpp (host) -------------------------------------------------------------------
 // Canonical icosphere: nodes [n][3], faces [f][3]

@@ -144,35 +144,45 @@ __global__ void __launch_bounds__(kTB) k_taylor_stage2(R nodes, const int4 *__re
         for (int k = 0; k < 6; ++k) p.partial[16 * b + 8 + k] = v[k];
 }
 
-__global__ void k_taylor_stage3(TaylorPlan p) {
-    const int cap = blockIdx.x * blockDim.x + threadIdx.x;
-    if (cap >= p.n_caps) return;
-    double tot[5];
-    capsule_totals1(p, cap, tot);
-    double I[6] = {0, 0, 0, 0, 0, 0};
-    for (int b = p.cap_blk0[cap]; b < p.cap_blk0[cap + 1]; ++b)
-        for (int k = 0; k < 6; ++k) I[k] += p.partial[16 * b + 8 + k];
-    double *o = p.out + 12 * cap;
-    o[0] = tot[0];
-    o[1] = tot[1];
-    for (int k = 0; k < 3; ++k) o[2 + k] = p.origin[3 * cap + k] + tot[2 + k] / (4.0 * tot[0]);
-    for (int k = 0; k < 6; ++k) o[5 + k] = I[k];
-    o[11] = 0.0;
+// One block; threads stride over the capsules.  In recording mode the block
+// writes the next ring slot and then advances the record counter.
+__global__ void k_taylor_stage3(TaylorPlan p, int record) {
+    double *base = p.out;
+    unsigned long long count = 0;
+    if (record) {
+        count = *p.ring_count;
+        base = p.ring + (size_t)(count % (unsigned long long)p.ring_len) * p.n_caps * 12;
+    }
+    for (int cap = threadIdx.x; cap < p.n_caps; cap += blockDim.x) {
+        double tot[5];
+        capsule_totals1(p, cap, tot);
+        double I[6] = {0, 0, 0, 0, 0, 0};
+        for (int b = p.cap_blk0[cap]; b < p.cap_blk0[cap + 1]; ++b)
+            for (int k = 0; k < 6; ++k) I[k] += p.partial[16 * b + 8 + k];
+        double *o = base + 12 * cap;
+        o[0] = tot[0];
+        o[1] = tot[1];
+        for (int k = 0; k < 3; ++k) o[2 + k] = p.origin[3 * cap + k] + tot[2 + k] / (4.0 * tot[0]);
+        for (int k = 0; k < 6; ++k) o[5 + k] = I[k];
+        o[11] = 0.0;
+    }
+    __syncthreads();
+    if (record && threadIdx.x == 0) *p.ring_count = count + 1;
 }
 
 template <typename R>
-static void taylor_impl(R nodes, const MeshDev &m, const TaylorPlan &p, cudaStream_t s) {
+static void taylor_impl(R nodes, const MeshDev &m, const TaylorPlan &p, bool record, cudaStream_t s) {
     k_taylor_stage1<R><<<p.total_blocks, kTB, 0, s>>>(nodes, (const int4 *)m.tri, p);
     k_taylor_stage2<R><<<p.total_blocks, kTB, 0, s>>>(nodes, (const int4 *)m.tri, p);
-    k_taylor_stage3<<<(p.n_caps + 127) / 128, 128, 0, s>>>(p);
+    k_taylor_stage3<<<1, 256, 0, s>>>(p, record ? 1 : 0);
 }
 
-void launch_taylor(int prec, const MeshDev &m, const TaylorPlan &p, cudaStream_t s) {
-    if (p.n_caps == 0) return;
+void launch_taylor(int prec, const MeshDev &m, const TaylorPlan &p, bool record, cudaStream_t s) {
+    if (p.n_caps == 0 || (record && !p.ring)) return;
     if (prec == kF64)
-        taylor_impl(NodeRead<double>{(const dvec4 *)m.x}, m, p, s);
+        taylor_impl(NodeRead<double>{(const dvec4 *)m.x}, m, p, record, s);
     else
-        taylor_impl(NodeRead<float>{(const float4 *)m.x, (const float4 *)m.x_lo}, m, p, s);
+        taylor_impl(NodeRead<float>{(const float4 *)m.x, (const float4 *)m.x_lo}, m, p, record, s);
 }
 
 }  // namespace iblbm

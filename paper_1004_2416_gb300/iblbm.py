@@ -88,6 +88,9 @@ _SIGS = {
     "iblbm_get_mesh": (_int, [_vp, _int, _ip, _ip, _i32p]),
     "iblbm_get_taylor": (_int, [_vp, _int, _dp]),
     "iblbm_icosphere": (_int, [_int, _dbl, _dp, _dp, _i32p]),
+    "iblbm_set_taylor_recording": (_int, [_vp, _int, _int]),
+    "iblbm_get_taylor_records": (_int, [_vp, _int, _int, _dp, ctypes.POINTER(ctypes.c_int64), _ip]),
+    "iblbm_profile_kernels": (_int, [_vp, _int, _dp]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -289,6 +292,25 @@ class Sim:
 
     def get_node_velocities(self, capsule_id: int = -1):
         return self._nodes(iblbm_get_node_velocities, capsule_id)
+
+    def set_taylor_recording(self, every: int, ring: int = 1024):
+        _check(iblbm_set_taylor_recording(self._h, every, ring), self._h)
+
+    def taylor_records(self, capsule_id: int = 0, max_records: int = 1 << 20):
+        """(steps [n], records [n, 16]) of the recorded shape measures."""
+        n = _int()
+        _check(iblbm_get_taylor_records(self._h, capsule_id, 0, None, None, ctypes.byref(n)), self._h)
+        out = np.empty((max(1, min(max_records, 1 << 24)), 16), np.float64)
+        steps = np.empty(out.shape[0], np.int64)
+        _check(iblbm_get_taylor_records(self._h, capsule_id, out.shape[0], _d(out),
+                                        steps.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                        ctypes.byref(n)), self._h)
+        return steps[:n.value], out[:n.value]
+
+    def profile_kernels(self, n_steps: int) -> dict:
+        ms = np.zeros(4, np.float64)
+        _check(iblbm_profile_kernels(self._h, int(n_steps), _d(ms)), self._h)
+        return dict(zip(("force_spread", "collide_stream", "interp_advect", "taylor"), ms.tolist()))
 
     def taylor(self, capsule_id: int = 0) -> dict:
         out = np.empty(16, np.float64)

@@ -47,7 +47,8 @@ def test_lattice_only_ragged(prec):
     assert rel_inf(g_gpu, g_ref) < tol
     u_ref = np.einsum("ia,izyx->azyx", c.astype(float), f) / f.sum(axis=0)
     assert rel_inf(s.get_velocity(), u_ref) < tol
-    assert abs(s.get_density().sum() - f.sum(axis=0).sum()) / f.sum(axis=0).sum() < 1e-12
+    mass_tol = {"fp64": 1e-13, "fp32": 1e-8, "fp16": 1e-5}[prec]  # rounding of the storage type
+    assert abs(s.get_density().sum() - f.sum(axis=0).sum()) / f.sum(axis=0).sum() < mass_tol
 
 
 @pytest.mark.parametrize("shape", [(1, 1, 4), (3, 2, 5), (33, 9, 2)])
