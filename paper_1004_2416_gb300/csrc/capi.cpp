@@ -171,11 +171,10 @@ int ensure_mesh(iblbm_sim *s) {
     void *adj_off = A(sizeof(int) * (nn + 1));
     void *adj = A(sizeof(int) * 3 * nf);
     void *tri4 = A(sizeof(int) * 4 * nf);
-    void *fconst = A(v4 * nf);
-    void *A0 = A(rb * nf);
+    void *fconst = A(3 * v4 * nf);
     void *capmod = A(v4 * nc);
     if (!m.x || (s->prec != kF64 && !m.x_lo) || !m.F || !m.u || !adj_off || !adj || !tri4 ||
-        !fconst || !A0 || !capmod)
+        !fconst || !capmod)
         return fail(s, IBLBM_ERR_OOM, "membrane table allocation failed");
 
     // node -> (face, corner) lists in ascending face order
@@ -192,7 +191,8 @@ int ensure_mesh(iblbm_sim *s) {
             for (int k = 0; k < 3; ++k) ent[fill[s->tri[3 * f + k]]++] = 4 * f + k;
     }
     std::vector<int> t4(4 * (size_t)nf);
-    std::vector<double> fc(4 * (size_t)nf), a0(nf), cm(4 * (size_t)nc, 0.0);
+    std::vector<double> fc(12 * (size_t)nf, 0.0), cm(4 * (size_t)nc, 0.0);
+    const bool split = s->prec != kF64;  // float builds: G as float hi + lo
     for (int c = 0; c < nc; ++c) {
         const Capsule &cp = s->caps[c];
         cm[4 * c] = cp.ks / 6.0;
@@ -214,11 +214,18 @@ int ensure_mesh(iblbm_sim *s) {
         const double G22 = V[0] * V[0] + V[1] * V[1] + V[2] * V[2];
         const double det = G11 * G22 - G12 * G12;
         if (!(det > 0.0)) return fail(s, IBLBM_ERR_ARG, "degenerate reference face");
-        fc[4 * f] = G22 / det;      // alpha
-        fc[4 * f + 1] = G12 / det;  // beta
-        fc[4 * f + 2] = G11 / det;  // gamma
-        fc[4 * f + 3] = 1.0 / det;  // kappa
-        a0[f] = 0.5 * std::sqrt(det);
+        double *q = fc.data() + 12 * (size_t)f;
+        q[0] = G22 / det;  // alpha
+        q[1] = G12 / det;  // beta
+        q[2] = G11 / det;  // gamma
+        q[3] = 1.0 / det;  // kappa
+        q[4] = 0.5 * std::sqrt(det);  // A0
+        const double G[3] = {G11, G12, G22};
+        for (int k = 0; k < 3; ++k) {
+            const double hi = split ? (double)(float)G[k] : G[k];
+            q[5 + k] = hi;
+            q[8 + k] = split ? (double)(float)(G[k] - hi) : 0.0;
+        }
     }
     auto up_real = [&](void *dst, const std::vector<double> &v) -> cudaError_t {
         if (s->prec == kF64)
@@ -232,7 +239,6 @@ int ensure_mesh(iblbm_sim *s) {
     CK(cudaMemcpyAsync(adj, ent.data(), sizeof(int) * ent.size(), cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(tri4, t4.data(), sizeof(int) * t4.size(), cudaMemcpyHostToDevice, s->stream));
     CK(up_real(fconst, fc));
-    CK(up_real(A0, a0));
     CK(up_real(capmod, cm));
     CK(cudaMemsetAsync(m.F, 0, v4 * nn, s->stream));
     CK(cudaMemsetAsync(m.u, 0, v4 * nn, s->stream));
@@ -240,7 +246,6 @@ int ensure_mesh(iblbm_sim *s) {
     m.adj = (const int *)adj;
     m.tri = (const int *)tri4;
     m.fconst = fconst;
-    m.A0 = A0;
     m.capmod = capmod;
     s->mesh = m;
     // positions
@@ -468,7 +473,7 @@ int iblbm_create(iblbm_sim **out, int nx, int ny, int nz, double tau, int precis
     }
     iblbm_sim *s = new (std::nothrow) iblbm_sim();
     if (!s) return IBLBM_ERR_OOM;
-    s->L = make_lattice(nx, ny, nz);
+    s->L = make_lattice(nx, ny, nz, precision != kF64);
     s->prec = precision;
     s->delta = delta_points;
     s->tau = tau;

@@ -130,6 +130,31 @@ __device__ __forceinline__ void two_sum_add(float &hi, float &lo, float d) {
     hi = t;
 }
 
+// Double-float (unevaluated sum h + l of two floats) helpers.
+struct DF {
+    float h, l;
+};
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+    float s = a + b;
+    float bb = s - a;
+    return DF{s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ DF df_fast_two_sum(float a, float b) {  // |a| >= |b|
+    float s = a + b;
+    return DF{s, b - (s - a)};
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+    float p = a.h * b.h;
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    return df_fast_two_sum(p, e);
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    DF s = df_two_sum(a.h, b.h);
+    return df_fast_two_sum(s.h, s.l + (a.l + b.l));
+}
+
 __device__ __forceinline__ int wrap_index(int a, int n) {
     int r = a % n;
     return r < 0 ? r + n : r;

@@ -18,16 +18,24 @@
 // shell of the lattice), and a warp reduction gives the node velocity.
 //
 // Face energy gradient.  With the current edge vectors u = x_b - x_a,
-// v = x_c - x_a, their Gram entries g11 = u.u, g12 = u.v, g22 = v.v and the
-// reference constants alpha, beta, gamma, kappa of the face (the entries of the
-// inverse reference Gram matrix and 1/det of it, prepared on the host), the
-// invariants of Sec. II.B are
-//     I1 = alpha g11 - 2 beta g12 + gamma g22 - 2,
-//     I2 = kappa (g11 g22 - g12^2) - 1,
-// and with w1 = dw/dI1 = k_s (I1 + 1)/6, w2 = dw/dI2 = (k_alpha I2 - k_s)/6
-//     dW/du = 2 A0 [(w1 alpha + w2 kappa g22) u - (w1 beta + w2 kappa g12) v],
-//     dW/dv = 2 A0 [(w1 gamma + w2 kappa g11) v - (w1 beta + w2 kappa g12) u];
+// v = x_c - x_a, their Gram entries g11 = u.u, g12 = u.v, g22 = v.v, the
+// reference Gram entries G11, G12, G22 and the reference constants
+// alpha = G22/det, beta = G12/det, gamma = G11/det, kappa = 1/det
+// (det = G11 G22 - G12^2; prepared on the host), the invariants of Sec. II.B
+// are, with the deviations d = g - G,
+//     I1 = alpha d11 - 2 beta d12 + gamma d22,
+//     I2 = I1 + kappa (d11 d22 - d12^2),
+// (tr(G^-1 g) - 2 and det g / det G - 1 written so that nothing of order one
+// cancels), and with w1 = dw/dI1 = k_s (I1 + 1)/6, w2 = dw/dI2 =
+// (k_alpha I2 - k_s)/6 and kappa G22 = alpha, kappa G12 = beta, kappa G11 = gamma
+//     dW/du = s_uu u + s_uv v,   dW/dv = s_uv u + s_vv v,
+//     s_uu =  2 A0 [k_s/6 (I1 alpha - kappa d22) + k_alpha/6 I2 kappa g22],
+//     s_uv = -2 A0 [k_s/6 (I1 beta  - kappa d12) + k_alpha/6 I2 kappa g12],
+//     s_vv =  2 A0 [k_s/6 (I1 gamma - kappa d11) + k_alpha/6 I2 kappa g11];
 // the corner forces are F_b = -dW/du, F_c = -dW/dv, F_a = dW/du + dW/dv.
+// In the float builds the edges and the Gram entries are formed in
+// double-float arithmetic from the hi/lo node coordinates, so the deviations
+// d keep their relative precision even for strains of 1e-4.
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -44,6 +52,14 @@ struct PosView<double> {
         dvec4 pa = x[a], pb = x[b], pc = x[c];
         u[0] = pb.x - pa.x; u[1] = pb.y - pa.y; u[2] = pb.z - pa.z;
         v[0] = pc.x - pa.x; v[1] = pc.y - pa.y; v[2] = pc.z - pa.z;
+    }
+    // edges u, v and the Gram deviations d = g - G0 (G0 in c1.y, c1.z, c1.w)
+    __device__ __forceinline__ void edge_gram(int a, int b, int c, const dvec4 &c1, const dvec4 &c2,
+                                              double u[3], double v[3], double d[3]) const {
+        edges(a, b, c, u, v);
+        d[0] = (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) - c1.y;
+        d[1] = (u[0] * v[0] + u[1] * v[1] + u[2] * v[2]) - c1.z;
+        d[2] = (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) - c1.w;
     }
     __device__ __forceinline__ void approx(int n, double p[3]) const {
         dvec4 q = x[n];
@@ -74,6 +90,30 @@ struct PosView<float> {
         v[0] = (hc.x - ha.x) + (lc.x - la.x);
         v[1] = (hc.y - ha.y) + (lc.y - la.y);
         v[2] = (hc.z - ha.z) + (lc.z - la.z);
+    }
+    // Edges as double-float pairs, Gram entries in double-float, deviations
+    // from the reference Gram entries (hi in c1.y..w, lo in c2.x..z) in float.
+    __device__ __forceinline__ void edge_gram(int a, int b, int c, const float4 &c1, const float4 &c2,
+                                              float u[3], float v[3], float d[3]) const {
+        float4 ha = hi[a], hb = hi[b], hc = hi[c];
+        float4 la = lo[a], lb = lo[b], lc = lo[c];
+        DF U[3], V[3];
+        U[0] = df_two_sum(hb.x - ha.x, lb.x - la.x);
+        U[1] = df_two_sum(hb.y - ha.y, lb.y - la.y);
+        U[2] = df_two_sum(hb.z - ha.z, lb.z - la.z);
+        V[0] = df_two_sum(hc.x - ha.x, lc.x - la.x);
+        V[1] = df_two_sum(hc.y - ha.y, lc.y - la.y);
+        V[2] = df_two_sum(hc.z - ha.z, lc.z - la.z);
+        DF g11 = df_add(df_add(df_mul(U[0], U[0]), df_mul(U[1], U[1])), df_mul(U[2], U[2]));
+        DF g12 = df_add(df_add(df_mul(U[0], V[0]), df_mul(U[1], V[1])), df_mul(U[2], V[2]));
+        DF g22 = df_add(df_add(df_mul(V[0], V[0]), df_mul(V[1], V[1])), df_mul(V[2], V[2]));
+        d[0] = (g11.h - c1.y) + (g11.l - c2.x);
+        d[1] = (g12.h - c1.z) + (g12.l - c2.y);
+        d[2] = (g22.h - c1.w) + (g22.l - c2.z);
+        for (int k = 0; k < 3; ++k) {
+            u[k] = U[k].h;
+            v[k] = V[k].h;
+        }
     }
     // p holds hi in [0..2] and lo in [3..5]
     __device__ __forceinline__ void approx(int n, float p[6]) const {
@@ -121,11 +161,11 @@ template <int N, typename T>
 __global__ void __launch_bounds__(256)
     k_force_spread(int n_nodes, PosView<T> pos, const int *__restrict__ adj_off,
                    const int *__restrict__ adj, const int4 *__restrict__ tri,
-                   const typename Vec4<T>::type *__restrict__ fconst, const T *__restrict__ A0,
+                   const typename Vec4<T>::type *__restrict__ fconst,
                    const typename Vec4<T>::type *__restrict__ capmod,
                    typename Vec4<T>::type *__restrict__ nodeF,
                    typename Vec4<T>::type *__restrict__ force, uint8_t *__restrict__ flags, int nx,
-                   int ny, int nz, int ntx, int nty, int *status) {
+                   int ny, int nz, int ftx, int fty, int nfx, int nfy, int *status) {
     using V4 = typename Vec4<T>::type;
     const int lane = threadIdx.x & 31;
     const int node = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
@@ -137,21 +177,19 @@ __global__ void __launch_bounds__(256)
         const int ent = adj[e];
         const int f = ent >> 2, corner = ent & 3;
         const int4 t = tri[f];
-        T u[3], v[3];
-        pos.edges(t.x, t.y, t.z, u, v);
-        const V4 c = fconst[f];  // alpha, beta, gamma, kappa
-        const T a2 = T(2) * A0[f];
+        const V4 c0 = fconst[3 * f];      // alpha, beta, gamma, kappa
+        const V4 c1 = fconst[3 * f + 1];  // A0, G11, G12, G22 (hi parts in float builds)
+        const V4 c2 = fconst[3 * f + 2];  // lo parts of G11, G12, G22 (float builds)
+        T u[3], v[3], d[3];
+        pos.edge_gram(t.x, t.y, t.z, c1, c2, u, v, d);
         const V4 m = capmod[t.w];  // k_s/6, k_alpha/6
-        const T g11 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        const T g12 = u[0] * v[0] + u[1] * v[1] + u[2] * v[2];
-        const T g22 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-        const T I1 = c.x * g11 - T(2) * c.y * g12 + c.z * g22 - T(2);
-        const T I2 = c.w * (g11 * g22 - g12 * g12) - T(1);
-        const T w1 = m.x * (I1 + T(1));
-        const T w2 = m.y * I2 - m.x;
-        const T s_uu = a2 * (w1 * c.x + w2 * c.w * g22);
-        const T s_uv = -a2 * (w1 * c.y + w2 * c.w * g12);
-        const T s_vv = a2 * (w1 * c.z + w2 * c.w * g11);
+        const T I1 = c0.x * d[0] - T(2) * c0.y * d[1] + c0.z * d[2];
+        const T I2 = I1 + c0.w * (d[0] * d[2] - d[1] * d[1]);
+        const T a2 = T(2) * c1.x;
+        const T kI2 = m.y * I2 * c0.w;  // k_alpha/6 I2 kappa
+        const T s_uu = a2 * (m.x * (I1 * c0.x - c0.w * d[2]) + kI2 * (c1.w + d[2]));
+        const T s_uv = -a2 * (m.x * (I1 * c0.y - c0.w * d[1]) + kI2 * (c1.z + d[1]));
+        const T s_vv = a2 * (m.x * (I1 * c0.z - c0.w * d[0]) + kI2 * (c1.y + d[0]));
         T ku, kv;
         if (corner == 0) {
             ku = s_uu + s_uv;
@@ -196,7 +234,7 @@ __global__ void __launch_bounds__(256)
         const int xw = wrap_index(X, nx), yw = wrap_index(Y, ny);
         const long long cell = xw + (long long)nx * (yw + (long long)ny * Z);
         add_force(&force[cell], w * fx, w * fy, w * fz);
-        flags[((long long)Z * nty + yw / kTileY) * ntx + xw / kTileX] = 1;
+        flags[((long long)Z * nfy + yw / fty) * nfx + xw / ftx] = 1;
     }
 }
 
@@ -323,8 +361,8 @@ static void force_spread_impl(const Lattice &L, const MeshDev &m, void *force, u
     unsigned nb = (unsigned)((m.n_nodes + kNodesPerBlock - 1) / kNodesPerBlock);
     k_force_spread<N, T><<<nb, 32 * kNodesPerBlock, 0, s>>>(
         m.n_nodes, view<T>(m), m.adj_off, m.adj, (const int4 *)m.tri, (const V4 *)m.fconst,
-        (const T *)m.A0, (const V4 *)m.capmod, (V4 *)m.F, (V4 *)force, flags, L.nx, L.ny, L.nz,
-        L.ntx, L.nty, status);
+        (const V4 *)m.capmod, (V4 *)m.F, (V4 *)force, flags, L.nx, L.ny, L.nz,
+        L.ftx, L.fty, L.nfx, L.nfy, status);
 }
 
 template <int N, typename S, typename T>

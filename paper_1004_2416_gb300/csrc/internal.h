@@ -11,27 +11,41 @@
 
 namespace iblbm {
 
-// Lattice geometry.  Tiles of kTileX x kTileY x 1 cells are the unit of the
-// collide-stream thread block and of the sparse force-density bookkeeping.
+// Lattice geometry.  The scalar collide-stream kernel works on tiles of
+// kTileX x kTileY x 1 cells; the vectorised one on whole x-rows (4 cells per
+// thread, nx/4 lanes per row, nx/4 a power of two <= 32).  The sparse
+// force-density flags have the granularity of the kernel in use:
+// ftx x fty x 1 cells per flag.
 constexpr int kTileX = 32;
 constexpr int kTileY = 8;
 
 struct Lattice {
     int nx, ny, nz;
-    int ntx, nty;  // tiles along x and y
+    int ntx, nty;   // scalar-kernel tiles along x and y
+    int lanes_row;  // vectorised kernel: nx / 4 lanes per row; 0 = scalar kernel
+    int ftx, fty;   // cells per force flag along x and y
+    int nfx, nfy;   // flags along x and y
     long long ncell;
-    long long ntiles;
+    long long ntiles;  // number of force flags
 };
 
-inline Lattice make_lattice(int nx, int ny, int nz) {
+inline bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// vec: allow the vectorised kernel (float and half storage).
+inline Lattice make_lattice(int nx, int ny, int nz, bool vec) {
     Lattice L;
     L.nx = nx;
     L.ny = ny;
     L.nz = nz;
     L.ntx = (nx + kTileX - 1) / kTileX;
     L.nty = (ny + kTileY - 1) / kTileY;
+    L.lanes_row = (vec && nx % 4 == 0 && is_pow2(nx / 4) && nx / 4 <= 32) ? nx / 4 : 0;
+    L.ftx = L.lanes_row ? nx : kTileX;
+    L.fty = L.lanes_row ? 1 : kTileY;
+    L.nfx = (nx + L.ftx - 1) / L.ftx;
+    L.nfy = (ny + L.fty - 1) / L.fty;
     L.ncell = (long long)nx * ny * nz;
-    L.ntiles = (long long)L.ntx * L.nty * nz;
+    L.ntiles = (long long)L.nfx * L.nfy * nz;
     return L;
 }
 
@@ -50,8 +64,8 @@ struct MeshDev {
     const int *adj_off;   // [n_nodes + 1]
     const int *adj;       // [adj_off[n]] entries face*4 + corner
     const int *tri;       // int4 [n_faces]: a, b, c, capsule
-    const void *fconst;   // Vec4 [n_faces]: alpha, beta, gamma, kappa
-    const void *A0;       // T [n_faces]
+    const void *fconst;   // Vec4 [n_faces][3]: (alpha, beta, gamma, kappa),
+                          // (A0, G11, G12, G22), (G11, G12, G22 low parts, 0)
     const void *capmod;   // Vec4 [n_caps]: k_s/6, k_alpha/6, 0, 0
 };
 

@@ -115,6 +115,154 @@ __global__ void __launch_bounds__(kTileX *kTileY)
     }
 }
 
+// Vector loads and stores of 4 consecutive cells of one direction.
+template <typename S>
+struct Quad;
+template <>
+struct Quad<float> {
+    static __device__ __forceinline__ void load(const float *p, float v[4]) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+    static __device__ __forceinline__ void store(float *p, float a, float b, float c, float d) {
+        *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+    }
+};
+template <>
+struct Quad<__half> {
+    static __device__ __forceinline__ void load(const __half *p, float v[4]) {
+        const uint2 q = __ldg(reinterpret_cast<const uint2 *>(p));
+        const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&q.x));
+        const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&q.y));
+        v[0] = a.x * kHalfInvScale; v[1] = a.y * kHalfInvScale;
+        v[2] = b.x * kHalfInvScale; v[3] = b.y * kHalfInvScale;
+    }
+    static __device__ __forceinline__ void store(__half *p, float a, float b, float c, float d) {
+        const __half2 lo = __floats2half2_rn(a * kHalfScale, b * kHalfScale);
+        const __half2 hi = __floats2half2_rn(c * kHalfScale, d * kHalfScale);
+        uint2 q;
+        q.x = *reinterpret_cast<const unsigned *>(&lo);
+        q.y = *reinterpret_cast<const unsigned *>(&hi);
+        *reinterpret_cast<uint2 *>(p) = q;
+    }
+};
+
+// Vectorised collide-and-stream for nx = 4 * LR, LR a power of two <= 32:
+// each thread owns 4 consecutive cells of one x-row, LR lanes cover the row,
+// a warp covers 32 / LR rows and a block of 8 warps 8 * 32 / LR rows.  All 19
+// loads and stores are 16-byte (float) or 8-byte (half) vectors.  Streaming
+// along x shifts a thread's 4 post-collision values by one cell; the value
+// that crosses into the neighbouring thread's quad comes by a warp shuffle
+// within the row's lane segment, which also closes the periodic wrap in x.
+// One force flag per row.
+template <typename S, int LR>
+__global__ void __launch_bounds__(256, 2)
+    k_collide_stream_x4(const S *__restrict__ src, S *__restrict__ dst,
+                        const float4 *__restrict__ fcur, const uint8_t *__restrict__ flag_cur,
+                        float4 *__restrict__ fold, uint8_t *__restrict__ flag_old, int ny, int nz,
+                        int ncell, float omega, float u_wall, int *status) {
+    constexpr int NX = 4 * LR;
+    constexpr int RPW = 32 / LR;
+    const int lane = threadIdx.x & 31;
+    const int lx = lane & (LR - 1);
+    const int nrows = ny * nz;
+    const int row_raw = blockIdx.x * (8 * RPW) + (threadIdx.x >> 5) * RPW + lane / LR;
+    const bool active = row_raw < nrows;
+    const int row = active ? row_raw : nrows - 1;  // inactive lanes still join the shuffles
+    const int y = row % ny, z = row / ny;
+    const int x0 = 4 * lx;
+    const int cell0 = x0 + NX * row;
+
+    const bool has_old = flag_old[row] != 0;
+    const bool has_cur = flag_cur[row] != 0;
+    if (has_old && active) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) fold[cell0 + k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncwarp();
+    if (has_old && active && lx == 0) flag_old[row] = 0;
+
+    float g[19][4];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) Quad<S>::load(src + (size_t)i * ncell + cell0, g[i]);
+
+    float drho[4], ux[4], uy[4], uz[4], fx[4], fy[4], fz[4], uu15[4], uf[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            d += g[i][k];
+            if (q_cx(i)) jx += q_cx(i) > 0 ? g[i][k] : -g[i][k];
+            if (q_cy(i)) jy += q_cy(i) > 0 ? g[i][k] : -g[i][k];
+            if (q_cz(i)) jz += q_cz(i) > 0 ? g[i][k] : -g[i][k];
+        }
+        fx[k] = fy[k] = fz[k] = 0.f;
+        if (has_cur) {
+            const float4 f = fcur[cell0 + k];
+            fx[k] = f.x; fy[k] = f.y; fz[k] = f.z;
+        }
+        const float rho = 1.f + d;
+        if (active && !(rho > 0.5f && rho < 2.f)) set_status(status, kStatusUnstable);
+        const float inv = 1.f / rho;
+        drho[k] = d;
+        ux[k] = (jx + 0.5f * fx[k]) * inv;
+        uy[k] = (jy + 0.5f * fy[k]) * inv;
+        uz[k] = (jz + 0.5f * fz[k]) * inv;
+        uu15[k] = 1.5f * (ux[k] * ux[k] + uy[k] * uy[k] + uz[k] * uz[k]);
+        uf[k] = ux[k] * fx[k] + uy[k] * fy[k] + uz[k] * fz[k];
+    }
+    const float guo = 1.f - 0.5f * omega;
+    const int yp = (y + 1 == ny) ? 0 : y + 1;
+    const int ym = (y == 0) ? ny - 1 : y - 1;
+    const int left = (lx + LR - 1) & (LR - 1), right = (lx + 1) & (LR - 1);
+
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int cx = q_cx(i), cy = q_cy(i), cz = q_cz(i);
+        const float w = q_w<float>(i);
+        float p[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float cu = 0.f;
+            if (cx) cu += cx > 0 ? ux[k] : -ux[k];
+            if (cy) cu += cy > 0 ? uy[k] : -uy[k];
+            if (cz) cu += cz > 0 ? uz[k] : -uz[k];
+            const float rho = 1.f + drho[k];
+            const float geq = w * (drho[k] + rho * (3.f * cu + 4.5f * cu * cu - uu15[k]));
+            p[k] = g[i][k] - omega * (g[i][k] - geq);
+            if (has_cur) {
+                float cf = 0.f;
+                if (cx) cf += cx > 0 ? fx[k] : -fx[k];
+                if (cy) cf += cy > 0 ? fy[k] : -fy[k];
+                if (cz) cf += cz > 0 ? fz[k] : -fz[k];
+                p[k] += guo * w * (3.f * (cf - uf[k]) + 9.f * cu * cf);
+            }
+        }
+        // x shift of the quad (before any branch: every lane takes part)
+        float o0 = p[0], o1 = p[1], o2 = p[2], o3 = p[3];
+        if (cx > 0) {
+            const float in = __shfl_sync(0xffffffffu, p[3], left, LR);
+            o0 = in; o1 = p[0]; o2 = p[1]; o3 = p[2];
+        } else if (cx < 0) {
+            const float in = __shfl_sync(0xffffffffu, p[0], right, LR);
+            o0 = p[1]; o1 = p[2]; o2 = p[3]; o3 = in;
+        }
+        if (!active) continue;
+        if ((cz > 0 && z + 1 == nz) || (cz < 0 && z == 0)) {
+            // bounce-back into the opposite direction of the same cells
+            const float uw = (cz > 0) ? u_wall : -u_wall;
+            const float wall = (cx == 0) ? 0.f : 6.f * w * (cx > 0 ? uw : -uw);
+            Quad<S>::store(dst + (size_t)q_opp(i) * ncell + cell0, p[0] - wall, p[1] - wall,
+                           p[2] - wall, p[3] - wall);
+        } else {
+            const int yt = cy > 0 ? yp : (cy < 0 ? ym : y);
+            const int rt = yt + ny * (z + cz);
+            Quad<S>::store(dst + (size_t)i * ncell + x0 + NX * rt, o0, o1, o2, o3);
+        }
+    }
+}
+
 template <typename S, typename T>
 __global__ void k_init_fluid(S *pop, int nx, int ny, int nz, long long ncell, int mode,
                              double u_wall) {
@@ -183,6 +331,29 @@ __global__ void k_force_to_f64(const typename Vec4<T>::type *force, long long nc
 
 static inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+template <typename S, int LR>
+static void collide_x4(const Lattice &L, const CollideArgs &a, cudaStream_t s) {
+    constexpr int rows_per_block = 8 * (32 / LR);
+    const int nrows = L.ny * L.nz;
+    const unsigned nb = (unsigned)((nrows + rows_per_block - 1) / rows_per_block);
+    k_collide_stream_x4<S, LR><<<nb, 256, 0, s>>>(
+        (const S *)a.src, (S *)a.dst, (const float4 *)a.fcur, a.flag_cur, (float4 *)a.fold,
+        a.flag_old, L.ny, L.nz, (int)L.ncell, (float)(1.0 / a.tau), (float)a.u_wall, a.status);
+}
+
+template <typename S>
+static bool collide_vec(const Lattice &L, const CollideArgs &a, cudaStream_t s) {
+    switch (L.lanes_row) {
+        case 1: collide_x4<S, 1>(L, a, s); return true;
+        case 2: collide_x4<S, 2>(L, a, s); return true;
+        case 4: collide_x4<S, 4>(L, a, s); return true;
+        case 8: collide_x4<S, 8>(L, a, s); return true;
+        case 16: collide_x4<S, 16>(L, a, s); return true;
+        case 32: collide_x4<S, 32>(L, a, s); return true;
+        default: return false;
+    }
+}
+
 template <typename S, typename T>
 static void collide_impl(const Lattice &L, const CollideArgs &a, cudaStream_t s) {
     using V4 = typename Vec4<T>::type;
@@ -194,8 +365,11 @@ static void collide_impl(const Lattice &L, const CollideArgs &a, cudaStream_t s)
 
 void launch_collide_stream(int prec, const Lattice &L, const CollideArgs &a, cudaStream_t s) {
     if (prec == kF64) collide_impl<double, double>(L, a, s);
-    else if (prec == kF32) collide_impl<float, float>(L, a, s);
-    else collide_impl<__half, float>(L, a, s);
+    else if (prec == kF32) {
+        if (!collide_vec<float>(L, a, s)) collide_impl<float, float>(L, a, s);
+    } else {
+        if (!collide_vec<__half>(L, a, s)) collide_impl<__half, float>(L, a, s);
+    }
 }
 
 void launch_init_fluid(int prec, const Lattice &L, void *pop, int mode, double u_wall,

@@ -105,10 +105,17 @@ __global__ void __launch_bounds__(kTB) k_taylor_stage1(R nodes, const int4 *__re
         for (int k = 0; k < 5; ++k) p.partial[16 * b + k] = v[k];
 }
 
-__device__ __forceinline__ void capsule_totals1(const TaylorPlan &p, int cap, double tot[5]) {
-    for (int k = 0; k < 5; ++k) tot[k] = 0.0;
-    for (int b = p.cap_blk0[cap]; b < p.cap_blk0[cap + 1]; ++b)
-        for (int k = 0; k < 5; ++k) tot[k] += p.partial[16 * b + k];
+// Totals of K partial entries (from entry `first`) over the blocks of one
+// capsule, by one full warp: lane l sums blocks l, l+32, ... in order, then a
+// fixed butterfly; every lane returns the same totals.
+template <int K>
+__device__ __forceinline__ void capsule_totals(const TaylorPlan &p, int cap, int first, double tot[K]) {
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < K; ++k) tot[k] = 0.0;
+    for (int b = p.cap_blk0[cap] + lane; b < p.cap_blk0[cap + 1]; b += 32)
+        for (int k = 0; k < K; ++k) tot[k] += p.partial[16 * b + first + k];
+    for (int k = 0; k < K; ++k)
+        for (int o = 16; o > 0; o >>= 1) tot[k] += __shfl_xor_sync(0xffffffffu, tot[k], o);
 }
 
 template <typename R>
@@ -117,10 +124,11 @@ __global__ void __launch_bounds__(kTB) k_taylor_stage2(R nodes, const int4 *__re
     __shared__ double cen_sh[3];
     const int b = blockIdx.x;
     const int cap = p.blk_cap[b];
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         double tot[5];
-        capsule_totals1(p, cap, tot);
-        for (int k = 0; k < 3; ++k) cen_sh[k] = p.origin[3 * cap + k] + tot[2 + k] / (4.0 * tot[0]);
+        capsule_totals<5>(p, cap, 0, tot);
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 3; ++k) cen_sh[k] = p.origin[3 * cap + k] + tot[2 + k] / (4.0 * tot[0]);
     }
     __syncthreads();
     double v[6] = {0, 0, 0, 0, 0, 0};
@@ -144,27 +152,28 @@ __global__ void __launch_bounds__(kTB) k_taylor_stage2(R nodes, const int4 *__re
         for (int k = 0; k < 6; ++k) p.partial[16 * b + 8 + k] = v[k];
 }
 
-// One block; threads stride over the capsules.  In recording mode the block
-// writes the next ring slot and then advances the record counter.
-__global__ void k_taylor_stage3(TaylorPlan p, int record) {
+// One block of 32 warps; warp w takes capsules w, w + 32, ...  In recording
+// mode the block writes the next ring slot and then advances the counter.
+__global__ void __launch_bounds__(1024) k_taylor_stage3(TaylorPlan p, int record) {
     double *base = p.out;
     unsigned long long count = 0;
     if (record) {
         count = *p.ring_count;
         base = p.ring + (size_t)(count % (unsigned long long)p.ring_len) * p.n_caps * 12;
     }
-    for (int cap = threadIdx.x; cap < p.n_caps; cap += blockDim.x) {
-        double tot[5];
-        capsule_totals1(p, cap, tot);
-        double I[6] = {0, 0, 0, 0, 0, 0};
-        for (int b = p.cap_blk0[cap]; b < p.cap_blk0[cap + 1]; ++b)
-            for (int k = 0; k < 6; ++k) I[k] += p.partial[16 * b + 8 + k];
-        double *o = base + 12 * cap;
-        o[0] = tot[0];
-        o[1] = tot[1];
-        for (int k = 0; k < 3; ++k) o[2 + k] = p.origin[3 * cap + k] + tot[2 + k] / (4.0 * tot[0]);
-        for (int k = 0; k < 6; ++k) o[5 + k] = I[k];
-        o[11] = 0.0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int cap = warp; cap < p.n_caps; cap += blockDim.x >> 5) {
+        double tot[5], I[6];
+        capsule_totals<5>(p, cap, 0, tot);
+        capsule_totals<6>(p, cap, 8, I);
+        if (lane == 0) {
+            double *o = base + 12 * cap;
+            o[0] = tot[0];
+            o[1] = tot[1];
+            for (int k = 0; k < 3; ++k) o[2 + k] = p.origin[3 * cap + k] + tot[2 + k] / (4.0 * tot[0]);
+            for (int k = 0; k < 6; ++k) o[5 + k] = I[k];
+            o[11] = 0.0;
+        }
     }
     __syncthreads();
     if (record && threadIdx.x == 0) *p.ring_count = count + 1;
@@ -174,7 +183,7 @@ template <typename R>
 static void taylor_impl(R nodes, const MeshDev &m, const TaylorPlan &p, bool record, cudaStream_t s) {
     k_taylor_stage1<R><<<p.total_blocks, kTB, 0, s>>>(nodes, (const int4 *)m.tri, p);
     k_taylor_stage2<R><<<p.total_blocks, kTB, 0, s>>>(nodes, (const int4 *)m.tri, p);
-    k_taylor_stage3<<<1, 256, 0, s>>>(p, record ? 1 : 0);
+    k_taylor_stage3<<<1, 1024, 0, s>>>(p, record ? 1 : 0);
 }
 
 void launch_taylor(int prec, const MeshDev &m, const TaylorPlan &p, bool record, cudaStream_t s) {
