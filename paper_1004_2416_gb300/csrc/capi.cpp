@@ -24,7 +24,7 @@ struct Capsule {
     double origin[3];  // reference centre (mean of the reference nodes)
 };
 
-constexpr int kGraphSteps = 16;  // steps per captured graph (even)
+constexpr int kGraphSteps = 32;  // steps per captured graph (even)
 
 thread_local std::string g_create_error;
 
@@ -39,6 +39,12 @@ struct iblbm_sim {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    // Side stream for the Taylor record of a step: it runs concurrently with
+    // the next step's spreading and collide-stream and is joined before the
+    // next interpolation (the only kernel that moves the nodes it reads).
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool side_pending = false;
     iblbm_allocator alloc{};
     bool has_alloc = false;
     size_t pop_bytes = 0;  // one population buffer
@@ -131,11 +137,14 @@ int ensure_scratch(iblbm_sim *s, size_t bytes) {
 size_t real_bytes(const iblbm_sim *s) { return s->prec == kF64 ? 8 : 4; }
 
 void free_ring(iblbm_sim *s);
+void join_side(iblbm_sim *s);
 
 // (Re)builds the device membrane tables after capsules were added.  Current
 // node positions of existing capsules are kept.
 int ensure_mesh(iblbm_sim *s) {
     if (!s->mesh_dirty) return IBLBM_OK;
+    join_side(s);  // nothing may still read the tables that are rebuilt below
+    CK(cudaStreamSynchronize(s->stream));
     const int nn = (int)(s->X0.size() / 3), nf = (int)(s->tri.size() / 3), nc = (int)s->caps.size();
     std::vector<double> xcur(s->X0);
     if (s->dev_nodes > 0) {
@@ -360,11 +369,33 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) 
     a.status = s->d_status;
     launch_collide_stream(s->prec, s->L, a, s->stream);
     if (ev) cudaEventRecord(ev[2], s->stream);
+    if (s->side_pending) {  // the previous record still reads the positions
+        cudaStreamWaitEvent(s->stream, s->ev_join, 0);
+        s->side_pending = false;
+    }
     launch_interp_advect(s->prec, s->delta, s->L, s->mesh, s->pop[n], s->force[n], s->stream);
     if (ev) cudaEventRecord(ev[3], s->stream);
-    if (record) launch_taylor(s->prec, s->mesh, s->plan, true, s->stream);
+    if (record) {
+        if (ev) {  // timed: keep it on the main stream
+            launch_taylor(s->prec, s->mesh, s->plan, true, s->stream);
+        } else {
+            cudaEventRecord(s->ev_fork, s->stream);
+            cudaStreamWaitEvent(s->side, s->ev_fork, 0);
+            launch_taylor(s->prec, s->mesh, s->plan, true, s->side);
+            cudaEventRecord(s->ev_join, s->side);
+            s->side_pending = true;
+        }
+    }
     if (ev) cudaEventRecord(ev[4], s->stream);
     s->cur = n;
+}
+
+// Makes the main stream wait for an outstanding Taylor record.
+void join_side(iblbm_sim *s) {
+    if (s->side_pending) {
+        cudaStreamWaitEvent(s->stream, s->ev_join, 0);
+        s->side_pending = false;
+    }
 }
 
 int check_sim(const iblbm_sim *s) { return s ? IBLBM_OK : IBLBM_ERR_ARG; }
@@ -377,6 +408,7 @@ int status_from_bits(int bits) {
 
 int sync_status(iblbm_sim *s) {
     CK(cudaSetDevice(s->device));
+    join_side(s);
     CK(cudaStreamSynchronize(s->stream));
     int bits = 0;
     CK(cudaMemcpy(&bits, s->d_status, sizeof(int), cudaMemcpyDeviceToHost));
@@ -498,6 +530,14 @@ int iblbm_create(iblbm_sim **out, int nx, int ny, int nz, double tau, int precis
         }
         s->own_stream = true;
     }
+    if (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        g_create_error = "stream or event creation failed";
+        iblbm_destroy(s);
+        return IBLBM_ERR_CUDA;
+    }
     const size_t el = precision == kF64 ? 8 : (precision == kF32 ? 4 : 2);
     s->pop_bytes = 19 * el * (size_t)s->L.ncell;
     s->vec_bytes = 4 * real_bytes(s) * (size_t)s->L.ncell;
@@ -536,6 +576,7 @@ int iblbm_destroy(iblbm_sim *s) {
     if (!s) return IBLBM_OK;
     cudaSetDevice(s->device);
     if (s->stream) cudaStreamSynchronize(s->stream);
+    if (s->side) cudaStreamSynchronize(s->side);
     drop_graphs(s);
     for (int k = 0; k < 2; ++k) {
         dev_free(s, s->pop[k]);
@@ -547,6 +588,12 @@ int iblbm_destroy(iblbm_sim *s) {
     free_ring(s);
     for (void *p : s->mesh_allocs) dev_free(s, p);
     for (void *p : s->plan_allocs) dev_free(s, p);
+    if (s->side) {
+        cudaStreamSynchronize(s->side);
+        cudaStreamDestroy(s->side);
+    }
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
     return IBLBM_OK;
@@ -685,7 +732,11 @@ int iblbm_step(iblbm_sim *s, int64_t n_steps) {
                 cudaGraph_t graph = nullptr;
                 const int cur0 = s->cur;
                 CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+                const bool pending0 = s->side_pending;
+                s->side_pending = false;  // a record before the graph is joined outside it
                 for (int k = 0; k < G; ++k) enqueue_step(s, record_after(s, k));
+                join_side(s);
+                s->side_pending = pending0;
                 cudaError_t e = cudaStreamEndCapture(s->stream, &graph);
                 s->cur = cur0;
                 if (e != cudaSuccess) return cuda_fail(s, e, "graph capture");
@@ -696,6 +747,7 @@ int iblbm_step(iblbm_sim *s, int64_t n_steps) {
                     return cuda_fail(s, e, "graph instantiation");
                 }
             }
+            join_side(s);
             CK(cudaGraphLaunch(g, s->stream));
             for (int k = 0; k < G; ++k)
                 if (record_after(s, k)) s->rec_steps.push_back(s->steps + k + 1);
@@ -718,6 +770,7 @@ int iblbm_set_taylor_recording(iblbm_sim *s, int every, int ring) {
     if (every < 0 || (every > 0 && (ring < 1 || ring > (1 << 24))))
         return fail(s, IBLBM_ERR_ARG, "every must be >= 0 and ring in 1..2^24");
     CK(cudaSetDevice(s->device));
+    join_side(s);
     CK(cudaStreamSynchronize(s->stream));
     free_ring(s);
     drop_graphs(s);
@@ -760,6 +813,7 @@ int iblbm_profile_kernels(iblbm_sim *s, int n_steps, double ms_out[4]) {
     if (rc) return rc;
     rc = ensure_ring(s);
     if (rc) return rc;
+    join_side(s);
     std::vector<cudaEvent_t> ev(5 * (size_t)n_steps, nullptr);
     for (auto &e : ev) CK(cudaEventCreate(&e));
     for (int k = 0; k < n_steps; ++k) {

@@ -257,34 +257,49 @@ __global__ void __launch_bounds__(256)
         pc[0] = p[0]; pc[1] = p[1]; pc[2] = p[2];
     }
     const int bx = stencil_first<N>(pc[0]), by = stencil_first<N>(pc[1]), bz = stencil_first<N>(pc[2]);
-    T ax = T(0), ay = T(0), az = T(0);
+    // Each lane owns up to ITER stencil cells; all their population loads are
+    // issued before any is used.
     constexpr int NC = N * N * N;
-    for (int k = lane; k < NC; k += 32) {
+    constexpr int ITER = (NC + 31) / 32;
+    T w[ITER];
+    long long cell[ITER];
+#pragma unroll
+    for (int it = 0; it < ITER; ++it) {
+        const int k = lane + 32 * it;
         const int kx = k % N, ky = (k / N) % N, kz = k / (N * N);
         const int X = bx + kx, Y = by + ky, Z = bz + kz;
-        if (Z < 0 || Z >= nz) continue;  // reported by the spreading kernel
-        T d[3];
-        pos.rel(p, X, Y, Z, d);
-        const T w = delta_phi<N>(d[0]) * delta_phi<N>(d[1]) * delta_phi<N>(d[2]);
-        if (w == T(0)) continue;
-        const int xw = wrap_index(X, nx), yw = wrap_index(Y, ny);
-        const long long cell = xw + (long long)nx * (yw + (long long)ny * Z);
-        T g[19];
+        w[it] = T(0);
+        cell[it] = 0;
+        if (k < NC && Z >= 0 && Z < nz) {  // a stencil beyond a wall is reported by the spreading
+            T d[3];
+            pos.rel(p, X, Y, Z, d);
+            w[it] = delta_phi<N>(d[0]) * delta_phi<N>(d[1]) * delta_phi<N>(d[2]);
+            cell[it] = wrap_index(X, nx) + (long long)nx * (wrap_index(Y, ny) + (long long)ny * Z);
+        }
+    }
+    T g[ITER][19];
 #pragma unroll
-        for (int i = 0; i < 19; ++i) g[i] = Store<S, T>::load(pop + i * ncell + cell);
+    for (int it = 0; it < ITER; ++it)
+#pragma unroll
+        for (int i = 0; i < 19; ++i)
+            g[it][i] = (w[it] != T(0)) ? Store<S, T>::load(pop + i * ncell + cell[it]) : T(0);
+    T ax = T(0), ay = T(0), az = T(0);
+#pragma unroll
+    for (int it = 0; it < ITER; ++it) {
+        if (w[it] == T(0)) continue;
         T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
-            drho += g[i];
-            if (q_cx(i)) jx += q_cx(i) > 0 ? g[i] : -g[i];
-            if (q_cy(i)) jy += q_cy(i) > 0 ? g[i] : -g[i];
-            if (q_cz(i)) jz += q_cz(i) > 0 ? g[i] : -g[i];
+            drho += g[it][i];
+            if (q_cx(i)) jx += q_cx(i) > 0 ? g[it][i] : -g[it][i];
+            if (q_cy(i)) jy += q_cy(i) > 0 ? g[it][i] : -g[it][i];
+            if (q_cz(i)) jz += q_cz(i) > 0 ? g[it][i] : -g[it][i];
         }
-        const V4 f = force[cell];
+        const V4 f = force[cell[it]];
         const T inv_rho = T(1) / (T(1) + drho);
-        ax += w * ((jx + T(0.5) * f.x) * inv_rho);
-        ay += w * ((jy + T(0.5) * f.y) * inv_rho);
-        az += w * ((jz + T(0.5) * f.z) * inv_rho);
+        ax += w[it] * ((jx + T(0.5) * f.x) * inv_rho);
+        ay += w[it] * ((jy + T(0.5) * f.y) * inv_rho);
+        az += w[it] * ((jz + T(0.5) * f.z) * inv_rho);
     }
     ax = warp_sum(ax);
     ay = warp_sum(ay);

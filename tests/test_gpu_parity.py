@@ -51,6 +51,60 @@ def test_lattice_only_ragged(prec):
     assert abs(s.get_density().sum() - f.sum(axis=0).sum()) / f.sum(axis=0).sum() < mass_tol
 
 
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+@pytest.mark.parametrize("shape", [(4, 3, 5), (8, 5, 7), (32, 9, 6), (64, 7, 5), (128, 5, 9)])
+def test_lattice_vectorised_rows(shape, prec):
+    """The 4-cells-per-thread collide-stream (nx/4 a power of two <= 32), with
+    row counts that leave idle lanes in the last block."""
+    nx, ny, nz = shape
+    tau, uw = 0.9, 0.04
+    f0 = O.init_couette(nx, ny, nz, uw) + W.population_noise(shape, 2e-3, seed=11)
+    from paper_1004_2416_gb300 import Sim
+
+    s = Sim(nx, ny, nz, tau=tau, precision=prec, delta_points=3)
+    s.set_shear_walls(uw)
+    s.set_populations(f0)
+    s.step(23)
+    f = f0
+    for _ in range(23):
+        f = O.lbm_step(f, tau, uw)
+    _, w, _ = O.d3q19()
+    wb = w[:, None, None, None]
+    tol = {"fp32": 1e-5, "fp16": 3e-3}[prec]
+    assert rel_inf(s.get_populations() - wb, f - wb) < tol
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+@pytest.mark.parametrize("delta", [2, 4])
+def test_one_step_vectorised_path(prec, delta):
+    """Coupled step on a lattice that takes the vectorised kernel (nx = 64)."""
+    c = W.Capsule((31.3, 17.6, 14.2), 5.0, 3, W.k_s_for(0.05, 5.0))
+    case = W.Case("vec", (64, 36, 29), 1.0, delta, prec, 0.02, [c], 1)
+    g = gpu_sim(case)
+    o = oracle_sim(case)
+    x0 = o.get_nodes() + W.jitter(o.n_nodes, 0.15, seed=13)
+    f0 = o.get_f() + W.population_noise(case.shape, 1e-3, seed=14)
+    g.set_nodes(x0)
+    o.set_nodes(x0)
+    g.set_populations(f0)
+    o.set_f(f0)
+    g.step(1)
+    o.step(1)
+    tol = ONE_STEP_TOL[prec]
+    assert rel_inf(g.get_node_forces(), o.get_node_forces()) < 1e-5
+    assert rel_inf(g.get_force_field(), o.get_force_field()) < 1e-5
+    _, w, _ = O.d3q19()
+    wb = w[:, None, None, None]
+    assert rel_inf(g.get_populations() - wb, o.get_f() - wb) < tol
+    assert rel_inf(g.get_velocity(), o.get_velocity()) < tol
+    assert rel_inf(g.get_node_velocities(), o.get_node_velocities()) < tol
+    # a second step: the previous step's force tiles must have been cleared
+    g.step(1)
+    o.step(1)
+    assert rel_inf(g.get_force_field(), o.get_force_field()) < 1e-5
+    assert rel_inf(g.get_populations() - wb, o.get_f() - wb) < tol
+
+
 @pytest.mark.parametrize("shape", [(1, 1, 4), (3, 2, 5), (33, 9, 2)])
 def test_lattice_degenerate_shapes(shape):
     nx, ny, nz = shape
@@ -230,3 +284,26 @@ def test_setters_round_trip():
     cid = s32.add_capsule_icosphere((9.5, 4.5, 5.5), 2.5, 2)
     s32.set_nodes(x, cid)
     assert np.abs(s32.get_nodes(cid) - x).max() < 1e-12
+
+
+@pytest.mark.parametrize("every", [1, 5])
+def test_taylor_recording_ring(every):
+    """Records taken inside the step sequence (direct launches and captured
+    graphs, on the side stream) equal the immediate reduction of the same
+    state, and the recorded history matches the oracle's trajectory."""
+    case = _small_case(delta=3, precision="fp64", steps=0)
+    g = gpu_sim(case)
+    g.set_taylor_recording(every, ring=512)
+    o = oracle_sim(case)
+    hist = []
+    for chunk in (7, 150, 3):  # 150 covers several graph replays
+        g.step(chunk)
+        for _ in range(chunk):
+            o.step(1)
+            hist.append(o.taylor(0)["D"])
+    steps, rec = g.taylor_records(0)
+    assert list(steps) == [k for k in range(every, 161, every)]
+    now = g.taylor(0)
+    assert np.array_equal(rec[-1], np.array([now[k] for k in now]))
+    for st, r in zip(steps, rec):
+        assert abs(r[0] - hist[st - 1]) <= 1e-10 * abs(hist[st - 1]) + 1e-13
