@@ -45,6 +45,7 @@ struct iblbm_sim {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool side_pending = false;
+    const char *launch_fail = nullptr;  // first kernel group whose launch failed
     iblbm_allocator alloc{};
     bool has_alloc = false;
     size_t pop_bytes = 0;  // one population buffer
@@ -353,9 +354,14 @@ void free_ring(iblbm_sim *s) {
 // ev[0] | spread | ev[1] | collide | ev[2] | interpolate | ev[3] | reductions | ev[4].
 void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) {
     const int c = s->cur, n = 1 - s->cur;
+    auto mark = [s](const char *what) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess && !s->launch_fail) s->launch_fail = what;
+    };
     if (ev) cudaEventRecord(ev[0], s->stream);
     launch_force_spread(s->prec, s->delta, s->L, s->mesh, s->force[n], s->flags[n], s->d_status,
                         s->stream);
+    mark("membrane force + spreading");
     if (ev) cudaEventRecord(ev[1], s->stream);
     CollideArgs a;
     a.src = s->pop[c];
@@ -368,12 +374,15 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) 
     a.u_wall = s->u_wall;
     a.status = s->d_status;
     launch_collide_stream(s->prec, s->L, a, s->stream);
+    mark("collide-stream");
     if (ev) cudaEventRecord(ev[2], s->stream);
     if (s->side_pending) {  // the previous record still reads the positions
         cudaStreamWaitEvent(s->stream, s->ev_join, 0);
         s->side_pending = false;
+        mark("join of the Taylor record");
     }
     launch_interp_advect(s->prec, s->delta, s->L, s->mesh, s->pop[n], s->force[n], s->stream);
+    mark("interpolation + advection");
     if (ev) cudaEventRecord(ev[3], s->stream);
     if (record) {
         if (ev) {  // timed: keep it on the main stream
@@ -381,10 +390,12 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) 
         } else {
             cudaEventRecord(s->ev_fork, s->stream);
             cudaStreamWaitEvent(s->side, s->ev_fork, 0);
+            mark("fork of the Taylor record");
             launch_taylor(s->prec, s->mesh, s->plan, true, s->side);
             cudaEventRecord(s->ev_join, s->side);
             s->side_pending = true;
         }
+        mark("Taylor record");
     }
     if (ev) cudaEventRecord(ev[4], s->stream);
     s->cur = n;
@@ -714,10 +725,12 @@ int iblbm_step(iblbm_sim *s, int64_t n_steps) {
     if (!s) return IBLBM_ERR_ARG;
     if (n_steps < 0) return fail(s, IBLBM_ERR_ARG, "negative step count");
     CK(cudaSetDevice(s->device));
+    cudaGetLastError();  // an error left by some earlier, unrelated call is not ours
     int rc = ensure_mesh(s);
     if (rc) return rc;
     rc = ensure_ring(s);
     if (rc) return rc;
+    s->launch_fail = nullptr;
     const int G = graph_len_for(s);
     if (G != s->graph_len) {
         drop_graphs(s);
@@ -731,12 +744,13 @@ int iblbm_step(iblbm_sim *s, int64_t n_steps) {
             if (!g) {
                 cudaGraph_t graph = nullptr;
                 const int cur0 = s->cur;
+                // An outstanding record of a direct step is joined before the
+                // capture; the graph joins its own records before it ends, so
+                // no event recorded inside the capture is waited on outside it.
+                join_side(s);
                 CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-                const bool pending0 = s->side_pending;
-                s->side_pending = false;  // a record before the graph is joined outside it
                 for (int k = 0; k < G; ++k) enqueue_step(s, record_after(s, k));
                 join_side(s);
-                s->side_pending = pending0;
                 cudaError_t e = cudaStreamEndCapture(s->stream, &graph);
                 s->cur = cur0;
                 if (e != cudaSuccess) return cuda_fail(s, e, "graph capture");
@@ -760,7 +774,10 @@ int iblbm_step(iblbm_sim *s, int64_t n_steps) {
             s->steps++;
             left--;
         }
+        if (s->launch_fail) break;
     }
+    if (s->launch_fail)
+        return fail(s, IBLBM_ERR_CUDA, std::string("kernel launch failed: ") + s->launch_fail);
     CK(cudaGetLastError());
     return IBLBM_OK;
 }
