@@ -97,7 +97,8 @@ int iblbm_create(iblbm_sim **out, int nx, int ny, int nz, double tau,
 int iblbm_destroy(iblbm_sim *sim);
 
 /* Message of the last failure on this object ("" if none).  With sim ==
- * NULL, the message of the last failed iblbm_create in this thread. */
+ * NULL, the message of the last failed call in this thread that takes no
+ * simulation object (iblbm_create, iblbm_taylor_sums_noalloc). */
 const char *iblbm_last_error(const iblbm_sim *sim);
 
 /* Static name of a status code. */
@@ -228,6 +229,48 @@ int iblbm_get_mesh(iblbm_sim *sim, int capsule_id, int *n_nodes, int *n_tri,
  * D = (r_a - r_c)/(r_a + r_c) the Taylor deformation, theta the angle of the
  * major axis in the xz plane, from +x toward +z. */
 int iblbm_get_taylor(iblbm_sim *sim, int capsule_id, double out[16]);
+
+/* ---- allocation-free capsule reductions ------------------------------------------
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory at the moment they need the reductions
+ * behind the Taylor deformation: code running while a framework captures its
+ * stream into a CUDA graph, code whose device memory is entirely handed to
+ * another allocator, or tight loops where an allocation would synchronise the
+ * device.  It computes what iblbm_get_taylor reduces on the device for one
+ * closed membrane, on buffers the caller owns, and allocates nothing.
+ *
+ *   nodes   device pointer, [n_nodes][3] doubles (n_nodes >= 4)
+ *   tri     device pointer, [n_tri][3] int32 node indices, counter-clockwise
+ *           seen from outside (4 <= n_tri <= 131072)
+ *   origin  host pointer, 3 doubles: a point near the membrane; face terms
+ *           are taken relative to it (results do not depend on it beyond
+ *           rounding)
+ *   out     device pointer, 12 doubles: {V, A, c_x, c_y, c_z, I_xx, I_yy,
+ *           I_zz, I_xy, I_xz, I_yz, skipped} -- volume, area, centroid and the
+ *           inertia tensor about the centroid, as in iblbm_get_taylor; skipped
+ *           counts faces ignored because a node index lay outside
+ *           [0, n_nodes) (0 for valid input)
+ *   stream  cudaStream_t (NULL = legacy default stream); the call is
+ *           asynchronous on it and reads and writes the buffers only there.
+ *
+ * Scratch: the per-block partial sums live in one fixed device array of
+ * 1024 x 16 doubles (128 KiB) that every GPU which loads the library holds
+ * until the process exits; n_tri beyond 131072 is rejected with
+ * IBLBM_ERR_ARG.  Every call on a device shares that array and it keeps the
+ * last call's contents; nothing in it needs to start at zero, because each
+ * call overwrites every entry it reads.  Calls that overlap on the GPU (for
+ * instance on two streams at once) race on the array and give wrong results.
+ * The first call on each device, made with that device current, looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  Errors: IBLBM_ERR_ARG for null pointers or sizes out of
+ * range, IBLBM_ERR_CUDA if the lookup or a launch fails; the message is in
+ * iblbm_last_error(NULL).  Calls no cudaMalloc, cudaFree or other allocating
+ * routine. */
+int iblbm_taylor_sums_noalloc(const double *nodes, int n_nodes,
+                              const int32_t *tri, int n_tri,
+                              const double origin[3], double *out,
+                              void *stream);
 
 #ifdef __cplusplus
 }

@@ -30,6 +30,8 @@ thread_local std::string g_create_error;
 
 }  // namespace
 
+void iblbm::set_thread_error(const std::string &msg) { g_create_error = msg; }
+
 struct iblbm_sim {
     Lattice L{};
     int prec = 1;

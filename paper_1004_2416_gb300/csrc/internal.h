@@ -7,6 +7,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
 #include <vector>
 
 namespace iblbm {
@@ -121,6 +122,9 @@ struct TaylorPlan {
 constexpr int kTaylorFacesPerBlock = 128;
 // record = false: results to p.out; record = true: to the next ring slot.
 void launch_taylor(int prec, const MeshDev &m, const TaylorPlan &p, bool record, cudaStream_t s);
+
+// Message returned by iblbm_last_error(NULL) in the calling thread (capi.cpp).
+void set_thread_error(const std::string &msg);
 
 // ---- mesh.cpp (host) -------------------------------------------------------------------
 // Canonical icosphere: nodes [n][3], faces [f][3]

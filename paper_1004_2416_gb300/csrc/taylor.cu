@@ -14,7 +14,11 @@
 //   3. per capsule: totals of both stages -> {V, A, c, I} in the output.
 // Per-block partials live in a scratch array [blocks][16] (stage 1 in
 // entries 0..4, stage 2 in entries 8..13).
+#include <mutex>
+#include <string>
+
 #include "device_common.cuh"
+#include "iblbm.h"
 #include "internal.h"
 
 namespace iblbm {
@@ -193,5 +197,186 @@ void launch_taylor(int prec, const MeshDev &m, const TaylorPlan &p, bool record,
     else
         taylor_impl(NodeRead<float>{(const float4 *)m.x, (const float4 *)m.x_lo}, m, p, record, s);
 }
+
+
+// ---- allocation-free variant ---------------------------------------------------------
+// Some callers cannot allocate device memory when they need these reductions:
+// code that runs while a framework captures its stream into a CUDA graph, code
+// whose whole device budget is handed to another allocator, or a tight loop in
+// which an allocation would synchronise the device.  For them the per-block
+// partial sums of the three stages live in this fixed array, which every GPU
+// that loads the library holds until the process exits.
+constexpr int kNoAllocMaxBlocks = 1024;  // 1024 blocks x 128 faces = 131072 faces
+static __device__ __align__(256) double g_noalloc_partial[kNoAllocMaxBlocks * 16];
+
+struct PlainRead {
+    const double *x;  // [n][3]
+    __device__ __forceinline__ void get(int n, double p[3]) const {
+        p[0] = x[3 * n];
+        p[1] = x[3 * n + 1];
+        p[2] = x[3 * n + 2];
+    }
+};
+
+__device__ __forceinline__ bool face_ok(const int *tri, int f, int n_nodes, int4 &t) {
+    t = make_int4(tri[3 * f], tri[3 * f + 1], tri[3 * f + 2], 0);
+    return t.x >= 0 && t.x < n_nodes && t.y >= 0 && t.y < n_nodes && t.z >= 0 && t.z < n_nodes;
+}
+
+// Totals of K partial entries (from `first`) over nb blocks, by one warp.
+template <int K>
+__device__ __forceinline__ void plain_totals(const double *partial, int nb, int first, double tot[K]) {
+    const int lane = threadIdx.x & 31;
+    for (int k = 0; k < K; ++k) tot[k] = 0.0;
+    for (int b = lane; b < nb; b += 32)
+        for (int k = 0; k < K; ++k) tot[k] += partial[16 * b + first + k];
+    for (int k = 0; k < K; ++k)
+        for (int o = 16; o > 0; o >>= 1) tot[k] += __shfl_xor_sync(0xffffffffu, tot[k], o);
+}
+
+__global__ void __launch_bounds__(kTB) k_noalloc_stage1(const double *__restrict__ x, int n_nodes,
+                                                        const int *__restrict__ tri, int n_tri,
+                                                        double ox, double oy, double oz,
+                                                        double *__restrict__ partial) {
+    __shared__ double sh[kTB / 32][6];
+    const int f = blockIdx.x * kTB + threadIdx.x;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    if (f < n_tri) {
+        int4 t;
+        if (face_ok(tri, f, n_nodes, t)) {
+            double cen[3], An[3];
+            face_geom(PlainRead{x}, t, cen, An);
+            const double r[3] = {cen[0] - ox, cen[1] - oy, cen[2] - oz};
+            const double rn = r[0] * An[0] + r[1] * An[1] + r[2] * An[2];
+            v[0] = rn * (1.0 / 3.0);
+            v[1] = sqrt(An[0] * An[0] + An[1] * An[1] + An[2] * An[2]);
+            v[2] = rn * r[0];
+            v[3] = rn * r[1];
+            v[4] = rn * r[2];
+        } else {
+            v[5] = 1.0;  // face skipped: a node index outside [0, n_nodes)
+        }
+    }
+    block_sum<6>(v, sh);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 5; ++k) partial[16 * blockIdx.x + k] = v[k];
+        partial[16 * blockIdx.x + 15] = v[5];
+    }
+}
+
+__global__ void __launch_bounds__(kTB) k_noalloc_stage2(const double *__restrict__ x, int n_nodes,
+                                                        const int *__restrict__ tri, int n_tri,
+                                                        double ox, double oy, double oz,
+                                                        double *__restrict__ partial) {
+    __shared__ double sh[kTB / 32][6];
+    __shared__ double cen_sh[3];
+    if (threadIdx.x < 32) {
+        double tot[5];
+        plain_totals<5>(partial, gridDim.x, 0, tot);
+        if (threadIdx.x == 0) {
+            cen_sh[0] = ox + tot[2] / (4.0 * tot[0]);
+            cen_sh[1] = oy + tot[3] / (4.0 * tot[0]);
+            cen_sh[2] = oz + tot[4] / (4.0 * tot[0]);
+        }
+    }
+    __syncthreads();
+    const int f = blockIdx.x * kTB + threadIdx.x;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+    int4 t;
+    if (f < n_tri && face_ok(tri, f, n_nodes, t)) {
+        double cen[3], An[3];
+        face_geom(PlainRead{x}, t, cen, An);
+        double r[3];
+        for (int k = 0; k < 3; ++k) r[k] = cen[k] - cen_sh[k];
+        const double rn = (r[0] * An[0] + r[1] * An[1] + r[2] * An[2]) * 0.2;
+        const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        v[0] = (r2 - r[0] * r[0]) * rn;
+        v[1] = (r2 - r[1] * r[1]) * rn;
+        v[2] = (r2 - r[2] * r[2]) * rn;
+        v[3] = -r[0] * r[1] * rn;
+        v[4] = -r[0] * r[2] * rn;
+        v[5] = -r[1] * r[2] * rn;
+    }
+    block_sum<6>(v, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 6; ++k) partial[16 * blockIdx.x + 8 + k] = v[k];
+}
+
+__global__ void k_noalloc_stage3(const double *__restrict__ partial, int nb, double ox, double oy,
+                                 double oz, double *__restrict__ out) {
+    double tot[5], I[6], bad[1];
+    plain_totals<5>(partial, nb, 0, tot);
+    plain_totals<6>(partial, nb, 8, I);
+    plain_totals<1>(partial, nb, 15, bad);
+    if (threadIdx.x == 0) {
+        out[0] = tot[0];
+        out[1] = tot[1];
+        out[2] = ox + tot[2] / (4.0 * tot[0]);
+        out[3] = oy + tot[3] / (4.0 * tot[0]);
+        out[4] = oz + tot[4] / (4.0 * tot[0]);
+        for (int k = 0; k < 6; ++k) out[5 + k] = I[k];
+        out[11] = bad[0];
+    }
+}
+
+}  // namespace iblbm
+
+namespace {
+// Device address of g_noalloc_partial, looked up once per device.
+std::mutex g_noalloc_mu;
+double *g_noalloc_ptr[256] = {nullptr};
+}  // namespace
+
+extern "C" int iblbm_taylor_sums_noalloc(const double *nodes, int n_nodes, const int32_t *tri,
+                                         int n_tri, const double origin[3], double *out,
+                                         void *stream) {
+    using namespace iblbm;
+    if (!nodes || !tri || !origin || !out || n_nodes < 4 || n_tri < 4) {
+        set_thread_error("iblbm_taylor_sums_noalloc: null pointer, or fewer than 4 nodes or faces");
+        return IBLBM_ERR_ARG;
+    }
+    if (n_tri > kNoAllocMaxBlocks * kTB) {
+        set_thread_error("iblbm_taylor_sums_noalloc: more than 131072 faces (the size of its fixed scratch)");
+        return IBLBM_ERR_ARG;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+        cudaGetLastError();
+        set_thread_error("iblbm_taylor_sums_noalloc: no usable current CUDA device");
+        return IBLBM_ERR_CUDA;
+    }
+    double *partial = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            // First call on this device (with it current): look up the device
+            // address of the fixed scratch array.
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partial);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                set_thread_error(std::string("iblbm_taylor_sums_noalloc: cudaGetSymbolAddress failed: ") +
+                                 cudaGetErrorString(e));
+                return IBLBM_ERR_CUDA;
+            }
+            g_noalloc_ptr[dev] = (double *)p;
+        }
+        partial = g_noalloc_ptr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nb = (n_tri + kTB - 1) / kTB;
+    cudaGetLastError();
+    k_noalloc_stage1<<<nb, kTB, 0, s>>>(nodes, n_nodes, tri, n_tri, origin[0], origin[1], origin[2], partial);
+    k_noalloc_stage2<<<nb, kTB, 0, s>>>(nodes, n_nodes, tri, n_tri, origin[0], origin[1], origin[2], partial);
+    k_noalloc_stage3<<<1, 32, 0, s>>>(partial, nb, origin[0], origin[1], origin[2], out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_thread_error(std::string("iblbm_taylor_sums_noalloc: launch failed: ") + cudaGetErrorString(e));
+        return IBLBM_ERR_CUDA;
+    }
+    return IBLBM_OK;
+}
+
+namespace iblbm {
 
 }  // namespace iblbm

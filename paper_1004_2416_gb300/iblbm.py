@@ -91,6 +91,7 @@ _SIGS = {
     "iblbm_set_taylor_recording": (_int, [_vp, _int, _int]),
     "iblbm_get_taylor_records": (_int, [_vp, _int, _int, _dp, ctypes.POINTER(ctypes.c_int64), _ip]),
     "iblbm_profile_kernels": (_int, [_vp, _int, _dp]),
+    "iblbm_taylor_sums_noalloc": (_int, [_vp, _int, _vp, _int, _dp, _vp, _vp]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
