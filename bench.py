@@ -44,9 +44,10 @@ def _args():
     p.add_argument("--steps", type=int, default=20000)
     p.add_argument("--warmup", type=int, default=200)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--delta", type=int, default=4)
-    p.add_argument("--G", type=float, default=0.0125)
-    p.add_argument("--precision", default="fp32")
+    p.add_argument("--workload", choices=["config1", "config2", "config4", "config5"], default="config2")
+    p.add_argument("--delta", type=int, default=4, help="config 2 only")
+    p.add_argument("--G", type=float, default=0.0125, help="config 2 only")
+    p.add_argument("--precision", default=None, help="override the workload's storage precision")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-budget-s", type=float, default=20.0)
@@ -57,7 +58,17 @@ def _args():
 def _workload(a):
     from paper_1004_2416_gb300 import workloads as W
 
-    return W.config2(G=a.G, delta=a.delta, precision=a.precision)
+    if a.workload == "config1":
+        case = W.config1()
+    elif a.workload == "config4":
+        case = W.config4()
+    elif a.workload == "config5":
+        case = W.config5()
+    else:
+        case = W.config2(G=a.G, delta=a.delta)
+    if a.precision:
+        case.precision = a.precision
+    return case
 
 
 def _config(case, a):
@@ -71,13 +82,13 @@ def _config(case, a):
         "faces": 20 * 4 ** c.subdivisions,
         "radius": c.radius,
         "delta_points": case.delta,
-        "reduced_shear_rate_G": a.G,
+        "reduced_shear_rate_G": round(c.radius * (case.tau - 0.5) / 3.0 * 2.0 * case.u_wall / case.shape[2] / c.k_s, 6),
         "k_s": c.k_s,
         "u_wall": case.u_wall,
         "tau": case.tau,
         "storage": f"{case.precision} deviations from rest equilibrium",
         "step": "forces+spread, collide-stream, interpolate+advect, FP64 Taylor reductions recorded",
-        "l2": "inputs larger than L2: two population buffers of 159 MB each",
+        "l2": f"inputs larger than L2: two population buffers of {19 * case.ncell * BYTES_PER_CELL[case.precision] // 38 / 1e6:.0f} MB each",
         "parallelism": "replicas (one independent simulation per rank)",
     }
 
@@ -194,10 +205,10 @@ def _kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def _ncu_traffic(precision: str):
+def _ncu_traffic(workload: str, precision: str):
     """DRAM bytes per collide-and-stream launch from the committed ncu summary,
     or None when the summary is absent or was taken on other kernel source."""
-    path = os.path.join(ROOT, "profiles", f"collide_stream_config2_{precision}.txt")
+    path = os.path.join(ROOT, "profiles", f"collide_stream_{workload}_{precision}.txt")
     try:
         kv = {}
         with open(path) as fh:
@@ -289,7 +300,7 @@ def run_ours(a):
     algo_bytes = BYTES_PER_CELL[case.precision] * cells
     k_ms = prof["collide_stream"]
     achieved = algo_bytes / (k_ms * 1e-3) / 1e9
-    traffic = _ncu_traffic(case.precision)
+    traffic = _ncu_traffic(a.workload, case.precision)
     roofline = {"kernel": "k_collide_stream", "bound": "hbm", "achieved": round(achieved, 1),
                 "peak": peak, "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,

@@ -14,7 +14,7 @@ namespace iblbm {
 
 // Lattice geometry.  The scalar collide-stream kernel works on tiles of
 // kTileX x kTileY x 1 cells; the vectorised one on whole x-rows (4 cells per
-// thread, nx/4 lanes per row, nx/4 a power of two <= 32).  The sparse
+// thread, nx/4 lanes per row, nx/4 a power of two <= 256).  The sparse
 // force-density flags have the granularity of the kernel in use:
 // ftx x fty x 1 cells per flag.
 constexpr int kTileX = 32;
@@ -40,7 +40,7 @@ inline Lattice make_lattice(int nx, int ny, int nz, bool vec) {
     L.nz = nz;
     L.ntx = (nx + kTileX - 1) / kTileX;
     L.nty = (ny + kTileY - 1) / kTileY;
-    L.lanes_row = (vec && nx % 4 == 0 && is_pow2(nx / 4) && nx / 4 <= 32) ? nx / 4 : 0;
+    L.lanes_row = (vec && nx % 4 == 0 && is_pow2(nx / 4) && nx / 4 <= 256) ? nx / 4 : 0;
     L.ftx = L.lanes_row ? nx : kTileX;
     L.fty = L.lanes_row ? 1 : kTileY;
     L.nfx = (nx + L.ftx - 1) / L.ftx;

@@ -147,14 +147,54 @@ struct Quad<__half> {
     }
 };
 
-// Vectorised collide-and-stream for nx = 4 * LR, LR a power of two <= 32:
-// each thread owns 4 consecutive cells of one x-row, LR lanes cover the row,
-// a warp covers 32 / LR rows and a block of 8 warps 8 * 32 / LR rows.  All 19
-// loads and stores are 16-byte (float) or 8-byte (half) vectors.  Streaming
-// along x shifts a thread's 4 post-collision values by one cell; the value
-// that crosses into the neighbouring thread's quad comes by a warp shuffle
-// within the row's lane segment, which also closes the periodic wrap in x.
-// One force flag per row.
+// Vectorised collide-and-stream for nx = 4 * LR, LR a power of two <= 256:
+// each thread owns 4 consecutive cells of one x-row and LR lanes cover the
+// row.  With LR <= 32 a warp covers 32 / LR rows; with LR > 32 a row spans
+// LR / 32 warps.  A block has 8 warps.  All 19 loads and stores are 16-byte
+// (float) or 8-byte (half) vectors.  Streaming along x shifts a thread's 4
+// post-collision values by one cell; the value that crosses into the
+// neighbouring thread's quad comes by a warp shuffle (within the row's lane
+// segment when LR <= 32, which also closes the periodic wrap in x); when a row
+// spans several warps, the edge lanes of the warps exchange that value
+// through a shared-memory slot per direction.  One force flag per row.
+template <int LR>
+struct XShift {
+    static constexpr int WPR = LR > 32 ? LR / 32 : 1;  // warps per row
+    float (*xchg)[8][2];  // [19][warp][side], used when WPR > 1
+    int lane, warp, wr, row_warp0;
+    // value arriving from the left neighbour cell (direction with c_x = +1)
+    __device__ __forceinline__ float from_left(float v, int i) const {
+        if constexpr (LR <= 32) {
+            const int lx = lane & (LR - 1);
+            return __shfl_sync(0xffffffffu, v, (lx + LR - 1) & (LR - 1), LR);
+        } else {
+            float in = __shfl_sync(0xffffffffu, v, (lane + 31) & 31);
+            if (lane == 31) xchg[i][warp][0] = v;
+            __syncthreads();
+            if (lane == 0) in = xchg[i][row_warp0 + (wr + WPR - 1) % WPR][0];
+            return in;
+        }
+    }
+    // value arriving from the right neighbour cell (direction with c_x = -1)
+    __device__ __forceinline__ float from_right(float v, int i) const {
+        if constexpr (LR <= 32) {
+            const int lx = lane & (LR - 1);
+            return __shfl_sync(0xffffffffu, v, (lx + 1) & (LR - 1), LR);
+        } else {
+            float in = __shfl_sync(0xffffffffu, v, (lane + 1) & 31);
+            if (lane == 0) xchg[i][warp][1] = v;
+            __syncthreads();
+            if (lane == 31) in = xchg[i][row_warp0 + (wr + 1) % WPR][1];
+            return in;
+        }
+    }
+};
+
+template <int LR>
+__host__ __device__ constexpr int rows_per_block() {
+    return LR <= 32 ? 8 * (32 / LR) : 8 / (LR / 32);
+}
+
 template <typename S, int LR>
 __global__ void __launch_bounds__(256, 2)
     k_collide_stream_x4(const S *__restrict__ src, S *__restrict__ dst,
@@ -162,13 +202,28 @@ __global__ void __launch_bounds__(256, 2)
                         float4 *__restrict__ fold, uint8_t *__restrict__ flag_old, int ny, int nz,
                         int ncell, float omega, float u_wall, int *status) {
     constexpr int NX = 4 * LR;
-    constexpr int RPW = 32 / LR;
-    const int lane = threadIdx.x & 31;
-    const int lx = lane & (LR - 1);
+    __shared__ float xchg[LR > 32 ? 19 : 1][8][2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nrows = ny * nz;
-    const int row_raw = blockIdx.x * (8 * RPW) + (threadIdx.x >> 5) * RPW + lane / LR;
+    int row_raw, lx;
+    XShift<LR> sh;
+    sh.xchg = xchg;
+    sh.lane = lane;
+    sh.warp = warp;
+    if constexpr (LR <= 32) {
+        row_raw = blockIdx.x * rows_per_block<LR>() + warp * (32 / LR) + lane / LR;
+        lx = lane & (LR - 1);
+        sh.wr = 0;
+        sh.row_warp0 = 0;
+    } else {
+        constexpr int WPR = LR / 32;
+        row_raw = blockIdx.x * rows_per_block<LR>() + warp / WPR;
+        sh.wr = warp % WPR;
+        sh.row_warp0 = warp - sh.wr;
+        lx = sh.wr * 32 + lane;
+    }
     const bool active = row_raw < nrows;
-    const int row = active ? row_raw : nrows - 1;  // inactive lanes still join the shuffles
+    const int row = active ? row_raw : nrows - 1;  // inactive lanes still join the exchanges
     const int y = row % ny, z = row / ny;
     const int x0 = 4 * lx;
     const int cell0 = x0 + NX * row;
@@ -179,7 +234,8 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
         for (int k = 0; k < 4; ++k) fold[cell0 + k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    __syncwarp();
+    if constexpr (LR <= 32) __syncwarp();  // every lane of the row has read its flag
+    else __syncthreads();
     if (has_old && active && lx == 0) flag_old[row] = 0;
 
     float g[19][4];
@@ -215,7 +271,6 @@ __global__ void __launch_bounds__(256, 2)
     const float guo = 1.f - 0.5f * omega;
     const int yp = (y + 1 == ny) ? 0 : y + 1;
     const int ym = (y == 0) ? ny - 1 : y - 1;
-    const int left = (lx + LR - 1) & (LR - 1), right = (lx + 1) & (LR - 1);
 
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
@@ -242,10 +297,10 @@ __global__ void __launch_bounds__(256, 2)
         // x shift of the quad (before any branch: every lane takes part)
         float o0 = p[0], o1 = p[1], o2 = p[2], o3 = p[3];
         if (cx > 0) {
-            const float in = __shfl_sync(0xffffffffu, p[3], left, LR);
+            const float in = sh.from_left(p[3], i);
             o0 = in; o1 = p[0]; o2 = p[1]; o3 = p[2];
         } else if (cx < 0) {
-            const float in = __shfl_sync(0xffffffffu, p[0], right, LR);
+            const float in = sh.from_right(p[0], i);
             o0 = p[1]; o1 = p[2]; o2 = p[3]; o3 = in;
         }
         if (!active) continue;
@@ -333,9 +388,9 @@ static inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + 
 
 template <typename S, int LR>
 static void collide_x4(const Lattice &L, const CollideArgs &a, cudaStream_t s) {
-    constexpr int rows_per_block = 8 * (32 / LR);
+    constexpr int rpb = rows_per_block<LR>();
     const int nrows = L.ny * L.nz;
-    const unsigned nb = (unsigned)((nrows + rows_per_block - 1) / rows_per_block);
+    const unsigned nb = (unsigned)((nrows + rpb - 1) / rpb);
     k_collide_stream_x4<S, LR><<<nb, 256, 0, s>>>(
         (const S *)a.src, (S *)a.dst, (const float4 *)a.fcur, a.flag_cur, (float4 *)a.fold,
         a.flag_old, L.ny, L.nz, (int)L.ncell, (float)(1.0 / a.tau), (float)a.u_wall, a.status);
@@ -350,6 +405,9 @@ static bool collide_vec(const Lattice &L, const CollideArgs &a, cudaStream_t s) 
         case 8: collide_x4<S, 8>(L, a, s); return true;
         case 16: collide_x4<S, 16>(L, a, s); return true;
         case 32: collide_x4<S, 32>(L, a, s); return true;
+        case 64: collide_x4<S, 64>(L, a, s); return true;
+        case 128: collide_x4<S, 128>(L, a, s); return true;
+        case 256: collide_x4<S, 256>(L, a, s); return true;
         default: return false;
     }
 }

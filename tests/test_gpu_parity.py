@@ -52,7 +52,8 @@ def test_lattice_only_ragged(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
-@pytest.mark.parametrize("shape", [(4, 3, 5), (8, 5, 7), (32, 9, 6), (64, 7, 5), (128, 5, 9)])
+@pytest.mark.parametrize("shape", [(4, 3, 5), (8, 5, 7), (32, 9, 6), (64, 7, 5), (128, 5, 9),
+                                   (256, 3, 7), (512, 2, 3), (1024, 1, 3)])
 def test_lattice_vectorised_rows(shape, prec):
     """The 4-cells-per-thread collide-stream (nx/4 a power of two <= 32), with
     row counts that leave idle lanes in the last block."""
