@@ -150,45 +150,27 @@ struct Quad<__half> {
 // Vectorised collide-and-stream for nx = 4 * LR, LR a power of two <= 256:
 // each thread owns 4 consecutive cells of one x-row and LR lanes cover the
 // row.  With LR <= 32 a warp covers 32 / LR rows; with LR > 32 a row spans
-// LR / 32 warps.  A block has 8 warps.  All 19 loads and stores are 16-byte
+// LR / 32 warps.  A block has 8 warps.  All 19 loads and the stores are 16-byte
 // (float) or 8-byte (half) vectors.  Streaming along x shifts a thread's 4
 // post-collision values by one cell; the value that crosses into the
 // neighbouring thread's quad comes by a warp shuffle (within the row's lane
-// segment when LR <= 32, which also closes the periodic wrap in x); when a row
-// spans several warps, the edge lanes of the warps exchange that value
-// through a shared-memory slot per direction.  One force flag per row.
+// segment when LR <= 32, which also closes the periodic wrap in x).  When a
+// row spans several warps the value that crosses a warp edge is written by
+// its own lane with a scalar store, and the receiving edge lane stores the
+// other three elements of its quad as scalars: no barrier and no shared
+// memory.  One force flag per row.
 template <int LR>
-struct XShift {
-    static constexpr int WPR = LR > 32 ? LR / 32 : 1;  // warps per row
-    float (*xchg)[8][2];  // [19][warp][side], used when WPR > 1
-    int lane, warp, wr, row_warp0;
-    // value arriving from the left neighbour cell (direction with c_x = +1)
-    __device__ __forceinline__ float from_left(float v, int i) const {
-        if constexpr (LR <= 32) {
-            const int lx = lane & (LR - 1);
-            return __shfl_sync(0xffffffffu, v, (lx + LR - 1) & (LR - 1), LR);
-        } else {
-            float in = __shfl_sync(0xffffffffu, v, (lane + 31) & 31);
-            if (lane == 31) xchg[i][warp][0] = v;
-            __syncthreads();
-            if (lane == 0) in = xchg[i][row_warp0 + (wr + WPR - 1) % WPR][0];
-            return in;
-        }
-    }
-    // value arriving from the right neighbour cell (direction with c_x = -1)
-    __device__ __forceinline__ float from_right(float v, int i) const {
-        if constexpr (LR <= 32) {
-            const int lx = lane & (LR - 1);
-            return __shfl_sync(0xffffffffu, v, (lx + 1) & (LR - 1), LR);
-        } else {
-            float in = __shfl_sync(0xffffffffu, v, (lane + 1) & 31);
-            if (lane == 0) xchg[i][warp][1] = v;
-            __syncthreads();
-            if (lane == 31) in = xchg[i][row_warp0 + (wr + 1) % WPR][1];
-            return in;
-        }
-    }
-};
+__device__ __forceinline__ float from_left(float v, int lane) {
+    constexpr int W = LR <= 32 ? LR : 32;
+    const int lx = lane & (W - 1);
+    return __shfl_sync(0xffffffffu, v, (lx + W - 1) & (W - 1), W);
+}
+template <int LR>
+__device__ __forceinline__ float from_right(float v, int lane) {
+    constexpr int W = LR <= 32 ? LR : 32;
+    const int lx = lane & (W - 1);
+    return __shfl_sync(0xffffffffu, v, (lx + 1) & (W - 1), W);
+}
 
 template <int LR>
 __host__ __device__ constexpr int rows_per_block() {
@@ -202,25 +184,16 @@ __global__ void __launch_bounds__(256, 2)
                         float4 *__restrict__ fold, uint8_t *__restrict__ flag_old, int ny, int nz,
                         int ncell, float omega, float u_wall, int *status) {
     constexpr int NX = 4 * LR;
-    __shared__ float xchg[LR > 32 ? 19 : 1][8][2];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nrows = ny * nz;
     int row_raw, lx;
-    XShift<LR> sh;
-    sh.xchg = xchg;
-    sh.lane = lane;
-    sh.warp = warp;
     if constexpr (LR <= 32) {
         row_raw = blockIdx.x * rows_per_block<LR>() + warp * (32 / LR) + lane / LR;
         lx = lane & (LR - 1);
-        sh.wr = 0;
-        sh.row_warp0 = 0;
     } else {
         constexpr int WPR = LR / 32;
         row_raw = blockIdx.x * rows_per_block<LR>() + warp / WPR;
-        sh.wr = warp % WPR;
-        sh.row_warp0 = warp - sh.wr;
-        lx = sh.wr * 32 + lane;
+        lx = (warp % WPR) * 32 + lane;
     }
     const bool active = row_raw < nrows;
     const int row = active ? row_raw : nrows - 1;  // inactive lanes still join the exchanges
@@ -297,10 +270,10 @@ __global__ void __launch_bounds__(256, 2)
         // x shift of the quad (before any branch: every lane takes part)
         float o0 = p[0], o1 = p[1], o2 = p[2], o3 = p[3];
         if (cx > 0) {
-            const float in = sh.from_left(p[3], i);
+            const float in = from_left<LR>(p[3], lane);
             o0 = in; o1 = p[0]; o2 = p[1]; o3 = p[2];
         } else if (cx < 0) {
-            const float in = sh.from_right(p[0], i);
+            const float in = from_right<LR>(p[0], lane);
             o0 = p[1]; o1 = p[2]; o2 = p[3]; o3 = in;
         }
         if (!active) continue;
@@ -312,8 +285,25 @@ __global__ void __launch_bounds__(256, 2)
                            p[2] - wall, p[3] - wall);
         } else {
             const int yt = cy > 0 ? yp : (cy < 0 ? ym : y);
-            const int rt = yt + ny * (z + cz);
-            Quad<S>::store(dst + (size_t)i * ncell + x0 + NX * rt, o0, o1, o2, o3);
+            S *rowp = dst + (size_t)i * ncell + (size_t)NX * (yt + ny * (z + cz));
+            if constexpr (LR > 32) {
+                // warp edges: the crossing value is stored by its own lane
+                if (cx > 0 && lane == 0) {
+                    Store<S, float>::store(rowp + x0 + 1, o1);
+                    Store<S, float>::store(rowp + x0 + 2, o2);
+                    Store<S, float>::store(rowp + x0 + 3, o3);
+                } else if (cx < 0 && lane == 31) {
+                    Store<S, float>::store(rowp + x0, o0);
+                    Store<S, float>::store(rowp + x0 + 1, o1);
+                    Store<S, float>::store(rowp + x0 + 2, o2);
+                } else {
+                    Quad<S>::store(rowp + x0, o0, o1, o2, o3);
+                }
+                if (cx > 0 && lane == 31) Store<S, float>::store(rowp + ((x0 + 4) & (NX - 1)), p[3]);
+                if (cx < 0 && lane == 0) Store<S, float>::store(rowp + ((x0 + NX - 1) & (NX - 1)), p[0]);
+            } else {
+                Quad<S>::store(rowp + x0, o0, o1, o2, o3);
+            }
         }
     }
 }

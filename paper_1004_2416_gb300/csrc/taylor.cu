@@ -4,7 +4,8 @@
 // about the centroid.
 //
 // The faces of a capsule are split over several blocks (FP64 arithmetic is
-// scarce per SM, so a capsule is spread over many SMs).  Three launches, each
+// scarce per SM, so a capsule is spread over many SMs; in the float builds the
+// per-face terms are formed in float and only the sums are in double).  Three launches, each
 // a fixed-order reduction, so results are bitwise reproducible:
 //   1. per block: V = 1/3 sum r.(A n), A = sum |A n|, m = sum (r.(A n)) r with
 //      r the face centroid minus the capsule's origin (its reference centre);
@@ -85,6 +86,105 @@ __device__ __forceinline__ void face_geom(R nodes, const int4 t, double cen[3], 
     An[2] = 0.5 * (e1[0] * e2[1] - e1[1] * e2[0]);
 }
 
+// Terms of one face for the two stages.  FP64 build: double throughout.
+// Float builds: node coordinates relative to the capsule origin are formed
+// from the hi/lo pairs and the face terms are evaluated in float (relative
+// error ~1e-7, well inside the float build's tolerance); only the sums over
+// faces and blocks are carried in double.
+template <typename R>
+struct FaceMath;
+
+template <>
+struct FaceMath<NodeRead<double>> {
+    static __device__ __forceinline__ void stage1(const NodeRead<double> &nodes, int4 t,
+                                                  const double o[3], double v[5]) {
+        double cen[3], An[3];
+        face_geom(nodes, t, cen, An);
+        double r[3];
+        for (int k = 0; k < 3; ++k) r[k] = cen[k] - o[k];
+        const double rn = r[0] * An[0] + r[1] * An[1] + r[2] * An[2];
+        v[0] = rn * (1.0 / 3.0);
+        v[1] = sqrt(An[0] * An[0] + An[1] * An[1] + An[2] * An[2]);
+        v[2] = rn * r[0];
+        v[3] = rn * r[1];
+        v[4] = rn * r[2];
+    }
+    static __device__ __forceinline__ void stage2(const NodeRead<double> &nodes, int4 t,
+                                                  const double o[3], const double c[3], double v[6]) {
+        double cen[3], An[3];
+        face_geom(nodes, t, cen, An);
+        double r[3];
+        for (int k = 0; k < 3; ++k) r[k] = cen[k] - c[k];
+        const double rn = (r[0] * An[0] + r[1] * An[1] + r[2] * An[2]) * 0.2;
+        const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        v[0] = (r2 - r[0] * r[0]) * rn;
+        v[1] = (r2 - r[1] * r[1]) * rn;
+        v[2] = (r2 - r[2] * r[2]) * rn;
+        v[3] = -r[0] * r[1] * rn;
+        v[4] = -r[0] * r[2] * rn;
+        v[5] = -r[1] * r[2] * rn;
+    }
+};
+
+template <>
+struct FaceMath<NodeRead<float>> {
+    // node n relative to the origin, whose hi/lo split is (oh, ol)
+    static __device__ __forceinline__ void rel(const NodeRead<float> &nodes, int n, const float oh[3],
+                                               const float ol[3], float r[3]) {
+        const float4 h = nodes.hi[n], l = nodes.lo[n];
+        r[0] = (h.x - oh[0]) + (l.x - ol[0]);
+        r[1] = (h.y - oh[1]) + (l.y - ol[1]);
+        r[2] = (h.z - oh[2]) + (l.z - ol[2]);
+    }
+    static __device__ __forceinline__ void geom(const NodeRead<float> &nodes, int4 t, const double o[3],
+                                                float cen[3], float An[3]) {
+        float oh[3], ol[3];
+        for (int k = 0; k < 3; ++k) {
+            oh[k] = (float)o[k];
+            ol[k] = (float)(o[k] - (double)oh[k]);
+        }
+        float a[3], b[3], c[3];
+        rel(nodes, t.x, oh, ol, a);
+        rel(nodes, t.y, oh, ol, b);
+        rel(nodes, t.z, oh, ol, c);
+        float e1[3], e2[3];
+        for (int k = 0; k < 3; ++k) {
+            e1[k] = b[k] - a[k];
+            e2[k] = c[k] - a[k];
+            cen[k] = (a[k] + b[k] + c[k]) * (1.0f / 3.0f);
+        }
+        An[0] = 0.5f * (e1[1] * e2[2] - e1[2] * e2[1]);
+        An[1] = 0.5f * (e1[2] * e2[0] - e1[0] * e2[2]);
+        An[2] = 0.5f * (e1[0] * e2[1] - e1[1] * e2[0]);
+    }
+    static __device__ __forceinline__ void stage1(const NodeRead<float> &nodes, int4 t,
+                                                  const double o[3], double v[5]) {
+        float r[3], An[3];
+        geom(nodes, t, o, r, An);
+        const float rn = r[0] * An[0] + r[1] * An[1] + r[2] * An[2];
+        v[0] = (double)rn * (1.0 / 3.0);
+        v[1] = (double)sqrtf(An[0] * An[0] + An[1] * An[1] + An[2] * An[2]);
+        v[2] = (double)(rn * r[0]);
+        v[3] = (double)(rn * r[1]);
+        v[4] = (double)(rn * r[2]);
+    }
+    static __device__ __forceinline__ void stage2(const NodeRead<float> &nodes, int4 t,
+                                                  const double o[3], const double c[3], double v[6]) {
+        float cen[3], An[3];
+        geom(nodes, t, o, cen, An);
+        float r[3];
+        for (int k = 0; k < 3; ++k) r[k] = cen[k] - (float)(c[k] - o[k]);
+        const float rn = (r[0] * An[0] + r[1] * An[1] + r[2] * An[2]) * 0.2f;
+        const float r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        v[0] = (double)((r2 - r[0] * r[0]) * rn);
+        v[1] = (double)((r2 - r[1] * r[1]) * rn);
+        v[2] = (double)((r2 - r[2] * r[2]) * rn);
+        v[3] = (double)(-r[0] * r[1] * rn);
+        v[4] = (double)(-r[0] * r[2] * rn);
+        v[5] = (double)(-r[1] * r[2] * rn);
+    }
+};
+
 template <typename R>
 __global__ void __launch_bounds__(kTB) k_taylor_stage1(R nodes, const int4 *__restrict__ tri, TaylorPlan p) {
     __shared__ double sh[kTB / 32][5];
@@ -93,16 +193,7 @@ __global__ void __launch_bounds__(kTB) k_taylor_stage1(R nodes, const int4 *__re
     double v[5] = {0, 0, 0, 0, 0};
     if ((int)threadIdx.x < p.blk_nface[b]) {
         const int4 t = tri[p.blk_face0[b] + threadIdx.x];
-        double cen[3], An[3];
-        face_geom(nodes, t, cen, An);
-        double r[3];
-        for (int k = 0; k < 3; ++k) r[k] = cen[k] - p.origin[3 * cap + k];
-        const double rn = r[0] * An[0] + r[1] * An[1] + r[2] * An[2];
-        v[0] = rn * (1.0 / 3.0);
-        v[1] = sqrt(An[0] * An[0] + An[1] * An[1] + An[2] * An[2]);
-        v[2] = rn * r[0];
-        v[3] = rn * r[1];
-        v[4] = rn * r[2];
+        FaceMath<R>::stage1(nodes, t, p.origin + 3 * cap, v);
     }
     block_sum<5>(v, sh);
     if (threadIdx.x == 0)
@@ -138,18 +229,7 @@ __global__ void __launch_bounds__(kTB) k_taylor_stage2(R nodes, const int4 *__re
     double v[6] = {0, 0, 0, 0, 0, 0};
     if ((int)threadIdx.x < p.blk_nface[b]) {
         const int4 t = tri[p.blk_face0[b] + threadIdx.x];
-        double cen[3], An[3];
-        face_geom(nodes, t, cen, An);
-        double r[3];
-        for (int k = 0; k < 3; ++k) r[k] = cen[k] - cen_sh[k];
-        const double rn = (r[0] * An[0] + r[1] * An[1] + r[2] * An[2]) * 0.2;
-        const double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-        v[0] = (r2 - r[0] * r[0]) * rn;
-        v[1] = (r2 - r[1] * r[1]) * rn;
-        v[2] = (r2 - r[2] * r[2]) * rn;
-        v[3] = -r[0] * r[1] * rn;
-        v[4] = -r[0] * r[2] * rn;
-        v[5] = -r[1] * r[2] * rn;
+        FaceMath<R>::stage2(nodes, t, p.origin + 3 * cap, cen_sh, v);
     }
     block_sum<6>(v, sh);
     if (threadIdx.x == 0)

@@ -227,8 +227,14 @@ def test_taylor_matches_oracle(prec):
     xg = s.get_nodes(cid)
     Tg = s.taylor(cid)
     To = O.taylor(xg, tri)
+    # FP64 build: double throughout; float builds: per-face terms in float,
+    # sums in double (relative error of order 1e-7 in the sums)
+    tol = 1e-11 if prec == "fp64" else 2e-6
+    scale = {k: max(abs(v), 1.0) for k, v in To.items()}
+    for k in ("I_xy", "I_xz", "I_yz"):
+        scale[k] = max(scale[k], abs(To["I_xx"]))
     for k, v in To.items():
-        assert abs(Tg[k] - v) <= 1e-11 * max(abs(v), 1.0), (k, Tg[k], v)
+        assert abs(Tg[k] - v) <= tol * scale[k], (k, Tg[k], v)
 
 
 # ---- edge cases ------------------------------------------------------------------------------
