@@ -300,8 +300,11 @@ int ensure_mesh(iblbm_sim *s) {
         p.origin = (const double *)P(sizeof(double) * 3 * nc);
         p.partial = (double *)P(sizeof(double) * 16 * nb);
         p.out = (double *)P(sizeof(double) * 12 * nc);
-        if (!p.blk_cap || !p.blk_face0 || !p.blk_nface || !p.cap_blk0 || !p.origin || !p.partial || !p.out)
+        p.ticket = (unsigned *)P(sizeof(unsigned));
+        if (!p.blk_cap || !p.blk_face0 || !p.blk_nface || !p.cap_blk0 || !p.origin || !p.partial ||
+            !p.out || !p.ticket)
             return fail(s, IBLBM_ERR_OOM, "Taylor plan allocation failed");
+        CK(cudaMemsetAsync(p.ticket, 0, sizeof(unsigned), s->stream));
         CK(cudaMemcpyAsync((void *)p.blk_cap, bcap.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s->stream));
         CK(cudaMemcpyAsync((void *)p.blk_face0, bf0.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s->stream));
         CK(cudaMemcpyAsync((void *)p.blk_nface, bnf.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s->stream));

@@ -16,7 +16,7 @@ namespace iblbm {
 // kTileX x kTileY x 1 cells; the vectorised one on whole x-rows (4 cells per
 // thread, nx/4 lanes per row, nx/4 a power of two <= 256).  The sparse
 // force-density flags have the granularity of the kernel in use:
-// ftx x fty x 1 cells per flag.
+// ftx x fty x 1 cells per flag (32 x 8 tiles, or 32-cell segments of a row).
 constexpr int kTileX = 32;
 constexpr int kTileY = 8;
 
@@ -41,7 +41,7 @@ inline Lattice make_lattice(int nx, int ny, int nz, bool vec) {
     L.ntx = (nx + kTileX - 1) / kTileX;
     L.nty = (ny + kTileY - 1) / kTileY;
     L.lanes_row = (vec && nx % 4 == 0 && is_pow2(nx / 4) && nx / 4 <= 256) ? nx / 4 : 0;
-    L.ftx = L.lanes_row ? nx : kTileX;
+    L.ftx = L.lanes_row ? (nx < 32 ? nx : 32) : kTileX;  // vector kernel: 32-cell row segments
     L.fty = L.lanes_row ? 1 : kTileY;
     L.nfx = (nx + L.ftx - 1) / L.ftx;
     L.nfy = (ny + L.fty - 1) / L.fty;
@@ -118,8 +118,9 @@ struct TaylorPlan {
     double *ring;           // [ring_len][n_caps][12] recorded results (or null)
     int ring_len;
     unsigned long long *ring_count;  // records written so far
+    unsigned *ticket;       // blocks of the last stage done (returns to 0)
 };
-constexpr int kTaylorFacesPerBlock = 128;
+constexpr int kTaylorFacesPerBlock = 512;  // 128 threads x 4 faces
 // record = false: results to p.out; record = true: to the next ring slot.
 void launch_taylor(int prec, const MeshDev &m, const TaylorPlan &p, bool record, cudaStream_t s);
 

@@ -158,7 +158,7 @@ struct Quad<__half> {
 // row spans several warps the value that crosses a warp edge is written by
 // its own lane with a scalar store, and the receiving edge lane stores the
 // other three elements of its quad as scalars: no barrier and no shared
-// memory.  One force flag per row.
+// memory.  One force flag per 32-cell segment of a row.
 template <int LR>
 __device__ __forceinline__ float from_left(float v, int lane) {
     constexpr int W = LR <= 32 ? LR : 32;
@@ -201,15 +201,18 @@ __global__ void __launch_bounds__(256, 2)
     const int x0 = 4 * lx;
     const int cell0 = x0 + NX * row;
 
-    const bool has_old = flag_old[row] != 0;
-    const bool has_cur = flag_cur[row] != 0;
+    // force flags per 32-cell segment of a row (the whole row if nx < 32); the
+    // lanes of one segment are consecutive lanes of one warp
+    constexpr int FTX = NX < 32 ? NX : 32;
+    const int fidx = row * (NX / FTX) + x0 / FTX;
+    const bool has_old = flag_old[fidx] != 0;
+    const bool has_cur = flag_cur[fidx] != 0;
     if (has_old && active) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) fold[cell0 + k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    if constexpr (LR <= 32) __syncwarp();  // every lane of the row has read its flag
-    else __syncthreads();
-    if (has_old && active && lx == 0) flag_old[row] = 0;
+    __syncwarp();  // every lane of the segment has read its flag
+    if (has_old && active && x0 % FTX == 0) flag_old[fidx] = 0;
 
     float g[19][4];
 #pragma unroll

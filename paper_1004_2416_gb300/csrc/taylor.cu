@@ -13,8 +13,9 @@
 //      forms the centroid c = origin + m / (4 V), then sums the inertia terms
 //      of its faces about c;
 //   3. per capsule: totals of both stages -> {V, A, c, I} in the output.
-// Per-block partials live in a scratch array [blocks][16] (stage 1 in
-// entries 0..4, stage 2 in entries 8..13).
+// A block of 128 threads takes up to 512 faces (4 per thread).  Per-block
+// partials live in a scratch array [blocks][16] (stage 1 in entries 0..4,
+// stage 2 in entries 8..13).
 #include <mutex>
 #include <string>
 
@@ -46,7 +47,7 @@ struct NodeRead<float> {
     }
 };
 
-constexpr int kTB = kTaylorFacesPerBlock;  // threads per block, one face each
+constexpr int kTB = 128;  // threads per block
 
 // Fixed-order block sum of K doubles per thread; result valid in thread 0.
 template <int K>
@@ -191,9 +192,11 @@ __global__ void __launch_bounds__(kTB) k_taylor_stage1(R nodes, const int4 *__re
     const int b = blockIdx.x;
     const int cap = p.blk_cap[b];
     double v[5] = {0, 0, 0, 0, 0};
-    if ((int)threadIdx.x < p.blk_nface[b]) {
-        const int4 t = tri[p.blk_face0[b] + threadIdx.x];
-        FaceMath<R>::stage1(nodes, t, p.origin + 3 * cap, v);
+    for (int j = threadIdx.x; j < p.blk_nface[b]; j += kTB) {
+        const int4 t = tri[p.blk_face0[b] + j];
+        double w[5];
+        FaceMath<R>::stage1(nodes, t, p.origin + 3 * cap, w);
+        for (int k = 0; k < 5; ++k) v[k] += w[k];
     }
     block_sum<5>(v, sh);
     if (threadIdx.x == 0)
@@ -227,26 +230,31 @@ __global__ void __launch_bounds__(kTB) k_taylor_stage2(R nodes, const int4 *__re
     }
     __syncthreads();
     double v[6] = {0, 0, 0, 0, 0, 0};
-    if ((int)threadIdx.x < p.blk_nface[b]) {
-        const int4 t = tri[p.blk_face0[b] + threadIdx.x];
-        FaceMath<R>::stage2(nodes, t, p.origin + 3 * cap, cen_sh, v);
+    for (int j = threadIdx.x; j < p.blk_nface[b]; j += kTB) {
+        const int4 t = tri[p.blk_face0[b] + j];
+        double w[6];
+        FaceMath<R>::stage2(nodes, t, p.origin + 3 * cap, cen_sh, w);
+        for (int k = 0; k < 6; ++k) v[k] += w[k];
     }
     block_sum<6>(v, sh);
     if (threadIdx.x == 0)
         for (int k = 0; k < 6; ++k) p.partial[16 * b + 8 + k] = v[k];
 }
 
-// One block of 32 warps; warp w takes capsules w, w + 32, ...  In recording
-// mode the block writes the next ring slot and then advances the counter.
-__global__ void __launch_bounds__(1024) k_taylor_stage3(TaylorPlan p, int record) {
+// One warp per capsule, 8 capsules per block, as many blocks as needed (the
+// FP64 work is spread over the SMs).  In recording mode every block writes its
+// capsules into the next ring slot and the last block to finish advances the
+// record counter.
+__global__ void __launch_bounds__(256) k_taylor_stage3(TaylorPlan p, int record) {
     double *base = p.out;
     unsigned long long count = 0;
     if (record) {
         count = *p.ring_count;
         base = p.ring + (size_t)(count % (unsigned long long)p.ring_len) * p.n_caps * 12;
     }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int cap = warp; cap < p.n_caps; cap += blockDim.x >> 5) {
+    const int lane = threadIdx.x & 31;
+    const int cap = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (cap < p.n_caps) {
         double tot[5], I[6];
         capsule_totals<5>(p, cap, 0, tot);
         capsule_totals<6>(p, cap, 8, I);
@@ -259,15 +267,23 @@ __global__ void __launch_bounds__(1024) k_taylor_stage3(TaylorPlan p, int record
             o[11] = 0.0;
         }
     }
-    __syncthreads();
-    if (record && threadIdx.x == 0) *p.ring_count = count + 1;
+    if (record) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(p.ticket, 1u) == gridDim.x - 1) {
+                *p.ticket = 0u;
+                *p.ring_count = count + 1;
+            }
+        }
+    }
 }
 
 template <typename R>
 static void taylor_impl(R nodes, const MeshDev &m, const TaylorPlan &p, bool record, cudaStream_t s) {
     k_taylor_stage1<R><<<p.total_blocks, kTB, 0, s>>>(nodes, (const int4 *)m.tri, p);
     k_taylor_stage2<R><<<p.total_blocks, kTB, 0, s>>>(nodes, (const int4 *)m.tri, p);
-    k_taylor_stage3<<<1, 1024, 0, s>>>(p, record ? 1 : 0);
+    k_taylor_stage3<<<(p.n_caps + 7) / 8, 256, 0, s>>>(p, record ? 1 : 0);
 }
 
 void launch_taylor(int prec, const MeshDev &m, const TaylorPlan &p, bool record, cudaStream_t s) {
