@@ -269,17 +269,18 @@ int ensure_mesh(iblbm_sim *s) {
         launch_f64_to_nodes(s->prec, s->mesh, 0, nn, s->d_scratch, s->stream);
         CK(cudaGetLastError());
     }
-    // Taylor plan: kTaylorFacesPerBlock faces per block
+    // Taylor plan: taylor_faces_per_block faces per block
     {
         std::vector<int> bcap, bf0, bnf, cb0(nc + 1, 0);
         std::vector<double> org(3 * (size_t)nc);
+        const int fpb = taylor_faces_per_block(nf);
         for (int c = 0; c < nc; ++c) {
             const Capsule &cp = s->caps[c];
             cb0[c] = (int)bcap.size();
-            for (int f = 0; f < cp.n_faces; f += kTaylorFacesPerBlock) {
+            for (int f = 0; f < cp.n_faces; f += fpb) {
                 bcap.push_back(c);
                 bf0.push_back(cp.face0 + f);
-                bnf.push_back(std::min(kTaylorFacesPerBlock, cp.n_faces - f));
+                bnf.push_back(std::min(fpb, cp.n_faces - f));
             }
             for (int k = 0; k < 3; ++k) org[3 * c + k] = cp.origin[k];
         }

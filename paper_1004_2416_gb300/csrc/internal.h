@@ -120,7 +120,16 @@ struct TaylorPlan {
     unsigned long long *ring_count;  // records written so far
     unsigned *ticket;       // blocks of the last stage done (returns to 0)
 };
-constexpr int kTaylorFacesPerBlock = 512;  // 128 threads x 4 faces
+// A block of 128 threads takes between 128 and kTaylorMaxFacesPerBlock faces:
+// as few as keep about two blocks per SM busy, so small meshes get short
+// chains and large ones fewer FP64 block reductions.
+constexpr int kTaylorThreads = 128;
+constexpr int kTaylorMaxFacesPerBlock = 1024;
+inline int taylor_faces_per_block(long long total_faces) {
+    long long f = kTaylorThreads;
+    while (f < kTaylorMaxFacesPerBlock && total_faces / f > 2 * 152) f *= 2;
+    return (int)f;
+}
 // record = false: results to p.out; record = true: to the next ring slot.
 void launch_taylor(int prec, const MeshDev &m, const TaylorPlan &p, bool record, cudaStream_t s);
 

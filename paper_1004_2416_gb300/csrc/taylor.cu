@@ -13,7 +13,7 @@
 //      forms the centroid c = origin + m / (4 V), then sums the inertia terms
 //      of its faces about c;
 //   3. per capsule: totals of both stages -> {V, A, c, I} in the output.
-// A block of 128 threads takes up to 512 faces (4 per thread).  Per-block
+// A block of 128 threads takes 128 to 1024 faces (chosen by the host).  Per-block
 // partials live in a scratch array [blocks][16] (stage 1 in entries 0..4,
 // stage 2 in entries 8..13).
 #include <mutex>
@@ -47,7 +47,7 @@ struct NodeRead<float> {
     }
 };
 
-constexpr int kTB = 128;  // threads per block
+constexpr int kTB = kTaylorThreads;  // threads per block
 
 // Fixed-order block sum of K doubles per thread; result valid in thread 0.
 template <int K>
