@@ -78,7 +78,15 @@ typedef struct {
     int64_t step;      /* completed time steps */
     double tau;
     double u_wall;
+    int n_runs;        /* lattices of a batch (1 for a single lattice) */
 } iblbm_info;
+
+/* One independent lattice of a batch (see iblbm_create_batch). */
+typedef struct {
+    int nx, ny, nz;
+    double tau;
+    double u_wall;  /* walls at z = -1/2 and nz - 1/2 move with -u_wall, +u_wall */
+} iblbm_run_spec;
 
 /* ---- life cycle ---------------------------------------------------------- */
 
@@ -92,6 +100,18 @@ typedef struct {
 int iblbm_create(iblbm_sim **out, int nx, int ny, int nz, double tau,
                  int precision, int delta_points, void *stream,
                  const iblbm_allocator *alloc);
+
+/* Creates a batch of n_runs independent lattices (runs) of uneven sizes, each
+ * with its own relaxation time and wall speed, advanced together: every time
+ * step is one launch per sub-step for all runs, the collide-and-stream being a
+ * persistent kernel that walks a work list of (run, tile) pairs.  Capsules
+ * are added to a run with iblbm_add_capsule_icosphere_in_run; capsule ids are
+ * global over the batch.  Fluid getters of the whole lattice apply only to a
+ * batch of one run; use the iblbm_get_run_* functions otherwise.  Limits: as
+ * iblbm_create for each run, 1 <= n_runs <= 2^20, all cells <= 2^31 - 1. */
+int iblbm_create_batch(iblbm_sim **out, const iblbm_run_spec *runs, int n_runs,
+                       int precision, int delta_points, void *stream,
+                       const iblbm_allocator *alloc);
 
 /* Frees all device and host memory of the object (NULL is accepted). */
 int iblbm_destroy(iblbm_sim *sim);
@@ -130,6 +150,23 @@ int iblbm_add_capsule_icosphere(iblbm_sim *sim, double cx, double cy,
  * most 32 faces. */
 int iblbm_add_capsule_mesh(iblbm_sim *sim, const double *ref_xyz, int n_nodes,
                            const int32_t *tri, int n_tri, int *capsule_id);
+
+/* As iblbm_add_capsule_icosphere, into run `run` of a batch (run 0 for a
+ * single lattice); coordinates are those of the run's own lattice. */
+int iblbm_add_capsule_icosphere_in_run(iblbm_sim *sim, int run, double cx,
+                                       double cy, double cz, double radius,
+                                       int subdivisions, int *capsule_id);
+
+/* Batch only: times the persistent collide-and-stream kernel on the runs of
+ * each distinct box size with each tile shape (32x8, 16x16, 8x32, 64x4,
+ * 128x2, 256x1 cells per 256-thread block), `repeats` launches per shape,
+ * and keeps the fastest shape per size.  Must precede the first step (it
+ * overwrites the second population buffer only).  A single lattice has fixed
+ * kernels and returns at once. */
+int iblbm_autotune_tiles(iblbm_sim *sim, int repeats);
+
+/* Tile shape (cells along x and y per block) used for a run. */
+int iblbm_get_run_tile(const iblbm_sim *sim, int run, int *tx, int *ty);
 
 /* Skalak law, Eq. (constitutivelaw) (Sec. II.B): shear modulus k_s and
  * area-dilation modulus k_alpha = C k_s.  capsule_id = -1 sets every capsule.
@@ -205,6 +242,12 @@ int iblbm_set_populations(iblbm_sim *sim, const double *host_in);
 /* Force density f(X, t) spread in the last step (Eq. forcespreading),
  * [3][nz][ny][nx]; zero before the first step. */
 int iblbm_get_force_field(iblbm_sim *sim, double *host_out);
+
+/* Per-run variants of the velocity and population access of a batch
+ * ([3][nz][ny][nx] and [19][nz][ny][nx] of that run). */
+int iblbm_get_run_velocity(iblbm_sim *sim, int run, double *host_out);
+int iblbm_get_run_populations(iblbm_sim *sim, int run, double *host_out);
+int iblbm_set_run_populations(iblbm_sim *sim, int run, const double *host_in);
 
 /* Node positions [n][3] of one capsule (capsule_id >= 0) or of all capsules
  * in id order (capsule_id = -1). */

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -20,9 +21,13 @@ namespace {
 
 struct Capsule {
     int node0, n_nodes, face0, n_faces;
+    int run;  // lattice (run) of a batch; 0 for a single lattice
     double ks, ka;
     double origin[3];  // reference centre (mean of the reference nodes)
 };
+
+// Tile shapes the batched collide kernel can use (tx * ty = 256 threads).
+constexpr int kTileShapes[6][2] = {{32, 8}, {16, 16}, {8, 32}, {64, 4}, {128, 2}, {256, 1}};
 
 constexpr int kGraphSteps = 32;  // steps per captured graph (even)
 
@@ -50,8 +55,9 @@ struct iblbm_sim {
     const char *launch_fail = nullptr;  // first kernel group whose launch failed
     iblbm_allocator alloc{};
     bool has_alloc = false;
-    size_t pop_bytes = 0;  // one population buffer
-    size_t vec_bytes = 0;  // one force buffer
+    size_t pop_bytes = 0;   // one population buffer
+    size_t vec_bytes = 0;   // one force buffer
+    size_t flag_bytes = 0;  // one flag buffer
     void *pop[2] = {nullptr, nullptr};
     int cur = 0;  // pop[cur] holds f(t); force[cur] the last spread force
     void *force[2] = {nullptr, nullptr};
@@ -78,6 +84,17 @@ struct iblbm_sim {
     double *d_ring = nullptr;
     unsigned long long *d_ring_count = nullptr;
     std::vector<int64_t> rec_steps;  // step number of every record enqueued
+
+    // Batch of independent runs (iblbm_create_batch): run table, work list of
+    // (run, tile) pairs for the persistent collide kernel, per-node run index.
+    bool batch = false;
+    std::vector<RunDesc> runs;
+    std::vector<long long> run_tile_cap;  // flags reserved per run (largest tile count)
+    RunDesc *d_runs = nullptr;
+    int2 *d_items = nullptr;
+    int n_items = 0;
+    int batch_grid = 0;
+    int *d_node_run = nullptr;
 
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int graph_len = 0;
@@ -185,9 +202,18 @@ int ensure_mesh(iblbm_sim *s) {
     void *tri4 = A(sizeof(int) * 4 * nf);
     void *fconst = A(3 * v4 * nf);
     void *capmod = A(v4 * nc);
+    void *node_run = s->batch ? A(sizeof(int) * nn) : nullptr;
     if (!m.x || (s->prec != kF64 && !m.x_lo) || !m.F || !m.u || !adj_off || !adj || !tri4 ||
-        !fconst || !capmod)
+        !fconst || !capmod || (s->batch && !node_run))
         return fail(s, IBLBM_ERR_OOM, "membrane table allocation failed");
+    if (s->batch) {
+        std::vector<int> nr(nn, 0);
+        for (const Capsule &cp : s->caps)
+            for (int n = cp.node0; n < cp.node0 + cp.n_nodes; ++n) nr[n] = cp.run;
+        CK(cudaMemcpyAsync(node_run, nr.data(), sizeof(int) * nn, cudaMemcpyHostToDevice, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+    }
+    s->d_node_run = (int *)node_run;
 
     // node -> (face, corner) lists in ascending face order
     std::vector<int> off(nn + 1, 0), ent(3 * (size_t)nf);
@@ -366,7 +392,7 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) 
     };
     if (ev) cudaEventRecord(ev[0], s->stream);
     launch_force_spread(s->prec, s->delta, s->L, s->mesh, s->force[n], s->flags[n], s->d_status,
-                        s->stream);
+                        s->batch ? s->d_runs : nullptr, s->d_node_run, s->stream);
     mark("membrane force + spreading");
     if (ev) cudaEventRecord(ev[1], s->stream);
     CollideArgs a;
@@ -379,7 +405,12 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) 
     a.tau = s->tau;
     a.u_wall = s->u_wall;
     a.status = s->d_status;
-    launch_collide_stream(s->prec, s->L, a, s->stream);
+    if (s->batch) {
+        BatchArgs b{s->d_runs, s->d_items, s->n_items, s->batch_grid};
+        launch_collide_batch(s->prec, b, a, s->stream);
+    } else {
+        launch_collide_stream(s->prec, s->L, a, s->stream);
+    }
     mark("collide-stream");
     if (ev) cudaEventRecord(ev[2], s->stream);
     if (s->side_pending) {  // the previous record still reads the positions
@@ -387,7 +418,8 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) 
         s->side_pending = false;
         mark("join of the Taylor record");
     }
-    launch_interp_advect(s->prec, s->delta, s->L, s->mesh, s->pop[n], s->force[n], s->stream);
+    launch_interp_advect(s->prec, s->delta, s->L, s->mesh, s->pop[n], s->force[n],
+                         s->batch ? s->d_runs : nullptr, s->d_node_run, s->stream);
     mark("interpolation + advection");
     if (ev) cudaEventRecord(ev[3], s->stream);
     if (record) {
@@ -451,8 +483,10 @@ int capsule_range(iblbm_sim *s, int id, int *first, int *count) {
     return IBLBM_OK;
 }
 
-int add_capsule(iblbm_sim *s, const double *xyz, int n_nodes, const int *tri, int n_tri, int *id) {
+int add_capsule(iblbm_sim *s, int run, const double *xyz, int n_nodes, const int *tri, int n_tri,
+                int *id) {
     if (n_nodes < 4 || n_tri < 4 || !xyz || !tri) return fail(s, IBLBM_ERR_ARG, "bad mesh arguments");
+    if (run < 0 || run >= (s->batch ? (int)s->runs.size() : 1)) return fail(s, IBLBM_ERR_ARG, "no such run");
     for (int k = 0; k < 3 * n_tri; ++k)
         if (tri[k] < 0 || tri[k] >= n_nodes) return fail(s, IBLBM_ERR_ARG, "face index out of range");
     for (int k = 0; k < 3 * n_nodes; ++k)
@@ -462,6 +496,7 @@ int add_capsule(iblbm_sim *s, const double *xyz, int n_nodes, const int *tri, in
     c.n_nodes = n_nodes;
     c.face0 = (int)(s->tri.size() / 3);
     c.n_faces = n_tri;
+    c.run = run;
     c.ks = 0.0;
     c.ka = 0.0;
     for (int k = 0; k < 3; ++k) {
@@ -499,6 +534,128 @@ const char *iblbm_last_error(const iblbm_sim *s) {
     return s ? s->err.c_str() : g_create_error.c_str();
 }
 
+}  // extern "C"
+
+namespace {
+
+// Streams, events and the state buffers for `cells` lattice cells and
+// `tiles` force flags; zeroes forces, flags and the status word.
+int setup_object(iblbm_sim *s, void *stream, const iblbm_allocator *alloc, long long cells,
+                 long long tiles) {
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        cudaGetLastError();
+        g_create_error = "no CUDA device";
+        return IBLBM_ERR_CUDA;
+    }
+    if (alloc) {
+        s->alloc = *alloc;
+        s->has_alloc = true;
+    }
+    if (stream) {
+        s->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            g_create_error = "cudaStreamCreate failed";
+            return IBLBM_ERR_CUDA;
+        }
+        s->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        g_create_error = "stream or event creation failed";
+        return IBLBM_ERR_CUDA;
+    }
+    const size_t el = s->prec == kF64 ? 8 : (s->prec == kF32 ? 4 : 2);
+    s->pop_bytes = 19 * el * (size_t)cells;
+    s->vec_bytes = 4 * real_bytes(s) * (size_t)cells;
+    s->flag_bytes = (size_t)tiles;
+    bool ok = true;
+    for (int k = 0; k < 2 && ok; ++k) {
+        s->pop[k] = dev_alloc(s, s->pop_bytes);
+        s->force[k] = dev_alloc(s, s->vec_bytes);
+        s->flags[k] = (uint8_t *)dev_alloc(s, s->flag_bytes);
+        ok = s->pop[k] && s->force[k] && s->flags[k];
+    }
+    s->d_status = (int *)dev_alloc(s, sizeof(int));
+    if (!ok || !s->d_status) {
+        g_create_error = "device allocation failed";
+        return IBLBM_ERR_OOM;
+    }
+    for (int k = 0; k < 2; ++k) {
+        cudaMemsetAsync(s->force[k], 0, s->vec_bytes, s->stream);
+        cudaMemsetAsync(s->flags[k], 0, s->flag_bytes, s->stream);
+    }
+    cudaMemsetAsync(s->d_status, 0, sizeof(int), s->stream);
+    return IBLBM_OK;
+}
+
+int finish_create(iblbm_sim *s, iblbm_sim **out) {
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        g_create_error = std::string("initialisation failed: ") + cudaGetErrorString(e);
+        iblbm_destroy(s);
+        return IBLBM_ERR_CUDA;
+    }
+    *out = s;
+    return IBLBM_OK;
+}
+
+// Lattice of one run and the byte offsets of its populations and forces.
+Lattice run_lattice(const iblbm_sim *s, int run, size_t *pop_off, size_t *vec_off) {
+    if (!s->batch) {
+        *pop_off = 0;
+        *vec_off = 0;
+        return s->L;
+    }
+    const RunDesc &R = s->runs[run];
+    const size_t el = s->prec == kF64 ? 8 : (s->prec == kF32 ? 4 : 2);
+    *pop_off = 19 * el * (size_t)R.cell_off;
+    *vec_off = 4 * real_bytes(s) * (size_t)R.cell_off;
+    return make_lattice(R.nx, R.ny, R.nz, false);
+}
+
+// (Re)builds the work list of the batched collide kernel and uploads the run
+// table; flag regions of the runs are fixed (reserved for the largest tile
+// count of any tile shape).
+int upload_batch_tables(iblbm_sim *s) {
+    std::vector<int2> items;
+    long long off = 0;
+    for (size_t r = 0; r < s->runs.size(); ++r) {
+        RunDesc &R = s->runs[r];
+        R.ntx = (R.nx + R.tx - 1) / R.tx;
+        R.nty = (R.ny + R.ty - 1) / R.ty;
+        R.tile_off = off;
+        off += s->run_tile_cap[r];
+        const int nt = R.ntx * R.nty * R.nz;
+        for (int t = 0; t < nt; ++t) items.push_back(make_int2((int)r, t));
+    }
+    dev_free(s, s->d_runs);
+    dev_free(s, s->d_items);
+    s->d_runs = (RunDesc *)dev_alloc(s, sizeof(RunDesc) * s->runs.size());
+    s->d_items = (int2 *)dev_alloc(s, sizeof(int2) * items.size());
+    if (!s->d_runs || !s->d_items) return fail(s, IBLBM_ERR_OOM, "run table allocation failed");
+    CK(cudaMemcpyAsync(s->d_runs, s->runs.data(), sizeof(RunDesc) * s->runs.size(),
+                       cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice,
+                       s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->n_items = (int)items.size();
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
+    const long long want = (long long)sms * collide_batch_blocks_per_sm(s->prec);
+    s->batch_grid = (int)std::max(1LL, std::min<long long>(want, s->n_items));
+    drop_graphs(s);
+    return IBLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 int iblbm_create(iblbm_sim **out, int nx, int ny, int nz, double tau, int precision,
                  int delta_points, void *stream, const iblbm_allocator *alloc) {
     if (!out) return IBLBM_ERR_ARG;
@@ -526,67 +683,88 @@ int iblbm_create(iblbm_sim **out, int nx, int ny, int nz, double tau, int precis
     s->prec = precision;
     s->delta = delta_points;
     s->tau = tau;
-    if (cudaGetDevice(&s->device) != cudaSuccess) {
-        cudaGetLastError();
-        g_create_error = "no CUDA device";
-        delete s;
-        return IBLBM_ERR_CUDA;
-    }
-    if (alloc) {
-        s->alloc = *alloc;
-        s->has_alloc = true;
-    }
-    if (stream) {
-        s->stream = (cudaStream_t)stream;
-    } else {
-        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
-            cudaGetLastError();
-            g_create_error = "cudaStreamCreate failed";
-            delete s;
-            return IBLBM_ERR_CUDA;
-        }
-        s->own_stream = true;
-    }
-    if (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess) {
-        cudaGetLastError();
-        g_create_error = "stream or event creation failed";
+    int rc = setup_object(s, stream, alloc, s->L.ncell, s->L.ntiles);
+    if (rc) {
         iblbm_destroy(s);
-        return IBLBM_ERR_CUDA;
+        return rc;
     }
-    const size_t el = precision == kF64 ? 8 : (precision == kF32 ? 4 : 2);
-    s->pop_bytes = 19 * el * (size_t)s->L.ncell;
-    s->vec_bytes = 4 * real_bytes(s) * (size_t)s->L.ncell;
-    bool ok = true;
-    for (int k = 0; k < 2 && ok; ++k) {
-        s->pop[k] = dev_alloc(s, s->pop_bytes);
-        s->force[k] = dev_alloc(s, s->vec_bytes);
-        s->flags[k] = (uint8_t *)dev_alloc(s, (size_t)s->L.ntiles);
-        ok = s->pop[k] && s->force[k] && s->flags[k];
-    }
-    s->d_status = (int *)dev_alloc(s, sizeof(int));
-    ok = ok && s->d_status;
-    if (!ok) {
-        g_create_error = "device allocation failed";
-        iblbm_destroy(s);
-        return IBLBM_ERR_OOM;
-    }
-    for (int k = 0; k < 2; ++k) {
-        cudaMemsetAsync(s->force[k], 0, s->vec_bytes, s->stream);
-        cudaMemsetAsync(s->flags[k], 0, (size_t)s->L.ntiles, s->stream);
-    }
-    cudaMemsetAsync(s->d_status, 0, sizeof(int), s->stream);
     launch_init_fluid(s->prec, s->L, s->pop[0], 0, 0.0, s->stream);
-    cudaError_t e = cudaStreamSynchronize(s->stream);
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        g_create_error = std::string("initialisation failed: ") + cudaGetErrorString(e);
-        iblbm_destroy(s);
-        return IBLBM_ERR_CUDA;
+    return finish_create(s, out);
+}
+
+int iblbm_create_batch(iblbm_sim **out, const iblbm_run_spec *specs, int n_runs, int precision,
+                       int delta_points, void *stream, const iblbm_allocator *alloc) {
+    if (!out) return IBLBM_ERR_ARG;
+    *out = nullptr;
+    g_create_error.clear();
+    if (!specs || n_runs < 1 || n_runs > (1 << 20)) {
+        g_create_error = "need 1 <= n_runs <= 2^20 run specifications";
+        return IBLBM_ERR_ARG;
     }
-    *out = s;
-    return IBLBM_OK;
+    if (precision < 0 || precision > 2 || delta_points < 2 || delta_points > 4) {
+        g_create_error = "precision must be 0..2 and delta_points 2..4";
+        return IBLBM_ERR_ARG;
+    }
+    if (alloc && (!alloc->alloc || !alloc->free)) {
+        g_create_error = "allocator needs both alloc and free";
+        return IBLBM_ERR_ARG;
+    }
+    long long cells = 0, tiles = 0;
+    for (int r = 0; r < n_runs; ++r) {
+        const iblbm_run_spec &q = specs[r];
+        if (q.nx < 1 || q.ny < 1 || q.nz < 1 || !(q.tau > 0.5) || !std::isfinite(q.tau) ||
+            !std::isfinite(q.u_wall) || std::fabs(q.u_wall) > 0.3) {
+            g_create_error = "run " + std::to_string(r) + ": bad size, tau or wall speed";
+            return IBLBM_ERR_ARG;
+        }
+        cells += (long long)q.nx * q.ny * q.nz;
+    }
+    if (cells > 2147483647LL) {
+        g_create_error = "more than 2^31 - 1 cells in the batch";
+        return IBLBM_ERR_ARG;
+    }
+    iblbm_sim *s = new (std::nothrow) iblbm_sim();
+    if (!s) return IBLBM_ERR_OOM;
+    s->batch = true;
+    s->prec = precision;
+    s->delta = delta_points;
+    s->tau = specs[0].tau;
+    s->u_wall = specs[0].u_wall;
+    long long off = 0;
+    for (int r = 0; r < n_runs; ++r) {
+        const iblbm_run_spec &q = specs[r];
+        RunDesc R{};
+        R.nx = q.nx;
+        R.ny = q.ny;
+        R.nz = q.nz;
+        R.tx = 32;
+        R.ty = 8;
+        R.cell_off = off;
+        R.ncell = (long long)q.nx * q.ny * q.nz;
+        R.omega = 1.0 / q.tau;
+        R.u_wall = q.u_wall;
+        off += R.ncell;
+        long long cap = 0;
+        for (const auto &sh : kTileShapes)
+            cap = std::max(cap, (long long)((q.nx + sh[0] - 1) / sh[0]) * ((q.ny + sh[1] - 1) / sh[1]) * q.nz);
+        s->run_tile_cap.push_back(cap);
+        tiles += cap;
+        s->runs.push_back(R);
+    }
+    s->L = make_lattice(specs[0].nx, specs[0].ny, specs[0].nz, false);
+    int rc = setup_object(s, stream, alloc, cells, tiles);
+    if (!rc) rc = upload_batch_tables(s);
+    if (rc) {
+        if (!s->err.empty()) g_create_error = s->err;
+        iblbm_destroy(s);
+        return rc;
+    }
+    for (int r = 0; r < n_runs; ++r) {
+        size_t po, vo;
+        const Lattice Lr = run_lattice(s, r, &po, &vo);
+        launch_init_fluid(s->prec, Lr, (char *)s->pop[0] + po, 0, 0.0, s->stream);
+    }
+    return finish_create(s, out);
 }
 
 int iblbm_destroy(iblbm_sim *s) {
@@ -602,6 +780,8 @@ int iblbm_destroy(iblbm_sim *s) {
     }
     dev_free(s, s->d_status);
     dev_free(s, s->d_scratch);
+    dev_free(s, s->d_runs);
+    dev_free(s, s->d_items);
     free_ring(s);
     for (void *p : s->mesh_allocs) dev_free(s, p);
     for (void *p : s->plan_allocs) dev_free(s, p);
@@ -627,6 +807,7 @@ int iblbm_get_info(const iblbm_sim *s, iblbm_info *out) {
     out->n_nodes = (int)(s->X0.size() / 3);
     out->n_faces = (int)(s->tri.size() / 3);
     out->step = s->steps;
+    out->n_runs = s->batch ? (int)s->runs.size() : 1;
     out->tau = s->tau;
     out->u_wall = s->u_wall;
     return IBLBM_OK;
@@ -638,6 +819,13 @@ int iblbm_set_shear_walls(iblbm_sim *s, double u_wall) {
         return fail(s, IBLBM_ERR_ARG, "wall speed must be finite and |u_wall| <= 0.3");
     s->u_wall = u_wall;
     drop_graphs(s);
+    if (s->batch) {  // every run of a batch
+        for (RunDesc &R : s->runs) R.u_wall = u_wall;
+        CK(cudaSetDevice(s->device));
+        join_side(s);
+        CK(cudaStreamSynchronize(s->stream));
+        return upload_batch_tables(s);
+    }
     return IBLBM_OK;
 }
 
@@ -650,7 +838,7 @@ int iblbm_add_capsule_icosphere(iblbm_sim *s, double cx, double cy, double cz, d
     std::vector<int> tri;
     const double c[3] = {cx, cy, cz};
     icosphere(subdivisions, radius, c, nodes, tri);
-    return add_capsule(s, nodes.data(), (int)(nodes.size() / 3), tri.data(), (int)(tri.size() / 3),
+    return add_capsule(s, 0, nodes.data(), (int)(nodes.size() / 3), tri.data(), (int)(tri.size() / 3),
                        capsule_id);
 }
 
@@ -670,7 +858,7 @@ int iblbm_icosphere(int subdivisions, double radius, const double center[3], dou
 int iblbm_add_capsule_mesh(iblbm_sim *s, const double *ref_xyz, int n_nodes, const int32_t *tri,
                            int n_tri, int *capsule_id) {
     if (!s) return IBLBM_ERR_ARG;
-    return add_capsule(s, ref_xyz, n_nodes, (const int *)tri, n_tri, capsule_id);
+    return add_capsule(s, 0, ref_xyz, n_nodes, (const int *)tri, n_tri, capsule_id);
 }
 
 int iblbm_set_skalak(iblbm_sim *s, int capsule_id, double k_s, double C) {
@@ -711,11 +899,18 @@ int iblbm_init_fluid(iblbm_sim *s, int mode) {
     if (!s) return IBLBM_ERR_ARG;
     if (mode != 0 && mode != 1) return fail(s, IBLBM_ERR_ARG, "mode must be 0 or 1");
     CK(cudaSetDevice(s->device));
+    join_side(s);
     s->cur = 0;
-    launch_init_fluid(s->prec, s->L, s->pop[0], mode, s->u_wall, s->stream);
+    const int nr = s->batch ? (int)s->runs.size() : 1;
+    for (int r = 0; r < nr; ++r) {
+        size_t po, vo;
+        const Lattice Lr = run_lattice(s, r, &po, &vo);
+        const double uw = s->batch ? s->runs[r].u_wall : s->u_wall;
+        launch_init_fluid(s->prec, Lr, (char *)s->pop[0] + po, mode, uw, s->stream);
+    }
     for (int k = 0; k < 2; ++k) {
         CK(cudaMemsetAsync(s->force[k], 0, s->vec_bytes, s->stream));
-        CK(cudaMemsetAsync(s->flags[k], 0, (size_t)s->L.ntiles, s->stream));
+        CK(cudaMemsetAsync(s->flags[k], 0, s->flag_bytes, s->stream));
     }
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s->stream));
@@ -864,76 +1059,196 @@ int iblbm_sync(iblbm_sim *s) {
     return sync_status(s);
 }
 
-int iblbm_get_velocity(iblbm_sim *s, double *host_out) {
-    if (!s || !host_out) return IBLBM_ERR_ARG;
-    int rc = sync_status(s);
-    if (rc) return rc;
-    const size_t n = (size_t)s->L.ncell;
-    rc = ensure_scratch(s, sizeof(double) * 3 * n);
-    if (rc) return rc;
-    launch_moments(s->prec, s->L, s->pop[s->cur], s->force[s->cur], nullptr, s->d_scratch, s->stream);
-    CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(host_out, s->d_scratch, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s->stream));
-    CK(cudaStreamSynchronize(s->stream));
+}  // extern "C"
+
+namespace {
+
+int check_run(iblbm_sim *s, int run) {
+    if (run < 0 || run >= (s->batch ? (int)s->runs.size() : 1)) return fail(s, IBLBM_ERR_ARG, "no such run");
     return IBLBM_OK;
 }
 
-int iblbm_get_density(iblbm_sim *s, double *host_out) {
+// what: 0 velocity [3][cells], 1 density [cells], 2 populations [19][cells],
+// 3 force density [3][cells]
+int lattice_get(iblbm_sim *s, int run, int what, double *host_out) {
     if (!s || !host_out) return IBLBM_ERR_ARG;
-    int rc = sync_status(s);
+    int rc = check_run(s, run);
     if (rc) return rc;
-    const size_t n = (size_t)s->L.ncell;
+    rc = sync_status(s);
+    if (rc) return rc;
+    size_t po, vo;
+    const Lattice Lr = run_lattice(s, run, &po, &vo);
+    const size_t per = (what == 1) ? 1 : (what == 2 ? 19 : 3);
+    const size_t n = per * (size_t)Lr.ncell;
     rc = ensure_scratch(s, sizeof(double) * n);
     if (rc) return rc;
-    launch_moments(s->prec, s->L, s->pop[s->cur], s->force[s->cur], s->d_scratch, nullptr, s->stream);
+    const void *pop = (const char *)s->pop[s->cur] + po;
+    const void *force = (const char *)s->force[s->cur] + vo;
+    if (what == 0) launch_moments(s->prec, Lr, pop, force, nullptr, s->d_scratch, s->stream);
+    else if (what == 1) launch_moments(s->prec, Lr, pop, force, s->d_scratch, nullptr, s->stream);
+    else if (what == 2) launch_pop_to_f64(s->prec, Lr, pop, s->d_scratch, s->stream);
+    else launch_force_to_f64(s->prec, Lr, force, s->d_scratch, s->stream);
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(host_out, s->d_scratch, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     return IBLBM_OK;
 }
 
-int iblbm_get_populations(iblbm_sim *s, double *host_out) {
-    if (!s || !host_out) return IBLBM_ERR_ARG;
-    int rc = sync_status(s);
-    if (rc) return rc;
-    const size_t n = 19 * (size_t)s->L.ncell;
-    rc = ensure_scratch(s, sizeof(double) * n);
-    if (rc) return rc;
-    launch_pop_to_f64(s->prec, s->L, s->pop[s->cur], s->d_scratch, s->stream);
-    CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(host_out, s->d_scratch, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
-    CK(cudaStreamSynchronize(s->stream));
-    return IBLBM_OK;
-}
-
-int iblbm_set_populations(iblbm_sim *s, const double *host_in) {
+int lattice_set_populations(iblbm_sim *s, int run, const double *host_in) {
     if (!s || !host_in) return IBLBM_ERR_ARG;
-    int rc = sync_status(s);
+    int rc = check_run(s, run);
     if (rc) return rc;
-    const size_t n = 19 * (size_t)s->L.ncell;
+    rc = sync_status(s);
+    if (rc) return rc;
+    size_t po, vo;
+    const Lattice Lr = run_lattice(s, run, &po, &vo);
+    const size_t n = 19 * (size_t)Lr.ncell;
     for (size_t k = 0; k < n; ++k)
         if (!std::isfinite(host_in[k])) return fail(s, IBLBM_ERR_ARG, "non-finite population");
     rc = ensure_scratch(s, sizeof(double) * n);
     if (rc) return rc;
     CK(cudaMemcpyAsync(s->d_scratch, host_in, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
-    launch_f64_to_pop(s->prec, s->L, s->d_scratch, s->pop[s->cur], s->stream);
+    launch_f64_to_pop(s->prec, Lr, s->d_scratch, (char *)s->pop[s->cur] + po, s->stream);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s->stream));
     return IBLBM_OK;
 }
 
-int iblbm_get_force_field(iblbm_sim *s, double *host_out) {
-    if (!s || !host_out) return IBLBM_ERR_ARG;
-    int rc = sync_status(s);
-    if (rc) return rc;
-    const size_t n = (size_t)s->L.ncell;
-    rc = ensure_scratch(s, sizeof(double) * 3 * n);
-    if (rc) return rc;
-    launch_force_to_f64(s->prec, s->L, s->force[s->cur], s->d_scratch, s->stream);
-    CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(host_out, s->d_scratch, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s->stream));
-    CK(cudaStreamSynchronize(s->stream));
+int whole_lattice_only(iblbm_sim *s) {
+    if (s && s->batch && s->runs.size() > 1)
+        return fail(s, IBLBM_ERR_STATE, "a batch of several runs: use the per-run getter");
     return IBLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int iblbm_get_velocity(iblbm_sim *s, double *out) {
+    int rc = whole_lattice_only(s);
+    return rc ? rc : lattice_get(s, 0, 0, out);
+}
+int iblbm_get_density(iblbm_sim *s, double *out) {
+    int rc = whole_lattice_only(s);
+    return rc ? rc : lattice_get(s, 0, 1, out);
+}
+int iblbm_get_populations(iblbm_sim *s, double *out) {
+    int rc = whole_lattice_only(s);
+    return rc ? rc : lattice_get(s, 0, 2, out);
+}
+int iblbm_get_force_field(iblbm_sim *s, double *out) {
+    int rc = whole_lattice_only(s);
+    return rc ? rc : lattice_get(s, 0, 3, out);
+}
+int iblbm_set_populations(iblbm_sim *s, const double *in) {
+    int rc = whole_lattice_only(s);
+    return rc ? rc : lattice_set_populations(s, 0, in);
+}
+int iblbm_get_run_velocity(iblbm_sim *s, int run, double *out) { return lattice_get(s, run, 0, out); }
+int iblbm_get_run_populations(iblbm_sim *s, int run, double *out) { return lattice_get(s, run, 2, out); }
+int iblbm_set_run_populations(iblbm_sim *s, int run, const double *in) {
+    return lattice_set_populations(s, run, in);
+}
+
+int iblbm_add_capsule_icosphere_in_run(iblbm_sim *s, int run, double cx, double cy, double cz,
+                                       double radius, int subdivisions, int *capsule_id) {
+    if (!s) return IBLBM_ERR_ARG;
+    if (subdivisions < 0 || subdivisions > 7 || !(radius > 0.0) || !std::isfinite(radius))
+        return fail(s, IBLBM_ERR_ARG, "subdivisions must be 0..7 and radius positive");
+    std::vector<double> nodes;
+    std::vector<int> tri;
+    const double c[3] = {cx, cy, cz};
+    icosphere(subdivisions, radius, c, nodes, tri);
+    return add_capsule(s, run, nodes.data(), (int)(nodes.size() / 3), tri.data(), (int)(tri.size() / 3),
+                       capsule_id);
+}
+
+int iblbm_get_run_tile(const iblbm_sim *s, int run, int *tx, int *ty) {
+    if (!s || !tx || !ty) return IBLBM_ERR_ARG;
+    if (!s->batch) {
+        *tx = s->L.ftx;
+        *ty = s->L.fty;
+        return run == 0 ? IBLBM_OK : IBLBM_ERR_ARG;
+    }
+    if (run < 0 || run >= (int)s->runs.size()) return IBLBM_ERR_ARG;
+    *tx = s->runs[run].tx;
+    *ty = s->runs[run].ty;
+    return IBLBM_OK;
+}
+
+int iblbm_autotune_tiles(iblbm_sim *s, int repeats) {
+    if (!s || repeats < 1 || repeats > 1000) return IBLBM_ERR_ARG;
+    if (!s->batch) return IBLBM_OK;  // a single lattice has fixed kernels
+    if (s->steps != 0) return fail(s, IBLBM_ERR_STATE, "tile autotuning must precede the first step");
+    CK(cudaSetDevice(s->device));
+    join_side(s);
+    CK(cudaStreamSynchronize(s->stream));
+    // distinct box sizes
+    std::vector<std::array<int, 3>> sizes;
+    for (const RunDesc &R : s->runs) {
+        std::array<int, 3> k = {R.nx, R.ny, R.nz};
+        if (std::find(sizes.begin(), sizes.end(), k) == sizes.end()) sizes.push_back(k);
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const std::vector<RunDesc> saved = s->runs;
+    std::vector<int> best_shape(sizes.size(), 0);
+    for (size_t z = 0; z < sizes.size(); ++z) {
+        float best = 1e30f;
+        for (int c = 0; c < 6; ++c) {
+            // only the runs of this size, all with candidate shape c
+            s->runs = saved;
+            std::vector<int> keep;
+            for (size_t r = 0; r < s->runs.size(); ++r) {
+                RunDesc &R = s->runs[r];
+                R.tx = kTileShapes[c][0];
+                R.ty = kTileShapes[c][1];
+                if (R.nx == sizes[z][0] && R.ny == sizes[z][1] && R.nz == sizes[z][2]) keep.push_back((int)r);
+            }
+            int rc = upload_batch_tables(s);
+            if (rc) break;
+            std::vector<int2> items;
+            for (int r : keep) {
+                const RunDesc &R = s->runs[r];
+                const int nt = R.ntx * R.nty * R.nz;
+                for (int t = 0; t < nt; ++t) items.push_back(make_int2(r, t));
+            }
+            CK(cudaMemcpy(s->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
+            BatchArgs b{s->d_runs, s->d_items, (int)items.size(),
+                        std::min(s->batch_grid, (int)items.size())};
+            CollideArgs a{};
+            a.src = s->pop[s->cur];
+            a.dst = s->pop[1 - s->cur];  // overwritten by the next step
+            a.fcur = s->force[1 - s->cur];
+            a.flag_cur = s->flags[1 - s->cur];  // all zero before the first step
+            a.fold = s->force[s->cur];
+            a.flag_old = s->flags[s->cur];
+            a.status = s->d_status;
+            launch_collide_batch(s->prec, b, a, s->stream);  // warm-up
+            CK(cudaEventRecord(e0, s->stream));
+            for (int k = 0; k < repeats; ++k) launch_collide_batch(s->prec, b, a, s->stream);
+            CK(cudaEventRecord(e1, s->stream));
+            CK(cudaEventSynchronize(e1));
+            CK(cudaGetLastError());
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                best_shape[z] = c;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    s->runs = saved;
+    for (RunDesc &R : s->runs)
+        for (size_t z = 0; z < sizes.size(); ++z)
+            if (R.nx == sizes[z][0] && R.ny == sizes[z][1] && R.nz == sizes[z][2]) {
+                R.tx = kTileShapes[best_shape[z]][0];
+                R.ty = kTileShapes[best_shape[z]][1];
+            }
+    return upload_batch_tables(s);
 }
 
 static int node_get(iblbm_sim *s, int id, int which, double *host_out) {

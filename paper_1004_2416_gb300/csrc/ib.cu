@@ -164,12 +164,14 @@ __global__ void __launch_bounds__(256)
                    const typename Vec4<T>::type *__restrict__ fconst,
                    const typename Vec4<T>::type *__restrict__ capmod,
                    typename Vec4<T>::type *__restrict__ nodeF,
-                   typename Vec4<T>::type *__restrict__ force, uint8_t *__restrict__ flags, int nx,
-                   int ny, int nz, int ftx, int fty, int nfx, int nfy, int *status) {
+                   typename Vec4<T>::type *__restrict__ force, uint8_t *__restrict__ flags,
+                   RunDesc single, const RunDesc *__restrict__ runs,
+                   const int *__restrict__ node_run, int *status) {
     using V4 = typename Vec4<T>::type;
     const int lane = threadIdx.x & 31;
     const int node = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
     if (node >= n_nodes) return;
+    const RunDesc R = runs ? runs[node_run[node]] : single;
 
     T fx = T(0), fy = T(0), fz = T(0);
     const int e0 = adj_off[node], e1 = adj_off[node + 1];
@@ -223,7 +225,7 @@ __global__ void __launch_bounds__(256)
     for (int k = lane; k < NC; k += 32) {
         const int kx = k % N, ky = (k / N) % N, kz = k / (N * N);
         const int X = bx + kx, Y = by + ky, Z = bz + kz;
-        if (Z < 0 || Z >= nz) {
+        if (Z < 0 || Z >= R.nz) {
             set_status(status, kStatusStencil);
             continue;
         }
@@ -231,10 +233,10 @@ __global__ void __launch_bounds__(256)
         pos.rel(p, X, Y, Z, d);
         const T w = delta_phi<N>(d[0]) * delta_phi<N>(d[1]) * delta_phi<N>(d[2]);
         if (w == T(0)) continue;
-        const int xw = wrap_index(X, nx), yw = wrap_index(Y, ny);
-        const long long cell = xw + (long long)nx * (yw + (long long)ny * Z);
-        add_force(&force[cell], w * fx, w * fy, w * fz);
-        flags[((long long)Z * nfy + yw / fty) * nfx + xw / ftx] = 1;
+        const int xw = wrap_index(X, R.nx), yw = wrap_index(Y, R.ny);
+        const long long cell = xw + (long long)R.nx * (yw + (long long)R.ny * Z);
+        add_force(&force[R.cell_off + cell], w * fx, w * fy, w * fz);
+        flags[R.tile_off + ((long long)Z * R.nty + yw / R.ty) * R.ntx + xw / R.tx] = 1;
     }
 }
 
@@ -242,12 +244,17 @@ template <int N, typename S, typename T>
 __global__ void __launch_bounds__(256)
     k_interp_advect(int n_nodes, PosView<T> pos, const S *__restrict__ pop,
                     const typename Vec4<T>::type *__restrict__ force,
-                    typename Vec4<T>::type *__restrict__ nodeU, int nx, int ny, int nz,
-                    long long ncell) {
+                    typename Vec4<T>::type *__restrict__ nodeU, RunDesc single,
+                    const RunDesc *__restrict__ runs, const int *__restrict__ node_run) {
     using V4 = typename Vec4<T>::type;
     const int lane = threadIdx.x & 31;
     const int node = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
     if (node >= n_nodes) return;
+    const RunDesc R = runs ? runs[node_run[node]] : single;
+    const int nx = R.nx, ny = R.ny, nz = R.nz;
+    const long long ncell = R.ncell;
+    pop += 19 * R.cell_off;
+    force += R.cell_off;
     T p[kPosLen<T>];
     pos.approx(node, p);
     T pc[3];
@@ -369,56 +376,73 @@ PosView<float> view<float>(const MeshDev &m) {
 
 constexpr int kNodesPerBlock = 8;  // 8 warps of 32
 
+// The single lattice as a run descriptor (its force flags are the lattice's).
+static RunDesc single_run(const Lattice &L) {
+    RunDesc R{};
+    R.nx = L.nx;
+    R.ny = L.ny;
+    R.nz = L.nz;
+    R.tx = L.ftx;
+    R.ty = L.fty;
+    R.ntx = L.nfx;
+    R.nty = L.nfy;
+    R.ncell = L.ncell;
+    return R;
+}
+
 template <int N, typename T>
 static void force_spread_impl(const Lattice &L, const MeshDev &m, void *force, uint8_t *flags,
-                              int *status, cudaStream_t s) {
+                              int *status, const RunDesc *runs, const int *node_run,
+                              cudaStream_t s) {
     using V4 = typename Vec4<T>::type;
     unsigned nb = (unsigned)((m.n_nodes + kNodesPerBlock - 1) / kNodesPerBlock);
     k_force_spread<N, T><<<nb, 32 * kNodesPerBlock, 0, s>>>(
         m.n_nodes, view<T>(m), m.adj_off, m.adj, (const int4 *)m.tri, (const V4 *)m.fconst,
-        (const V4 *)m.capmod, (V4 *)m.F, (V4 *)force, flags, L.nx, L.ny, L.nz,
-        L.ftx, L.fty, L.nfx, L.nfy, status);
+        (const V4 *)m.capmod, (V4 *)m.F, (V4 *)force, flags, single_run(L), runs, node_run,
+        status);
 }
 
 template <int N, typename S, typename T>
 static void interp_impl(const Lattice &L, const MeshDev &m, const void *pop, const void *force,
-                        cudaStream_t s) {
+                        const RunDesc *runs, const int *node_run, cudaStream_t s) {
     using V4 = typename Vec4<T>::type;
     unsigned nb = (unsigned)((m.n_nodes + kNodesPerBlock - 1) / kNodesPerBlock);
     k_interp_advect<N, S, T><<<nb, 32 * kNodesPerBlock, 0, s>>>(
-        m.n_nodes, view<T>(m), (const S *)pop, (const V4 *)force, (V4 *)m.u, L.nx, L.ny, L.nz,
-        L.ncell);
+        m.n_nodes, view<T>(m), (const S *)pop, (const V4 *)force, (V4 *)m.u, single_run(L), runs,
+        node_run);
 }
 
 void launch_force_spread(int prec, int delta, const Lattice &L, const MeshDev &m, void *force,
-                         uint8_t *flags, int *status, cudaStream_t s) {
+                         uint8_t *flags, int *status, const RunDesc *runs, const int *node_run,
+                         cudaStream_t s) {
     if (m.n_nodes == 0) return;
     if (prec == kF64) {
-        if (delta == 2) force_spread_impl<2, double>(L, m, force, flags, status, s);
-        else if (delta == 3) force_spread_impl<3, double>(L, m, force, flags, status, s);
-        else force_spread_impl<4, double>(L, m, force, flags, status, s);
+        if (delta == 2) force_spread_impl<2, double>(L, m, force, flags, status, runs, node_run, s);
+        else if (delta == 3) force_spread_impl<3, double>(L, m, force, flags, status, runs, node_run, s);
+        else force_spread_impl<4, double>(L, m, force, flags, status, runs, node_run, s);
     } else {
-        if (delta == 2) force_spread_impl<2, float>(L, m, force, flags, status, s);
-        else if (delta == 3) force_spread_impl<3, float>(L, m, force, flags, status, s);
-        else force_spread_impl<4, float>(L, m, force, flags, status, s);
+        if (delta == 2) force_spread_impl<2, float>(L, m, force, flags, status, runs, node_run, s);
+        else if (delta == 3) force_spread_impl<3, float>(L, m, force, flags, status, runs, node_run, s);
+        else force_spread_impl<4, float>(L, m, force, flags, status, runs, node_run, s);
     }
 }
 
 void launch_interp_advect(int prec, int delta, const Lattice &L, const MeshDev &m, const void *pop,
-                          const void *force, cudaStream_t s) {
+                          const void *force, const RunDesc *runs, const int *node_run,
+                          cudaStream_t s) {
     if (m.n_nodes == 0) return;
     if (prec == kF64) {
-        if (delta == 2) interp_impl<2, double, double>(L, m, pop, force, s);
-        else if (delta == 3) interp_impl<3, double, double>(L, m, pop, force, s);
-        else interp_impl<4, double, double>(L, m, pop, force, s);
+        if (delta == 2) interp_impl<2, double, double>(L, m, pop, force, runs, node_run, s);
+        else if (delta == 3) interp_impl<3, double, double>(L, m, pop, force, runs, node_run, s);
+        else interp_impl<4, double, double>(L, m, pop, force, runs, node_run, s);
     } else if (prec == kF32) {
-        if (delta == 2) interp_impl<2, float, float>(L, m, pop, force, s);
-        else if (delta == 3) interp_impl<3, float, float>(L, m, pop, force, s);
-        else interp_impl<4, float, float>(L, m, pop, force, s);
+        if (delta == 2) interp_impl<2, float, float>(L, m, pop, force, runs, node_run, s);
+        else if (delta == 3) interp_impl<3, float, float>(L, m, pop, force, runs, node_run, s);
+        else interp_impl<4, float, float>(L, m, pop, force, runs, node_run, s);
     } else {
-        if (delta == 2) interp_impl<2, __half, float>(L, m, pop, force, s);
-        else if (delta == 3) interp_impl<3, __half, float>(L, m, pop, force, s);
-        else interp_impl<4, __half, float>(L, m, pop, force, s);
+        if (delta == 2) interp_impl<2, __half, float>(L, m, pop, force, runs, node_run, s);
+        else if (delta == 3) interp_impl<3, __half, float>(L, m, pop, force, runs, node_run, s);
+        else interp_impl<4, __half, float>(L, m, pop, force, runs, node_run, s);
     }
 }
 

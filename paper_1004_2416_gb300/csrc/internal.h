@@ -52,6 +52,27 @@ inline Lattice make_lattice(int nx, int ny, int nz, bool vec) {
 
 enum Prec { kF64 = 0, kF32 = 1, kF16 = 2 };
 
+// One lattice of a batch of independent runs (a single simulation is a batch
+// of one run for the IB kernels).  The runs' cells, force vectors and
+// populations are concatenated: populations of run r start at 19 * cell_off
+// ([19][ncell] within the run), its force vectors at cell_off, its force flags
+// at tile_off.  Tiles (= force flag tiles) are tx x ty x 1 cells.
+struct RunDesc {
+    int nx, ny, nz;
+    int tx, ty;    // tile shape
+    int ntx, nty;  // tiles along x and y
+    int pad;
+    long long cell_off, tile_off, ncell;
+    double omega, u_wall;
+};
+
+struct BatchArgs {
+    const RunDesc *runs;   // device [n_runs]
+    const int2 *items;     // device [n_items]: (run, tile within the run)
+    int n_items;
+    int grid;              // persistent grid size
+};
+
 // Device views of the membrane data, all capsules concatenated.
 struct MeshDev {
     int n_nodes;
@@ -83,6 +104,9 @@ struct CollideArgs {
     int *status;
 };
 void launch_collide_stream(int prec, const Lattice &L, const CollideArgs &a, cudaStream_t s);
+// batched persistent variant: CollideArgs pointers are the concatenated buffers
+void launch_collide_batch(int prec, const BatchArgs &b, const CollideArgs &a, cudaStream_t s);
+int collide_batch_blocks_per_sm(int prec);
 // mode 0: rest; mode 1: linear Couette equilibrium
 void launch_init_fluid(int prec, const Lattice &L, void *pop, int mode, double u_wall, cudaStream_t s);
 // rho [ncell] and u [3][ncell] in double from populations + half the force
@@ -93,10 +117,14 @@ void launch_f64_to_pop(int prec, const Lattice &L, const double *in, void *pop, 
 void launch_force_to_f64(int prec, const Lattice &L, const void *force, double *out, cudaStream_t s);
 
 // ---- ib.cu ----------------------------------------------------------------------
+// runs / node_run: device run table and per-node run index of a batch, or
+// null for a single lattice described by L.
 void launch_force_spread(int prec, int delta, const Lattice &L, const MeshDev &m, void *force,
-                         uint8_t *flags, int *status, cudaStream_t s);
+                         uint8_t *flags, int *status, const RunDesc *runs, const int *node_run,
+                         cudaStream_t s);
 void launch_interp_advect(int prec, int delta, const Lattice &L, const MeshDev &m, const void *pop,
-                          const void *force, cudaStream_t s);
+                          const void *force, const RunDesc *runs, const int *node_run,
+                          cudaStream_t s);
 // node data <-> host doubles [n][3]
 void launch_nodes_to_f64(int prec, const MeshDev &m, int which, int first, int count, double *out,
                          cudaStream_t s);

@@ -15,38 +15,20 @@
 
 namespace iblbm {
 
-// One thread per cell, one 32 x 8 x 1 tile per block.  Reads 19 coalesced
-// values of f(t) at its own cell, collides, and pushes each post-collision
-// value to the neighbour cell x + c_i (periodic in x and y).  A value that
-// would cross a wall plane is reflected into the opposite direction of the
-// same cell with Ladd's moving-wall term -2 w_i (c_i . u_w) / c_s^2.
+// Collide-and-stream of one cell (x, y, z) of an nx x ny x nz lattice whose
+// populations start at src / dst and force density at fcur.  Reads the 19
+// values of f(t) at the cell, collides, and pushes each post-collision value to
+// the neighbour cell x + c_i (periodic in x and y).  A value that would cross
+// a wall plane is reflected into the opposite direction of the same cell with
+// Ladd's moving-wall term -2 w_i (c_i . u_w) / c_s^2.
 template <typename S, typename T>
-__global__ void __launch_bounds__(kTileX *kTileY)
-    k_collide_stream(const S *__restrict__ src, S *__restrict__ dst,
-                     const typename Vec4<T>::type *__restrict__ fcur,
-                     const uint8_t *__restrict__ flag_cur,
-                     typename Vec4<T>::type *__restrict__ fold, uint8_t *__restrict__ flag_old,
-                     int nx, int ny, int nz, int ntx, int nty, long long ncell, T omega,
-                     T u_wall, int *status) {
+__device__ __forceinline__ void collide_cell(const S *__restrict__ src, S *__restrict__ dst,
+                                             const typename Vec4<T>::type *__restrict__ fcur,
+                                             bool has_cur, int x, int y, int z, int nx, int ny,
+                                             int nz, long long ncell, T omega, T u_wall,
+                                             int *status) {
     using V4 = typename Vec4<T>::type;
-    const int x = blockIdx.x * kTileX + threadIdx.x;
-    const int y = blockIdx.y * kTileY + threadIdx.y;
-    const int z = blockIdx.z;
-    const long long tile = ((long long)z * nty + blockIdx.y) * ntx + blockIdx.x;
-    const bool inside = (x < nx) && (y < ny);
     const long long cell = x + (long long)nx * (y + (long long)ny * z);
-
-    // Block-uniform flags.  The previous step's force tiles are cleared here:
-    // nothing reads them after the interpolation of the previous step.
-    const bool has_old = flag_old[tile] != 0;
-    const bool has_cur = flag_cur[tile] != 0;
-    if (has_old) {
-        if (inside) fold[cell] = V4{};
-        __syncthreads();
-        if (threadIdx.x == 0 && threadIdx.y == 0) flag_old[tile] = 0;
-    }
-    if (!inside) return;
-
     T g[19];
 #pragma unroll
     for (int i = 0; i < 19; ++i) g[i] = Store<S, T>::load(src + i * ncell + cell);
@@ -112,6 +94,74 @@ __global__ void __launch_bounds__(kTileX *kTileY)
             const long long t = xt + (long long)nx * (yt + (long long)ny * zt);
             Store<S, T>::store(dst + i * ncell + t, post);
         }
+    }
+}
+
+// One thread per cell, one 32 x 8 x 1 tile per block.
+template <typename S, typename T>
+__global__ void __launch_bounds__(kTileX *kTileY)
+    k_collide_stream(const S *__restrict__ src, S *__restrict__ dst,
+                     const typename Vec4<T>::type *__restrict__ fcur,
+                     const uint8_t *__restrict__ flag_cur,
+                     typename Vec4<T>::type *__restrict__ fold, uint8_t *__restrict__ flag_old,
+                     int nx, int ny, int nz, int ntx, int nty, long long ncell, T omega,
+                     T u_wall, int *status) {
+    using V4 = typename Vec4<T>::type;
+    const int x = blockIdx.x * kTileX + threadIdx.x;
+    const int y = blockIdx.y * kTileY + threadIdx.y;
+    const int z = blockIdx.z;
+    const long long tile = ((long long)z * nty + blockIdx.y) * ntx + blockIdx.x;
+    const bool inside = (x < nx) && (y < ny);
+    const long long cell = x + (long long)nx * (y + (long long)ny * z);
+
+    // Block-uniform flags.  The previous step's force tiles are cleared here:
+    // nothing reads them after the interpolation of the previous step.
+    const bool has_old = flag_old[tile] != 0;
+    const bool has_cur = flag_cur[tile] != 0;
+    if (has_old) {
+        if (inside) fold[cell] = V4{};
+        __syncthreads();
+        if (threadIdx.x == 0 && threadIdx.y == 0) flag_old[tile] = 0;
+    }
+    if (!inside) return;
+    collide_cell<S, T>(src, dst, fcur, has_cur, x, y, z, nx, ny, nz, ncell, omega, u_wall, status);
+}
+
+// Batched, persistent collide-and-stream over many independent lattices
+// (runs).  The work list holds (run, tile) pairs of every run; each block
+// walks it with a grid stride.  A run's tiles have its own shape tx x ty
+// (tx * ty = 256 threads), picked per box size by the autotuner; the force
+// flags of a run use the same tiles.
+template <typename S, typename T>
+__global__ void __launch_bounds__(256)
+    k_collide_batch(const S *__restrict__ src, S *__restrict__ dst,
+                    const typename Vec4<T>::type *__restrict__ fcur,
+                    const uint8_t *__restrict__ flag_cur,
+                    typename Vec4<T>::type *__restrict__ fold, uint8_t *__restrict__ flag_old,
+                    const RunDesc *__restrict__ runs, const int2 *__restrict__ items, int n_items,
+                    int *status) {
+    using V4 = typename Vec4<T>::type;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int2 w = items[it];
+        const RunDesc R = runs[w.x];
+        const int per_z = R.ntx * R.nty;
+        const int z = w.y / per_z, rem = w.y - z * per_z;
+        const int tyi = rem / R.ntx, txi = rem - tyi * R.ntx;
+        const int x = txi * R.tx + (int)threadIdx.x % R.tx;
+        const int y = tyi * R.ty + (int)threadIdx.x / R.tx;
+        const bool inside = x < R.nx && y < R.ny;
+        const long long tile = R.tile_off + w.y;
+        const bool has_old = flag_old[tile] != 0;
+        const bool has_cur = flag_cur[tile] != 0;
+        if (has_old) {
+            if (inside) fold[R.cell_off + x + (long long)R.nx * (y + (long long)R.ny * z)] = V4{};
+            __syncthreads();
+            if (threadIdx.x == 0) flag_old[tile] = 0;
+        }
+        if (inside)
+            collide_cell<S, T>(src + 19 * R.cell_off, dst + 19 * R.cell_off, fcur + R.cell_off,
+                               has_cur, x, y, z, R.nx, R.ny, R.nz, R.ncell, (T)R.omega,
+                               (T)R.u_wall, status);
     }
 }
 
@@ -421,6 +471,34 @@ void launch_collide_stream(int prec, const Lattice &L, const CollideArgs &a, cud
     } else {
         if (!collide_vec<__half>(L, a, s)) collide_impl<__half, float>(L, a, s);
     }
+}
+
+template <typename S, typename T>
+static void collide_batch_impl(const BatchArgs &b, const CollideArgs &a, cudaStream_t s) {
+    using V4 = typename Vec4<T>::type;
+    k_collide_batch<S, T><<<b.grid, 256, 0, s>>>(
+        (const S *)a.src, (S *)a.dst, (const V4 *)a.fcur, a.flag_cur, (V4 *)a.fold, a.flag_old,
+        b.runs, b.items, b.n_items, a.status);
+}
+
+void launch_collide_batch(int prec, const BatchArgs &b, const CollideArgs &a, cudaStream_t s) {
+    if (b.n_items == 0) return;
+    if (prec == kF64) collide_batch_impl<double, double>(b, a, s);
+    else if (prec == kF32) collide_batch_impl<float, float>(b, a, s);
+    else collide_batch_impl<__half, float>(b, a, s);
+}
+
+int collide_batch_blocks_per_sm(int prec) {
+    int n = 0;
+    cudaError_t e;
+    if (prec == kF64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide_batch<double, double>, 256, 0);
+    else if (prec == kF32) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide_batch<float, float>, 256, 0);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide_batch<__half, float>, 256, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n > 0 ? n : 1;
 }
 
 void launch_init_fluid(int prec, const Lattice &L, void *pop, int mode, double u_wall,

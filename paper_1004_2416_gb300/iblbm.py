@@ -59,7 +59,12 @@ class iblbm_allocator(ctypes.Structure):
 class iblbm_info(ctypes.Structure):
     _fields_ = [("nx", _int), ("ny", _int), ("nz", _int), ("precision", _int),
                 ("delta_points", _int), ("n_capsules", _int), ("n_nodes", _int),
-                ("n_faces", _int), ("step", ctypes.c_int64), ("tau", _dbl), ("u_wall", _dbl)]
+                ("n_faces", _int), ("step", ctypes.c_int64), ("tau", _dbl), ("u_wall", _dbl),
+                ("n_runs", _int)]
+
+
+class iblbm_run_spec(ctypes.Structure):
+    _fields_ = [("nx", _int), ("ny", _int), ("nz", _int), ("tau", _dbl), ("u_wall", _dbl)]
 
 
 _SIGS = {
@@ -92,6 +97,14 @@ _SIGS = {
     "iblbm_get_taylor_records": (_int, [_vp, _int, _int, _dp, ctypes.POINTER(ctypes.c_int64), _ip]),
     "iblbm_profile_kernels": (_int, [_vp, _int, _dp]),
     "iblbm_taylor_sums_noalloc": (_int, [_vp, _int, _vp, _int, _dp, _vp, _vp]),
+    "iblbm_create_batch": (_int, [ctypes.POINTER(_vp), ctypes.POINTER(iblbm_run_spec), _int, _int, _int,
+                                  _vp, ctypes.POINTER(iblbm_allocator)]),
+    "iblbm_add_capsule_icosphere_in_run": (_int, [_vp, _int, _dbl, _dbl, _dbl, _dbl, _int, _ip]),
+    "iblbm_autotune_tiles": (_int, [_vp, _int]),
+    "iblbm_get_run_tile": (_int, [_vp, _int, _ip, _ip]),
+    "iblbm_get_run_velocity": (_int, [_vp, _int, _dp]),
+    "iblbm_get_run_populations": (_int, [_vp, _int, _dp]),
+    "iblbm_set_run_populations": (_int, [_vp, _int, _dp]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -177,6 +190,59 @@ class Sim:
         self.shape = (nx, ny, nz)
         self.ncell = nx * ny * nz
         self._ncaps = 0
+
+    @classmethod
+    def batch(cls, runs, precision="fp32", delta_points: int = 3, stream=None):
+        """Batch of independent lattices; runs = [(nx, ny, nz, tau, u_wall), ...]."""
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        arr = (iblbm_run_spec * len(runs))(*[iblbm_run_spec(int(a), int(b), int(c), float(t), float(u))
+                                             for a, b, c, t, u in runs])
+        h = _vp()
+        rc = iblbm_create_batch(ctypes.byref(h), arr, len(runs), prec, delta_points,
+                                _stream_handle(stream), None)
+        if rc != IBLBM_OK:
+            raise IblbmError(rc, iblbm_last_error(None).decode(errors="replace"))
+        self = cls.__new__(cls)
+        self._keep = None
+        self._h = h
+        self.runs = [tuple(r[:3]) for r in runs]
+        self.shape = self.runs[0]
+        self.ncell = sum(a * b * c for a, b, c in self.runs)
+        self._ncaps = 0
+        return self
+
+    def add_capsule_icosphere_in_run(self, run: int, center, radius: float, subdivisions: int) -> int:
+        cid = _int()
+        _check(iblbm_add_capsule_icosphere_in_run(self._h, run, *map(float, center), float(radius),
+                                                  int(subdivisions), ctypes.byref(cid)), self._h)
+        self._ncaps += 1
+        return cid.value
+
+    def autotune_tiles(self, repeats: int = 5):
+        _check(iblbm_autotune_tiles(self._h, repeats), self._h)
+
+    def run_tile(self, run: int):
+        tx, ty = _int(), _int()
+        _check(iblbm_get_run_tile(self._h, run, ctypes.byref(tx), ctypes.byref(ty)), self._h)
+        return tx.value, ty.value
+
+    def get_run_velocity(self, run: int):
+        nx, ny, nz = self.runs[run]
+        out = np.empty((3, nz, ny, nx), np.float64)
+        _check(iblbm_get_run_velocity(self._h, run, _d(out)), self._h)
+        return out
+
+    def get_run_populations(self, run: int):
+        nx, ny, nz = self.runs[run]
+        out = np.empty((19, nz, ny, nx), np.float64)
+        _check(iblbm_get_run_populations(self._h, run, _d(out)), self._h)
+        return out
+
+    def set_run_populations(self, run: int, f):
+        nx, ny, nz = self.runs[run]
+        f = np.ascontiguousarray(f, np.float64)
+        assert f.shape == (19, nz, ny, nx)
+        _check(iblbm_set_run_populations(self._h, run, _d(f)), self._h)
 
     def close(self):
         if getattr(self, "_h", None):
