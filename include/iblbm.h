@@ -215,6 +215,30 @@ int iblbm_get_taylor_records(iblbm_sim *sim, int capsule_id, int max_records,
  * iblbm_step.  Synchronising. */
 int iblbm_profile_kernels(iblbm_sim *sim, int n_steps, double ms_out[4]);
 
+/* ---- adjoint (gradient of the final Taylor deformation) ----------------------
+ *
+ * Reverse-mode differentiation of n time steps, for a single lattice with
+ * exactly one capsule.  iblbm_adjoint_forward advances n_steps like
+ * iblbm_step, keeping a checkpoint of the populations and node positions every
+ * `checkpoint_every` steps (at the start of each segment).
+ * iblbm_adjoint_backward then gives the Taylor deformation D of the final
+ * shape (Sec. III) and its derivatives: with respect to the shear modulus k_s
+ * at fixed C = k_alpha / k_s, to the wall speed u_wall (including, when the
+ * run started from iblbm_init_fluid(1) at step 0, the dependence of the
+ * initial Couette state on u_wall), to the reference node positions X0
+ * (dD_dX0, [n][3]) and to the node positions at the start of the run
+ * (dD_dx0, [n][3]); when the capsule started in its reference shape, the
+ * derivative with respect to that shape is dD_dX0 + dD_dx0.  Each segment is
+ * recomputed from its checkpoint, keeping every forward quantity of its
+ * steps, and swept backwards through the transposes of the interpolation,
+ * collide-and-stream, spreading and membrane-force kernels; dD/dx of the final
+ * shape seeds the sweep.  The simulation is left in its final state.  Any
+ * output pointer but D may be NULL.  Synchronising. */
+int iblbm_adjoint_forward(iblbm_sim *sim, int64_t n_steps, int checkpoint_every);
+int iblbm_adjoint_backward(iblbm_sim *sim, int capsule_id, double *D,
+                           double *dD_dks, double *dD_duw, double *dD_dX0,
+                           double *dD_dx0);
+
 /* Waits for the stream and returns the first device error recorded since the
  * last call that returned it (then clears it). */
 int iblbm_sync(iblbm_sim *sim);
@@ -224,6 +248,13 @@ int iblbm_sync(iblbm_sim *sim);
  * [10*4^m + 2][3] and faces tri_out [20*4^m][3] (either may be NULL). */
 int iblbm_icosphere(int subdivisions, double radius, const double center[3],
                     double *nodes_out, int32_t *tri_out);
+
+/* Host-only utility: the Taylor deformation D of Sec. III of one closed
+ * membrane (nodes [n][3], faces [m][3]) and, if dD_dx is not NULL, its
+ * gradient with respect to the node positions [n][3], in double precision by
+ * a reverse pass through the inertia-tensor and eigenvalue computation. */
+int iblbm_taylor_gradient(const double *nodes, int n_nodes, const int32_t *tri,
+                          int n_tri, double *D_out, double *dD_dx);
 
 /* ---- read-back and state access (synchronising) ------------------------------ */
 

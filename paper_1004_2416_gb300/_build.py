@@ -21,7 +21,7 @@ OBJ = os.path.join(HERE, "_build")
 LIB_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIB_DIR, "libiblbm.so")
 
-CUDA_UNITS = ["lbm.cu", "ib.cu", "taylor.cu"]
+CUDA_UNITS = ["lbm.cu", "ib.cu", "taylor.cu", "adjoint.cu"]
 HOST_UNITS = ["capi.cpp", "mesh.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -96,6 +96,22 @@ struct iblbm_sim {
     int batch_grid = 0;
     int *d_node_run = nullptr;
 
+    // Adjoint: checkpoints of the forward run and the buffers of the reverse sweep.
+    struct Adjoint {
+        bool ready = false;
+        int K = 0;
+        int64_t n = 0, t_start = 0;
+        bool couette_start = false;
+        std::vector<void *> ck_pop, ck_x;
+        std::vector<void *> tr_pop, tr_g, tr_flags, tr_x, tr_F;
+        void *lam[2] = {nullptr, nullptr}, *lamx[2] = {nullptr, nullptr};
+        void *mu = nullptr, *lamg = nullptr, *lamF = nullptr, *fref = nullptr;
+        uint8_t *zero_flags = nullptr;
+        double *uw_partial = nullptr, *gX0 = nullptr, *gks = nullptr;
+        std::vector<void *> allocs;
+    } adj;
+    int init_mode = 0;
+
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int graph_len = 0;
     int64_t steps = 0;
@@ -782,6 +798,7 @@ int iblbm_destroy(iblbm_sim *s) {
     dev_free(s, s->d_scratch);
     dev_free(s, s->d_runs);
     dev_free(s, s->d_items);
+    for (void *p : s->adj.allocs) dev_free(s, p);
     free_ring(s);
     for (void *p : s->mesh_allocs) dev_free(s, p);
     for (void *p : s->plan_allocs) dev_free(s, p);
@@ -855,6 +872,15 @@ int iblbm_icosphere(int subdivisions, double radius, const double center[3], dou
     return IBLBM_OK;
 }
 
+int iblbm_taylor_gradient(const double *nodes, int n_nodes, const int32_t *tri, int n_tri,
+                          double *D_out, double *dD_dx) {
+    if (!nodes || !tri || !D_out || n_nodes < 4 || n_tri < 4) return IBLBM_ERR_ARG;
+    for (int k = 0; k < 3 * n_tri; ++k)
+        if (tri[k] < 0 || tri[k] >= n_nodes) return IBLBM_ERR_ARG;
+    *D_out = taylor_D_and_gradient(nodes, n_nodes, (const int *)tri, n_tri, dD_dx);
+    return std::isfinite(*D_out) ? IBLBM_OK : IBLBM_ERR_ARG;
+}
+
 int iblbm_add_capsule_mesh(iblbm_sim *s, const double *ref_xyz, int n_nodes, const int32_t *tri,
                            int n_tri, int *capsule_id) {
     if (!s) return IBLBM_ERR_ARG;
@@ -915,6 +941,7 @@ int iblbm_init_fluid(iblbm_sim *s, int mode) {
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s->stream));
     s->steps = 0;
+    s->init_mode = mode;
     if (s->d_ring) {
         CK(cudaMemset(s->d_ring_count, 0, sizeof(unsigned long long)));
         s->rec_steps.clear();
@@ -981,6 +1008,280 @@ int iblbm_step(iblbm_sim *s, int64_t n_steps) {
         return fail(s, IBLBM_ERR_CUDA, std::string("kernel launch failed: ") + s->launch_fail);
     CK(cudaGetLastError());
     return IBLBM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+void adj_free(iblbm_sim *s) {
+    for (void *p : s->adj.allocs) dev_free(s, p);
+    s->adj = iblbm_sim::Adjoint{};
+}
+
+void *adj_alloc(iblbm_sim *s, size_t bytes) {
+    void *p = dev_alloc(s, bytes);
+    if (p) s->adj.allocs.push_back(p);
+    return p;
+}
+
+size_t pos_bytes(const iblbm_sim *s) { return (size_t)s->mesh.n_nodes * 32; }  // dvec4 or hi+lo float4
+size_t nodevec_bytes(const iblbm_sim *s) { return (size_t)s->mesh.n_nodes * 4 * real_bytes(s); }
+
+cudaError_t copy_pos_out(iblbm_sim *s, void *dst) {
+    const size_t n = (size_t)s->mesh.n_nodes;
+    if (s->prec == kF64) return cudaMemcpyAsync(dst, s->mesh.x, n * 32, cudaMemcpyDeviceToDevice, s->stream);
+    cudaError_t e = cudaMemcpyAsync(dst, s->mesh.x, n * 16, cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync((char *)dst + n * 16, s->mesh.x_lo, n * 16, cudaMemcpyDeviceToDevice, s->stream);
+    return e;
+}
+
+cudaError_t copy_pos_in(iblbm_sim *s, const void *src) {
+    const size_t n = (size_t)s->mesh.n_nodes;
+    if (s->prec == kF64) return cudaMemcpyAsync(s->mesh.x, src, n * 32, cudaMemcpyDeviceToDevice, s->stream);
+    cudaError_t e = cudaMemcpyAsync(s->mesh.x, src, n * 16, cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->mesh.x_lo, (const char *)src + n * 16, n * 16, cudaMemcpyDeviceToDevice, s->stream);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int iblbm_adjoint_forward(iblbm_sim *s, int64_t n_steps, int checkpoint_every) {
+    if (!s) return IBLBM_ERR_ARG;
+    if (s->batch) return fail(s, IBLBM_ERR_STATE, "the adjoint works on a single lattice");
+    if (s->caps.size() != 1) return fail(s, IBLBM_ERR_STATE, "the adjoint needs exactly one capsule");
+    if (n_steps < 1 || checkpoint_every < 1 || checkpoint_every > n_steps)
+        return fail(s, IBLBM_ERR_ARG, "need n_steps >= 1 and 1 <= checkpoint_every <= n_steps");
+    CK(cudaSetDevice(s->device));
+    int rc = ensure_mesh(s);
+    if (rc) return rc;
+    join_side(s);
+    CK(cudaStreamSynchronize(s->stream));
+    adj_free(s);
+    iblbm_sim::Adjoint &A = s->adj;
+    A.K = checkpoint_every;
+    A.n = n_steps;
+    A.t_start = s->steps;
+    A.couette_start = (s->steps == 0 && s->init_mode == 1);
+    const int64_t nck = (n_steps + A.K - 1) / A.K;
+    for (int64_t c = 0; c < nck; ++c) {
+        void *p = adj_alloc(s, s->pop_bytes), *x = adj_alloc(s, pos_bytes(s));
+        if (!p || !x) {
+            adj_free(s);
+            return fail(s, IBLBM_ERR_OOM, "checkpoint allocation failed");
+        }
+        A.ck_pop.push_back(p);
+        A.ck_x.push_back(x);
+    }
+    for (int64_t c = 0; c < nck; ++c) {
+        CK(cudaMemcpyAsync(A.ck_pop[c], s->pop[s->cur], s->pop_bytes, cudaMemcpyDeviceToDevice, s->stream));
+        CK(copy_pos_out(s, A.ck_x[c]));
+        rc = iblbm_step(s, std::min<int64_t>(A.K, n_steps - c * A.K));
+        if (rc) return rc;
+    }
+    rc = sync_status(s);
+    if (rc) return rc;
+    A.ready = true;
+    return IBLBM_OK;
+}
+
+int iblbm_adjoint_backward(iblbm_sim *s, int capsule_id, double *D_out, double *dD_dks, double *dD_duw,
+                           double *dD_dX0, double *dD_dx0) {
+    if (!s || !D_out) return IBLBM_ERR_ARG;
+    iblbm_sim::Adjoint &A = s->adj;
+    if (!A.ready || s->steps != A.t_start + A.n || s->mesh_dirty)
+        return fail(s, IBLBM_ERR_STATE, "run iblbm_adjoint_forward first, with no step since");
+    if (capsule_id != 0) return fail(s, IBLBM_ERR_ARG, "no such capsule");
+    CK(cudaSetDevice(s->device));
+    int rc = sync_status(s);
+    if (rc) return rc;
+    const MeshDev &m = s->mesh;
+    const int n = m.n_nodes, nf = m.n_faces;
+    const size_t vb = 4 * real_bytes(s);
+    const int K = A.K;
+    // reverse-sweep buffers (kept for repeated backward passes)
+    if (A.tr_pop.empty()) {
+        bool ok = true;
+        for (int k = 0; k <= K && ok; ++k) {
+            void *p = adj_alloc(s, s->pop_bytes);
+            ok = p != nullptr;
+            A.tr_pop.push_back(p);
+        }
+        for (int k = 0; k < K && ok; ++k) {
+            A.tr_g.push_back(adj_alloc(s, s->vec_bytes));
+            A.tr_flags.push_back(adj_alloc(s, s->flag_bytes));
+            A.tr_x.push_back(adj_alloc(s, pos_bytes(s)));
+            A.tr_F.push_back(adj_alloc(s, nodevec_bytes(s)));
+            ok = A.tr_g.back() && A.tr_flags.back() && A.tr_x.back() && A.tr_F.back();
+        }
+        const size_t lb = 19 * real_bytes(s) * (size_t)s->L.ncell;
+        for (int k = 0; k < 2 && ok; ++k) {
+            A.lam[k] = adj_alloc(s, lb);
+            A.lamx[k] = adj_alloc(s, nodevec_bytes(s));
+            ok = A.lam[k] && A.lamx[k];
+        }
+        A.mu = adj_alloc(s, s->vec_bytes);
+        A.lamg = adj_alloc(s, s->vec_bytes);
+        A.lamF = adj_alloc(s, nodevec_bytes(s));
+        A.fref = adj_alloc(s, 2 * vb * nf);
+        A.zero_flags = (uint8_t *)adj_alloc(s, s->flag_bytes);
+        A.uw_partial = (double *)adj_alloc(s, sizeof(double) * (size_t)((s->L.ncell + 255) / 256));
+        A.gX0 = (double *)adj_alloc(s, sizeof(double) * 3 * n);
+        A.gks = (double *)adj_alloc(s, sizeof(double) * n);
+        ok = ok && A.mu && A.lamg && A.lamF && A.fref && A.zero_flags && A.uw_partial && A.gX0 && A.gks;
+        if (!ok) {
+            A.tr_pop.clear();
+            return fail(s, IBLBM_ERR_OOM, "adjoint buffer allocation failed");
+        }
+        // reference edges of every face
+        std::vector<double> fr(8 * (size_t)nf, 0.0);
+        for (int f = 0; f < nf; ++f) {
+            const int a = s->tri[3 * f], b = s->tri[3 * f + 1], c = s->tri[3 * f + 2];
+            for (int k = 0; k < 3; ++k) {
+                fr[8 * f + k] = s->X0[3 * b + k] - s->X0[3 * a + k];
+                fr[8 * f + 4 + k] = s->X0[3 * c + k] - s->X0[3 * a + k];
+            }
+        }
+        if (s->prec == kF64) {
+            CK(cudaMemcpy(A.fref, fr.data(), fr.size() * 8, cudaMemcpyHostToDevice));
+        } else {
+            std::vector<float> ff(fr.begin(), fr.end());
+            CK(cudaMemcpy(A.fref, ff.data(), ff.size() * 4, cudaMemcpyHostToDevice));
+        }
+        CK(cudaMemset(A.zero_flags, 0, s->flag_bytes));
+    }
+    // the final state is restored afterwards
+    void *save_x = adj_alloc(s, pos_bytes(s));
+    void *save_F = adj_alloc(s, nodevec_bytes(s));
+    void *save_u = adj_alloc(s, nodevec_bytes(s));
+    if (!save_x || !save_F || !save_u) return fail(s, IBLBM_ERR_OOM, "adjoint buffer allocation failed");
+    CK(copy_pos_out(s, save_x));
+    CK(cudaMemcpyAsync(save_F, m.F, nodevec_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(save_u, m.u, nodevec_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
+    // seed: D of the final shape and dD/dx (host, FP64)
+    std::vector<double> xT(3 * (size_t)n), seed(3 * (size_t)n);
+    rc = ensure_scratch(s, sizeof(double) * 3 * n);
+    if (rc) return rc;
+    launch_nodes_to_f64(s->prec, m, 0, 0, n, s->d_scratch, s->stream);
+    CK(cudaMemcpyAsync(xT.data(), s->d_scratch, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    *D_out = taylor_D_and_gradient(xT.data(), n, s->tri.data(), nf, seed.data());
+    if (s->prec == kF64) {
+        std::vector<double> sv(4 * (size_t)n, 0.0);
+        for (int i = 0; i < n; ++i)
+            for (int k = 0; k < 3; ++k) sv[4 * i + k] = seed[3 * i + k];
+        CK(cudaMemcpy(A.lamx[0], sv.data(), sv.size() * 8, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> sv(4 * (size_t)n, 0.0f);
+        for (int i = 0; i < n; ++i)
+            for (int k = 0; k < 3; ++k) sv[4 * i + k] = (float)seed[3 * i + k];
+        CK(cudaMemcpy(A.lamx[0], sv.data(), sv.size() * 4, cudaMemcpyHostToDevice));
+    }
+    const size_t lb = 19 * real_bytes(s) * (size_t)s->L.ncell;
+    const int nblk = (int)((s->L.ncell + 255) / 256);
+    CK(cudaMemsetAsync(A.lam[0], 0, lb, s->stream));
+    CK(cudaMemsetAsync(A.mu, 0, s->vec_bytes, s->stream));
+    CK(cudaMemsetAsync(A.lamg, 0, s->vec_bytes, s->stream));
+    CK(cudaMemsetAsync(A.uw_partial, 0, sizeof(double) * nblk, s->stream));
+    CK(cudaMemsetAsync(A.gX0, 0, sizeof(double) * 3 * n, s->stream));
+    CK(cudaMemsetAsync(A.gks, 0, sizeof(double) * n, s->stream));
+    int cur = 0;
+    const int64_t nck = (int64_t)A.ck_pop.size();
+    for (int64_t seg = nck - 1; seg >= 0; --seg) {
+        const int len = (int)std::min<int64_t>(K, A.n - seg * K);
+        // recompute the segment, keeping every forward quantity of each step
+        CK(cudaMemcpyAsync(A.tr_pop[0], A.ck_pop[seg], s->pop_bytes, cudaMemcpyDeviceToDevice, s->stream));
+        CK(copy_pos_in(s, A.ck_x[seg]));
+        for (int k = 0; k < len; ++k) {
+            CK(copy_pos_out(s, A.tr_x[k]));
+            CK(cudaMemsetAsync(A.tr_g[k], 0, s->vec_bytes, s->stream));
+            CK(cudaMemsetAsync(A.tr_flags[k], 0, s->flag_bytes, s->stream));
+            launch_force_spread(s->prec, s->delta, s->L, m, A.tr_g[k], (uint8_t *)A.tr_flags[k], s->d_status,
+                                nullptr, nullptr, s->stream);
+            CK(cudaMemcpyAsync(A.tr_F[k], m.F, nodevec_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
+            CollideArgs a{};
+            a.src = A.tr_pop[k];
+            a.dst = A.tr_pop[k + 1];
+            a.fcur = A.tr_g[k];
+            a.flag_cur = (const uint8_t *)A.tr_flags[k];
+            a.fold = A.tr_g[k];          // never written: flag_old is all zero
+            a.flag_old = A.zero_flags;
+            a.tau = s->tau;
+            a.u_wall = s->u_wall;
+            a.status = s->d_status;
+            launch_collide_stream(s->prec, s->L, a, s->stream);
+            launch_interp_advect(s->prec, s->delta, s->L, m, A.tr_pop[k + 1], A.tr_g[k], nullptr, nullptr,
+                                 s->stream);
+        }
+        // reverse sweep over the segment
+        for (int k = len - 1; k >= 0; --k) {
+            AdjStepArgs q{};
+            q.L = s->L;
+            q.mesh = m;
+            q.x = A.tr_x[k];
+            q.x_lo = s->prec == kF64 ? nullptr : (char *)A.tr_x[k] + (size_t)n * 16;
+            q.pop0 = A.tr_pop[k];
+            q.pop1 = A.tr_pop[k + 1];
+            q.g = A.tr_g[k];
+            q.flags = (const uint8_t *)A.tr_flags[k];
+            q.F = A.tr_F[k];
+            q.fref = A.fref;
+            q.lamx_in = A.lamx[cur];
+            q.lamx_out = A.lamx[1 - cur];
+            q.lam_in = A.lam[cur];
+            q.lam_out = A.lam[1 - cur];
+            q.mu = A.mu;
+            q.lamg = A.lamg;
+            q.lamF = A.lamF;
+            q.uw_partial = A.uw_partial;
+            q.gX0 = A.gX0;
+            q.gks = A.gks;
+            q.omega = 1.0 / s->tau;
+            launch_adjoint_step(s->prec, s->delta, q, s->stream);
+            cur = 1 - cur;
+        }
+        CK(cudaGetLastError());
+    }
+    if (A.couette_start) launch_adjoint_init_uw(s->prec, s->L, A.lam[cur], s->u_wall, A.uw_partial, s->stream);
+    CK(cudaGetLastError());
+    // gradients to the host
+    std::vector<double> uwp(nblk), gk(n), g0(3 * (size_t)n);
+    CK(cudaMemcpyAsync(uwp.data(), A.uw_partial, sizeof(double) * nblk, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(gk.data(), A.gks, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(g0.data(), A.gX0, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s->stream));
+    std::vector<double> lx(4 * (size_t)n);
+    if (s->prec == kF64) {
+        CK(cudaMemcpyAsync(lx.data(), A.lamx[cur], sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+    } else {
+        std::vector<float> lf(4 * (size_t)n);
+        CK(cudaMemcpyAsync(lf.data(), A.lamx[cur], sizeof(float) * 4 * n, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        for (size_t k = 0; k < lf.size(); ++k) lx[k] = lf[k];
+    }
+    double duw = 0.0, dks = 0.0;
+    for (double v : uwp) duw += v;
+    for (double v : gk) dks += v;
+    if (dD_dks) *dD_dks = dks;
+    if (dD_duw) *dD_duw = duw;
+    if (dD_dX0) std::memcpy(dD_dX0, g0.data(), sizeof(double) * 3 * n);
+    if (dD_dx0)
+        for (int i = 0; i < n; ++i)
+            for (int k = 0; k < 3; ++k) dD_dx0[3 * i + k] = lx[4 * i + k];
+    // restore the final state of the forward run
+    CK(copy_pos_in(s, save_x));
+    CK(cudaMemcpyAsync(m.F, save_F, nodevec_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaMemcpyAsync(m.u, save_u, nodevec_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
+    rc = sync_status(s);
+    for (void *p : {save_x, save_F, save_u}) {
+        A.allocs.erase(std::find(A.allocs.begin(), A.allocs.end(), p));
+        dev_free(s, p);
+    }
+    return rc;
 }
 
 int iblbm_set_taylor_recording(iblbm_sim *s, int every, int ring) {

@@ -131,6 +131,34 @@ void launch_nodes_to_f64(int prec, const MeshDev &m, int which, int first, int c
 void launch_f64_to_nodes(int prec, const MeshDev &m, int first, int count, const double *in,
                          cudaStream_t s);
 
+// ---- adjoint.cu ---------------------------------------------------------------------
+// Buffers of one reverse step (step t of a single lattice).
+struct AdjStepArgs {
+    Lattice L;
+    MeshDev mesh;
+    void *x, *x_lo;         // stored node positions x(t) (hi/lo for float builds)
+    const void *pop0;       // f(t)
+    const void *pop1;       // f(t+1)
+    const void *g;          // force density g(t)
+    const uint8_t *flags;   // force flags of step t
+    const void *F;          // node forces F(t)
+    const void *fref;       // reference edges U, V per face, Vec4 [2][n_faces]
+    void *lamx_in;          // node adjoint after the step (Vec4 per node)
+    void *lamx_out;         // node adjoint before the step
+    void *lam_in;           // population adjoint after the step, T [19][ncell] (also corrected in place)
+    void *lam_out;          // population adjoint before the step
+    void *mu, *lamg;        // lattice work fields, Vec4 per cell
+    void *lamF;             // node-force adjoint, Vec4 per node
+    double *uw_partial;     // per collide-adjoint block: d/du_wall (accumulated)
+    double *gX0;            // [n][3] d/dX0 (accumulated)
+    double *gks;            // [n] d/dk_s (accumulated)
+    double omega;
+};
+void launch_adjoint_step(int prec, int delta, const AdjStepArgs &A, cudaStream_t s);
+// sum over cells of lam_f(0) . d f(0)/d u_wall for the linear-Couette start
+void launch_adjoint_init_uw(int prec, const Lattice &L, const void *lam, double u_wall, double *partial,
+                            cudaStream_t s);
+
 // ---- taylor.cu ----------------------------------------------------------------------
 // Per-capsule FP64 sums: out[c*12 + k] = {V, A, cx, cy, cz, Ixx, Iyy, Izz, Ixy, Ixz, Iyz, 0}
 struct TaylorPlan {
@@ -171,5 +199,8 @@ void icosphere(int m, double r, const double c[3], std::vector<double> &nodes,
 // Host eigen-decomposition of a symmetric 3x3 matrix: ascending values,
 // eigenvectors in columns of vec (row-major 3x3).
 void sym_eig3(const double A[9], double val[3], double vec[9]);
+// Taylor deformation D of a closed membrane and, if grad is not null, dD/dx
+// [n][3] (host, FP64).
+double taylor_D_and_gradient(const double *x, int n, const int *tri, int m, double *grad);
 
 }  // namespace iblbm

@@ -211,3 +211,128 @@ void sym_eig3(const double A[9], double val[3], double vec[9]) {
 }
 
 }  // namespace iblbm
+
+namespace iblbm {
+
+// Taylor deformation of a closed membrane and its gradient with respect to
+// the node positions, in double precision on the host.  Forward: face area
+// vectors A n = (x2 - x1) x (x3 - x1)/2, face centroids r about a fixed origin
+// o, V = 1/3 sum r.(A n), centroid offset d = sum (r.(A n)) r / (4 V), q = r - d,
+// I = 1/5 sum (q.(A n)) (|q|^2 1 - q q^T), J = I / V, eigenvalues Ja <= Jb <= Jc,
+// r_a^2 = 5/2 (Jb + Jc - Ja), r_c^2 = 5/2 (Ja + Jb - Jc), D = (r_a - r_c)/(r_a + r_c).
+// Reverse: the same chain taken backwards, with dJ_k = v_k^T dJ v_k for the
+// eigenvalues.  The origin o cancels mathematically and is held fixed.
+double taylor_D_and_gradient(const double *x, int n, const int *tri, int m, double *grad) {
+    double o[3] = {0, 0, 0};
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 3; ++k) o[k] += x[3 * i + k];
+    for (int k = 0; k < 3; ++k) o[k] /= n;
+    std::vector<double> r(3 * (size_t)m), An(3 * (size_t)m), rn(m);
+    double V = 0.0, mom[3] = {0, 0, 0};
+    for (int f = 0; f < m; ++f) {
+        const double *p1 = x + 3 * tri[3 * f], *p2 = x + 3 * tri[3 * f + 1], *p3 = x + 3 * tri[3 * f + 2];
+        double e1[3], e2[3];
+        for (int k = 0; k < 3; ++k) {
+            e1[k] = p2[k] - p1[k];
+            e2[k] = p3[k] - p1[k];
+            r[3 * f + k] = (p1[k] + p2[k] + p3[k]) / 3.0 - o[k];
+        }
+        double *a = &An[3 * f];
+        a[0] = 0.5 * (e1[1] * e2[2] - e1[2] * e2[1]);
+        a[1] = 0.5 * (e1[2] * e2[0] - e1[0] * e2[2]);
+        a[2] = 0.5 * (e1[0] * e2[1] - e1[1] * e2[0]);
+        rn[f] = r[3 * f] * a[0] + r[3 * f + 1] * a[1] + r[3 * f + 2] * a[2];
+        V += rn[f] / 3.0;
+        for (int k = 0; k < 3; ++k) mom[k] += rn[f] * r[3 * f + k];
+    }
+    double d[3];
+    for (int k = 0; k < 3; ++k) d[k] = mom[k] / (4.0 * V);
+    double I[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    std::vector<double> q(3 * (size_t)m), qn(m);
+    for (int f = 0; f < m; ++f) {
+        double *qq = &q[3 * f];
+        for (int k = 0; k < 3; ++k) qq[k] = r[3 * f + k] - d[k];
+        qn[f] = qq[0] * An[3 * f] + qq[1] * An[3 * f + 1] + qq[2] * An[3 * f + 2];
+        const double q2 = qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) I[3 * a + b] += 0.2 * qn[f] * ((a == b ? q2 : 0.0) - qq[a] * qq[b]);
+    }
+    double J[9], val[3], vec[9];
+    for (int k = 0; k < 9; ++k) J[k] = I[k] / V;
+    sym_eig3(J, val, vec);
+    const double ra = std::sqrt(2.5 * (val[1] + val[2] - val[0]));
+    const double rc = std::sqrt(2.5 * (val[0] + val[1] - val[2]));
+    const double D = (ra - rc) / (ra + rc);
+    if (!grad) return D;
+    // ---- reverse
+    const double dra = 2.0 * rc / ((ra + rc) * (ra + rc));
+    const double drc = -2.0 * ra / ((ra + rc) * (ra + rc));
+    const double cra = 2.5 / (2.0 * ra), crc = 2.5 / (2.0 * rc);
+    const double Jbar_k[3] = {dra * cra * -1.0 + drc * crc * 1.0,  // Ja
+                              dra * cra * 1.0 + drc * crc * 1.0,   // Jb
+                              dra * cra * 1.0 + drc * crc * -1.0}; // Jc
+    double Jbar[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < 3; ++k)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) Jbar[3 * a + b] += Jbar_k[k] * vec[3 * a + k] * vec[3 * b + k];
+    double Ibar[9], Vbar = 0.0;
+    for (int k = 0; k < 9; ++k) {
+        Ibar[k] = Jbar[k] / V;
+        Vbar -= Jbar[k] * I[k] / (V * V);
+    }
+    const double trI = Ibar[0] + Ibar[4] + Ibar[8];
+    std::vector<double> rbar(3 * (size_t)m, 0.0), Abar(3 * (size_t)m, 0.0);
+    double dbar[3] = {0, 0, 0};
+    for (int f = 0; f < m; ++f) {
+        const double *qq = &q[3 * f];
+        const double q2 = qq[0] * qq[0] + qq[1] * qq[1] + qq[2] * qq[2];
+        double Iq[3];
+        for (int a = 0; a < 3; ++a) Iq[a] = Ibar[3 * a] * qq[0] + Ibar[3 * a + 1] * qq[1] + Ibar[3 * a + 2] * qq[2];
+        const double qIq = qq[0] * Iq[0] + qq[1] * Iq[1] + qq[2] * Iq[2];
+        const double qnbar = 0.2 * (q2 * trI - qIq);
+        for (int a = 0; a < 3; ++a) {
+            const double qbar = qnbar * An[3 * f + a] + 0.2 * qn[f] * (2.0 * qq[a] * trI - 2.0 * Iq[a]);
+            rbar[3 * f + a] += qbar;
+            dbar[a] -= qbar;
+            Abar[3 * f + a] += qnbar * qq[a];
+        }
+    }
+    double mbar[3];
+    for (int k = 0; k < 3; ++k) {
+        mbar[k] = dbar[k] / (4.0 * V);
+        Vbar -= dbar[k] * mom[k] / (4.0 * V * V);
+    }
+    for (int f = 0; f < m; ++f) {
+        const double *rr = &r[3 * f];
+        const double rnbar = mbar[0] * rr[0] + mbar[1] * rr[1] + mbar[2] * rr[2] + Vbar / 3.0;
+        for (int a = 0; a < 3; ++a) {
+            rbar[3 * f + a] += rn[f] * mbar[a] + rnbar * An[3 * f + a];
+            Abar[3 * f + a] += rnbar * rr[a];
+        }
+    }
+    for (int i = 0; i < 3 * n; ++i) grad[i] = 0.0;
+    for (int f = 0; f < m; ++f) {
+        const int i1 = tri[3 * f], i2 = tri[3 * f + 1], i3 = tri[3 * f + 2];
+        const double *p1 = x + 3 * i1, *p2 = x + 3 * i2, *p3 = x + 3 * i3;
+        double e1[3], e2[3];
+        for (int k = 0; k < 3; ++k) {
+            e1[k] = p2[k] - p1[k];
+            e2[k] = p3[k] - p1[k];
+        }
+        const double *Ab = &Abar[3 * f];
+        // An = e1 x e2 / 2: e1bar = (e2 x Abar)/2, e2bar = (Abar x e1)/2
+        const double e1b[3] = {0.5 * (e2[1] * Ab[2] - e2[2] * Ab[1]), 0.5 * (e2[2] * Ab[0] - e2[0] * Ab[2]),
+                               0.5 * (e2[0] * Ab[1] - e2[1] * Ab[0])};
+        const double e2b[3] = {0.5 * (Ab[1] * e1[2] - Ab[2] * e1[1]), 0.5 * (Ab[2] * e1[0] - Ab[0] * e1[2]),
+                               0.5 * (Ab[0] * e1[1] - Ab[1] * e1[0])};
+        for (int k = 0; k < 3; ++k) {
+            const double rb = rbar[3 * f + k] / 3.0;
+            grad[3 * i1 + k] += rb - e1b[k] - e2b[k];
+            grad[3 * i2 + k] += rb + e1b[k];
+            grad[3 * i3 + k] += rb + e2b[k];
+        }
+    }
+    return D;
+}
+
+}  // namespace iblbm

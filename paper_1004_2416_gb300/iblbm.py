@@ -97,6 +97,9 @@ _SIGS = {
     "iblbm_get_taylor_records": (_int, [_vp, _int, _int, _dp, ctypes.POINTER(ctypes.c_int64), _ip]),
     "iblbm_profile_kernels": (_int, [_vp, _int, _dp]),
     "iblbm_taylor_sums_noalloc": (_int, [_vp, _int, _vp, _int, _dp, _vp, _vp]),
+    "iblbm_taylor_gradient": (_int, [_dp, _int, _i32p, _int, _dp, _dp]),
+    "iblbm_adjoint_forward": (_int, [_vp, ctypes.c_int64, _int]),
+    "iblbm_adjoint_backward": (_int, [_vp, _int, _dp, _dp, _dp, _dp, _dp]),
     "iblbm_create_batch": (_int, [ctypes.POINTER(_vp), ctypes.POINTER(iblbm_run_spec), _int, _int, _int,
                                   _vp, ctypes.POINTER(iblbm_allocator)]),
     "iblbm_add_capsule_icosphere_in_run": (_int, [_vp, _int, _dbl, _dbl, _dbl, _dbl, _int, _ip]),
@@ -163,6 +166,16 @@ def icosphere(subdivisions: int, radius: float, center=(0.0, 0.0, 0.0)):
     c = np.ascontiguousarray(center, np.float64)
     _check(iblbm_icosphere(subdivisions, radius, _d(c), _d(nodes), tri.ctypes.data_as(_i32p)))
     return nodes, tri
+
+
+def taylor_gradient(nodes, tri):
+    """(D, dD/dx [n, 3]) of one closed membrane (host, FP64)."""
+    x = np.ascontiguousarray(nodes, np.float64)
+    t = np.ascontiguousarray(tri, np.int32)
+    D = ctypes.c_double()
+    g = np.empty_like(x)
+    _check(iblbm_taylor_gradient(_d(x), len(x), t.ctypes.data_as(_i32p), len(t), ctypes.byref(D), _d(g)))
+    return D.value, g
 
 
 TAYLOR_KEYS = ("D", "theta", "r_a", "r_b", "r_c", "V", "A", "c_x", "c_y", "c_z",
@@ -378,6 +391,18 @@ class Sim:
         ms = np.zeros(4, np.float64)
         _check(iblbm_profile_kernels(self._h, int(n_steps), _d(ms)), self._h)
         return dict(zip(("force_spread", "collide_stream", "interp_advect", "taylor"), ms.tolist()))
+
+    def adjoint_forward(self, n_steps: int, checkpoint_every: int):
+        _check(iblbm_adjoint_forward(self._h, int(n_steps), int(checkpoint_every)), self._h)
+
+    def adjoint_backward(self, capsule_id: int = 0) -> dict:
+        n = self.n_nodes(capsule_id)
+        D, dks, duw = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        gX0 = np.empty((n, 3), np.float64)
+        gx0 = np.empty((n, 3), np.float64)
+        _check(iblbm_adjoint_backward(self._h, capsule_id, ctypes.byref(D), ctypes.byref(dks),
+                                      ctypes.byref(duw), _d(gX0), _d(gx0)), self._h)
+        return {"D": D.value, "dD_dks": dks.value, "dD_duw": duw.value, "dD_dX0": gX0, "dD_dx0": gx0}
 
     def taylor(self, capsule_id: int = 0) -> dict:
         out = np.empty(16, np.float64)

@@ -76,3 +76,24 @@ def test_create_without_device_or_with_bad_args_fails_cleanly():
     with pytest.raises(B.IblbmError) as e:
         B.Sim(0, 8, 8)
     assert e.value.code == B.IBLBM_ERR_ARG
+
+
+def test_taylor_gradient_against_oracle_finite_differences():
+    """The host reverse pass through the Taylor deformation against central
+    differences of the oracle's D (and its D itself)."""
+    import oracle as O
+    from paper_1004_2416_gb300 import iblbm as B
+
+    rng = np.random.default_rng(3)
+    x0, tri = O.icosphere(2, 4.0, (10.0, 11.0, 9.0))
+    th = 0.4
+    R = np.array([[np.cos(th), 0, -np.sin(th)], [0, 1, 0], [np.sin(th), 0, np.cos(th)]])
+    x = ((x0 - x0.mean(0)) * np.array([1.2, 1.0, 0.85])) @ R.T + x0.mean(0) + 0.05 * rng.standard_normal(x0.shape)
+    D, g = B.taylor_gradient(x, tri)
+    assert D == pytest.approx(O.taylor(x, tri)["D"], rel=1e-12)
+    h = 1e-6
+    for _ in range(6):
+        d = rng.standard_normal(x.shape)
+        d /= np.linalg.norm(d)
+        fd = (O.taylor(x + h * d, tri)["D"] - O.taylor(x - h * d, tri)["D"]) / (2 * h)
+        assert np.sum(g * d) == pytest.approx(fd, rel=1e-6, abs=1e-9)

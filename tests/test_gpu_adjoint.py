@@ -1,0 +1,74 @@
+"""Adjoint extension: the gradient of the final Taylor deformation with respect
+to the shear modulus, the wall speed (capillary number) and the reference node
+positions, from the hand-written reverse sweep, against central finite
+differences of the FP64 oracle (tests/golden/adjoint_fd_*.json, written by
+tests/golden/make_adjoint_fd.py, which calls only the oracle)."""
+import importlib.util
+import json
+import os
+
+import numpy as np
+import pytest
+
+from cases import gpu_sim
+from conftest import GOLDEN
+
+pytestmark = pytest.mark.gpu
+
+_spec = importlib.util.spec_from_file_location("make_adjoint_fd", os.path.join(GOLDEN, "make_adjoint_fd.py"))
+FDMOD = importlib.util.module_from_spec(_spec)
+_spec.loader.exec_module(FDMOD)
+
+
+def _fd(name):
+    with open(os.path.join(GOLDEN, f"adjoint_fd_{name}.json")) as fh:
+        return json.load(fh)
+
+
+def _check(r, fd, n_nodes, tol, capsys, label):
+    dirs = FDMOD.directions(n_nodes, fd["n_directions"], fd["directions_seed"])
+    gtot = r["dD_dX0"] + r["dD_dx0"]
+    along = [float(np.sum(gtot * d)) for d in dirs]
+    gnorm = float(np.linalg.norm(gtot))
+    with capsys.disabled():
+        print(f"\n{label}: D {r['D']:.8g} (fd {fd['D']:.8g}); dD/dks {r['dD_dks']:.8g} (fd {fd['dD_dks']:.8g}); "
+              f"dD/duw {r['dD_duw']:.8g} (fd {fd['dD_duw']:.8g}); dD/dX0 along "
+              f"{np.round(along, 8).tolist()} (fd {np.round(fd['dD_dX0_along'], 8).tolist()}), |grad| {gnorm:.4g}")
+    assert r["dD_dks"] == pytest.approx(fd["dD_dks"], rel=tol)
+    assert r["dD_duw"] == pytest.approx(fd["dD_duw"], rel=tol)
+    for a, b in zip(along, fd["dD_dX0_along"]):
+        assert abs(a - b) <= tol * gnorm
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_adjoint_small_against_oracle_fd(prec, capsys):
+    case, _, _ = FDMOD.case("small")
+    fd = _fd("small")
+    g = gpu_sim(case, precision=prec)
+    g.adjoint_forward(case.steps, 50)
+    x_end = g.get_nodes()
+    f_end = g.get_populations()
+    r = g.adjoint_backward(0)
+    assert r["D"] == pytest.approx(fd["D"], rel=1e-9 if prec == "fp64" else 1e-4)
+    _check(r, fd, len(x_end), 1e-6 if prec == "fp64" else 1e-3, capsys, f"adjoint {prec}")
+    # the simulation is left in its final state
+    assert np.array_equal(g.get_nodes(), x_end)
+    assert np.array_equal(g.get_populations(), f_end)
+    # a second backward pass gives the same gradient
+    r2 = g.adjoint_backward(0)
+    assert r2["dD_dks"] == pytest.approx(r["dD_dks"], rel=1e-5)
+
+
+def test_adjoint_requires_forward_run():
+    from paper_1004_2416_gb300 import iblbm as B
+
+    case, _, _ = FDMOD.case("small")
+    g = gpu_sim(case, precision="fp32")
+    with pytest.raises(B.IblbmError) as e:
+        g.adjoint_backward(0)
+    assert e.value.code == B.IBLBM_ERR_STATE
+    g.adjoint_forward(10, 5)
+    g.step(1)
+    with pytest.raises(B.IblbmError) as e:
+        g.adjoint_backward(0)
+    assert e.value.code == B.IBLBM_ERR_STATE
