@@ -53,6 +53,7 @@ def _args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-budget-s", type=float, default=20.0)
     p.add_argument("--profile-steps", type=int, default=500)
+    p.add_argument("--no-adjoint", action="store_true", help="skip the config-5 adjoint timing")
     return p.parse_args()
 
 
@@ -305,6 +306,70 @@ def _oracle_run(case, budget_s: float, max_steps: int):
     return n, dt
 
 
+# ---- adjoint timing (config 5) ---------------------------------------------------------------------
+
+def _adjoint_timing(stream):
+    """Config 5 (64^3, FP32, one 1280-face capsule, phi3): 2000 steps forward with
+    checkpoints every 100 steps, then the reverse sweep for dD/dk_s, dD/du_wall and
+    dD/dX0; host wall-clock times of both, each ending in a synchronisation.  The
+    gradient is compared with the FP64 oracle's central differences when the
+    reference file is present."""
+    import importlib.util
+
+    import numpy as np
+    import torch
+
+    from paper_1004_2416_gb300 import workloads as W
+
+    case = W.config5()
+    sim = _make_sim(case, stream)
+    X0 = sim.get_nodes()
+    sim.adjoint_forward(200, 100)  # warm-up: kernels, graphs and reverse-sweep buffers
+    sim.adjoint_backward(0)
+
+    def reset():
+        sim.init_fluid(1)
+        sim.set_nodes(X0)
+        torch.cuda.synchronize()
+
+    reset()
+    t0 = time.perf_counter()
+    sim.step(case.steps)
+    sim.sync()
+    plain = time.perf_counter() - t0
+    reset()
+    t0 = time.perf_counter()
+    sim.adjoint_forward(case.steps, 100)
+    fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    r = sim.adjoint_backward(0)
+    bwd = time.perf_counter() - t0
+    out = {"workload": case.name, "steps": case.steps, "checkpoint_every": 100,
+           "plain_forward_ms": round(plain * 1e3, 2), "forward_with_checkpoints_ms": round(fwd * 1e3, 2),
+           "backward_ms": round(bwd * 1e3, 2), "backward_over_forward": round(bwd / plain, 3),
+           "D": r["D"], "dD_dks": r["dD_dks"], "dD_duw": r["dD_duw"],
+           "dD_dG": r["dD_duw"] * case.capsules[0].k_s * case.shape[2] / (2.0 * (case.tau - 0.5) / 3.0 * case.capsules[0].radius)}
+    path = os.path.join(ROOT, "tests", "golden", "adjoint_fd_config5.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            fd = json.load(fh)
+        spec = importlib.util.spec_from_file_location("mkfd", os.path.join(ROOT, "tests", "golden", "make_adjoint_fd.py"))
+        mk = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(mk)
+        g = r["dD_dX0"] + r["dD_dx0"]
+        dirs = mk.directions(len(g), fd["n_directions"], fd["directions_seed"])
+        gn = float(np.linalg.norm(g))
+        out["vs_oracle_fd"] = {
+            "dD_dks_rel": abs(r["dD_dks"] - fd["dD_dks"]) / abs(fd["dD_dks"]),
+            "dD_duw_rel": abs(r["dD_duw"] - fd["dD_duw"]) / abs(fd["dD_duw"]),
+            "dD_dX0_directions_err_over_norm": [abs(float(np.sum(g * d)) - b) / gn
+                                                for d, b in zip(dirs, fd["dD_dX0_along"])],
+            "D_rel": abs(r["D"] - fd["D"]) / abs(fd["D"]),
+        }
+    sim.close()
+    return out
+
+
 # ---- our arm ------------------------------------------------------------------------------------
 
 def run_ours(a):
@@ -412,6 +477,10 @@ def run_ours(a):
                    "sample": f"{n} full oracle steps (FP64, single thread) of the same workload after one "
                              f"untimed step, {dt:.1f} s"}
 
+    adjoint = None
+    if grp.rank == 0 and not a.no_adjoint and a.workload == "config2":
+        adjoint = _adjoint_timing(stream)
+
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": grp.ws,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(ms_max / a.steps, 5),
@@ -423,6 +492,7 @@ def run_ours(a):
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": KERNEL_LAUNCHES_PER_STEP * a.steps,
         "final_D": D_last,
+        "adjoint": adjoint,
     }
     sim.close()
     grp.close()

@@ -72,3 +72,30 @@ def test_adjoint_requires_forward_run():
     with pytest.raises(B.IblbmError) as e:
         g.adjoint_backward(0)
     assert e.value.code == B.IBLBM_ERR_STATE
+
+
+def test_autograd_function_against_oracle_fd():
+    """torch.autograd through TaylorDeformation: D.backward() gives the
+    oracle's finite-difference gradients."""
+    torch = pytest.importorskip("torch")
+    import oracle as O
+    from paper_1004_2416_gb300.autograd import ShearSetup, taylor_deformation
+
+    case, _, _ = FDMOD.case("small")
+    fd = _fd("small")
+    cap = case.capsules[0]
+    X0np, tri = O.icosphere(cap.subdivisions, cap.radius, cap.center)
+    setup = ShearSetup(shape=case.shape, tri=tri, steps=case.steps, checkpoint_every=50,
+                       precision="fp64", delta_points=case.delta)
+    ks = torch.tensor(cap.k_s, dtype=torch.float64, requires_grad=True)
+    uw = torch.tensor(case.u_wall, dtype=torch.float64, requires_grad=True)
+    X0 = torch.tensor(X0np, dtype=torch.float64, requires_grad=True)
+    D = taylor_deformation(ks, uw, X0, setup)
+    D.backward()
+    assert float(D) == pytest.approx(fd["D"], rel=1e-9)
+    assert float(ks.grad) == pytest.approx(fd["dD_dks"], rel=1e-6)
+    assert float(uw.grad) == pytest.approx(fd["dD_duw"], rel=1e-6)
+    dirs = FDMOD.directions(len(X0np), fd["n_directions"], fd["directions_seed"])
+    g = X0.grad.numpy()
+    for d, b in zip(dirs, fd["dD_dX0_along"]):
+        assert float(np.sum(g * d)) == pytest.approx(b, abs=1e-6 * np.linalg.norm(g))
