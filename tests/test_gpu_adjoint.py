@@ -99,3 +99,16 @@ def test_autograd_function_against_oracle_fd():
     g = X0.grad.numpy()
     for d, b in zip(dirs, fd["dD_dX0_along"]):
         assert float(np.sum(g * d)) == pytest.approx(b, abs=1e-6 * np.linalg.norm(g))
+
+
+def test_adjoint_config5_against_oracle_fd(capsys):
+    """Config 5 as stated: 64^3, FP32, one 1280-face capsule of radius 8,
+    G = 0.0125, phi3, 2000 steps, checkpoints every 100 steps; the gradient of
+    the final D against FP64 central differences within 1e-3."""
+    case, _, _ = FDMOD.case("config5")
+    fd = _fd("config5")
+    g = gpu_sim(case, precision="fp32")
+    g.adjoint_forward(case.steps, 100)
+    r = g.adjoint_backward(0)
+    assert r["D"] == pytest.approx(fd["D"], rel=1e-4)
+    _check(r, fd, len(r["dD_dX0"]), 1e-3, capsys, "adjoint config5 fp32")
