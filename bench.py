@@ -427,6 +427,7 @@ def run_ours(a):
     # end to end through the C ABI with pinned host buffers
     e2e = None
     if not a.no_e2e and not batch:
+        nx, ny, nz = case.shape
         f_host = torch.empty(19 * cells, dtype=torch.float64, pin_memory=True).numpy().reshape(19, nz, ny, nx)
         x_host = torch.empty(case.n_nodes * 3, dtype=torch.float64, pin_memory=True).numpy().reshape(-1, 3)
         out_nodes = torch.empty(case.n_nodes * 3, dtype=torch.float64, pin_memory=True).numpy()
