@@ -108,7 +108,14 @@ struct iblbm_sim {
         void *mu = nullptr, *lamg = nullptr, *lamF = nullptr, *fref = nullptr;
         uint8_t *zero_flags = nullptr;
         double *uw_partial = nullptr, *gX0 = nullptr, *gks = nullptr;
-        std::vector<void *> allocs;
+        void *save_x = nullptr, *save_F = nullptr, *save_u = nullptr;
+        std::vector<void *> allocs;      // reverse-sweep buffers, kept while K is unchanged
+        std::vector<void *> ck_allocs;   // checkpoints of the last forward run
+        // captured segment sweeps keyed by (segment length, parity of the
+        // adjoint double buffers at its start); valid for graph_mesh/graph_uw
+        std::vector<std::pair<std::pair<int, int>, cudaGraphExec_t>> graphs;
+        MeshDev graph_mesh{};
+        double graph_uw = 0.0;
     } adj;
     int init_mode = 0;
 
@@ -798,7 +805,9 @@ int iblbm_destroy(iblbm_sim *s) {
     dev_free(s, s->d_scratch);
     dev_free(s, s->d_runs);
     dev_free(s, s->d_items);
+    for (auto &g : s->adj.graphs) cudaGraphExecDestroy(g.second);
     for (void *p : s->adj.allocs) dev_free(s, p);
+    for (void *p : s->adj.ck_allocs) dev_free(s, p);
     free_ring(s);
     for (void *p : s->mesh_allocs) dev_free(s, p);
     for (void *p : s->plan_allocs) dev_free(s, p);
@@ -1014,9 +1023,35 @@ int iblbm_step(iblbm_sim *s, int64_t n_steps) {
 
 namespace {
 
+void adj_drop_graphs(iblbm_sim *s) {
+    for (auto &g : s->adj.graphs) cudaGraphExecDestroy(g.second);
+    s->adj.graphs.clear();
+}
+
 void adj_free(iblbm_sim *s) {
+    adj_drop_graphs(s);
     for (void *p : s->adj.allocs) dev_free(s, p);
+    for (void *p : s->adj.ck_allocs) dev_free(s, p);
     s->adj = iblbm_sim::Adjoint{};
+}
+
+void adj_free_checkpoints(iblbm_sim *s) {
+    for (void *p : s->adj.ck_allocs) dev_free(s, p);
+    s->adj.ck_allocs.clear();
+    s->adj.ck_pop.clear();
+    s->adj.ck_x.clear();
+}
+
+void *ck_alloc(iblbm_sim *s, size_t bytes) {
+    void *p = dev_alloc(s, bytes);
+    if (p) s->adj.ck_allocs.push_back(p);
+    return p;
+}
+
+bool same_mesh(const MeshDev &a, const MeshDev &b) {
+    return a.n_nodes == b.n_nodes && a.n_faces == b.n_faces && a.n_caps == b.n_caps && a.x == b.x &&
+           a.x_lo == b.x_lo && a.F == b.F && a.u == b.u && a.adj_off == b.adj_off && a.adj == b.adj &&
+           a.tri == b.tri && a.fconst == b.fconst && a.capmod == b.capmod;
 }
 
 void *adj_alloc(iblbm_sim *s, size_t bytes) {
@@ -1061,15 +1096,18 @@ int iblbm_adjoint_forward(iblbm_sim *s, int64_t n_steps, int checkpoint_every) {
     if (rc) return rc;
     join_side(s);
     CK(cudaStreamSynchronize(s->stream));
-    adj_free(s);
+    // the reverse-sweep buffers depend on K and on the mesh size only
+    if (s->adj.K != checkpoint_every || !same_mesh(s->adj.graph_mesh, s->mesh)) adj_free(s);
+    else adj_free_checkpoints(s);
     iblbm_sim::Adjoint &A = s->adj;
+    A.ready = false;
     A.K = checkpoint_every;
     A.n = n_steps;
     A.t_start = s->steps;
     A.couette_start = (s->steps == 0 && s->init_mode == 1);
     const int64_t nck = (n_steps + A.K - 1) / A.K;
     for (int64_t c = 0; c < nck; ++c) {
-        void *p = adj_alloc(s, s->pop_bytes), *x = adj_alloc(s, pos_bytes(s));
+        void *p = ck_alloc(s, s->pop_bytes), *x = ck_alloc(s, pos_bytes(s));
         if (!p || !x) {
             adj_free(s);
             return fail(s, IBLBM_ERR_OOM, "checkpoint allocation failed");
@@ -1132,11 +1170,20 @@ int iblbm_adjoint_backward(iblbm_sim *s, int capsule_id, double *D_out, double *
         A.uw_partial = (double *)adj_alloc(s, sizeof(double) * (size_t)((s->L.ncell + 255) / 256));
         A.gX0 = (double *)adj_alloc(s, sizeof(double) * 3 * n);
         A.gks = (double *)adj_alloc(s, sizeof(double) * n);
-        ok = ok && A.mu && A.lamg && A.lamF && A.fref && A.zero_flags && A.uw_partial && A.gX0 && A.gks;
+        // the final state is restored from these afterwards
+        A.save_x = adj_alloc(s, pos_bytes(s));
+        A.save_F = adj_alloc(s, nodevec_bytes(s));
+        A.save_u = adj_alloc(s, nodevec_bytes(s));
+        ok = ok && A.mu && A.lamg && A.lamF && A.fref && A.zero_flags && A.uw_partial && A.gX0 && A.gks &&
+             A.save_x && A.save_F && A.save_u;
         if (!ok) {
-            A.tr_pop.clear();
+            adj_free(s);
             return fail(s, IBLBM_ERR_OOM, "adjoint buffer allocation failed");
         }
+        CK(cudaMemset(A.zero_flags, 0, s->flag_bytes));
+        A.graph_mesh = m;
+    }
+    {
         // reference edges of every face
         std::vector<double> fr(8 * (size_t)nf, 0.0);
         for (int f = 0; f < nf; ++f) {
@@ -1152,13 +1199,8 @@ int iblbm_adjoint_backward(iblbm_sim *s, int capsule_id, double *D_out, double *
             std::vector<float> ff(fr.begin(), fr.end());
             CK(cudaMemcpy(A.fref, ff.data(), ff.size() * 4, cudaMemcpyHostToDevice));
         }
-        CK(cudaMemset(A.zero_flags, 0, s->flag_bytes));
     }
-    // the final state is restored afterwards
-    void *save_x = adj_alloc(s, pos_bytes(s));
-    void *save_F = adj_alloc(s, nodevec_bytes(s));
-    void *save_u = adj_alloc(s, nodevec_bytes(s));
-    if (!save_x || !save_F || !save_u) return fail(s, IBLBM_ERR_OOM, "adjoint buffer allocation failed");
+    void *const save_x = A.save_x, *const save_F = A.save_F, *const save_u = A.save_u;
     CK(copy_pos_out(s, save_x));
     CK(cudaMemcpyAsync(save_F, m.F, nodevec_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
     CK(cudaMemcpyAsync(save_u, m.u, nodevec_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
@@ -1191,24 +1233,22 @@ int iblbm_adjoint_backward(iblbm_sim *s, int capsule_id, double *D_out, double *
     CK(cudaMemsetAsync(A.gks, 0, sizeof(double) * n, s->stream));
     int cur = 0;
     const int64_t nck = (int64_t)A.ck_pop.size();
-    for (int64_t seg = nck - 1; seg >= 0; --seg) {
-        const int len = (int)std::min<int64_t>(K, A.n - seg * K);
-        // recompute the segment, keeping every forward quantity of each step
-        CK(cudaMemcpyAsync(A.tr_pop[0], A.ck_pop[seg], s->pop_bytes, cudaMemcpyDeviceToDevice, s->stream));
-        CK(copy_pos_in(s, A.ck_x[seg]));
+    // recompute of one segment (every forward quantity of its steps kept),
+    // then the reverse sweep over it; enqueued on the stream
+    auto segment = [&](int len, int cur0) {
         for (int k = 0; k < len; ++k) {
-            CK(copy_pos_out(s, A.tr_x[k]));
-            CK(cudaMemsetAsync(A.tr_g[k], 0, s->vec_bytes, s->stream));
-            CK(cudaMemsetAsync(A.tr_flags[k], 0, s->flag_bytes, s->stream));
+            copy_pos_out(s, A.tr_x[k]);
+            cudaMemsetAsync(A.tr_g[k], 0, s->vec_bytes, s->stream);
+            cudaMemsetAsync(A.tr_flags[k], 0, s->flag_bytes, s->stream);
             launch_force_spread(s->prec, s->delta, s->L, m, A.tr_g[k], (uint8_t *)A.tr_flags[k], s->d_status,
                                 nullptr, nullptr, s->stream);
-            CK(cudaMemcpyAsync(A.tr_F[k], m.F, nodevec_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
+            cudaMemcpyAsync(A.tr_F[k], m.F, nodevec_bytes(s), cudaMemcpyDeviceToDevice, s->stream);
             CollideArgs a{};
             a.src = A.tr_pop[k];
             a.dst = A.tr_pop[k + 1];
             a.fcur = A.tr_g[k];
             a.flag_cur = (const uint8_t *)A.tr_flags[k];
-            a.fold = A.tr_g[k];          // never written: flag_old is all zero
+            a.fold = A.tr_g[k];  // never written: flag_old is all zero
             a.flag_old = A.zero_flags;
             a.tau = s->tau;
             a.u_wall = s->u_wall;
@@ -1217,7 +1257,7 @@ int iblbm_adjoint_backward(iblbm_sim *s, int capsule_id, double *D_out, double *
             launch_interp_advect(s->prec, s->delta, s->L, m, A.tr_pop[k + 1], A.tr_g[k], nullptr, nullptr,
                                  s->stream);
         }
-        // reverse sweep over the segment
+        int c = cur0;
         for (int k = len - 1; k >= 0; --k) {
             AdjStepArgs q{};
             q.L = s->L;
@@ -1230,10 +1270,10 @@ int iblbm_adjoint_backward(iblbm_sim *s, int capsule_id, double *D_out, double *
             q.flags = (const uint8_t *)A.tr_flags[k];
             q.F = A.tr_F[k];
             q.fref = A.fref;
-            q.lamx_in = A.lamx[cur];
-            q.lamx_out = A.lamx[1 - cur];
-            q.lam_in = A.lam[cur];
-            q.lam_out = A.lam[1 - cur];
+            q.lamx_in = A.lamx[c];
+            q.lamx_out = A.lamx[1 - c];
+            q.lam_in = A.lam[c];
+            q.lam_out = A.lam[1 - c];
             q.mu = A.mu;
             q.lamg = A.lamg;
             q.lamF = A.lamF;
@@ -1242,9 +1282,34 @@ int iblbm_adjoint_backward(iblbm_sim *s, int capsule_id, double *D_out, double *
             q.gks = A.gks;
             q.omega = 1.0 / s->tau;
             launch_adjoint_step(s->prec, s->delta, q, s->stream);
-            cur = 1 - cur;
+            c = 1 - c;
         }
-        CK(cudaGetLastError());
+    };
+    for (int64_t seg = nck - 1; seg >= 0; --seg) {
+        const int len = (int)std::min<int64_t>(K, A.n - seg * K);
+        CK(cudaMemcpyAsync(A.tr_pop[0], A.ck_pop[seg], s->pop_bytes, cudaMemcpyDeviceToDevice, s->stream));
+        CK(copy_pos_in(s, A.ck_x[seg]));
+        if (A.graph_uw != s->u_wall) {
+            adj_drop_graphs(s);
+            A.graph_uw = s->u_wall;
+        }
+        const std::pair<int, int> key(len, cur);
+        cudaGraphExec_t ge = nullptr;
+        for (auto &g : A.graphs)
+            if (g.first == key) ge = g.second;
+        if (!ge) {
+            cudaGraph_t graph = nullptr;
+            CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+            segment(len, cur);
+            cudaError_t e = cudaStreamEndCapture(s->stream, &graph);
+            if (e != cudaSuccess) return cuda_fail(s, e, "capture of the adjoint segment");
+            e = cudaGraphInstantiate(&ge, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return cuda_fail(s, e, "instantiation of the adjoint segment");
+            A.graphs.push_back({key, ge});
+        }
+        CK(cudaGraphLaunch(ge, s->stream));
+        if (len % 2) cur = 1 - cur;
     }
     if (A.couette_start) launch_adjoint_init_uw(s->prec, s->L, A.lam[cur], s->u_wall, A.uw_partial, s->stream);
     CK(cudaGetLastError());
@@ -1276,12 +1341,7 @@ int iblbm_adjoint_backward(iblbm_sim *s, int capsule_id, double *D_out, double *
     CK(copy_pos_in(s, save_x));
     CK(cudaMemcpyAsync(m.F, save_F, nodevec_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
     CK(cudaMemcpyAsync(m.u, save_u, nodevec_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
-    rc = sync_status(s);
-    for (void *p : {save_x, save_F, save_u}) {
-        A.allocs.erase(std::find(A.allocs.begin(), A.allocs.end(), p));
-        dev_free(s, p);
-    }
-    return rc;
+    return sync_status(s);
 }
 
 int iblbm_set_taylor_recording(iblbm_sim *s, int every, int ring) {
