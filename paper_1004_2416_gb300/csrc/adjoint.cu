@@ -10,8 +10,9 @@
 // they run, the transposes of: the interpolation (k_adj_interp, and the sparse
 // k_adj_correct that folds the lattice part into lam_f and lam_g), the
 // collide-and-stream (k_adj_collide), the spreading (k_adj_spread) and the
-// membrane forces (k_adj_membrane).  Forward quantities of step t (f(t),
-// f(t+1), g(t), x(t), F(t)) come from a recomputation of the step.
+// membrane forces (k_adj_membrane).  Forward quantities of step t come from a
+// recomputation of the step: x(t), F(t), g(t) and the moments (j, rho) of f(t)
+// and f(t+1), which are all the transposes need of the populations.
 #include "device_common.cuh"
 #include "ib_common.cuh"
 #include "internal.h"
@@ -82,10 +83,13 @@ __device__ __forceinline__ void node_stencil(const PosView<T> &pos, int node, T 
     b[2] = stencil_first<N>(pc[2]);
 }
 
-// density and velocity (j + g/2)/rho of a stored population set
+// Moments of the stored populations of a step, kept by the recomputation so
+// that the reverse sweep never reads populations: M = (j_x, j_y, j_z, rho - 1).
 template <typename S, typename T>
-__device__ __forceinline__ void cell_moments(const S *__restrict__ pop, long long ncell, long long cell,
-                                             T gx, T gy, T gz, T &rho, T u[3]) {
+__global__ void __launch_bounds__(256)
+    k_adj_moments(const S *__restrict__ pop, typename Vec4<T>::type *__restrict__ M, long long ncell) {
+    const long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (cell >= ncell) return;
     T drho = T(0), j[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
@@ -95,11 +99,19 @@ __device__ __forceinline__ void cell_moments(const S *__restrict__ pop, long lon
         if (q_cy(i)) j[1] += q_cy(i) > 0 ? v : -v;
         if (q_cz(i)) j[2] += q_cz(i) > 0 ? v : -v;
     }
-    rho = T(1) + drho;
+    M[cell] = typename Vec4<T>::type{j[0], j[1], j[2], drho};
+}
+
+// density and velocity (j + g/2)/rho of a cell from its stored moments
+template <typename T>
+__device__ __forceinline__ void cell_moments(const typename Vec4<T>::type *__restrict__ M, long long cell,
+                                             T gx, T gy, T gz, T &rho, T u[3]) {
+    const typename Vec4<T>::type m = M[cell];
+    rho = T(1) + m.w;
     const T inv = T(1) / rho;
-    u[0] = (j[0] + T(0.5) * gx) * inv;
-    u[1] = (j[1] + T(0.5) * gy) * inv;
-    u[2] = (j[2] + T(0.5) * gz) * inv;
+    u[0] = (m.x + T(0.5) * gx) * inv;
+    u[1] = (m.y + T(0.5) * gy) * inv;
+    u[2] = (m.z + T(0.5) * gz) * inv;
 }
 
 __device__ __forceinline__ void add_vec(float4 *f, float x, float y, float z) { add_force(f, x, y, z); }
@@ -109,9 +121,9 @@ __device__ __forceinline__ void add_vec(dvec4 *f, double x, double y, double z) 
 // lam_U = lam_x(t+1).  The lattice adjoint of u(X) is mu(X) = sum_i lam_U_i
 // delta(X - x_i) (a spreading, accumulated with atomics); the node part is
 // sum_X (lam_U_i . u(X)) grad delta.  Output lam_x(t) = lam_U + that term.
-template <int N, typename S, typename T>
+template <int N, typename T>
 __global__ void __launch_bounds__(256)
-    k_adj_interp(int n_nodes, PosView<T> pos, const S *__restrict__ pop1,
+    k_adj_interp(int n_nodes, PosView<T> pos, const typename Vec4<T>::type *__restrict__ M1,
                  const typename Vec4<T>::type *__restrict__ g, const typename Vec4<T>::type *__restrict__ lamU,
                  typename Vec4<T>::type *__restrict__ mu, typename Vec4<T>::type *__restrict__ lamx_out,
                  int nx, int ny, int nz, long long ncell) {
@@ -129,7 +141,7 @@ __global__ void __launch_bounds__(256)
         if (!c.ok) continue;
         const V4 gv = g[c.cell];
         T rho, u[3];
-        cell_moments<S, T>(pop1, ncell, c.cell, gv.x, gv.y, gv.z, rho, u);
+        cell_moments<T>(M1, c.cell, gv.x, gv.y, gv.z, rho, u);
         if (c.w != T(0)) add_vec(&mu[c.cell], lu.x * c.w, lu.y * c.w, lu.z * c.w);
         const T lu_u = lu.x * u[0] + lu.y * u[1] + lu.z * u[2];
         for (int a = 0; a < 3; ++a) acc[a] += lu_u * c.gw[a];
@@ -141,36 +153,45 @@ __global__ void __launch_bounds__(256)
 // ---- lattice part of the interpolation adjoint ------------------------------------------
 // In the force-flagged cells of step t: lam_f'(X)_j += mu . (c_j - u)/rho
 // (u and rho from f(t+1) and g(t)), lam_g(X) = mu / (2 rho); mu is cleared.
-template <typename S, typename T>
+// One warp per force flag (ftx <= 32 cells along x, fty rows); warps of clear
+// flags return at once.
+template <typename T>
 __global__ void __launch_bounds__(256)
-    k_adj_correct(const S *__restrict__ pop1, const typename Vec4<T>::type *__restrict__ g,
+    k_adj_correct(const typename Vec4<T>::type *__restrict__ M1, const typename Vec4<T>::type *__restrict__ g,
                   const uint8_t *__restrict__ flags, typename Vec4<T>::type *__restrict__ mu,
                   T *__restrict__ lam, typename Vec4<T>::type *__restrict__ lamg, Lattice L) {
     using V4 = typename Vec4<T>::type;
-    const long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (cell >= L.ncell) return;
-    const int x = (int)(cell % L.nx);
-    const long long r = cell / L.nx;
-    const int y = (int)(r % L.ny), z = (int)(r / L.ny);
-    if (!flags[((long long)z * L.nfy + y / L.fty) * L.nfx + x / L.ftx]) return;
-    const V4 gv = g[cell];
-    T rho, u[3];
-    cell_moments<S, T>(pop1, L.ncell, cell, gv.x, gv.y, gv.z, rho, u);
-    const V4 m = mu[cell];
-    const T h = T(0.5) / rho;
-    lamg[cell] = V4{m.x * h, m.y * h, m.z * h, T(0)};
-    if (m.x != T(0) || m.y != T(0) || m.z != T(0)) {
-        const T inv = T(1) / rho;
-        const T mu_u = m.x * u[0] + m.y * u[1] + m.z * u[2];
+    const long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (t >= L.ntiles || !flags[t]) return;
+    const int lane = threadIdx.x & 31;
+    const int fx = (int)(t % L.nfx);
+    const long long r = t / L.nfx;
+    const int fy = (int)(r % L.nfy), z = (int)(r / L.nfy);
+    const int x = fx * L.ftx + lane;
+    if (lane >= L.ftx || x >= L.nx) return;
+    for (int k = 0; k < L.fty; ++k) {
+        const int y = fy * L.fty + k;
+        if (y >= L.ny) break;
+        const long long cell = x + (long long)L.nx * (y + (long long)L.ny * z);
+        const V4 gv = g[cell];
+        T rho, u[3];
+        cell_moments<T>(M1, cell, gv.x, gv.y, gv.z, rho, u);
+        const V4 m = mu[cell];
+        const T h = T(0.5) / rho;
+        lamg[cell] = V4{m.x * h, m.y * h, m.z * h, T(0)};
+        if (m.x != T(0) || m.y != T(0) || m.z != T(0)) {
+            const T inv = T(1) / rho;
+            const T mu_u = m.x * u[0] + m.y * u[1] + m.z * u[2];
 #pragma unroll
-        for (int i = 0; i < 19; ++i) {
-            T mc = -mu_u;
-            if (q_cx(i)) mc += q_cx(i) > 0 ? m.x : -m.x;
-            if (q_cy(i)) mc += q_cy(i) > 0 ? m.y : -m.y;
-            if (q_cz(i)) mc += q_cz(i) > 0 ? m.z : -m.z;
-            lam[i * L.ncell + cell] += mc * inv;
+            for (int i = 0; i < 19; ++i) {
+                T mc = -mu_u;
+                if (q_cx(i)) mc += q_cx(i) > 0 ? m.x : -m.x;
+                if (q_cy(i)) mc += q_cy(i) > 0 ? m.y : -m.y;
+                if (q_cz(i)) mc += q_cz(i) > 0 ? m.z : -m.z;
+                lam[i * L.ncell + cell] += mc * inv;
+            }
+            mu[cell] = V4{};
         }
-        mu[cell] = V4{};
     }
 }
 
@@ -185,9 +206,12 @@ __global__ void __launch_bounds__(256)
 //   A_rho = sum_i a_i dfeq_i/drho,  A_u = sum_i a_i dfeq_i/du,
 //   B_u = sum_i a_i dGuo_i/du,  K = omega A_u + B_u,
 // and lam_g += K/(2 rho) + sum_i a_i dGuo_i/dg (in force-flagged cells).
-template <typename S, typename T>
+// g(t) is cleared after it is read.
+// I: unsigned type wide enough for the cell index (32-bit divisions when the
+// lattice has fewer than 2^32 cells).
+template <typename T, typename I>
 __global__ void __launch_bounds__(256)
-    k_adj_collide(const S *__restrict__ pop0, const typename Vec4<T>::type *__restrict__ g,
+    k_adj_collide(const typename Vec4<T>::type *__restrict__ M0, typename Vec4<T>::type *__restrict__ g,
                   const uint8_t *__restrict__ flags, const T *__restrict__ lam_in, T *__restrict__ lam_out,
                   typename Vec4<T>::type *__restrict__ lamg, double *__restrict__ uw_partial, Lattice L,
                   T omega) {
@@ -197,11 +221,15 @@ __global__ void __launch_bounds__(256)
     double uwg = 0.0;
     if (cell < L.ncell) {
         const int nx = L.nx, ny = L.ny, nz = L.nz;
-        const int x = (int)(cell % nx);
-        const long long r = cell / nx;
-        const int y = (int)(r % ny), z = (int)(r / ny);
-        const int xp = (x + 1 == nx) ? 0 : x + 1, xm = (x == 0) ? nx - 1 : x - 1;
-        const int yp = (y + 1 == ny) ? 0 : y + 1, ym = (y == 0) ? ny - 1 : y - 1;
+        const I c32 = (I)cell;
+        const I r = c32 / (I)nx;
+        const int x = (int)(c32 - r * (I)nx);
+        const I zq = r / (I)ny;
+        const int y = (int)(r - zq * (I)ny), z = (int)zq;
+        // offsets of the periodic neighbours in x and y, and of the planes in z
+        const long long sy = nx, sz = (long long)nx * ny;
+        const long long dxp = (x + 1 == nx) ? 1 - nx : 1, dxm = (x == 0) ? nx - 1 : -1;
+        const long long dyp = (y + 1 == ny) ? (1 - ny) * sy : sy, dym = (y == 0) ? (ny - 1) * sy : -sy;
         T a[19];
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
@@ -210,16 +238,19 @@ __global__ void __launch_bounds__(256)
                 a[i] = lam_in[q_opp(i) * L.ncell + cell];
                 if (cx) uwg += (double)a[i] * (-6.0 * q_w<double>(i) * cx * (cz > 0 ? 1.0 : -1.0));
             } else {
-                const int xt = cx > 0 ? xp : (cx < 0 ? xm : x);
-                const int yt = cy > 0 ? yp : (cy < 0 ? ym : y);
-                a[i] = lam_in[i * L.ncell + xt + (long long)nx * (yt + (long long)ny * (z + cz))];
+                const long long nb = cell + (cx > 0 ? dxp : (cx < 0 ? dxm : 0)) +
+                                     (cy > 0 ? dyp : (cy < 0 ? dym : 0)) + cz * sz;
+                a[i] = lam_in[i * L.ncell + nb];
             }
         }
         const bool flagged = flags[((long long)z * L.nfy + y / L.fty) * L.nfx + x / L.ftx] != 0;
         V4 gv{};
-        if (flagged) gv = g[cell];
+        if (flagged) {
+            gv = g[cell];
+            g[cell] = V4{};  // last reader of g(t): leave the buffer zero for the next recomputation
+        }
         T rho, u[3];
-        cell_moments<S, T>(pop0, L.ncell, cell, gv.x, gv.y, gv.z, rho, u);
+        cell_moments<T>(M0, cell, gv.x, gv.y, gv.z, rho, u);
         const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
         const T guo = T(1) - T(0.5) * omega;
         T Arho = T(0), Au[3] = {T(0), T(0), T(0)}, Bu[3] = {T(0), T(0), T(0)}, Gg[3] = {T(0), T(0), T(0)};
@@ -466,20 +497,25 @@ PosView<float> adj_view<float>(void *x, void *x_lo) {
 static unsigned node_blocks(int n) { return (unsigned)((n + 7) / 8); }
 static unsigned cell_blocks(long long n) { return (unsigned)((n + 255) / 256); }
 
-template <int N, typename S, typename T>
+template <int N, typename T>
 static void adj_step_impl(const AdjStepArgs &A, cudaStream_t s) {
     using V4 = typename Vec4<T>::type;
     const Lattice &L = A.L;
     const MeshDev &m = A.mesh;
     const PosView<T> pos = adj_view<T>(A.x, A.x_lo);
-    k_adj_interp<N, S, T><<<node_blocks(m.n_nodes), 256, 0, s>>>(
-        m.n_nodes, pos, (const S *)A.pop1, (const V4 *)A.g, (const V4 *)A.lamx_in, (V4 *)A.mu,
+    k_adj_interp<N, T><<<node_blocks(m.n_nodes), 256, 0, s>>>(
+        m.n_nodes, pos, (const V4 *)A.M1, (const V4 *)A.g, (const V4 *)A.lamx_in, (V4 *)A.mu,
         (V4 *)A.lamx_out, L.nx, L.ny, L.nz, L.ncell);
-    k_adj_correct<S, T><<<cell_blocks(L.ncell), 256, 0, s>>>(
-        (const S *)A.pop1, (const V4 *)A.g, A.flags, (V4 *)A.mu, (T *)A.lam_in, (V4 *)A.lamg, L);
-    k_adj_collide<S, T><<<cell_blocks(L.ncell), 256, 0, s>>>(
-        (const S *)A.pop0, (const V4 *)A.g, A.flags, (const T *)A.lam_in, (T *)A.lam_out, (V4 *)A.lamg,
-        A.uw_partial, L, (T)A.omega);
+    k_adj_correct<T><<<(unsigned)((L.ntiles + 7) / 8), 256, 0, s>>>(
+        (const V4 *)A.M1, (const V4 *)A.g, A.flags, (V4 *)A.mu, (T *)A.lam_in, (V4 *)A.lamg, L);
+    if (L.ncell <= 0xffffffffLL)
+        k_adj_collide<T, unsigned><<<cell_blocks(L.ncell), 256, 0, s>>>(
+            (const V4 *)A.M0, (V4 *)A.g, A.flags, (const T *)A.lam_in, (T *)A.lam_out, (V4 *)A.lamg,
+            A.uw_partial, L, (T)A.omega);
+    else
+        k_adj_collide<T, unsigned long long><<<cell_blocks(L.ncell), 256, 0, s>>>(
+            (const V4 *)A.M0, (V4 *)A.g, A.flags, (const T *)A.lam_in, (T *)A.lam_out, (V4 *)A.lamg,
+            A.uw_partial, L, (T)A.omega);
     k_adj_spread<N, T><<<node_blocks(m.n_nodes), 256, 0, s>>>(
         m.n_nodes, pos, (const V4 *)A.F, (const V4 *)A.lamg, (V4 *)A.lamF, (V4 *)A.lamx_out, L.nx, L.ny, L.nz);
     k_adj_membrane<T><<<node_blocks(m.n_nodes), 256, 0, s>>>(
@@ -487,20 +523,27 @@ static void adj_step_impl(const AdjStepArgs &A, cudaStream_t s) {
         (const V4 *)m.capmod, (const V4 *)A.F, (const V4 *)A.lamF, (V4 *)A.lamx_out, A.gX0, A.gks);
 }
 
+// Storage precision only enters through the moments; the reverse sweep runs
+// in double for the FP64 build and in float otherwise.
 void launch_adjoint_step(int prec, int delta, const AdjStepArgs &A, cudaStream_t s) {
     if (prec == kF64) {
-        if (delta == 2) adj_step_impl<2, double, double>(A, s);
-        else if (delta == 3) adj_step_impl<3, double, double>(A, s);
-        else adj_step_impl<4, double, double>(A, s);
-    } else if (prec == kF32) {
-        if (delta == 2) adj_step_impl<2, float, float>(A, s);
-        else if (delta == 3) adj_step_impl<3, float, float>(A, s);
-        else adj_step_impl<4, float, float>(A, s);
+        if (delta == 2) adj_step_impl<2, double>(A, s);
+        else if (delta == 3) adj_step_impl<3, double>(A, s);
+        else adj_step_impl<4, double>(A, s);
     } else {
-        if (delta == 2) adj_step_impl<2, __half, float>(A, s);
-        else if (delta == 3) adj_step_impl<3, __half, float>(A, s);
-        else adj_step_impl<4, __half, float>(A, s);
+        if (delta == 2) adj_step_impl<2, float>(A, s);
+        else if (delta == 3) adj_step_impl<3, float>(A, s);
+        else adj_step_impl<4, float>(A, s);
     }
+}
+
+void launch_adjoint_moments(int prec, const Lattice &L, const void *pop, void *M, cudaStream_t s) {
+    if (prec == kF64)
+        k_adj_moments<double, double><<<cell_blocks(L.ncell), 256, 0, s>>>((const double *)pop, (dvec4 *)M, L.ncell);
+    else if (prec == kF32)
+        k_adj_moments<float, float><<<cell_blocks(L.ncell), 256, 0, s>>>((const float *)pop, (float4 *)M, L.ncell);
+    else
+        k_adj_moments<__half, float><<<cell_blocks(L.ncell), 256, 0, s>>>((const __half *)pop, (float4 *)M, L.ncell);
 }
 
 void launch_adjoint_init_uw(int prec, const Lattice &L, const void *lam, double u_wall, double *partial,

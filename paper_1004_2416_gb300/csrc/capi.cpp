@@ -103,12 +103,14 @@ struct iblbm_sim {
         int64_t n = 0, t_start = 0;
         bool couette_start = false;
         std::vector<void *> ck_pop, ck_x;
-        std::vector<void *> tr_pop, tr_g, tr_flags, tr_x, tr_F;
+        void *trp[2] = {nullptr, nullptr};            // recomputation populations (ping-pong)
+        std::vector<void *> tr_M, tr_g, tr_flags, tr_x, tr_F;  // kept forward quantities of a segment
         void *lam[2] = {nullptr, nullptr}, *lamx[2] = {nullptr, nullptr};
         void *mu = nullptr, *lamg = nullptr, *lamF = nullptr, *fref = nullptr;
         uint8_t *zero_flags = nullptr;
         double *uw_partial = nullptr, *gX0 = nullptr, *gks = nullptr;
         void *save_x = nullptr, *save_F = nullptr, *save_u = nullptr;
+        bool g_dirty = true;             // tr_g may hold a force density (zeroed before use)
         std::vector<void *> allocs;      // reverse-sweep buffers, kept while K is unchanged
         std::vector<void *> ck_allocs;   // checkpoints of the last forward run
         // captured segment sweeps keyed by (segment length, parity of the
@@ -1142,12 +1144,14 @@ int iblbm_adjoint_backward(iblbm_sim *s, int capsule_id, double *D_out, double *
     const size_t vb = 4 * real_bytes(s);
     const int K = A.K;
     // reverse-sweep buffers (kept for repeated backward passes)
-    if (A.tr_pop.empty()) {
-        bool ok = true;
+    if (A.tr_M.empty()) {
+        A.trp[0] = adj_alloc(s, s->pop_bytes);
+        A.trp[1] = adj_alloc(s, s->pop_bytes);
+        bool ok = A.trp[0] && A.trp[1];
         for (int k = 0; k <= K && ok; ++k) {
-            void *p = adj_alloc(s, s->pop_bytes);
+            void *p = adj_alloc(s, 4 * real_bytes(s) * (size_t)s->L.ncell);
             ok = p != nullptr;
-            A.tr_pop.push_back(p);
+            A.tr_M.push_back(p);
         }
         for (int k = 0; k < K && ok; ++k) {
             A.tr_g.push_back(adj_alloc(s, s->vec_bytes));
@@ -1231,21 +1235,27 @@ int iblbm_adjoint_backward(iblbm_sim *s, int capsule_id, double *D_out, double *
     CK(cudaMemsetAsync(A.uw_partial, 0, sizeof(double) * nblk, s->stream));
     CK(cudaMemsetAsync(A.gX0, 0, sizeof(double) * 3 * n, s->stream));
     CK(cudaMemsetAsync(A.gks, 0, sizeof(double) * n, s->stream));
+    if (A.g_dirty)
+        for (void *p : A.tr_g) CK(cudaMemsetAsync(p, 0, s->vec_bytes, s->stream));
+    A.g_dirty = true;  // until the sweep has completed
     int cur = 0;
     const int64_t nck = (int64_t)A.ck_pop.size();
     // recompute of one segment (every forward quantity of its steps kept),
     // then the reverse sweep over it; enqueued on the stream
+    // tr_g[k] are all zero here: zeroed at allocation, and the reverse step of
+    // step k clears the cells it has read.  The collide keeps the moments of
+    // f(k) (M[k]); those of the segment's last state come from a moments pass.
     auto segment = [&](int len, int cur0) {
         for (int k = 0; k < len; ++k) {
             copy_pos_out(s, A.tr_x[k]);
-            cudaMemsetAsync(A.tr_g[k], 0, s->vec_bytes, s->stream);
             cudaMemsetAsync(A.tr_flags[k], 0, s->flag_bytes, s->stream);
-            launch_force_spread(s->prec, s->delta, s->L, m, A.tr_g[k], (uint8_t *)A.tr_flags[k], s->d_status,
+            MeshDev mk = m;
+            mk.F = A.tr_F[k];  // node forces of step k, kept for the reverse step
+            launch_force_spread(s->prec, s->delta, s->L, mk, A.tr_g[k], (uint8_t *)A.tr_flags[k], s->d_status,
                                 nullptr, nullptr, s->stream);
-            cudaMemcpyAsync(A.tr_F[k], m.F, nodevec_bytes(s), cudaMemcpyDeviceToDevice, s->stream);
             CollideArgs a{};
-            a.src = A.tr_pop[k];
-            a.dst = A.tr_pop[k + 1];
+            a.src = A.trp[k & 1];
+            a.dst = A.trp[(k + 1) & 1];
             a.fcur = A.tr_g[k];
             a.flag_cur = (const uint8_t *)A.tr_flags[k];
             a.fold = A.tr_g[k];  // never written: flag_old is all zero
@@ -1253,10 +1263,12 @@ int iblbm_adjoint_backward(iblbm_sim *s, int capsule_id, double *D_out, double *
             a.tau = s->tau;
             a.u_wall = s->u_wall;
             a.status = s->d_status;
+            a.moments = A.tr_M[k];
             launch_collide_stream(s->prec, s->L, a, s->stream);
-            launch_interp_advect(s->prec, s->delta, s->L, m, A.tr_pop[k + 1], A.tr_g[k], nullptr, nullptr,
+            launch_interp_advect(s->prec, s->delta, s->L, m, A.trp[(k + 1) & 1], A.tr_g[k], nullptr, nullptr,
                                  s->stream);
         }
+        launch_adjoint_moments(s->prec, s->L, A.trp[len & 1], A.tr_M[len], s->stream);
         int c = cur0;
         for (int k = len - 1; k >= 0; --k) {
             AdjStepArgs q{};
@@ -1264,8 +1276,8 @@ int iblbm_adjoint_backward(iblbm_sim *s, int capsule_id, double *D_out, double *
             q.mesh = m;
             q.x = A.tr_x[k];
             q.x_lo = s->prec == kF64 ? nullptr : (char *)A.tr_x[k] + (size_t)n * 16;
-            q.pop0 = A.tr_pop[k];
-            q.pop1 = A.tr_pop[k + 1];
+            q.M0 = A.tr_M[k];
+            q.M1 = A.tr_M[k + 1];
             q.g = A.tr_g[k];
             q.flags = (const uint8_t *)A.tr_flags[k];
             q.F = A.tr_F[k];
@@ -1287,7 +1299,7 @@ int iblbm_adjoint_backward(iblbm_sim *s, int capsule_id, double *D_out, double *
     };
     for (int64_t seg = nck - 1; seg >= 0; --seg) {
         const int len = (int)std::min<int64_t>(K, A.n - seg * K);
-        CK(cudaMemcpyAsync(A.tr_pop[0], A.ck_pop[seg], s->pop_bytes, cudaMemcpyDeviceToDevice, s->stream));
+        CK(cudaMemcpyAsync(A.trp[0], A.ck_pop[seg], s->pop_bytes, cudaMemcpyDeviceToDevice, s->stream));
         CK(copy_pos_in(s, A.ck_x[seg]));
         if (A.graph_uw != s->u_wall) {
             adj_drop_graphs(s);
@@ -1341,7 +1353,9 @@ int iblbm_adjoint_backward(iblbm_sim *s, int capsule_id, double *D_out, double *
     CK(copy_pos_in(s, save_x));
     CK(cudaMemcpyAsync(m.F, save_F, nodevec_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
     CK(cudaMemcpyAsync(m.u, save_u, nodevec_bytes(s), cudaMemcpyDeviceToDevice, s->stream));
-    return sync_status(s);
+    rc = sync_status(s);
+    if (rc == IBLBM_OK) A.g_dirty = false;
+    return rc;
 }
 
 int iblbm_set_taylor_recording(iblbm_sim *s, int every, int ring) {

@@ -102,6 +102,9 @@ struct CollideArgs {
     double tau;
     double u_wall;
     int *status;
+    // optional: moments (j_x, j_y, j_z, rho - 1) of f(t) per cell, Vec4 (the
+    // adjoint's recomputation keeps them); null in a plain step
+    void *moments = nullptr;
 };
 void launch_collide_stream(int prec, const Lattice &L, const CollideArgs &a, cudaStream_t s);
 // batched persistent variant: CollideArgs pointers are the concatenated buffers
@@ -137,9 +140,9 @@ struct AdjStepArgs {
     Lattice L;
     MeshDev mesh;
     void *x, *x_lo;         // stored node positions x(t) (hi/lo for float builds)
-    const void *pop0;       // f(t)
-    const void *pop1;       // f(t+1)
-    const void *g;          // force density g(t)
+    const void *M0;         // moments of f(t): Vec4 per cell (j_x, j_y, j_z, rho - 1)
+    const void *M1;         // moments of f(t+1)
+    void *g;                // force density g(t); cleared by the reverse step
     const uint8_t *flags;   // force flags of step t
     const void *F;          // node forces F(t)
     const void *fref;       // reference edges U, V per face, Vec4 [2][n_faces]
@@ -155,6 +158,8 @@ struct AdjStepArgs {
     double omega;
 };
 void launch_adjoint_step(int prec, int delta, const AdjStepArgs &A, cudaStream_t s);
+// moments (j, rho - 1) of a population set, Vec4 per cell, for the reverse sweep
+void launch_adjoint_moments(int prec, const Lattice &L, const void *pop, void *M, cudaStream_t s);
 // sum over cells of lam_f(0) . d f(0)/d u_wall for the linear-Couette start
 void launch_adjoint_init_uw(int prec, const Lattice &L, const void *lam, double u_wall, double *partial,
                             cudaStream_t s);

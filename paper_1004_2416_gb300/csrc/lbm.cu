@@ -26,7 +26,8 @@ __device__ __forceinline__ void collide_cell(const S *__restrict__ src, S *__res
                                              const typename Vec4<T>::type *__restrict__ fcur,
                                              bool has_cur, int x, int y, int z, int nx, int ny,
                                              int nz, long long ncell, T omega, T u_wall,
-                                             int *status) {
+                                             int *status,
+                                             typename Vec4<T>::type *__restrict__ moments = nullptr) {
     using V4 = typename Vec4<T>::type;
     const long long cell = x + (long long)nx * (y + (long long)ny * z);
     T g[19];
@@ -41,6 +42,7 @@ __device__ __forceinline__ void collide_cell(const S *__restrict__ src, S *__res
         if (q_cy(i)) jy += q_cy(i) > 0 ? g[i] : -g[i];
         if (q_cz(i)) jz += q_cz(i) > 0 ? g[i] : -g[i];
     }
+    if (moments) moments[cell] = V4{jx, jy, jz, drho};
     T fx = T(0), fy = T(0), fz = T(0);
     if (has_cur) {
         V4 f = fcur[cell];
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(kTileX *kTileY)
                      const uint8_t *__restrict__ flag_cur,
                      typename Vec4<T>::type *__restrict__ fold, uint8_t *__restrict__ flag_old,
                      int nx, int ny, int nz, int ntx, int nty, long long ncell, T omega,
-                     T u_wall, int *status) {
+                     T u_wall, int *status, typename Vec4<T>::type *__restrict__ moments) {
     using V4 = typename Vec4<T>::type;
     const int x = blockIdx.x * kTileX + threadIdx.x;
     const int y = blockIdx.y * kTileY + threadIdx.y;
@@ -124,7 +126,7 @@ __global__ void __launch_bounds__(kTileX *kTileY)
         if (threadIdx.x == 0 && threadIdx.y == 0) flag_old[tile] = 0;
     }
     if (!inside) return;
-    collide_cell<S, T>(src, dst, fcur, has_cur, x, y, z, nx, ny, nz, ncell, omega, u_wall, status);
+    collide_cell<S, T>(src, dst, fcur, has_cur, x, y, z, nx, ny, nz, ncell, omega, u_wall, status, moments);
 }
 
 // Batched, persistent collide-and-stream over many independent lattices
@@ -227,12 +229,13 @@ __host__ __device__ constexpr int rows_per_block() {
     return LR <= 32 ? 8 * (32 / LR) : 8 / (LR / 32);
 }
 
-template <typename S, int LR>
+// WM: also write the moments of f(t), float4 (j, rho - 1) per cell.
+template <typename S, int LR, bool WM>
 __global__ void __launch_bounds__(256, 2)
     k_collide_stream_x4(const S *__restrict__ src, S *__restrict__ dst,
                         const float4 *__restrict__ fcur, const uint8_t *__restrict__ flag_cur,
                         float4 *__restrict__ fold, uint8_t *__restrict__ flag_old, int ny, int nz,
-                        int ncell, float omega, float u_wall, int *status) {
+                        int ncell, float omega, float u_wall, int *status, float4 *__restrict__ moments) {
     constexpr int NX = 4 * LR;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nrows = ny * nz;
@@ -278,6 +281,9 @@ __global__ void __launch_bounds__(256, 2)
             if (q_cx(i)) jx += q_cx(i) > 0 ? g[i][k] : -g[i][k];
             if (q_cy(i)) jy += q_cy(i) > 0 ? g[i][k] : -g[i][k];
             if (q_cz(i)) jz += q_cz(i) > 0 ? g[i][k] : -g[i][k];
+        }
+        if constexpr (WM) {
+            if (active) moments[cell0 + k] = make_float4(jx, jy, jz, d);
         }
         fx[k] = fy[k] = fz[k] = 0.f;
         if (has_cur) {
@@ -434,9 +440,16 @@ static void collide_x4(const Lattice &L, const CollideArgs &a, cudaStream_t s) {
     constexpr int rpb = rows_per_block<LR>();
     const int nrows = L.ny * L.nz;
     const unsigned nb = (unsigned)((nrows + rpb - 1) / rpb);
-    k_collide_stream_x4<S, LR><<<nb, 256, 0, s>>>(
-        (const S *)a.src, (S *)a.dst, (const float4 *)a.fcur, a.flag_cur, (float4 *)a.fold,
-        a.flag_old, L.ny, L.nz, (int)L.ncell, (float)(1.0 / a.tau), (float)a.u_wall, a.status);
+    if (a.moments)
+        k_collide_stream_x4<S, LR, true><<<nb, 256, 0, s>>>(
+            (const S *)a.src, (S *)a.dst, (const float4 *)a.fcur, a.flag_cur, (float4 *)a.fold,
+            a.flag_old, L.ny, L.nz, (int)L.ncell, (float)(1.0 / a.tau), (float)a.u_wall, a.status,
+            (float4 *)a.moments);
+    else
+        k_collide_stream_x4<S, LR, false><<<nb, 256, 0, s>>>(
+            (const S *)a.src, (S *)a.dst, (const float4 *)a.fcur, a.flag_cur, (float4 *)a.fold,
+            a.flag_old, L.ny, L.nz, (int)L.ncell, (float)(1.0 / a.tau), (float)a.u_wall, a.status,
+            nullptr);
 }
 
 template <typename S>
@@ -461,7 +474,8 @@ static void collide_impl(const Lattice &L, const CollideArgs &a, cudaStream_t s)
     dim3 grid(L.ntx, L.nty, L.nz), block(kTileX, kTileY);
     k_collide_stream<S, T><<<grid, block, 0, s>>>(
         (const S *)a.src, (S *)a.dst, (const V4 *)a.fcur, a.flag_cur, (V4 *)a.fold, a.flag_old,
-        L.nx, L.ny, L.nz, L.ntx, L.nty, L.ncell, (T)(1.0 / a.tau), (T)a.u_wall, a.status);
+        L.nx, L.ny, L.nz, L.ntx, L.nty, L.ncell, (T)(1.0 / a.tau), (T)a.u_wall, a.status,
+        (V4 *)a.moments);
 }
 
 void launch_collide_stream(int prec, const Lattice &L, const CollideArgs &a, cudaStream_t s) {
