@@ -54,6 +54,10 @@ def _args():
     p.add_argument("--cpu-budget-s", type=float, default=20.0)
     p.add_argument("--profile-steps", type=int, default=500)
     p.add_argument("--no-adjoint", action="store_true", help="skip the config-5 adjoint timing")
+    p.add_argument("--adjoint-only", action="store_true",
+                   help="only the config-5 adjoint timing, printed as {\"adjoint\": ...}")
+    p.add_argument("--adjoint-steps", type=int, default=None,
+                   help="steps of the adjoint timing (default: the workload's 2000)")
     return p.parse_args()
 
 
@@ -308,12 +312,12 @@ def _oracle_run(case, budget_s: float, max_steps: int):
 
 # ---- adjoint timing (config 5) ---------------------------------------------------------------------
 
-def _adjoint_timing(stream):
+def _adjoint_timing(stream, steps=None):
     """Config 5 (64^3, FP32, one 1280-face capsule, phi3): 2000 steps forward with
     checkpoints every 100 steps, then the reverse sweep for dD/dk_s, dD/du_wall and
     dD/dX0; host wall-clock times of both, each ending in a synchronisation.  The
     gradient is compared with the FP64 oracle's central differences when the
-    reference file is present."""
+    reference file is present and the run has the workload's full length."""
     import importlib.util
 
     import numpy as np
@@ -322,6 +326,7 @@ def _adjoint_timing(stream):
     from paper_1004_2416_gb300 import workloads as W
 
     case = W.config5()
+    n_steps = case.steps if steps is None else max(100, 100 * (steps // 100))
     sim = _make_sim(case, stream)
     X0 = sim.get_nodes()
     sim.adjoint_forward(200, 100)  # warm-up: kernels, graphs and reverse-sweep buffers
@@ -334,23 +339,23 @@ def _adjoint_timing(stream):
 
     reset()
     t0 = time.perf_counter()
-    sim.step(case.steps)
+    sim.step(n_steps)
     sim.sync()
     plain = time.perf_counter() - t0
     reset()
     t0 = time.perf_counter()
-    sim.adjoint_forward(case.steps, 100)
+    sim.adjoint_forward(n_steps, 100)
     fwd = time.perf_counter() - t0
     t0 = time.perf_counter()
     r = sim.adjoint_backward(0)
     bwd = time.perf_counter() - t0
-    out = {"workload": case.name, "steps": case.steps, "checkpoint_every": 100,
+    out = {"workload": case.name, "steps": n_steps, "checkpoint_every": 100,
            "plain_forward_ms": round(plain * 1e3, 2), "forward_with_checkpoints_ms": round(fwd * 1e3, 2),
            "backward_ms": round(bwd * 1e3, 2), "backward_over_forward": round(bwd / plain, 3),
            "D": r["D"], "dD_dks": r["dD_dks"], "dD_duw": r["dD_duw"],
            "dD_dG": r["dD_duw"] * case.capsules[0].k_s * case.shape[2] / (2.0 * (case.tau - 0.5) / 3.0 * case.capsules[0].radius)}
     path = os.path.join(ROOT, "tests", "golden", "adjoint_fd_config5.json")
-    if os.path.exists(path):
+    if os.path.exists(path) and n_steps == case.steps:
         with open(path) as fh:
             fd = json.load(fh)
         spec = importlib.util.spec_from_file_location("mkfd", os.path.join(ROOT, "tests", "golden", "make_adjoint_fd.py"))
@@ -380,6 +385,12 @@ def run_ours(a):
 
     grp = _Group("nccl")
     torch.cuda.set_device(grp.local)
+    if a.adjoint_only:
+        out = _adjoint_timing(torch.cuda.Stream(), a.adjoint_steps)
+        grp.close()
+        if grp.rank == 0:
+            print(json.dumps({"adjoint": out}), flush=True)
+        return
     case = _workload(a)
     stream = torch.cuda.Stream()
     sim = _make_sim(case, stream)
@@ -480,7 +491,7 @@ def run_ours(a):
 
     adjoint = None
     if grp.rank == 0 and not a.no_adjoint and a.workload == "config2":
-        adjoint = _adjoint_timing(stream)
+        adjoint = _adjoint_timing(stream, a.adjoint_steps)
 
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": grp.ws,

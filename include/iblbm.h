@@ -81,7 +81,7 @@ typedef struct {
     int n_runs;        /* lattices of a batch (1 for a single lattice) */
 } iblbm_info;
 
-/* One independent lattice of a batch (see iblbm_create_batch). */
+/* One independent lattice of a batch (see iblbm_batch_create). */
 typedef struct {
     int nx, ny, nz;
     double tau;
@@ -109,7 +109,7 @@ int iblbm_create(iblbm_sim **out, int nx, int ny, int nz, double tau,
  * global over the batch.  Fluid getters of the whole lattice apply only to a
  * batch of one run; use the iblbm_get_run_* functions otherwise.  Limits: as
  * iblbm_create for each run, 1 <= n_runs <= 2^20, all cells <= 2^31 - 1. */
-int iblbm_create_batch(iblbm_sim **out, const iblbm_run_spec *runs, int n_runs,
+int iblbm_batch_create(iblbm_sim **out, const iblbm_run_spec *runs, int n_runs,
                        int precision, int delta_points, void *stream,
                        const iblbm_allocator *alloc);
 
@@ -238,6 +238,41 @@ int iblbm_adjoint_forward(iblbm_sim *sim, int64_t n_steps, int checkpoint_every)
 int iblbm_adjoint_backward(iblbm_sim *sim, int capsule_id, double *D,
                            double *dD_dks, double *dD_duw, double *dD_dX0,
                            double *dD_dx0);
+
+/* Both halves in one call, for a capsule that starts in its reference shape:
+ * advances n_steps with checkpoints every checkpoint_every steps and returns
+ * dD/dk_s (fixed C and u_wall), dD/dCa and dD/dX0 [n][3] (the reference shape,
+ * which is also the initial shape), and D if not NULL.  Ca is the reduced
+ * shear rate G = gdot eta r / k_s of Sec. III, varied through the wall speed
+ * at fixed k_s: gdot = 2 u_wall / nz, eta = (tau - 1/2) / 3, and r the mean
+ * distance of the reference nodes from their mean (the icosphere radius).
+ * Errors as the two calls above.  Synchronising. */
+int iblbm_adjoint_taylor(iblbm_sim *sim, int capsule_id, int64_t n_steps,
+                         int checkpoint_every, double *dD_dks, double *dD_dCa,
+                         double *dD_dX0, double *D);
+
+/* ---- checkpoint and restart ---------------------------------------------------
+ *
+ * A checkpoint holds the dynamic state after a completed step: the
+ * populations f(t), the force density of the last spreading with its tile
+ * flags, the node positions (with their low parts in float builds), the last
+ * node forces and velocities, the step count and the fluid start mode.  The
+ * configuration (lattice, precision, stencil, meshes, moduli, walls, tau) is
+ * not stored: a checkpoint restores only into an object created and filled
+ * with the same configuration, which restore checks (sizes, precision, node
+ * and face counts) before writing anything.
+ * iblbm_checkpoint_size gives the byte size of a checkpoint.
+ * iblbm_checkpoint_save writes it to buf: device memory (on_device = 1) or
+ * host memory (on_device = 0, pageable or pinned), owned by the caller, at
+ * least that size; iblbm_checkpoint_restore reads it back.  Layout: a 256-byte
+ * header (magic "IBLBMCK1", version, sizes), then the sections above, each at
+ * a 256-byte aligned offset, in the library's storage formats.  Errors:
+ * IBLBM_ERR_ARG for NULL pointers, a buffer on the wrong side, a bad header or
+ * a configuration mismatch; IBLBM_ERR_CUDA for a failed copy.  Both calls
+ * synchronise; a pending adjoint forward run is discarded by a restore. */
+int iblbm_checkpoint_size(iblbm_sim *sim, size_t *bytes);
+int iblbm_checkpoint_save(iblbm_sim *sim, void *buf, int on_device);
+int iblbm_checkpoint_restore(iblbm_sim *sim, const void *buf, int on_device);
 
 /* Waits for the stream and returns the first device error recorded since the
  * last call that returned it (then clears it). */

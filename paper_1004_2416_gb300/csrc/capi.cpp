@@ -85,7 +85,7 @@ struct iblbm_sim {
     unsigned long long *d_ring_count = nullptr;
     std::vector<int64_t> rec_steps;  // step number of every record enqueued
 
-    // Batch of independent runs (iblbm_create_batch): run table, work list of
+    // Batch of independent runs (iblbm_batch_create): run table, work list of
     // (run, tile) pairs for the persistent collide kernel, per-node run index.
     bool batch = false;
     std::vector<RunDesc> runs;
@@ -717,7 +717,7 @@ int iblbm_create(iblbm_sim **out, int nx, int ny, int nz, double tau, int precis
     return finish_create(s, out);
 }
 
-int iblbm_create_batch(iblbm_sim **out, const iblbm_run_spec *specs, int n_runs, int precision,
+int iblbm_batch_create(iblbm_sim **out, const iblbm_run_spec *specs, int n_runs, int precision,
                        int delta_points, void *stream, const iblbm_allocator *alloc) {
     if (!out) return IBLBM_ERR_ARG;
     *out = nullptr;
@@ -1694,6 +1694,204 @@ int iblbm_get_taylor(iblbm_sim *s, int id, double out[16]) {
     CK(cudaMemcpyAsync(r, s->plan.out + 12 * id, sizeof(r), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     taylor_from_sums(r, out);
+    return IBLBM_OK;
+}
+
+// ---- adjoint in one call ---------------------------------------------------------
+
+int iblbm_adjoint_taylor(iblbm_sim *s, int capsule_id, int64_t n_steps, int checkpoint_every, double *dD_dks,
+                         double *dD_dCa, double *dD_dX0, double *D) {
+    if (!s) return IBLBM_ERR_ARG;
+    if (capsule_id != 0 || s->caps.size() != 1) return fail(s, IBLBM_ERR_ARG, "no such capsule");
+    int rc = iblbm_adjoint_forward(s, n_steps, checkpoint_every);
+    if (rc) return rc;
+    const Capsule &c = s->caps[0];
+    const int n = c.n_nodes;
+    std::vector<double> gX0(3 * (size_t)n), gx0(3 * (size_t)n);
+    double d = 0.0, dks = 0.0, duw = 0.0;
+    rc = iblbm_adjoint_backward(s, 0, &d, &dks, &duw, gX0.data(), gx0.data());
+    if (rc) return rc;
+    // nominal radius: mean distance of the reference nodes from their mean
+    double r = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double *X = &s->X0[3 * (size_t)(c.node0 + i)];
+        const double dx = X[0] - c.origin[0], dy = X[1] - c.origin[1], dz = X[2] - c.origin[2];
+        r += std::sqrt(dx * dx + dy * dy + dz * dz);
+    }
+    r /= n;
+    const double eta = (s->tau - 0.5) / 3.0;
+    // G = (2 u_wall / nz) eta r / k_s  =>  dD/dG = dD/du_wall * nz k_s / (2 eta r)
+    if (dD_dCa) *dD_dCa = duw * s->L.nz * c.ks / (2.0 * eta * r);
+    if (dD_dks) *dD_dks = dks;
+    if (dD_dX0)
+        for (size_t k = 0; k < gX0.size(); ++k) dD_dX0[k] = gX0[k] + gx0[k];
+    if (D) *D = d;
+    return IBLBM_OK;
+}
+
+// ---- checkpoint and restart -------------------------------------------------------
+
+}  // extern "C"
+
+namespace {
+
+struct CkptHeader {
+    char magic[8];
+    int32_t version, precision, delta, n_runs;
+    int32_t nx, ny, nz, init_mode;
+    int32_t n_nodes, n_faces, n_caps, pad;
+    int64_t steps;
+    uint64_t pop_bytes, vec_bytes, flag_bytes, x_bytes, xlo_bytes, node_bytes;
+};
+static_assert(sizeof(CkptHeader) <= 256, "checkpoint header must fit its 256-byte slot");
+
+constexpr char kCkptMagic[8] = {'I', 'B', 'L', 'B', 'M', 'C', 'K', '1'};
+
+size_t ck_align(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Section offsets: header, populations, force density, flags, x, x_lo, F, u.
+struct CkptLayout {
+    size_t off[8];
+    size_t total;
+};
+
+CkptLayout ckpt_layout(const CkptHeader &h) {
+    const size_t sz[7] = {h.pop_bytes, h.vec_bytes, h.flag_bytes, h.x_bytes, h.xlo_bytes, h.node_bytes,
+                          h.node_bytes};
+    CkptLayout L;
+    L.off[0] = 0;
+    size_t o = 256;
+    for (int k = 0; k < 7; ++k) {
+        L.off[k + 1] = o;
+        o += ck_align(sz[k]);
+    }
+    L.total = o;
+    return L;
+}
+
+CkptHeader ckpt_header(const iblbm_sim *s) {
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1;
+    h.precision = s->prec;
+    h.delta = s->delta;
+    h.n_runs = s->batch ? (int32_t)s->runs.size() : 1;
+    h.nx = s->L.nx;
+    h.ny = s->L.ny;
+    h.nz = s->L.nz;
+    h.init_mode = s->init_mode;
+    h.n_nodes = s->mesh.n_nodes;
+    h.n_faces = s->mesh.n_faces;
+    h.n_caps = (int32_t)s->caps.size();
+    h.steps = s->steps;
+    h.pop_bytes = s->pop_bytes;
+    h.vec_bytes = s->vec_bytes;
+    h.flag_bytes = s->flag_bytes;
+    const size_t rb = s->prec == kF64 ? 8 : 4;
+    h.x_bytes = (size_t)s->mesh.n_nodes * 4 * rb;
+    h.xlo_bytes = s->prec == kF64 ? 0 : (size_t)s->mesh.n_nodes * 16;
+    h.node_bytes = (size_t)s->mesh.n_nodes * 4 * rb;
+    return h;
+}
+
+// buf must be device memory (on_device) or host memory (not on_device)
+int check_side(iblbm_sim *s, const void *buf, int on_device) {
+    cudaPointerAttributes at{};
+    cudaError_t e = cudaPointerGetAttributes(&at, buf);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        at.type = cudaMemoryTypeUnregistered;
+    }
+    const bool dev = at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (on_device && !dev) return fail(s, IBLBM_ERR_ARG, "on_device = 1 but the buffer is not device memory");
+    if (!on_device && at.type == cudaMemoryTypeDevice)
+        return fail(s, IBLBM_ERR_ARG, "on_device = 0 but the buffer is device memory");
+    return IBLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int iblbm_checkpoint_size(iblbm_sim *s, size_t *bytes) {
+    if (!s || !bytes) return IBLBM_ERR_ARG;
+    CK(cudaSetDevice(s->device));
+    int rc = ensure_mesh(s);
+    if (rc) return rc;
+    *bytes = ckpt_layout(ckpt_header(s)).total;
+    return IBLBM_OK;
+}
+
+int iblbm_checkpoint_save(iblbm_sim *s, void *buf, int on_device) {
+    if (!s || !buf) return IBLBM_ERR_ARG;
+    int rc = sync_status(s);
+    if (rc) return rc;
+    rc = ensure_mesh(s);
+    if (rc) return rc;
+    rc = check_side(s, buf, on_device);
+    if (rc) return rc;
+    const CkptHeader h = ckpt_header(s);
+    const CkptLayout L = ckpt_layout(h);
+    char *b = (char *)buf;
+    const void *src[7] = {s->pop[s->cur], s->force[s->cur], s->flags[s->cur], s->mesh.x, s->mesh.x_lo,
+                          s->mesh.F, s->mesh.u};
+    const size_t sz[7] = {h.pop_bytes, h.vec_bytes, h.flag_bytes, h.x_bytes, h.xlo_bytes, h.node_bytes,
+                          h.node_bytes};
+    // padding bytes (after the header and each section) are written as zeros
+    auto zero = [&](size_t off, size_t n) -> cudaError_t {
+        if (!n) return cudaSuccess;
+        if (on_device) return cudaMemsetAsync(b + off, 0, n, s->stream);
+        std::memset(b + off, 0, n);
+        return cudaSuccess;
+    };
+    CK(cudaMemcpyAsync(b, &h, sizeof(h), cudaMemcpyDefault, s->stream));
+    CK(zero(sizeof(h), 256 - sizeof(h)));
+    for (int k = 0; k < 7; ++k) {
+        if (sz[k]) CK(cudaMemcpyAsync(b + L.off[k + 1], src[k], sz[k], cudaMemcpyDefault, s->stream));
+        const size_t end = k < 6 ? L.off[k + 2] : L.total;
+        CK(zero(L.off[k + 1] + sz[k], end - L.off[k + 1] - sz[k]));
+    }
+    CK(cudaStreamSynchronize(s->stream));
+    return IBLBM_OK;
+}
+
+int iblbm_checkpoint_restore(iblbm_sim *s, const void *buf, int on_device) {
+    if (!s || !buf) return IBLBM_ERR_ARG;
+    int rc = sync_status(s);
+    if (rc) return rc;
+    rc = ensure_mesh(s);
+    if (rc) return rc;
+    rc = check_side(s, buf, on_device);
+    if (rc) return rc;
+    CkptHeader h;
+    CK(cudaMemcpy(&h, buf, sizeof(h), cudaMemcpyDefault));
+    const CkptHeader mine = ckpt_header(s);
+    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1)
+        return fail(s, IBLBM_ERR_ARG, "not a checkpoint of this library (magic or version)");
+    if (h.precision != mine.precision || h.delta != mine.delta || h.n_runs != mine.n_runs || h.nx != mine.nx ||
+        h.ny != mine.ny || h.nz != mine.nz || h.n_nodes != mine.n_nodes || h.n_faces != mine.n_faces ||
+        h.n_caps != mine.n_caps || h.pop_bytes != mine.pop_bytes || h.vec_bytes != mine.vec_bytes ||
+        h.flag_bytes != mine.flag_bytes || h.x_bytes != mine.x_bytes || h.xlo_bytes != mine.xlo_bytes ||
+        h.node_bytes != mine.node_bytes)
+        return fail(s, IBLBM_ERR_ARG, "checkpoint of a different configuration");
+    if (h.steps < 0 || (h.init_mode != 0 && h.init_mode != 1))
+        return fail(s, IBLBM_ERR_ARG, "corrupt checkpoint header");
+    const CkptLayout L = ckpt_layout(h);
+    const char *b = (const char *)buf;
+    void *dst[7] = {s->pop[s->cur], s->force[s->cur], s->flags[s->cur], s->mesh.x, s->mesh.x_lo,
+                    s->mesh.F, s->mesh.u};
+    const size_t sz[7] = {h.pop_bytes, h.vec_bytes, h.flag_bytes, h.x_bytes, h.xlo_bytes, h.node_bytes,
+                          h.node_bytes};
+    for (int k = 0; k < 7; ++k)
+        if (sz[k]) CK(cudaMemcpyAsync(dst[k], b + L.off[k + 1], sz[k], cudaMemcpyDefault, s->stream));
+    // the other force buffer is all zero between steps
+    CK(cudaMemsetAsync(s->force[1 - s->cur], 0, s->vec_bytes, s->stream));
+    CK(cudaMemsetAsync(s->flags[1 - s->cur], 0, s->flag_bytes, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->steps = h.steps;
+    s->init_mode = h.init_mode;
+    s->adj.ready = false;
     return IBLBM_OK;
 }
 

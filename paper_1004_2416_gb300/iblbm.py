@@ -100,7 +100,11 @@ _SIGS = {
     "iblbm_taylor_gradient": (_int, [_dp, _int, _i32p, _int, _dp, _dp]),
     "iblbm_adjoint_forward": (_int, [_vp, ctypes.c_int64, _int]),
     "iblbm_adjoint_backward": (_int, [_vp, _int, _dp, _dp, _dp, _dp, _dp]),
-    "iblbm_create_batch": (_int, [ctypes.POINTER(_vp), ctypes.POINTER(iblbm_run_spec), _int, _int, _int,
+    "iblbm_adjoint_taylor": (_int, [_vp, _int, ctypes.c_int64, _int, _dp, _dp, _dp, _dp]),
+    "iblbm_checkpoint_size": (_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "iblbm_checkpoint_save": (_int, [_vp, _vp, _int]),
+    "iblbm_checkpoint_restore": (_int, [_vp, _vp, _int]),
+    "iblbm_batch_create": (_int, [ctypes.POINTER(_vp), ctypes.POINTER(iblbm_run_spec), _int, _int, _int,
                                   _vp, ctypes.POINTER(iblbm_allocator)]),
     "iblbm_add_capsule_icosphere_in_run": (_int, [_vp, _int, _dbl, _dbl, _dbl, _dbl, _int, _ip]),
     "iblbm_autotune_tiles": (_int, [_vp, _int]),
@@ -131,6 +135,21 @@ def _check(rc: int, handle=None):
 
 def _d(a: np.ndarray):
     return a.ctypes.data_as(_dp)
+
+
+def _buffer(buf, need: int):
+    """(pointer, on_device) of a contiguous byte buffer: a numpy array or a torch
+    tensor on the host or the device, of at least `need` bytes."""
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"] or buf.nbytes < need:
+            raise ValueError(f"need a C-contiguous buffer of at least {need} bytes")
+        return ctypes.c_void_p(buf.ctypes.data), 0
+    if hasattr(buf, "data_ptr") and hasattr(buf, "is_cuda"):
+        nbytes = buf.numel() * buf.element_size()
+        if not buf.is_contiguous() or nbytes < need:
+            raise ValueError(f"need a contiguous buffer of at least {need} bytes")
+        return ctypes.c_void_p(buf.data_ptr()), 1 if buf.is_cuda else 0
+    raise TypeError("checkpoint buffers are numpy arrays or torch tensors")
 
 
 def _stream_handle(stream) -> int | None:
@@ -211,7 +230,7 @@ class Sim:
         arr = (iblbm_run_spec * len(runs))(*[iblbm_run_spec(int(a), int(b), int(c), float(t), float(u))
                                              for a, b, c, t, u in runs])
         h = _vp()
-        rc = iblbm_create_batch(ctypes.byref(h), arr, len(runs), prec, delta_points,
+        rc = iblbm_batch_create(ctypes.byref(h), arr, len(runs), prec, delta_points,
                                 _stream_handle(stream), None)
         if rc != IBLBM_OK:
             raise IblbmError(rc, iblbm_last_error(None).decode(errors="replace"))
@@ -403,6 +422,36 @@ class Sim:
         _check(iblbm_adjoint_backward(self._h, capsule_id, ctypes.byref(D), ctypes.byref(dks),
                                       ctypes.byref(duw), _d(gX0), _d(gx0)), self._h)
         return {"D": D.value, "dD_dks": dks.value, "dD_duw": duw.value, "dD_dX0": gX0, "dD_dx0": gx0}
+
+    def adjoint_taylor(self, n_steps: int, checkpoint_every: int, capsule_id: int = 0) -> dict:
+        """Forward run with checkpoints and reverse sweep in one call: D and its
+        derivatives with respect to k_s, the capillary number (through u_wall)
+        and the reference (= initial) shape X0."""
+        n = self.n_nodes(capsule_id)
+        D, dks, dca = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        gX0 = np.empty((n, 3), np.float64)
+        _check(iblbm_adjoint_taylor(self._h, capsule_id, int(n_steps), int(checkpoint_every), ctypes.byref(dks),
+                                    ctypes.byref(dca), _d(gX0), ctypes.byref(D)), self._h)
+        return {"D": D.value, "dD_dks": dks.value, "dD_dCa": dca.value, "dD_dX0": gX0}
+
+    def checkpoint_size(self) -> int:
+        n = ctypes.c_size_t()
+        _check(iblbm_checkpoint_size(self._h, ctypes.byref(n)), self._h)
+        return n.value
+
+    def checkpoint_save(self, buf=None):
+        """Writes a checkpoint into buf (a uint8 torch tensor on the device or a
+        numpy uint8 array on the host, at least checkpoint_size() bytes) or, with
+        buf None, into a new numpy array, which is returned."""
+        if buf is None:
+            buf = np.empty(self.checkpoint_size(), np.uint8)
+        ptr, dev = _buffer(buf, self.checkpoint_size())
+        _check(iblbm_checkpoint_save(self._h, ptr, dev), self._h)
+        return buf
+
+    def checkpoint_restore(self, buf):
+        ptr, dev = _buffer(buf, self.checkpoint_size())
+        _check(iblbm_checkpoint_restore(self._h, ptr, dev), self._h)
 
     def taylor(self, capsule_id: int = 0) -> dict:
         out = np.empty(16, np.float64)

@@ -112,3 +112,25 @@ def test_adjoint_config5_against_oracle_fd(capsys):
     r = g.adjoint_backward(0)
     assert r["D"] == pytest.approx(fd["D"], rel=1e-4)
     _check(r, fd, len(r["dD_dX0"]), 1e-3, capsys, "adjoint config5 fp32")
+
+
+def test_adjoint_taylor_one_call(capsys):
+    """The one-call entry point: dD/dCa is dD/du_wall scaled by du_wall/dG at
+    fixed k_s (G = (2 u_wall / nz) eta r / k_s), and dD/dX0 moves the reference
+    and the initial shape together, as the finite differences do."""
+    case, _, _ = FDMOD.case("small")
+    fd = _fd("small")
+    cap = case.capsules[0]
+    g = gpu_sim(case, precision="fp64")
+    r = g.adjoint_taylor(case.steps, 50)
+    eta = (case.tau - 0.5) / 3.0
+    fd_dCa = fd["dD_duw"] * case.shape[2] * cap.k_s / (2.0 * eta * cap.radius)
+    with capsys.disabled():
+        print(f"\nadjoint one call: dD/dCa {r['dD_dCa']:.8g} (fd {fd_dCa:.8g})")
+    assert r["D"] == pytest.approx(fd["D"], rel=1e-9)
+    assert r["dD_dks"] == pytest.approx(fd["dD_dks"], rel=1e-6)
+    assert r["dD_dCa"] == pytest.approx(fd_dCa, rel=1e-6)
+    dirs = FDMOD.directions(len(r["dD_dX0"]), fd["n_directions"], fd["directions_seed"])
+    gnorm = float(np.linalg.norm(r["dD_dX0"]))
+    for d, b in zip(dirs, fd["dD_dX0_along"]):
+        assert abs(float(np.sum(r["dD_dX0"] * d)) - b) <= 1e-6 * gnorm
