@@ -103,8 +103,14 @@ struct iblbm_sim {
         int64_t n = 0, t_start = 0;
         bool couette_start = false;
         std::vector<void *> ck_pop, ck_x;
-        void *trp[2] = {nullptr, nullptr};            // recomputation populations (ping-pong)
-        std::vector<void *> tr_M, tr_g, tr_flags, tr_x, tr_F;  // kept forward quantities of a segment
+        // Two sets of recomputation buffers: the segment before the one being
+        // swept backwards is recomputed into the other set on a second stream.
+        struct Trace {
+            void *pop[2] = {nullptr, nullptr};  // recomputation populations (ping-pong)
+            std::vector<void *> M, g, flags, x, F;  // kept forward quantities of a segment
+        } tr[2];
+        cudaStream_t rstream = nullptr;  // recomputation stream
+        cudaEvent_t ev_start = nullptr, ev_rec[2] = {nullptr, nullptr}, ev_rev[2] = {nullptr, nullptr};
         void *lam[2] = {nullptr, nullptr}, *lamx[2] = {nullptr, nullptr};
         void *mu = nullptr, *lamg = nullptr, *lamF = nullptr, *fref = nullptr;
         uint8_t *zero_flags = nullptr;
@@ -113,9 +119,10 @@ struct iblbm_sim {
         bool g_dirty = true;             // tr_g may hold a force density (zeroed before use)
         std::vector<void *> allocs;      // reverse-sweep buffers, kept while K is unchanged
         std::vector<void *> ck_allocs;   // checkpoints of the last forward run
-        // captured segment sweeps keyed by (segment length, parity of the
-        // adjoint double buffers at its start); valid for graph_mesh/graph_uw
-        std::vector<std::pair<std::pair<int, int>, cudaGraphExec_t>> graphs;
+        // captured recomputations (kind 0) keyed by (segment length, set) and
+        // reverse sweeps (kind 1) by (length, set, parity of the adjoint double
+        // buffers at the start); valid for graph_mesh / graph_uw
+        std::vector<std::pair<std::array<int, 4>, cudaGraphExec_t>> graphs;
         MeshDev graph_mesh{};
         double graph_uw = 0.0;
     } adj;
@@ -128,6 +135,8 @@ struct iblbm_sim {
 };
 
 namespace {
+
+void adj_free(iblbm_sim *s);
 
 int fail(iblbm_sim *s, int code, const std::string &msg) {
     if (s) s->err = msg;
@@ -807,9 +816,7 @@ int iblbm_destroy(iblbm_sim *s) {
     dev_free(s, s->d_scratch);
     dev_free(s, s->d_runs);
     dev_free(s, s->d_items);
-    for (auto &g : s->adj.graphs) cudaGraphExecDestroy(g.second);
-    for (void *p : s->adj.allocs) dev_free(s, p);
-    for (void *p : s->adj.ck_allocs) dev_free(s, p);
+    adj_free(s);
     free_ring(s);
     for (void *p : s->mesh_allocs) dev_free(s, p);
     for (void *p : s->plan_allocs) dev_free(s, p);
@@ -1031,9 +1038,14 @@ void adj_drop_graphs(iblbm_sim *s) {
 }
 
 void adj_free(iblbm_sim *s) {
+    iblbm_sim::Adjoint &A = s->adj;
+    if (A.rstream) cudaStreamSynchronize(A.rstream);
     adj_drop_graphs(s);
-    for (void *p : s->adj.allocs) dev_free(s, p);
-    for (void *p : s->adj.ck_allocs) dev_free(s, p);
+    for (void *p : A.allocs) dev_free(s, p);
+    for (void *p : A.ck_allocs) dev_free(s, p);
+    if (A.rstream) cudaStreamDestroy(A.rstream);
+    for (cudaEvent_t e : {A.ev_start, A.ev_rec[0], A.ev_rec[1], A.ev_rev[0], A.ev_rev[1]})
+        if (e) cudaEventDestroy(e);
     s->adj = iblbm_sim::Adjoint{};
 }
 
@@ -1065,21 +1077,23 @@ void *adj_alloc(iblbm_sim *s, size_t bytes) {
 size_t pos_bytes(const iblbm_sim *s) { return (size_t)s->mesh.n_nodes * 32; }  // dvec4 or hi+lo float4
 size_t nodevec_bytes(const iblbm_sim *s) { return (size_t)s->mesh.n_nodes * 4 * real_bytes(s); }
 
-cudaError_t copy_pos_out(iblbm_sim *s, void *dst) {
+cudaError_t copy_pos_out(iblbm_sim *s, void *dst, cudaStream_t st = nullptr) {
+    if (!st) st = s->stream;
     const size_t n = (size_t)s->mesh.n_nodes;
-    if (s->prec == kF64) return cudaMemcpyAsync(dst, s->mesh.x, n * 32, cudaMemcpyDeviceToDevice, s->stream);
-    cudaError_t e = cudaMemcpyAsync(dst, s->mesh.x, n * 16, cudaMemcpyDeviceToDevice, s->stream);
+    if (s->prec == kF64) return cudaMemcpyAsync(dst, s->mesh.x, n * 32, cudaMemcpyDeviceToDevice, st);
+    cudaError_t e = cudaMemcpyAsync(dst, s->mesh.x, n * 16, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync((char *)dst + n * 16, s->mesh.x_lo, n * 16, cudaMemcpyDeviceToDevice, s->stream);
+        e = cudaMemcpyAsync((char *)dst + n * 16, s->mesh.x_lo, n * 16, cudaMemcpyDeviceToDevice, st);
     return e;
 }
 
-cudaError_t copy_pos_in(iblbm_sim *s, const void *src) {
+cudaError_t copy_pos_in(iblbm_sim *s, const void *src, cudaStream_t st = nullptr) {
+    if (!st) st = s->stream;
     const size_t n = (size_t)s->mesh.n_nodes;
-    if (s->prec == kF64) return cudaMemcpyAsync(s->mesh.x, src, n * 32, cudaMemcpyDeviceToDevice, s->stream);
-    cudaError_t e = cudaMemcpyAsync(s->mesh.x, src, n * 16, cudaMemcpyDeviceToDevice, s->stream);
+    if (s->prec == kF64) return cudaMemcpyAsync(s->mesh.x, src, n * 32, cudaMemcpyDeviceToDevice, st);
+    cudaError_t e = cudaMemcpyAsync(s->mesh.x, src, n * 16, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s->mesh.x_lo, (const char *)src + n * 16, n * 16, cudaMemcpyDeviceToDevice, s->stream);
+        e = cudaMemcpyAsync(s->mesh.x_lo, (const char *)src + n * 16, n * 16, cudaMemcpyDeviceToDevice, st);
     return e;
 }
 
@@ -1144,21 +1158,24 @@ int iblbm_adjoint_backward(iblbm_sim *s, int capsule_id, double *D_out, double *
     const size_t vb = 4 * real_bytes(s);
     const int K = A.K;
     // reverse-sweep buffers (kept for repeated backward passes)
-    if (A.tr_M.empty()) {
-        A.trp[0] = adj_alloc(s, s->pop_bytes);
-        A.trp[1] = adj_alloc(s, s->pop_bytes);
-        bool ok = A.trp[0] && A.trp[1];
-        for (int k = 0; k <= K && ok; ++k) {
-            void *p = adj_alloc(s, 4 * real_bytes(s) * (size_t)s->L.ncell);
-            ok = p != nullptr;
-            A.tr_M.push_back(p);
-        }
-        for (int k = 0; k < K && ok; ++k) {
-            A.tr_g.push_back(adj_alloc(s, s->vec_bytes));
-            A.tr_flags.push_back(adj_alloc(s, s->flag_bytes));
-            A.tr_x.push_back(adj_alloc(s, pos_bytes(s)));
-            A.tr_F.push_back(adj_alloc(s, nodevec_bytes(s)));
-            ok = A.tr_g.back() && A.tr_flags.back() && A.tr_x.back() && A.tr_F.back();
+    if (A.tr[0].M.empty()) {
+        bool ok = true;
+        for (auto &T : A.tr) {
+            T.pop[0] = adj_alloc(s, s->pop_bytes);
+            T.pop[1] = adj_alloc(s, s->pop_bytes);
+            ok = ok && T.pop[0] && T.pop[1];
+            for (int k = 0; k <= K && ok; ++k) {
+                void *p = adj_alloc(s, 4 * real_bytes(s) * (size_t)s->L.ncell);
+                ok = p != nullptr;
+                T.M.push_back(p);
+            }
+            for (int k = 0; k < K && ok; ++k) {
+                T.g.push_back(adj_alloc(s, s->vec_bytes));
+                T.flags.push_back(adj_alloc(s, s->flag_bytes));
+                T.x.push_back(adj_alloc(s, pos_bytes(s)));
+                T.F.push_back(adj_alloc(s, nodevec_bytes(s)));
+                ok = T.g.back() && T.flags.back() && T.x.back() && T.F.back();
+            }
         }
         const size_t lb = 19 * real_bytes(s) * (size_t)s->L.ncell;
         for (int k = 0; k < 2 && ok; ++k) {
@@ -1184,6 +1201,9 @@ int iblbm_adjoint_backward(iblbm_sim *s, int capsule_id, double *D_out, double *
             adj_free(s);
             return fail(s, IBLBM_ERR_OOM, "adjoint buffer allocation failed");
         }
+        CK(cudaStreamCreateWithFlags(&A.rstream, cudaStreamNonBlocking));
+        for (cudaEvent_t *e : {&A.ev_start, &A.ev_rec[0], &A.ev_rec[1], &A.ev_rev[0], &A.ev_rev[1]})
+            CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
         CK(cudaMemset(A.zero_flags, 0, s->flag_bytes));
         A.graph_mesh = m;
     }
@@ -1236,51 +1256,60 @@ int iblbm_adjoint_backward(iblbm_sim *s, int capsule_id, double *D_out, double *
     CK(cudaMemsetAsync(A.gX0, 0, sizeof(double) * 3 * n, s->stream));
     CK(cudaMemsetAsync(A.gks, 0, sizeof(double) * n, s->stream));
     if (A.g_dirty)
-        for (void *p : A.tr_g) CK(cudaMemsetAsync(p, 0, s->vec_bytes, s->stream));
+        for (auto &T : A.tr)
+            for (void *p : T.g) CK(cudaMemsetAsync(p, 0, s->vec_bytes, s->stream));
     A.g_dirty = true;  // until the sweep has completed
-    int cur = 0;
+    if (A.graph_uw != s->u_wall) {
+        adj_drop_graphs(s);
+        A.graph_uw = s->u_wall;
+    }
     const int64_t nck = (int64_t)A.ck_pop.size();
-    // recompute of one segment (every forward quantity of its steps kept),
-    // then the reverse sweep over it; enqueued on the stream
-    // tr_g[k] are all zero here: zeroed at allocation, and the reverse step of
-    // step k clears the cells it has read.  The collide keeps the moments of
-    // f(k) (M[k]); those of the segment's last state come from a moments pass.
-    auto segment = [&](int len, int cur0) {
+    // Recomputation of one segment into trace set b on the recomputation
+    // stream: every forward quantity of its steps is kept.  The force
+    // densities T.g[k] are all zero here: zeroed at allocation, and the reverse
+    // step of step k clears the cells it has read.  The collide keeps the
+    // moments of f(k) (M[k]); those of the segment's last state come from a
+    // moments pass.  Only this stream moves the mesh positions.
+    auto recompute = [&](int len, int b, cudaStream_t st) {
+        const iblbm_sim::Adjoint::Trace &T = A.tr[b];
         for (int k = 0; k < len; ++k) {
-            copy_pos_out(s, A.tr_x[k]);
-            cudaMemsetAsync(A.tr_flags[k], 0, s->flag_bytes, s->stream);
+            copy_pos_out(s, T.x[k], st);
+            cudaMemsetAsync(T.flags[k], 0, s->flag_bytes, st);
             MeshDev mk = m;
-            mk.F = A.tr_F[k];  // node forces of step k, kept for the reverse step
-            launch_force_spread(s->prec, s->delta, s->L, mk, A.tr_g[k], (uint8_t *)A.tr_flags[k], s->d_status,
-                                nullptr, nullptr, s->stream);
+            mk.F = T.F[k];  // node forces of step k, kept for the reverse step
+            launch_force_spread(s->prec, s->delta, s->L, mk, T.g[k], (uint8_t *)T.flags[k], s->d_status,
+                                nullptr, nullptr, st);
             CollideArgs a{};
-            a.src = A.trp[k & 1];
-            a.dst = A.trp[(k + 1) & 1];
-            a.fcur = A.tr_g[k];
-            a.flag_cur = (const uint8_t *)A.tr_flags[k];
-            a.fold = A.tr_g[k];  // never written: flag_old is all zero
+            a.src = T.pop[k & 1];
+            a.dst = T.pop[(k + 1) & 1];
+            a.fcur = T.g[k];
+            a.flag_cur = (const uint8_t *)T.flags[k];
+            a.fold = T.g[k];  // never written: flag_old is all zero
             a.flag_old = A.zero_flags;
             a.tau = s->tau;
             a.u_wall = s->u_wall;
             a.status = s->d_status;
-            a.moments = A.tr_M[k];
-            launch_collide_stream(s->prec, s->L, a, s->stream);
-            launch_interp_advect(s->prec, s->delta, s->L, m, A.trp[(k + 1) & 1], A.tr_g[k], nullptr, nullptr,
-                                 s->stream);
+            a.moments = T.M[k];
+            launch_collide_stream(s->prec, s->L, a, st);
+            launch_interp_advect(s->prec, s->delta, s->L, m, T.pop[(k + 1) & 1], T.g[k], nullptr, nullptr, st);
         }
-        launch_adjoint_moments(s->prec, s->L, A.trp[len & 1], A.tr_M[len], s->stream);
+        launch_adjoint_moments(s->prec, s->L, T.pop[len & 1], T.M[len], st);
+    };
+    // reverse sweep over a segment kept in set b, on the main stream
+    auto reverse = [&](int len, int b, int cur0) {
+        const iblbm_sim::Adjoint::Trace &T = A.tr[b];
         int c = cur0;
         for (int k = len - 1; k >= 0; --k) {
             AdjStepArgs q{};
             q.L = s->L;
             q.mesh = m;
-            q.x = A.tr_x[k];
-            q.x_lo = s->prec == kF64 ? nullptr : (char *)A.tr_x[k] + (size_t)n * 16;
-            q.M0 = A.tr_M[k];
-            q.M1 = A.tr_M[k + 1];
-            q.g = A.tr_g[k];
-            q.flags = (const uint8_t *)A.tr_flags[k];
-            q.F = A.tr_F[k];
+            q.x = T.x[k];
+            q.x_lo = s->prec == kF64 ? nullptr : (char *)T.x[k] + (size_t)n * 16;
+            q.M0 = T.M[k];
+            q.M1 = T.M[k + 1];
+            q.g = T.g[k];
+            q.flags = (const uint8_t *)T.flags[k];
+            q.F = T.F[k];
             q.fref = A.fref;
             q.lamx_in = A.lamx[c];
             q.lamx_out = A.lamx[1 - c];
@@ -1297,30 +1326,57 @@ int iblbm_adjoint_backward(iblbm_sim *s, int capsule_id, double *D_out, double *
             c = 1 - c;
         }
     };
-    for (int64_t seg = nck - 1; seg >= 0; --seg) {
-        const int len = (int)std::min<int64_t>(K, A.n - seg * K);
-        CK(cudaMemcpyAsync(A.trp[0], A.ck_pop[seg], s->pop_bytes, cudaMemcpyDeviceToDevice, s->stream));
-        CK(copy_pos_in(s, A.ck_x[seg]));
-        if (A.graph_uw != s->u_wall) {
-            adj_drop_graphs(s);
-            A.graph_uw = s->u_wall;
-        }
-        const std::pair<int, int> key(len, cur);
+    // launch of a captured graph of either kind (captured on first use)
+    auto run_graph = [&](int kind, int len, int b, int cur0, cudaStream_t st) -> int {
+        const std::array<int, 4> key{kind, len, b, cur0};
         cudaGraphExec_t ge = nullptr;
         for (auto &g : A.graphs)
             if (g.first == key) ge = g.second;
         if (!ge) {
             cudaGraph_t graph = nullptr;
-            CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-            segment(len, cur);
-            cudaError_t e = cudaStreamEndCapture(s->stream, &graph);
+            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            if (kind == 0) recompute(len, b, st);
+            else reverse(len, b, cur0);
+            cudaError_t e = cudaStreamEndCapture(st, &graph);
             if (e != cudaSuccess) return cuda_fail(s, e, "capture of the adjoint segment");
             e = cudaGraphInstantiate(&ge, graph, 0);
             cudaGraphDestroy(graph);
             if (e != cudaSuccess) return cuda_fail(s, e, "instantiation of the adjoint segment");
             A.graphs.push_back({key, ge});
         }
-        CK(cudaGraphLaunch(ge, s->stream));
+        CK(cudaGraphLaunch(ge, st));
+        return IBLBM_OK;
+    };
+    auto seg_len = [&](int64_t seg) { return (int)std::min<int64_t>(K, A.n - seg * K); };
+    // recomputation of segment seg into set b: its checkpoint, then the graph
+    auto enqueue_recompute = [&](int64_t seg, int b) -> int {
+        cudaStream_t st = A.rstream;
+        CK(cudaMemcpyAsync(A.tr[b].pop[0], A.ck_pop[seg], s->pop_bytes, cudaMemcpyDeviceToDevice, st));
+        CK(copy_pos_in(s, A.ck_x[seg], st));
+        int r = run_graph(0, seg_len(seg), b, 0, st);
+        if (r) return r;
+        CK(cudaEventRecord(A.ev_rec[b], st));
+        return IBLBM_OK;
+    };
+    // everything enqueued so far (saved final state, zeroed buffers) comes first
+    CK(cudaEventRecord(A.ev_start, s->stream));
+    CK(cudaStreamWaitEvent(A.rstream, A.ev_start, 0));
+    int cur = 0;
+    rc = enqueue_recompute(nck - 1, 0);
+    if (rc) return rc;
+    for (int64_t seg = nck - 1; seg >= 0; --seg) {
+        const int b = (int)((nck - 1 - seg) & 1);
+        if (seg > 0) {
+            // the other set is free once the sweep of segment seg + 1 is done
+            if (seg + 1 < nck) CK(cudaStreamWaitEvent(A.rstream, A.ev_rev[1 - b], 0));
+            rc = enqueue_recompute(seg - 1, 1 - b);
+            if (rc) return rc;
+        }
+        CK(cudaStreamWaitEvent(s->stream, A.ev_rec[b], 0));
+        const int len = seg_len(seg);
+        rc = run_graph(1, len, b, cur, s->stream);
+        if (rc) return rc;
+        CK(cudaEventRecord(A.ev_rev[b], s->stream));
         if (len % 2) cur = 1 - cur;
     }
     if (A.couette_start) launch_adjoint_init_uw(s->prec, s->L, A.lam[cur], s->u_wall, A.uw_partial, s->stream);
