@@ -7,10 +7,10 @@
 //   F = F(x; X0, k_s),  g = S(x) F,  f' = L(f, g; u_w),
 //   U_i = sum_X u(X; f', g) delta(X - x_i),  x' = x + U,
 // with u = (sum_i c_i f'_i + g/2)/rho.  The kernels below are, in the order
-// they run, the transposes of: the interpolation (k_adj_interp, and the sparse
-// k_adj_correct that folds the lattice part into lam_f and lam_g), the
-// collide-and-stream (k_adj_collide), the spreading (k_adj_spread) and the
-// membrane forces (k_adj_membrane).  Forward quantities of step t come from a
+// they run, the transposes of: the interpolation (k_adj_interp, which also
+// adds its lattice part to lam_f and lam_g), the collide-and-stream
+// (k_adj_collide), the spreading (k_adj_spread) and the membrane forces
+// (k_adj_membrane).  Forward quantities of step t come from a
 // recomputation of the step: x(t), F(t), g(t) and the moments (j, rho) of f(t)
 // and f(t+1), which are all the transposes need of the populations.
 #include "device_common.cuh"
@@ -118,15 +118,20 @@ __device__ __forceinline__ void add_vec(float4 *f, float x, float y, float z) { 
 __device__ __forceinline__ void add_vec(dvec4 *f, double x, double y, double z) { add_force(f, x, y, z); }
 
 // ---- transpose of the interpolation U_i = sum_X u(X) delta(X - x_i) ----------------------
-// lam_U = lam_x(t+1).  The lattice adjoint of u(X) is mu(X) = sum_i lam_U_i
-// delta(X - x_i) (a spreading, accumulated with atomics); the node part is
-// sum_X (lam_U_i . u(X)) grad delta.  Output lam_x(t) = lam_U + that term.
+// lam_U = lam_x(t+1).  The node part is sum_X (lam_U_i . u(X)) grad delta, so
+// lam_x(t) = lam_U + that term.  The lattice adjoint of u(X) is
+// m(X) = sum_i lam_U_i delta(X - x_i); through u = (j + g/2)/rho it reaches
+// the populations after the step, lam_f'(X)_j += m . (c_j - u)/rho, and the
+// force density, lam_g(X) = m / (2 rho).  Both are linear in m, so every
+// node adds its own share with atomics: P = lam_U w / rho, s = P . u,
+// lam_f'(X)_j += P . c_j - s and mu(X) += P / 2 (the part of lam_g, which the
+// collide adjoint picks up and clears).
 template <int N, typename T>
 __global__ void __launch_bounds__(256)
     k_adj_interp(int n_nodes, PosView<T> pos, const typename Vec4<T>::type *__restrict__ M1,
                  const typename Vec4<T>::type *__restrict__ g, const typename Vec4<T>::type *__restrict__ lamU,
-                 typename Vec4<T>::type *__restrict__ mu, typename Vec4<T>::type *__restrict__ lamx_out,
-                 int nx, int ny, int nz, long long ncell) {
+                 typename Vec4<T>::type *__restrict__ mu, T *__restrict__ lam,
+                 typename Vec4<T>::type *__restrict__ lamx_out, int nx, int ny, int nz, long long ncell) {
     using V4 = typename Vec4<T>::type;
     const int lane = threadIdx.x & 31;
     const int node = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
@@ -142,57 +147,25 @@ __global__ void __launch_bounds__(256)
         const V4 gv = g[c.cell];
         T rho, u[3];
         cell_moments<T>(M1, c.cell, gv.x, gv.y, gv.z, rho, u);
-        if (c.w != T(0)) add_vec(&mu[c.cell], lu.x * c.w, lu.y * c.w, lu.z * c.w);
+        if (c.w != T(0)) {
+            const T wr = c.w / rho;
+            const T P[3] = {lu.x * wr, lu.y * wr, lu.z * wr};
+            const T sP = P[0] * u[0] + P[1] * u[1] + P[2] * u[2];
+            add_vec(&mu[c.cell], T(0.5) * P[0], T(0.5) * P[1], T(0.5) * P[2]);
+#pragma unroll
+            for (int j = 0; j < 19; ++j) {
+                T v = -sP;
+                if (q_cx(j)) v += q_cx(j) > 0 ? P[0] : -P[0];
+                if (q_cy(j)) v += q_cy(j) > 0 ? P[1] : -P[1];
+                if (q_cz(j)) v += q_cz(j) > 0 ? P[2] : -P[2];
+                atomicAdd(lam + j * ncell + c.cell, v);
+            }
+        }
         const T lu_u = lu.x * u[0] + lu.y * u[1] + lu.z * u[2];
         for (int a = 0; a < 3; ++a) acc[a] += lu_u * c.gw[a];
     }
     for (int a = 0; a < 3; ++a) acc[a] = warp_sum(acc[a]);
     if (lane == 0) lamx_out[node] = V4{lu.x + acc[0], lu.y + acc[1], lu.z + acc[2], T(0)};
-}
-
-// ---- lattice part of the interpolation adjoint ------------------------------------------
-// In the force-flagged cells of step t: lam_f'(X)_j += mu . (c_j - u)/rho
-// (u and rho from f(t+1) and g(t)), lam_g(X) = mu / (2 rho); mu is cleared.
-// One warp per force flag (ftx <= 32 cells along x, fty rows); warps of clear
-// flags return at once.
-template <typename T>
-__global__ void __launch_bounds__(256)
-    k_adj_correct(const typename Vec4<T>::type *__restrict__ M1, const typename Vec4<T>::type *__restrict__ g,
-                  const uint8_t *__restrict__ flags, typename Vec4<T>::type *__restrict__ mu,
-                  T *__restrict__ lam, typename Vec4<T>::type *__restrict__ lamg, Lattice L) {
-    using V4 = typename Vec4<T>::type;
-    const long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    if (t >= L.ntiles || !flags[t]) return;
-    const int lane = threadIdx.x & 31;
-    const int fx = (int)(t % L.nfx);
-    const long long r = t / L.nfx;
-    const int fy = (int)(r % L.nfy), z = (int)(r / L.nfy);
-    const int x = fx * L.ftx + lane;
-    if (lane >= L.ftx || x >= L.nx) return;
-    for (int k = 0; k < L.fty; ++k) {
-        const int y = fy * L.fty + k;
-        if (y >= L.ny) break;
-        const long long cell = x + (long long)L.nx * (y + (long long)L.ny * z);
-        const V4 gv = g[cell];
-        T rho, u[3];
-        cell_moments<T>(M1, cell, gv.x, gv.y, gv.z, rho, u);
-        const V4 m = mu[cell];
-        const T h = T(0.5) / rho;
-        lamg[cell] = V4{m.x * h, m.y * h, m.z * h, T(0)};
-        if (m.x != T(0) || m.y != T(0) || m.z != T(0)) {
-            const T inv = T(1) / rho;
-            const T mu_u = m.x * u[0] + m.y * u[1] + m.z * u[2];
-#pragma unroll
-            for (int i = 0; i < 19; ++i) {
-                T mc = -mu_u;
-                if (q_cx(i)) mc += q_cx(i) > 0 ? m.x : -m.x;
-                if (q_cy(i)) mc += q_cy(i) > 0 ? m.y : -m.y;
-                if (q_cz(i)) mc += q_cz(i) > 0 ? m.z : -m.z;
-                lam[i * L.ncell + cell] += mc * inv;
-            }
-            mu[cell] = V4{};
-        }
-    }
 }
 
 // ---- transpose of the collide-and-stream -----------------------------------------------
@@ -205,7 +178,12 @@ __global__ void __launch_bounds__(256)
 //   lam_j = (1 - omega) a_j + omega A_rho + K . (c_j - u)/rho,
 //   A_rho = sum_i a_i dfeq_i/drho,  A_u = sum_i a_i dfeq_i/du,
 //   B_u = sum_i a_i dGuo_i/du,  K = omega A_u + B_u,
-// and lam_g += K/(2 rho) + sum_i a_i dGuo_i/dg (in force-flagged cells).
+// and lam_g = mu + K/(2 rho) + sum_i a_i dGuo_i/dg in force-flagged cells
+// (mu: the interpolation adjoint's part).
+// Every one of these sums is a linear form in the weighted moments
+// S0 = sum w a, S1 = sum w a c, S2 = sum w a c c^T of the pulled adjoints
+// (f_eq and the Guo term are quadratic in c), and sum a dGuo/dg equals A_u,
+// so the kernel gathers the 19 adjoints once and forms the 10 moments.
 // g(t) is cleared after it is read.
 // I: unsigned type wide enough for the cell index (32-bit divisions when the
 // lattice has fewer than 2^32 cells).
@@ -213,81 +191,100 @@ template <typename T, typename I>
 __global__ void __launch_bounds__(256)
     k_adj_collide(const typename Vec4<T>::type *__restrict__ M0, typename Vec4<T>::type *__restrict__ g,
                   const uint8_t *__restrict__ flags, const T *__restrict__ lam_in, T *__restrict__ lam_out,
-                  typename Vec4<T>::type *__restrict__ lamg, double *__restrict__ uw_partial, Lattice L,
-                  T omega) {
+                  typename Vec4<T>::type *__restrict__ mu, typename Vec4<T>::type *__restrict__ lamg,
+                  double *__restrict__ uw_partial, Lattice L, T omega) {
     using V4 = typename Vec4<T>::type;
     __shared__ double red[8];
     const long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     double uwg = 0.0;
     if (cell < L.ncell) {
         const int nx = L.nx, ny = L.ny, nz = L.nz;
-        const I c32 = (I)cell;
-        const I r = c32 / (I)nx;
-        const int x = (int)(c32 - r * (I)nx);
+        const I c = (I)cell;
+        const I r = c / (I)nx;
+        const int x = (int)(c - r * (I)nx);
         const I zq = r / (I)ny;
         const int y = (int)(r - zq * (I)ny), z = (int)zq;
-        // offsets of the periodic neighbours in x and y, and of the planes in z
-        const long long sy = nx, sz = (long long)nx * ny;
-        const long long dxp = (x + 1 == nx) ? 1 - nx : 1, dxm = (x == 0) ? nx - 1 : -1;
-        const long long dyp = (y + 1 == ny) ? (1 - ny) * sy : sy, dym = (y == 0) ? (ny - 1) * sy : -sy;
+        // offsets of the periodic neighbours in x and y and of the planes in z
+        // (unsigned wrap-around: every sum lands inside the lattice)
+        const I sy = (I)nx, sz = (I)nx * (I)ny;
+        const I dxp = (x + 1 == nx) ? (I)1 - (I)nx : (I)1, dxm = (x == 0) ? (I)nx - (I)1 : ~(I)0;
+        const I dyp = (y + 1 == ny) ? sy - sz : sy, dym = (y == 0) ? sz - sy : (I)0 - sy;
         T a[19];
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
             const int cx = q_cx(i), cy = q_cy(i), cz = q_cz(i);
             if ((cz > 0 && z + 1 == nz) || (cz < 0 && z == 0)) {
-                a[i] = lam_in[q_opp(i) * L.ncell + cell];
+                a[i] = (lam_in + q_opp(i) * L.ncell)[c];
                 if (cx) uwg += (double)a[i] * (-6.0 * q_w<double>(i) * cx * (cz > 0 ? 1.0 : -1.0));
             } else {
-                const long long nb = cell + (cx > 0 ? dxp : (cx < 0 ? dxm : 0)) +
-                                     (cy > 0 ? dyp : (cy < 0 ? dym : 0)) + cz * sz;
-                a[i] = lam_in[i * L.ncell + nb];
+                I nb = c;
+                if (cx) nb += cx > 0 ? dxp : dxm;
+                if (cy) nb += cy > 0 ? dyp : dym;
+                if (cz) nb += cz > 0 ? sz : (I)0 - sz;
+                a[i] = (lam_in + i * L.ncell)[nb];
             }
         }
-        const bool flagged = flags[((long long)z * L.nfy + y / L.fty) * L.nfx + x / L.ftx] != 0;
+        const bool flagged = flags[((I)z * (I)L.nfy + (I)(y / L.fty)) * (I)L.nfx + (I)(x / L.ftx)] != 0;
         V4 gv{};
         if (flagged) {
-            gv = g[cell];
-            g[cell] = V4{};  // last reader of g(t): leave the buffer zero for the next recomputation
+            gv = g[c];
+            g[c] = V4{};  // last reader of g(t): leave the buffer zero for the next recomputation
         }
         T rho, u[3];
-        cell_moments<T>(M0, cell, gv.x, gv.y, gv.z, rho, u);
-        const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-        const T guo = T(1) - T(0.5) * omega;
-        T Arho = T(0), Au[3] = {T(0), T(0), T(0)}, Bu[3] = {T(0), T(0), T(0)}, Gg[3] = {T(0), T(0), T(0)};
+        cell_moments<T>(M0, (long long)c, gv.x, gv.y, gv.z, rho, u);
+        // weighted moments of the pulled adjoints: S0 = sum w a, S1 = sum w a c,
+        // S2 = sum w a c c^T (xx, yy, zz, xy, xz, yz)
+        T S0 = T(0), S1[3] = {T(0), T(0), T(0)}, S2[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
-            const T c[3] = {T(q_cx(i)), T(q_cy(i)), T(q_cz(i))};
+            const int cx = q_cx(i), cy = q_cy(i), cz = q_cz(i);
             const T aw = a[i] * q_w<T>(i);
-            const T cu = c[0] * u[0] + c[1] * u[1] + c[2] * u[2];
-            const T cg = c[0] * gv.x + c[1] * gv.y + c[2] * gv.z;
-            Arho += aw * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * uu);
-            for (int d = 0; d < 3; ++d) {
-                Au[d] += aw * (T(3) * c[d] + T(9) * cu * c[d] - T(3) * u[d]);
-                if (flagged) {
-                    const T gd = d == 0 ? gv.x : (d == 1 ? gv.y : gv.z);
-                    Bu[d] += aw * (T(-3) * gd + T(9) * cg * c[d]);
-                    Gg[d] += aw * (T(3) * (c[d] - u[d]) + T(9) * cu * c[d]);
-                }
-            }
+            S0 += aw;
+            if (cx) { S1[0] += cx > 0 ? aw : -aw; S2[0] += aw; }
+            if (cy) { S1[1] += cy > 0 ? aw : -aw; S2[1] += aw; }
+            if (cz) { S1[2] += cz > 0 ? aw : -aw; S2[2] += aw; }
+            if (cx && cy) S2[3] += cx * cy > 0 ? aw : -aw;
+            if (cx && cz) S2[4] += cx * cz > 0 ? aw : -aw;
+            if (cy && cz) S2[5] += cy * cz > 0 ? aw : -aw;
         }
-        T K[3];
-        for (int d = 0; d < 3; ++d) K[d] = omega * rho * Au[d] + guo * Bu[d];
+        const T S2u[3] = {S2[0] * u[0] + S2[3] * u[1] + S2[4] * u[2],
+                          S2[3] * u[0] + S2[1] * u[1] + S2[5] * u[2],
+                          S2[4] * u[0] + S2[5] * u[1] + S2[2] * u[2]};
+        const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+        // A_rho = sum a dfeq/drho, A_u = sum a dfeq/du (= sum a dGuo/dg as well)
+        const T Arho = S0 * (T(1) - T(1.5) * uu) + T(3) * (S1[0] * u[0] + S1[1] * u[1] + S1[2] * u[2]) +
+                       T(4.5) * (u[0] * S2u[0] + u[1] * S2u[1] + u[2] * S2u[2]);
+        T Au[3], K[3];
+        const T guo = T(1) - T(0.5) * omega;
+        for (int d = 0; d < 3; ++d) Au[d] = T(3) * S1[d] + T(9) * S2u[d] - T(3) * u[d] * S0;
+        for (int d = 0; d < 3; ++d) K[d] = omega * rho * Au[d];
+        if (flagged) {
+            // B_u = sum a dGuo/du = -3 g S0 + 9 S2 g
+            const T gg[3] = {gv.x, gv.y, gv.z};
+            const T S2g[3] = {S2[0] * gg[0] + S2[3] * gg[1] + S2[4] * gg[2],
+                              S2[3] * gg[0] + S2[1] * gg[1] + S2[5] * gg[2],
+                              S2[4] * gg[0] + S2[5] * gg[1] + S2[2] * gg[2]};
+            for (int d = 0; d < 3; ++d) K[d] += guo * (T(-3) * gg[d] * S0 + T(9) * S2g[d]);
+        }
         const T inv = T(1) / rho;
-        const T Ku = K[0] * u[0] + K[1] * u[1] + K[2] * u[2];
+        const T Ki[3] = {K[0] * inv, K[1] * inv, K[2] * inv};
+        const T base = omega * Arho - (Ki[0] * u[0] + Ki[1] * u[1] + Ki[2] * u[2]);
+        const T keep = T(1) - omega;
 #pragma unroll
         for (int j = 0; j < 19; ++j) {
-            T Kc = -Ku;
-            if (q_cx(j)) Kc += q_cx(j) > 0 ? K[0] : -K[0];
-            if (q_cy(j)) Kc += q_cy(j) > 0 ? K[1] : -K[1];
-            if (q_cz(j)) Kc += q_cz(j) > 0 ? K[2] : -K[2];
-            lam_out[j * L.ncell + cell] = (T(1) - omega) * a[j] + omega * Arho + Kc * inv;
+            T v = base;
+            if (q_cx(j)) v += q_cx(j) > 0 ? Ki[0] : -Ki[0];
+            if (q_cy(j)) v += q_cy(j) > 0 ? Ki[1] : -Ki[1];
+            if (q_cz(j)) v += q_cz(j) > 0 ? Ki[2] : -Ki[2];
+            (lam_out + j * L.ncell)[c] = keep * a[j] + v;
         }
         if (flagged) {
-            V4 lg = lamg[cell];
-            lg.x += K[0] * T(0.5) * inv + guo * Gg[0];
-            lg.y += K[1] * T(0.5) * inv + guo * Gg[1];
-            lg.z += K[2] * T(0.5) * inv + guo * Gg[2];
-            lamg[cell] = lg;
+            // the interpolation's part (mu, nonzero only in stencil cells, all
+            // of them flagged) is taken and cleared here
+            const V4 m = mu[c];
+            lamg[c] = V4{m.x + T(0.5) * Ki[0] + guo * Au[0], m.y + T(0.5) * Ki[1] + guo * Au[1],
+                         m.z + T(0.5) * Ki[2] + guo * Au[2], T(0)};
+            mu[c] = V4{};
         }
     }
     for (int o = 16; o > 0; o >>= 1) uwg += __shfl_xor_sync(0xffffffffu, uwg, o);
@@ -504,18 +501,16 @@ static void adj_step_impl(const AdjStepArgs &A, cudaStream_t s) {
     const MeshDev &m = A.mesh;
     const PosView<T> pos = adj_view<T>(A.x, A.x_lo);
     k_adj_interp<N, T><<<node_blocks(m.n_nodes), 256, 0, s>>>(
-        m.n_nodes, pos, (const V4 *)A.M1, (const V4 *)A.g, (const V4 *)A.lamx_in, (V4 *)A.mu,
+        m.n_nodes, pos, (const V4 *)A.M1, (const V4 *)A.g, (const V4 *)A.lamx_in, (V4 *)A.mu, (T *)A.lam_in,
         (V4 *)A.lamx_out, L.nx, L.ny, L.nz, L.ncell);
-    k_adj_correct<T><<<(unsigned)((L.ntiles + 7) / 8), 256, 0, s>>>(
-        (const V4 *)A.M1, (const V4 *)A.g, A.flags, (V4 *)A.mu, (T *)A.lam_in, (V4 *)A.lamg, L);
     if (L.ncell <= 0xffffffffLL)
         k_adj_collide<T, unsigned><<<cell_blocks(L.ncell), 256, 0, s>>>(
-            (const V4 *)A.M0, (V4 *)A.g, A.flags, (const T *)A.lam_in, (T *)A.lam_out, (V4 *)A.lamg,
-            A.uw_partial, L, (T)A.omega);
+            (const V4 *)A.M0, (V4 *)A.g, A.flags, (const T *)A.lam_in, (T *)A.lam_out, (V4 *)A.mu,
+            (V4 *)A.lamg, A.uw_partial, L, (T)A.omega);
     else
         k_adj_collide<T, unsigned long long><<<cell_blocks(L.ncell), 256, 0, s>>>(
-            (const V4 *)A.M0, (V4 *)A.g, A.flags, (const T *)A.lam_in, (T *)A.lam_out, (V4 *)A.lamg,
-            A.uw_partial, L, (T)A.omega);
+            (const V4 *)A.M0, (V4 *)A.g, A.flags, (const T *)A.lam_in, (T *)A.lam_out, (V4 *)A.mu,
+            (V4 *)A.lamg, A.uw_partial, L, (T)A.omega);
     k_adj_spread<N, T><<<node_blocks(m.n_nodes), 256, 0, s>>>(
         m.n_nodes, pos, (const V4 *)A.F, (const V4 *)A.lamg, (V4 *)A.lamF, (V4 *)A.lamx_out, L.nx, L.ny, L.nz);
     k_adj_membrane<T><<<node_blocks(m.n_nodes), 256, 0, s>>>(
