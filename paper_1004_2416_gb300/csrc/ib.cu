@@ -259,7 +259,10 @@ PosView<float> view<float>(const MeshDev &m) {
     return PosView<float>{(float4 *)m.x, (float4 *)m.x_lo};
 }
 
-constexpr int kNodesPerBlock = 8;  // 8 warps of 32
+// Two warps (nodes) per block: a few thousand node warps then spread evenly
+// over the 152 SMs (whole 8-warp blocks left some SMs with half as many
+// warps again as others, and those set the kernel's time).
+constexpr int kNodesPerBlock = 2;
 
 // The single lattice as a run descriptor (its force flags are the lattice's).
 static RunDesc single_run(const Lattice &L) {
