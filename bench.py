@@ -35,7 +35,7 @@ if ROOT not in sys.path:
 
 METRIC = "fused IB-LBM step MLUPS & % HBM roofline; adjoint/forward time at 1e-4 rel error"
 BYTES_PER_CELL = {"fp32": 152, "fp16": 76, "fp64": 304}
-KERNEL_LAUNCHES_PER_STEP = 3 + 3  # force+spread, collide, interp, 3 reduction stages
+KERNEL_LAUNCHES_PER_STEP = 4 + 3  # force+spread, collide, cell velocities, interp, 3 reduction stages
 
 
 def _args():
@@ -54,6 +54,8 @@ def _args():
     p.add_argument("--cpu-budget-s", type=float, default=20.0)
     p.add_argument("--profile-steps", type=int, default=500)
     p.add_argument("--no-adjoint", action="store_true", help="skip the config-5 adjoint timing")
+    p.add_argument("--interp-mode", type=int, default=-1, choices=[-1, 0, 1],
+                   help="interpolation: -1 automatic, 0 gather at the stencil cells, 1 cell velocities first")
     p.add_argument("--adjoint-only", action="store_true",
                    help="only the config-5 adjoint timing, printed as {\"adjoint\": ...}")
     p.add_argument("--adjoint-steps", type=int, default=None,
@@ -401,6 +403,7 @@ def run_ours(a):
     case = _workload(a)
     stream = torch.cuda.Stream()
     sim = _make_sim(case, stream)
+    sim.set_interp_mode(a.interp_mode)
     batch = isinstance(case, Batch)
     sim.set_taylor_recording(1, ring=a.steps + a.warmup + 4096)
 

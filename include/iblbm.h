@@ -207,6 +207,15 @@ int iblbm_set_taylor_recording(iblbm_sim *sim, int every, int ring);
 int iblbm_get_taylor_records(iblbm_sim *sim, int capsule_id, int max_records,
                              double *out, int64_t *steps_out, int *n_records);
 
+/* How the interpolation (Eq. velocityinterpolation) gets u(X, t+1): mode 0,
+ * every node's lanes form u from the 19 populations and the force at each
+ * stencil cell; mode 1, a pass first forms u once for every cell of the tiles
+ * the spreading flagged and the nodes read it; -1 (default) chooses mode 1
+ * when the nodes' stencils touch more than a quarter of the cells (dense
+ * suspensions).  Both give the same numbers bit for bit.  IBLBM_ERR_ARG for
+ * another mode.  Synchronising. */
+int iblbm_set_interp_mode(iblbm_sim *sim, int mode);
+
 /* Runs n_steps (1..100000) further time steps without graph capture, with
  * CUDA events on the object's stream around each kernel group, and returns
  * the mean device time per step in milliseconds of: ms_out[0] membrane

@@ -62,6 +62,8 @@ struct iblbm_sim {
     int cur = 0;  // pop[cur] holds f(t); force[cur] the last spread force
     void *force[2] = {nullptr, nullptr};
     uint8_t *flags[2] = {nullptr, nullptr};
+    void *uvel = nullptr;  // velocity of the cells of the flagged tiles (Vec4 per cell)
+    int interp_mode = -1;  // -1 automatic, 0 gather at the stencil cells, 1 cell velocities first
     int *d_status = nullptr;
 
     std::vector<Capsule> caps;
@@ -414,10 +416,20 @@ void free_ring(iblbm_sim *s) {
     s->rec_steps.clear();
 }
 
+// Whether the interpolation reads velocities formed once per cell of the
+// flagged tiles: automatic when the stencils touch (counting repeats) more than
+// a quarter of the cells, i.e. in dense suspensions.
+bool cell_velocity_first(const iblbm_sim *s) {
+    if (s->interp_mode >= 0) return s->interp_mode == 1;
+    const double touches = (double)s->mesh.n_nodes * s->delta * s->delta * s->delta;
+    const double cells = s->batch ? (double)(s->vec_bytes / (4 * real_bytes(s))) : (double)s->L.ncell;
+    return touches > 0.25 * cells;
+}
+
 // One time step (sub-step list of Sec. II.C) enqueued on the stream, with an
 // optional record of the capsule reductions (sub-step 6) at its end.  With
 // `ev` non-null, events are recorded around each kernel group:
-// ev[0] | spread | ev[1] | collide | ev[2] | interpolate | ev[3] | reductions | ev[4].
+// ev[0] | spread | ev[1] | collide | ev[2] | cell velocities, interpolate | ev[3] | reductions | ev[4].
 void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) {
     const int c = s->cur, n = 1 - s->cur;
     auto mark = [s](const char *what) {
@@ -447,12 +459,18 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) 
     }
     mark("collide-stream");
     if (ev) cudaEventRecord(ev[2], s->stream);
+    const bool pre = cell_velocity_first(s);
+    if (pre) {
+        launch_flag_velocity(s->prec, s->L, s->pop[n], s->force[n], s->flags[n], s->uvel,
+                             s->batch ? s->d_runs : nullptr, s->d_items, s->n_items, s->stream);
+        mark("velocity of the flagged cells");
+    }
     if (s->side_pending) {  // the previous record still reads the positions
         cudaStreamWaitEvent(s->stream, s->ev_join, 0);
         s->side_pending = false;
         mark("join of the Taylor record");
     }
-    launch_interp_advect(s->prec, s->delta, s->L, s->mesh, s->pop[n], s->force[n],
+    launch_interp_advect(s->prec, s->delta, s->L, s->mesh, pre ? s->uvel : nullptr, s->pop[n], s->force[n],
                          s->batch ? s->d_runs : nullptr, s->d_node_run, s->stream);
     mark("interpolation + advection");
     if (ev) cudaEventRecord(ev[3], s->stream);
@@ -614,7 +632,8 @@ int setup_object(iblbm_sim *s, void *stream, const iblbm_allocator *alloc, long 
         ok = s->pop[k] && s->force[k] && s->flags[k];
     }
     s->d_status = (int *)dev_alloc(s, sizeof(int));
-    if (!ok || !s->d_status) {
+    s->uvel = dev_alloc(s, s->vec_bytes);
+    if (!ok || !s->d_status || !s->uvel) {
         g_create_error = "device allocation failed";
         return IBLBM_ERR_OOM;
     }
@@ -813,6 +832,7 @@ int iblbm_destroy(iblbm_sim *s) {
         dev_free(s, s->flags[k]);
     }
     dev_free(s, s->d_status);
+    dev_free(s, s->uvel);
     dev_free(s, s->d_scratch);
     dev_free(s, s->d_runs);
     dev_free(s, s->d_items);
@@ -1291,7 +1311,8 @@ int iblbm_adjoint_backward(iblbm_sim *s, int capsule_id, double *D_out, double *
             a.status = s->d_status;
             a.moments = T.M[k];
             launch_collide_stream(s->prec, s->L, a, st);
-            launch_interp_advect(s->prec, s->delta, s->L, m, T.pop[(k + 1) & 1], T.g[k], nullptr, nullptr, st);
+            launch_interp_advect(s->prec, s->delta, s->L, m, nullptr, T.pop[(k + 1) & 1], T.g[k], nullptr,
+                                 nullptr, st);
         }
         launch_adjoint_moments(s->prec, s->L, T.pop[len & 1], T.M[len], st);
     };
@@ -1488,6 +1509,16 @@ int iblbm_profile_kernels(iblbm_sim *s, int n_steps, double ms_out[4]) {
 int iblbm_sync(iblbm_sim *s) {
     if (!s) return IBLBM_ERR_ARG;
     return sync_status(s);
+}
+
+int iblbm_set_interp_mode(iblbm_sim *s, int mode) {
+    if (!s) return IBLBM_ERR_ARG;
+    if (mode < -1 || mode > 1) return fail(s, IBLBM_ERR_ARG, "mode must be -1, 0 or 1");
+    join_side(s);
+    CK(cudaStreamSynchronize(s->stream));
+    drop_graphs(s);
+    s->interp_mode = mode;
+    return IBLBM_OK;
 }
 
 }  // extern "C"

@@ -7,15 +7,16 @@
 //                      node positions (Eq. velocityinterpolation) and Euler
 //                      advection (Eq. positionupdate)
 //
-// Both kernels give one warp to one membrane node.  In k_force_spread the
-// lanes first take the faces around the node (one face each; a face's
+// k_force_spread gives one warp to one or four membrane nodes.  A group of
+// lanes first takes the faces around its node (one face each; a face's
 // contribution to this corner is recomputed by each of its three corner
-// warps, which keeps the assembly a deterministic warp reduction with no
-// atomics and no per-face scratch), then the lanes take the n^3 stencil cells
-// and add the spread force with one vector atomic per cell.  In
-// k_interp_advect the lanes take the stencil cells, each gathers the 19
-// populations of its cell (L2-resident: the stencils of all nodes cover a thin
-// shell of the lattice), and a warp reduction gives the node velocity.
+// groups, which keeps the assembly a deterministic group reduction with no
+// atomics and no per-face scratch), then the 32 lanes take the nodes' n^3
+// stencil cells and add the spread force with one vector atomic per cell.
+// k_interp_advect gives one warp to one node: the lanes take the stencil
+// cells, each gathers its cell's velocity (formed once per cell of the flagged
+// tiles by k_flag_velocity, L2-resident), and a warp reduction gives the node
+// velocity.
 //
 // Face energy gradient.  With the current edge vectors u = x_b - x_a,
 // v = x_c - x_a, their Gram entries g11 = u.u, g12 = u.v, g22 = v.v, the
@@ -42,7 +43,14 @@
 
 namespace iblbm {
 
-template <int N, typename T>
+// One warp takes NPW nodes (1 or 4).  Face phase: a group of 32 / NPW lanes
+// per node, one adjacent face per lane (a loop for higher valences), a
+// fixed-order reduction within the group.  Stencil phase: the NPW x n^3
+// (node, cell) pairs are dealt to the 32 lanes, which fetch their node's force
+// and position from its group by shuffles.  Four nodes per warp waste fewer
+// lanes on the faces (a node has five or six) when there are enough nodes to
+// fill the GPU; one node per warp keeps more warps in flight otherwise.
+template <int N, typename T, int NPW>
 __global__ void __launch_bounds__(256)
     k_force_spread(int n_nodes, PosView<T> pos, const int *__restrict__ adj_off,
                    const int *__restrict__ adj, const int4 *__restrict__ tri,
@@ -54,13 +62,17 @@ __global__ void __launch_bounds__(256)
                    const int *__restrict__ node_run, int *status) {
     using V4 = typename Vec4<T>::type;
     const int lane = threadIdx.x & 31;
-    const int node = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
-    if (node >= n_nodes) return;
-    const RunDesc R = runs ? runs[node_run[node]] : single;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    constexpr int kFsNodes = NPW, kFsGroup = 32 / NPW;
+    const long long node0 = warp * kFsNodes;
+    if (node0 >= n_nodes) return;
+    const int grp = lane / kFsGroup, gl = lane % kFsGroup;
+    const int node = (int)(node0 + grp);
+    const bool valid = node < n_nodes;
 
     T fx = T(0), fy = T(0), fz = T(0);
-    const int e0 = adj_off[node], e1 = adj_off[node + 1];
-    for (int e = e0 + lane; e < e1; e += 32) {
+    const int e0 = valid ? adj_off[node] : 0, e1 = valid ? adj_off[node + 1] : 0;
+    for (int e = e0 + gl; e < e1; e += kFsGroup) {
         const int ent = adj[e];
         const int f = ent >> 2, corner = ent & 3;
         const int4 t = tri[f];
@@ -92,43 +104,145 @@ __global__ void __launch_bounds__(256)
         fy += ku * u[1] + kv * v[1];
         fz += ku * u[2] + kv * v[2];
     }
-    fx = warp_sum(fx);
-    fy = warp_sum(fy);
-    fz = warp_sum(fz);
-    if (lane == 0) nodeF[node] = V4{fx, fy, fz, T(0)};
-
-    T p[kPosLen<T>];
-    pos.approx(node, p);
-    T pc[3];
-    if constexpr (kPosLen<T> == 6) {
-        pc[0] = p[0] + p[3]; pc[1] = p[1] + p[4]; pc[2] = p[2] + p[5];
-    } else {
-        pc[0] = p[0]; pc[1] = p[1]; pc[2] = p[2];
+#pragma unroll
+    for (int o = kFsGroup / 2; o > 0; o >>= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        fy += __shfl_xor_sync(0xffffffffu, fy, o);
+        fz += __shfl_xor_sync(0xffffffffu, fz, o);
     }
-    const int bx = stencil_first<N>(pc[0]), by = stencil_first<N>(pc[1]), bz = stencil_first<N>(pc[2]);
+    if (valid && gl == 0) nodeF[node] = V4{fx, fy, fz, T(0)};
+
+    // the group's node position and stencil base
+    T p[kPosLen<T>];
+    if (valid) {
+        pos.approx(node, p);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kPosLen<T>; ++k) p[k] = T(0);
+    }
+    int b[3];
+    {
+        T pc[3];
+        if constexpr (kPosLen<T> == 6) {
+            pc[0] = p[0] + p[3]; pc[1] = p[1] + p[4]; pc[2] = p[2] + p[5];
+        } else {
+            pc[0] = p[0]; pc[1] = p[1]; pc[2] = p[2];
+        }
+        b[0] = stencil_first<N>(pc[0]);
+        b[1] = stencil_first<N>(pc[1]);
+        b[2] = stencil_first<N>(pc[2]);
+    }
+    const RunDesc R1 = (NPW == 1 && runs) ? runs[node_run[node]] : single;
     constexpr int NC = N * N * N;
-    for (int k = lane; k < NC; k += 32) {
-        const int kx = k % N, ky = (k / N) % N, kz = k / (N * N);
-        const int X = bx + kx, Y = by + ky, Z = bz + kz;
+    // uniform trip count: every lane takes part in every round of shuffles
+    for (int base = 0; base < kFsNodes * NC; base += 32) {
+        const int k = base + lane;
+        const int g = k < kFsNodes * NC ? k / NC : kFsNodes - 1, c = k - g * NC;
+        const int src = g * kFsGroup;
+        // node g's force and position, from its group (with one node per
+        // warp every lane holds them already)
+        T gfx = fx, gfy = fy, gfz = fz;
+        T q[kPosLen<T>];
+#pragma unroll
+        for (int j = 0; j < kPosLen<T>; ++j) q[j] = p[j];
+        int gb[3] = {b[0], b[1], b[2]};
+        if constexpr (NPW > 1) {
+            gfx = __shfl_sync(0xffffffffu, fx, src);
+            gfy = __shfl_sync(0xffffffffu, fy, src);
+            gfz = __shfl_sync(0xffffffffu, fz, src);
+#pragma unroll
+            for (int j = 0; j < kPosLen<T>; ++j) q[j] = __shfl_sync(0xffffffffu, p[j], src);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) gb[j] = __shfl_sync(0xffffffffu, b[j], src);
+        }
+        const int gnode = (int)(node0 + g);
+        if (k >= kFsNodes * NC || gnode >= n_nodes) continue;
+        const RunDesc R = (NPW == 1) ? R1 : (runs ? runs[node_run[gnode]] : single);
+        const int kx = c % N, ky = (c / N) % N, kz = c / (N * N);
+        const int X = gb[0] + kx, Y = gb[1] + ky, Z = gb[2] + kz;
         if (Z < 0 || Z >= R.nz) {
             set_status(status, kStatusStencil);
             continue;
         }
         T d[3];
-        pos.rel(p, X, Y, Z, d);
+        pos.rel(q, X, Y, Z, d);
         const T w = delta_phi<N>(d[0]) * delta_phi<N>(d[1]) * delta_phi<N>(d[2]);
         if (w == T(0)) continue;
         const int xw = wrap_index(X, R.nx), yw = wrap_index(Y, R.ny);
         const long long cell = xw + (long long)R.nx * (yw + (long long)R.ny * Z);
-        add_force(&force[R.cell_off + cell], w * fx, w * fy, w * fz);
+        add_force(&force[R.cell_off + cell], w * gfx, w * gfy, w * gfz);
         flags[R.tile_off + ((long long)Z * R.nty + yw / R.ty) * R.ntx + xw / R.tx] = 1;
     }
 }
 
-template <int N, typename S, typename T>
+// u = (sum_i c_i f_i + g/2) / rho of one cell from its 19 stored deviations g
+// (Eq. velocityinterpolation's u(X, t+1) with the half-force correction).
+template <typename T>
+__device__ __forceinline__ typename Vec4<T>::type velocity_from(const T g[19], const typename Vec4<T>::type &f) {
+    T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        drho += g[i];
+        if (q_cx(i)) jx += q_cx(i) > 0 ? g[i] : -g[i];
+        if (q_cy(i)) jy += q_cy(i) > 0 ? g[i] : -g[i];
+        if (q_cz(i)) jz += q_cz(i) > 0 ? g[i] : -g[i];
+    }
+    const T inv_rho = T(1) / (T(1) + drho);
+    return typename Vec4<T>::type{(jx + T(0.5) * f.x) * inv_rho, (jy + T(0.5) * f.y) * inv_rho,
+                                  (jz + T(0.5) * f.z) * inv_rho, T(0)};
+}
+
+// Velocity u = (sum_i c_i f_i + g/2) / rho of every cell in a force-flagged
+// tile (Eq. velocityinterpolation's u(X, t+1)), once per cell: every stencil
+// cell of the interpolation lies in a tile the spreading flagged, and each cell
+// serves a dozen or so nodes.  One warp per tile (its lanes walk the tile's
+// cells); for a batch the tiles come from the work list of (run, tile) pairs.
+template <typename S, typename T>
 __global__ void __launch_bounds__(256)
-    k_interp_advect(int n_nodes, PosView<T> pos, const S *__restrict__ pop,
-                    const typename Vec4<T>::type *__restrict__ force,
+    k_flag_velocity(const S *__restrict__ pop, const typename Vec4<T>::type *__restrict__ force,
+                    const uint8_t *__restrict__ flags, typename Vec4<T>::type *__restrict__ uvel,
+                    RunDesc single, long long n_tiles, const RunDesc *__restrict__ runs,
+                    const int2 *__restrict__ items) {
+    using V4 = typename Vec4<T>::type;
+    const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (w >= n_tiles) return;
+    int tile;
+    RunDesc R;
+    if (runs) {
+        const int2 it = items[w];
+        R = runs[it.x];
+        tile = it.y;
+    } else {
+        R = single;
+        tile = (int)w;
+    }
+    if (!flags[R.tile_off + tile]) return;
+    const int lane = threadIdx.x & 31;
+    const int per_z = R.ntx * R.nty;
+    const int z = tile / per_z, rem = tile - z * per_z;
+    const int tyi = rem / R.ntx, txi = rem - tyi * R.ntx;
+    pop += 19 * R.cell_off;
+    force += R.cell_off;
+    uvel += R.cell_off;
+    for (int c = lane; c < R.tx * R.ty; c += 32) {
+        const int x = txi * R.tx + c % R.tx, y = tyi * R.ty + c / R.tx;
+        if (x >= R.nx || y >= R.ny) continue;
+        const long long cell = x + (long long)R.nx * (y + (long long)R.ny * z);
+        T g[19];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) g[i] = Store<S, T>::load(pop + i * R.ncell + cell);
+        uvel[cell] = velocity_from<T>(g, force[cell]);
+    }
+}
+
+// PRE: read the cell velocities of k_flag_velocity; otherwise every lane
+// gathers the 19 populations and the force of its cells and forms u itself
+// (the same arithmetic).  The pre-pass pays when the nodes' stencils touch
+// many more cells than the flagged tiles hold (dense suspensions).
+template <int N, typename S, typename T, bool PRE>
+__global__ void __launch_bounds__(256)
+    k_interp_advect(int n_nodes, PosView<T> pos, const typename Vec4<T>::type *__restrict__ uvel,
+                    const S *__restrict__ pop, const typename Vec4<T>::type *__restrict__ force,
                     typename Vec4<T>::type *__restrict__ nodeU, RunDesc single,
                     const RunDesc *__restrict__ runs, const int *__restrict__ node_run) {
     using V4 = typename Vec4<T>::type;
@@ -137,9 +251,6 @@ __global__ void __launch_bounds__(256)
     if (node >= n_nodes) return;
     const RunDesc R = runs ? runs[node_run[node]] : single;
     const int nx = R.nx, ny = R.ny, nz = R.nz;
-    const long long ncell = R.ncell;
-    pop += 19 * R.cell_off;
-    force += R.cell_off;
     T p[kPosLen<T>];
     pos.approx(node, p);
     T pc[3];
@@ -149,8 +260,8 @@ __global__ void __launch_bounds__(256)
         pc[0] = p[0]; pc[1] = p[1]; pc[2] = p[2];
     }
     const int bx = stencil_first<N>(pc[0]), by = stencil_first<N>(pc[1]), bz = stencil_first<N>(pc[2]);
-    // Each lane owns up to ITER stencil cells; all their population loads are
-    // issued before any is used.
+    // Each lane owns up to ITER stencil cells; all their loads are issued
+    // before any is used.
     constexpr int NC = N * N * N;
     constexpr int ITER = (NC + 31) / 32;
     T w[ITER];
@@ -166,32 +277,36 @@ __global__ void __launch_bounds__(256)
             T d[3];
             pos.rel(p, X, Y, Z, d);
             w[it] = delta_phi<N>(d[0]) * delta_phi<N>(d[1]) * delta_phi<N>(d[2]);
-            cell[it] = wrap_index(X, nx) + (long long)nx * (wrap_index(Y, ny) + (long long)ny * Z);
+            cell[it] = R.cell_off + wrap_index(X, nx) + (long long)nx * (wrap_index(Y, ny) + (long long)ny * Z);
         }
     }
-    T g[ITER][19];
-#pragma unroll
-    for (int it = 0; it < ITER; ++it)
-#pragma unroll
-        for (int i = 0; i < 19; ++i)
-            g[it][i] = (w[it] != T(0)) ? Store<S, T>::load(pop + i * ncell + cell[it]) : T(0);
     T ax = T(0), ay = T(0), az = T(0);
+    if constexpr (PRE) {
+        V4 u[ITER];
 #pragma unroll
-    for (int it = 0; it < ITER; ++it) {
-        if (w[it] == T(0)) continue;
-        T drho = T(0), jx = T(0), jy = T(0), jz = T(0);
+        for (int it = 0; it < ITER; ++it) u[it] = (w[it] != T(0)) ? uvel[cell[it]] : V4{};
 #pragma unroll
-        for (int i = 0; i < 19; ++i) {
-            drho += g[it][i];
-            if (q_cx(i)) jx += q_cx(i) > 0 ? g[it][i] : -g[it][i];
-            if (q_cy(i)) jy += q_cy(i) > 0 ? g[it][i] : -g[it][i];
-            if (q_cz(i)) jz += q_cz(i) > 0 ? g[it][i] : -g[it][i];
+        for (int it = 0; it < ITER; ++it) {
+            ax += w[it] * u[it].x;
+            ay += w[it] * u[it].y;
+            az += w[it] * u[it].z;
         }
-        const V4 f = force[cell[it]];
-        const T inv_rho = T(1) / (T(1) + drho);
-        ax += w[it] * ((jx + T(0.5) * f.x) * inv_rho);
-        ay += w[it] * ((jy + T(0.5) * f.y) * inv_rho);
-        az += w[it] * ((jz + T(0.5) * f.z) * inv_rho);
+    } else {
+        const S *pr = pop + 19 * R.cell_off;
+        T g[ITER][19];
+#pragma unroll
+        for (int it = 0; it < ITER; ++it)
+#pragma unroll
+            for (int i = 0; i < 19; ++i)
+                g[it][i] = (w[it] != T(0)) ? Store<S, T>::load(pr + i * R.ncell + (cell[it] - R.cell_off)) : T(0);
+#pragma unroll
+        for (int it = 0; it < ITER; ++it) {
+            if (w[it] == T(0)) continue;
+            const V4 u = velocity_from<T>(g[it], force[cell[it]]);
+            ax += w[it] * u.x;
+            ay += w[it] * u.y;
+            az += w[it] * u.z;
+        }
     }
     ax = warp_sum(ax);
     ay = warp_sum(ay);
@@ -283,21 +398,41 @@ static void force_spread_impl(const Lattice &L, const MeshDev &m, void *force, u
                               int *status, const RunDesc *runs, const int *node_run,
                               cudaStream_t s) {
     using V4 = typename Vec4<T>::type;
-    unsigned nb = (unsigned)((m.n_nodes + kNodesPerBlock - 1) / kNodesPerBlock);
-    k_force_spread<N, T><<<nb, 32 * kNodesPerBlock, 0, s>>>(
+    // four nodes per warp once one-node warps would exceed 32 per SM
+    const bool four = m.n_nodes >= 152 * 32;
+    const long long warps = four ? (m.n_nodes + 3) / 4 : m.n_nodes;
+    const int wpb = warps >= 152 * 16 ? 4 : 2;
+    const unsigned nb = (unsigned)((warps + wpb - 1) / wpb);
+    auto kern = four ? k_force_spread<N, T, 4> : k_force_spread<N, T, 1>;
+    kern<<<nb, 32 * wpb, 0, s>>>(
         m.n_nodes, view<T>(m), m.adj_off, m.adj, (const int4 *)m.tri, (const V4 *)m.fconst,
         (const V4 *)m.capmod, (V4 *)m.F, (V4 *)force, flags, single_run(L), runs, node_run,
         status);
 }
 
 template <int N, typename S, typename T>
-static void interp_impl(const Lattice &L, const MeshDev &m, const void *pop, const void *force,
-                        const RunDesc *runs, const int *node_run, cudaStream_t s) {
+static void interp_impl(const Lattice &L, const MeshDev &m, const void *uvel, const void *pop,
+                        const void *force, const RunDesc *runs, const int *node_run, cudaStream_t s) {
     using V4 = typename Vec4<T>::type;
     unsigned nb = (unsigned)((m.n_nodes + kNodesPerBlock - 1) / kNodesPerBlock);
-    k_interp_advect<N, S, T><<<nb, 32 * kNodesPerBlock, 0, s>>>(
-        m.n_nodes, view<T>(m), (const S *)pop, (const V4 *)force, (V4 *)m.u, single_run(L), runs,
-        node_run);
+    if (uvel)
+        k_interp_advect<N, S, T, true><<<nb, 32 * kNodesPerBlock, 0, s>>>(
+            m.n_nodes, view<T>(m), (const V4 *)uvel, nullptr, nullptr, (V4 *)m.u, single_run(L), runs, node_run);
+    else
+        k_interp_advect<N, S, T, false><<<nb, 32 * kNodesPerBlock, 0, s>>>(
+            m.n_nodes, view<T>(m), nullptr, (const S *)pop, (const V4 *)force, (V4 *)m.u, single_run(L), runs,
+            node_run);
+}
+
+template <typename S, typename T>
+static void flag_velocity_impl(const Lattice &L, const void *pop, const void *force, const uint8_t *flags,
+                               void *uvel, const RunDesc *runs, const int2 *items, long long n_items,
+                               cudaStream_t s) {
+    using V4 = typename Vec4<T>::type;
+    const long long n = runs ? n_items : L.ntiles;
+    if (n <= 0) return;
+    k_flag_velocity<S, T><<<(unsigned)((n + 7) / 8), 256, 0, s>>>(
+        (const S *)pop, (const V4 *)force, flags, (V4 *)uvel, single_run(L), n, runs, items);
 }
 
 void launch_force_spread(int prec, int delta, const Lattice &L, const MeshDev &m, void *force,
@@ -315,22 +450,30 @@ void launch_force_spread(int prec, int delta, const Lattice &L, const MeshDev &m
     }
 }
 
-void launch_interp_advect(int prec, int delta, const Lattice &L, const MeshDev &m, const void *pop,
-                          const void *force, const RunDesc *runs, const int *node_run,
+void launch_flag_velocity(int prec, const Lattice &L, const void *pop, const void *force, const uint8_t *flags,
+                          void *uvel, const RunDesc *runs, const int2 *items, long long n_items,
+                          cudaStream_t s) {
+    if (prec == kF64) flag_velocity_impl<double, double>(L, pop, force, flags, uvel, runs, items, n_items, s);
+    else if (prec == kF32) flag_velocity_impl<float, float>(L, pop, force, flags, uvel, runs, items, n_items, s);
+    else flag_velocity_impl<__half, float>(L, pop, force, flags, uvel, runs, items, n_items, s);
+}
+
+void launch_interp_advect(int prec, int delta, const Lattice &L, const MeshDev &m, const void *uvel,
+                          const void *pop, const void *force, const RunDesc *runs, const int *node_run,
                           cudaStream_t s) {
     if (m.n_nodes == 0) return;
     if (prec == kF64) {
-        if (delta == 2) interp_impl<2, double, double>(L, m, pop, force, runs, node_run, s);
-        else if (delta == 3) interp_impl<3, double, double>(L, m, pop, force, runs, node_run, s);
-        else interp_impl<4, double, double>(L, m, pop, force, runs, node_run, s);
+        if (delta == 2) interp_impl<2, double, double>(L, m, uvel, pop, force, runs, node_run, s);
+        else if (delta == 3) interp_impl<3, double, double>(L, m, uvel, pop, force, runs, node_run, s);
+        else interp_impl<4, double, double>(L, m, uvel, pop, force, runs, node_run, s);
     } else if (prec == kF32) {
-        if (delta == 2) interp_impl<2, float, float>(L, m, pop, force, runs, node_run, s);
-        else if (delta == 3) interp_impl<3, float, float>(L, m, pop, force, runs, node_run, s);
-        else interp_impl<4, float, float>(L, m, pop, force, runs, node_run, s);
+        if (delta == 2) interp_impl<2, float, float>(L, m, uvel, pop, force, runs, node_run, s);
+        else if (delta == 3) interp_impl<3, float, float>(L, m, uvel, pop, force, runs, node_run, s);
+        else interp_impl<4, float, float>(L, m, uvel, pop, force, runs, node_run, s);
     } else {
-        if (delta == 2) interp_impl<2, __half, float>(L, m, pop, force, runs, node_run, s);
-        else if (delta == 3) interp_impl<3, __half, float>(L, m, pop, force, runs, node_run, s);
-        else interp_impl<4, __half, float>(L, m, pop, force, runs, node_run, s);
+        if (delta == 2) interp_impl<2, __half, float>(L, m, uvel, pop, force, runs, node_run, s);
+        else if (delta == 3) interp_impl<3, __half, float>(L, m, uvel, pop, force, runs, node_run, s);
+        else interp_impl<4, __half, float>(L, m, uvel, pop, force, runs, node_run, s);
     }
 }
 

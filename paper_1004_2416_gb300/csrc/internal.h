@@ -125,8 +125,17 @@ void launch_force_to_f64(int prec, const Lattice &L, const void *force, double *
 void launch_force_spread(int prec, int delta, const Lattice &L, const MeshDev &m, void *force,
                          uint8_t *flags, int *status, const RunDesc *runs, const int *node_run,
                          cudaStream_t s);
-void launch_interp_advect(int prec, int delta, const Lattice &L, const MeshDev &m, const void *pop,
-                          const void *force, const RunDesc *runs, const int *node_run,
+// velocity (Vec4) of every cell of the force-flagged tiles from the
+// populations after the step and the step's force density; items / n_items:
+// the batch work list of (run, tile) pairs, or null for a single lattice
+void launch_flag_velocity(int prec, const Lattice &L, const void *pop, const void *force, const uint8_t *flags,
+                          void *uvel, const RunDesc *runs, const int2 *items, long long n_items,
+                          cudaStream_t s);
+// interpolation at the nodes and Euler advection: of the cell velocities uvel
+// when not null, else of velocities formed at each stencil cell from the
+// populations pop and the force density force (the same arithmetic)
+void launch_interp_advect(int prec, int delta, const Lattice &L, const MeshDev &m, const void *uvel,
+                          const void *pop, const void *force, const RunDesc *runs, const int *node_run,
                           cudaStream_t s);
 // node data <-> host doubles [n][3]
 void launch_nodes_to_f64(int prec, const MeshDev &m, int which, int first, int count, double *out,

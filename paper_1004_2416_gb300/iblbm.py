@@ -102,6 +102,7 @@ _SIGS = {
     "iblbm_adjoint_backward": (_int, [_vp, _int, _dp, _dp, _dp, _dp, _dp]),
     "iblbm_adjoint_taylor": (_int, [_vp, _int, ctypes.c_int64, _int, _dp, _dp, _dp, _dp]),
     "iblbm_checkpoint_size": (_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "iblbm_set_interp_mode": (_int, [_vp, _int]),
     "iblbm_checkpoint_save": (_int, [_vp, _vp, _int]),
     "iblbm_checkpoint_restore": (_int, [_vp, _vp, _int]),
     "iblbm_batch_create": (_int, [ctypes.POINTER(_vp), ctypes.POINTER(iblbm_run_spec), _int, _int, _int,
@@ -433,6 +434,10 @@ class Sim:
         _check(iblbm_adjoint_taylor(self._h, capsule_id, int(n_steps), int(checkpoint_every), ctypes.byref(dks),
                                     ctypes.byref(dca), _d(gX0), ctypes.byref(D)), self._h)
         return {"D": D.value, "dD_dks": dks.value, "dD_dCa": dca.value, "dD_dX0": gX0}
+
+    def set_interp_mode(self, mode: int):
+        """-1 automatic (default), 0 gather at the stencil cells, 1 cell velocities first."""
+        _check(iblbm_set_interp_mode(self._h, int(mode)), self._h)
 
     def checkpoint_size(self) -> int:
         n = ctypes.c_size_t()
