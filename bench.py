@@ -54,6 +54,8 @@ def _args():
     p.add_argument("--cpu-budget-s", type=float, default=20.0)
     p.add_argument("--profile-steps", type=int, default=500)
     p.add_argument("--no-adjoint", action="store_true", help="skip the config-5 adjoint timing")
+    p.add_argument("--record-every", type=int, default=1,
+                   help="steps between device records of the capsule reductions (sub-step 6)")
     p.add_argument("--interp-mode", type=int, default=-1, choices=[-1, 0, 1],
                    help="interpolation: -1 automatic, 0 gather at the stencil cells, 1 cell velocities first")
     p.add_argument("--adjoint-only", action="store_true",
@@ -153,6 +155,7 @@ def _config(case, a):
         "tau": case.tau,
         "storage": f"{case.precision} deviations from rest equilibrium",
         "step": "forces+spread, collide-stream, interpolate+advect, FP64 Taylor reductions recorded",
+        "record_every": a.record_every,
         "l2": f"inputs larger than L2: two population buffers of {19 * case.ncell * BYTES_PER_CELL[case.precision] // 38 / 1e6:.0f} MB each",
         "parallelism": "replicas (one independent simulation per rank)",
     }
@@ -405,7 +408,7 @@ def run_ours(a):
     sim = _make_sim(case, stream)
     sim.set_interp_mode(a.interp_mode)
     batch = isinstance(case, Batch)
-    sim.set_taylor_recording(1, ring=a.steps + a.warmup + 4096)
+    sim.set_taylor_recording(a.record_every, ring=(a.steps + a.warmup) // max(1, a.record_every) + 4096)
 
     sim.step(a.warmup)
     sim.sync()

@@ -613,7 +613,12 @@ int setup_object(iblbm_sim *s, void *stream, const iblbm_allocator *alloc, long 
         }
         s->own_stream = true;
     }
-    if (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
+    // The Taylor record runs beside the next step's spreading and collide; at
+    // the highest priority its few blocks start at once instead of queueing
+    // behind the collide's, so the interpolation that joins it does not wait.
+    int least_prio = 0, greatest_prio = 0;
+    cudaDeviceGetStreamPriorityRange(&least_prio, &greatest_prio);
+    if (cudaStreamCreateWithPriority(&s->side, cudaStreamNonBlocking, greatest_prio) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
@@ -1020,7 +1025,8 @@ int iblbm_step(iblbm_sim *s, int64_t n_steps) {
                 cudaError_t e = cudaStreamEndCapture(s->stream, &graph);
                 s->cur = cur0;
                 if (e != cudaSuccess) return cuda_fail(s, e, "graph capture");
-                e = cudaGraphInstantiate(&g, graph, 0);
+                // kernel nodes keep the priority of the stream they were captured on
+                e = cudaGraphInstantiate(&g, graph, cudaGraphInstantiateFlagUseNodePriority);
                 cudaGraphDestroy(graph);
                 if (e != cudaSuccess) {
                     g = nullptr;
