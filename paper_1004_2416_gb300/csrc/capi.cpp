@@ -46,12 +46,15 @@ struct iblbm_sim {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    // Side stream for the Taylor record of a step: it runs concurrently with
-    // the next step's spreading and collide-stream and is joined before the
-    // next interpolation (the only kernel that moves the nodes it reads).
+    // Side stream for the Taylor record of a step.  The interpolation of a
+    // recorded step also writes the new positions into one of two snapshot
+    // buffers, which the record reads; it runs concurrently with the next
+    // steps and is joined before an interpolation writes its buffer again.
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    bool side_pending = false;
+    cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+    bool side_pending[2] = {false, false};
+    void *snap_x[2] = {nullptr, nullptr}, *snap_lo[2] = {nullptr, nullptr};
+    int rec_buf = 0;  // snapshot buffer of the next record
     const char *launch_fail = nullptr;  // first kernel group whose launch failed
     iblbm_allocator alloc{};
     bool has_alloc = false;
@@ -231,6 +234,12 @@ int ensure_mesh(iblbm_sim *s) {
     m.n_caps = nc;
     m.x = A(v4 * nn);
     m.x_lo = s->prec == kF64 ? nullptr : A(v4 * nn);
+    for (int b = 0; b < 2; ++b) {
+        s->snap_x[b] = A(v4 * nn);
+        s->snap_lo[b] = s->prec == kF64 ? nullptr : A(v4 * nn);
+        if (!s->snap_x[b] || (s->prec != kF64 && !s->snap_lo[b]))
+            return fail(s, IBLBM_ERR_OOM, "membrane table allocation failed");
+    }
     m.F = A(v4 * nn);
     m.u = A(v4 * nn);
     void *adj_off = A(sizeof(int) * (nn + 1));
@@ -465,25 +474,32 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) 
                              s->batch ? s->d_runs : nullptr, s->d_items, s->n_items, s->stream);
         mark("velocity of the flagged cells");
     }
-    if (s->side_pending) {  // the previous record still reads the positions
-        cudaStreamWaitEvent(s->stream, s->ev_join, 0);
-        s->side_pending = false;
+    const bool side_rec = record && !ev;  // timed runs keep the record on the main stream
+    const int b = s->rec_buf;
+    if (side_rec && s->side_pending[b]) {  // an earlier record still reads this snapshot
+        cudaStreamWaitEvent(s->stream, s->ev_join[b], 0);
+        s->side_pending[b] = false;
         mark("join of the Taylor record");
     }
     launch_interp_advect(s->prec, s->delta, s->L, s->mesh, pre ? s->uvel : nullptr, s->pop[n], s->force[n],
-                         s->batch ? s->d_runs : nullptr, s->d_node_run, s->stream);
+                         s->batch ? s->d_runs : nullptr, s->d_node_run, s->stream,
+                         side_rec ? s->snap_x[b] : nullptr, side_rec ? s->snap_lo[b] : nullptr);
     mark("interpolation + advection");
     if (ev) cudaEventRecord(ev[3], s->stream);
     if (record) {
-        if (ev) {  // timed: keep it on the main stream
+        if (ev) {
             launch_taylor(s->prec, s->mesh, s->plan, true, s->stream);
         } else {
+            MeshDev snap = s->mesh;
+            snap.x = s->snap_x[b];
+            snap.x_lo = s->snap_lo[b];
             cudaEventRecord(s->ev_fork, s->stream);
             cudaStreamWaitEvent(s->side, s->ev_fork, 0);
             mark("fork of the Taylor record");
-            launch_taylor(s->prec, s->mesh, s->plan, true, s->side);
-            cudaEventRecord(s->ev_join, s->side);
-            s->side_pending = true;
+            launch_taylor(s->prec, snap, s->plan, true, s->side);
+            cudaEventRecord(s->ev_join[b], s->side);
+            s->side_pending[b] = true;
+            s->rec_buf = 1 - b;
         }
         mark("Taylor record");
     }
@@ -491,12 +507,13 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) 
     s->cur = n;
 }
 
-// Makes the main stream wait for an outstanding Taylor record.
+// Makes the main stream wait for the outstanding Taylor records.
 void join_side(iblbm_sim *s) {
-    if (s->side_pending) {
-        cudaStreamWaitEvent(s->stream, s->ev_join, 0);
-        s->side_pending = false;
-    }
+    for (int b = 0; b < 2; ++b)
+        if (s->side_pending[b]) {
+            cudaStreamWaitEvent(s->stream, s->ev_join[b], 0);
+            s->side_pending[b] = false;
+        }
 }
 
 int check_sim(const iblbm_sim *s) { return s ? IBLBM_OK : IBLBM_ERR_ARG; }
@@ -620,7 +637,8 @@ int setup_object(iblbm_sim *s, void *stream, const iblbm_allocator *alloc, long 
     cudaDeviceGetStreamPriorityRange(&least_prio, &greatest_prio);
     if (cudaStreamCreateWithPriority(&s->side, cudaStreamNonBlocking, greatest_prio) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&s->ev_join[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_join[1], cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         g_create_error = "stream or event creation failed";
         return IBLBM_ERR_CUDA;
@@ -850,7 +868,8 @@ int iblbm_destroy(iblbm_sim *s) {
         cudaStreamDestroy(s->side);
     }
     if (s->ev_fork) cudaEventDestroy(s->ev_fork);
-    if (s->ev_join) cudaEventDestroy(s->ev_join);
+    for (cudaEvent_t e : s->ev_join)
+        if (e) cudaEventDestroy(e);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
     return IBLBM_OK;
@@ -1019,6 +1038,7 @@ int iblbm_step(iblbm_sim *s, int64_t n_steps) {
                 // capture; the graph joins its own records before it ends, so
                 // no event recorded inside the capture is waited on outside it.
                 join_side(s);
+                s->rec_buf = 0;  // a graph starts with nothing pending and snapshot 0
                 CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
                 for (int k = 0; k < G; ++k) enqueue_step(s, record_after(s, k));
                 join_side(s);

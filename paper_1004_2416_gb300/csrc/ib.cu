@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(256)
     k_interp_advect(int n_nodes, PosView<T> pos, const typename Vec4<T>::type *__restrict__ uvel,
                     const S *__restrict__ pop, const typename Vec4<T>::type *__restrict__ force,
                     typename Vec4<T>::type *__restrict__ nodeU, RunDesc single,
-                    const RunDesc *__restrict__ runs, const int *__restrict__ node_run) {
+                    const RunDesc *__restrict__ runs, const int *__restrict__ node_run, PosView<T> snap) {
     using V4 = typename Vec4<T>::type;
     const int lane = threadIdx.x & 31;
     const int node = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
@@ -313,7 +313,7 @@ __global__ void __launch_bounds__(256)
     az = warp_sum(az);
     if (lane == 0) {
         nodeU[node] = V4{ax, ay, az, T(0)};
-        pos.advance(node, ax, ay, az);
+        pos.advance(node, ax, ay, az, snap);
     }
 }
 
@@ -412,16 +412,22 @@ static void force_spread_impl(const Lattice &L, const MeshDev &m, void *force, u
 
 template <int N, typename S, typename T>
 static void interp_impl(const Lattice &L, const MeshDev &m, const void *uvel, const void *pop,
-                        const void *force, const RunDesc *runs, const int *node_run, cudaStream_t s) {
+                        const void *force, const RunDesc *runs, const int *node_run, cudaStream_t s,
+                        void *snap_x, void *snap_lo) {
     using V4 = typename Vec4<T>::type;
+    MeshDev sm{};
+    sm.x = snap_x;
+    sm.x_lo = snap_lo;
+    const PosView<T> snap = view<T>(sm);
     unsigned nb = (unsigned)((m.n_nodes + kNodesPerBlock - 1) / kNodesPerBlock);
     if (uvel)
         k_interp_advect<N, S, T, true><<<nb, 32 * kNodesPerBlock, 0, s>>>(
-            m.n_nodes, view<T>(m), (const V4 *)uvel, nullptr, nullptr, (V4 *)m.u, single_run(L), runs, node_run);
+            m.n_nodes, view<T>(m), (const V4 *)uvel, nullptr, nullptr, (V4 *)m.u, single_run(L), runs, node_run,
+            snap);
     else
         k_interp_advect<N, S, T, false><<<nb, 32 * kNodesPerBlock, 0, s>>>(
             m.n_nodes, view<T>(m), nullptr, (const S *)pop, (const V4 *)force, (V4 *)m.u, single_run(L), runs,
-            node_run);
+            node_run, snap);
 }
 
 template <typename S, typename T>
@@ -460,20 +466,20 @@ void launch_flag_velocity(int prec, const Lattice &L, const void *pop, const voi
 
 void launch_interp_advect(int prec, int delta, const Lattice &L, const MeshDev &m, const void *uvel,
                           const void *pop, const void *force, const RunDesc *runs, const int *node_run,
-                          cudaStream_t s) {
+                          cudaStream_t s, void *snap_x, void *snap_lo) {
     if (m.n_nodes == 0) return;
     if (prec == kF64) {
-        if (delta == 2) interp_impl<2, double, double>(L, m, uvel, pop, force, runs, node_run, s);
-        else if (delta == 3) interp_impl<3, double, double>(L, m, uvel, pop, force, runs, node_run, s);
-        else interp_impl<4, double, double>(L, m, uvel, pop, force, runs, node_run, s);
+        if (delta == 2) interp_impl<2, double, double>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo);
+        else if (delta == 3) interp_impl<3, double, double>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo);
+        else interp_impl<4, double, double>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo);
     } else if (prec == kF32) {
-        if (delta == 2) interp_impl<2, float, float>(L, m, uvel, pop, force, runs, node_run, s);
-        else if (delta == 3) interp_impl<3, float, float>(L, m, uvel, pop, force, runs, node_run, s);
-        else interp_impl<4, float, float>(L, m, uvel, pop, force, runs, node_run, s);
+        if (delta == 2) interp_impl<2, float, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo);
+        else if (delta == 3) interp_impl<3, float, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo);
+        else interp_impl<4, float, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo);
     } else {
-        if (delta == 2) interp_impl<2, __half, float>(L, m, uvel, pop, force, runs, node_run, s);
-        else if (delta == 3) interp_impl<3, __half, float>(L, m, uvel, pop, force, runs, node_run, s);
-        else interp_impl<4, __half, float>(L, m, uvel, pop, force, runs, node_run, s);
+        if (delta == 2) interp_impl<2, __half, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo);
+        else if (delta == 3) interp_impl<3, __half, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo);
+        else interp_impl<4, __half, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo);
     }
 }
 

@@ -34,10 +34,13 @@ struct PosView<double> {
     __device__ __forceinline__ void rel(const double p[3], int X, int Y, int Z, double d[3]) const {
         d[0] = X - p[0]; d[1] = Y - p[1]; d[2] = Z - p[2];
     }
-    __device__ __forceinline__ void advance(int n, double dx, double dy, double dz) const {
+    // x_n += (dx, dy, dz); the new position also goes to `copy` if it has storage
+    __device__ __forceinline__ void advance(int n, double dx, double dy, double dz,
+                                            const PosView<double> &copy) const {
         dvec4 q = x[n];
         q.x += dx; q.y += dy; q.z += dz;
         x[n] = q;
+        if (copy.x) copy.x[n] = q;
     }
 };
 
@@ -91,13 +94,17 @@ struct PosView<float> {
         d[1] = ((float)Y - p[1]) - p[4];
         d[2] = ((float)Z - p[2]) - p[5];
     }
-    __device__ __forceinline__ void advance(int n, float dx, float dy, float dz) const {
+    __device__ __forceinline__ void advance(int n, float dx, float dy, float dz, const PosView<float> &copy) const {
         float4 h = hi[n], l = lo[n];
         two_sum_add(h.x, l.x, dx);
         two_sum_add(h.y, l.y, dy);
         two_sum_add(h.z, l.z, dz);
         hi[n] = h;
         lo[n] = l;
+        if (copy.hi) {
+            copy.hi[n] = h;
+            copy.lo[n] = l;
+        }
     }
 };
 

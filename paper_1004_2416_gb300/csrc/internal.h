@@ -134,9 +134,11 @@ void launch_flag_velocity(int prec, const Lattice &L, const void *pop, const voi
 // interpolation at the nodes and Euler advection: of the cell velocities uvel
 // when not null, else of velocities formed at each stencil cell from the
 // populations pop and the force density force (the same arithmetic)
+// snap_x / snap_lo (may be null): a second copy of the advanced positions,
+// in the layout of m.x / m.x_lo
 void launch_interp_advect(int prec, int delta, const Lattice &L, const MeshDev &m, const void *uvel,
                           const void *pop, const void *force, const RunDesc *runs, const int *node_run,
-                          cudaStream_t s);
+                          cudaStream_t s, void *snap_x = nullptr, void *snap_lo = nullptr);
 // node data <-> host doubles [n][3]
 void launch_nodes_to_f64(int prec, const MeshDev &m, int which, int first, int count, double *out,
                          cudaStream_t s);
