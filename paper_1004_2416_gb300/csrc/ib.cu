@@ -264,48 +264,61 @@ __global__ void __launch_bounds__(256)
     // before any is used.
     constexpr int NC = N * N * N;
     constexpr int ITER = (NC + 31) / 32;
-    T w[ITER];
+    // The loads depend only on the cell index, so they are issued before the
+    // weights are formed (cells of zero weight are read and not used).
+    bool in[ITER];
     long long cell[ITER];
+    int X[ITER], Y[ITER], Z[ITER];
 #pragma unroll
     for (int it = 0; it < ITER; ++it) {
         const int k = lane + 32 * it;
         const int kx = k % N, ky = (k / N) % N, kz = k / (N * N);
-        const int X = bx + kx, Y = by + ky, Z = bz + kz;
-        w[it] = T(0);
-        cell[it] = 0;
-        if (k < NC && Z >= 0 && Z < nz) {  // a stencil beyond a wall is reported by the spreading
-            T d[3];
-            pos.rel(p, X, Y, Z, d);
-            w[it] = delta_phi<N>(d[0]) * delta_phi<N>(d[1]) * delta_phi<N>(d[2]);
-            cell[it] = R.cell_off + wrap_index(X, nx) + (long long)nx * (wrap_index(Y, ny) + (long long)ny * Z);
-        }
+        X[it] = bx + kx;
+        Y[it] = by + ky;
+        Z[it] = bz + kz;
+        // a stencil beyond a wall is reported by the spreading
+        in[it] = k < NC && Z[it] >= 0 && Z[it] < nz;
+        cell[it] = in[it] ? wrap_index(X[it], nx) + (long long)nx * (wrap_index(Y[it], ny) + (long long)ny * Z[it]) : 0;
     }
     T ax = T(0), ay = T(0), az = T(0);
     if constexpr (PRE) {
+        const V4 *ur = uvel + R.cell_off;
         V4 u[ITER];
 #pragma unroll
-        for (int it = 0; it < ITER; ++it) u[it] = (w[it] != T(0)) ? uvel[cell[it]] : V4{};
+        for (int it = 0; it < ITER; ++it) u[it] = in[it] ? ur[cell[it]] : V4{};
 #pragma unroll
         for (int it = 0; it < ITER; ++it) {
-            ax += w[it] * u[it].x;
-            ay += w[it] * u[it].y;
-            az += w[it] * u[it].z;
+            if (!in[it]) continue;
+            T d[3];
+            pos.rel(p, X[it], Y[it], Z[it], d);
+            const T w = delta_phi<N>(d[0]) * delta_phi<N>(d[1]) * delta_phi<N>(d[2]);
+            if (w == T(0)) continue;
+            ax += w * u[it].x;
+            ay += w * u[it].y;
+            az += w * u[it].z;
         }
     } else {
         const S *pr = pop + 19 * R.cell_off;
+        const V4 *fr = force + R.cell_off;
         T g[ITER][19];
-#pragma unroll
-        for (int it = 0; it < ITER; ++it)
-#pragma unroll
-            for (int i = 0; i < 19; ++i)
-                g[it][i] = (w[it] != T(0)) ? Store<S, T>::load(pr + i * R.ncell + (cell[it] - R.cell_off)) : T(0);
+        V4 f[ITER];
 #pragma unroll
         for (int it = 0; it < ITER; ++it) {
-            if (w[it] == T(0)) continue;
-            const V4 u = velocity_from<T>(g[it], force[cell[it]]);
-            ax += w[it] * u.x;
-            ay += w[it] * u.y;
-            az += w[it] * u.z;
+#pragma unroll
+            for (int i = 0; i < 19; ++i) g[it][i] = in[it] ? Store<S, T>::load(pr + i * R.ncell + cell[it]) : T(0);
+            f[it] = in[it] ? fr[cell[it]] : V4{};
+        }
+#pragma unroll
+        for (int it = 0; it < ITER; ++it) {
+            if (!in[it]) continue;
+            T d[3];
+            pos.rel(p, X[it], Y[it], Z[it], d);
+            const T w = delta_phi<N>(d[0]) * delta_phi<N>(d[1]) * delta_phi<N>(d[2]);
+            if (w == T(0)) continue;
+            const V4 u = velocity_from<T>(g[it], f[it]);
+            ax += w * u.x;
+            ay += w * u.y;
+            az += w * u.z;
         }
     }
     ax = warp_sum(ax);
