@@ -64,10 +64,15 @@ def _declare(L):
     L.orc_d3q19.argtypes = [_ip, _dp, _ip]
     L.orc_feq.argtypes = [c_int, c_double, _dp]
     L.orc_feq.restype = c_double
+    L.orc_feq_linear.argtypes = [c_int, c_double, _dp]
+    L.orc_feq_linear.restype = c_double
     L.orc_guo.argtypes = [c_int, c_double, _dp, _dp]
     L.orc_guo.restype = c_double
     L.orc_moments.argtypes = [_dp, _dp, _dp, _dp]
     L.orc_lbm_step.argtypes = [c_int, c_int, c_int, c_double, c_double, _dp, _dp, _dp]
+    L.orc_lbm_step_eq.argtypes = [c_int, c_int, c_int, c_double, c_double, _dp, _dp, _dp, c_int]
+    L.orc_sim_set_integrator.argtypes = [c_void_p, c_int]
+    L.orc_sim_set_equilibrium.argtypes = [c_void_p, c_int]
     L.orc_init_couette.argtypes = [c_int, c_int, c_int, c_double, _dp]
     L.orc_phi.argtypes = [c_int, c_double]
     L.orc_phi.restype = c_double
@@ -129,6 +134,11 @@ def feq(i: int, rho: float, u) -> float:
     return lib().orc_feq(i, rho, _d(_f64(u)))
 
 
+def feq_linear(i: int, rho: float, u) -> float:
+    """The linearised equilibrium of Sec. IV.A."""
+    return lib().orc_feq_linear(i, rho, _d(_f64(u)))
+
+
 def guo(i: int, tau: float, u, f) -> float:
     return lib().orc_guo(i, tau, _d(_f64(u)), _d(_f64(f)))
 
@@ -140,8 +150,10 @@ def moments(fi, force):
     return float(rho[0]), u
 
 
-def lbm_step(f: np.ndarray, tau: float, u_wall: float, force: np.ndarray | None = None):
-    """One Eq. (lbequation) step of ``f`` shaped [19, nz, ny, nx]."""
+def lbm_step(f: np.ndarray, tau: float, u_wall: float, force: np.ndarray | None = None, order: int = 2):
+    """One Eq. (lbequation) step of ``f`` shaped [19, nz, ny, nx] with the
+    equilibrium of Eq. (equilibrium) (order 2) or the linearised one of
+    Sec. IV.A (order 1)."""
     f = _f64(f)
     _, nz, ny, nx = f.shape
     out = np.zeros_like(f)
@@ -149,7 +161,7 @@ def lbm_step(f: np.ndarray, tau: float, u_wall: float, force: np.ndarray | None 
     keep = _f64(force) if force is not None else None
     if keep is not None:
         fp = _d(keep)
-    rc = lib().orc_lbm_step(nx, ny, nz, tau, u_wall, _d(f), fp, _d(out))
+    rc = lib().orc_lbm_step_eq(nx, ny, nz, tau, u_wall, _d(f), fp, _d(out), order)
     if rc:
         raise ValueError(f"orc_lbm_step returned {rc}")
     return out
@@ -290,6 +302,16 @@ class Sim:
 
     def init_couette(self):
         lib().orc_sim_init_couette(self._h)
+
+    def set_integrator(self, mode: int):
+        """0: Euler, Eq. (positionupdate); 1: Adams-Bashforth (Sec. II.C)."""
+        if lib().orc_sim_set_integrator(self._h, mode):
+            raise ValueError("integrator must be 0 or 1")
+
+    def set_equilibrium(self, order: int):
+        """2: Eq. (equilibrium); 1: linearised (Sec. IV.A)."""
+        if lib().orc_sim_set_equilibrium(self._h, order):
+            raise ValueError("equilibrium order must be 1 or 2")
 
     def step(self, n: int = 1):
         rc = lib().orc_sim_step(self._h, n)

@@ -55,6 +55,13 @@ double orc_feq(int i, double rho, const double u[3]) {
     return weight(i) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
 }
 
+/* The linearised equilibrium of Sec. IV.A, f_i^eq = w_i rho (1 + 3 c_i.u):
+ * the second-order terms of Eq. (equilibrium) dropped. */
+double orc_feq_linear(int i, double rho, const double u[3]) {
+    double cu = C[i][0] * u[0] + C[i][1] * u[1] + C[i][2] * u[2];
+    return weight(i) * rho * (1.0 + 3.0 * cu);
+}
+
 /* Eq. (latticeforce) with c_s^2 = 1/3:
  * F_i = (1 - 1/(2 tau)) w_i [ (c_i - u)/c_s^2 + (c_i.u) c_i / c_s^4 ] . f */
 double orc_guo(int i, double tau, const double u[3], const double f[3]) {
@@ -95,7 +102,15 @@ static int wrap(int a, int n) { return ((a % n) + n) % n; }
  * (-u_wall, 0, 0) at the bottom plane z = -1/2. */
 int orc_lbm_step(int nx, int ny, int nz, double tau, double u_wall,
                  const double *f, const double *force, double *f_out) {
-    if (nx < 1 || ny < 1 || nz < 1 || !(tau > 0.5)) return -1;
+    return orc_lbm_step_eq(nx, ny, nz, tau, u_wall, f, force, f_out, 2);
+}
+
+/* The same step with the equilibrium of the given order: 2 for Eq.
+ * (equilibrium), 1 for the linearised one of Sec. IV.A (the forcing term is
+ * Eq. (latticeforce) in both; the paper changes only the equilibrium). */
+int orc_lbm_step_eq(int nx, int ny, int nz, double tau, double u_wall,
+                    const double *f, const double *force, double *f_out, int order) {
+    if (nx < 1 || ny < 1 || nz < 1 || !(tau > 0.5) || (order != 1 && order != 2)) return -1;
     const size_t N = (size_t)nx * ny * nz;
     const double cs2 = 1.0 / 3.0;
     int opp[19];
@@ -110,8 +125,8 @@ int orc_lbm_step(int nx, int ny, int nz, double tau, double u_wall,
                     for (int a = 0; a < 3; ++a) fc[a] = force[a * N + cell];
                 orc_moments(fi, fc, &rho, u);
                 for (int i = 0; i < 19; ++i) {
-                    double post = fi[i] - (fi[i] - orc_feq(i, rho, u)) / tau +
-                                  orc_guo(i, tau, u, fc);
+                    double eq = order == 2 ? orc_feq(i, rho, u) : orc_feq_linear(i, rho, u);
+                    double post = fi[i] - (fi[i] - eq) / tau + orc_guo(i, tau, u, fc);
                     int zt = z + C[i][2];
                     if (zt < 0 || zt >= nz) {
                         double uw = (zt >= nz) ? u_wall : -u_wall;

@@ -43,6 +43,9 @@ void orc_d3q19(int c[19][3], double w[19], int opp[19]);
 /* Eq. (equilibrium): f_i^eq = w_i rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u). */
 double orc_feq(int i, double rho, const double u[3]);
 
+/* Sec. IV.A: the linearised equilibrium w_i rho (1 + 3 c.u). */
+double orc_feq_linear(int i, double rho, const double u[3]);
+
 /* Eq. (latticeforce), Guo forcing term F_i for body force density f. */
 double orc_guo(int i, double tau, const double u[3], const double f[3]);
 
@@ -57,6 +60,9 @@ void orc_moments(const double fi[19], const double force[3], double *rho,
  * (velocity +u_wall).  f, f_out: [19][cells]; force: [3][cells] or NULL. */
 int orc_lbm_step(int nx, int ny, int nz, double tau, double u_wall,
                  const double *f, const double *force, double *f_out);
+/* The same with the equilibrium of order 2 (Eq. equilibrium) or 1 (Sec. IV.A). */
+int orc_lbm_step_eq(int nx, int ny, int nz, double tau, double u_wall,
+                    const double *f, const double *force, double *f_out, int order);
 
 /* Equilibrium populations of the linear Couette profile
  * u_x(z) = (2 u_wall / nz) (z - (nz - 1)/2), rho = 1. */
@@ -135,6 +141,11 @@ int orc_sim_n_nodes(const orc_sim *s);
 void orc_sim_init_couette(orc_sim *s);
 /* n_steps of the sub-step list: forces, spread, LBM, interpolate, advect. */
 int orc_sim_step(orc_sim *s, int n_steps);
+/* Variants: integrator 0 = Euler, Eq. (positionupdate); 1 = the
+ * Adams-Bashforth rule of Sec. II.C.  Equilibrium order 2 = Eq. (equilibrium),
+ * 1 = linearised (Sec. IV.A).  Return -1 for other values. */
+int orc_sim_set_integrator(orc_sim *s, int mode);
+int orc_sim_set_equilibrium(orc_sim *s, int order);
 void orc_sim_get_f(const orc_sim *s, double *f);
 void orc_sim_set_f(orc_sim *s, const double *f);
 void orc_sim_get_nodes(const orc_sim *s, double *x);

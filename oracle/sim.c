@@ -6,8 +6,14 @@
  *   3. one lattice Boltzmann step with f(X, t), Eq. (lbequation);
  *   4. node velocities u_i(t+1) by interpolation of the new lattice velocity
  *      at the old positions, Eq. (velocityinterpolation);
- *   5. Euler advection x_i(t+1) = x_i(t) + u_i(t+1), Eq. (positionupdate).
+ *   5. Euler advection x_i(t+1) = x_i(t) + u_i(t+1), Eq. (positionupdate),
+ *      or, as a variant, the Adams-Bashforth rule of Sec. II.C,
+ *      x_i(t+1) = x_i(t) + 3/2 u_i(t+1) - 1/2 u_i(t).
  * Test infrastructure only.
+ *
+ * Reading (Adams-Bashforth): the rule needs the velocity u_i(t) of the step
+ * before; the first step after the start, after the nodes were set by hand or
+ * after the integrator was chosen takes the Euler rule instead.
  *
  * Reading: the lattice velocity that is interpolated in sub-step 4 is
  * u(X, t+1) = (sum_i c_i f_i(X, t+1) + f(X, t)/2) / rho(X, t+1), i.e.
@@ -35,8 +41,9 @@ struct orc_sim {
     int n_caps, n_nodes, n_tri;
     int cap_node0[1024], cap_nn[1024], cap_tri0[1024], cap_nt[1024];
     double cap_ks[1024], cap_ka[1024];
-    double *X0, *x, *F, *u;
+    double *X0, *x, *F, *u, *u_prev;
     int *tri;
+    int integrator, eq_order, have_prev;
 };
 
 orc_sim *orc_sim_create(int nx, int ny, int nz, double tau, int delta_n,
@@ -47,6 +54,7 @@ orc_sim *orc_sim_create(int nx, int ny, int nz, double tau, int delta_n,
     if (!s) return NULL;
     s->nx = nx; s->ny = ny; s->nz = nz; s->n = delta_n;
     s->tau = tau; s->u_wall = u_wall;
+    s->eq_order = 2;
     s->N = (size_t)nx * ny * nz;
     s->f = (double *)calloc(19 * s->N, sizeof(double));
     s->f_new = (double *)calloc(19 * s->N, sizeof(double));
@@ -62,7 +70,7 @@ orc_sim *orc_sim_create(int nx, int ny, int nz, double tau, int delta_n,
 void orc_sim_destroy(orc_sim *s) {
     if (!s) return;
     free(s->f); free(s->f_new); free(s->force);
-    free(s->X0); free(s->x); free(s->F); free(s->u); free(s->tri);
+    free(s->X0); free(s->x); free(s->F); free(s->u); free(s->u_prev); free(s->tri);
     free(s);
 }
 
@@ -78,9 +86,11 @@ int orc_sim_add_capsule(orc_sim *s, int n_nodes, const double *X0, int n_tri,
     if (Fn) s->F = Fn;
     double *un = (double *)realloc(s->u, sizeof(double) * 3 * nn);
     if (un) s->u = un;
+    double *upn = (double *)realloc(s->u_prev, sizeof(double) * 3 * nn);
+    if (upn) s->u_prev = upn;
     int *tn = (int *)realloc(s->tri, sizeof(int) * 3 * nt);
     if (tn) s->tri = tn;
-    if (!X0n || !xn || !Fn || !un || !tn) return -2;
+    if (!X0n || !xn || !Fn || !un || !upn || !tn) return -2;
     for (int t = 0; t < 3 * n_tri; ++t) {
         if (tri[t] < 0 || tri[t] >= n_nodes) return -1;
         s->tri[3 * s->n_tri + t] = tri[t];
@@ -98,7 +108,21 @@ int orc_sim_add_capsule(orc_sim *s, int n_nodes, const double *X0, int n_tri,
     s->cap_ka[id] = ka;
     s->n_nodes = nn;
     s->n_tri = nt;
+    s->have_prev = 0;
     return id;
+}
+
+int orc_sim_set_integrator(orc_sim *s, int mode) {
+    if (mode != 0 && mode != 1) return -1;
+    s->integrator = mode;
+    s->have_prev = 0;
+    return 0;
+}
+
+int orc_sim_set_equilibrium(orc_sim *s, int order) {
+    if (order != 1 && order != 2) return -1;
+    s->eq_order = order;
+    return 0;
 }
 
 int orc_sim_n_nodes(const orc_sim *s) { return s->n_nodes; }
@@ -137,17 +161,22 @@ int orc_sim_step(orc_sim *s, int n_steps) {
         rc = orc_spread(s->nx, s->ny, s->nz, s->n, s->n_nodes, s->x, s->F, s->force);
         if (rc) break;
         /* 3. lattice Boltzmann step with f(X, t) */
-        rc = orc_lbm_step(s->nx, s->ny, s->nz, s->tau, s->u_wall, s->f, s->force, s->f_new);
+        rc = orc_lbm_step_eq(s->nx, s->ny, s->nz, s->tau, s->u_wall, s->f, s->force, s->f_new, s->eq_order);
         if (rc) break;
         double *tmp = s->f;
         s->f = s->f_new;
         s->f_new = tmp;
-        /* 4. interpolation of u(X, t+1) at x_i(t) */
+        /* 4. interpolation of u(X, t+1) at x_i(t); u_i(t) kept */
+        memcpy(s->u_prev, s->u, sizeof(double) * 3 * s->n_nodes);
         velocity_field(s, ufield, NULL);
         rc = orc_interpolate(s->nx, s->ny, s->nz, s->n, s->n_nodes, s->x, ufield, s->u);
         if (rc) break;
-        /* 5. Euler advection */
-        for (int k = 0; k < 3 * s->n_nodes; ++k) s->x[k] += s->u[k];
+        /* 5. advection: Euler, or Adams-Bashforth once u_i(t) exists */
+        if (s->integrator == 1 && s->have_prev)
+            for (int k = 0; k < 3 * s->n_nodes; ++k) s->x[k] += 1.5 * s->u[k] - 0.5 * s->u_prev[k];
+        else
+            for (int k = 0; k < 3 * s->n_nodes; ++k) s->x[k] += s->u[k];
+        s->have_prev = 1;
     }
     free(ufield);
     return rc;
@@ -164,6 +193,7 @@ void orc_sim_get_nodes(const orc_sim *s, double *x) {
 }
 void orc_sim_set_nodes(orc_sim *s, const double *x) {
     memcpy(s->x, x, sizeof(double) * 3 * s->n_nodes);
+    s->have_prev = 0;
 }
 void orc_sim_get_force_field(const orc_sim *s, double *force) {
     memcpy(force, s->force, sizeof(double) * 3 * s->N);
