@@ -56,6 +56,10 @@ def _args():
     p.add_argument("--no-adjoint", action="store_true", help="skip the config-5 adjoint timing")
     p.add_argument("--record-every", type=int, default=1,
                    help="steps between device records of the capsule reductions (sub-step 6)")
+    p.add_argument("--equilibrium", type=int, default=2, choices=[1, 2],
+                   help="2: Eq. (equilibrium); 1: the linearised equilibrium of Sec. IV.A")
+    p.add_argument("--integrator", type=int, default=0, choices=[0, 1],
+                   help="node advection: 0 Euler, 1 Adams-Bashforth")
     p.add_argument("--interp-mode", type=int, default=-1, choices=[-1, 0, 1],
                    help="interpolation: -1 automatic, 0 gather at the stencil cells, 1 cell velocities first")
     p.add_argument("--adjoint-only", action="store_true",
@@ -156,6 +160,8 @@ def _config(case, a):
         "storage": f"{case.precision} deviations from rest equilibrium",
         "step": "forces+spread, collide-stream, interpolate+advect, FP64 Taylor reductions recorded",
         "record_every": a.record_every,
+        "equilibrium": "second order, Eq. (equilibrium)" if a.equilibrium == 2 else "linearised, Sec. IV.A",
+        "advection": "Euler" if a.integrator == 0 else "Adams-Bashforth",
         "l2": f"inputs larger than L2: two population buffers of {19 * case.ncell * BYTES_PER_CELL[case.precision] // 38 / 1e6:.0f} MB each",
         "parallelism": "replicas (one independent simulation per rank)",
     }
@@ -300,9 +306,10 @@ def _ncu_traffic(workload: str, precision: str):
 
 # ---- CPU oracle ------------------------------------------------------------------------------
 
-def _oracle_run(case, budget_s: float, max_steps: int):
+def _oracle_run(case, budget_s: float, max_steps: int, a=None):
     """Times the FP64 oracle on the full workload: one untimed step, then as many
-    timed steps as fit in the budget (at least one, at most max_steps)."""
+    timed steps as fit in the budget (at least one, at most max_steps), with the
+    method variants of the run's arguments."""
     import oracle as O
 
     O.build()
@@ -311,6 +318,9 @@ def _oracle_run(case, budget_s: float, max_steps: int):
     for c in case.capsules:
         X0, tri = O.icosphere(c.subdivisions, c.radius, c.center)
         o.add_capsule(X0, tri, c.k_s, c.C * c.k_s)
+    if a is not None:
+        o.set_equilibrium(getattr(a, "equilibrium", 2))
+        o.set_integrator(getattr(a, "integrator", 0))
     t0 = time.perf_counter()
     o.step(1)
     t1 = time.perf_counter() - t0
@@ -407,6 +417,8 @@ def run_ours(a):
     stream = torch.cuda.Stream()
     sim = _make_sim(case, stream)
     sim.set_interp_mode(a.interp_mode)
+    sim.set_equilibrium(a.equilibrium)
+    sim.set_integrator(a.integrator)
     batch = isinstance(case, Batch)
     sim.set_taylor_recording(a.record_every, ring=(a.steps + a.warmup) // max(1, a.record_every) + 4096)
 
@@ -490,14 +502,14 @@ def run_ours(a):
         if batch:
             cells_done, dt = 0, 0.0
             for c in case.cases:
-                n, t = _oracle_run(c, a.cpu_budget_s / len(case.cases), a.steps)
+                n, t = _oracle_run(c, a.cpu_budget_s / len(case.cases), a.steps, a)
                 cells_done += c.ncell * n
                 dt += t
             cpu = {"value": round(cells_done / dt / 1e6, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
                    "sample": f"every run of the batch stepped by the FP64 oracle (single thread) for a "
                              f"bounded number of steps each, {dt:.1f} s in total"}
         else:
-            n, dt = _oracle_run(case, a.cpu_budget_s, a.steps)
+            n, dt = _oracle_run(case, a.cpu_budget_s, a.steps, a)
             cpu = {"value": round(cells * n / dt / 1e6, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
                    "sample": f"{n} full oracle steps (FP64, single thread) of the same workload after one "
                              f"untimed step, {dt:.1f} s"}
@@ -531,7 +543,7 @@ def run_reference(a):
         return
     case = _workload(a)
     w = min(a.warmup, 1)
-    n, dt = _oracle_run(case, max(a.cpu_budget_s, 30.0), a.steps)
+    n, dt = _oracle_run(case, max(a.cpu_budget_s, 30.0), a.steps, a)
     value = case.ncell * n / dt / 1e6
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MLUPS", "n_gpus": ws,

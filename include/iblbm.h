@@ -207,6 +207,19 @@ int iblbm_set_taylor_recording(iblbm_sim *sim, int every, int ring);
 int iblbm_get_taylor_records(iblbm_sim *sim, int capsule_id, int max_records,
                              double *out, int64_t *steps_out, int *n_records);
 
+/* Method variants the paper describes beside the main scheme.
+ * iblbm_set_integrator: node advection by Eq. (positionupdate) (mode 0, the
+ * default) or by the Adams-Bashforth rule of Sec. II.C,
+ * x_i(t+1) = x_i(t) + 3/2 u_i(t+1) - 1/2 u_i(t) (mode 1); the first step after
+ * the choice, after capsules are added or nodes are set takes the Euler rule
+ * (no u_i(t) yet).  iblbm_set_equilibrium: order 2 (default) for Eq.
+ * (equilibrium), order 1 for the linearised equilibrium
+ * w_i rho (1 + 3 c_i.u) of Sec. IV.A (the forcing term is Eq. (latticeforce)
+ * in both).  The adjoint covers mode 0 and order 2 only (IBLBM_ERR_STATE
+ * otherwise).  IBLBM_ERR_ARG for other values.  Synchronising. */
+int iblbm_set_integrator(iblbm_sim *sim, int mode);
+int iblbm_set_equilibrium(iblbm_sim *sim, int order);
+
 /* How the interpolation (Eq. velocityinterpolation) gets u(X, t+1): mode 0,
  * every node's lanes form u from the 19 populations and the force at each
  * stencil cell; mode 1, a pass first forms u once for every cell of the tiles

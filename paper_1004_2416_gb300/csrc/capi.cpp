@@ -67,6 +67,13 @@ struct iblbm_sim {
     uint8_t *flags[2] = {nullptr, nullptr};
     void *uvel = nullptr;  // velocity of the cells of the flagged tiles (Vec4 per cell)
     int interp_mode = -1;  // -1 automatic, 0 gather at the stencil cells, 1 cell velocities first
+    // Method variants: node advection 0 = Euler (Eq. positionupdate), 1 =
+    // Adams-Bashforth (Sec. II.C), which needs the node velocities of the step
+    // before (ab2_ready); equilibrium order 2 = Eq. (equilibrium), 1 = the
+    // linearised form of Sec. IV.A.
+    int integrator = 0;
+    bool ab2_ready = false;
+    int eq_order = 2;
     int *d_status = nullptr;
 
     std::vector<Capsule> caps;
@@ -387,6 +394,7 @@ int ensure_mesh(iblbm_sim *s) {
     CK(cudaStreamSynchronize(s->stream));
     s->dev_nodes = nn;
     s->mesh_dirty = false;
+    s->ab2_ready = false;
     return IBLBM_OK;
 }
 
@@ -460,6 +468,7 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) 
     a.tau = s->tau;
     a.u_wall = s->u_wall;
     a.status = s->d_status;
+    a.eq_order = s->eq_order;
     if (s->batch) {
         BatchArgs b{s->d_runs, s->d_items, s->n_items, s->batch_grid};
         launch_collide_batch(s->prec, b, a, s->stream);
@@ -483,7 +492,9 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) 
     }
     launch_interp_advect(s->prec, s->delta, s->L, s->mesh, pre ? s->uvel : nullptr, s->pop[n], s->force[n],
                          s->batch ? s->d_runs : nullptr, s->d_node_run, s->stream,
-                         side_rec ? s->snap_x[b] : nullptr, side_rec ? s->snap_lo[b] : nullptr);
+                         side_rec ? s->snap_x[b] : nullptr, side_rec ? s->snap_lo[b] : nullptr,
+                         s->integrator == 1 && s->ab2_ready ? 1 : 0);
+    s->ab2_ready = true;  // m.u now holds u_i(t+1)
     mark("interpolation + advection");
     if (ev) cudaEventRecord(ev[3], s->stream);
     if (record) {
@@ -1029,7 +1040,8 @@ int iblbm_step(iblbm_sim *s, int64_t n_steps) {
     const int period = s->rec_every > 0 ? s->rec_every : 1;
     int64_t left = n_steps;
     while (left > 0) {
-        if (left >= G && s->steps % period == 0) {
+        // a graph is captured with the Adams-Bashforth history in place
+        if (left >= G && s->steps % period == 0 && (s->integrator == 0 || s->ab2_ready)) {
             cudaGraphExec_t &g = s->graph[s->cur];
             if (!g) {
                 cudaGraph_t graph = nullptr;
@@ -1151,6 +1163,8 @@ int iblbm_adjoint_forward(iblbm_sim *s, int64_t n_steps, int checkpoint_every) {
     if (!s) return IBLBM_ERR_ARG;
     if (s->batch) return fail(s, IBLBM_ERR_STATE, "the adjoint works on a single lattice");
     if (s->caps.size() != 1) return fail(s, IBLBM_ERR_STATE, "the adjoint needs exactly one capsule");
+    if (s->integrator != 0 || s->eq_order != 2)
+        return fail(s, IBLBM_ERR_STATE, "the adjoint covers Euler advection and the full equilibrium only");
     if (n_steps < 1 || checkpoint_every < 1 || checkpoint_every > n_steps)
         return fail(s, IBLBM_ERR_ARG, "need n_steps >= 1 and 1 <= checkpoint_every <= n_steps");
     CK(cudaSetDevice(s->device));
@@ -1537,6 +1551,29 @@ int iblbm_sync(iblbm_sim *s) {
     return sync_status(s);
 }
 
+int iblbm_set_integrator(iblbm_sim *s, int mode) {
+    if (!s) return IBLBM_ERR_ARG;
+    if (mode != 0 && mode != 1) return fail(s, IBLBM_ERR_ARG, "integrator must be 0 (Euler) or 1 (Adams-Bashforth)");
+    join_side(s);
+    CK(cudaStreamSynchronize(s->stream));
+    drop_graphs(s);
+    s->integrator = mode;
+    s->ab2_ready = false;
+    s->adj.ready = false;
+    return IBLBM_OK;
+}
+
+int iblbm_set_equilibrium(iblbm_sim *s, int order) {
+    if (!s) return IBLBM_ERR_ARG;
+    if (order != 1 && order != 2) return fail(s, IBLBM_ERR_ARG, "equilibrium order must be 1 or 2");
+    join_side(s);
+    CK(cudaStreamSynchronize(s->stream));
+    drop_graphs(s);
+    s->eq_order = order;
+    s->adj.ready = false;
+    return IBLBM_OK;
+}
+
 int iblbm_set_interp_mode(iblbm_sim *s, int mode) {
     if (!s) return IBLBM_ERR_ARG;
     if (mode < -1 || mode > 1) return fail(s, IBLBM_ERR_ARG, "mode must be -1, 0 or 1");
@@ -1780,6 +1817,7 @@ int iblbm_set_nodes(iblbm_sim *s, int id, const double *host_in) {
     launch_f64_to_nodes(s->prec, s->mesh, first, count, s->d_scratch, s->stream);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s->stream));
+    s->ab2_ready = false;  // the velocity history no longer matches the positions
     return IBLBM_OK;
 }
 
@@ -1852,7 +1890,7 @@ struct CkptHeader {
     char magic[8];
     int32_t version, precision, delta, n_runs;
     int32_t nx, ny, nz, init_mode;
-    int32_t n_nodes, n_faces, n_caps, pad;
+    int32_t n_nodes, n_faces, n_caps, flags;  // flags bit 0: Adams-Bashforth history present
     int64_t steps;
     uint64_t pop_bytes, vec_bytes, flag_bytes, x_bytes, xlo_bytes, node_bytes;
 };
@@ -1897,6 +1935,7 @@ CkptHeader ckpt_header(const iblbm_sim *s) {
     h.n_nodes = s->mesh.n_nodes;
     h.n_faces = s->mesh.n_faces;
     h.n_caps = (int32_t)s->caps.size();
+    h.flags = s->ab2_ready ? 1 : 0;
     h.steps = s->steps;
     h.pop_bytes = s->pop_bytes;
     h.vec_bytes = s->vec_bytes;
@@ -2004,6 +2043,7 @@ int iblbm_checkpoint_restore(iblbm_sim *s, const void *buf, int on_device) {
     CK(cudaStreamSynchronize(s->stream));
     s->steps = h.steps;
     s->init_mode = h.init_mode;
+    s->ab2_ready = (h.flags & 1) != 0;
     s->adj.ready = false;
     return IBLBM_OK;
 }

@@ -244,7 +244,8 @@ __global__ void __launch_bounds__(256)
     k_interp_advect(int n_nodes, PosView<T> pos, const typename Vec4<T>::type *__restrict__ uvel,
                     const S *__restrict__ pop, const typename Vec4<T>::type *__restrict__ force,
                     typename Vec4<T>::type *__restrict__ nodeU, RunDesc single,
-                    const RunDesc *__restrict__ runs, const int *__restrict__ node_run, PosView<T> snap) {
+                    const RunDesc *__restrict__ runs, const int *__restrict__ node_run, PosView<T> snap,
+                    int ab2) {
     using V4 = typename Vec4<T>::type;
     const int lane = threadIdx.x & 31;
     const int node = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
@@ -325,8 +326,14 @@ __global__ void __launch_bounds__(256)
     ay = warp_sum(ay);
     az = warp_sum(az);
     if (lane == 0) {
+        if (ab2) {  // Sec. II.C: x += 3/2 u_i(t+1) - 1/2 u_i(t)
+            const V4 uo = nodeU[node];
+            pos.advance(node, T(1.5) * ax - T(0.5) * uo.x, T(1.5) * ay - T(0.5) * uo.y,
+                        T(1.5) * az - T(0.5) * uo.z, snap);
+        } else {  // Eq. (positionupdate)
+            pos.advance(node, ax, ay, az, snap);
+        }
         nodeU[node] = V4{ax, ay, az, T(0)};
-        pos.advance(node, ax, ay, az, snap);
     }
 }
 
@@ -426,7 +433,7 @@ static void force_spread_impl(const Lattice &L, const MeshDev &m, void *force, u
 template <int N, typename S, typename T>
 static void interp_impl(const Lattice &L, const MeshDev &m, const void *uvel, const void *pop,
                         const void *force, const RunDesc *runs, const int *node_run, cudaStream_t s,
-                        void *snap_x, void *snap_lo) {
+                        void *snap_x, void *snap_lo, int ab2) {
     using V4 = typename Vec4<T>::type;
     MeshDev sm{};
     sm.x = snap_x;
@@ -436,11 +443,11 @@ static void interp_impl(const Lattice &L, const MeshDev &m, const void *uvel, co
     if (uvel)
         k_interp_advect<N, S, T, true><<<nb, 32 * kNodesPerBlock, 0, s>>>(
             m.n_nodes, view<T>(m), (const V4 *)uvel, nullptr, nullptr, (V4 *)m.u, single_run(L), runs, node_run,
-            snap);
+            snap, ab2);
     else
         k_interp_advect<N, S, T, false><<<nb, 32 * kNodesPerBlock, 0, s>>>(
             m.n_nodes, view<T>(m), nullptr, (const S *)pop, (const V4 *)force, (V4 *)m.u, single_run(L), runs,
-            node_run, snap);
+            node_run, snap, ab2);
 }
 
 template <typename S, typename T>
@@ -479,20 +486,20 @@ void launch_flag_velocity(int prec, const Lattice &L, const void *pop, const voi
 
 void launch_interp_advect(int prec, int delta, const Lattice &L, const MeshDev &m, const void *uvel,
                           const void *pop, const void *force, const RunDesc *runs, const int *node_run,
-                          cudaStream_t s, void *snap_x, void *snap_lo) {
+                          cudaStream_t s, void *snap_x, void *snap_lo, int ab2) {
     if (m.n_nodes == 0) return;
     if (prec == kF64) {
-        if (delta == 2) interp_impl<2, double, double>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo);
-        else if (delta == 3) interp_impl<3, double, double>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo);
-        else interp_impl<4, double, double>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo);
+        if (delta == 2) interp_impl<2, double, double>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2);
+        else if (delta == 3) interp_impl<3, double, double>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2);
+        else interp_impl<4, double, double>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2);
     } else if (prec == kF32) {
-        if (delta == 2) interp_impl<2, float, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo);
-        else if (delta == 3) interp_impl<3, float, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo);
-        else interp_impl<4, float, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo);
+        if (delta == 2) interp_impl<2, float, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2);
+        else if (delta == 3) interp_impl<3, float, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2);
+        else interp_impl<4, float, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2);
     } else {
-        if (delta == 2) interp_impl<2, __half, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo);
-        else if (delta == 3) interp_impl<3, __half, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo);
-        else interp_impl<4, __half, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo);
+        if (delta == 2) interp_impl<2, __half, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2);
+        else if (delta == 3) interp_impl<3, __half, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2);
+        else interp_impl<4, __half, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2);
     }
 }
 

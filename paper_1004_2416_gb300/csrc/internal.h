@@ -105,6 +105,7 @@ struct CollideArgs {
     // optional: moments (j_x, j_y, j_z, rho - 1) of f(t) per cell, Vec4 (the
     // adjoint's recomputation keeps them); null in a plain step
     void *moments = nullptr;
+    int eq_order = 2;  // 2: Eq. (equilibrium); 1: the linearised form of Sec. IV.A
 };
 void launch_collide_stream(int prec, const Lattice &L, const CollideArgs &a, cudaStream_t s);
 // batched persistent variant: CollideArgs pointers are the concatenated buffers
@@ -135,10 +136,11 @@ void launch_flag_velocity(int prec, const Lattice &L, const void *pop, const voi
 // when not null, else of velocities formed at each stencil cell from the
 // populations pop and the force density force (the same arithmetic)
 // snap_x / snap_lo (may be null): a second copy of the advanced positions,
-// in the layout of m.x / m.x_lo
+// in the layout of m.x / m.x_lo.  ab2: advance by the Adams-Bashforth rule
+// with the previous node velocities in m.u instead of Euler's.
 void launch_interp_advect(int prec, int delta, const Lattice &L, const MeshDev &m, const void *uvel,
                           const void *pop, const void *force, const RunDesc *runs, const int *node_run,
-                          cudaStream_t s, void *snap_x = nullptr, void *snap_lo = nullptr);
+                          cudaStream_t s, void *snap_x = nullptr, void *snap_lo = nullptr, int ab2 = 0);
 // node data <-> host doubles [n][3]
 void launch_nodes_to_f64(int prec, const MeshDev &m, int which, int first, int count, double *out,
                          cudaStream_t s);

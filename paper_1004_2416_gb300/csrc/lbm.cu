@@ -21,7 +21,9 @@ namespace iblbm {
 // the neighbour cell x + c_i (periodic in x and y).  A value that would cross
 // a wall plane is reflected into the opposite direction of the same cell with
 // Ladd's moving-wall term -2 w_i (c_i . u_w) / c_s^2.
-template <typename S, typename T>
+// LIN: the linearised equilibrium w_i rho (1 + 3 c_i.u) of Sec. IV.A instead
+// of Eq. (equilibrium); the forcing term is Eq. (latticeforce) either way.
+template <typename S, typename T, bool LIN = false>
 __device__ __forceinline__ void collide_cell(const S *__restrict__ src, S *__restrict__ dst,
                                              const typename Vec4<T>::type *__restrict__ fcur,
                                              bool has_cur, int x, int y, int z, int nx, int ny,
@@ -74,8 +76,8 @@ __device__ __forceinline__ void collide_cell(const S *__restrict__ src, S *__res
         if (cx) cu += cx > 0 ? ux : -ux;
         if (cy) cu += cy > 0 ? uy : -uy;
         if (cz) cu += cz > 0 ? uz : -uz;
-        // Eq. (equilibrium) minus the rest weight
-        const T geq = w * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - uu15));
+        // Eq. (equilibrium) (or its linearised form) minus the rest weight
+        const T geq = LIN ? w * (drho + rho * (T(3) * cu)) : w * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - uu15));
         T post = g[i] - omega * (g[i] - geq);
         if (has_cur) {
             // Eq. (latticeforce) with c_s^2 = 1/3
@@ -100,7 +102,7 @@ __device__ __forceinline__ void collide_cell(const S *__restrict__ src, S *__res
 }
 
 // One thread per cell, one 32 x 8 x 1 tile per block.
-template <typename S, typename T>
+template <typename S, typename T, bool LIN>
 __global__ void __launch_bounds__(kTileX *kTileY)
     k_collide_stream(const S *__restrict__ src, S *__restrict__ dst,
                      const typename Vec4<T>::type *__restrict__ fcur,
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(kTileX *kTileY)
         if (threadIdx.x == 0 && threadIdx.y == 0) flag_old[tile] = 0;
     }
     if (!inside) return;
-    collide_cell<S, T>(src, dst, fcur, has_cur, x, y, z, nx, ny, nz, ncell, omega, u_wall, status, moments);
+    collide_cell<S, T, LIN>(src, dst, fcur, has_cur, x, y, z, nx, ny, nz, ncell, omega, u_wall, status, moments);
 }
 
 // Batched, persistent collide-and-stream over many independent lattices
@@ -134,7 +136,7 @@ __global__ void __launch_bounds__(kTileX *kTileY)
 // walks it with a grid stride.  A run's tiles have its own shape tx x ty
 // (tx * ty = 256 threads), picked per box size by the autotuner; the force
 // flags of a run use the same tiles.
-template <typename S, typename T>
+template <typename S, typename T, bool LIN>
 __global__ void __launch_bounds__(256)
     k_collide_batch(const S *__restrict__ src, S *__restrict__ dst,
                     const typename Vec4<T>::type *__restrict__ fcur,
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(256)
             if (threadIdx.x == 0) flag_old[tile] = 0;
         }
         if (inside)
-            collide_cell<S, T>(src + 19 * R.cell_off, dst + 19 * R.cell_off, fcur + R.cell_off,
+            collide_cell<S, T, LIN>(src + 19 * R.cell_off, dst + 19 * R.cell_off, fcur + R.cell_off,
                                has_cur, x, y, z, R.nx, R.ny, R.nz, R.ncell, (T)R.omega,
                                (T)R.u_wall, status);
     }
@@ -230,7 +232,8 @@ __host__ __device__ constexpr int rows_per_block() {
 }
 
 // WM: also write the moments of f(t), float4 (j, rho - 1) per cell.
-template <typename S, int LR, bool WM>
+// LIN: the linearised equilibrium (as collide_cell).
+template <typename S, int LR, bool WM, bool LIN = false>
 __global__ void __launch_bounds__(256, 2)
     k_collide_stream_x4(const S *__restrict__ src, S *__restrict__ dst,
                         const float4 *__restrict__ fcur, const uint8_t *__restrict__ flag_cur,
@@ -316,7 +319,8 @@ __global__ void __launch_bounds__(256, 2)
             if (cy) cu += cy > 0 ? uy[k] : -uy[k];
             if (cz) cu += cz > 0 ? uz[k] : -uz[k];
             const float rho = 1.f + drho[k];
-            const float geq = w * (drho[k] + rho * (3.f * cu + 4.5f * cu * cu - uu15[k]));
+            const float geq = LIN ? w * (drho[k] + rho * (3.f * cu))
+                                  : w * (drho[k] + rho * (3.f * cu + 4.5f * cu * cu - uu15[k]));
             p[k] = g[i][k] - omega * (g[i][k] - geq);
             if (has_cur) {
                 float cf = 0.f;
@@ -440,11 +444,18 @@ static void collide_x4(const Lattice &L, const CollideArgs &a, cudaStream_t s) {
     constexpr int rpb = rows_per_block<LR>();
     const int nrows = L.ny * L.nz;
     const unsigned nb = (unsigned)((nrows + rpb - 1) / rpb);
+    // the moments are kept only by the adjoint's recomputation, which runs
+    // with the full equilibrium
     if (a.moments)
         k_collide_stream_x4<S, LR, true><<<nb, 256, 0, s>>>(
             (const S *)a.src, (S *)a.dst, (const float4 *)a.fcur, a.flag_cur, (float4 *)a.fold,
             a.flag_old, L.ny, L.nz, (int)L.ncell, (float)(1.0 / a.tau), (float)a.u_wall, a.status,
             (float4 *)a.moments);
+    else if (a.eq_order == 1)
+        k_collide_stream_x4<S, LR, false, true><<<nb, 256, 0, s>>>(
+            (const S *)a.src, (S *)a.dst, (const float4 *)a.fcur, a.flag_cur, (float4 *)a.fold,
+            a.flag_old, L.ny, L.nz, (int)L.ncell, (float)(1.0 / a.tau), (float)a.u_wall, a.status,
+            nullptr);
     else
         k_collide_stream_x4<S, LR, false><<<nb, 256, 0, s>>>(
             (const S *)a.src, (S *)a.dst, (const float4 *)a.fcur, a.flag_cur, (float4 *)a.fold,
@@ -472,7 +483,8 @@ template <typename S, typename T>
 static void collide_impl(const Lattice &L, const CollideArgs &a, cudaStream_t s) {
     using V4 = typename Vec4<T>::type;
     dim3 grid(L.ntx, L.nty, L.nz), block(kTileX, kTileY);
-    k_collide_stream<S, T><<<grid, block, 0, s>>>(
+    auto kern = a.eq_order == 1 ? k_collide_stream<S, T, true> : k_collide_stream<S, T, false>;
+    kern<<<grid, block, 0, s>>>(
         (const S *)a.src, (S *)a.dst, (const V4 *)a.fcur, a.flag_cur, (V4 *)a.fold, a.flag_old,
         L.nx, L.ny, L.nz, L.ntx, L.nty, L.ncell, (T)(1.0 / a.tau), (T)a.u_wall, a.status,
         (V4 *)a.moments);
@@ -490,7 +502,8 @@ void launch_collide_stream(int prec, const Lattice &L, const CollideArgs &a, cud
 template <typename S, typename T>
 static void collide_batch_impl(const BatchArgs &b, const CollideArgs &a, cudaStream_t s) {
     using V4 = typename Vec4<T>::type;
-    k_collide_batch<S, T><<<b.grid, 256, 0, s>>>(
+    auto kern = a.eq_order == 1 ? k_collide_batch<S, T, true> : k_collide_batch<S, T, false>;
+    kern<<<b.grid, 256, 0, s>>>(
         (const S *)a.src, (S *)a.dst, (const V4 *)a.fcur, a.flag_cur, (V4 *)a.fold, a.flag_old,
         b.runs, b.items, b.n_items, a.status);
 }
@@ -505,9 +518,12 @@ void launch_collide_batch(int prec, const BatchArgs &b, const CollideArgs &a, cu
 int collide_batch_blocks_per_sm(int prec) {
     int n = 0;
     cudaError_t e;
-    if (prec == kF64) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide_batch<double, double>, 256, 0);
-    else if (prec == kF32) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide_batch<float, float>, 256, 0);
-    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide_batch<__half, float>, 256, 0);
+    if (prec == kF64)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide_batch<double, double, false>, 256, 0);
+    else if (prec == kF32)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide_batch<float, float, false>, 256, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide_batch<__half, float, false>, 256, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 1;

@@ -103,6 +103,8 @@ _SIGS = {
     "iblbm_adjoint_taylor": (_int, [_vp, _int, ctypes.c_int64, _int, _dp, _dp, _dp, _dp]),
     "iblbm_checkpoint_size": (_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "iblbm_set_interp_mode": (_int, [_vp, _int]),
+    "iblbm_set_integrator": (_int, [_vp, _int]),
+    "iblbm_set_equilibrium": (_int, [_vp, _int]),
     "iblbm_checkpoint_save": (_int, [_vp, _vp, _int]),
     "iblbm_checkpoint_restore": (_int, [_vp, _vp, _int]),
     "iblbm_batch_create": (_int, [ctypes.POINTER(_vp), ctypes.POINTER(iblbm_run_spec), _int, _int, _int,
@@ -434,6 +436,14 @@ class Sim:
         _check(iblbm_adjoint_taylor(self._h, capsule_id, int(n_steps), int(checkpoint_every), ctypes.byref(dks),
                                     ctypes.byref(dca), _d(gX0), ctypes.byref(D)), self._h)
         return {"D": D.value, "dD_dks": dks.value, "dD_dCa": dca.value, "dD_dX0": gX0}
+
+    def set_integrator(self, mode: int):
+        """0: Euler (Eq. positionupdate); 1: Adams-Bashforth (Sec. II.C)."""
+        _check(iblbm_set_integrator(self._h, int(mode)), self._h)
+
+    def set_equilibrium(self, order: int):
+        """2: Eq. (equilibrium); 1: the linearised form of Sec. IV.A."""
+        _check(iblbm_set_equilibrium(self._h, int(order)), self._h)
 
     def set_interp_mode(self, mode: int):
         """-1 automatic (default), 0 gather at the stencil cells, 1 cell velocities first."""
