@@ -22,7 +22,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
-_SOURCES = ["lattice.c", "ibm.c", "membrane.c", "mesh.c", "taylor.c", "sim.c"]
+_SOURCES = ["lattice.c", "ibm.c", "membrane.c", "mesh.c", "taylor.c", "diag.c", "sim.c"]
 _lock = threading.Lock()
 _lib = None
 
@@ -89,6 +89,10 @@ def _declare(L):
     L.orc_icosphere.argtypes = [c_int, c_double, _dp, _dp, _ip]
     L.orc_taylor.argtypes = [c_int, _dp, c_int, _ip, _dp]
     L.orc_eig3.argtypes = [_dp, _dp, _dp]
+    L.orc_tank_treading.argtypes = [c_int, _dp, _dp, _dp, _dp, c_double, _dp]
+    L.orc_tank_treading.restype = c_double
+    L.orc_ellipsoid_fit.argtypes = [c_int, _dp, _dp, _dp]
+    L.orc_face_area_stats.argtypes = [c_int, _ip, _dp, _dp, _dp]
     L.orc_sim_create.argtypes = [c_int, c_int, c_int, c_double, c_int, c_double]
     L.orc_sim_create.restype = c_void_p
     L.orc_sim_destroy.argtypes = [c_void_p]
@@ -361,3 +365,35 @@ class Sim:
         start = sum(n for n, _ in self._caps[:cid])
         n, tri = self._caps[cid]
         return taylor(x[start:start + n], tri)
+
+
+# ---- diagnostics ------------------------------------------------------------------------------
+
+def tank_treading(x0, x1, c0, c1, dt: float):
+    """(per-node omega [n], mean omega) about the centroids in the xz plane."""
+    x0, x1 = _f64(x0), _f64(x1)
+    om = np.zeros(x0.shape[0])
+    mean = lib().orc_tank_treading(x0.shape[0], _d(x0), _d(x1), _d(_f64(c0)), _d(_f64(c1)), dt, _d(om))
+    return om, mean
+
+
+FIT_KEYS = ("zeta_x", "zeta_y", "zeta_z", "zeta_xz", "r_a", "r_b", "r_c", "D", "theta")
+
+
+def ellipsoid_fit(x, c) -> dict:
+    x = _f64(x)
+    out = np.zeros(9)
+    rc = lib().orc_ellipsoid_fit(x.shape[0], _d(x), _d(_f64(c)), _d(out))
+    if rc:
+        raise ValueError(f"orc_ellipsoid_fit returned {rc}")
+    return dict(zip(FIT_KEYS, out.tolist()))
+
+
+def face_area_stats(tri, X0, x):
+    tri = _i32(tri)
+    out = np.zeros(3)
+    rc = lib().orc_face_area_stats(tri.shape[0], _i(tri), _d(_f64(X0)), _d(_f64(x)), _d(out))
+    if rc:
+        raise ValueError(f"orc_face_area_stats returned {rc}")
+    return {"mean": out[0], "std": out[1], "max": out[2]}
+

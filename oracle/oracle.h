@@ -126,6 +126,18 @@ int orc_taylor(int n_nodes, const double *x, int n_tri, const int *tri,
  * ascending, eigenvectors in the columns of vec. */
 void orc_eig3(const double A[9], double eval[3], double vec[9]);
 
+/* ---- diag.c : shape and mesh diagnostics --------------------------------- */
+
+/* Angular velocity omega_i = -dphi_i/dt of every node about the centroid in
+ * the xz plane between two snapshots (c0, c1 the centroids); returns the mean. */
+double orc_tank_treading(int n, const double *x0, const double *x1, const double c0[3],
+                         const double c1[3], double dt, double *omega);
+/* Eq. (chisquare) fit about c: out[9] = {zeta_x, zeta_y, zeta_z, zeta_xz,
+ * r_a, r_b, r_c, D, theta}. */
+int orc_ellipsoid_fit(int n, const double *x, const double c[3], double out[9]);
+/* Relative face area deviation dA/A0: out = {mean, standard deviation, max |.|}. */
+int orc_face_area_stats(int n_tri, const int *tri, const double *X0, const double *x, double out[3]);
+
 /* ---- sim.c : Sec. II.C sub-step list ------------------------------------- */
 
 typedef struct orc_sim orc_sim;
