@@ -446,6 +446,15 @@ def run_ours(a):
     nodes_per_s = grp.ws * case.n_nodes * a.steps / (ms_max * 1e-3)
     steps_rec, rec = sim.taylor_records(0, max_records=1)
     D_last = float(rec[-1][0]) if len(rec) else None
+    final_shape = None
+    if not batch and case.capsules:
+        # diagnostics of capsule 0 after the timed steps (host side, untimed)
+        T = sim.taylor(0)
+        fit = B.ellipsoid_fit(sim.get_nodes(0), [T["c_x"], T["c_y"], T["c_z"]])
+        q = sim.mesh_quality(0)
+        final_shape = {"D": T["D"], "theta": T["theta"], "D_ellipsoid_fit": fit["D"],
+                       "theta_ellipsoid_fit": fit["theta"], "face_area_dev_mean": q["dA_mean"],
+                       "face_area_dev_std": q["dA_std"], "volume_drift": q["dV"]}
 
     # per-kernel device times with CUDA events on the launching stream
     prof = sim.profile_kernels(a.profile_steps)
@@ -529,6 +538,7 @@ def run_ours(a):
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": KERNEL_LAUNCHES_PER_STEP * a.steps,
         "final_D": D_last,
+        "final_shape": final_shape,
         "adjoint": adjoint,
     }
     sim.close()

@@ -313,6 +313,32 @@ int iblbm_icosphere(int subdivisions, double radius, const double center[3],
 int iblbm_taylor_gradient(const double *nodes, int n_nodes, const int32_t *tri,
                           int n_tri, double *D_out, double *dD_dx);
 
+/* Host-only diagnostics of a capsule shape (Sec. III), no device needed.
+ * iblbm_tank_treading: the angular velocity omega_i = -dphi_i/dt of each node
+ * between two snapshots [n][3] taken dt apart, phi_i its angle about the
+ * capsule centroid (c_then, c_now) projected on the xz plane, measured from +x
+ * toward +z (so the rotation of simple shear u_x = gdot z is positive; a stiff
+ * sphere turns at gdot/2), the angle difference taken in (-pi, pi];
+ * omega_nodes [n] and *omega_mean (the mean) may be NULL.
+ * iblbm_ellipsoid_fit: the linear least-squares fit of Eq. (chisquare) to the
+ * nodes [n][3] relative to center, out[9] = {zeta_x, zeta_y, zeta_z, zeta_xz,
+ * r_a, r_b, r_c (semiaxes 1/sqrt of the eigenvalues of Q, descending),
+ * D = (r_a - r_c)/(r_a + r_c), theta (major axis in the xz plane, from +x
+ * toward +z, x component >= 0)}; IBLBM_ERR_ARG when the fit is singular or Q
+ * is not positive definite.  Errors: IBLBM_ERR_ARG for NULL pointers or
+ * sizes; the message is in iblbm_last_error(NULL). */
+int iblbm_tank_treading(const double *x_then, const double *x_now, int n_nodes,
+                        const double c_then[3], const double c_now[3], double dt,
+                        double *omega_nodes, double *omega_mean);
+int iblbm_ellipsoid_fit(const double *nodes, int n_nodes, const double center[3],
+                        double out[9]);
+
+/* Mesh degradation of a capsule (Sec. V, Fig. degrade) from its current nodes:
+ * out[4] = {mean, standard deviation (about the mean, over faces) and largest
+ * magnitude of the relative face area deviation dA/A0 against the reference
+ * faces, relative volume drift V/V0 - 1 (signed tetrahedra)}.  Synchronising. */
+int iblbm_mesh_quality(iblbm_sim *sim, int capsule_id, double out[4]);
+
 /* ---- read-back and state access (synchronising) ------------------------------ */
 
 /* Lattice velocity u = (sum_i c_i f_i + f/2)/rho of the current populations

@@ -1551,6 +1551,45 @@ int iblbm_sync(iblbm_sim *s) {
     return sync_status(s);
 }
 
+int iblbm_tank_treading(const double *x_then, const double *x_now, int n_nodes, const double c_then[3],
+                        const double c_now[3], double dt, double *omega_nodes, double *omega_mean) {
+    if (!x_then || !x_now || !c_then || !c_now || n_nodes < 1 || !(dt != 0.0) || !std::isfinite(dt)) {
+        set_thread_error("need node arrays, centroids, n_nodes >= 1 and a finite dt != 0");
+        return IBLBM_ERR_ARG;
+    }
+    const double m = tank_treading(n_nodes, x_then, x_now, c_then, c_now, dt, omega_nodes);
+    if (omega_mean) *omega_mean = m;
+    return IBLBM_OK;
+}
+
+int iblbm_ellipsoid_fit(const double *nodes, int n_nodes, const double center[3], double out[9]) {
+    if (!nodes || !center || !out || n_nodes < 4) {
+        set_thread_error("need nodes, center, out and n_nodes >= 4");
+        return IBLBM_ERR_ARG;
+    }
+    if (ellipsoid_fit(n_nodes, nodes, center, out)) {
+        set_thread_error("the node cloud does not determine an ellipsoid (singular or not positive)");
+        return IBLBM_ERR_ARG;
+    }
+    return IBLBM_OK;
+}
+
+int iblbm_mesh_quality(iblbm_sim *s, int capsule_id, double out[4]) {
+    if (!s || !out) return IBLBM_ERR_ARG;
+    if (capsule_id < 0 || capsule_id >= (int)s->caps.size()) return fail(s, IBLBM_ERR_ARG, "no such capsule");
+    const Capsule &c = s->caps[capsule_id];
+    std::vector<double> x(3 * (size_t)c.n_nodes);
+    int rc = iblbm_get_nodes(s, capsule_id, x.data());
+    if (rc) return rc;
+    std::vector<int> tri(3 * (size_t)c.n_faces);
+    for (size_t k = 0; k < tri.size(); ++k) tri[k] = s->tri[3 * (size_t)c.face0 + k] - c.node0;
+    const double *X0 = &s->X0[3 * (size_t)c.node0];
+    face_area_stats(c.n_faces, tri.data(), X0, x.data(), out);
+    const double v0 = closed_volume(c.n_faces, tri.data(), X0);
+    out[3] = closed_volume(c.n_faces, tri.data(), x.data()) / v0 - 1.0;
+    return IBLBM_OK;
+}
+
 int iblbm_set_integrator(iblbm_sim *s, int mode) {
     if (!s) return IBLBM_ERR_ARG;
     if (mode != 0 && mode != 1) return fail(s, IBLBM_ERR_ARG, "integrator must be 0 (Euler) or 1 (Adams-Bashforth)");

@@ -220,5 +220,12 @@ void sym_eig3(const double A[9], double val[3], double vec[9]);
 // Taylor deformation D of a closed membrane and, if grad is not null, dD/dx
 // [n][3] (host, FP64).
 double taylor_D_and_gradient(const double *x, int n, const int *tri, int m, double *grad);
+// Diagnostics (host): node angular velocities about the centroid in the xz
+// plane (returns the mean); the fit of Eq. (chisquare); face area deviations.
+double tank_treading(int n, const double *x0, const double *x1, const double c0[3], const double c1[3],
+                     double dt, double *omega);
+int ellipsoid_fit(int n, const double *x, const double c[3], double out[9]);
+void face_area_stats(int m, const int *tri, const double *X0, const double *x, double out[3]);
+double closed_volume(int m, const int *tri, const double *x);
 
 }  // namespace iblbm

@@ -42,6 +42,10 @@ double triple(const V3 &a, const V3 &b, const V3 &c) {
            a.z * (b.x * c.y - b.y * c.x);
 }
 
+V3 cross(const V3 &a, const V3 &b) {
+    return V3{a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
 }  // namespace
 
 void icosphere(int m, double r, const double c[3], std::vector<double> &nodes,
@@ -333,6 +337,138 @@ double taylor_D_and_gradient(const double *x, int n, const int *tri, int m, doub
         }
     }
     return D;
+}
+
+
+// ---- shape and mesh diagnostics (Sec. III, Sec. V) -------------------------------------
+
+// Angular velocity of each node about the centroid in the xz plane between
+// two snapshots dt apart: omega = -(phi1 - phi0)/dt, phi from +x toward +z
+// (positive in the rotation sense of u_x = gdot z), the difference taken in
+// (-pi, pi].  Returns the mean.
+double tank_treading(int n, const double *x0, const double *x1, const double c0[3], const double c1[3],
+                     double dt, double *omega) {
+    double sum = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double dx0 = x0[3 * i] - c0[0], dz0 = x0[3 * i + 2] - c0[2];
+        const double dx1 = x1[3 * i] - c1[0], dz1 = x1[3 * i + 2] - c1[2];
+        // angle from the first to the second direction: atan2 of their cross
+        // and dot products, already in (-pi, pi]
+        const double cross = dx0 * dz1 - dz0 * dx1, dot = dx0 * dx1 + dz0 * dz1;
+        const double w = -std::atan2(cross, dot) / dt;
+        if (omega) omega[i] = w;
+        sum += w;
+    }
+    return n > 0 ? sum / n : 0.0;
+}
+
+// Linear least-squares fit of Eq. (chisquare) about c by the normal equations
+// (4 x 4, Cholesky), then the semiaxes 1/sqrt(lambda) of Q: the y axis is
+// decoupled, the xz block is a 2 x 2 symmetric matrix solved in closed form.
+// out = {zeta_x, zeta_y, zeta_z, zeta_xz, r_a, r_b, r_c, D, theta}.
+int ellipsoid_fit(int n, const double *x, const double c[3], double out[9]) {
+    if (n < 4) return -1;
+    double M[4][4] = {}, r[4] = {};
+    for (int i = 0; i < n; ++i) {
+        const double px = x[3 * i] - c[0], py = x[3 * i + 1] - c[1], pz = x[3 * i + 2] - c[2];
+        const double row[4] = {px * px, py * py, pz * pz, -2.0 * px * pz};
+        for (int a = 0; a < 4; ++a) {
+            r[a] += row[a];
+            for (int b = 0; b < 4; ++b) M[a][b] += row[a] * row[b];
+        }
+    }
+    double Lc[4][4] = {};
+    for (int j = 0; j < 4; ++j) {
+        double d = M[j][j];
+        for (int k = 0; k < j; ++k) d -= Lc[j][k] * Lc[j][k];
+        if (!(d > 0.0)) return -2;
+        Lc[j][j] = std::sqrt(d);
+        for (int i = j + 1; i < 4; ++i) {
+            double v = M[i][j];
+            for (int k = 0; k < j; ++k) v -= Lc[i][k] * Lc[j][k];
+            Lc[i][j] = v / Lc[j][j];
+        }
+    }
+    double y[4], z[4];
+    for (int i = 0; i < 4; ++i) {
+        double v = r[i];
+        for (int k = 0; k < i; ++k) v -= Lc[i][k] * y[k];
+        y[i] = v / Lc[i][i];
+    }
+    for (int i = 3; i >= 0; --i) {
+        double v = y[i];
+        for (int k = i + 1; k < 4; ++k) v -= Lc[k][i] * z[k];
+        z[i] = v / Lc[i][i];
+    }
+    // xz block [[zx, -zxz], [-zxz, zz]]
+    const double a = z[0], b = -z[3], d = z[2];
+    const double mid = 0.5 * (a + d), rad = std::sqrt(0.25 * (a - d) * (a - d) + b * b);
+    const double l_small = mid - rad, l_big = mid + rad, l_y = z[1];
+    if (!(l_small > 0.0) || !(l_y > 0.0)) return -3;
+    double ax[3] = {1.0 / std::sqrt(l_small), 1.0 / std::sqrt(l_y), 1.0 / std::sqrt(l_big)};
+    std::sort(ax, ax + 3, [](double p, double q) { return p > q; });
+    // major axis in the xz plane: eigenvector of the smaller eigenvalue
+    double vx, vz;
+    if (std::fabs(b) > 0.0) {
+        vx = b;
+        vz = l_small - a;
+        if (std::fabs(vx) + std::fabs(vz) == 0.0) vx = 1.0;
+    } else if (a <= d) {
+        vx = 1.0;
+        vz = 0.0;
+    } else {
+        vx = 0.0;
+        vz = 1.0;
+    }
+    if (vx < 0.0) {
+        vx = -vx;
+        vz = -vz;
+    }
+    for (int k = 0; k < 4; ++k) out[k] = z[k];
+    out[4] = ax[0];
+    out[5] = ax[1];
+    out[6] = ax[2];
+    out[7] = (ax[0] - ax[2]) / (ax[0] + ax[2]);
+    out[8] = std::atan2(vz, vx);
+    return 0;
+}
+
+// Relative face area deviation dA/A0 of the faces [m][3] between reference
+// X0 and current x: {mean, standard deviation about the mean (1/m), max |.|}.
+// Volume enclosed by the outward-oriented faces [m][3]: sum of the signed
+// tetrahedra spanned with the first node.
+double closed_volume(int m, const int *tri, const double *x) {
+    const double *o = x + 3 * tri[0];
+    double v = 0.0;
+    for (int f = 0; f < m; ++f) {
+        const double *a = x + 3 * tri[3 * f], *b = x + 3 * tri[3 * f + 1], *c = x + 3 * tri[3 * f + 2];
+        v += triple(V3{a[0] - o[0], a[1] - o[1], a[2] - o[2]}, V3{b[0] - o[0], b[1] - o[1], b[2] - o[2]},
+                    V3{c[0] - o[0], c[1] - o[1], c[2] - o[2]});
+    }
+    return v / 6.0;
+}
+
+void face_area_stats(int m, const int *tri, const double *X0, const double *x, double out[3]) {
+    auto area = [&](const double *p, int f) {
+        const double *a = p + 3 * tri[3 * f], *b = p + 3 * tri[3 * f + 1], *c = p + 3 * tri[3 * f + 2];
+        const V3 u{b[0] - a[0], b[1] - a[1], b[2] - a[2]}, v{c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+        const V3 w = cross(u, v);
+        return 0.5 * std::sqrt(w.x * w.x + w.y * w.y + w.z * w.z);
+    };
+    std::vector<double> rel(m);
+    double sum = 0.0, mx = 0.0;
+    for (int f = 0; f < m; ++f) {
+        const double a0 = area(X0, f);
+        rel[f] = (area(x, f) - a0) / a0;
+        sum += rel[f];
+        mx = std::max(mx, std::fabs(rel[f]));
+    }
+    const double mean = m > 0 ? sum / m : 0.0;
+    double ss = 0.0;
+    for (int f = 0; f < m; ++f) ss += (rel[f] - mean) * (rel[f] - mean);
+    out[0] = mean;
+    out[1] = m > 0 ? std::sqrt(ss / m) : 0.0;
+    out[2] = mx;
 }
 
 }  // namespace iblbm

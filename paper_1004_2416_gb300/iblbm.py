@@ -104,6 +104,9 @@ _SIGS = {
     "iblbm_checkpoint_size": (_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "iblbm_set_interp_mode": (_int, [_vp, _int]),
     "iblbm_set_integrator": (_int, [_vp, _int]),
+    "iblbm_tank_treading": (_int, [_dp, _dp, _int, _dp, _dp, _dbl, _dp, _dp]),
+    "iblbm_ellipsoid_fit": (_int, [_dp, _int, _dp, _dp]),
+    "iblbm_mesh_quality": (_int, [_vp, _int, _dp]),
     "iblbm_set_equilibrium": (_int, [_vp, _int]),
     "iblbm_checkpoint_save": (_int, [_vp, _vp, _int]),
     "iblbm_checkpoint_restore": (_int, [_vp, _vp, _int]),
@@ -437,6 +440,12 @@ class Sim:
                                     ctypes.byref(dca), _d(gX0), ctypes.byref(D)), self._h)
         return {"D": D.value, "dD_dks": dks.value, "dD_dCa": dca.value, "dD_dX0": gX0}
 
+    def mesh_quality(self, capsule_id: int = 0) -> dict:
+        """Face-area deviation statistics and volume drift of a capsule."""
+        out = np.zeros(4)
+        _check(iblbm_mesh_quality(self._h, capsule_id, _d(out)), self._h)
+        return {"dA_mean": out[0], "dA_std": out[1], "dA_max": out[2], "dV": out[3]}
+
     def set_integrator(self, mode: int):
         """0: Euler (Eq. positionupdate); 1: Adams-Bashforth (Sec. II.C)."""
         _check(iblbm_set_integrator(self._h, int(mode)), self._h)
@@ -472,3 +481,27 @@ class Sim:
         out = np.empty(16, np.float64)
         _check(iblbm_get_taylor(self._h, capsule_id, _d(out)), self._h)
         return dict(zip(TAYLOR_KEYS, out.tolist()))
+
+
+def tank_treading(x_then, x_now, c_then, c_now, dt: float):
+    """Per-node angular velocities [n] about the centroid in the xz plane, and
+    their mean (host only)."""
+    x0 = np.ascontiguousarray(x_then, np.float64)
+    x1 = np.ascontiguousarray(x_now, np.float64)
+    om = np.empty(x0.shape[0], np.float64)
+    mean = ctypes.c_double()
+    _check(iblbm_tank_treading(_d(x0), _d(x1), x0.shape[0], _d(np.ascontiguousarray(c_then, np.float64)),
+                               _d(np.ascontiguousarray(c_now, np.float64)), float(dt), _d(om), ctypes.byref(mean)))
+    return om, mean.value
+
+
+FIT_KEYS = ("zeta_x", "zeta_y", "zeta_z", "zeta_xz", "r_a", "r_b", "r_c", "D", "theta")
+
+
+def ellipsoid_fit(nodes, center) -> dict:
+    """The fit of Eq. (chisquare) about center (host only)."""
+    x = np.ascontiguousarray(nodes, np.float64)
+    out = np.empty(9, np.float64)
+    _check(iblbm_ellipsoid_fit(_d(x), x.shape[0], _d(np.ascontiguousarray(center, np.float64)), _d(out)))
+    return dict(zip(FIT_KEYS, out.tolist()))
+

@@ -97,3 +97,33 @@ def test_taylor_gradient_against_oracle_finite_differences():
         d /= np.linalg.norm(d)
         fd = (O.taylor(x + h * d, tri)["D"] - O.taylor(x - h * d, tri)["D"]) / (2 * h)
         assert np.sum(g * d) == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+def test_diagnostics_against_oracle():
+    """The library's host diagnostics (normal equations and a closed-form 2 x 2
+    eigen-solution for the fit; cross/dot angles for the rotation) against the
+    oracle's (QR and Jacobi; atan2 differences) on a deformed, rotated and
+    jittered icosphere."""
+    import oracle as O
+    from paper_1004_2416_gb300 import iblbm as B
+
+    rng = np.random.default_rng(8)
+    X0, tri = O.icosphere(3, 6.0, (0.0, 0.0, 0.0))
+    th = 0.37
+    R = np.array([[np.cos(th), 0, -np.sin(th)], [0, 1, 0], [np.sin(th), 0, np.cos(th)]])
+    x = (X0 * np.array([1.25, 0.95, 0.8])) @ R.T + 0.02 * rng.standard_normal(X0.shape)
+    c = np.array([20.0, 30.0, 15.0])
+    x = x + c
+    a = B.ellipsoid_fit(x, c)
+    b = O.ellipsoid_fit(x, c)
+    for k in O.FIT_KEYS:
+        assert a[k] == pytest.approx(b[k], rel=1e-10, abs=1e-12), k
+    # tank-treading between two snapshots
+    y = (x - c) @ np.array([[np.cos(0.02), 0, np.sin(0.02)], [0, 1, 0], [-np.sin(0.02), 0, np.cos(0.02)]]).T + c + 0.3
+    om_a, m_a = B.tank_treading(x, y, c, c + 0.3, 2.0)
+    om_b, m_b = O.tank_treading(x, y, c, c + 0.3, 2.0)
+    assert np.allclose(om_a, om_b, rtol=1e-12, atol=1e-14)
+    assert m_a == pytest.approx(m_b, rel=1e-12)
+    assert m_a == pytest.approx(0.01, rel=1e-9)
+    with pytest.raises(B.IblbmError):
+        B.ellipsoid_fit(x[:3], c)
