@@ -44,9 +44,10 @@ def _args():
     p.add_argument("--steps", type=int, default=20000)
     p.add_argument("--warmup", type=int, default=200)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["config1", "config2", "config3", "config4", "config5"],
+    p.add_argument("--workload", choices=["config1", "config2", "config3", "config4", "config5",
+                                          "convergence35", "convergence70", "convergence140"],
                    default="config2")
-    p.add_argument("--delta", type=int, default=4, help="config 2 only")
+    p.add_argument("--delta", type=int, default=4, help="stencil of config 2 and the convergence workloads")
     p.add_argument("--G", type=float, default=0.0125, help="config 2 only")
     p.add_argument("--precision", default=None, help="override the workload's storage precision")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -84,6 +85,9 @@ def _workload(a):
         case = W.config4()
     elif a.workload == "config5":
         case = W.config5()
+    elif a.workload.startswith("convergence"):
+        # the coupled-convergence series of Sec. IV.C (phi from --delta, default 4)
+        case = W.convergence_case(int(a.workload[len("convergence"):]), a.delta)
     else:
         case = W.config2(G=a.G, delta=a.delta)
     if a.precision:

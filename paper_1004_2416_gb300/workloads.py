@@ -95,6 +95,20 @@ def config5() -> Case:
     return single_capsule("config5-64^3-fp32-r8-1280f-phi3", 64, 8.0, 3, 0.0125, 3, "fp32", 2000)
 
 
+def convergence_case(H: int, delta: int, precision: str = "fp32", Re: float = 0.02, G: float = 0.01) -> Case:
+    """The coupled-convergence series of Sec. IV.C (Tab. convergence): a cubic
+    box of side H with H/r = 10, N_f = 1280, 5120, 20480 faces for H = 35, 70,
+    140 (mean edge / dx = 0.53), Re = gdot r^2 / nu = 0.02, G = 0.01, tau = 1,
+    run to kappa t = gdot t / G = 120."""
+    m = {35: 3, 70: 4, 140: 5}[H]
+    r = H / 10.0
+    gdot = Re * eta() / (r * r)
+    steps = int(round(120.0 * G / gdot))
+    c = Capsule(((H - 1) / 2, (H - 1) / 2, (H - 1) / 2), r, m, k_s_for(G, r, gdot))
+    return Case(f"convergence-H{H}-{precision}-{20 * 4 ** m}f-phi{delta}", (H, H, H), TAU, delta, precision,
+                u_wall_for(H, gdot), [c], steps)
+
+
 def config3_specs(seed: int = 3, n_runs: int = 64):
     """Independent runs: (side, radius, subdivisions, G) per run."""
     rng = np.random.default_rng(seed)
