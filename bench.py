@@ -283,8 +283,9 @@ def _peaks():
 
 
 def _kernel_source_hash() -> str:
+    """Hash of the sources that define the collide-and-stream kernels."""
     h = hashlib.sha256()
-    for f in ("lbm.cu", "device_common.cuh", "internal.h"):
+    for f in ("lbm.cu", "device_common.cuh"):
         with open(os.path.join(ROOT, "paper_1004_2416_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
