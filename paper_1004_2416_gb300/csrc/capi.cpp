@@ -46,15 +46,17 @@ struct iblbm_sim {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    // Side stream for the Taylor record of a step.  The interpolation of a
-    // recorded step also writes the new positions into one of two snapshot
-    // buffers, which the record reads; it runs concurrently with the next
-    // steps and is joined before an interpolation writes its buffer again.
+    // Side stream for the Taylor records.  The interpolation of a recorded
+    // step also writes the new positions into the next slot of a ring of
+    // 2 kTaylorBatch snapshots (two halves); when a half is full (or at a
+    // flush) one launch on the side stream reduces its snapshots, concurrently
+    // with the next steps, and is joined before the half is written again.
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
     bool side_pending[2] = {false, false};
-    void *snap_x[2] = {nullptr, nullptr}, *snap_lo[2] = {nullptr, nullptr};
-    int rec_buf = 0;  // snapshot buffer of the next record
+    void *snap_x = nullptr, *snap_lo = nullptr;  // [2 kTaylorBatch][n_nodes] in the layout of mesh.x / x_lo
+    int rec_half = 0, rec_fill = 0;  // half being filled and its snapshots so far
+    int rec_batch = 1;               // snapshots per half (<= kTaylorBatch)
     const char *launch_fail = nullptr;  // first kernel group whose launch failed
     iblbm_allocator alloc{};
     bool has_alloc = false;
@@ -204,6 +206,7 @@ size_t real_bytes(const iblbm_sim *s) { return s->prec == kF64 ? 8 : 4; }
 
 void free_ring(iblbm_sim *s);
 void join_side(iblbm_sim *s);
+void reduce_snapshots(iblbm_sim *s);
 
 // (Re)builds the device membrane tables after capsules were added.  Current
 // node positions of existing capsules are kept.
@@ -241,12 +244,15 @@ int ensure_mesh(iblbm_sim *s) {
     m.n_caps = nc;
     m.x = A(v4 * nn);
     m.x_lo = s->prec == kF64 ? nullptr : A(v4 * nn);
-    for (int b = 0; b < 2; ++b) {
-        s->snap_x[b] = A(v4 * nn);
-        s->snap_lo[b] = s->prec == kF64 ? nullptr : A(v4 * nn);
-        if (!s->snap_x[b] || (s->prec != kF64 && !s->snap_lo[b]))
-            return fail(s, IBLBM_ERR_OOM, "membrane table allocation failed");
-    }
+    s->snap_x = A(2 * kTaylorBatch * v4 * nn);
+    s->snap_lo = s->prec == kF64 ? nullptr : A(2 * kTaylorBatch * v4 * nn);
+    if (!s->snap_x || (s->prec != kF64 && !s->snap_lo))
+        return fail(s, IBLBM_ERR_OOM, "membrane table allocation failed");
+    s->rec_half = 0;
+    s->rec_fill = 0;
+    // batches pay where the launches cost more than the reductions (few faces);
+    // a large suspension reduces each record at once
+    s->rec_batch = nf <= 32768 ? kTaylorBatch : 1;
     m.F = A(v4 * nn);
     m.u = A(v4 * nn);
     void *adj_off = A(sizeof(int) * (nn + 1));
@@ -377,7 +383,7 @@ int ensure_mesh(iblbm_sim *s) {
         p.blk_nface = (const int *)P(sizeof(int) * nb);
         p.cap_blk0 = (const int *)P(sizeof(int) * (nc + 1));
         p.origin = (const double *)P(sizeof(double) * 3 * nc);
-        p.partial = (double *)P(sizeof(double) * 16 * nb);
+        p.partial = (double *)P(sizeof(double) * 16 * nb * kTaylorBatch);
         p.out = (double *)P(sizeof(double) * 12 * nc);
         p.ticket = (unsigned *)P(sizeof(unsigned));
         if (!p.blk_cap || !p.blk_face0 || !p.blk_nface || !p.cap_blk0 || !p.origin || !p.partial ||
@@ -484,15 +490,18 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) 
         mark("velocity of the flagged cells");
     }
     const bool side_rec = record && !ev;  // timed runs keep the record on the main stream
-    const int b = s->rec_buf;
-    if (side_rec && s->side_pending[b]) {  // an earlier record still reads this snapshot
-        cudaStreamWaitEvent(s->stream, s->ev_join[b], 0);
-        s->side_pending[b] = false;
+    const int h = s->rec_half;
+    if (side_rec && s->rec_fill == 0 && s->side_pending[h]) {  // the half's last batch still reads it
+        cudaStreamWaitEvent(s->stream, s->ev_join[h], 0);
+        s->side_pending[h] = false;
         mark("join of the Taylor record");
     }
+    const size_t slot = (size_t)h * s->rec_batch + s->rec_fill;
+    const size_t v4 = 4 * real_bytes(s) * (size_t)s->mesh.n_nodes;
+    void *sx = side_rec ? (char *)s->snap_x + slot * v4 : nullptr;
+    void *sl = side_rec && s->snap_lo ? (char *)s->snap_lo + slot * (size_t)16 * s->mesh.n_nodes : nullptr;
     launch_interp_advect(s->prec, s->delta, s->L, s->mesh, pre ? s->uvel : nullptr, s->pop[n], s->force[n],
-                         s->batch ? s->d_runs : nullptr, s->d_node_run, s->stream,
-                         side_rec ? s->snap_x[b] : nullptr, side_rec ? s->snap_lo[b] : nullptr,
+                         s->batch ? s->d_runs : nullptr, s->d_node_run, s->stream, sx, sl,
                          s->integrator == 1 && s->ab2_ready ? 1 : 0);
     s->ab2_ready = true;  // m.u now holds u_i(t+1)
     mark("interpolation + advection");
@@ -500,17 +509,8 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) 
     if (record) {
         if (ev) {
             launch_taylor(s->prec, s->mesh, s->plan, true, s->stream);
-        } else {
-            MeshDev snap = s->mesh;
-            snap.x = s->snap_x[b];
-            snap.x_lo = s->snap_lo[b];
-            cudaEventRecord(s->ev_fork, s->stream);
-            cudaStreamWaitEvent(s->side, s->ev_fork, 0);
-            mark("fork of the Taylor record");
-            launch_taylor(s->prec, snap, s->plan, true, s->side);
-            cudaEventRecord(s->ev_join[b], s->side);
-            s->side_pending[b] = true;
-            s->rec_buf = 1 - b;
+        } else if (++s->rec_fill == s->rec_batch) {
+            reduce_snapshots(s);
         }
         mark("Taylor record");
     }
@@ -518,8 +518,28 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) 
     s->cur = n;
 }
 
-// Makes the main stream wait for the outstanding Taylor records.
+// Reduces the snapshots of the half being filled on the side stream (one
+// launch) and moves on to the other half.
+void reduce_snapshots(iblbm_sim *s) {
+    const int h = s->rec_half;
+    if (s->rec_fill > 0) {
+        cudaEventRecord(s->ev_fork, s->stream);
+        cudaStreamWaitEvent(s->side, s->ev_fork, 0);
+        launch_taylor_snapshots(s->prec, s->mesh, s->plan, true, s->snap_x, s->snap_lo, h * s->rec_batch,
+                                2 * s->rec_batch, s->rec_fill, s->side);
+        cudaEventRecord(s->ev_join[h], s->side);
+        s->side_pending[h] = true;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess && !s->launch_fail) s->launch_fail = "Taylor record";
+    }
+    s->rec_half = 1 - h;
+    s->rec_fill = 0;
+}
+
+// Reduces any snapshots not yet reduced and makes the main stream wait for
+// the outstanding Taylor records.
 void join_side(iblbm_sim *s) {
+    if (s->rec_fill > 0) reduce_snapshots(s);
     for (int b = 0; b < 2; ++b)
         if (s->side_pending[b]) {
             cudaStreamWaitEvent(s->stream, s->ev_join[b], 0);
@@ -1050,7 +1070,8 @@ int iblbm_step(iblbm_sim *s, int64_t n_steps) {
                 // capture; the graph joins its own records before it ends, so
                 // no event recorded inside the capture is waited on outside it.
                 join_side(s);
-                s->rec_buf = 0;  // a graph starts with nothing pending and snapshot 0
+                s->rec_half = 0;  // a graph starts with nothing pending, at the first half
+                s->rec_fill = 0;
                 CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
                 for (int k = 0; k < G; ++k) enqueue_step(s, record_after(s, k));
                 join_side(s);

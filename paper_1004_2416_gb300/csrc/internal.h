@@ -187,7 +187,7 @@ struct TaylorPlan {
     const int *blk_nface;   // [total_blocks]
     const int *cap_blk0;    // [n_caps + 1] first block of each capsule
     const double *origin;   // [n_caps][3]
-    double *partial;        // scratch [total_blocks][16]
+    double *partial;        // scratch [kTaylorBatch][total_blocks][16]
     double *out;            // [n_caps][12] results of an immediate reduction
     double *ring;           // [ring_len][n_caps][12] recorded results (or null)
     int ring_len;
@@ -206,6 +206,12 @@ inline int taylor_faces_per_block(long long total_faces) {
 }
 // record = false: results to p.out; record = true: to the next ring slot.
 void launch_taylor(int prec, const MeshDev &m, const TaylorPlan &p, bool record, cudaStream_t s);
+// The same for n_snap (<= kTaylorBatch) position snapshots in one launch:
+// snapshot k in slot (first + k) % slots of a ring of snapshots laid out like
+// m.x / m.x_lo ([slots][n_nodes]); recorded to n_snap consecutive ring records.
+constexpr int kTaylorBatch = 8;
+void launch_taylor_snapshots(int prec, const MeshDev &m, const TaylorPlan &p, bool record, const void *snap_x,
+                             const void *snap_lo, int first, int slots, int n_snap, cudaStream_t s);
 
 // Message returned by iblbm_last_error(NULL) in the calling thread (capi.cpp).
 void set_thread_error(const std::string &msg);

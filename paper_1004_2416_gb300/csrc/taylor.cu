@@ -3,6 +3,9 @@
 // tensor I_ab = 1/5 sum_faces A_i (r_i^2 delta_ab r_g - r_ia r_ib r_ig) n_ig
 // about the centroid.
 //
+// Recorded reductions take several position snapshots per launch (grid y),
+// so the cost of the launches is shared by consecutive records.
+//
 // The faces of a capsule are split over several blocks (FP64 arithmetic is
 // scarce per SM, so a capsule is spread over many SMs; in the float builds the
 // per-face terms are formed in float and only the sums are in double).  Three launches, each
@@ -34,6 +37,10 @@ struct NodeRead<double> {
         dvec4 q = x[n];
         p[0] = q.x; p[1] = q.y; p[2] = q.z;
     }
+    // the same view moved to snapshot k of a ring of snapshots of `stride` nodes
+    __device__ __forceinline__ NodeRead at(long long k, long long stride) const {
+        return NodeRead{x + k * stride};
+    }
 };
 template <>
 struct NodeRead<float> {
@@ -45,6 +52,18 @@ struct NodeRead<float> {
         p[1] = (double)h.y + (double)l.y;
         p[2] = (double)h.z + (double)l.z;
     }
+    __device__ __forceinline__ NodeRead at(long long k, long long stride) const {
+        return NodeRead{hi + k * stride, lo + k * stride};
+    }
+};
+
+// A launch reduces n_snap position snapshots at once (grid y): snapshot k
+// lives in slot (first + k) of a ring of `slots` snapshots of n_nodes each
+// (one snapshot, slot 0, for the current positions).
+struct SnapSet {
+    int first, slots, n_snap;
+    long long stride;
+    __device__ __forceinline__ long long slot(int k) const { return (first + k) % slots; }
 };
 
 constexpr int kTB = kTaylorThreads;  // threads per block
@@ -187,10 +206,13 @@ struct FaceMath<NodeRead<float>> {
 };
 
 template <typename R>
-__global__ void __launch_bounds__(kTB) k_taylor_stage1(R nodes, const int4 *__restrict__ tri, TaylorPlan p) {
+__global__ void __launch_bounds__(kTB) k_taylor_stage1(R nodes0, const int4 *__restrict__ tri, TaylorPlan p,
+                                                       SnapSet ss) {
     __shared__ double sh[kTB / 32][5];
+    const R nodes = nodes0.at(ss.slot(blockIdx.y), ss.stride);
     const int b = blockIdx.x;
     const int cap = p.blk_cap[b];
+    double *partial = p.partial + (size_t)blockIdx.y * p.total_blocks * 16;
     double v[5] = {0, 0, 0, 0, 0};
     for (int j = threadIdx.x; j < p.blk_nface[b]; j += kTB) {
         const int4 t = tri[p.blk_face0[b] + j];
@@ -200,31 +222,35 @@ __global__ void __launch_bounds__(kTB) k_taylor_stage1(R nodes, const int4 *__re
     }
     block_sum<5>(v, sh);
     if (threadIdx.x == 0)
-        for (int k = 0; k < 5; ++k) p.partial[16 * b + k] = v[k];
+        for (int k = 0; k < 5; ++k) partial[16 * b + k] = v[k];
 }
 
 // Totals of K partial entries (from entry `first`) over the blocks of one
 // capsule, by one full warp: lane l sums blocks l, l+32, ... in order, then a
 // fixed butterfly; every lane returns the same totals.
 template <int K>
-__device__ __forceinline__ void capsule_totals(const TaylorPlan &p, int cap, int first, double tot[K]) {
+__device__ __forceinline__ void capsule_totals(const TaylorPlan &p, const double *partial, int cap, int first,
+                                               double tot[K]) {
     const int lane = threadIdx.x & 31;
     for (int k = 0; k < K; ++k) tot[k] = 0.0;
     for (int b = p.cap_blk0[cap] + lane; b < p.cap_blk0[cap + 1]; b += 32)
-        for (int k = 0; k < K; ++k) tot[k] += p.partial[16 * b + first + k];
+        for (int k = 0; k < K; ++k) tot[k] += partial[16 * b + first + k];
     for (int k = 0; k < K; ++k)
         for (int o = 16; o > 0; o >>= 1) tot[k] += __shfl_xor_sync(0xffffffffu, tot[k], o);
 }
 
 template <typename R>
-__global__ void __launch_bounds__(kTB) k_taylor_stage2(R nodes, const int4 *__restrict__ tri, TaylorPlan p) {
+__global__ void __launch_bounds__(kTB) k_taylor_stage2(R nodes0, const int4 *__restrict__ tri, TaylorPlan p,
+                                                       SnapSet ss) {
     __shared__ double sh[kTB / 32][6];
     __shared__ double cen_sh[3];
+    const R nodes = nodes0.at(ss.slot(blockIdx.y), ss.stride);
     const int b = blockIdx.x;
     const int cap = p.blk_cap[b];
+    double *partial = p.partial + (size_t)blockIdx.y * p.total_blocks * 16;
     if (threadIdx.x < 32) {
         double tot[5];
-        capsule_totals<5>(p, cap, 0, tot);
+        capsule_totals<5>(p, partial, cap, 0, tot);
         if (threadIdx.x == 0)
             for (int k = 0; k < 3; ++k) cen_sh[k] = p.origin[3 * cap + k] + tot[2 + k] / (4.0 * tot[0]);
     }
@@ -238,26 +264,27 @@ __global__ void __launch_bounds__(kTB) k_taylor_stage2(R nodes, const int4 *__re
     }
     block_sum<6>(v, sh);
     if (threadIdx.x == 0)
-        for (int k = 0; k < 6; ++k) p.partial[16 * b + 8 + k] = v[k];
+        for (int k = 0; k < 6; ++k) partial[16 * b + 8 + k] = v[k];
 }
 
 // One warp per capsule, 8 capsules per block, as many blocks as needed (the
-// FP64 work is spread over the SMs).  In recording mode every block writes its
-// capsules into the next ring slot and the last block to finish advances the
-// record counter.
-__global__ void __launch_bounds__(256) k_taylor_stage3(TaylorPlan p, int record) {
+// FP64 work is spread over the SMs), grid y over the snapshots.  In recording
+// mode snapshot k goes to ring record count + k, and the last block to finish
+// advances the record counter by the number of snapshots.
+__global__ void __launch_bounds__(256) k_taylor_stage3(TaylorPlan p, int record, SnapSet ss) {
     double *base = p.out;
     unsigned long long count = 0;
     if (record) {
         count = *p.ring_count;
-        base = p.ring + (size_t)(count % (unsigned long long)p.ring_len) * p.n_caps * 12;
+        base = p.ring + (size_t)((count + blockIdx.y) % (unsigned long long)p.ring_len) * p.n_caps * 12;
     }
+    const double *partial = p.partial + (size_t)blockIdx.y * p.total_blocks * 16;
     const int lane = threadIdx.x & 31;
     const int cap = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (cap < p.n_caps) {
         double tot[5], I[6];
-        capsule_totals<5>(p, cap, 0, tot);
-        capsule_totals<6>(p, cap, 8, I);
+        capsule_totals<5>(p, partial, cap, 0, tot);
+        capsule_totals<6>(p, partial, cap, 8, I);
         if (lane == 0) {
             double *o = base + 12 * cap;
             o[0] = tot[0];
@@ -271,27 +298,35 @@ __global__ void __launch_bounds__(256) k_taylor_stage3(TaylorPlan p, int record)
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
-            if (atomicAdd(p.ticket, 1u) == gridDim.x - 1) {
+            if (atomicAdd(p.ticket, 1u) == gridDim.x * gridDim.y - 1) {
                 *p.ticket = 0u;
-                *p.ring_count = count + 1;
+                *p.ring_count = count + gridDim.y;
             }
         }
     }
 }
 
 template <typename R>
-static void taylor_impl(R nodes, const MeshDev &m, const TaylorPlan &p, bool record, cudaStream_t s) {
-    k_taylor_stage1<R><<<p.total_blocks, kTB, 0, s>>>(nodes, (const int4 *)m.tri, p);
-    k_taylor_stage2<R><<<p.total_blocks, kTB, 0, s>>>(nodes, (const int4 *)m.tri, p);
-    k_taylor_stage3<<<(p.n_caps + 7) / 8, 256, 0, s>>>(p, record ? 1 : 0);
+static void taylor_impl(R nodes, const MeshDev &m, const TaylorPlan &p, bool record, SnapSet ss,
+                        cudaStream_t s) {
+    const dim3 g12(p.total_blocks, ss.n_snap), g3((p.n_caps + 7) / 8, ss.n_snap);
+    k_taylor_stage1<R><<<g12, kTB, 0, s>>>(nodes, (const int4 *)m.tri, p, ss);
+    k_taylor_stage2<R><<<g12, kTB, 0, s>>>(nodes, (const int4 *)m.tri, p, ss);
+    k_taylor_stage3<<<g3, 256, 0, s>>>(p, record ? 1 : 0, ss);
 }
 
 void launch_taylor(int prec, const MeshDev &m, const TaylorPlan &p, bool record, cudaStream_t s) {
-    if (p.n_caps == 0 || (record && !p.ring)) return;
+    launch_taylor_snapshots(prec, m, p, record, m.x, m.x_lo, 0, 1, 1, s);
+}
+
+void launch_taylor_snapshots(int prec, const MeshDev &m, const TaylorPlan &p, bool record, const void *snap_x,
+                             const void *snap_lo, int first, int slots, int n_snap, cudaStream_t s) {
+    if (p.n_caps == 0 || n_snap < 1 || (record && !p.ring)) return;
+    const SnapSet ss{first, slots, n_snap, (long long)m.n_nodes};
     if (prec == kF64)
-        taylor_impl(NodeRead<double>{(const dvec4 *)m.x}, m, p, record, s);
+        taylor_impl(NodeRead<double>{(const dvec4 *)snap_x}, m, p, record, ss, s);
     else
-        taylor_impl(NodeRead<float>{(const float4 *)m.x, (const float4 *)m.x_lo}, m, p, record, s);
+        taylor_impl(NodeRead<float>{(const float4 *)snap_x, (const float4 *)snap_lo}, m, p, record, ss, s);
 }
 
 
