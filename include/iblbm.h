@@ -79,6 +79,9 @@ typedef struct {
     double tau;
     double u_wall;
     int n_runs;        /* lattices of a batch (1 for a single lattice) */
+    int64_t kernel_launches; /* kernels the library has launched for time steps
+                                (membrane, collide, interpolation and record
+                                kernels; a graph replay counts its kernels) */
 } iblbm_info;
 
 /* One independent lattice of a batch (see iblbm_batch_create). */

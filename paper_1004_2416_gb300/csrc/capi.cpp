@@ -143,6 +143,8 @@ struct iblbm_sim {
     int init_mode = 0;
 
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int64_t graph_kernels[2] = {0, 0};  // kernels in each captured graph
+    int64_t launches = 0;               // kernels launched for time steps
     int graph_len = 0;
     int64_t steps = 0;
     std::string err;
@@ -515,6 +517,7 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) 
         mark("Taylor record");
     }
     if (ev) cudaEventRecord(ev[4], s->stream);
+    s->launches += 3 + (pre ? 1 : 0) + (record && ev ? 3 : 0);
     s->cur = n;
 }
 
@@ -527,6 +530,7 @@ void reduce_snapshots(iblbm_sim *s) {
         cudaStreamWaitEvent(s->side, s->ev_fork, 0);
         launch_taylor_snapshots(s->prec, s->mesh, s->plan, true, s->snap_x, s->snap_lo, h * s->rec_batch,
                                 2 * s->rec_batch, s->rec_fill, s->side);
+        s->launches += 3;
         cudaEventRecord(s->ev_join[h], s->side);
         s->side_pending[h] = true;
         cudaError_t e = cudaGetLastError();
@@ -920,6 +924,7 @@ int iblbm_get_info(const iblbm_sim *s, iblbm_info *out) {
     out->n_runs = s->batch ? (int)s->runs.size() : 1;
     out->tau = s->tau;
     out->u_wall = s->u_wall;
+    out->kernel_launches = s->launches;
     return IBLBM_OK;
 }
 
@@ -1072,11 +1077,14 @@ int iblbm_step(iblbm_sim *s, int64_t n_steps) {
                 join_side(s);
                 s->rec_half = 0;  // a graph starts with nothing pending, at the first half
                 s->rec_fill = 0;
+                const int64_t launches0 = s->launches;
                 CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
                 for (int k = 0; k < G; ++k) enqueue_step(s, record_after(s, k));
                 join_side(s);
                 cudaError_t e = cudaStreamEndCapture(s->stream, &graph);
                 s->cur = cur0;
+                s->graph_kernels[cur0] = s->launches - launches0;  // counted when replayed
+                s->launches = launches0;
                 if (e != cudaSuccess) return cuda_fail(s, e, "graph capture");
                 // kernel nodes keep the priority of the stream they were captured on
                 e = cudaGraphInstantiate(&g, graph, cudaGraphInstantiateFlagUseNodePriority);
@@ -1088,6 +1096,7 @@ int iblbm_step(iblbm_sim *s, int64_t n_steps) {
             }
             join_side(s);
             CK(cudaGraphLaunch(g, s->stream));
+            s->launches += s->graph_kernels[s->cur];
             for (int k = 0; k < G; ++k)
                 if (record_after(s, k)) s->rec_steps.push_back(s->steps + k + 1);
             left -= G;  // G is even: buffer parity unchanged

@@ -60,7 +60,7 @@ class iblbm_info(ctypes.Structure):
     _fields_ = [("nx", _int), ("ny", _int), ("nz", _int), ("precision", _int),
                 ("delta_points", _int), ("n_capsules", _int), ("n_nodes", _int),
                 ("n_faces", _int), ("step", ctypes.c_int64), ("tau", _dbl), ("u_wall", _dbl),
-                ("n_runs", _int)]
+                ("n_runs", _int), ("kernel_launches", ctypes.c_int64)]
 
 
 class iblbm_run_spec(ctypes.Structure):

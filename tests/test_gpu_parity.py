@@ -336,3 +336,26 @@ def test_interp_modes_bit_identical(prec):
     assert np.abs(out[0][1]).max() > 0
     assert np.array_equal(out[0][0], out[1][0])
     assert np.array_equal(out[0][1], out[1][1])
+
+
+def test_kernel_launch_count():
+    """The library counts the kernels it launches for time steps, graph
+    replays included: three per step (spreading, collide, interpolation), one
+    more with the per-cell velocity pass, and three per batch of records."""
+    case = _small_case(precision="fp32", steps=0)
+    g = gpu_sim(case)
+    g.set_interp_mode(0)
+    n0 = g.info().kernel_launches
+    g.step(70)  # two 32-step graphs and six direct steps
+    assert g.info().kernel_launches - n0 == 3 * 70
+    g.set_interp_mode(1)
+    n1 = g.info().kernel_launches
+    g.step(40)
+    assert g.info().kernel_launches - n1 == 4 * 40
+    g.set_interp_mode(0)
+    g.set_taylor_recording(1, ring=256)
+    n2 = g.info().kernel_launches
+    g.step(64)  # two graphs of 32 steps, each reducing its records in four batches of eight
+    g.sync()
+    assert g.info().kernel_launches - n2 == 3 * 64 + 3 * 8
+    g.close()
