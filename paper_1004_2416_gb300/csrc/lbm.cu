@@ -169,11 +169,22 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// Vector loads and stores of 4 consecutive cells of one direction.
+// Vector loads and stores of 4 consecutive cells of one direction.  The
+// *_raw forms move the stored values without the binary16 scale (kScale
+// storage units per unit of g; a power of two, so scaling is exact).
 template <typename S>
 struct Quad;
 template <>
 struct Quad<float> {
+    static constexpr float kScale = 1.f;
+    static __device__ __forceinline__ void load_raw(const float *p, float2 &a, float2 &b) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+        a = make_float2(q.x, q.y);
+        b = make_float2(q.z, q.w);
+    }
+    static __device__ __forceinline__ void store_raw(float *p, float a, float b, float c, float d) {
+        *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+    }
     static __device__ __forceinline__ void load(const float *p, float v[4]) {
         const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
         v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
@@ -184,6 +195,20 @@ struct Quad<float> {
 };
 template <>
 struct Quad<__half> {
+    static constexpr float kScale = kHalfScale;
+    static __device__ __forceinline__ void load_raw(const __half *p, float2 &a, float2 &b) {
+        const uint2 q = __ldg(reinterpret_cast<const uint2 *>(p));
+        a = __half22float2(*reinterpret_cast<const __half2 *>(&q.x));
+        b = __half22float2(*reinterpret_cast<const __half2 *>(&q.y));
+    }
+    static __device__ __forceinline__ void store_raw(__half *p, float a, float b, float c, float d) {
+        const __half2 lo = __floats2half2_rn(a, b);
+        const __half2 hi = __floats2half2_rn(c, d);
+        uint2 q;
+        q.x = *reinterpret_cast<const unsigned *>(&lo);
+        q.y = *reinterpret_cast<const unsigned *>(&hi);
+        *reinterpret_cast<uint2 *>(p) = q;
+    }
     static __device__ __forceinline__ void load(const __half *p, float v[4]) {
         const uint2 q = __ldg(reinterpret_cast<const uint2 *>(p));
         const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&q.x));
@@ -213,6 +238,24 @@ struct Quad<__half> {
 // its own lane with a scalar store, and the receiving edge lane stores the
 // other three elements of its quad as scalars: no barrier and no shared
 // memory.  One force flag per 32-cell segment of a row.
+// Paired FP32 arithmetic (two cells per instruction).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Scalar store of a value already in storage units.
+template <typename S>
+struct StoreRaw;
+template <>
+struct StoreRaw<float> {
+    static __device__ __forceinline__ void store(float *p, float v) { *p = v; }
+};
+template <>
+struct StoreRaw<__half> {
+    static __device__ __forceinline__ void store(__half *p, float v) { *p = __float2half_rn(v); }
+};
+
 template <int LR>
 __device__ __forceinline__ float from_left(float v, int lane) {
     constexpr int W = LR <= 32 ? LR : 32;
@@ -270,42 +313,71 @@ __global__ void __launch_bounds__(256, 2)
     __syncwarp();  // every lane of the segment has read its flag
     if (has_old && active && x0 % FTX == 0) flag_old[fidx] = 0;
 
-    float g[19][4];
+    // Arithmetic on cell pairs (0,1) and (2,3) with the paired FP32
+    // instructions of sm_100+, in storage units: G = kScale g, so binary16
+    // values are used as loaded (exact power-of-two scale folded into the
+    // per-cell quantities).
+    constexpr float SC = Quad<S>::kScale, ISC = 1.f / Quad<S>::kScale;
+    float2 g[19][2];
 #pragma unroll
-    for (int i = 0; i < 19; ++i) Quad<S>::load(src + (size_t)i * ncell + cell0, g[i]);
+    for (int i = 0; i < 19; ++i) Quad<S>::load_raw(src + (size_t)i * ncell + cell0, g[i][0], g[i][1]);
 
-    float drho[4], ux[4], uy[4], uz[4], fx[4], fy[4], fz[4], uu15[4], uf[4];
+    // per cell: moments, velocity with the half force, and the pair vectors
+    // of the per-direction arithmetic
+    float2 Ux[2], Uy[2], Uz[2], Ds[2], Rs[2], Nuu[2], Fx[2], Fy[2], Fz[2], Uf[2];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        float d = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+    for (int h = 0; h < 2; ++h) {
+        float2 d = make_float2(0.f, 0.f), jx = d, jy = d, jz = d;
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
-            d += g[i][k];
-            if (q_cx(i)) jx += q_cx(i) > 0 ? g[i][k] : -g[i][k];
-            if (q_cy(i)) jy += q_cy(i) > 0 ? g[i][k] : -g[i][k];
-            if (q_cz(i)) jz += q_cz(i) > 0 ? g[i][k] : -g[i][k];
+            d = add2(d, g[i][h]);
+            if (q_cx(i)) jx = q_cx(i) > 0 ? add2(jx, g[i][h]) : sub2(jx, g[i][h]);
+            if (q_cy(i)) jy = q_cy(i) > 0 ? add2(jy, g[i][h]) : sub2(jy, g[i][h]);
+            if (q_cz(i)) jz = q_cz(i) > 0 ? add2(jz, g[i][h]) : sub2(jz, g[i][h]);
         }
-        if constexpr (WM) {
-            if (active) moments[cell0 + k] = make_float4(jx, jy, jz, d);
-        }
-        fx[k] = fy[k] = fz[k] = 0.f;
+        Ds[h] = d;
+        float fv[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
         if (has_cur) {
-            const float4 f = fcur[cell0 + k];
-            fx[k] = f.x; fy[k] = f.y; fz[k] = f.z;
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const float4 f = fcur[cell0 + 2 * h + e];
+                fv[e][0] = f.x; fv[e][1] = f.y; fv[e][2] = f.z;
+            }
         }
-        const float rho = 1.f + d;
-        if (active && !(rho > 0.5f && rho < 2.f)) set_status(status, kStatusUnstable);
-        const float inv = 1.f / rho;
-        drho[k] = d;
-        ux[k] = (jx + 0.5f * fx[k]) * inv;
-        uy[k] = (jy + 0.5f * fy[k]) * inv;
-        uz[k] = (jz + 0.5f * fz[k]) * inv;
-        uu15[k] = 1.5f * (ux[k] * ux[k] + uy[k] * uy[k] + uz[k] * uz[k]);
-        uf[k] = ux[k] * fx[k] + uy[k] * fy[k] + uz[k] * fz[k];
+        float ux[2], uy[2], uz[2], rs[2], nuu[2], uf[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float de = (e ? d.y : d.x) * ISC, jxe = (e ? jx.y : jx.x) * ISC;
+            const float jye = (e ? jy.y : jy.x) * ISC, jze = (e ? jz.y : jz.x) * ISC;
+            if constexpr (WM) {
+                if (active) moments[cell0 + 2 * h + e] = make_float4(jxe, jye, jze, de);
+            }
+            const float rho = 1.f + de;
+            if (active && !(rho > 0.5f && rho < 2.f)) set_status(status, kStatusUnstable);
+            const float inv = 1.f / rho;
+            ux[e] = (jxe + 0.5f * fv[e][0]) * inv;
+            uy[e] = (jye + 0.5f * fv[e][1]) * inv;
+            uz[e] = (jze + 0.5f * fv[e][2]) * inv;
+            rs[e] = SC * rho;
+            nuu[e] = -1.5f * (ux[e] * ux[e] + uy[e] * uy[e] + uz[e] * uz[e]);
+            uf[e] = ux[e] * fv[e][0] + uy[e] * fv[e][1] + uz[e] * fv[e][2];
+        }
+        Ux[h] = make_float2(ux[0], ux[1]);
+        Uy[h] = make_float2(uy[0], uy[1]);
+        Uz[h] = make_float2(uz[0], uz[1]);
+        Rs[h] = make_float2(rs[0], rs[1]);
+        Nuu[h] = make_float2(nuu[0], nuu[1]);
+        Fx[h] = make_float2(fv[0][0], fv[1][0]);
+        Fy[h] = make_float2(fv[0][1], fv[1][1]);
+        Fz[h] = make_float2(fv[0][2], fv[1][2]);
+        Uf[h] = make_float2(uf[0], uf[1]);
     }
-    const float guo = 1.f - 0.5f * omega;
-    const int yp = (y + 1 == ny) ? 0 : y + 1;
-    const int ym = (y == 0) ? ny - 1 : y - 1;
+    const float guo_s = SC * (1.f - 0.5f * omega);
+    const float2 om2 = make_float2(omega, omega), keep2 = make_float2(1.f - omega, 1.f - omega);
+    const bool top = z + 1 == nz, bottom = z == 0;
+    // destination row offsets: this row, the periodic neighbour rows in y, the planes in z
+    const int row0 = NX * row, plane = NX * ny;
+    const int dyp = (y + 1 == ny) ? NX * (1 - ny) : NX, dym = (y == 0) ? NX * (ny - 1) : -NX;
 
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
@@ -313,22 +385,29 @@ __global__ void __launch_bounds__(256, 2)
         const float w = q_w<float>(i);
         float p[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float cu = 0.f;
-            if (cx) cu += cx > 0 ? ux[k] : -ux[k];
-            if (cy) cu += cy > 0 ? uy[k] : -uy[k];
-            if (cz) cu += cz > 0 ? uz[k] : -uz[k];
-            const float rho = 1.f + drho[k];
-            const float geq = LIN ? w * (drho[k] + rho * (3.f * cu))
-                                  : w * (drho[k] + rho * (3.f * cu + 4.5f * cu * cu - uu15[k]));
-            p[k] = g[i][k] - omega * (g[i][k] - geq);
+        for (int h = 0; h < 2; ++h) {
+            float2 cu = make_float2(0.f, 0.f);
+            if (cx) cu = cx > 0 ? add2(cu, Ux[h]) : sub2(cu, Ux[h]);
+            if (cy) cu = cy > 0 ? add2(cu, Uy[h]) : sub2(cu, Uy[h]);
+            if (cz) cu = cz > 0 ? add2(cu, Uz[h]) : sub2(cu, Uz[h]);
+            // Eq. (equilibrium) (or its linearised form) minus the rest weight,
+            // in storage units: w (D + kScale rho (3 cu + 9/2 cu^2 - 3/2 u.u))
+            const float2 poly = LIN ? mul2(cu, make_float2(3.f, 3.f))
+                                    : fma2(fma2(cu, make_float2(4.5f, 4.5f), make_float2(3.f, 3.f)), cu, Nuu[h]);
+            const float2 geq = mul2(make_float2(w, w), fma2(Rs[h], poly, Ds[h]));
+            float2 post = fma2(om2, geq, mul2(keep2, g[i][h]));
             if (has_cur) {
-                float cf = 0.f;
-                if (cx) cf += cx > 0 ? fx[k] : -fx[k];
-                if (cy) cf += cy > 0 ? fy[k] : -fy[k];
-                if (cz) cf += cz > 0 ? fz[k] : -fz[k];
-                p[k] += guo * w * (3.f * (cf - uf[k]) + 9.f * cu * cf);
+                // Eq. (latticeforce): (1 - omega/2) w (3 (c - u) + 9 (c.u) c) . f
+                float2 cf = make_float2(0.f, 0.f);
+                if (cx) cf = cx > 0 ? add2(cf, Fx[h]) : sub2(cf, Fx[h]);
+                if (cy) cf = cy > 0 ? add2(cf, Fy[h]) : sub2(cf, Fy[h]);
+                if (cz) cf = cz > 0 ? add2(cf, Fz[h]) : sub2(cf, Fz[h]);
+                const float2 t = fma2(mul2(make_float2(9.f, 9.f), cu), cf,
+                                      mul2(make_float2(3.f, 3.f), sub2(cf, Uf[h])));
+                post = fma2(make_float2(guo_s * w, guo_s * w), t, post);
             }
+            p[2 * h] = post.x;
+            p[2 * h + 1] = post.y;
         }
         // x shift of the quad (before any branch: every lane takes part)
         float o0 = p[0], o1 = p[1], o2 = p[2], o3 = p[3];
@@ -340,32 +419,32 @@ __global__ void __launch_bounds__(256, 2)
             o0 = p[1]; o1 = p[2]; o2 = p[3]; o3 = in;
         }
         if (!active) continue;
-        if ((cz > 0 && z + 1 == nz) || (cz < 0 && z == 0)) {
-            // bounce-back into the opposite direction of the same cells
+        if (cz > 0 ? top : (cz < 0 ? bottom : false)) {
+            // bounce-back into the opposite direction of the same cells, with
+            // the moving-wall term in storage units
             const float uw = (cz > 0) ? u_wall : -u_wall;
-            const float wall = (cx == 0) ? 0.f : 6.f * w * (cx > 0 ? uw : -uw);
-            Quad<S>::store(dst + (size_t)q_opp(i) * ncell + cell0, p[0] - wall, p[1] - wall,
-                           p[2] - wall, p[3] - wall);
+            const float wall = (cx == 0) ? 0.f : SC * 6.f * w * (cx > 0 ? uw : -uw);
+            Quad<S>::store_raw(dst + (size_t)q_opp(i) * ncell + cell0, p[0] - wall, p[1] - wall,
+                               p[2] - wall, p[3] - wall);
         } else {
-            const int yt = cy > 0 ? yp : (cy < 0 ? ym : y);
-            S *rowp = dst + (size_t)i * ncell + (size_t)NX * (yt + ny * (z + cz));
+            S *rowp = dst + (size_t)i * ncell + (row0 + (cy > 0 ? dyp : (cy < 0 ? dym : 0)) + cz * plane);
             if constexpr (LR > 32) {
                 // warp edges: the crossing value is stored by its own lane
                 if (cx > 0 && lane == 0) {
-                    Store<S, float>::store(rowp + x0 + 1, o1);
-                    Store<S, float>::store(rowp + x0 + 2, o2);
-                    Store<S, float>::store(rowp + x0 + 3, o3);
+                    StoreRaw<S>::store(rowp + x0 + 1, o1);
+                    StoreRaw<S>::store(rowp + x0 + 2, o2);
+                    StoreRaw<S>::store(rowp + x0 + 3, o3);
                 } else if (cx < 0 && lane == 31) {
-                    Store<S, float>::store(rowp + x0, o0);
-                    Store<S, float>::store(rowp + x0 + 1, o1);
-                    Store<S, float>::store(rowp + x0 + 2, o2);
+                    StoreRaw<S>::store(rowp + x0, o0);
+                    StoreRaw<S>::store(rowp + x0 + 1, o1);
+                    StoreRaw<S>::store(rowp + x0 + 2, o2);
                 } else {
-                    Quad<S>::store(rowp + x0, o0, o1, o2, o3);
+                    Quad<S>::store_raw(rowp + x0, o0, o1, o2, o3);
                 }
-                if (cx > 0 && lane == 31) Store<S, float>::store(rowp + ((x0 + 4) & (NX - 1)), p[3]);
-                if (cx < 0 && lane == 0) Store<S, float>::store(rowp + ((x0 + NX - 1) & (NX - 1)), p[0]);
+                if (cx > 0 && lane == 31) StoreRaw<S>::store(rowp + ((x0 + 4) & (NX - 1)), p[3]);
+                if (cx < 0 && lane == 0) StoreRaw<S>::store(rowp + ((x0 + NX - 1) & (NX - 1)), p[0]);
             } else {
-                Quad<S>::store(rowp + x0, o0, o1, o2, o3);
+                Quad<S>::store_raw(rowp + x0, o0, o1, o2, o3);
             }
         }
     }
