@@ -323,8 +323,10 @@ __global__ void __launch_bounds__(256, 2)
     for (int i = 0; i < 19; ++i) Quad<S>::load_raw(src + (size_t)i * ncell + cell0, g[i][0], g[i][1]);
 
     // per cell: moments, velocity with the half force, and the pair vectors
-    // of the per-direction arithmetic
-    float2 Ux[2], Uy[2], Uz[2], Ds[2], Rs[2], Nuu[2], Fx[2], Fy[2], Fz[2], Uf[2];
+    // of the per-direction arithmetic.  A = D + kScale rho (-3/2 u.u) is the
+    // part of the equilibrium (minus the weight) common to all directions
+    // (D alone for the linearised form); Ufm = -3 u.f.
+    float2 Ux[2], Uy[2], Uz[2], Rs[2], A[2], Fx[2], Fy[2], Fz[2], Ufm[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         float2 d = make_float2(0.f, 0.f), jx = d, jy = d, jz = d;
@@ -335,7 +337,6 @@ __global__ void __launch_bounds__(256, 2)
             if (q_cy(i)) jy = q_cy(i) > 0 ? add2(jy, g[i][h]) : sub2(jy, g[i][h]);
             if (q_cz(i)) jz = q_cz(i) > 0 ? add2(jz, g[i][h]) : sub2(jz, g[i][h]);
         }
-        Ds[h] = d;
         float fv[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
         if (has_cur) {
 #pragma unroll
@@ -344,10 +345,11 @@ __global__ void __launch_bounds__(256, 2)
                 fv[e][0] = f.x; fv[e][1] = f.y; fv[e][2] = f.z;
             }
         }
-        float ux[2], uy[2], uz[2], rs[2], nuu[2], uf[2];
+        float ux[2], uy[2], uz[2], rs[2], ac[2], ufm[2];
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
-            const float de = (e ? d.y : d.x) * ISC, jxe = (e ? jx.y : jx.x) * ISC;
+            const float dr = e ? d.y : d.x;
+            const float de = dr * ISC, jxe = (e ? jx.y : jx.x) * ISC;
             const float jye = (e ? jy.y : jy.x) * ISC, jze = (e ? jz.y : jz.x) * ISC;
             if constexpr (WM) {
                 if (active) moments[cell0 + 2 * h + e] = make_float4(jxe, jye, jze, de);
@@ -359,56 +361,30 @@ __global__ void __launch_bounds__(256, 2)
             uy[e] = (jye + 0.5f * fv[e][1]) * inv;
             uz[e] = (jze + 0.5f * fv[e][2]) * inv;
             rs[e] = SC * rho;
-            nuu[e] = -1.5f * (ux[e] * ux[e] + uy[e] * uy[e] + uz[e] * uz[e]);
-            uf[e] = ux[e] * fv[e][0] + uy[e] * fv[e][1] + uz[e] * fv[e][2];
+            ac[e] = LIN ? dr : dr + rs[e] * (-1.5f * (ux[e] * ux[e] + uy[e] * uy[e] + uz[e] * uz[e]));
+            ufm[e] = -3.f * (ux[e] * fv[e][0] + uy[e] * fv[e][1] + uz[e] * fv[e][2]);
         }
         Ux[h] = make_float2(ux[0], ux[1]);
         Uy[h] = make_float2(uy[0], uy[1]);
         Uz[h] = make_float2(uz[0], uz[1]);
         Rs[h] = make_float2(rs[0], rs[1]);
-        Nuu[h] = make_float2(nuu[0], nuu[1]);
+        A[h] = make_float2(ac[0], ac[1]);
         Fx[h] = make_float2(fv[0][0], fv[1][0]);
         Fy[h] = make_float2(fv[0][1], fv[1][1]);
         Fz[h] = make_float2(fv[0][2], fv[1][2]);
-        Uf[h] = make_float2(uf[0], uf[1]);
+        Ufm[h] = make_float2(ufm[0], ufm[1]);
     }
     const float guo_s = SC * (1.f - 0.5f * omega);
-    const float2 om2 = make_float2(omega, omega), keep2 = make_float2(1.f - omega, 1.f - omega);
+    const float2 keep2 = make_float2(1.f - omega, 1.f - omega);
     const bool top = z + 1 == nz, bottom = z == 0;
     // destination row offsets: this row, the periodic neighbour rows in y, the planes in z
     const int row0 = NX * row, plane = NX * ny;
     const int dyp = (y + 1 == ny) ? NX * (1 - ny) : NX, dym = (y == 0) ? NX * (ny - 1) : -NX;
 
-#pragma unroll
-    for (int i = 0; i < 19; ++i) {
+    // x shift, wall bounce-back and store of the post-collision values p of
+    // direction i
+    auto emit = [&](const int i, const float p[4]) {
         const int cx = q_cx(i), cy = q_cy(i), cz = q_cz(i);
-        const float w = q_w<float>(i);
-        float p[4];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            float2 cu = make_float2(0.f, 0.f);
-            if (cx) cu = cx > 0 ? add2(cu, Ux[h]) : sub2(cu, Ux[h]);
-            if (cy) cu = cy > 0 ? add2(cu, Uy[h]) : sub2(cu, Uy[h]);
-            if (cz) cu = cz > 0 ? add2(cu, Uz[h]) : sub2(cu, Uz[h]);
-            // Eq. (equilibrium) (or its linearised form) minus the rest weight,
-            // in storage units: w (D + kScale rho (3 cu + 9/2 cu^2 - 3/2 u.u))
-            const float2 poly = LIN ? mul2(cu, make_float2(3.f, 3.f))
-                                    : fma2(fma2(cu, make_float2(4.5f, 4.5f), make_float2(3.f, 3.f)), cu, Nuu[h]);
-            const float2 geq = mul2(make_float2(w, w), fma2(Rs[h], poly, Ds[h]));
-            float2 post = fma2(om2, geq, mul2(keep2, g[i][h]));
-            if (has_cur) {
-                // Eq. (latticeforce): (1 - omega/2) w (3 (c - u) + 9 (c.u) c) . f
-                float2 cf = make_float2(0.f, 0.f);
-                if (cx) cf = cx > 0 ? add2(cf, Fx[h]) : sub2(cf, Fx[h]);
-                if (cy) cf = cy > 0 ? add2(cf, Fy[h]) : sub2(cf, Fy[h]);
-                if (cz) cf = cz > 0 ? add2(cf, Fz[h]) : sub2(cf, Fz[h]);
-                const float2 t = fma2(mul2(make_float2(9.f, 9.f), cu), cf,
-                                      mul2(make_float2(3.f, 3.f), sub2(cf, Uf[h])));
-                post = fma2(make_float2(guo_s * w, guo_s * w), t, post);
-            }
-            p[2 * h] = post.x;
-            p[2 * h + 1] = post.y;
-        }
         // x shift of the quad (before any branch: every lane takes part)
         float o0 = p[0], o1 = p[1], o2 = p[2], o3 = p[3];
         if (cx > 0) {
@@ -418,12 +394,12 @@ __global__ void __launch_bounds__(256, 2)
             const float in = from_right<LR>(p[0], lane);
             o0 = p[1]; o1 = p[2]; o2 = p[3]; o3 = in;
         }
-        if (!active) continue;
+        if (!active) return;
         if (cz > 0 ? top : (cz < 0 ? bottom : false)) {
             // bounce-back into the opposite direction of the same cells, with
             // the moving-wall term in storage units
             const float uw = (cz > 0) ? u_wall : -u_wall;
-            const float wall = (cx == 0) ? 0.f : SC * 6.f * w * (cx > 0 ? uw : -uw);
+            const float wall = (cx == 0) ? 0.f : SC * 6.f * q_w<float>(i) * (cx > 0 ? uw : -uw);
             Quad<S>::store_raw(dst + (size_t)q_opp(i) * ncell + cell0, p[0] - wall, p[1] - wall,
                                p[2] - wall, p[3] - wall);
         } else {
@@ -447,6 +423,63 @@ __global__ void __launch_bounds__(256, 2)
                 Quad<S>::store_raw(rowp + x0, o0, o1, o2, o3);
             }
         }
+    };
+
+    // rest direction: c = 0, equilibrium w0 A, force term w0 (1 - omega/2) (-3 u.f)
+    {
+        const float w = q_w<float>(0);
+        const float2 omw = make_float2(omega * w, omega * w), gw = make_float2(guo_s * w, guo_s * w);
+        float p[4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            float2 post = fma2(omw, A[h], mul2(keep2, g[0][h]));
+            if (has_cur) post = fma2(gw, Ufm[h], post);
+            p[2 * h] = post.x;
+            p[2 * h + 1] = post.y;
+        }
+        emit(0, p);
+    }
+    // direction pairs (c, -c), c with its first nonzero component positive:
+    // with r = kScale rho c.u the equilibrium (minus the weight) is
+    // w (A + 9/2 r c.u +- 3 r) (Eq. equilibrium; the linearised form drops the
+    // quadratic term) and the force term (Eq. latticeforce)
+    // (1 - omega/2) w (9 (c.u)(c.f) - 3 u.f +- 3 c.f)
+#pragma unroll
+    for (int j = 1; j < 19; j += 2) {
+        const int ip = (q_cx(j) > 0 || (q_cx(j) == 0 && (q_cy(j) > 0 || (q_cy(j) == 0 && q_cz(j) > 0))))
+                           ? j : q_opp(j);
+        const int im = q_opp(ip);
+        const int cx = q_cx(ip), cy = q_cy(ip), cz = q_cz(ip);
+        const float w = q_w<float>(ip);
+        const float2 omw = make_float2(omega * w, omega * w), gw = make_float2(guo_s * w, guo_s * w);
+        float pp[4], pm[4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            // c.u from the first nonzero component (positive) on
+            float2 cu = cx ? Ux[h] : (cy ? Uy[h] : Uz[h]);
+            if (cx && cy) cu = cy > 0 ? add2(cu, Uy[h]) : sub2(cu, Uy[h]);
+            if ((cx || cy) && cz) cu = cz > 0 ? add2(cu, Uz[h]) : sub2(cu, Uz[h]);
+            const float2 r = mul2(Rs[h], cu);
+            const float2 e = LIN ? A[h] : fma2(mul2(r, make_float2(4.5f, 4.5f)), cu, A[h]);
+            const float2 gp = fma2(r, make_float2(3.f, 3.f), e);
+            const float2 gm = fma2(r, make_float2(-3.f, -3.f), e);
+            float2 postp = fma2(omw, gp, mul2(keep2, g[ip][h]));
+            float2 postm = fma2(omw, gm, mul2(keep2, g[im][h]));
+            if (has_cur) {
+                float2 cf = cx ? Fx[h] : (cy ? Fy[h] : Fz[h]);
+                if (cx && cy) cf = cy > 0 ? add2(cf, Fy[h]) : sub2(cf, Fy[h]);
+                if ((cx || cy) && cz) cf = cz > 0 ? add2(cf, Fz[h]) : sub2(cf, Fz[h]);
+                const float2 base = fma2(mul2(cu, cf), make_float2(9.f, 9.f), Ufm[h]);
+                postp = fma2(gw, fma2(cf, make_float2(3.f, 3.f), base), postp);
+                postm = fma2(gw, fma2(cf, make_float2(-3.f, -3.f), base), postm);
+            }
+            pp[2 * h] = postp.x;
+            pp[2 * h + 1] = postp.y;
+            pm[2 * h] = postm.x;
+            pm[2 * h + 1] = postm.y;
+        }
+        emit(ip, pp);
+        emit(im, pm);
     }
 }
 
