@@ -37,6 +37,8 @@
 // In the float builds the edges and the Gram entries are formed in
 // double-float arithmetic from the hi/lo node coordinates, so the deviations
 // d keep their relative precision even for strains of 1e-4.
+#include <type_traits>
+
 #include "device_common.cuh"
 #include "ib_common.cuh"
 #include "internal.h"
@@ -235,6 +237,50 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Four stored deviations of consecutive cells in float (16-byte, or 8-byte
+// binary16, vector load); the values equal Store<S, float>::load's.
+template <typename S>
+__device__ __forceinline__ void load_quad(const S *p, float v[4]);
+template <>
+__device__ __forceinline__ void load_quad<float>(const float *p, float v[4]) {
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+template <>
+__device__ __forceinline__ void load_quad<__half>(const __half *p, float v[4]) {
+    const uint2 q = __ldg(reinterpret_cast<const uint2 *>(p));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&q.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&q.y));
+    v[0] = a.x * kHalfInvScale; v[1] = a.y * kHalfInvScale;
+    v[2] = b.x * kHalfInvScale; v[3] = b.y * kHalfInvScale;
+}
+
+// k_flag_velocity for a lattice flagged per ftx-cell segment of an x-row
+// (ftx a multiple of 4 dividing nx, so flag index = cell / ftx): one thread
+// takes four consecutive cells of a segment with vector loads (the same
+// arithmetic per cell).
+template <typename S>
+__global__ void __launch_bounds__(256)
+    k_flag_velocity_x4(const S *__restrict__ pop, const float4 *__restrict__ force,
+                       const uint8_t *__restrict__ flags, float4 *__restrict__ uvel, long long ncell,
+                       int ftx) {
+    const long long cell0 = 4 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
+    if (cell0 >= ncell || !flags[cell0 / ftx]) return;
+    float g[4][19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        float v[4];
+        load_quad<S>(pop + i * ncell + cell0, v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) g[k][i] = v[k];
+    }
+    float4 f[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) f[k] = force[cell0 + k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) uvel[cell0 + k] = velocity_from<float>(g[k], f[k]);
+}
+
 // PRE: read the cell velocities of k_flag_velocity; otherwise every lane
 // gathers the 19 populations and the force of its cells and forms u itself
 // (the same arithmetic).  The pre-pass pays when the nodes' stencils touch
@@ -326,6 +372,107 @@ __global__ void __launch_bounds__(256)
     ay = warp_sum(ay);
     az = warp_sum(az);
     if (lane == 0) {
+        if (ab2) {  // Sec. II.C: x += 3/2 u_i(t+1) - 1/2 u_i(t)
+            const V4 uo = nodeU[node];
+            pos.advance(node, T(1.5) * ax - T(0.5) * uo.x, T(1.5) * ay - T(0.5) * uo.y,
+                        T(1.5) * az - T(0.5) * uo.z, snap);
+        } else {  // Eq. (positionupdate)
+            pos.advance(node, ax, ay, az, snap);
+        }
+        nodeU[node] = V4{ax, ay, az, T(0)};
+    }
+}
+
+// k_interp_advect with four nodes per warp (dense suspensions): a group of 8
+// lanes per node, lane gl of a group takes the stencil cells gl, gl + 8, ...
+// of its node and the group sums in a fixed order (identical in both PRE
+// forms, so the two interpolation modes still agree bit for bit).  Groups past
+// the last node repeat the last node's work and write nothing.
+template <int N, typename S, typename T, bool PRE>
+__global__ void __launch_bounds__(256)
+    k_interp_advect4(int n_nodes, PosView<T> pos, const typename Vec4<T>::type *__restrict__ uvel,
+                     const S *__restrict__ pop, const typename Vec4<T>::type *__restrict__ force,
+                     typename Vec4<T>::type *__restrict__ nodeU, RunDesc single,
+                     const RunDesc *__restrict__ runs, const int *__restrict__ node_run, PosView<T> snap,
+                     int ab2) {
+    using V4 = typename Vec4<T>::type;
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    if (warp * 4 >= n_nodes) return;  // the whole warp
+    const long long gnode = warp * 4 + (lane >> 3);
+    const int gl = lane & 7;
+    const bool valid = gnode < n_nodes;
+    const int node = valid ? (int)gnode : n_nodes - 1;
+    const RunDesc R = runs ? runs[node_run[node]] : single;
+    const int nx = R.nx, ny = R.ny, nz = R.nz;
+    T p[kPosLen<T>];
+    pos.approx(node, p);
+    T pc[3];
+    if constexpr (kPosLen<T> == 6) {
+        pc[0] = p[0] + p[3]; pc[1] = p[1] + p[4]; pc[2] = p[2] + p[5];
+    } else {
+        pc[0] = p[0]; pc[1] = p[1]; pc[2] = p[2];
+    }
+    const int bx = stencil_first<N>(pc[0]), by = stencil_first<N>(pc[1]), bz = stencil_first<N>(pc[2]);
+    constexpr int NC = N * N * N;
+    constexpr int ITER = (NC + 7) / 8;
+    bool in[ITER];
+    long long cell[ITER];
+    int X[ITER], Y[ITER], Z[ITER];
+#pragma unroll
+    for (int it = 0; it < ITER; ++it) {
+        const int k = gl + 8 * it;
+        const int kx = k % N, ky = (k / N) % N, kz = k / (N * N);
+        X[it] = bx + kx;
+        Y[it] = by + ky;
+        Z[it] = bz + kz;
+        in[it] = k < NC && Z[it] >= 0 && Z[it] < nz;
+        cell[it] = in[it] ? wrap_index(X[it], nx) + (long long)nx * (wrap_index(Y[it], ny) + (long long)ny * Z[it]) : 0;
+    }
+    T ax = T(0), ay = T(0), az = T(0);
+    if constexpr (PRE) {
+        const V4 *ur = uvel + R.cell_off;
+        V4 u[ITER];
+#pragma unroll
+        for (int it = 0; it < ITER; ++it) u[it] = in[it] ? ur[cell[it]] : V4{};
+#pragma unroll
+        for (int it = 0; it < ITER; ++it) {
+            if (!in[it]) continue;
+            T d[3];
+            pos.rel(p, X[it], Y[it], Z[it], d);
+            const T w = delta_phi<N>(d[0]) * delta_phi<N>(d[1]) * delta_phi<N>(d[2]);
+            if (w == T(0)) continue;
+            ax += w * u[it].x;
+            ay += w * u[it].y;
+            az += w * u[it].z;
+        }
+    } else {
+        const S *pr = pop + 19 * R.cell_off;
+        const V4 *fr = force + R.cell_off;
+#pragma unroll
+        for (int it = 0; it < ITER; ++it) {
+            if (!in[it]) continue;
+            T g[19];
+#pragma unroll
+            for (int i = 0; i < 19; ++i) g[i] = Store<S, T>::load(pr + i * R.ncell + cell[it]);
+            const V4 f = fr[cell[it]];
+            T d[3];
+            pos.rel(p, X[it], Y[it], Z[it], d);
+            const T w = delta_phi<N>(d[0]) * delta_phi<N>(d[1]) * delta_phi<N>(d[2]);
+            if (w == T(0)) continue;
+            const V4 u = velocity_from<T>(g, f);
+            ax += w * u.x;
+            ay += w * u.y;
+            az += w * u.z;
+        }
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        az += __shfl_xor_sync(0xffffffffu, az, o);
+    }
+    if (valid && gl == 0) {
         if (ab2) {  // Sec. II.C: x += 3/2 u_i(t+1) - 1/2 u_i(t)
             const V4 uo = nodeU[node];
             pos.advance(node, T(1.5) * ax - T(0.5) * uo.x, T(1.5) * ay - T(0.5) * uo.y,
@@ -439,6 +586,21 @@ static void interp_impl(const Lattice &L, const MeshDev &m, const void *uvel, co
     sm.x = snap_x;
     sm.x_lo = snap_lo;
     const PosView<T> snap = view<T>(sm);
+    if (m.n_nodes >= 152 * 32) {
+        // four nodes per warp once one-node warps would exceed 32 per SM
+        const long long warps = (m.n_nodes + 3) / 4;
+        const int wpb = warps >= 152 * 16 ? 4 : 2;
+        const unsigned nb4 = (unsigned)((warps + wpb - 1) / wpb);
+        if (uvel)
+            k_interp_advect4<N, S, T, true><<<nb4, 32 * wpb, 0, s>>>(
+                m.n_nodes, view<T>(m), (const V4 *)uvel, nullptr, nullptr, (V4 *)m.u, single_run(L), runs,
+                node_run, snap, ab2);
+        else
+            k_interp_advect4<N, S, T, false><<<nb4, 32 * wpb, 0, s>>>(
+                m.n_nodes, view<T>(m), nullptr, (const S *)pop, (const V4 *)force, (V4 *)m.u, single_run(L),
+                runs, node_run, snap, ab2);
+        return;
+    }
     unsigned nb = (unsigned)((m.n_nodes + kNodesPerBlock - 1) / kNodesPerBlock);
     if (uvel)
         k_interp_advect<N, S, T, true><<<nb, 32 * kNodesPerBlock, 0, s>>>(
@@ -455,6 +617,15 @@ static void flag_velocity_impl(const Lattice &L, const void *pop, const void *fo
                                void *uvel, const RunDesc *runs, const int2 *items, long long n_items,
                                cudaStream_t s) {
     using V4 = typename Vec4<T>::type;
+    if constexpr (!std::is_same<S, double>::value) {
+        if (!runs && L.lanes_row && L.fty == 1 && L.ftx % 4 == 0 && L.nx % L.ftx == 0) {
+            const long long quads = L.ncell / 4;
+            if (quads <= 0) return;
+            k_flag_velocity_x4<S><<<(unsigned)((quads + 255) / 256), 256, 0, s>>>(
+                (const S *)pop, (const float4 *)force, flags, (float4 *)uvel, L.ncell, L.ftx);
+            return;
+        }
+    }
     const long long n = runs ? n_items : L.ntiles;
     if (n <= 0) return;
     k_flag_velocity<S, T><<<(unsigned)((n + 7) / 8), 256, 0, s>>>(

@@ -338,6 +338,61 @@ def test_interp_modes_bit_identical(prec):
     assert np.array_equal(out[0][1], out[1][1])
 
 
+def _dense_case(precision):
+    """Eight capsules of 642 nodes (5 136 nodes: the membrane kernels take
+    four nodes per warp) on a lattice whose rows take the vectorised kernels."""
+    shape = (128, 64, 64)
+    r, G = 6.0, 0.02
+    centres = W.rsa_centres(shape, 8, r, seed=8, z_margin=r + 4.0)
+    caps = [W.Capsule(c, r, 3, W.k_s_for(G, r)) for c in centres]
+    return W.Case("dense", shape, 1.0, 3, precision, W.u_wall_for(shape[2]), caps, 1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
+def test_one_step_dense_suspension(prec):
+    """Every sub-step of one coupled step with more than 152 x 32 nodes."""
+    case = _dense_case(prec)
+    g = gpu_sim(case)
+    o = oracle_sim(case)
+    assert o.n_nodes >= 152 * 32
+    x0 = o.get_nodes() + W.jitter(o.n_nodes, 0.15, seed=31)
+    f0 = o.get_f() + W.population_noise(case.shape, 1e-3, seed=32)
+    g.set_nodes(x0)
+    o.set_nodes(x0)
+    g.set_populations(f0)
+    o.set_f(f0)
+    g.step(1)
+    o.step(1)
+    tol = ONE_STEP_TOL[prec]
+    assert rel_inf(g.get_node_forces(), o.get_node_forces()) < (1e-12 if prec == "fp64" else 1e-5)
+    assert rel_inf(g.get_force_field(), o.get_force_field()) < (1e-12 if prec == "fp64" else 1e-5)
+    _, w, _ = O.d3q19()
+    wb = w[:, None, None, None]
+    assert rel_inf(g.get_populations() - wb, o.get_f() - wb) < tol
+    assert rel_inf(g.get_velocity(), o.get_velocity()) < tol
+    assert rel_inf(g.get_node_velocities(), o.get_node_velocities()) < tol
+    assert np.abs(g.get_nodes() - o.get_nodes()).max() < tol * 1e-1
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_interp_modes_bit_identical_dense(prec):
+    """As above with four nodes per interpolation warp."""
+    case = _dense_case(prec)
+    o = oracle_sim(case)
+    f0 = o.get_f() + W.population_noise(case.shape, 1e-3, seed=33)
+    out = []
+    for mode in (0, 1):
+        g = gpu_sim(case)
+        g.set_populations(f0)
+        g.set_interp_mode(mode)
+        g.step(1)
+        out.append((g.get_nodes(), g.get_node_velocities()))
+        g.close()
+    assert np.abs(out[0][1]).max() > 0
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+
+
 def test_kernel_launch_count():
     """The library counts the kernels it launches for time steps, graph
     replays included: three per step (spreading, collide, interpolation), one
