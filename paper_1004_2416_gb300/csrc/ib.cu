@@ -11,12 +11,14 @@
 // lanes first takes the faces around its node (one face each; a face's
 // contribution to this corner is recomputed by each of its three corner
 // groups, which keeps the assembly a deterministic group reduction with no
-// atomics and no per-face scratch), then the 32 lanes take the nodes' n^3
-// stencil cells and add the spread force with one vector atomic per cell.
-// k_interp_advect gives one warp to one node: the lanes take the stencil
-// cells, each gathers its cell's velocity (formed once per cell of the flagged
-// tiles by k_flag_velocity, L2-resident), and a warp reduction gives the node
-// velocity.
+// atomics and no per-face scratch), then the group's lanes take the node's
+// stencil rows (n cells along x each) and add the spread force with one
+// vector atomic per cell.  k_interp_advect gives a group of lanes to a node in
+// the same way: the lanes take the stencil rows, read the velocity of each
+// cell (formed once per cell of the flagged tiles by k_flag_velocity,
+// L2-resident, or formed from the populations on the spot) and a group
+// reduction gives the node velocity.  The delta function is separable: its n
+// x factors are formed once per lane, its y and z factors once per row.
 //
 // Face energy gradient.  With the current edge vectors u = x_b - x_a,
 // v = x_c - x_a, their Gram entries g11 = u.u, g12 = u.v, g22 = v.v, the
@@ -47,11 +49,11 @@ namespace iblbm {
 
 // One warp takes NPW nodes (1 or 4).  Face phase: a group of 32 / NPW lanes
 // per node, one adjacent face per lane (a loop for higher valences), a
-// fixed-order reduction within the group.  Stencil phase: the NPW x n^3
-// (node, cell) pairs are dealt to the 32 lanes, which fetch their node's force
-// and position from its group by shuffles.  Four nodes per warp waste fewer
-// lanes on the faces (a node has five or six) when there are enough nodes to
-// fill the GPU; one node per warp keeps more warps in flight otherwise.
+// fixed-order butterfly reduction within the group that leaves the node force
+// in every lane of the group.  Stencil phase: the group's lanes take the
+// node's n^2 stencil rows.  Four nodes per warp waste fewer lanes on the faces
+// (a node has five or six) when there are enough nodes to fill the GPU; one
+// node per warp keeps more warps in flight otherwise.
 template <int N, typename T, int NPW>
 __global__ void __launch_bounds__(256)
     k_force_spread(int n_nodes, PosView<T> pos, const int *__restrict__ adj_off,
@@ -114,66 +116,74 @@ __global__ void __launch_bounds__(256)
     }
     if (valid && gl == 0) nodeF[node] = V4{fx, fy, fz, T(0)};
 
-    // the group's node position and stencil base
+    if (!valid) return;  // no shuffles below
+
+    // Stencil phase: lane gl of the node's group takes the stencil pieces
+    // gl, gl + 32 / NPW, ... of its node (CX cells along x of one row
+    // (ky, kz)); a piece's y and z weights and its wrapped row base are formed
+    // once, the x weights once per lane when the pieces are whole rows.
+    // Force flag tiles are powers of two.
+    // pieces: whole rows with four nodes per warp; with one node per warp
+    // pieces that spread the n^3 cells over most of the 32 lanes
+    constexpr int CX = NPW == 1 ? (N == 4 ? 2 : 1) : N, SPR = N / CX, NS = N * N * SPR;
     T p[kPosLen<T>];
-    if (valid) {
-        pos.approx(node, p);
+    pos.approx(node, p);
+    T pc[3];
+    if constexpr (kPosLen<T> == 6) {
+        pc[0] = p[0] + p[3]; pc[1] = p[1] + p[4]; pc[2] = p[2] + p[5];
     } else {
-#pragma unroll
-        for (int k = 0; k < kPosLen<T>; ++k) p[k] = T(0);
+        pc[0] = p[0]; pc[1] = p[1]; pc[2] = p[2];
     }
-    int b[3];
-    {
-        T pc[3];
-        if constexpr (kPosLen<T> == 6) {
-            pc[0] = p[0] + p[3]; pc[1] = p[1] + p[4]; pc[2] = p[2] + p[5];
-        } else {
-            pc[0] = p[0]; pc[1] = p[1]; pc[2] = p[2];
+    const int bx = stencil_first<N>(pc[0]), by = stencil_first<N>(pc[1]), bz = stencil_first<N>(pc[2]);
+    const RunDesc R = runs ? runs[node_run[node]] : single;
+    const int sx = __ffs(R.tx) - 1, sy = __ffs(R.ty) - 1;
+    const int xw0 = wrap_index(bx, R.nx);
+    T wrow[CX == N ? N : 1];
+    if constexpr (CX == N) {
+#pragma unroll
+        for (int kx = 0; kx < N; ++kx) {
+            T d[3];
+            pos.rel(p, bx + kx, by, bz, d);
+            wrow[kx] = delta_phi<N>(d[0]);
         }
-        b[0] = stencil_first<N>(pc[0]);
-        b[1] = stencil_first<N>(pc[1]);
-        b[2] = stencil_first<N>(pc[2]);
     }
-    const RunDesc R1 = (NPW == 1 && runs) ? runs[node_run[node]] : single;
-    constexpr int NC = N * N * N;
-    // uniform trip count: every lane takes part in every round of shuffles
-    for (int base = 0; base < kFsNodes * NC; base += 32) {
-        const int k = base + lane;
-        const int g = k < kFsNodes * NC ? k / NC : kFsNodes - 1, c = k - g * NC;
-        const int src = g * kFsGroup;
-        // node g's force and position, from its group (with one node per
-        // warp every lane holds them already)
-        T gfx = fx, gfy = fy, gfz = fz;
-        T q[kPosLen<T>];
-#pragma unroll
-        for (int j = 0; j < kPosLen<T>; ++j) q[j] = p[j];
-        int gb[3] = {b[0], b[1], b[2]};
-        if constexpr (NPW > 1) {
-            gfx = __shfl_sync(0xffffffffu, fx, src);
-            gfy = __shfl_sync(0xffffffffu, fy, src);
-            gfz = __shfl_sync(0xffffffffu, fz, src);
-#pragma unroll
-            for (int j = 0; j < kPosLen<T>; ++j) q[j] = __shfl_sync(0xffffffffu, p[j], src);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) gb[j] = __shfl_sync(0xffffffffu, b[j], src);
-        }
-        const int gnode = (int)(node0 + g);
-        if (k >= kFsNodes * NC || gnode >= n_nodes) continue;
-        const RunDesc R = (NPW == 1) ? R1 : (runs ? runs[node_run[gnode]] : single);
-        const int kx = c % N, ky = (c / N) % N, kz = c / (N * N);
-        const int X = gb[0] + kx, Y = gb[1] + ky, Z = gb[2] + kz;
+    V4 *fr = force + R.cell_off;
+    uint8_t *flr = flags + R.tile_off;
+    for (int sl = gl; sl < NS; sl += kFsGroup) {
+        const int r = sl / SPR, kx0 = (sl % SPR) * CX;
+        const int Y = by + r % N, Z = bz + r / N;
         if (Z < 0 || Z >= R.nz) {
             set_status(status, kStatusStencil);
             continue;
         }
         T d[3];
-        pos.rel(q, X, Y, Z, d);
-        const T w = delta_phi<N>(d[0]) * delta_phi<N>(d[1]) * delta_phi<N>(d[2]);
-        if (w == T(0)) continue;
-        const int xw = wrap_index(X, R.nx), yw = wrap_index(Y, R.ny);
-        const long long cell = xw + (long long)R.nx * (yw + (long long)R.ny * Z);
-        add_force(&force[R.cell_off + cell], w * gfx, w * gfy, w * gfz);
-        flags[R.tile_off + ((long long)Z * R.nty + yw / R.ty) * R.ntx + xw / R.tx] = 1;
+        pos.rel(p, bx, Y, Z, d);
+        const T wy = delta_phi<N>(d[1]), wz = delta_phi<N>(d[2]);
+        const int yw = wrap_index(Y, R.ny);
+        const long long rc = (long long)R.nx * (yw + (long long)R.ny * Z);
+        const long long rt = ((long long)Z * R.nty + (yw >> sy)) * R.ntx;
+        int last = -1;
+#pragma unroll
+        for (int c = 0; c < CX; ++c) {
+            T wxv;
+            if constexpr (CX == N) {
+                wxv = wrow[c];
+            } else {
+                T dx[3];
+                pos.rel(p, bx + kx0 + c, by, bz, dx);
+                wxv = delta_phi<N>(dx[0]);
+            }
+            const T w = wxv * wy * wz;
+            if (w == T(0)) continue;
+            const int xa = xw0 + kx0 + c;
+            const int xw = xa < R.nx ? xa : wrap_index(xa, R.nx);
+            add_force(&fr[rc + xw], w * fx, w * fy, w * fz);
+            const int xt = xw >> sx;
+            if (xt != last) {
+                flr[rt + xt] = 1;
+                last = xt;
+            }
+        }
     }
 }
 
@@ -260,32 +270,48 @@ __device__ __forceinline__ void load_quad<__half>(const __half *p, float v[4]) {
 // takes four consecutive cells of a segment with vector loads (the same
 // arithmetic per cell).
 template <typename S>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(S) == 2 ? 4 : 3)
     k_flag_velocity_x4(const S *__restrict__ pop, const float4 *__restrict__ force,
                        const uint8_t *__restrict__ flags, float4 *__restrict__ uvel, long long ncell,
                        int ftx) {
     const long long cell0 = 4 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
     if (cell0 >= ncell || !flags[cell0 / ftx]) return;
-    float g[4][19];
+    // velocity_from's sums, in its order, as the loads arrive
+    float drho[4] = {0.f, 0.f, 0.f, 0.f}, jx[4] = {0.f, 0.f, 0.f, 0.f};
+    float jy[4] = {0.f, 0.f, 0.f, 0.f}, jz[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         float v[4];
         load_quad<S>(pop + i * ncell + cell0, v);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) g[k][i] = v[k];
+        for (int k = 0; k < 4; ++k) {
+            drho[k] += v[k];
+            if (q_cx(i)) jx[k] += q_cx(i) > 0 ? v[k] : -v[k];
+            if (q_cy(i)) jy[k] += q_cy(i) > 0 ? v[k] : -v[k];
+            if (q_cz(i)) jz[k] += q_cz(i) > 0 ? v[k] : -v[k];
+        }
     }
-    float4 f[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) f[k] = force[cell0 + k];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) uvel[cell0 + k] = velocity_from<float>(g[k], f[k]);
+    for (int k = 0; k < 4; ++k) {
+        const float4 f = force[cell0 + k];
+        const float inv_rho = 1.f / (1.f + drho[k]);
+        uvel[cell0 + k] = make_float4((jx[k] + 0.5f * f.x) * inv_rho, (jy[k] + 0.5f * f.y) * inv_rho,
+                                      (jz[k] + 0.5f * f.z) * inv_rho, 0.f);
+    }
 }
 
-// PRE: read the cell velocities of k_flag_velocity; otherwise every lane
-// gathers the 19 populations and the force of its cells and forms u itself
-// (the same arithmetic).  The pre-pass pays when the nodes' stencils touch
-// many more cells than the flagged tiles hold (dense suspensions).
-template <int N, typename S, typename T, bool PRE>
+// Interpolation and advection, NPW = 1 or 4 nodes per warp (four for dense
+// suspensions), a group of 32 / NPW lanes per node.  Lane gl of a group takes
+// the stencil pieces gl, gl + 32 / NPW, ... of its node (piece = CX
+// consecutive cells along x of one stencil row (ky, kz); y and z weights once per piece, x weights once
+// per lane when the pieces are whole rows) and the group sums in a fixed
+// order.  PRE: read the cell velocities of k_flag_velocity; otherwise the lane
+// gathers the 19 populations and the force of each cell and forms u itself
+// with the same arithmetic, so both forms give the same bits.  The loads
+// depend only on the cell index and are issued before the weights are used
+// (cells of zero weight are read and not used).  Groups past the last node
+// repeat its work and write nothing.
+template <int N, typename S, typename T, bool PRE, int NPW>
 __global__ void __launch_bounds__(256)
     k_interp_advect(int n_nodes, PosView<T> pos, const typename Vec4<T>::type *__restrict__ uvel,
                     const S *__restrict__ pop, const typename Vec4<T>::type *__restrict__ force,
@@ -293,114 +319,18 @@ __global__ void __launch_bounds__(256)
                     const RunDesc *__restrict__ runs, const int *__restrict__ node_run, PosView<T> snap,
                     int ab2) {
     using V4 = typename Vec4<T>::type;
-    const int lane = threadIdx.x & 31;
-    const int node = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
-    if (node >= n_nodes) return;
-    const RunDesc R = runs ? runs[node_run[node]] : single;
-    const int nx = R.nx, ny = R.ny, nz = R.nz;
-    T p[kPosLen<T>];
-    pos.approx(node, p);
-    T pc[3];
-    if constexpr (kPosLen<T> == 6) {
-        pc[0] = p[0] + p[3]; pc[1] = p[1] + p[4]; pc[2] = p[2] + p[5];
-    } else {
-        pc[0] = p[0]; pc[1] = p[1]; pc[2] = p[2];
-    }
-    const int bx = stencil_first<N>(pc[0]), by = stencil_first<N>(pc[1]), bz = stencil_first<N>(pc[2]);
-    // Each lane owns up to ITER stencil cells; all their loads are issued
-    // before any is used.
-    constexpr int NC = N * N * N;
-    constexpr int ITER = (NC + 31) / 32;
-    // The loads depend only on the cell index, so they are issued before the
-    // weights are formed (cells of zero weight are read and not used).
-    bool in[ITER];
-    long long cell[ITER];
-    int X[ITER], Y[ITER], Z[ITER];
-#pragma unroll
-    for (int it = 0; it < ITER; ++it) {
-        const int k = lane + 32 * it;
-        const int kx = k % N, ky = (k / N) % N, kz = k / (N * N);
-        X[it] = bx + kx;
-        Y[it] = by + ky;
-        Z[it] = bz + kz;
-        // a stencil beyond a wall is reported by the spreading
-        in[it] = k < NC && Z[it] >= 0 && Z[it] < nz;
-        cell[it] = in[it] ? wrap_index(X[it], nx) + (long long)nx * (wrap_index(Y[it], ny) + (long long)ny * Z[it]) : 0;
-    }
-    T ax = T(0), ay = T(0), az = T(0);
-    if constexpr (PRE) {
-        const V4 *ur = uvel + R.cell_off;
-        V4 u[ITER];
-#pragma unroll
-        for (int it = 0; it < ITER; ++it) u[it] = in[it] ? ur[cell[it]] : V4{};
-#pragma unroll
-        for (int it = 0; it < ITER; ++it) {
-            if (!in[it]) continue;
-            T d[3];
-            pos.rel(p, X[it], Y[it], Z[it], d);
-            const T w = delta_phi<N>(d[0]) * delta_phi<N>(d[1]) * delta_phi<N>(d[2]);
-            if (w == T(0)) continue;
-            ax += w * u[it].x;
-            ay += w * u[it].y;
-            az += w * u[it].z;
-        }
-    } else {
-        const S *pr = pop + 19 * R.cell_off;
-        const V4 *fr = force + R.cell_off;
-        T g[ITER][19];
-        V4 f[ITER];
-#pragma unroll
-        for (int it = 0; it < ITER; ++it) {
-#pragma unroll
-            for (int i = 0; i < 19; ++i) g[it][i] = in[it] ? Store<S, T>::load(pr + i * R.ncell + cell[it]) : T(0);
-            f[it] = in[it] ? fr[cell[it]] : V4{};
-        }
-#pragma unroll
-        for (int it = 0; it < ITER; ++it) {
-            if (!in[it]) continue;
-            T d[3];
-            pos.rel(p, X[it], Y[it], Z[it], d);
-            const T w = delta_phi<N>(d[0]) * delta_phi<N>(d[1]) * delta_phi<N>(d[2]);
-            if (w == T(0)) continue;
-            const V4 u = velocity_from<T>(g[it], f[it]);
-            ax += w * u.x;
-            ay += w * u.y;
-            az += w * u.z;
-        }
-    }
-    ax = warp_sum(ax);
-    ay = warp_sum(ay);
-    az = warp_sum(az);
-    if (lane == 0) {
-        if (ab2) {  // Sec. II.C: x += 3/2 u_i(t+1) - 1/2 u_i(t)
-            const V4 uo = nodeU[node];
-            pos.advance(node, T(1.5) * ax - T(0.5) * uo.x, T(1.5) * ay - T(0.5) * uo.y,
-                        T(1.5) * az - T(0.5) * uo.z, snap);
-        } else {  // Eq. (positionupdate)
-            pos.advance(node, ax, ay, az, snap);
-        }
-        nodeU[node] = V4{ax, ay, az, T(0)};
-    }
-}
-
-// k_interp_advect with four nodes per warp (dense suspensions): a group of 8
-// lanes per node, lane gl of a group takes the stencil cells gl, gl + 8, ...
-// of its node and the group sums in a fixed order (identical in both PRE
-// forms, so the two interpolation modes still agree bit for bit).  Groups past
-// the last node repeat the last node's work and write nothing.
-template <int N, typename S, typename T, bool PRE>
-__global__ void __launch_bounds__(256)
-    k_interp_advect4(int n_nodes, PosView<T> pos, const typename Vec4<T>::type *__restrict__ uvel,
-                     const S *__restrict__ pop, const typename Vec4<T>::type *__restrict__ force,
-                     typename Vec4<T>::type *__restrict__ nodeU, RunDesc single,
-                     const RunDesc *__restrict__ runs, const int *__restrict__ node_run, PosView<T> snap,
-                     int ab2) {
-    using V4 = typename Vec4<T>::type;
+    constexpr int G = 32 / NPW;
+    // cells per piece (whole rows with four nodes per warp; single cells with
+    // one, so that one load instruction of the warp covers whole x-rows of the
+    // stencil), pieces per row
+    constexpr int CX = NPW == 1 ? 1 : N, SPR = N / CX;
+    constexpr int NS = N * N * SPR;                              // pieces per node
+    constexpr int RPL = (NS + G - 1) / G;                        // pieces per lane, at most
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    if (warp * 4 >= n_nodes) return;  // the whole warp
-    const long long gnode = warp * 4 + (lane >> 3);
-    const int gl = lane & 7;
+    if (warp * NPW >= n_nodes) return;  // the whole warp
+    const long long gnode = warp * NPW + lane / G;
+    const int gl = lane % G;
     const bool valid = gnode < n_nodes;
     const int node = valid ? (int)gnode : n_nodes - 1;
     const RunDesc R = runs ? runs[node_run[node]] : single;
@@ -414,60 +344,109 @@ __global__ void __launch_bounds__(256)
         pc[0] = p[0]; pc[1] = p[1]; pc[2] = p[2];
     }
     const int bx = stencil_first<N>(pc[0]), by = stencil_first<N>(pc[1]), bz = stencil_first<N>(pc[2]);
-    constexpr int NC = N * N * N;
-    constexpr int ITER = (NC + 7) / 8;
-    bool in[ITER];
-    long long cell[ITER];
-    int X[ITER], Y[ITER], Z[ITER];
+    const int xw0 = wrap_index(bx, nx);
+    // this lane's pieces; a stencil beyond a wall is reported by the spreading
+    bool in[RPL];
+    long long rc[RPL];
+    int Y[RPL], Z[RPL], KX[RPL], XW[RPL][CX];
 #pragma unroll
-    for (int it = 0; it < ITER; ++it) {
-        const int k = gl + 8 * it;
-        const int kx = k % N, ky = (k / N) % N, kz = k / (N * N);
-        X[it] = bx + kx;
-        Y[it] = by + ky;
-        Z[it] = bz + kz;
-        in[it] = k < NC && Z[it] >= 0 && Z[it] < nz;
-        cell[it] = in[it] ? wrap_index(X[it], nx) + (long long)nx * (wrap_index(Y[it], ny) + (long long)ny * Z[it]) : 0;
+    for (int j = 0; j < RPL; ++j) {
+        const int sl = gl + G * j, r = sl / SPR;
+        KX[j] = (sl % SPR) * CX;
+        Y[j] = by + r % N;
+        Z[j] = bz + r / N;
+        in[j] = sl < NS && Z[j] >= 0 && Z[j] < nz;
+        rc[j] = in[j] ? (long long)nx * (wrap_index(Y[j], ny) + (long long)ny * Z[j]) : 0;
+#pragma unroll
+        for (int c = 0; c < CX; ++c) {
+            const int xa = xw0 + KX[j] + c;
+            XW[j][c] = xa < nx ? xa : wrap_index(xa, nx);
+        }
     }
+    // x factors: once per lane for whole rows, else per cell
+    T wrow[CX == N ? N : 1];
+    if constexpr (CX == N) {
+#pragma unroll
+        for (int kx = 0; kx < N; ++kx) {
+            T d[3];
+            pos.rel(p, bx + kx, by, bz, d);
+            wrow[kx] = delta_phi<N>(d[0]);
+        }
+    }
+    auto weight = [&](int j, int c, T wyz_y, T wyz_z) -> T {
+        T wxv;
+        if constexpr (CX == N) {
+            wxv = wrow[c];
+        } else {
+            T d[3];
+            pos.rel(p, bx + KX[j] + c, by, bz, d);
+            wxv = delta_phi<N>(d[0]);
+        }
+        return wxv * wyz_y * wyz_z;
+    };
     T ax = T(0), ay = T(0), az = T(0);
     if constexpr (PRE) {
         const V4 *ur = uvel + R.cell_off;
-        V4 u[ITER];
+        V4 u[RPL][CX];
 #pragma unroll
-        for (int it = 0; it < ITER; ++it) u[it] = in[it] ? ur[cell[it]] : V4{};
+        for (int j = 0; j < RPL; ++j)
 #pragma unroll
-        for (int it = 0; it < ITER; ++it) {
-            if (!in[it]) continue;
+            for (int c = 0; c < CX; ++c) u[j][c] = in[j] ? ur[rc[j] + XW[j][c]] : V4{};
+#pragma unroll
+        for (int j = 0; j < RPL; ++j) {
+            if (!in[j]) continue;
             T d[3];
-            pos.rel(p, X[it], Y[it], Z[it], d);
-            const T w = delta_phi<N>(d[0]) * delta_phi<N>(d[1]) * delta_phi<N>(d[2]);
-            if (w == T(0)) continue;
-            ax += w * u[it].x;
-            ay += w * u[it].y;
-            az += w * u[it].z;
+            pos.rel(p, bx, Y[j], Z[j], d);
+            const T wy = delta_phi<N>(d[1]), wz = delta_phi<N>(d[2]);
+#pragma unroll
+            for (int c = 0; c < CX; ++c) {
+                const T w = weight(j, c, wy, wz);
+                if (w == T(0)) continue;
+                ax += w * u[j][c].x;
+                ay += w * u[j][c].y;
+                az += w * u[j][c].z;
+            }
         }
     } else {
         const S *pr = pop + 19 * R.cell_off;
         const V4 *fr = force + R.cell_off;
+        constexpr bool ALL = RPL * CX <= 4;  // every load of the lane in flight at once
+        T g[ALL ? RPL : 1][CX][19];
+        V4 f[ALL ? RPL : 1][CX];
+        auto load = [&](int j, int slot) {
 #pragma unroll
-        for (int it = 0; it < ITER; ++it) {
-            if (!in[it]) continue;
-            T g[19];
+            for (int c = 0; c < CX; ++c) {
 #pragma unroll
-            for (int i = 0; i < 19; ++i) g[i] = Store<S, T>::load(pr + i * R.ncell + cell[it]);
-            const V4 f = fr[cell[it]];
+                for (int i = 0; i < 19; ++i)
+                    g[slot][c][i] = in[j] ? Store<S, T>::load(pr + i * R.ncell + rc[j] + XW[j][c]) : T(0);
+                f[slot][c] = in[j] ? fr[rc[j] + XW[j][c]] : V4{};
+            }
+        };
+        if constexpr (ALL) {
+#pragma unroll
+            for (int j = 0; j < RPL; ++j) load(j, j);
+        }
+#pragma unroll
+        for (int j = 0; j < RPL; ++j) {
+            if (!in[j]) continue;
+            const int slot = ALL ? j : 0;
+            if constexpr (!ALL) load(j, 0);
             T d[3];
-            pos.rel(p, X[it], Y[it], Z[it], d);
-            const T w = delta_phi<N>(d[0]) * delta_phi<N>(d[1]) * delta_phi<N>(d[2]);
-            if (w == T(0)) continue;
-            const V4 u = velocity_from<T>(g, f);
-            ax += w * u.x;
-            ay += w * u.y;
-            az += w * u.z;
+            pos.rel(p, bx, Y[j], Z[j], d);
+            const T wy = delta_phi<N>(d[1]), wz = delta_phi<N>(d[2]);
+#pragma unroll
+            for (int c = 0; c < CX; ++c) {
+                const T w = weight(j, c, wy, wz);
+                if (w == T(0)) continue;
+                const V4 u = velocity_from<T>(g[slot][c], f[slot][c]);
+                ax += w * u.x;
+                ay += w * u.y;
+                az += w * u.z;
+            }
         }
     }
 #pragma unroll
-    for (int o = 4; o > 0; o >>= 1) {
+    for (int o = G / 2; o > 0; o >>= 1) {
         ax += __shfl_xor_sync(0xffffffffu, ax, o);
         ay += __shfl_xor_sync(0xffffffffu, ay, o);
         az += __shfl_xor_sync(0xffffffffu, az, o);
@@ -586,30 +565,15 @@ static void interp_impl(const Lattice &L, const MeshDev &m, const void *uvel, co
     sm.x = snap_x;
     sm.x_lo = snap_lo;
     const PosView<T> snap = view<T>(sm);
-    if (m.n_nodes >= 152 * 32) {
-        // four nodes per warp once one-node warps would exceed 32 per SM
-        const long long warps = (m.n_nodes + 3) / 4;
-        const int wpb = warps >= 152 * 16 ? 4 : 2;
-        const unsigned nb4 = (unsigned)((warps + wpb - 1) / wpb);
-        if (uvel)
-            k_interp_advect4<N, S, T, true><<<nb4, 32 * wpb, 0, s>>>(
-                m.n_nodes, view<T>(m), (const V4 *)uvel, nullptr, nullptr, (V4 *)m.u, single_run(L), runs,
-                node_run, snap, ab2);
-        else
-            k_interp_advect4<N, S, T, false><<<nb4, 32 * wpb, 0, s>>>(
-                m.n_nodes, view<T>(m), nullptr, (const S *)pop, (const V4 *)force, (V4 *)m.u, single_run(L),
-                runs, node_run, snap, ab2);
-        return;
-    }
-    unsigned nb = (unsigned)((m.n_nodes + kNodesPerBlock - 1) / kNodesPerBlock);
-    if (uvel)
-        k_interp_advect<N, S, T, true><<<nb, 32 * kNodesPerBlock, 0, s>>>(
-            m.n_nodes, view<T>(m), (const V4 *)uvel, nullptr, nullptr, (V4 *)m.u, single_run(L), runs, node_run,
-            snap, ab2);
-    else
-        k_interp_advect<N, S, T, false><<<nb, 32 * kNodesPerBlock, 0, s>>>(
-            m.n_nodes, view<T>(m), nullptr, (const S *)pop, (const V4 *)force, (V4 *)m.u, single_run(L), runs,
-            node_run, snap, ab2);
+    // four nodes per warp once one-node warps would exceed 32 per SM
+    const bool four = m.n_nodes >= 152 * 32;
+    const long long warps = four ? (m.n_nodes + 3) / 4 : m.n_nodes;
+    const int wpb = four && warps >= 152 * 16 ? 4 : kNodesPerBlock;
+    const unsigned nb = (unsigned)((warps + wpb - 1) / wpb);
+    auto kern = uvel ? (four ? k_interp_advect<N, S, T, true, 4> : k_interp_advect<N, S, T, true, 1>)
+                     : (four ? k_interp_advect<N, S, T, false, 4> : k_interp_advect<N, S, T, false, 1>);
+    kern<<<nb, 32 * wpb, 0, s>>>(m.n_nodes, view<T>(m), (const V4 *)uvel, (const S *)pop, (const V4 *)force,
+                                 (V4 *)m.u, single_run(L), runs, node_run, snap, ab2);
 }
 
 template <typename S, typename T>
