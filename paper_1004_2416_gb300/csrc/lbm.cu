@@ -234,10 +234,11 @@ struct Quad<__half> {
 // post-collision values by one cell; the value that crosses into the
 // neighbouring thread's quad comes by a warp shuffle (within the row's lane
 // segment when LR <= 32, which also closes the periodic wrap in x).  When a
-// row spans several warps the value that crosses a warp edge is written by
-// its own lane with a scalar store, and the receiving edge lane stores the
-// other three elements of its quad as scalars: no barrier and no shared
-// memory.  One force flag per 32-cell segment of a row.
+// row spans several warps every lane still stores its quad as one vector;
+// the edge lane that got the wrong crossing value (the shuffle wraps within
+// its own warp) rewrites that one cell after a block barrier with the value
+// the neighbouring warp's edge lane left in shared memory.  One force flag
+// per 32-cell segment of a row.
 // Paired FP32 arithmetic (two cells per instruction).
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
@@ -269,6 +270,10 @@ __device__ __forceinline__ float from_right(float v, int lane) {
     return __shfl_sync(0xffffffffu, v, (lx + 1) & (W - 1), W);
 }
 
+// Slot of a direction with c_x != 0 (1, 2 and 7..14) among the ten such
+// directions.
+__host__ __device__ constexpr int edge_slot(int i) { return i <= 2 ? i - 1 : i - 5; }
+
 template <int LR>
 __host__ __device__ constexpr int rows_per_block() {
     return LR <= 32 ? 8 * (32 / LR) : 8 / (LR / 32);
@@ -299,6 +304,7 @@ __global__ void __launch_bounds__(256, 2)
     const int y = row % ny, z = row / ny;
     const int x0 = 4 * lx;
     const int cell0 = x0 + NX * row;
+    __shared__ float edge[8][10];  // rows spanning several warps: crossing values by warp and direction
 
     // force flags per 32-cell segment of a row (the whole row if nx < 32); the
     // lanes of one segment are consecutive lanes of one warp
@@ -404,23 +410,11 @@ __global__ void __launch_bounds__(256, 2)
                                p[2] - wall, p[3] - wall);
         } else {
             S *rowp = dst + (size_t)i * ncell + (row0 + (cy > 0 ? dyp : (cy < 0 ? dym : 0)) + cz * plane);
+            Quad<S>::store_raw(rowp + x0, o0, o1, o2, o3);
             if constexpr (LR > 32) {
-                // warp edges: the crossing value is stored by its own lane
-                if (cx > 0 && lane == 0) {
-                    StoreRaw<S>::store(rowp + x0 + 1, o1);
-                    StoreRaw<S>::store(rowp + x0 + 2, o2);
-                    StoreRaw<S>::store(rowp + x0 + 3, o3);
-                } else if (cx < 0 && lane == 31) {
-                    StoreRaw<S>::store(rowp + x0, o0);
-                    StoreRaw<S>::store(rowp + x0 + 1, o1);
-                    StoreRaw<S>::store(rowp + x0 + 2, o2);
-                } else {
-                    Quad<S>::store_raw(rowp + x0, o0, o1, o2, o3);
-                }
-                if (cx > 0 && lane == 31) StoreRaw<S>::store(rowp + ((x0 + 4) & (NX - 1)), p[3]);
-                if (cx < 0 && lane == 0) StoreRaw<S>::store(rowp + ((x0 + NX - 1) & (NX - 1)), p[0]);
-            } else {
-                Quad<S>::store_raw(rowp + x0, o0, o1, o2, o3);
+                // the value that crosses into the neighbouring warp
+                if (cx > 0 && lane == 31) edge[warp][edge_slot(i)] = p[3];
+                if (cx < 0 && lane == 0) edge[warp][edge_slot(i)] = p[0];
             }
         }
     };
@@ -480,6 +474,24 @@ __global__ void __launch_bounds__(256, 2)
         }
         emit(ip, pp);
         emit(im, pm);
+    }
+    if constexpr (LR > 32) {
+        // lane 0 (c_x > 0) and lane 31 (c_x < 0) stored a value from their own
+        // warp's other edge; rewrite that cell with the neighbouring warp's
+        __syncthreads();
+        if (active && (lane == 0 || lane == 31)) {
+            constexpr int WPR = LR / 32;
+            const int wr = warp % WPR, wb = warp - wr;
+            const int from = wb + (lane == 0 ? (wr + WPR - 1) % WPR : (wr + 1) % WPR);
+#pragma unroll
+            for (int i = 1; i < 19; ++i) {
+                const int cx = q_cx(i), cy = q_cy(i), cz = q_cz(i);
+                if (cx == 0 || (cz > 0 ? top : (cz < 0 ? bottom : false))) continue;
+                if ((cx > 0) != (lane == 0)) continue;
+                S *rowp = dst + (size_t)i * ncell + (row0 + (cy > 0 ? dyp : (cy < 0 ? dym : 0)) + cz * plane);
+                StoreRaw<S>::store(rowp + x0 + (cx > 0 ? 0 : 3), edge[from][edge_slot(i)]);
+            }
+        }
     }
 }
 
