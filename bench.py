@@ -62,6 +62,8 @@ def _args():
                    help="node advection: 0 Euler, 1 Adams-Bashforth")
     p.add_argument("--interp-mode", type=int, default=-1, choices=[-1, 0, 1],
                    help="interpolation: -1 automatic, 0 gather at the stencil cells, 1 cell velocities first")
+    p.add_argument("--launch-overlap", type=int, default=-1, choices=[-1, 0, 1],
+                   help="step kernels with programmatic dependent launch: 1 on, 0 off, -1 automatic")
     p.add_argument("--adjoint-only", action="store_true",
                    help="only the config-5 adjoint timing, printed as {\"adjoint\": ...}")
     p.add_argument("--adjoint-steps", type=int, default=None,
@@ -421,6 +423,7 @@ def run_ours(a):
     stream = torch.cuda.Stream()
     sim = _make_sim(case, stream)
     sim.set_interp_mode(a.interp_mode)
+    sim.set_launch_overlap(a.launch_overlap)
     sim.set_equilibrium(a.equilibrium)
     sim.set_integrator(a.integrator)
     batch = isinstance(case, Batch)

@@ -228,9 +228,23 @@ int iblbm_set_equilibrium(iblbm_sim *sim, int order);
  * stencil cell; mode 1, a pass first forms u once for every cell of the tiles
  * the spreading flagged and the nodes read it; -1 (default) chooses mode 1
  * when the nodes' stencils touch more than a quarter of the cells (dense
- * suspensions).  Both give the same numbers bit for bit.  IBLBM_ERR_ARG for
- * another mode.  Synchronising. */
+ * suspensions).  Both give the same numbers bit for bit below 152 x 32
+ * nodes; above, mode 1 reduces four nodes per warp and the two agree to the
+ * rounding of the summation order.  IBLBM_ERR_ARG for another mode.
+ * Synchronising. */
 int iblbm_set_interp_mode(iblbm_sim *sim, int mode);
+
+/* Whether the kernels of a time step are launched with programmatic
+ * dependent launch: each kernel may start while the one before it in the
+ * step finishes, does what needs nothing of that kernel (the interpolation
+ * reads the node positions and forms its stencil indices and weights) and
+ * then waits for it.  mode 1 on, 0 off (one kernel after the other), -1
+ * (default) on where the membrane kernels take four nodes per warp (more than
+ * 152 x 32 nodes: dense suspensions, where it measured faster; for a single
+ * capsule it measured no faster or slower).  The results are the same up to
+ * the order of the spreading's atomic additions.  IBLBM_ERR_ARG for another
+ * mode.  Synchronising. */
+int iblbm_set_launch_overlap(iblbm_sim *sim, int mode);
 
 /* Runs n_steps (1..100000) further time steps without graph capture, with
  * CUDA events on the object's stream around each kernel group, and returns

@@ -69,6 +69,7 @@ struct iblbm_sim {
     uint8_t *flags[2] = {nullptr, nullptr};
     void *uvel = nullptr;  // velocity of the cells of the flagged tiles (Vec4 per cell)
     int interp_mode = -1;  // -1 automatic, 0 gather at the stencil cells, 1 cell velocities first
+    int overlap = -1;      // step kernels overlapping their predecessor: -1 automatic, 0 off, 1 on
     // Method variants: node advection 0 = Euler (Eq. positionupdate), 1 =
     // Adams-Bashforth (Sec. II.C), which needs the node velocities of the step
     // before (ab2_ready); equilibrium order 2 = Eq. (equilibrium), 1 = the
@@ -444,6 +445,15 @@ void free_ring(iblbm_sim *s) {
 // Whether the interpolation reads velocities formed once per cell of the
 // flagged tiles: automatic when the stencils touch (counting repeats) more than
 // a quarter of the cells, i.e. in dense suspensions.
+// Programmatic dependent launch of the step kernels: automatically where the
+// membrane kernels take four nodes per warp (a dense suspension, whose
+// interpolation has a long position-only prologue); measured slower or no
+// faster for one capsule.
+bool launch_overlap(const iblbm_sim *s) {
+    if (s->overlap >= 0) return s->overlap == 1;
+    return s->mesh.n_nodes >= 152 * 32;
+}
+
 bool cell_velocity_first(const iblbm_sim *s) {
     if (s->interp_mode >= 0) return s->interp_mode == 1;
     const double touches = (double)s->mesh.n_nodes * s->delta * s->delta * s->delta;
@@ -461,9 +471,10 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) 
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess && !s->launch_fail) s->launch_fail = what;
     };
+    const bool ov = launch_overlap(s);
     if (ev) cudaEventRecord(ev[0], s->stream);
     launch_force_spread(s->prec, s->delta, s->L, s->mesh, s->force[n], s->flags[n], s->d_status,
-                        s->batch ? s->d_runs : nullptr, s->d_node_run, s->stream);
+                        s->batch ? s->d_runs : nullptr, s->d_node_run, s->stream, ov);
     mark("membrane force + spreading");
     if (ev) cudaEventRecord(ev[1], s->stream);
     CollideArgs a;
@@ -479,16 +490,16 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) 
     a.eq_order = s->eq_order;
     if (s->batch) {
         BatchArgs b{s->d_runs, s->d_items, s->n_items, s->batch_grid};
-        launch_collide_batch(s->prec, b, a, s->stream);
+        launch_collide_batch(s->prec, b, a, s->stream, ov);
     } else {
-        launch_collide_stream(s->prec, s->L, a, s->stream);
+        launch_collide_stream(s->prec, s->L, a, s->stream, ov);
     }
     mark("collide-stream");
     if (ev) cudaEventRecord(ev[2], s->stream);
     const bool pre = cell_velocity_first(s);
     if (pre) {
         launch_flag_velocity(s->prec, s->L, s->pop[n], s->force[n], s->flags[n], s->uvel,
-                             s->batch ? s->d_runs : nullptr, s->d_items, s->n_items, s->stream);
+                             s->batch ? s->d_runs : nullptr, s->d_items, s->n_items, s->stream, ov);
         mark("velocity of the flagged cells");
     }
     const bool side_rec = record && !ev;  // timed runs keep the record on the main stream
@@ -504,7 +515,7 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) 
     void *sl = side_rec && s->snap_lo ? (char *)s->snap_lo + slot * (size_t)16 * s->mesh.n_nodes : nullptr;
     launch_interp_advect(s->prec, s->delta, s->L, s->mesh, pre ? s->uvel : nullptr, s->pop[n], s->force[n],
                          s->batch ? s->d_runs : nullptr, s->d_node_run, s->stream, sx, sl,
-                         s->integrator == 1 && s->ab2_ready ? 1 : 0);
+                         s->integrator == 1 && s->ab2_ready ? 1 : 0, ov);
     s->ab2_ready = true;  // m.u now holds u_i(t+1)
     mark("interpolation + advection");
     if (ev) cudaEventRecord(ev[3], s->stream);
@@ -1650,6 +1661,16 @@ int iblbm_set_interp_mode(iblbm_sim *s, int mode) {
     CK(cudaStreamSynchronize(s->stream));
     drop_graphs(s);
     s->interp_mode = mode;
+    return IBLBM_OK;
+}
+
+int iblbm_set_launch_overlap(iblbm_sim *s, int mode) {
+    if (!s) return IBLBM_ERR_ARG;
+    if (mode < -1 || mode > 1) return fail(s, IBLBM_ERR_ARG, "mode must be -1, 0 or 1");
+    join_side(s);
+    CK(cudaStreamSynchronize(s->stream));
+    drop_graphs(s);
+    s->overlap = mode;
     return IBLBM_OK;
 }
 

@@ -162,4 +162,15 @@ __device__ __forceinline__ int wrap_index(int a, int n) {
 
 __device__ __forceinline__ void set_status(int *status, int bit) { atomicOr(status, bit); }
 
+// Programmatic dependent launch (sm_90 and later).  A time-step kernel may be
+// launched while its predecessor in the stream still runs.  It calls
+// prior_grid_wait() before it touches anything that the predecessor writes,
+// or writes anything that the predecessor reads, and then allow_dependents(),
+// which lets the next kernel launch.  Waiting first makes the chain
+// transitive: when a kernel starts, the kernel two places before it has
+// completed, so what it does before the wait may read data of that kernel or
+// older ones.  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void prior_grid_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 }  // namespace iblbm

@@ -65,6 +65,8 @@ __global__ void __launch_bounds__(256)
                    RunDesc single, const RunDesc *__restrict__ runs,
                    const int *__restrict__ node_run, int *status) {
     using V4 = typename Vec4<T>::type;
+    prior_grid_wait();  // the node positions come from the previous interpolation
+    allow_dependents();
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     constexpr int kFsNodes = NPW, kFsGroup = 32 / NPW;
@@ -216,6 +218,8 @@ __global__ void __launch_bounds__(256)
                     RunDesc single, long long n_tiles, const RunDesc *__restrict__ runs,
                     const int2 *__restrict__ items) {
     using V4 = typename Vec4<T>::type;
+    prior_grid_wait();
+    allow_dependents();
     const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     if (w >= n_tiles) return;
     int tile;
@@ -274,6 +278,8 @@ __global__ void __launch_bounds__(256, sizeof(S) == 2 ? 4 : 3)
     k_flag_velocity_x4(const S *__restrict__ pop, const float4 *__restrict__ force,
                        const uint8_t *__restrict__ flags, float4 *__restrict__ uvel, long long ncell,
                        int ftx) {
+    prior_grid_wait();
+    allow_dependents();
     const long long cell0 = 4 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
     if (cell0 >= ncell || !flags[cell0 / ftx]) return;
     // velocity_from's sums, in its order, as the loads arrive
@@ -307,7 +313,8 @@ __global__ void __launch_bounds__(256, sizeof(S) == 2 ? 4 : 3)
 // per lane when the pieces are whole rows) and the group sums in a fixed
 // order.  PRE: read the cell velocities of k_flag_velocity; otherwise the lane
 // gathers the 19 populations and the force of each cell and forms u itself
-// with the same arithmetic, so both forms give the same bits.  The loads
+// with the same arithmetic, so for the same NPW both forms give the same
+// bits (the launcher takes NPW = 4 only with PRE).  The loads
 // depend only on the cell index and are issued before the weights are used
 // (cells of zero weight are read and not used).  Groups past the last node
 // repeat its work and write nothing.
@@ -384,6 +391,10 @@ __global__ void __launch_bounds__(256)
         }
         return wxv * wyz_y * wyz_z;
     };
+    // positions, stencil indices and x factors need nothing of the collide
+    // or velocity kernel before this one; the velocities do
+    prior_grid_wait();
+    allow_dependents();
     T ax = T(0), ay = T(0), az = T(0);
     if constexpr (PRE) {
         const V4 *ur = uvel + R.cell_off;
@@ -542,7 +553,7 @@ static RunDesc single_run(const Lattice &L) {
 template <int N, typename T>
 static void force_spread_impl(const Lattice &L, const MeshDev &m, void *force, uint8_t *flags,
                               int *status, const RunDesc *runs, const int *node_run,
-                              cudaStream_t s) {
+                              cudaStream_t s, bool ov) {
     using V4 = typename Vec4<T>::type;
     // four nodes per warp once one-node warps would exceed 32 per SM
     const bool four = m.n_nodes >= 152 * 32;
@@ -550,7 +561,7 @@ static void force_spread_impl(const Lattice &L, const MeshDev &m, void *force, u
     const int wpb = warps >= 152 * 16 ? 4 : 2;
     const unsigned nb = (unsigned)((warps + wpb - 1) / wpb);
     auto kern = four ? k_force_spread<N, T, 4> : k_force_spread<N, T, 1>;
-    kern<<<nb, 32 * wpb, 0, s>>>(
+    launch_maybe_overlapped(kern, dim3(nb), dim3(32 * wpb), s, ov,
         m.n_nodes, view<T>(m), m.adj_off, m.adj, (const int4 *)m.tri, (const V4 *)m.fconst,
         (const V4 *)m.capmod, (V4 *)m.F, (V4 *)force, flags, single_run(L), runs, node_run,
         status);
@@ -559,82 +570,86 @@ static void force_spread_impl(const Lattice &L, const MeshDev &m, void *force, u
 template <int N, typename S, typename T>
 static void interp_impl(const Lattice &L, const MeshDev &m, const void *uvel, const void *pop,
                         const void *force, const RunDesc *runs, const int *node_run, cudaStream_t s,
-                        void *snap_x, void *snap_lo, int ab2) {
+                        void *snap_x, void *snap_lo, int ab2, bool ov) {
     using V4 = typename Vec4<T>::type;
     MeshDev sm{};
     sm.x = snap_x;
     sm.x_lo = snap_lo;
     const PosView<T> snap = view<T>(sm);
-    // four nodes per warp once one-node warps would exceed 32 per SM
-    const bool four = m.n_nodes >= 152 * 32;
+    // four nodes per warp when reading the cell velocities and one-node warps
+    // would exceed 32 per SM; gathering the populations keeps one node per
+    // warp (all 19 loads of its cells in flight at once)
+    const bool four = uvel && m.n_nodes >= 152 * 32;
     const long long warps = four ? (m.n_nodes + 3) / 4 : m.n_nodes;
     const int wpb = four && warps >= 152 * 16 ? 4 : kNodesPerBlock;
     const unsigned nb = (unsigned)((warps + wpb - 1) / wpb);
     auto kern = uvel ? (four ? k_interp_advect<N, S, T, true, 4> : k_interp_advect<N, S, T, true, 1>)
-                     : (four ? k_interp_advect<N, S, T, false, 4> : k_interp_advect<N, S, T, false, 1>);
-    kern<<<nb, 32 * wpb, 0, s>>>(m.n_nodes, view<T>(m), (const V4 *)uvel, (const S *)pop, (const V4 *)force,
-                                 (V4 *)m.u, single_run(L), runs, node_run, snap, ab2);
+                     : k_interp_advect<N, S, T, false, 1>;
+    launch_maybe_overlapped(kern, dim3(nb), dim3(32 * wpb), s, ov, m.n_nodes, view<T>(m), (const V4 *)uvel,
+                            (const S *)pop, (const V4 *)force, (V4 *)m.u, single_run(L), runs, node_run, snap,
+                            ab2);
 }
 
 template <typename S, typename T>
 static void flag_velocity_impl(const Lattice &L, const void *pop, const void *force, const uint8_t *flags,
                                void *uvel, const RunDesc *runs, const int2 *items, long long n_items,
-                               cudaStream_t s) {
+                               cudaStream_t s, bool ov) {
     using V4 = typename Vec4<T>::type;
     if constexpr (!std::is_same<S, double>::value) {
         if (!runs && L.lanes_row && L.fty == 1 && L.ftx % 4 == 0 && L.nx % L.ftx == 0) {
             const long long quads = L.ncell / 4;
             if (quads <= 0) return;
-            k_flag_velocity_x4<S><<<(unsigned)((quads + 255) / 256), 256, 0, s>>>(
-                (const S *)pop, (const float4 *)force, flags, (float4 *)uvel, L.ncell, L.ftx);
+            launch_maybe_overlapped(k_flag_velocity_x4<S>, dim3((unsigned)((quads + 255) / 256)), dim3(256), s, ov,
+                                    (const S *)pop, (const float4 *)force, flags, (float4 *)uvel, L.ncell,
+                                    L.ftx);
             return;
         }
     }
     const long long n = runs ? n_items : L.ntiles;
     if (n <= 0) return;
-    k_flag_velocity<S, T><<<(unsigned)((n + 7) / 8), 256, 0, s>>>(
-        (const S *)pop, (const V4 *)force, flags, (V4 *)uvel, single_run(L), n, runs, items);
+    launch_maybe_overlapped(k_flag_velocity<S, T>, dim3((unsigned)((n + 7) / 8)), dim3(256), s, ov,
+                            (const S *)pop, (const V4 *)force, flags, (V4 *)uvel, single_run(L), n, runs, items);
 }
 
 void launch_force_spread(int prec, int delta, const Lattice &L, const MeshDev &m, void *force,
                          uint8_t *flags, int *status, const RunDesc *runs, const int *node_run,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool overlap) {
     if (m.n_nodes == 0) return;
     if (prec == kF64) {
-        if (delta == 2) force_spread_impl<2, double>(L, m, force, flags, status, runs, node_run, s);
-        else if (delta == 3) force_spread_impl<3, double>(L, m, force, flags, status, runs, node_run, s);
-        else force_spread_impl<4, double>(L, m, force, flags, status, runs, node_run, s);
+        if (delta == 2) force_spread_impl<2, double>(L, m, force, flags, status, runs, node_run, s, overlap);
+        else if (delta == 3) force_spread_impl<3, double>(L, m, force, flags, status, runs, node_run, s, overlap);
+        else force_spread_impl<4, double>(L, m, force, flags, status, runs, node_run, s, overlap);
     } else {
-        if (delta == 2) force_spread_impl<2, float>(L, m, force, flags, status, runs, node_run, s);
-        else if (delta == 3) force_spread_impl<3, float>(L, m, force, flags, status, runs, node_run, s);
-        else force_spread_impl<4, float>(L, m, force, flags, status, runs, node_run, s);
+        if (delta == 2) force_spread_impl<2, float>(L, m, force, flags, status, runs, node_run, s, overlap);
+        else if (delta == 3) force_spread_impl<3, float>(L, m, force, flags, status, runs, node_run, s, overlap);
+        else force_spread_impl<4, float>(L, m, force, flags, status, runs, node_run, s, overlap);
     }
 }
 
 void launch_flag_velocity(int prec, const Lattice &L, const void *pop, const void *force, const uint8_t *flags,
                           void *uvel, const RunDesc *runs, const int2 *items, long long n_items,
-                          cudaStream_t s) {
-    if (prec == kF64) flag_velocity_impl<double, double>(L, pop, force, flags, uvel, runs, items, n_items, s);
-    else if (prec == kF32) flag_velocity_impl<float, float>(L, pop, force, flags, uvel, runs, items, n_items, s);
-    else flag_velocity_impl<__half, float>(L, pop, force, flags, uvel, runs, items, n_items, s);
+                          cudaStream_t s, bool overlap) {
+    if (prec == kF64) flag_velocity_impl<double, double>(L, pop, force, flags, uvel, runs, items, n_items, s, overlap);
+    else if (prec == kF32) flag_velocity_impl<float, float>(L, pop, force, flags, uvel, runs, items, n_items, s, overlap);
+    else flag_velocity_impl<__half, float>(L, pop, force, flags, uvel, runs, items, n_items, s, overlap);
 }
 
 void launch_interp_advect(int prec, int delta, const Lattice &L, const MeshDev &m, const void *uvel,
                           const void *pop, const void *force, const RunDesc *runs, const int *node_run,
-                          cudaStream_t s, void *snap_x, void *snap_lo, int ab2) {
+                          cudaStream_t s, void *snap_x, void *snap_lo, int ab2, bool overlap) {
     if (m.n_nodes == 0) return;
     if (prec == kF64) {
-        if (delta == 2) interp_impl<2, double, double>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2);
-        else if (delta == 3) interp_impl<3, double, double>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2);
-        else interp_impl<4, double, double>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2);
+        if (delta == 2) interp_impl<2, double, double>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2, overlap);
+        else if (delta == 3) interp_impl<3, double, double>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2, overlap);
+        else interp_impl<4, double, double>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2, overlap);
     } else if (prec == kF32) {
-        if (delta == 2) interp_impl<2, float, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2);
-        else if (delta == 3) interp_impl<3, float, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2);
-        else interp_impl<4, float, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2);
+        if (delta == 2) interp_impl<2, float, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2, overlap);
+        else if (delta == 3) interp_impl<3, float, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2, overlap);
+        else interp_impl<4, float, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2, overlap);
     } else {
-        if (delta == 2) interp_impl<2, __half, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2);
-        else if (delta == 3) interp_impl<3, __half, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2);
-        else interp_impl<4, __half, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2);
+        if (delta == 2) interp_impl<2, __half, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2, overlap);
+        else if (delta == 3) interp_impl<3, __half, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2, overlap);
+        else interp_impl<4, __half, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2, overlap);
     }
 }
 

@@ -107,9 +107,29 @@ struct CollideArgs {
     void *moments = nullptr;
     int eq_order = 2;  // 2: Eq. (equilibrium); 1: the linearised form of Sec. IV.A
 };
-void launch_collide_stream(int prec, const Lattice &L, const CollideArgs &a, cudaStream_t s);
+// Launchers of the time-step kernels take `overlap`: launch with programmatic
+// stream serialization, so that the kernel may start while the previous kernel
+// of the stream still runs (the kernels wait for it where they must; see
+// prior_grid_wait).  Only the plain time step sets it.
+template <typename... P, typename... A>
+inline void launch_maybe_overlapped(void (*kernel)(P...), dim3 grid, dim3 block, cudaStream_t s, bool overlap,
+                                    A... args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t c = {};
+    c.gridDim = grid;
+    c.blockDim = block;
+    c.dynamicSmemBytes = 0;
+    c.stream = s;
+    c.attrs = at;
+    c.numAttrs = overlap ? 1 : 0;
+    cudaLaunchKernelEx(&c, kernel, args...);
+}
+void launch_collide_stream(int prec, const Lattice &L, const CollideArgs &a, cudaStream_t s, bool overlap = false);
 // batched persistent variant: CollideArgs pointers are the concatenated buffers
-void launch_collide_batch(int prec, const BatchArgs &b, const CollideArgs &a, cudaStream_t s);
+void launch_collide_batch(int prec, const BatchArgs &b, const CollideArgs &a, cudaStream_t s,
+                          bool overlap = false);
 int collide_batch_blocks_per_sm(int prec);
 // mode 0: rest; mode 1: linear Couette equilibrium
 void launch_init_fluid(int prec, const Lattice &L, void *pop, int mode, double u_wall, cudaStream_t s);
@@ -125,13 +145,13 @@ void launch_force_to_f64(int prec, const Lattice &L, const void *force, double *
 // null for a single lattice described by L.
 void launch_force_spread(int prec, int delta, const Lattice &L, const MeshDev &m, void *force,
                          uint8_t *flags, int *status, const RunDesc *runs, const int *node_run,
-                         cudaStream_t s);
+                         cudaStream_t s, bool overlap = false);
 // velocity (Vec4) of every cell of the force-flagged tiles from the
 // populations after the step and the step's force density; items / n_items:
 // the batch work list of (run, tile) pairs, or null for a single lattice
 void launch_flag_velocity(int prec, const Lattice &L, const void *pop, const void *force, const uint8_t *flags,
                           void *uvel, const RunDesc *runs, const int2 *items, long long n_items,
-                          cudaStream_t s);
+                          cudaStream_t s, bool overlap = false);
 // interpolation at the nodes and Euler advection: of the cell velocities uvel
 // when not null, else of velocities formed at each stencil cell from the
 // populations pop and the force density force (the same arithmetic)
@@ -140,7 +160,8 @@ void launch_flag_velocity(int prec, const Lattice &L, const void *pop, const voi
 // with the previous node velocities in m.u instead of Euler's.
 void launch_interp_advect(int prec, int delta, const Lattice &L, const MeshDev &m, const void *uvel,
                           const void *pop, const void *force, const RunDesc *runs, const int *node_run,
-                          cudaStream_t s, void *snap_x = nullptr, void *snap_lo = nullptr, int ab2 = 0);
+                          cudaStream_t s, void *snap_x = nullptr, void *snap_lo = nullptr, int ab2 = 0,
+                          bool overlap = false);
 // node data <-> host doubles [n][3]
 void launch_nodes_to_f64(int prec, const MeshDev &m, int which, int first, int count, double *out,
                          cudaStream_t s);

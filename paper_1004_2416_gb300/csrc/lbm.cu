@@ -111,6 +111,8 @@ __global__ void __launch_bounds__(kTileX *kTileY)
                      int nx, int ny, int nz, int ntx, int nty, long long ncell, T omega,
                      T u_wall, int *status, typename Vec4<T>::type *__restrict__ moments) {
     using V4 = typename Vec4<T>::type;
+    prior_grid_wait();
+    allow_dependents();
     const int x = blockIdx.x * kTileX + threadIdx.x;
     const int y = blockIdx.y * kTileY + threadIdx.y;
     const int z = blockIdx.z;
@@ -145,6 +147,8 @@ __global__ void __launch_bounds__(256)
                     const RunDesc *__restrict__ runs, const int2 *__restrict__ items, int n_items,
                     int *status) {
     using V4 = typename Vec4<T>::type;
+    prior_grid_wait();
+    allow_dependents();
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const int2 w = items[it];
         const RunDesc R = runs[w.x];
@@ -306,6 +310,12 @@ __global__ void __launch_bounds__(256, 2)
     const int cell0 = x0 + NX * row;
     __shared__ float edge[8][10];  // rows spanning several warps: crossing values by warp and direction
 
+    // the force flags and density come from the spreading kernel before this
+    // one (reading the populations before waiting for it puts the flags'
+    // round trip after the loads: slower)
+    prior_grid_wait();
+    allow_dependents();
+
     // force flags per 32-cell segment of a row (the whole row if nx < 32); the
     // lanes of one segment are consecutive lanes of one warp
     constexpr int FTX = NX < 32 ? NX : 32;
@@ -327,6 +337,7 @@ __global__ void __launch_bounds__(256, 2)
     float2 g[19][2];
 #pragma unroll
     for (int i = 0; i < 19; ++i) Quad<S>::load_raw(src + (size_t)i * ncell + cell0, g[i][0], g[i][1]);
+
 
     // per cell: moments, velocity with the half force, and the pair vectors
     // of the per-direction arithmetic.  A = D + kScale rho (-3/2 u.u) is the
@@ -564,79 +575,79 @@ __global__ void k_force_to_f64(const typename Vec4<T>::type *force, long long nc
 static inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 template <typename S, int LR>
-static void collide_x4(const Lattice &L, const CollideArgs &a, cudaStream_t s) {
+static void collide_x4(const Lattice &L, const CollideArgs &a, cudaStream_t s, bool ov) {
     constexpr int rpb = rows_per_block<LR>();
     const int nrows = L.ny * L.nz;
     const unsigned nb = (unsigned)((nrows + rpb - 1) / rpb);
     // the moments are kept only by the adjoint's recomputation, which runs
     // with the full equilibrium
     if (a.moments)
-        k_collide_stream_x4<S, LR, true><<<nb, 256, 0, s>>>(
+        launch_maybe_overlapped(k_collide_stream_x4<S, LR, true>, dim3(nb), dim3(256), s, ov,
             (const S *)a.src, (S *)a.dst, (const float4 *)a.fcur, a.flag_cur, (float4 *)a.fold,
             a.flag_old, L.ny, L.nz, (int)L.ncell, (float)(1.0 / a.tau), (float)a.u_wall, a.status,
             (float4 *)a.moments);
     else if (a.eq_order == 1)
-        k_collide_stream_x4<S, LR, false, true><<<nb, 256, 0, s>>>(
+        launch_maybe_overlapped(k_collide_stream_x4<S, LR, false, true>, dim3(nb), dim3(256), s, ov,
             (const S *)a.src, (S *)a.dst, (const float4 *)a.fcur, a.flag_cur, (float4 *)a.fold,
             a.flag_old, L.ny, L.nz, (int)L.ncell, (float)(1.0 / a.tau), (float)a.u_wall, a.status,
             nullptr);
     else
-        k_collide_stream_x4<S, LR, false><<<nb, 256, 0, s>>>(
+        launch_maybe_overlapped(k_collide_stream_x4<S, LR, false>, dim3(nb), dim3(256), s, ov,
             (const S *)a.src, (S *)a.dst, (const float4 *)a.fcur, a.flag_cur, (float4 *)a.fold,
             a.flag_old, L.ny, L.nz, (int)L.ncell, (float)(1.0 / a.tau), (float)a.u_wall, a.status,
             nullptr);
 }
 
 template <typename S>
-static bool collide_vec(const Lattice &L, const CollideArgs &a, cudaStream_t s) {
+static bool collide_vec(const Lattice &L, const CollideArgs &a, cudaStream_t s, bool ov) {
     switch (L.lanes_row) {
-        case 1: collide_x4<S, 1>(L, a, s); return true;
-        case 2: collide_x4<S, 2>(L, a, s); return true;
-        case 4: collide_x4<S, 4>(L, a, s); return true;
-        case 8: collide_x4<S, 8>(L, a, s); return true;
-        case 16: collide_x4<S, 16>(L, a, s); return true;
-        case 32: collide_x4<S, 32>(L, a, s); return true;
-        case 64: collide_x4<S, 64>(L, a, s); return true;
-        case 128: collide_x4<S, 128>(L, a, s); return true;
-        case 256: collide_x4<S, 256>(L, a, s); return true;
+        case 1: collide_x4<S, 1>(L, a, s, ov); return true;
+        case 2: collide_x4<S, 2>(L, a, s, ov); return true;
+        case 4: collide_x4<S, 4>(L, a, s, ov); return true;
+        case 8: collide_x4<S, 8>(L, a, s, ov); return true;
+        case 16: collide_x4<S, 16>(L, a, s, ov); return true;
+        case 32: collide_x4<S, 32>(L, a, s, ov); return true;
+        case 64: collide_x4<S, 64>(L, a, s, ov); return true;
+        case 128: collide_x4<S, 128>(L, a, s, ov); return true;
+        case 256: collide_x4<S, 256>(L, a, s, ov); return true;
         default: return false;
     }
 }
 
 template <typename S, typename T>
-static void collide_impl(const Lattice &L, const CollideArgs &a, cudaStream_t s) {
+static void collide_impl(const Lattice &L, const CollideArgs &a, cudaStream_t s, bool ov) {
     using V4 = typename Vec4<T>::type;
     dim3 grid(L.ntx, L.nty, L.nz), block(kTileX, kTileY);
     auto kern = a.eq_order == 1 ? k_collide_stream<S, T, true> : k_collide_stream<S, T, false>;
-    kern<<<grid, block, 0, s>>>(
+    launch_maybe_overlapped(kern, grid, block, s, ov,
         (const S *)a.src, (S *)a.dst, (const V4 *)a.fcur, a.flag_cur, (V4 *)a.fold, a.flag_old,
         L.nx, L.ny, L.nz, L.ntx, L.nty, L.ncell, (T)(1.0 / a.tau), (T)a.u_wall, a.status,
         (V4 *)a.moments);
 }
 
-void launch_collide_stream(int prec, const Lattice &L, const CollideArgs &a, cudaStream_t s) {
-    if (prec == kF64) collide_impl<double, double>(L, a, s);
+void launch_collide_stream(int prec, const Lattice &L, const CollideArgs &a, cudaStream_t s, bool overlap) {
+    if (prec == kF64) collide_impl<double, double>(L, a, s, overlap);
     else if (prec == kF32) {
-        if (!collide_vec<float>(L, a, s)) collide_impl<float, float>(L, a, s);
+        if (!collide_vec<float>(L, a, s, overlap)) collide_impl<float, float>(L, a, s, overlap);
     } else {
-        if (!collide_vec<__half>(L, a, s)) collide_impl<__half, float>(L, a, s);
+        if (!collide_vec<__half>(L, a, s, overlap)) collide_impl<__half, float>(L, a, s, overlap);
     }
 }
 
 template <typename S, typename T>
-static void collide_batch_impl(const BatchArgs &b, const CollideArgs &a, cudaStream_t s) {
+static void collide_batch_impl(const BatchArgs &b, const CollideArgs &a, cudaStream_t s, bool ov) {
     using V4 = typename Vec4<T>::type;
     auto kern = a.eq_order == 1 ? k_collide_batch<S, T, true> : k_collide_batch<S, T, false>;
-    kern<<<b.grid, 256, 0, s>>>(
+    launch_maybe_overlapped(kern, dim3(b.grid), dim3(256), s, ov,
         (const S *)a.src, (S *)a.dst, (const V4 *)a.fcur, a.flag_cur, (V4 *)a.fold, a.flag_old,
         b.runs, b.items, b.n_items, a.status);
 }
 
-void launch_collide_batch(int prec, const BatchArgs &b, const CollideArgs &a, cudaStream_t s) {
+void launch_collide_batch(int prec, const BatchArgs &b, const CollideArgs &a, cudaStream_t s, bool overlap) {
     if (b.n_items == 0) return;
-    if (prec == kF64) collide_batch_impl<double, double>(b, a, s);
-    else if (prec == kF32) collide_batch_impl<float, float>(b, a, s);
-    else collide_batch_impl<__half, float>(b, a, s);
+    if (prec == kF64) collide_batch_impl<double, double>(b, a, s, overlap);
+    else if (prec == kF32) collide_batch_impl<float, float>(b, a, s, overlap);
+    else collide_batch_impl<__half, float>(b, a, s, overlap);
 }
 
 int collide_batch_blocks_per_sm(int prec) {

@@ -103,6 +103,7 @@ _SIGS = {
     "iblbm_adjoint_taylor": (_int, [_vp, _int, ctypes.c_int64, _int, _dp, _dp, _dp, _dp]),
     "iblbm_checkpoint_size": (_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "iblbm_set_interp_mode": (_int, [_vp, _int]),
+    "iblbm_set_launch_overlap": (_int, [_vp, _int]),
     "iblbm_set_integrator": (_int, [_vp, _int]),
     "iblbm_tank_treading": (_int, [_dp, _dp, _int, _dp, _dp, _dbl, _dp, _dp]),
     "iblbm_ellipsoid_fit": (_int, [_dp, _int, _dp, _dp]),
@@ -457,6 +458,12 @@ class Sim:
     def set_interp_mode(self, mode: int):
         """-1 automatic (default), 0 gather at the stencil cells, 1 cell velocities first."""
         _check(iblbm_set_interp_mode(self._h, int(mode)), self._h)
+
+    def set_launch_overlap(self, mode):
+        """Programmatic dependent launch of the step kernels: True/1 on,
+        False/0 off, -1 automatic (default: on for dense suspensions)."""
+        m = -1 if mode == -1 else (1 if mode else 0)
+        _check(iblbm_set_launch_overlap(self._h, m), self._h)
 
     def checkpoint_size(self) -> int:
         n = ctypes.c_size_t()
