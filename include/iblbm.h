@@ -192,7 +192,10 @@ int iblbm_init_fluid(iblbm_sim *sim, int mode);
  * lbmmomenta0/1), interpolation of the new lattice velocity at the old node
  * positions (Eq. velocityinterpolation) and Euler advection
  * (Eq. positionupdate).  The lattice velocity that is interpolated is
- * (sum_i c_i f_i(t+1) + f(t)/2) / rho(t+1).  Asynchronous. */
+ * (sum_i c_i f_i(t+1) + f(t)/2) / rho(t+1).  Runs of 32 steps (or a
+ * multiple of the recording period) replay captured CUDA graphs; a single
+ * step without Taylor recording replays a captured one-step graph, the rest
+ * are launched kernel by kernel.  Asynchronous. */
 int iblbm_step(iblbm_sim *sim, int64_t n_steps);
 
 /* Sub-step 6 of the step list of Sec. II.C, kept on the device: after every
@@ -403,6 +406,32 @@ int iblbm_get_mesh(iblbm_sim *sim, int capsule_id, int *n_nodes, int *n_tri,
  * D = (r_a - r_c)/(r_a + r_c) the Taylor deformation, theta the angle of the
  * major axis in the xz plane, from +x toward +z. */
 int iblbm_get_taylor(iblbm_sim *sim, int capsule_id, double out[16]);
+
+/* ---- asynchronous read-back -------------------------------------------------------
+ *
+ * Enqueues on the object's stream, after the work already enqueued, and
+ * returns without synchronising:
+ *   host_nodes  (may be NULL) the positions of all nodes, [n_nodes][3]
+ *               doubles, capsules in order (as iblbm_get_nodes(sim, -1, ..));
+ *   host_sums   (may be NULL) the device reductions of every capsule,
+ *               [n_capsules][12] doubles {V, A, c_x, c_y, c_z, I_xx, I_yy,
+ *               I_zz, I_xy, I_xz, I_yz, 0} (as behind iblbm_get_taylor;
+ *               iblbm_taylor_from_sums turns one into the 16 shape values).
+ * The host buffers belong to the caller and are written when the stream
+ * reaches the copies: read them after the next synchronising call (e.g.
+ * iblbm_sync), and leave them alone until then.  Page-locked buffers
+ * (cudaHostAlloc, cudaHostRegister, torch pin_memory) let the copies run
+ * while the host enqueues further steps; pageable buffers make the copies
+ * synchronous.  The device conversions use buffers of the object, so a later
+ * read-back may be enqueued at once (the stream orders them).  Device errors
+ * come back from the next synchronising call.  IBLBM_ERR_ARG for a null
+ * object. */
+int iblbm_read_async(iblbm_sim *sim, double *host_nodes, double *host_sums);
+
+/* The 16 shape values of iblbm_get_taylor from one capsule's 12 reduced sums
+ * (host arithmetic only; no object needed).  IBLBM_ERR_ARG for null
+ * pointers. */
+int iblbm_taylor_from_sums(const double sums[12], double out[16]);
 
 /* ---- allocation-free capsule reductions ------------------------------------------
  *

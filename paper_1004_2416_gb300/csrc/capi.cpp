@@ -90,6 +90,8 @@ struct iblbm_sim {
     std::vector<void *> plan_allocs;
 
     double *d_scratch = nullptr;
+    double *d_readback = nullptr;  // iblbm_read_async's node conversion
+    size_t readback_bytes = 0;
     size_t scratch_bytes = 0;
 
     // Taylor recording: after every `rec_every`-th step (0 = off) the device
@@ -145,6 +147,9 @@ struct iblbm_sim {
 
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t graph_kernels[2] = {0, 0};  // kernels in each captured graph
+    // one-step graphs (by buffer parity) for single steps without records
+    cudaGraphExec_t graph1[2] = {nullptr, nullptr};
+    int64_t graph1_kernels[2] = {0, 0};
     int64_t launches = 0;               // kernels launched for time steps
     int graph_len = 0;
     int64_t steps = 0;
@@ -189,11 +194,16 @@ void dev_free(iblbm_sim *s, void *p) {
 }
 
 void drop_graphs(iblbm_sim *s) {
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 2; ++k) {
         if (s->graph[k]) {
             cudaGraphExecDestroy(s->graph[k]);
             s->graph[k] = nullptr;
         }
+        if (s->graph1[k]) {
+            cudaGraphExecDestroy(s->graph1[k]);
+            s->graph1[k] = nullptr;
+        }
+    }
 }
 
 int ensure_scratch(iblbm_sim *s, size_t bytes) {
@@ -902,6 +912,7 @@ int iblbm_destroy(iblbm_sim *s) {
     }
     dev_free(s, s->d_status);
     dev_free(s, s->uvel);
+    dev_free(s, s->d_readback);
     dev_free(s, s->d_scratch);
     dev_free(s, s->d_runs);
     dev_free(s, s->d_items);
@@ -1112,6 +1123,36 @@ int iblbm_step(iblbm_sim *s, int64_t n_steps) {
                 if (record_after(s, k)) s->rec_steps.push_back(s->steps + k + 1);
             left -= G;  // G is even: buffer parity unchanged
             s->steps += G;
+        } else if (s->rec_every <= 0 && (s->integrator == 0 || s->ab2_ready)) {
+            // a single step without records: a cached one-step graph (one
+            // launch call instead of one per kernel)
+            cudaGraphExec_t &g = s->graph1[s->cur];
+            if (!g) {
+                cudaGraph_t graph = nullptr;
+                const int cur0 = s->cur;
+                join_side(s);
+                const int64_t launches0 = s->launches;
+                CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+                enqueue_step(s, false);
+                cudaError_t e = cudaStreamEndCapture(s->stream, &graph);
+                s->cur = cur0;
+                s->graph1_kernels[cur0] = s->launches - launches0;
+                s->launches = launches0;
+                if (e != cudaSuccess) return cuda_fail(s, e, "graph capture");
+                e = cudaGraphInstantiate(&g, graph, cudaGraphInstantiateFlagUseNodePriority);
+                cudaGraphDestroy(graph);
+                if (e != cudaSuccess) {
+                    g = nullptr;
+                    return cuda_fail(s, e, "graph instantiation");
+                }
+            }
+            join_side(s);
+            CK(cudaGraphLaunch(g, s->stream));
+            s->launches += s->graph1_kernels[s->cur];
+            s->cur = 1 - s->cur;
+            s->ab2_ready = true;
+            s->steps++;
+            left--;
         } else {
             const bool rec = record_after(s, s->steps);
             enqueue_step(s, rec);
@@ -1935,6 +1976,43 @@ int iblbm_get_taylor(iblbm_sim *s, int id, double out[16]) {
     CK(cudaMemcpyAsync(r, s->plan.out + 12 * id, sizeof(r), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     taylor_from_sums(r, out);
+    return IBLBM_OK;
+}
+
+int iblbm_read_async(iblbm_sim *s, double *host_nodes, double *host_sums) {
+    if (!s) return IBLBM_ERR_ARG;
+    CK(cudaSetDevice(s->device));
+    int rc = ensure_mesh(s);
+    if (rc) return rc;
+    const int n = s->mesh.n_nodes, nc = (int)s->caps.size();
+    if (host_nodes && n > 0) {
+        const size_t bytes = sizeof(double) * 3 * (size_t)n;
+        if (s->readback_bytes < bytes) {
+            CK(cudaStreamSynchronize(s->stream));  // a pending copy may still read the old buffer
+            dev_free(s, s->d_readback);
+            s->d_readback = (double *)dev_alloc(s, bytes);
+            s->readback_bytes = s->d_readback ? bytes : 0;
+            if (!s->d_readback) return fail(s, IBLBM_ERR_OOM, "read-back buffer allocation failed");
+        }
+        launch_nodes_to_f64(s->prec, s->mesh, 0, 0, n, s->d_readback, s->stream);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(host_nodes, s->d_readback, bytes, cudaMemcpyDeviceToHost, s->stream));
+    }
+    if (host_sums && nc > 0) {
+        // the recorded reductions on the side stream share the partial sums:
+        // the stream waits for them (events only, no host synchronisation)
+        join_side(s);
+        launch_taylor(s->prec, s->mesh, s->plan, false, s->stream);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(host_sums, s->plan.out, sizeof(double) * 12 * (size_t)nc, cudaMemcpyDeviceToHost,
+                           s->stream));
+    }
+    return IBLBM_OK;
+}
+
+int iblbm_taylor_from_sums(const double sums[12], double out[16]) {
+    if (!sums || !out) return IBLBM_ERR_ARG;
+    taylor_from_sums(sums, out);
     return IBLBM_OK;
 }
 

@@ -104,6 +104,8 @@ _SIGS = {
     "iblbm_checkpoint_size": (_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "iblbm_set_interp_mode": (_int, [_vp, _int]),
     "iblbm_set_launch_overlap": (_int, [_vp, _int]),
+    "iblbm_read_async": (_int, [_vp, _vp, _vp]),
+    "iblbm_taylor_from_sums": (_int, [_vp, _vp]),
     "iblbm_set_integrator": (_int, [_vp, _int]),
     "iblbm_tank_treading": (_int, [_dp, _dp, _int, _dp, _dp, _dbl, _dp, _dp]),
     "iblbm_ellipsoid_fit": (_int, [_dp, _int, _dp, _dp]),
@@ -489,6 +491,17 @@ class Sim:
         _check(iblbm_get_taylor(self._h, capsule_id, _d(out)), self._h)
         return dict(zip(TAYLOR_KEYS, out.tolist()))
 
+    def read_async(self, nodes_out=None, sums_out=None):
+        """Enqueues copies of all node positions ([n][3] doubles) and of every
+        capsule's 12 reduced sums ([n_capsules][12] doubles) into the given
+        host arrays (numpy or CPU torch, preferably pinned) and returns at
+        once; they hold the values after the next synchronising call."""
+        inf = self.info()
+        n, nc = inf.n_nodes, inf.n_capsules
+        pn = _buffer(nodes_out, 24 * n)[0] if nodes_out is not None else None
+        ps = _buffer(sums_out, 96 * nc)[0] if sums_out is not None else None
+        _check(iblbm_read_async(self._h, pn, ps), self._h)
+
 
 def tank_treading(x_then, x_now, c_then, c_now, dt: float):
     """Per-node angular velocities [n] about the centroid in the xz plane, and
@@ -500,6 +513,14 @@ def tank_treading(x_then, x_now, c_then, c_now, dt: float):
     _check(iblbm_tank_treading(_d(x0), _d(x1), x0.shape[0], _d(np.ascontiguousarray(c_then, np.float64)),
                                _d(np.ascontiguousarray(c_now, np.float64)), float(dt), _d(om), ctypes.byref(mean)))
     return om, mean.value
+
+
+def taylor_from_sums(sums) -> dict:
+    """The shape values of Sim.taylor from one capsule's 12 reduced sums (host only)."""
+    r = np.ascontiguousarray(sums, np.float64).reshape(12)
+    out = np.empty(16, np.float64)
+    _check(iblbm_taylor_from_sums(_d(r), _d(out)))
+    return dict(zip(TAYLOR_KEYS, out.tolist()))
 
 
 FIT_KEYS = ("zeta_x", "zeta_y", "zeta_z", "zeta_xz", "r_a", "r_b", "r_c", "D", "theta")
