@@ -58,46 +58,65 @@ __device__ __forceinline__ void collide_cell(const S *__restrict__ src, S *__res
     const T ux = (jx + T(0.5) * fx) * inv_rho;
     const T uy = (jy + T(0.5) * fy) * inv_rho;
     const T uz = (jz + T(0.5) * fz) * inv_rho;
-    const T uu15 = T(1.5) * (ux * ux + uy * uy + uz * uz);
-    const T guo = T(1) - T(0.5) * omega;
-    const T uf = ux * fx + uy * fy + uz * fz;
+    // A = drho - 3/2 rho u.u: the part of the equilibrium (minus the weight)
+    // common to all directions (drho alone for the linearised form)
+    const T A = LIN ? drho : drho - T(1.5) * rho * (ux * ux + uy * uy + uz * uz);
+    const T ufm = T(-3) * (ux * fx + uy * fy + uz * fz);
+    const T keep = T(1) - omega, guo = T(1) - T(0.5) * omega;
 
-    const int xp = (x + 1 == nx) ? 0 : x + 1;
-    const int xm = (x == 0) ? nx - 1 : x - 1;
-    const int yp = (y + 1 == ny) ? 0 : y + 1;
-    const int ym = (y == 0) ? ny - 1 : y - 1;
-
-#pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        constexpr T zero = T(0);
+    // push offsets of the neighbour cells (periodic in x and y)
+    const long long sz = (long long)nx * ny;
+    const long long dyp = (y + 1 == ny) ? -(long long)(ny - 1) * nx : (long long)nx;
+    const long long dym = (y == 0) ? (long long)(ny - 1) * nx : -(long long)nx;
+    const int dxp = (x + 1 == nx) ? 1 - nx : 1, dxm = (x == 0) ? nx - 1 : -1;
+    auto emit = [&](const int i, const T post) {
         const int cx = q_cx(i), cy = q_cy(i), cz = q_cz(i);
-        const T w = q_w<T>(i);
-        T cu = zero;
-        if (cx) cu += cx > 0 ? ux : -ux;
-        if (cy) cu += cy > 0 ? uy : -uy;
-        if (cz) cu += cz > 0 ? uz : -uz;
-        // Eq. (equilibrium) (or its linearised form) minus the rest weight
-        const T geq = LIN ? w * (drho + rho * (T(3) * cu)) : w * (drho + rho * (T(3) * cu + T(4.5) * cu * cu - uu15));
-        T post = g[i] - omega * (g[i] - geq);
-        if (has_cur) {
-            // Eq. (latticeforce) with c_s^2 = 1/3
-            T cf = zero;
-            if (cx) cf += cx > 0 ? fx : -fx;
-            if (cy) cf += cy > 0 ? fy : -fy;
-            if (cz) cf += cz > 0 ? fz : -fz;
-            post += guo * w * (T(3) * (cf - uf) + T(9) * cu * cf);
-        }
-        const int zt = z + cz;
-        if ((cz > 0 && zt == nz) || (cz < 0 && z == 0)) {
+        if ((cz > 0 && z + 1 == nz) || (cz < 0 && z == 0)) {
             const T uw = (cz > 0) ? u_wall : -u_wall;
-            const T wall = (cx == 0) ? zero : T(6) * w * (cx > 0 ? uw : -uw);
+            const T wall = (cx == 0) ? T(0) : T(6) * q_w<T>(i) * (cx > 0 ? uw : -uw);
             Store<S, T>::store(dst + q_opp(i) * ncell + cell, post - wall);
         } else {
-            const int xt = cx > 0 ? xp : (cx < 0 ? xm : x);
-            const int yt = cy > 0 ? yp : (cy < 0 ? ym : y);
-            const long long t = xt + (long long)nx * (yt + (long long)ny * zt);
+            const long long t = cell + (cx > 0 ? dxp : (cx < 0 ? dxm : 0)) +
+                                (cy > 0 ? dyp : (cy < 0 ? dym : 0)) + cz * sz;
             Store<S, T>::store(dst + i * ncell + t, post);
         }
+    };
+    // rest direction: equilibrium w0 A, force term w0 (1 - omega/2)(-3 u.f)
+    {
+        const T w = q_w<T>(0);
+        T post = keep * g[0] + omega * w * A;
+        if (has_cur) post += guo * w * ufm;
+        emit(0, post);
+    }
+    // opposite pairs (c, -c), c with its first nonzero component positive:
+    // with r = rho c.u the equilibrium (minus the weight) is
+    // w (A + 9/2 r c.u +- 3 r) (Eq. equilibrium; the linearised form drops the
+    // quadratic term) and the force term (Eq. latticeforce, c_s^2 = 1/3)
+    // (1 - omega/2) w (9 (c.u)(c.f) - 3 u.f +- 3 c.f)
+#pragma unroll
+    for (int j = 1; j < 19; j += 2) {
+        const int ip = (q_cx(j) > 0 || (q_cx(j) == 0 && (q_cy(j) > 0 || (q_cy(j) == 0 && q_cz(j) > 0))))
+                           ? j : q_opp(j);
+        const int im = q_opp(ip);
+        const int cx = q_cx(ip), cy = q_cy(ip), cz = q_cz(ip);
+        const T w = q_w<T>(ip);
+        T cu = cx ? ux : (cy ? uy : uz);
+        if (cx && cy) cu = cy > 0 ? cu + uy : cu - uy;
+        if ((cx || cy) && cz) cu = cz > 0 ? cu + uz : cu - uz;
+        const T r = rho * cu;
+        const T e = LIN ? A : A + T(4.5) * r * cu;
+        T postp = keep * g[ip] + omega * w * (e + T(3) * r);
+        T postm = keep * g[im] + omega * w * (e - T(3) * r);
+        if (has_cur) {
+            T cf = cx ? fx : (cy ? fy : fz);
+            if (cx && cy) cf = cy > 0 ? cf + fy : cf - fy;
+            if ((cx || cy) && cz) cf = cz > 0 ? cf + fz : cf - fz;
+            const T base = T(9) * cu * cf + ufm;
+            postp += guo * w * (base + T(3) * cf);
+            postm += guo * w * (base - T(3) * cf);
+        }
+        emit(ip, postp);
+        emit(im, postm);
     }
 }
 
@@ -155,8 +174,8 @@ __global__ void __launch_bounds__(256)
         const int per_z = R.ntx * R.nty;
         const int z = w.y / per_z, rem = w.y - z * per_z;
         const int tyi = rem / R.ntx, txi = rem - tyi * R.ntx;
-        const int x = txi * R.tx + (int)threadIdx.x % R.tx;
-        const int y = tyi * R.ty + (int)threadIdx.x / R.tx;
+        const int x = txi * R.tx + ((int)threadIdx.x & (R.tx - 1));  // tile sides are powers of two
+        const int y = tyi * R.ty + ((int)threadIdx.x >> (__ffs(R.tx) - 1));
         const bool inside = x < R.nx && y < R.ny;
         const long long tile = R.tile_off + w.y;
         const bool has_old = flag_old[tile] != 0;
