@@ -111,6 +111,7 @@ struct iblbm_sim {
     int2 *d_items = nullptr;
     int n_items = 0;
     int batch_grid = 0;
+    bool batch_pairs = false;  // the batch collide takes two cells per thread
     int *d_node_run = nullptr;
 
     // Adjoint: checkpoints of the forward run and the buffers of the reverse sweep.
@@ -499,7 +500,7 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) 
     a.status = s->d_status;
     a.eq_order = s->eq_order;
     if (s->batch) {
-        BatchArgs b{s->d_runs, s->d_items, s->n_items, s->batch_grid};
+        BatchArgs b{s->d_runs, s->d_items, s->n_items, s->batch_grid, s->batch_pairs};
         launch_collide_batch(s->prec, b, a, s->stream, ov);
     } else {
         launch_collide_stream(s->prec, s->L, a, s->stream, ov);
@@ -778,7 +779,9 @@ int upload_batch_tables(iblbm_sim *s) {
     s->n_items = (int)items.size();
     int sms = 0;
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device));
-    const long long want = (long long)sms * collide_batch_blocks_per_sm(s->prec);
+    s->batch_pairs = s->prec != kF64;
+    for (const RunDesc &R : s->runs) s->batch_pairs = s->batch_pairs && R.nx % 2 == 0;
+    const long long want = (long long)sms * collide_batch_blocks_per_sm(s->prec, s->batch_pairs);
     s->batch_grid = (int)std::max(1LL, std::min<long long>(want, s->n_items));
     drop_graphs(s);
     return IBLBM_OK;
@@ -1872,7 +1875,7 @@ int iblbm_autotune_tiles(iblbm_sim *s, int repeats) {
             }
             CK(cudaMemcpy(s->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice));
             BatchArgs b{s->d_runs, s->d_items, (int)items.size(),
-                        std::min(s->batch_grid, (int)items.size())};
+                        std::min(s->batch_grid, (int)items.size()), s->batch_pairs};
             CollideArgs a{};
             a.src = s->pop[s->cur];
             a.dst = s->pop[1 - s->cur];  // overwritten by the next step

@@ -71,6 +71,7 @@ struct BatchArgs {
     const int2 *items;     // device [n_items]: (run, tile within the run)
     int n_items;
     int grid;              // persistent grid size
+    bool pairs = false;    // every run's rows have even length: two cells per thread (float builds)
 };
 
 // Device views of the membrane data, all capsules concatenated.
@@ -130,7 +131,7 @@ void launch_collide_stream(int prec, const Lattice &L, const CollideArgs &a, cud
 // batched persistent variant: CollideArgs pointers are the concatenated buffers
 void launch_collide_batch(int prec, const BatchArgs &b, const CollideArgs &a, cudaStream_t s,
                           bool overlap = false);
-int collide_batch_blocks_per_sm(int prec);
+int collide_batch_blocks_per_sm(int prec, bool pairs);
 // mode 0: rest; mode 1: linear Couette equilibrium
 void launch_init_fluid(int prec, const Lattice &L, void *pop, int mode, double u_wall, cudaStream_t s);
 // rho [ncell] and u [3][ncell] in double from populations + half the force

@@ -10,6 +10,8 @@
 // cell; only tiles flagged by the spreading kernel hold non-zero force, so
 // the collide kernel reads it only there and zeroes the previous step's
 // tiles as it passes.
+#include <type_traits>
+
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -525,6 +527,205 @@ __global__ void __launch_bounds__(256, 2)
     }
 }
 
+// ---- two cells per thread (rows of even length, float arithmetic) ------------------
+// Cells (x, x + 1), x even, of a row of even length: one 8-byte (float) or
+// 4-byte (binary16) load per direction, arithmetic on the pair with the
+// packed FP32 instructions, the directions with c_x = 0 and the wall
+// bounce-back stored as pairs, the shifted directions cell by cell.  The
+// arithmetic is collide_cell's (opposite pairs), in physical units.
+template <typename S>
+struct Pair;
+template <>
+struct Pair<float> {
+    static __device__ __forceinline__ float2 load(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+    static __device__ __forceinline__ void store(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+    static __device__ __forceinline__ void store1(float *p, float v) { *p = v; }
+};
+template <>
+struct Pair<__half> {
+    static __device__ __forceinline__ float2 load(const __half *p) {
+        const float2 f = __half22float2(__ldg(reinterpret_cast<const __half2 *>(p)));
+        return make_float2(f.x * kHalfInvScale, f.y * kHalfInvScale);
+    }
+    static __device__ __forceinline__ void store(__half *p, float2 v) {
+        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(v.x * kHalfScale, v.y * kHalfScale);
+    }
+    static __device__ __forceinline__ void store1(__half *p, float v) { *p = __float2half_rn(v * kHalfScale); }
+};
+
+template <typename S, bool LIN>
+__device__ __forceinline__ void collide_pair(const S *__restrict__ src, S *__restrict__ dst,
+                                             const float4 *__restrict__ fcur, bool has_cur, int x, int y,
+                                             int z, int nx, int ny, int nz, long long ncell, float omega,
+                                             float u_wall, int *status) {
+    const long long cell = x + (long long)nx * (y + (long long)ny * z);
+    float2 g[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) g[i] = Pair<S>::load(src + i * ncell + cell);
+    float2 d = make_float2(0.f, 0.f), jx = d, jy = d, jz = d;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        d = add2(d, g[i]);
+        if (q_cx(i)) jx = q_cx(i) > 0 ? add2(jx, g[i]) : sub2(jx, g[i]);
+        if (q_cy(i)) jy = q_cy(i) > 0 ? add2(jy, g[i]) : sub2(jy, g[i]);
+        if (q_cz(i)) jz = q_cz(i) > 0 ? add2(jz, g[i]) : sub2(jz, g[i]);
+    }
+    float fv[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    if (has_cur) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const float4 f = fcur[cell + e];
+            fv[e][0] = f.x; fv[e][1] = f.y; fv[e][2] = f.z;
+        }
+    }
+    float ux[2], uy[2], uz[2], rh[2], ac[2], ufm[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const float de = e ? d.y : d.x;
+        const float rho = 1.f + de;
+        if (!(rho > 0.5f && rho < 2.f)) set_status(status, kStatusUnstable);
+        const float inv = 1.f / rho;
+        ux[e] = ((e ? jx.y : jx.x) + 0.5f * fv[e][0]) * inv;
+        uy[e] = ((e ? jy.y : jy.x) + 0.5f * fv[e][1]) * inv;
+        uz[e] = ((e ? jz.y : jz.x) + 0.5f * fv[e][2]) * inv;
+        rh[e] = rho;
+        ac[e] = LIN ? de : de - 1.5f * rho * (ux[e] * ux[e] + uy[e] * uy[e] + uz[e] * uz[e]);
+        ufm[e] = -3.f * (ux[e] * fv[e][0] + uy[e] * fv[e][1] + uz[e] * fv[e][2]);
+    }
+    const float2 Ux = make_float2(ux[0], ux[1]), Uy = make_float2(uy[0], uy[1]), Uz = make_float2(uz[0], uz[1]);
+    const float2 R = make_float2(rh[0], rh[1]), A = make_float2(ac[0], ac[1]), Ufm = make_float2(ufm[0], ufm[1]);
+    const float2 Fx = make_float2(fv[0][0], fv[1][0]), Fy = make_float2(fv[0][1], fv[1][1]);
+    const float2 Fz = make_float2(fv[0][2], fv[1][2]);
+    const float guo = 1.f - 0.5f * omega;
+    const float2 keep2 = make_float2(1.f - omega, 1.f - omega);
+
+    // push offsets (periodic in x and y): cell x never wraps to the right and
+    // cell x + 1 never to the left
+    const long long sz = (long long)nx * ny;
+    const long long dyp = (y + 1 == ny) ? -(long long)(ny - 1) * nx : (long long)nx;
+    const long long dym = (y == 0) ? (long long)(ny - 1) * nx : -(long long)nx;
+    const int dxm0 = (x == 0) ? nx - 1 : -1, dxp1 = (x + 2 == nx) ? 1 - nx : 1;
+    auto emit = [&](const int i, const float2 post) {
+        const int cx = q_cx(i), cy = q_cy(i), cz = q_cz(i);
+        if ((cz > 0 && z + 1 == nz) || (cz < 0 && z == 0)) {
+            const float uw = (cz > 0) ? u_wall : -u_wall;
+            const float wall = (cx == 0) ? 0.f : 6.f * q_w<float>(i) * (cx > 0 ? uw : -uw);
+            Pair<S>::store(dst + q_opp(i) * ncell + cell, make_float2(post.x - wall, post.y - wall));
+        } else {
+            S *b = dst + i * ncell + cell + (cy > 0 ? dyp : (cy < 0 ? dym : 0)) + cz * sz;
+            if (cx == 0) {
+                Pair<S>::store(b, post);
+            } else if (cx > 0) {
+                Pair<S>::store1(b + 1, post.x);
+                Pair<S>::store1(b + 1 + dxp1, post.y);
+            } else {
+                Pair<S>::store1(b + dxm0, post.x);
+                Pair<S>::store1(b, post.y);
+            }
+        }
+    };
+    {
+        const float w = q_w<float>(0);
+        float2 post = fma2(make_float2(omega * w, omega * w), A, mul2(keep2, g[0]));
+        if (has_cur) post = fma2(make_float2(guo * w, guo * w), Ufm, post);
+        emit(0, post);
+    }
+#pragma unroll
+    for (int j = 1; j < 19; j += 2) {
+        const int ip = (q_cx(j) > 0 || (q_cx(j) == 0 && (q_cy(j) > 0 || (q_cy(j) == 0 && q_cz(j) > 0))))
+                           ? j : q_opp(j);
+        const int im = q_opp(ip);
+        const int cx = q_cx(ip), cy = q_cy(ip), cz = q_cz(ip);
+        const float w = q_w<float>(ip);
+        const float2 omw = make_float2(omega * w, omega * w), gw = make_float2(guo * w, guo * w);
+        float2 cu = cx ? Ux : (cy ? Uy : Uz);
+        if (cx && cy) cu = cy > 0 ? add2(cu, Uy) : sub2(cu, Uy);
+        if ((cx || cy) && cz) cu = cz > 0 ? add2(cu, Uz) : sub2(cu, Uz);
+        const float2 r = mul2(R, cu);
+        const float2 e = LIN ? A : fma2(mul2(r, make_float2(4.5f, 4.5f)), cu, A);
+        float2 postp = fma2(omw, fma2(r, make_float2(3.f, 3.f), e), mul2(keep2, g[ip]));
+        float2 postm = fma2(omw, fma2(r, make_float2(-3.f, -3.f), e), mul2(keep2, g[im]));
+        if (has_cur) {
+            float2 cf = cx ? Fx : (cy ? Fy : Fz);
+            if (cx && cy) cf = cy > 0 ? add2(cf, Fy) : sub2(cf, Fy);
+            if ((cx || cy) && cz) cf = cz > 0 ? add2(cf, Fz) : sub2(cf, Fz);
+            const float2 base = fma2(mul2(cu, cf), make_float2(9.f, 9.f), Ufm);
+            postp = fma2(gw, fma2(cf, make_float2(3.f, 3.f), base), postp);
+            postm = fma2(gw, fma2(cf, make_float2(-3.f, -3.f), base), postm);
+        }
+        emit(ip, postp);
+        emit(im, postm);
+    }
+}
+
+// k_collide_stream for rows of even length: a 32 x 8 x 1 tile per block of
+// 16 x 8 threads, two cells per thread.
+template <typename S, bool LIN>
+__global__ void __launch_bounds__(kTileX / 2 * kTileY)
+    k_collide_pair(const S *__restrict__ src, S *__restrict__ dst, const float4 *__restrict__ fcur,
+                   const uint8_t *__restrict__ flag_cur, float4 *__restrict__ fold, uint8_t *__restrict__ flag_old,
+                   int nx, int ny, int nz, int ntx, int nty, long long ncell, float omega, float u_wall,
+                   int *status) {
+    prior_grid_wait();
+    allow_dependents();
+    const int x = blockIdx.x * kTileX + 2 * (int)threadIdx.x;
+    const int y = blockIdx.y * kTileY + (int)threadIdx.y;
+    const int z = blockIdx.z;
+    const long long tile = ((long long)z * nty + blockIdx.y) * ntx + blockIdx.x;
+    const bool inside = (x < nx) && (y < ny);  // nx even: x + 1 < nx as well
+    const long long cell = x + (long long)nx * (y + (long long)ny * z);
+    const bool has_old = flag_old[tile] != 0;
+    const bool has_cur = flag_cur[tile] != 0;
+    if (has_old) {
+        if (inside) {
+            fold[cell] = make_float4(0.f, 0.f, 0.f, 0.f);
+            fold[cell + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && threadIdx.y == 0) flag_old[tile] = 0;
+    }
+    if (!inside) return;
+    collide_pair<S, LIN>(src, dst, fcur, has_cur, x, y, z, nx, ny, nz, ncell, omega, u_wall, status);
+}
+
+// k_collide_batch for runs whose rows all have even length: 128 threads per
+// (run, tile) item, two cells per thread.
+template <typename S, bool LIN>
+__global__ void __launch_bounds__(128)
+    k_collide_pair_batch(const S *__restrict__ src, S *__restrict__ dst, const float4 *__restrict__ fcur,
+                         const uint8_t *__restrict__ flag_cur, float4 *__restrict__ fold,
+                         uint8_t *__restrict__ flag_old, const RunDesc *__restrict__ runs,
+                         const int2 *__restrict__ items, int n_items, int *status) {
+    prior_grid_wait();
+    allow_dependents();
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int2 w = items[it];
+        const RunDesc R = runs[w.x];
+        const int per_z = R.ntx * R.nty;
+        const int z = w.y / per_z, rem = w.y - z * per_z;
+        const int tyi = rem / R.ntx, txi = rem - tyi * R.ntx;
+        const int hx = R.tx >> 1;  // pairs per tile row (tile sides are powers of two)
+        const int x = txi * R.tx + 2 * ((int)threadIdx.x & (hx - 1));
+        const int y = tyi * R.ty + ((int)threadIdx.x >> (__ffs(hx) - 1));
+        const bool inside = x < R.nx && y < R.ny;
+        const long long tile = R.tile_off + w.y;
+        const bool has_old = flag_old[tile] != 0;
+        const bool has_cur = flag_cur[tile] != 0;
+        if (has_old) {
+            if (inside) {
+                const long long c = R.cell_off + x + (long long)R.nx * (y + (long long)R.ny * z);
+                fold[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+                fold[c + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) flag_old[tile] = 0;
+        }
+        if (inside)
+            collide_pair<S, LIN>(src + 19 * R.cell_off, dst + 19 * R.cell_off, fcur + R.cell_off, has_cur, x, y,
+                                 z, R.nx, R.ny, R.nz, R.ncell, (float)R.omega, (float)R.u_wall, status);
+    }
+}
+
 template <typename S, typename T>
 __global__ void k_init_fluid(S *pop, int nx, int ny, int nz, long long ncell, int mode,
                              double u_wall) {
@@ -637,6 +838,15 @@ template <typename S, typename T>
 static void collide_impl(const Lattice &L, const CollideArgs &a, cudaStream_t s, bool ov) {
     using V4 = typename Vec4<T>::type;
     dim3 grid(L.ntx, L.nty, L.nz), block(kTileX, kTileY);
+    if constexpr (!std::is_same<T, double>::value) {
+        if (L.nx % 2 == 0 && !a.moments) {  // the adjoint's recomputation keeps the one-cell kernel
+            auto kern = a.eq_order == 1 ? k_collide_pair<S, true> : k_collide_pair<S, false>;
+            launch_maybe_overlapped(kern, grid, dim3(kTileX / 2, kTileY), s, ov, (const S *)a.src, (S *)a.dst,
+                                    (const float4 *)a.fcur, a.flag_cur, (float4 *)a.fold, a.flag_old, L.nx, L.ny,
+                                    L.nz, L.ntx, L.nty, L.ncell, (float)(1.0 / a.tau), (float)a.u_wall, a.status);
+            return;
+        }
+    }
     auto kern = a.eq_order == 1 ? k_collide_stream<S, T, true> : k_collide_stream<S, T, false>;
     launch_maybe_overlapped(kern, grid, block, s, ov,
         (const S *)a.src, (S *)a.dst, (const V4 *)a.fcur, a.flag_cur, (V4 *)a.fold, a.flag_old,
@@ -656,6 +866,15 @@ void launch_collide_stream(int prec, const Lattice &L, const CollideArgs &a, cud
 template <typename S, typename T>
 static void collide_batch_impl(const BatchArgs &b, const CollideArgs &a, cudaStream_t s, bool ov) {
     using V4 = typename Vec4<T>::type;
+    if constexpr (!std::is_same<T, double>::value) {
+        if (b.pairs) {
+            auto kern = a.eq_order == 1 ? k_collide_pair_batch<S, true> : k_collide_pair_batch<S, false>;
+            launch_maybe_overlapped(kern, dim3(b.grid), dim3(128), s, ov, (const S *)a.src, (S *)a.dst,
+                                    (const float4 *)a.fcur, a.flag_cur, (float4 *)a.fold, a.flag_old, b.runs, b.items,
+                                    b.n_items, a.status);
+            return;
+        }
+    }
     auto kern = a.eq_order == 1 ? k_collide_batch<S, T, true> : k_collide_batch<S, T, false>;
     launch_maybe_overlapped(kern, dim3(b.grid), dim3(256), s, ov,
         (const S *)a.src, (S *)a.dst, (const V4 *)a.fcur, a.flag_cur, (V4 *)a.fold, a.flag_old,
@@ -669,10 +888,14 @@ void launch_collide_batch(int prec, const BatchArgs &b, const CollideArgs &a, cu
     else collide_batch_impl<__half, float>(b, a, s, overlap);
 }
 
-int collide_batch_blocks_per_sm(int prec) {
+int collide_batch_blocks_per_sm(int prec, bool pairs) {
     int n = 0;
     cudaError_t e;
-    if (prec == kF64)
+    if (pairs && prec == kF32)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide_pair_batch<float, false>, 128, 0);
+    else if (pairs && prec == kF16)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide_pair_batch<__half, false>, 128, 0);
+    else if (prec == kF64)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide_batch<double, double, false>, 256, 0);
     else if (prec == kF32)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_collide_batch<float, float, false>, 256, 0);

@@ -24,11 +24,13 @@ def _small_case(delta=3, precision="fp32", shape=(40, 36, 28), r=5.0, m=3, G=0.0
 
 # ---- lattice only ------------------------------------------------------------------
 
+@pytest.mark.parametrize("shape", [(37, 19, 11), (38, 19, 11)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
-def test_lattice_only_ragged(prec):
+def test_lattice_only_ragged(prec, shape):
     """Collide-stream with moving walls on a ragged lattice (not a multiple of
-    the 32 x 8 tile), tau != 1, random start."""
-    shape, tau, uw = (37, 19, 11), 0.8, 0.03
+    the 32 x 8 tile), tau != 1, random start; odd rows take the one-cell
+    kernel, even rows (float builds) the two-cells-per-thread kernel."""
+    tau, uw = 0.8, 0.03
     nx, ny, nz = shape
     f0 = O.init_couette(nx, ny, nz, uw) + W.population_noise(shape, 2e-3, seed=1)
     from paper_1004_2416_gb300 import Sim
@@ -121,6 +123,28 @@ def test_lattice_degenerate_shapes(shape):
     for _ in range(17):
         f = O.lbm_step(f, 1.3, uw)
     assert np.abs(s.get_populations() - f).max() < 1e-14
+
+
+@pytest.mark.parametrize("shape", [(2, 3, 5), (6, 1, 3), (10, 2, 4)])
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
+def test_lattice_short_even_rows(prec, shape):
+    """Rows of 2, 6 and 10 cells in the two-cells-per-thread kernel: both
+    periodic wraps in x fall on one thread's pair."""
+    nx, ny, nz = shape
+    uw = 0.05
+    f0 = O.init_couette(nx, ny, nz, uw) + W.population_noise(shape, 1e-3, seed=3)
+    from paper_1004_2416_gb300 import Sim
+
+    s = Sim(nx, ny, nz, tau=1.3, precision=prec, delta_points=2)
+    s.set_shear_walls(uw)
+    s.set_populations(f0)
+    s.step(17)
+    f = f0
+    for _ in range(17):
+        f = O.lbm_step(f, 1.3, uw)
+    _, w, _ = O.d3q19()
+    wb = w[:, None, None, None]
+    assert rel_inf(s.get_populations() - wb, f - wb) < {"fp32": 1e-5, "fp16": 3e-3}[prec]
 
 
 # ---- one coupled step, every sub-step compared ------------------------------------------
