@@ -78,6 +78,30 @@ def test_lattice_vectorised_rows(shape, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp16"])
+@pytest.mark.parametrize("shape", [(256, 48, 52), (512, 32, 40)])
+def test_lattice_long_rows_full_blocks(shape, prec):
+    """Rows of two and four warps on lattices of a few thousand rows (every
+    block full): the warp-edge cells come from shared memory across the warps
+    of a block."""
+    nx, ny, nz = shape
+    tau, uw = 0.9, 0.04
+    f0 = O.init_couette(nx, ny, nz, uw) + W.population_noise(shape, 2e-3, seed=12)
+    from paper_1004_2416_gb300 import Sim
+
+    s = Sim(nx, ny, nz, tau=tau, precision=prec, delta_points=3)
+    s.set_shear_walls(uw)
+    s.set_populations(f0)
+    s.step(3)
+    f = f0
+    for _ in range(3):
+        f = O.lbm_step(f, tau, uw)
+    _, w, _ = O.d3q19()
+    wb = w[:, None, None, None]
+    tol = {"fp32": 1e-5, "fp16": 3e-3}[prec]
+    assert rel_inf(s.get_populations() - wb, f - wb) < tol
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
 @pytest.mark.parametrize("delta", [2, 4])
 def test_one_step_vectorised_path(prec, delta):
     """Coupled step on a lattice that takes the vectorised kernel (nx = 64)."""
