@@ -127,3 +127,27 @@ def test_diagnostics_against_oracle():
     assert m_a == pytest.approx(0.01, rel=1e-9)
     with pytest.raises(B.IblbmError):
         B.ellipsoid_fit(x[:3], c)
+
+
+def test_taylor_from_sums_against_oracle():
+    """The library's host conversion of a capsule's reduced sums (V, A, c, I)
+    into D, theta and the semi-axes (its own 3 x 3 eigen-solver) against the
+    oracle's values from its Jacobi route, on a stretched, tilted and jittered
+    icosphere."""
+    import oracle as O
+    from paper_1004_2416_gb300 import iblbm as B
+
+    rng = np.random.default_rng(5)
+    x0, tri = O.icosphere(3, 5.0, (12.0, 9.0, 10.0))
+    th = -0.3
+    R = np.array([[np.cos(th), 0, -np.sin(th)], [0, 1, 0], [np.sin(th), 0, np.cos(th)]])
+    x = ((x0 - x0.mean(0)) * np.array([1.3, 0.95, 0.8])) @ R.T + x0.mean(0) + 0.02 * rng.standard_normal(x0.shape)
+    ref = O.taylor(x, tri)
+    sums = [ref[k] for k in ("V", "A", "c_x", "c_y", "c_z", "I_xx", "I_yy", "I_zz", "I_xy", "I_xz", "I_yz")] + [0.0]
+    got = B.taylor_from_sums(np.array(sums))
+    for k in ("D", "r_a", "r_b", "r_c"):
+        assert got[k] == pytest.approx(ref[k], rel=1e-12), k
+    assert got["theta"] == pytest.approx(ref["theta"], abs=1e-12)
+    assert got["D"] > 0.1
+    with pytest.raises(B.IblbmError):
+        B._check(B.iblbm_taylor_from_sums(None, None))
