@@ -271,11 +271,13 @@ int ensure_mesh(iblbm_sim *s) {
     m.u = A(v4 * nn);
     void *adj_off = A(sizeof(int) * (nn + 1));
     void *adj = A(sizeof(int) * 3 * nf);
+    void *adj4 = A(sizeof(int) * 12 * nf);
+    void *node_cap = A(sizeof(int) * nn);
     void *tri4 = A(sizeof(int) * 4 * nf);
     void *fconst = A(3 * v4 * nf);
     void *capmod = A(v4 * nc);
     void *node_run = s->batch ? A(sizeof(int) * nn) : nullptr;
-    if (!m.x || (s->prec != kF64 && !m.x_lo) || !m.F || !m.u || !adj_off || !adj || !tri4 ||
+    if (!m.x || (s->prec != kF64 && !m.x_lo) || !m.F || !m.u || !adj_off || !adj || !adj4 || !node_cap || !tri4 ||
         !fconst || !capmod || (s->batch && !node_run))
         return fail(s, IBLBM_ERR_OOM, "membrane table allocation failed");
     if (s->batch) {
@@ -300,6 +302,16 @@ int ensure_mesh(iblbm_sim *s) {
         for (int f = 0; f < nf; ++f)
             for (int k = 0; k < 3; ++k) ent[fill[s->tri[3 * f + k]]++] = 4 * f + k;
     }
+    // the same entries with their face's nodes, so that one load gives the
+    // force kernel everything it needs before the positions
+    std::vector<int> ent4(12 * (size_t)nf), ncap(nn, 0);
+    for (size_t e = 0; e < ent.size(); ++e) {
+        const int f = ent[e] >> 2;
+        ent4[4 * e] = ent[e];
+        for (int k = 0; k < 3; ++k) ent4[4 * e + 1 + k] = s->tri[3 * f + k];
+    }
+    for (int c = 0; c < nc; ++c)
+        for (int n = s->caps[c].node0; n < s->caps[c].node0 + s->caps[c].n_nodes; ++n) ncap[n] = c;
     std::vector<int> t4(4 * (size_t)nf);
     std::vector<double> fc(12 * (size_t)nf, 0.0), cm(4 * (size_t)nc, 0.0);
     const bool split = s->prec != kF64;  // float builds: G as float hi + lo
@@ -347,6 +359,8 @@ int ensure_mesh(iblbm_sim *s) {
     };
     CK(cudaMemcpyAsync(adj_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(adj, ent.data(), sizeof(int) * ent.size(), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(adj4, ent4.data(), sizeof(int) * ent4.size(), cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(node_cap, ncap.data(), sizeof(int) * ncap.size(), cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(tri4, t4.data(), sizeof(int) * t4.size(), cudaMemcpyHostToDevice, s->stream));
     CK(up_real(fconst, fc));
     CK(up_real(capmod, cm));
@@ -354,6 +368,8 @@ int ensure_mesh(iblbm_sim *s) {
     CK(cudaMemsetAsync(m.u, 0, v4 * nn, s->stream));
     m.adj_off = (const int *)adj_off;
     m.adj = (const int *)adj;
+    m.adj4 = (const int *)adj4;
+    m.node_cap = (const int *)node_cap;
     m.tri = (const int *)tri4;
     m.fconst = fconst;
     m.capmod = capmod;

@@ -57,7 +57,7 @@ namespace iblbm {
 template <int N, typename T, int NPW>
 __global__ void __launch_bounds__(256)
     k_force_spread(int n_nodes, PosView<T> pos, const int *__restrict__ adj_off,
-                   const int *__restrict__ adj, const int4 *__restrict__ tri,
+                   const int4 *__restrict__ adj4, const int *__restrict__ node_cap,
                    const typename Vec4<T>::type *__restrict__ fconst,
                    const typename Vec4<T>::type *__restrict__ capmod,
                    typename Vec4<T>::type *__restrict__ nodeF,
@@ -78,16 +78,16 @@ __global__ void __launch_bounds__(256)
 
     T fx = T(0), fy = T(0), fz = T(0);
     const int e0 = valid ? adj_off[node] : 0, e1 = valid ? adj_off[node + 1] : 0;
+    const V4 m = capmod[valid ? node_cap[node] : 0];  // k_s/6, k_alpha/6 of the node's capsule
     for (int e = e0 + gl; e < e1; e += kFsGroup) {
-        const int ent = adj[e];
-        const int f = ent >> 2, corner = ent & 3;
-        const int4 t = tri[f];
+        // (face * 4 + corner, a, b, c): the positions can be loaded next
+        const int4 q = adj4[e];
+        const int f = q.x >> 2, corner = q.x & 3;
         const V4 c0 = fconst[3 * f];      // alpha, beta, gamma, kappa
         const V4 c1 = fconst[3 * f + 1];  // A0, G11, G12, G22 (hi parts in float builds)
         const V4 c2 = fconst[3 * f + 2];  // lo parts of G11, G12, G22 (float builds)
         T u[3], v[3], d[3];
-        pos.edge_gram(t.x, t.y, t.z, c1, c2, u, v, d);
-        const V4 m = capmod[t.w];  // k_s/6, k_alpha/6
+        pos.edge_gram(q.y, q.z, q.w, c1, c2, u, v, d);
         const T I1 = c0.x * d[0] - T(2) * c0.y * d[1] + c0.z * d[2];
         const T I2 = I1 + c0.w * (d[0] * d[2] - d[1] * d[1]);
         const T a2 = T(2) * c1.x;
@@ -562,7 +562,7 @@ static void force_spread_impl(const Lattice &L, const MeshDev &m, void *force, u
     const unsigned nb = (unsigned)((warps + wpb - 1) / wpb);
     auto kern = four ? k_force_spread<N, T, 4> : k_force_spread<N, T, 1>;
     launch_maybe_overlapped(kern, dim3(nb), dim3(32 * wpb), s, ov,
-        m.n_nodes, view<T>(m), m.adj_off, m.adj, (const int4 *)m.tri, (const V4 *)m.fconst,
+        m.n_nodes, view<T>(m), m.adj_off, (const int4 *)m.adj4, m.node_cap, (const V4 *)m.fconst,
         (const V4 *)m.capmod, (V4 *)m.F, (V4 *)force, flags, single_run(L), runs, node_run,
         status);
 }

@@ -86,6 +86,8 @@ struct MeshDev {
     void *u;      // node velocities, double4* / float4*
     const int *adj_off;   // [n_nodes + 1]
     const int *adj;       // [adj_off[n]] entries face*4 + corner
+    const int *adj4;      // int4 [adj_off[n]]: face*4 + corner, and the face's nodes a, b, c
+    const int *node_cap;  // [n_nodes] capsule of each node
     const int *tri;       // int4 [n_faces]: a, b, c, capsule
     const void *fconst;   // Vec4 [n_faces][3]: (alpha, beta, gamma, kappa),
                           // (A0, G11, G12, G22), (G11, G12, G22 low parts, 0)
