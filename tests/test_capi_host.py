@@ -151,3 +151,14 @@ def test_taylor_from_sums_against_oracle():
     assert got["D"] > 0.1
     with pytest.raises(B.IblbmError):
         B._check(B.iblbm_taylor_from_sums(None, None))
+
+
+def test_entry_points_reject_a_null_object():
+    """Calls on no object return IBLBM_ERR_ARG without touching a device."""
+    from paper_1004_2416_gb300 import iblbm as B
+
+    assert B.iblbm_set_launch_overlap(None, 1) == B.IBLBM_ERR_ARG
+    assert B.iblbm_set_interp_mode(None, 0) == B.IBLBM_ERR_ARG
+    assert B.iblbm_read_async(None, None, None) == B.IBLBM_ERR_ARG
+    assert B.iblbm_step(None, 1) == B.IBLBM_ERR_ARG
+    assert B.iblbm_sync(None) == B.IBLBM_ERR_ARG
