@@ -11,14 +11,16 @@
 // lanes first takes the faces around its node (one face each; a face's
 // contribution to this corner is recomputed by each of its three corner
 // groups, which keeps the assembly a deterministic group reduction with no
-// atomics and no per-face scratch), then the group's lanes take the node's
-// stencil rows (n cells along x each) and add the spread force with one
-// vector atomic per cell.  k_interp_advect gives a group of lanes to a node in
-// the same way: the lanes take the stencil rows, read the velocity of each
-// cell (formed once per cell of the flagged tiles by k_flag_velocity,
-// L2-resident, or formed from the populations on the spot) and a group
-// reduction gives the node velocity.  The delta function is separable: its n
-// x factors are formed once per lane, its y and z factors once per row.
+// atomics and no per-face scratch), then the group's lanes take pieces of the
+// node's stencil (whole rows of n cells along x with four nodes per warp;
+// one or two cells with one) and add the spread force with one vector atomic
+// per cell.  k_interp_advect gives a group of lanes to a node in the same
+// way: the lanes take stencil pieces, read the velocity of each cell (formed
+// once per cell of the flagged tiles by k_flag_velocity, L2-resident, or
+// formed from the populations on the spot) and a group reduction gives the
+// node velocity.  The delta function is separable: its x factors are formed
+// once per lane when the pieces are whole rows, its y and z factors once per
+// piece.
 //
 // Face energy gradient.  With the current edge vectors u = x_b - x_a,
 // v = x_c - x_a, their Gram entries g11 = u.u, g12 = u.v, g22 = v.v, the
