@@ -22,12 +22,13 @@
  * by orc_sim_get_velocity.
  *
  * Parity status: the coupled trajectory has no closed form.  It is pinned
- * through its parts (the pins of lattice.c, ibm.c, membrane.c) and by
- * physical checks: no force without deformation, mass conservation,
- * momentum balance of spreading, and the small-deformation theory of Sec. III
- * (D/G = 25/4, theta/pi = 1/4 - 15 G/8) within the deviations the paper
- * itself reports (Tab. convergence).  Coupled trajectory: parity unpinned
- * beyond these checks.
+ * through its parts (the pins of lattice.c, ibm.c, membrane.c), by physical
+ * checks (no force without deformation, mass conservation, momentum balance
+ * of spreading) and by the paper's printed numbers: run to kappa t = 120 on
+ * the smallest case of Tab. convergence (H = 35, 1 280 faces, 3-point
+ * stencil) it gives the table's deviations from the small-deformation theory
+ * of Sec. III (D/G = 25/4, theta/pi = 1/4 - 15 G/8) and a volume drift in the
+ * range of Sec. V.
  */
 #include <stdlib.h>
 #include <string.h>
