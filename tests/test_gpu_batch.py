@@ -97,3 +97,18 @@ def test_batch_errors():
     assert e.value.code == B.IBLBM_ERR_STATE
     with pytest.raises(B.IblbmError):
         B.Sim.batch([(8, 8, 8, 0.4, 0.0)])
+
+
+def test_batch_with_an_odd_row_length():
+    """One run with rows of odd length sends the whole FP32 batch through the
+    one-cell collide (every run with even rows takes two cells per thread)."""
+    cases = _runs()[:2]
+    c = W.Capsule((12.3, 9.8, 8.6), 3.0, 2, W.k_s_for(0.05, 3.0))
+    cases.append(W.Case("run25x20x18", (25, 20, 18), 1.0, 3, "fp32", W.u_wall_for(18), [c], 0))
+    b = _batch(cases, "fp32")
+    b.step(40)
+    for k, cs in enumerate(cases):
+        o = oracle_sim(cs)
+        o.step(40)
+        assert rel_inf(b.get_run_velocity(k), o.get_velocity()) < TOL["fp32"], k
+        assert np.abs(b.get_nodes(k) - o.get_nodes()).max() / cs.capsules[0].radius < TOL["fp32"], k
