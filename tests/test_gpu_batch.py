@@ -112,3 +112,17 @@ def test_batch_with_an_odd_row_length():
         o.step(40)
         assert rel_inf(b.get_run_velocity(k), o.get_velocity()) < TOL["fp32"], k
         assert np.abs(b.get_nodes(k) - o.get_nodes()).max() / cs.capsules[0].radius < TOL["fp32"], k
+
+
+def test_batch_with_launch_overlap():
+    """A batch with the step kernels launched to overlap their predecessor (the
+    automatic choice for large batches) against the runs' oracles."""
+    cases = _runs()
+    b = _batch(cases, "fp32")
+    b.set_launch_overlap(True)
+    b.step(40)
+    for k, c in enumerate(cases):
+        o = oracle_sim(c)
+        o.step(40)
+        assert rel_inf(b.get_run_velocity(k), o.get_velocity()) < TOL["fp32"], k
+        assert np.abs(b.get_nodes(k) - o.get_nodes()).max() / c.capsules[0].radius < TOL["fp32"], k
