@@ -25,10 +25,10 @@
  * through its parts (the pins of lattice.c, ibm.c, membrane.c), by physical
  * checks (no force without deformation, mass conservation, momentum balance
  * of spreading) and by the paper's printed numbers: run to kappa t = 120 on
- * the smallest case of Tab. convergence (H = 35, 1 280 faces, 3-point
- * stencil) it gives the table's deviations from the small-deformation theory
- * of Sec. III (D/G = 25/4, theta/pi = 1/4 - 15 G/8) and a volume drift in the
- * range of Sec. V.
+ * the smallest case of Tab. convergence (H = 35, 1 280 faces, 2-, 3- and
+ * 4-point stencils) it gives the table's deviations from the small-deformation
+ * theory of Sec. III (D/G = 25/4, theta/pi = 1/4 - 15 G/8) and volume drifts
+ * in the ranges of Sec. V.
  */
 #include <stdlib.h>
 #include <string.h>
