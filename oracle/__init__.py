@@ -6,7 +6,10 @@ CPU-baseline leg of ``bench.py`` may import this package.  The product path
 code with the CUDA library.
 
 The C library is built by :func:`build` with plain gcc (``-O2
--ffp-contract=off``, single-threaded).  Array conventions are those of
+-ffp-contract=off -fopenmp``).  It runs single-threaded unless
+:func:`set_threads` asks for more; the thread count changes no result
+(the whole-lattice loops write disjoint outputs, and the spreading, the
+membrane forces and every reduction stay serial in their fixed order).  Array conventions are those of
 ``oracle.h``: populations ``[19][nz][ny][nx]``, vector fields
 ``[3][nz][ny][nx]``, node arrays ``[n][3]``.
 """
@@ -38,7 +41,7 @@ def build(force: bool = False) -> str:
             return _LIB_PATH
     os.makedirs(_BUILD, exist_ok=True)
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
            "-o", tmp] + [os.path.join(_HERE, s) for s in _SOURCES] + ["-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
@@ -71,6 +74,8 @@ def _declare(L):
     L.orc_moments.argtypes = [_dp, _dp, _dp, _dp]
     L.orc_lbm_step.argtypes = [c_int, c_int, c_int, c_double, c_double, _dp, _dp, _dp]
     L.orc_lbm_step_eq.argtypes = [c_int, c_int, c_int, c_double, c_double, _dp, _dp, _dp, c_int]
+    L.orc_set_threads.argtypes = [c_int]
+    L.orc_get_threads.restype = c_int
     L.orc_sim_set_integrator.argtypes = [c_void_p, c_int]
     L.orc_sim_set_equilibrium.argtypes = [c_void_p, c_int]
     L.orc_init_couette.argtypes = [c_int, c_int, c_int, c_double, _dp]
@@ -103,6 +108,15 @@ def _declare(L):
     for name in ("get_f", "set_f", "get_nodes", "set_nodes", "get_force_field",
                  "get_node_forces", "get_node_velocities", "get_density", "get_velocity"):
         getattr(L, "orc_sim_" + name).argtypes = [c_void_p, _dp]
+
+
+def set_threads(n: int) -> None:
+    """Threads of the whole-lattice loops (1 = none); results do not change."""
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
 
 
 def _d(a: np.ndarray):

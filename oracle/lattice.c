@@ -17,6 +17,16 @@
 #include <stdlib.h>
 #include "oracle.h"
 
+/* Threads of the whole-lattice loops (orc_set_threads; 1 = no parallel
+ * region).  Each cell's update writes output elements that no other cell
+ * writes (streaming is a permutation; a bounced population lands in its own
+ * cell, in the direction no neighbour streams into), so results do not depend
+ * on the thread count. */
+static int g_threads = 1;
+
+void orc_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
+int orc_get_threads(void) { return g_threads; }
+
 /* Fig. d3q19: the TikZ coordinates of arrows 1..18 divided by two. */
 static const int C[19][3] = {
     {0, 0, 0},   {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
@@ -115,6 +125,8 @@ int orc_lbm_step_eq(int nx, int ny, int nz, double tau, double u_wall,
     const double cs2 = 1.0 / 3.0;
     int opp[19];
     for (int i = 0; i < 19; ++i) opp[i] = opposite(i);
+    const int nthreads = g_threads;
+#pragma omp parallel for collapse(2) schedule(static) num_threads(nthreads) if (nthreads > 1)
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {

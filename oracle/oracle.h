@@ -61,6 +61,12 @@ void orc_moments(const double fi[19], const double force[3], double *rho,
 int orc_lbm_step(int nx, int ny, int nz, double tau, double u_wall,
                  const double *f, const double *force, double *f_out);
 /* The same with the equilibrium of order 2 (Eq. equilibrium) or 1 (Sec. IV.A). */
+/* Threads of the whole-lattice loops (collide-and-stream and the velocity
+ * field); default 1.  Results are bit-identical for every count: each output
+ * element is written by one cell only, and the spreading, the membrane forces
+ * and every reduction stay serial in their fixed order. */
+void orc_set_threads(int n);
+int orc_get_threads(void);
 int orc_lbm_step_eq(int nx, int ny, int nz, double tau, double u_wall,
                     const double *f, const double *force, double *f_out, int order);
 

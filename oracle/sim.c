@@ -135,7 +135,10 @@ void orc_sim_init_couette(orc_sim *s) {
 
 /* Lattice velocity of Eq. (lbmmomenta1) with the last spread force. */
 static void velocity_field(const orc_sim *s, double *ufield, double *rho_out) {
-    for (size_t cell = 0; cell < s->N; ++cell) {
+    const int nthreads = orc_get_threads();
+    const long long N = (long long)s->N;
+#pragma omp parallel for schedule(static) num_threads(nthreads) if (nthreads > 1)
+    for (long long cell = 0; cell < N; ++cell) {
         double fi[19], fc[3], rho, u[3];
         for (int i = 0; i < 19; ++i) fi[i] = s->f[i * s->N + cell];
         for (int a = 0; a < 3; ++a) fc[a] = s->force[a * s->N + cell];
