@@ -312,13 +312,40 @@ def _ncu_traffic(workload: str, precision: str):
 
 # ---- CPU oracle ------------------------------------------------------------------------------
 
-def _oracle_run(case, budget_s: float, max_steps: int, a=None):
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def _host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def _oracle_run(case, budget_s: float, max_steps: int, a=None, threads: int = 1):
     """Times the FP64 oracle on the full workload: one untimed step, then as many
     timed steps as fit in the budget (at least one, at most max_steps), with the
-    method variants of the run's arguments."""
+    method variants of the run's arguments, its whole-lattice loops on
+    `threads` host threads (results do not depend on the count)."""
     import oracle as O
 
     O.build()
+    O.set_threads(threads)
     nx, ny, nz = case.shape
     o = O.Sim(nx, ny, nz, case.tau, case.delta, case.u_wall)
     for c in case.capsules:
@@ -335,7 +362,36 @@ def _oracle_run(case, budget_s: float, max_steps: int, a=None):
     o.step(n)
     dt = time.perf_counter() - t0
     o.close()
+    O.set_threads(1)
     return n, dt
+
+
+def _cpu_leg(case, a, budget_s, threads):
+    """(MLUPS, sample text) of the oracle on `threads` host threads."""
+    if isinstance(case, Batch):
+        cells_done, dt = 0, 0.0
+        for c in case.cases:
+            n, t = _oracle_run(c, budget_s / len(case.cases), a.steps, a, threads)
+            cells_done += c.ncell * n
+            dt += t
+        return cells_done / dt / 1e6, (f"every run of the batch stepped by the FP64 oracle for a bounded "
+                                       f"number of steps each, {dt:.1f} s in total")
+    n, dt = _oracle_run(case, budget_s, a.steps, a, threads)
+    return case.ncell * n / dt / 1e6, (f"{n} full FP64 oracle steps of the same workload after one untimed "
+                                       f"step, {dt:.1f} s")
+
+
+def _cpu_baseline(case, a):
+    """The oracle as it stands, timed on the host's cores: all of them (the
+    reported value) and one (beside it)."""
+    cores = _host_cores()
+    v_all, s_all = _cpu_leg(case, a, a.cpu_budget_s, cores)
+    v_one, s_one = _cpu_leg(case, a, a.cpu_budget_s, 1)
+    return {"value": round(v_all, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{s_all}; whole-lattice loops on {cores} OpenMP threads, spreading, membrane forces "
+                      f"and reductions serial",
+            "cpu_model": _cpu_model(), "nproc": os.cpu_count(),
+            "single_core": {"value": round(v_one, 4), "unit": "MLUPS", "cores": 1, "sample": s_one}}
 
 
 # ---- adjoint timing (config 5) ---------------------------------------------------------------------
@@ -428,9 +484,16 @@ def run_ours(a):
     sim.set_integrator(a.integrator)
     batch = isinstance(case, Batch)
     sim.set_taylor_recording(a.record_every, ring=(a.steps + a.warmup) // max(1, a.record_every) + 4096)
+    # the captured step graphs carry event nodes around each kernel group, so
+    # the kernel times below come from the timed steps themselves
+    sim.set_kernel_timing(True)
 
     sim.step(a.warmup)
+    # capture (not run) the graphs of the timed call, so the timed region
+    # holds graph launches only
+    sim.prepare_steps(a.steps)
     sim.sync()
+    sim.kernel_times()  # forget the warm-up's timings
     torch.cuda.synchronize()
     sampler = ClockSampler(_gpu_index(grp.local))
     time.sleep(0.3)
@@ -449,6 +512,7 @@ def run_ours(a):
     clocks = sampler.stop()
     ms = start.elapsed_time(end)
     sim.sync()  # raises on any device-side error of the timed region
+    live = sim.kernel_times()  # kernel groups of the timed steps (last replay of each graph)
     ms_max = grp.max(ms)
     cells = case.ncell
     value = aggregate_mlups(grp.ws, cells, a.steps, ms_max)
@@ -465,18 +529,29 @@ def run_ours(a):
                        "theta_ellipsoid_fit": fit["theta"], "face_area_dev_mean": q["dA_mean"],
                        "face_area_dev_std": q["dA_std"], "volume_drift": q["dV"]}
 
-    # per-kernel device times with CUDA events on the launching stream
+    # the Taylor record's device time, which runs on a side stream in the
+    # timed steps: profile mode (kernels launched one by one, the record on
+    # the main stream between events)
     prof = sim.profile_kernels(a.profile_steps)
     sim.sync()
     peak, peak_kind = _peaks()
     algo_bytes = BYTES_PER_CELL[case.precision] * cells
-    k_ms = prof["collide_stream"]
+    k_ms = live["collide_stream"]
     achieved = algo_bytes / (k_ms * 1e-3) / 1e9
     traffic = _ncu_traffic(a.workload, case.precision)
-    roofline = {"kernel": "k_collide_batch" if batch else "k_collide_stream", "bound": "hbm", "achieved": round(achieved, 1),
+    step_ms = ms_max / a.steps
+    roofline = {"kernel": sim.collide_kernel(), "bound": "hbm", "achieved": round(achieved, 1),
                 "peak": peak, "peak_kind": f"{peak_kind} copy bandwidth", "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "algorithmic_bytes_per_launch": algo_bytes, "kernel_ms": round(k_ms, 5)}
+                "algorithmic_bytes_per_launch": algo_bytes, "kernel_ms": round(k_ms, 5),
+                "kernel_ms_from": f"CUDA events in the timed step graphs, on a branch forked from the "
+                                  f"launching stream after the kernel before and after this one (the last "
+                                  f"replay of each graph: {live['steps']} steps)",
+                "kernel_ms_profile_mode": round(prof["collide_stream"], 5),
+                # the whole step against the same peak: algorithmic bytes of the
+                # collide (the only HBM-sized traffic of a step) over ms_per_step
+                "whole_step_frac": round(algo_bytes / (step_ms * 1e-3) / 1e9 / peak, 4),
+                "dram_frac": (round(traffic / (k_ms * 1e-3) / 1e9 / peak, 4) if traffic else None)}
 
     # end to end through the C ABI with pinned host buffers: the state is
     # uploaded, then every step is enqueued with an asynchronous read-back of
@@ -498,6 +573,12 @@ def run_ours(a):
         h = sim.handle
         k_e2e = a.steps
         sim.set_taylor_recording(0, 1)  # the read-back reduces the capsules of every step itself
+        sim.set_kernel_timing(False)  # a user's steps carry no timing events
+        # capture the one-step graphs of both buffer parities (untimed; the
+        # timed region uploads the state again)
+        for _ in range(2):
+            B.iblbm_step(h, 1)
+        sim.sync()
         p_nodes = [ctypes.c_void_p(b.ctypes.data) for b in out_nodes]
         p_sums = [ctypes.c_void_p(b.ctypes.data) for b in out_sums]
         grp.barrier()
@@ -530,20 +611,7 @@ def run_ours(a):
 
     cpu = None
     if grp.rank == 0 and grp.ws == 1 and not a.no_cpu_baseline:
-        if batch:
-            cells_done, dt = 0, 0.0
-            for c in case.cases:
-                n, t = _oracle_run(c, a.cpu_budget_s / len(case.cases), a.steps, a)
-                cells_done += c.ncell * n
-                dt += t
-            cpu = {"value": round(cells_done / dt / 1e6, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                   "sample": f"every run of the batch stepped by the FP64 oracle (single thread) for a "
-                             f"bounded number of steps each, {dt:.1f} s in total"}
-        else:
-            n, dt = _oracle_run(case, a.cpu_budget_s, a.steps, a)
-            cpu = {"value": round(cells * n / dt / 1e6, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                   "sample": f"{n} full oracle steps (FP64, single thread) of the same workload after one "
-                             f"untimed step, {dt:.1f} s"}
+        cpu = _cpu_baseline(case, a)
 
     adjoint = None
     if grp.rank == 0 and not a.no_adjoint and a.workload == "config2":
@@ -556,7 +624,14 @@ def run_ours(a):
         "dtype": "f32" if case.precision == "fp32" else ("f16-storage/f32" if case.precision == "fp16" else "f64"),
         "data": "synthetic", "config": _config(case, a),
         "membrane_nodes_per_s": round(nodes_per_s, 1),
-        "kernel_ms_per_step": {k: round(v, 5) for k, v in prof.items()},
+        "kernel_ms_per_step": {"force_spread": round(live["force_spread"], 5),
+                               "collide_stream": round(live["collide_stream"], 5),
+                               "interp_advect": round(live["interp_advect"], 5),
+                               "taylor_record_profile_mode": round(prof["taylor"], 5),
+                               "note": "first three: CUDA event nodes in the timed step graphs; their sum "
+                                       "is the main stream's step minus graph and join gaps; the Taylor "
+                                       "record runs beside them on a side stream (its time here from "
+                                       "profile mode, kernels launched one by one)"},
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": int(launches),
         "final_D": D_last,
@@ -575,16 +650,20 @@ def run_reference(a):
         return
     case = _workload(a)
     w = min(a.warmup, 1)
-    n, dt = _oracle_run(case, max(a.cpu_budget_s, 30.0), a.steps, a)
+    cores = _host_cores()
+    n, dt = _oracle_run(case, max(a.cpu_budget_s, 30.0), a.steps, a, cores)
     value = case.ncell * n / dt / 1e6
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MLUPS", "n_gpus": ws,
         "steps": n, "warmup": w, "ms_per_step": round(dt / n * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": _config(case, a),
-        "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": cores, "kind": "oracle",
                          "sample": f"{n} full FP64 oracle steps of the workload (of {a.steps} requested; "
-                                   f"each oracle step of 2.1 M cells takes seconds), after 1 untimed step"},
+                                   f"an oracle step of 2.1 M cells takes a fraction of a second on all "
+                                   f"cores), after 1 untimed step; whole-lattice loops on {cores} OpenMP "
+                                   f"threads, spreading, membrane forces and reductions serial",
+                         "cpu_model": _cpu_model(), "nproc": os.cpu_count()},
         "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

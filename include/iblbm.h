@@ -47,7 +47,7 @@ typedef enum {
     IBLBM_ERR_CUDA = -3,     /* a CUDA runtime call failed */
     IBLBM_ERR_UNSTABLE = -4, /* density left (0.5, 2) or became NaN */
     IBLBM_ERR_STENCIL = -5,  /* an IBM stencil cell lies beyond a wall */
-    IBLBM_ERR_TIMEOUT = -6,  /* a bounded device wait gave up */
+    /* -6 is not used: no kernel of the library waits on another */
     IBLBM_ERR_STATE = -7     /* call not valid in the current state */
 } iblbm_status;
 
@@ -192,11 +192,38 @@ int iblbm_init_fluid(iblbm_sim *sim, int mode);
  * lbmmomenta0/1), interpolation of the new lattice velocity at the old node
  * positions (Eq. velocityinterpolation) and Euler advection
  * (Eq. positionupdate).  The lattice velocity that is interpolated is
- * (sum_i c_i f_i(t+1) + f(t)/2) / rho(t+1).  Runs of 32 steps (or a
- * multiple of the recording period) replay captured CUDA graphs; a single
- * step without Taylor recording replays a captured one-step graph, the rest
- * are launched kernel by kernel.  Asynchronous. */
+ * (sum_i c_i f_i(t+1) + f(t)/2) / rho(t+1).  The steps replay captured CUDA
+ * graphs: n is split into a piece up to the next start of the Taylor
+ * recording period, whole graphs of 32 steps (or of a multiple of the
+ * recording period) and the remainder, each a graph captured on first use
+ * and cached (up to 16 per object, least recently used dropped).  Only the
+ * first step after choosing the Adams-Bashforth rule is launched kernel by
+ * kernel.  Asynchronous. */
 int iblbm_step(iblbm_sim *sim, int64_t n_steps);
+
+/* Captures and instantiates, without running anything, the graphs that
+ * iblbm_step(sim, n_steps) would replay from the current state, so that the
+ * following iblbm_step call only launches them (capture and instantiation
+ * cost host time, about 10 us per kernel).  Reduces and joins Taylor records
+ * still pending from earlier steps.  Asynchronous. */
+int iblbm_prepare_steps(iblbm_sim *sim, int64_t n_steps);
+
+/* Kernel timing inside the captured step graphs: with on = 1 every graph
+ * captured from now on carries CUDA event nodes around each step's kernel
+ * groups (membrane forces + spreading | collide-and-stream | cell velocities +
+ * interpolation + advection); the Taylor records stay on their side stream,
+ * so the steps run as they do without timing.  Drops the cached graphs.
+ * iblbm_get_kernel_times then returns the mean device time per step in
+ * milliseconds of the three groups, ms_out[3], over the steps of the last
+ * replay of every graph replayed since the previous call, and their number
+ * in *n_steps (may be NULL); zeros when none.  Synchronising.
+ * IBLBM_ERR_ARG for on outside {0, 1}. */
+int iblbm_set_kernel_timing(iblbm_sim *sim, int on);
+int iblbm_get_kernel_times(iblbm_sim *sim, double ms_out[3], int64_t *n_steps);
+
+/* Static name of the collide-and-stream kernel the steps of this object
+ * launch (template arguments included), "" for NULL. */
+const char *iblbm_collide_kernel(const iblbm_sim *sim);
 
 /* Sub-step 6 of the step list of Sec. II.C, kept on the device: after every
  * `every`-th step (counted from iblbm_init_fluid; every = 0 switches it off)
@@ -306,15 +333,22 @@ int iblbm_adjoint_taylor(iblbm_sim *sim, int capsule_id, int64_t n_steps,
  * iblbm_checkpoint_size gives the byte size of a checkpoint.
  * iblbm_checkpoint_save writes it to buf: device memory (on_device = 1) or
  * host memory (on_device = 0, pageable or pinned), owned by the caller, at
- * least that size; iblbm_checkpoint_restore reads it back.  Layout: a 256-byte
- * header (magic "IBLBMCK1", version, sizes), then the sections above, each at
- * a 256-byte aligned offset, in the library's storage formats.  Errors:
- * IBLBM_ERR_ARG for NULL pointers, a buffer on the wrong side, a bad header or
- * a configuration mismatch; IBLBM_ERR_CUDA for a failed copy.  Both calls
- * synchronise; a pending adjoint forward run is discarded by a restore. */
+ * least that size; iblbm_checkpoint_restore reads it back from a buffer of
+ * buf_bytes bytes.  Layout: a 256-byte header (magic "IBLBMCK1", version 2,
+ * sizes, and a 64-bit checksum of each section: the sum modulo 2^64 of the
+ * SplitMix64 finaliser applied to each little-endian 64-bit word plus its
+ * index times 0x9e3779b97f4a7c15, the last word zero-padded), then the
+ * sections above, each at a 256-byte aligned offset, in the library's storage
+ * formats.  Restore checks the header, the buffer length and every section's
+ * checksum before it writes anything.  Errors: IBLBM_ERR_ARG for NULL
+ * pointers, a buffer on the wrong side, a bad header, a configuration
+ * mismatch, a buffer shorter than the checkpoint or a checksum mismatch;
+ * IBLBM_ERR_CUDA for a failed copy.  Both calls synchronise; a pending
+ * adjoint forward run is discarded by a restore. */
 int iblbm_checkpoint_size(iblbm_sim *sim, size_t *bytes);
 int iblbm_checkpoint_save(iblbm_sim *sim, void *buf, int on_device);
-int iblbm_checkpoint_restore(iblbm_sim *sim, const void *buf, int on_device);
+int iblbm_checkpoint_restore(iblbm_sim *sim, const void *buf, size_t buf_bytes,
+                             int on_device);
 
 /* Waits for the stream and returns the first device error recorded since the
  * last call that returned it (then clears it). */
@@ -437,11 +471,12 @@ int iblbm_taylor_from_sums(const double sums[12], double out[16]);
  *
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory at the moment they need the reductions
- * behind the Taylor deformation: code running while a framework captures its
- * stream into a CUDA graph, code whose device memory is entirely handed to
- * another allocator, or tight loops where an allocation would synchronise the
- * device.  It computes what iblbm_get_taylor reduces on the device for one
- * closed membrane, on buffers the caller owns, and allocates nothing.
+ * behind the Taylor deformation: code whose device memory is entirely handed
+ * to another allocator (a framework's caching allocator or a fixed arena),
+ * plug-ins called back from such a framework, or tight loops where an
+ * allocation would synchronise the device.  It computes what iblbm_get_taylor
+ * reduces on the device for one closed membrane, on buffers the caller owns,
+ * and allocates nothing.
  *
  *   nodes   device pointer, [n_nodes][3] doubles (n_nodes >= 4)
  *   tri     device pointer, [n_tri][3] int32 node indices, counter-clockwise
@@ -465,8 +500,11 @@ int iblbm_taylor_from_sums(const double sums[12], double out[16]);
  * call overwrites every entry it reads.  Calls that overlap on the GPU (for
  * instance on two streams at once) race on the array and give wrong results.
  * The first call on each device, made with that device current, looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  Errors: IBLBM_ERR_ARG for null pointers or sizes out of
+ * array's device address (cudaGetSymbolAddress) and keeps it for the life of
+ * the process; make that first call before any stream capture.  A device
+ * reset (cudaDeviceReset) or the destruction of the device's primary context
+ * invalidates the kept address: do not call this entry point afterwards in the
+ * same process.  Errors: IBLBM_ERR_ARG for null pointers or sizes out of
  * range, IBLBM_ERR_CUDA if the lookup or a launch fails; the message is in
  * iblbm_last_error(NULL).  Calls no cudaMalloc, cudaFree or other allocating
  * routine. */

@@ -30,6 +30,7 @@ struct Capsule {
 constexpr int kTileShapes[6][2] = {{32, 8}, {16, 16}, {8, 32}, {64, 4}, {128, 2}, {256, 1}};
 
 constexpr int kGraphSteps = 32;  // steps per captured graph (even)
+constexpr int kMaxStepGraphs = 16;  // captured step sequences kept per object
 
 thread_local std::string g_create_error;
 
@@ -53,6 +54,12 @@ struct iblbm_sim {
     // with the next steps, and is joined before the half is written again.
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join[2] = {nullptr, nullptr};
+    // Kernel timing in captured steps: the timing events are recorded on a
+    // branch of the graph (this stream, forked from the main stream after each
+    // kernel group and joined at the end of the graph), so the main chain of
+    // kernels keeps its kernel-to-kernel edges.
+    cudaStream_t tstream = nullptr;
+    cudaEvent_t ev_tfork = nullptr;
     bool side_pending[2] = {false, false};
     void *snap_x = nullptr, *snap_lo = nullptr;  // [2 kTaylorBatch][n_nodes] in the layout of mesh.x / x_lo
     int rec_half = 0, rec_fill = 0;  // half being filled and its snapshots so far
@@ -90,6 +97,7 @@ struct iblbm_sim {
     std::vector<void *> plan_allocs;
 
     double *d_scratch = nullptr;
+    unsigned long long *d_cksum = nullptr;  // checkpoint section checksums
     double *d_readback = nullptr;  // iblbm_read_async's node conversion
     size_t readback_bytes = 0;
     size_t scratch_bytes = 0;
@@ -146,11 +154,22 @@ struct iblbm_sim {
     } adj;
     int init_mode = 0;
 
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    int64_t graph_kernels[2] = {0, 0};  // kernels in each captured graph
-    // one-step graphs (by buffer parity) for single steps without records
-    cudaGraphExec_t graph1[2] = {nullptr, nullptr};
-    int64_t graph1_kernels[2] = {0, 0};
+    // Captured step sequences: any run of steps from a phase of the recording
+    // period replays one of these graphs (at most kMaxStepGraphs, least
+    // recently used dropped first).
+    struct StepGraph {
+        int len = 0;            // steps in the graph
+        int cur = 0;            // buffer parity at its start (pop[cur] holds f(t))
+        int first_rec = -1;     // step of its first Taylor record (-1: none)
+        cudaGraphExec_t exec = nullptr;
+        int64_t kernels = 0;    // kernels per replay
+        uint64_t used = 0;      // replay stamp (least recently used is dropped)
+        std::vector<cudaEvent_t> ev;  // kernel timing: 4 per step (see kernel_timing)
+        bool timed = false;     // replayed since the last read of its events
+    };
+    std::vector<StepGraph> sgraphs;
+    uint64_t graph_clock = 0;
+    bool kernel_timing = false;  // graphs carry event nodes around the kernel groups
     int64_t launches = 0;               // kernels launched for time steps
     int graph_len = 0;
     int64_t steps = 0;
@@ -194,17 +213,16 @@ void dev_free(iblbm_sim *s, void *p) {
     else cudaFree(p);
 }
 
+void free_step_graph(iblbm_sim::StepGraph &g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (cudaEvent_t e : g.ev) cudaEventDestroy(e);
+    g.exec = nullptr;
+    g.ev.clear();
+}
+
 void drop_graphs(iblbm_sim *s) {
-    for (int k = 0; k < 2; ++k) {
-        if (s->graph[k]) {
-            cudaGraphExecDestroy(s->graph[k]);
-            s->graph[k] = nullptr;
-        }
-        if (s->graph1[k]) {
-            cudaGraphExecDestroy(s->graph1[k]);
-            s->graph1[k] = nullptr;
-        }
-    }
+    for (auto &g : s->sgraphs) free_step_graph(g);
+    s->sgraphs.clear();
 }
 
 int ensure_scratch(iblbm_sim *s, size_t bytes) {
@@ -383,23 +401,18 @@ int ensure_mesh(iblbm_sim *s) {
         launch_f64_to_nodes(s->prec, s->mesh, 0, nn, s->d_scratch, s->stream);
         CK(cudaGetLastError());
     }
-    // Taylor plan: taylor_faces_per_block faces per block
+    // Taylor plan: one block per capsule
     {
-        std::vector<int> bcap, bf0, bnf, cb0(nc + 1, 0);
+        std::vector<int> cf0(nc + 1, 0);
         std::vector<double> org(3 * (size_t)nc);
-        const int fpb = taylor_faces_per_block(nf);
+        int maxf = 1;
         for (int c = 0; c < nc; ++c) {
             const Capsule &cp = s->caps[c];
-            cb0[c] = (int)bcap.size();
-            for (int f = 0; f < cp.n_faces; f += fpb) {
-                bcap.push_back(c);
-                bf0.push_back(cp.face0 + f);
-                bnf.push_back(std::min(fpb, cp.n_faces - f));
-            }
+            cf0[c] = cp.face0;
+            maxf = std::max(maxf, cp.n_faces);
             for (int k = 0; k < 3; ++k) org[3 * c + k] = cp.origin[k];
         }
-        cb0[nc] = (int)bcap.size();
-        const int nb = (int)bcap.size();
+        cf0[nc] = nf;
         auto P = [&](size_t bytes) {
             void *p = dev_alloc(s, bytes);
             if (p) s->plan_allocs.push_back(p);
@@ -407,23 +420,16 @@ int ensure_mesh(iblbm_sim *s) {
         };
         TaylorPlan p{};
         p.n_caps = nc;
-        p.total_blocks = nb;
-        p.blk_cap = (const int *)P(sizeof(int) * nb);
-        p.blk_face0 = (const int *)P(sizeof(int) * nb);
-        p.blk_nface = (const int *)P(sizeof(int) * nb);
-        p.cap_blk0 = (const int *)P(sizeof(int) * (nc + 1));
+        p.cluster = taylor_cluster_size(maxf, taylor_max_cluster());
+        p.cap_face0 = (const int *)P(sizeof(int) * (nc + 1));
         p.origin = (const double *)P(sizeof(double) * 3 * nc);
-        p.partial = (double *)P(sizeof(double) * 16 * nb * kTaylorBatch);
         p.out = (double *)P(sizeof(double) * 12 * nc);
         p.ticket = (unsigned *)P(sizeof(unsigned));
-        if (!p.blk_cap || !p.blk_face0 || !p.blk_nface || !p.cap_blk0 || !p.origin || !p.partial ||
-            !p.out || !p.ticket)
+        if (!p.cap_face0 || !p.origin || !p.out || !p.ticket)
             return fail(s, IBLBM_ERR_OOM, "Taylor plan allocation failed");
         CK(cudaMemsetAsync(p.ticket, 0, sizeof(unsigned), s->stream));
-        CK(cudaMemcpyAsync((void *)p.blk_cap, bcap.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s->stream));
-        CK(cudaMemcpyAsync((void *)p.blk_face0, bf0.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s->stream));
-        CK(cudaMemcpyAsync((void *)p.blk_nface, bnf.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s->stream));
-        CK(cudaMemcpyAsync((void *)p.cap_blk0, cb0.data(), sizeof(int) * (nc + 1), cudaMemcpyHostToDevice, s->stream));
+        CK(cudaMemcpyAsync((void *)p.cap_face0, cf0.data(), sizeof(int) * (nc + 1), cudaMemcpyHostToDevice,
+                           s->stream));
         CK(cudaMemcpyAsync((void *)p.origin, org.data(), sizeof(double) * 3 * nc, cudaMemcpyHostToDevice, s->stream));
         s->plan = p;
     }
@@ -491,19 +497,31 @@ bool cell_velocity_first(const iblbm_sim *s) {
 // One time step (sub-step list of Sec. II.C) enqueued on the stream, with an
 // optional record of the capsule reductions (sub-step 6) at its end.  With
 // `ev` non-null, events are recorded around each kernel group:
-// ev[0] | spread | ev[1] | collide | ev[2] | cell velocities, interpolate | ev[3] | reductions | ev[4].
-void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) {
+// ev[0] | spread | ev[1] | collide | ev[2] | cell velocities, interpolate | ev[3] | reductions | ev[4],
+// the reductions then running on the main stream (profile mode).  With
+// `graph_ev` non-null instead (a step captured for kernel timing), the four
+// events ev[0..3] become event nodes of the graph and the record keeps its
+// place on the side stream.
+void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr, cudaEvent_t *graph_ev = nullptr) {
     const int c = s->cur, n = 1 - s->cur;
     auto mark = [s](const char *what) {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess && !s->launch_fail) s->launch_fail = what;
     };
+    auto gmark = [s, graph_ev](int k) {
+        if (!graph_ev) return;
+        cudaEventRecord(s->ev_tfork, s->stream);
+        cudaStreamWaitEvent(s->tstream, s->ev_tfork, 0);
+        cudaEventRecordWithFlags(graph_ev[k], s->tstream, cudaEventRecordExternal);
+    };
     const bool ov = launch_overlap(s);
     if (ev) cudaEventRecord(ev[0], s->stream);
+    gmark(0);
     launch_force_spread(s->prec, s->delta, s->L, s->mesh, s->force[n], s->flags[n], s->d_status,
                         s->batch ? s->d_runs : nullptr, s->d_node_run, s->stream, ov);
     mark("membrane force + spreading");
     if (ev) cudaEventRecord(ev[1], s->stream);
+    gmark(1);
     CollideArgs a;
     a.src = s->pop[c];
     a.dst = s->pop[n];
@@ -523,6 +541,7 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) 
     }
     mark("collide-stream");
     if (ev) cudaEventRecord(ev[2], s->stream);
+    gmark(2);
     const bool pre = cell_velocity_first(s);
     if (pre) {
         launch_flag_velocity(s->prec, s->L, s->pop[n], s->force[n], s->flags[n], s->uvel,
@@ -546,6 +565,7 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr) 
     s->ab2_ready = true;  // m.u now holds u_i(t+1)
     mark("interpolation + advection");
     if (ev) cudaEventRecord(ev[3], s->stream);
+    gmark(3);
     if (record) {
         if (ev) {
             launch_taylor(s->prec, s->mesh, s->plan, true, s->stream);
@@ -666,7 +686,6 @@ const char *iblbm_status_string(int status) {
         case IBLBM_ERR_CUDA: return "IBLBM_ERR_CUDA";
         case IBLBM_ERR_UNSTABLE: return "IBLBM_ERR_UNSTABLE";
         case IBLBM_ERR_STENCIL: return "IBLBM_ERR_STENCIL";
-        case IBLBM_ERR_TIMEOUT: return "IBLBM_ERR_TIMEOUT";
         case IBLBM_ERR_STATE: return "IBLBM_ERR_STATE";
         default: return "IBLBM_ERR_UNKNOWN";
     }
@@ -711,7 +730,9 @@ int setup_object(iblbm_sim *s, void *stream, const iblbm_allocator *alloc, long 
     if (cudaStreamCreateWithPriority(&s->side, cudaStreamNonBlocking, greatest_prio) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->ev_join[0], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&s->ev_join[1], cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&s->ev_join[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->tstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_tfork, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         g_create_error = "stream or event creation failed";
         return IBLBM_ERR_CUDA;
@@ -933,6 +954,7 @@ int iblbm_destroy(iblbm_sim *s) {
     dev_free(s, s->uvel);
     dev_free(s, s->d_readback);
     dev_free(s, s->d_scratch);
+    dev_free(s, s->d_cksum);
     dev_free(s, s->d_runs);
     dev_free(s, s->d_items);
     adj_free(s);
@@ -943,6 +965,11 @@ int iblbm_destroy(iblbm_sim *s) {
         cudaStreamSynchronize(s->side);
         cudaStreamDestroy(s->side);
     }
+    if (s->tstream) {
+        cudaStreamSynchronize(s->tstream);
+        cudaStreamDestroy(s->tstream);
+    }
+    if (s->ev_tfork) cudaEventDestroy(s->ev_tfork);
     if (s->ev_fork) cudaEventDestroy(s->ev_fork);
     for (cudaEvent_t e : s->ev_join)
         if (e) cudaEventDestroy(e);
@@ -1088,8 +1115,160 @@ int iblbm_init_fluid(iblbm_sim *s, int mode) {
     return IBLBM_OK;
 }
 
-int iblbm_step(iblbm_sim *s, int64_t n_steps) {
-    if (!s) return IBLBM_ERR_ARG;
+}  // extern "C"
+
+namespace {
+
+// Step (0-based, within a captured sequence) of the first Taylor record of a
+// sequence that starts `phase` steps into the recording period, or -1 when
+// none of its `len` steps records.
+int first_record(const iblbm_sim *s, int phase, int len) {
+    if (s->rec_every <= 0 || !s->d_ring) return -1;
+    const int k0 = (s->rec_every - 1 - phase % s->rec_every) % s->rec_every;
+    return k0 < len ? k0 : -1;
+}
+
+// The captured sequence of `len` steps from buffer parity `cur` whose first
+// record is at step first_rec, captured now if not cached.  Capturing runs
+// nothing: the host state it touches (buffer parity, the Adams-Bashforth
+// history flag, the snapshot ring) is put back, and only records still
+// pending from earlier steps are reduced and joined first.
+int step_graph(iblbm_sim *s, int len, int cur, int first_rec, iblbm_sim::StepGraph **out) {
+    for (auto &g : s->sgraphs)
+        if (g.len == len && g.cur == cur && g.first_rec == first_rec) {
+            *out = &g;
+            return IBLBM_OK;
+        }
+    if ((int)s->sgraphs.size() >= kMaxStepGraphs) {
+        auto lru = std::min_element(s->sgraphs.begin(), s->sgraphs.end(),
+                                    [](const iblbm_sim::StepGraph &a, const iblbm_sim::StepGraph &b) {
+                                        return a.used < b.used;
+                                    });
+        CK(cudaStreamSynchronize(s->stream));  // its last replay may still run
+        free_step_graph(*lru);
+        s->sgraphs.erase(lru);
+    }
+    iblbm_sim::StepGraph g;
+    g.len = len;
+    g.cur = cur;
+    g.first_rec = first_rec;
+    if (s->kernel_timing) {
+        g.ev.assign(4 * (size_t)len, nullptr);
+        for (auto &e : g.ev) {
+            cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) {
+                free_step_graph(g);
+                return cuda_fail(s, r, "timing event creation");
+            }
+        }
+    }
+    const int cur0 = s->cur;
+    const bool ab2_0 = s->ab2_ready;
+    join_side(s);  // the sequence starts with no record pending, at the first half
+    s->rec_half = 0;
+    s->rec_fill = 0;
+    const int64_t launches0 = s->launches;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        free_step_graph(g);
+        return cuda_fail(s, e, "graph capture");
+    }
+    s->cur = cur;
+    s->ab2_ready = true;  // only captured with the history in place (or Euler)
+    for (int k = 0; k < len; ++k) {
+        const bool rec = first_rec >= 0 && k >= first_rec && (k - first_rec) % s->rec_every == 0;
+        enqueue_step(s, rec, nullptr, g.ev.empty() ? nullptr : g.ev.data() + 4 * (size_t)k);
+    }
+    join_side(s);  // the sequence joins its own records before it ends
+    if (!g.ev.empty()) {  // and its timing branch
+        cudaEventRecord(s->ev_tfork, s->tstream);
+        cudaStreamWaitEvent(s->stream, s->ev_tfork, 0);
+    }
+    e = cudaStreamEndCapture(s->stream, &graph);
+    s->cur = cur0;
+    s->ab2_ready = ab2_0;
+    s->rec_half = 0;
+    s->rec_fill = 0;
+    g.kernels = s->launches - launches0;  // counted when replayed
+    s->launches = launches0;
+    if (e == cudaSuccess && s->launch_fail) e = cudaErrorLaunchFailure;
+    if (e == cudaSuccess)
+        // kernel nodes keep the priority of the stream they were captured on
+        e = cudaGraphInstantiate(&g.exec, graph, cudaGraphInstantiateFlagUseNodePriority);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        g.exec = nullptr;
+        free_step_graph(g);
+        if (s->launch_fail)
+            return fail(s, IBLBM_ERR_CUDA, std::string("kernel launch failed in capture: ") + s->launch_fail);
+        return cuda_fail(s, e, "graph capture");
+    }
+    s->sgraphs.push_back(std::move(g));
+    *out = &s->sgraphs.back();
+    return IBLBM_OK;
+}
+
+// Splits n steps from the current state into the pieces iblbm_step takes:
+// a direct step while the Adams-Bashforth history is missing, then captured
+// sequences -- up to the next start of the recording period, whole graphs of
+// graph_len_for() steps, and the remainder.  With `run` false the sequences
+// are only captured (iblbm_prepare_steps).
+int run_steps(iblbm_sim *s, int64_t n_steps, bool run) {
+    const int G = graph_len_for(s);
+    if (G != s->graph_len) {
+        drop_graphs(s);
+        s->graph_len = G;
+    }
+    const int period = s->rec_every > 0 ? s->rec_every : 1;
+    int cur = s->cur;
+    int64_t steps = s->steps;
+    bool ab2 = s->ab2_ready;
+    int64_t left = n_steps;
+    while (left > 0) {
+        if (s->integrator == 1 && !ab2) {
+            // the first Adams-Bashforth step takes Euler's rule, launched directly
+            if (run) {
+                const bool rec = record_after(s, s->steps);
+                enqueue_step(s, rec);
+                if (rec) s->rec_steps.push_back(s->steps + 1);
+                s->steps++;
+                if (s->launch_fail) break;
+            }
+            cur = 1 - cur;
+            steps++;
+            ab2 = true;
+            left--;
+            continue;
+        }
+        const int phase = (int)(steps % period);
+        const int len = (int)std::min<int64_t>(left, phase ? period - phase : G);
+        iblbm_sim::StepGraph *g = nullptr;
+        int rc = step_graph(s, len, cur, first_record(s, phase, len), &g);
+        if (rc) return rc;
+        if (run) {
+            join_side(s);
+            CK(cudaGraphLaunch(g->exec, s->stream));
+            g->used = ++s->graph_clock;
+            g->timed = !g->ev.empty();
+            s->launches += g->kernels;
+            for (int k = 0; k < len; ++k)
+                if (record_after(s, s->steps + k)) s->rec_steps.push_back(s->steps + k + 1);
+            s->steps += len;
+            s->cur = len % 2 ? 1 - s->cur : s->cur;
+            s->ab2_ready = true;
+        }
+        cur = len % 2 ? 1 - cur : cur;
+        steps += len;
+        left -= len;
+    }
+    if (s->launch_fail)
+        return fail(s, IBLBM_ERR_CUDA, std::string("kernel launch failed: ") + s->launch_fail);
+    CK(cudaGetLastError());
+    return IBLBM_OK;
+}
+
+int step_prologue(iblbm_sim *s, int64_t n_steps) {
     if (n_steps < 0) return fail(s, IBLBM_ERR_ARG, "negative step count");
     CK(cudaSetDevice(s->device));
     cudaGetLastError();  // an error left by some earlier, unrelated call is not ours
@@ -1098,93 +1277,62 @@ int iblbm_step(iblbm_sim *s, int64_t n_steps) {
     rc = ensure_ring(s);
     if (rc) return rc;
     s->launch_fail = nullptr;
-    const int G = graph_len_for(s);
-    if (G != s->graph_len) {
-        drop_graphs(s);
-        s->graph_len = G;
-    }
-    const int period = s->rec_every > 0 ? s->rec_every : 1;
-    int64_t left = n_steps;
-    while (left > 0) {
-        // a graph is captured with the Adams-Bashforth history in place
-        if (left >= G && s->steps % period == 0 && (s->integrator == 0 || s->ab2_ready)) {
-            cudaGraphExec_t &g = s->graph[s->cur];
-            if (!g) {
-                cudaGraph_t graph = nullptr;
-                const int cur0 = s->cur;
-                // An outstanding record of a direct step is joined before the
-                // capture; the graph joins its own records before it ends, so
-                // no event recorded inside the capture is waited on outside it.
-                join_side(s);
-                s->rec_half = 0;  // a graph starts with nothing pending, at the first half
-                s->rec_fill = 0;
-                const int64_t launches0 = s->launches;
-                CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-                for (int k = 0; k < G; ++k) enqueue_step(s, record_after(s, k));
-                join_side(s);
-                cudaError_t e = cudaStreamEndCapture(s->stream, &graph);
-                s->cur = cur0;
-                s->graph_kernels[cur0] = s->launches - launches0;  // counted when replayed
-                s->launches = launches0;
-                if (e != cudaSuccess) return cuda_fail(s, e, "graph capture");
-                // kernel nodes keep the priority of the stream they were captured on
-                e = cudaGraphInstantiate(&g, graph, cudaGraphInstantiateFlagUseNodePriority);
-                cudaGraphDestroy(graph);
-                if (e != cudaSuccess) {
-                    g = nullptr;
-                    return cuda_fail(s, e, "graph instantiation");
-                }
-            }
-            join_side(s);
-            CK(cudaGraphLaunch(g, s->stream));
-            s->launches += s->graph_kernels[s->cur];
-            for (int k = 0; k < G; ++k)
-                if (record_after(s, k)) s->rec_steps.push_back(s->steps + k + 1);
-            left -= G;  // G is even: buffer parity unchanged
-            s->steps += G;
-        } else if (s->rec_every <= 0 && (s->integrator == 0 || s->ab2_ready)) {
-            // a single step without records: a cached one-step graph (one
-            // launch call instead of one per kernel)
-            cudaGraphExec_t &g = s->graph1[s->cur];
-            if (!g) {
-                cudaGraph_t graph = nullptr;
-                const int cur0 = s->cur;
-                join_side(s);
-                const int64_t launches0 = s->launches;
-                CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-                enqueue_step(s, false);
-                cudaError_t e = cudaStreamEndCapture(s->stream, &graph);
-                s->cur = cur0;
-                s->graph1_kernels[cur0] = s->launches - launches0;
-                s->launches = launches0;
-                if (e != cudaSuccess) return cuda_fail(s, e, "graph capture");
-                e = cudaGraphInstantiate(&g, graph, cudaGraphInstantiateFlagUseNodePriority);
-                cudaGraphDestroy(graph);
-                if (e != cudaSuccess) {
-                    g = nullptr;
-                    return cuda_fail(s, e, "graph instantiation");
-                }
-            }
-            join_side(s);
-            CK(cudaGraphLaunch(g, s->stream));
-            s->launches += s->graph1_kernels[s->cur];
-            s->cur = 1 - s->cur;
-            s->ab2_ready = true;
-            s->steps++;
-            left--;
-        } else {
-            const bool rec = record_after(s, s->steps);
-            enqueue_step(s, rec);
-            if (rec) s->rec_steps.push_back(s->steps + 1);
-            s->steps++;
-            left--;
-        }
-        if (s->launch_fail) break;
-    }
-    if (s->launch_fail)
-        return fail(s, IBLBM_ERR_CUDA, std::string("kernel launch failed: ") + s->launch_fail);
-    CK(cudaGetLastError());
     return IBLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int iblbm_step(iblbm_sim *s, int64_t n_steps) {
+    if (!s) return IBLBM_ERR_ARG;
+    int rc = step_prologue(s, n_steps);
+    return rc ? rc : run_steps(s, n_steps, true);
+}
+
+int iblbm_prepare_steps(iblbm_sim *s, int64_t n_steps) {
+    if (!s) return IBLBM_ERR_ARG;
+    int rc = step_prologue(s, n_steps);
+    return rc ? rc : run_steps(s, n_steps, false);
+}
+
+int iblbm_set_kernel_timing(iblbm_sim *s, int on) {
+    if (!s) return IBLBM_ERR_ARG;
+    if (on != 0 && on != 1) return fail(s, IBLBM_ERR_ARG, "on must be 0 or 1");
+    CK(cudaSetDevice(s->device));
+    join_side(s);
+    CK(cudaStreamSynchronize(s->stream));
+    drop_graphs(s);
+    s->kernel_timing = on == 1;
+    return IBLBM_OK;
+}
+
+int iblbm_get_kernel_times(iblbm_sim *s, double ms_out[3], int64_t *n_steps) {
+    if (!s || !ms_out) return IBLBM_ERR_ARG;
+    int rc = sync_status(s);
+    if (rc) return rc;
+    double acc[3] = {0, 0, 0};
+    int64_t n = 0;
+    for (auto &g : s->sgraphs) {
+        if (!g.timed) continue;
+        for (int k = 0; k < g.len; ++k)
+            for (int j = 0; j < 3; ++j) {
+                float ms = 0.0f;
+                CK(cudaEventElapsedTime(&ms, g.ev[4 * (size_t)k + j], g.ev[4 * (size_t)k + j + 1]));
+                acc[j] += ms;
+            }
+        n += g.len;
+        g.timed = false;
+    }
+    for (int j = 0; j < 3; ++j) ms_out[j] = n ? acc[j] / n : 0.0;
+    if (n_steps) *n_steps = n;
+    return IBLBM_OK;
+}
+
+const char *iblbm_collide_kernel(const iblbm_sim *s) {
+    if (!s) return "";
+    if (s->batch) return collide_batch_kernel_name(s->prec, s->batch_pairs);
+    return collide_kernel_name(s->prec, s->L);
 }
 
 }  // extern "C"
@@ -2080,12 +2228,50 @@ struct CkptHeader {
     int32_t n_nodes, n_faces, n_caps, flags;  // flags bit 0: Adams-Bashforth history present
     int64_t steps;
     uint64_t pop_bytes, vec_bytes, flag_bytes, x_bytes, xlo_bytes, node_bytes;
+    uint64_t sum[7];  // checksum of each section (see launch_checksum)
 };
 static_assert(sizeof(CkptHeader) <= 256, "checkpoint header must fit its 256-byte slot");
 
 constexpr char kCkptMagic[8] = {'I', 'B', 'L', 'B', 'M', 'C', 'K', '1'};
 
 size_t ck_align(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr int32_t kCkptVersion = 2;
+
+// Host twin of launch_checksum (lbm.cu): the same sum modulo 2^64 of the
+// SplitMix64 finaliser of each 64-bit word plus its index times
+// 0x9e3779b97f4a7c15, the last word zero-padded.  The words are read
+// little-endian byte by byte (both hosts are little-endian, as is the GPU).
+uint64_t ck_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+uint64_t checksum_host(const unsigned char *p, size_t n) {
+    uint64_t acc = 0;
+    const size_t words = (n + 7) / 8;
+    for (size_t k = 0; k < words; ++k) {
+        uint64_t w = 0;
+        for (size_t b = 8 * k; b < n && b < 8 * k + 8; ++b) w |= (uint64_t)p[b] << (8 * (b - 8 * k));
+        acc += ck_mix(w + (uint64_t)k * 0x9e3779b97f4a7c15ull);
+    }
+    return acc;
+}
+
+// Checksums of n device ranges, into sums[] (host), on the object's stream.
+int checksums_device(iblbm_sim *s, const void *const *p, const size_t *n, int count, uint64_t *sums) {
+    if (!s->d_cksum) {
+        s->d_cksum = (unsigned long long *)dev_alloc(s, sizeof(unsigned long long) * 8);
+        if (!s->d_cksum) return fail(s, IBLBM_ERR_OOM, "checksum buffer allocation failed");
+    }
+    CK(cudaMemsetAsync(s->d_cksum, 0, sizeof(unsigned long long) * 8, s->stream));
+    for (int k = 0; k < count; ++k)
+        if (n[k]) launch_checksum(p[k], n[k], s->d_cksum + k, s->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(sums, s->d_cksum, sizeof(uint64_t) * count, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return IBLBM_OK;
+}
 
 // Section offsets: header, populations, force density, flags, x, x_lo, F, u.
 struct CkptLayout {
@@ -2111,7 +2297,7 @@ CkptHeader ckpt_header(const iblbm_sim *s) {
     CkptHeader h;
     std::memset(&h, 0, sizeof(h));
     std::memcpy(h.magic, kCkptMagic, 8);
-    h.version = 1;
+    h.version = kCkptVersion;
     h.precision = s->prec;
     h.delta = s->delta;
     h.n_runs = s->batch ? (int32_t)s->runs.size() : 1;
@@ -2177,6 +2363,9 @@ int iblbm_checkpoint_save(iblbm_sim *s, void *buf, int on_device) {
                           s->mesh.F, s->mesh.u};
     const size_t sz[7] = {h.pop_bytes, h.vec_bytes, h.flag_bytes, h.x_bytes, h.xlo_bytes, h.node_bytes,
                           h.node_bytes};
+    CkptHeader hs = h;
+    rc = checksums_device(s, src, sz, 7, hs.sum);
+    if (rc) return rc;
     // padding bytes (after the header and each section) are written as zeros
     auto zero = [&](size_t off, size_t n) -> cudaError_t {
         if (!n) return cudaSuccess;
@@ -2184,8 +2373,8 @@ int iblbm_checkpoint_save(iblbm_sim *s, void *buf, int on_device) {
         std::memset(b + off, 0, n);
         return cudaSuccess;
     };
-    CK(cudaMemcpyAsync(b, &h, sizeof(h), cudaMemcpyDefault, s->stream));
-    CK(zero(sizeof(h), 256 - sizeof(h)));
+    CK(cudaMemcpyAsync(b, &hs, sizeof(hs), cudaMemcpyDefault, s->stream));
+    CK(zero(sizeof(hs), 256 - sizeof(hs)));
     for (int k = 0; k < 7; ++k) {
         if (sz[k]) CK(cudaMemcpyAsync(b + L.off[k + 1], src[k], sz[k], cudaMemcpyDefault, s->stream));
         const size_t end = k < 6 ? L.off[k + 2] : L.total;
@@ -2195,7 +2384,7 @@ int iblbm_checkpoint_save(iblbm_sim *s, void *buf, int on_device) {
     return IBLBM_OK;
 }
 
-int iblbm_checkpoint_restore(iblbm_sim *s, const void *buf, int on_device) {
+int iblbm_checkpoint_restore(iblbm_sim *s, const void *buf, size_t buf_bytes, int on_device) {
     if (!s || !buf) return IBLBM_ERR_ARG;
     int rc = sync_status(s);
     if (rc) return rc;
@@ -2203,10 +2392,11 @@ int iblbm_checkpoint_restore(iblbm_sim *s, const void *buf, int on_device) {
     if (rc) return rc;
     rc = check_side(s, buf, on_device);
     if (rc) return rc;
+    if (buf_bytes < 256) return fail(s, IBLBM_ERR_ARG, "checkpoint buffer shorter than its header");
     CkptHeader h;
     CK(cudaMemcpy(&h, buf, sizeof(h), cudaMemcpyDefault));
     const CkptHeader mine = ckpt_header(s);
-    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1)
+    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != kCkptVersion)
         return fail(s, IBLBM_ERR_ARG, "not a checkpoint of this library (magic or version)");
     if (h.precision != mine.precision || h.delta != mine.delta || h.n_runs != mine.n_runs || h.nx != mine.nx ||
         h.ny != mine.ny || h.nz != mine.nz || h.n_nodes != mine.n_nodes || h.n_faces != mine.n_faces ||
@@ -2217,11 +2407,30 @@ int iblbm_checkpoint_restore(iblbm_sim *s, const void *buf, int on_device) {
     if (h.steps < 0 || (h.init_mode != 0 && h.init_mode != 1))
         return fail(s, IBLBM_ERR_ARG, "corrupt checkpoint header");
     const CkptLayout L = ckpt_layout(h);
+    if (buf_bytes < L.total)
+        return fail(s, IBLBM_ERR_ARG, "checkpoint buffer of " + std::to_string(buf_bytes) + " bytes, " +
+                                          std::to_string(L.total) + " needed");
     const char *b = (const char *)buf;
     void *dst[7] = {s->pop[s->cur], s->force[s->cur], s->flags[s->cur], s->mesh.x, s->mesh.x_lo,
                     s->mesh.F, s->mesh.u};
     const size_t sz[7] = {h.pop_bytes, h.vec_bytes, h.flag_bytes, h.x_bytes, h.xlo_bytes, h.node_bytes,
                           h.node_bytes};
+    // every section is checked before anything is written
+    uint64_t sums[7];
+    if (on_device) {
+        const void *p[7];
+        for (int k = 0; k < 7; ++k) p[k] = b + L.off[k + 1];
+        rc = checksums_device(s, p, sz, 7, sums);
+        if (rc) return rc;
+    } else {
+        for (int k = 0; k < 7; ++k) sums[k] = checksum_host((const unsigned char *)b + L.off[k + 1], sz[k]);
+    }
+    static const char *const kSection[7] = {"populations", "force density", "force flags", "node positions",
+                                            "node position low parts", "node forces", "node velocities"};
+    for (int k = 0; k < 7; ++k)
+        if (sums[k] != h.sum[k])
+            return fail(s, IBLBM_ERR_ARG, std::string("checkpoint checksum mismatch in the ") + kSection[k] +
+                                              " section (corrupt or truncated data)");
     for (int k = 0; k < 7; ++k)
         if (sz[k]) CK(cudaMemcpyAsync(dst[k], b + L.off[k + 1], sz[k], cudaMemcpyDefault, s->stream));
     // the other force buffer is all zero between steps

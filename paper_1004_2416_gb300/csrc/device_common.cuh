@@ -13,6 +13,7 @@ namespace iblbm {
 enum : int {
     kStatusUnstable = 1,  // density out of (0.5, 2) or NaN
     kStatusStencil = 2,   // an IBM stencil cell beyond a wall
+    kStatusTimeout = 4,   // a bounded wait for staged data gave up
 };
 
 // D3Q19 velocity set numbered as in Fig. d3q19 of the paper (the arrow i
@@ -172,5 +173,52 @@ __device__ __forceinline__ void set_status(int *status, int bit) { atomicOr(stat
 // older ones.  Without the launch attribute both are no-ops.
 __device__ __forceinline__ void prior_grid_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// ---- staging of tiles in shared memory by the bulk-copy (TMA) engine ----------------
+// An mbarrier in shared memory counts the bytes of the bulk copies issued
+// against it; a thread that waits on its phase parity sees the copied data.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// Orders this thread's generic-proxy shared-memory accesses (an mbarrier
+// init, reads of a buffer about to be refilled) before later bulk copies.
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_bytes(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+// Bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// from global to this block's shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_copy_to_smem(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+// Waits for phase `parity` of `bar`, giving up after limit_ns nanoseconds
+// (0: one try only).  Returns whether the phase completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, unsigned long long limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (limit_ns == 0) return false;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > limit_ns) return false;
+    return true;
+}
 
 }  // namespace iblbm

@@ -134,6 +134,13 @@ void launch_collide_stream(int prec, const Lattice &L, const CollideArgs &a, cud
 void launch_collide_batch(int prec, const BatchArgs &b, const CollideArgs &a, cudaStream_t s,
                           bool overlap = false);
 int collide_batch_blocks_per_sm(int prec, bool pairs);
+// Checksum of a device byte range (added into *out, which the caller zeroes):
+// the sum modulo 2^64 of the SplitMix64 finaliser of each 64-bit word plus
+// its index times 0x9e3779b97f4a7c15 (last word zero-padded).
+void launch_checksum(const void *p, size_t n_bytes, unsigned long long *out, cudaStream_t s);
+// Name of the collide-and-stream kernel a plain step launches (static string).
+const char *collide_kernel_name(int prec, const Lattice &L);
+const char *collide_batch_kernel_name(int prec, bool pairs);
 // mode 0: rest; mode 1: linear Couette equilibrium
 void launch_init_fluid(int prec, const Lattice &L, void *pop, int mode, double u_wall, cudaStream_t s);
 // rho [ncell] and u [3][ncell] in double from populations + half the force
@@ -205,29 +212,26 @@ void launch_adjoint_init_uw(int prec, const Lattice &L, const void *lam, double 
 // Per-capsule FP64 sums: out[c*12 + k] = {V, A, cx, cy, cz, Ixx, Iyy, Izz, Ixy, Ixz, Iyz, 0}
 struct TaylorPlan {
     int n_caps;
-    int total_blocks;
-    const int *blk_cap;     // [total_blocks] capsule of each block
-    const int *blk_face0;   // [total_blocks] first face of each block
-    const int *blk_nface;   // [total_blocks]
-    const int *cap_blk0;    // [n_caps + 1] first block of each capsule
+    int cluster;            // blocks per capsule (one thread-block cluster), 1..16
+    const int *cap_face0;   // [n_caps + 1] first face of each capsule
     const double *origin;   // [n_caps][3]
-    double *partial;        // scratch [kTaylorBatch][total_blocks][16]
     double *out;            // [n_caps][12] results of an immediate reduction
     double *ring;           // [ring_len][n_caps][12] recorded results (or null)
     int ring_len;
     unsigned long long *ring_count;  // records written so far
-    unsigned *ticket;       // blocks of the last stage done (returns to 0)
+    unsigned *ticket;       // blocks of a recording launch done (returns to 0)
 };
-// A block of 128 threads takes between 128 and kTaylorMaxFacesPerBlock faces:
-// as few as keep about two blocks per SM busy, so small meshes get short
-// chains and large ones fewer FP64 block reductions.
-constexpr int kTaylorThreads = 128;
-constexpr int kTaylorMaxFacesPerBlock = 1024;
-inline int taylor_faces_per_block(long long total_faces) {
-    long long f = kTaylorThreads;
-    while (f < kTaylorMaxFacesPerBlock && total_faces / f > 2 * 152) f *= 2;
-    return (int)f;
+// Blocks of kTaylorClusterThreads threads per capsule: about four faces per
+// thread, at most max_cluster (taylor_max_cluster()).
+constexpr int kTaylorClusterThreads = 128;
+inline int taylor_cluster_size(int max_faces_per_capsule, int max_cluster) {
+    int c = (max_faces_per_capsule + 4 * kTaylorClusterThreads - 1) / (4 * kTaylorClusterThreads);
+    return c < 1 ? 1 : (c > max_cluster ? max_cluster : c);
 }
+// Largest cluster the reduction kernel may use on this GPU (16 where allowed, else 8).
+int taylor_max_cluster();
+// Threads per block of the allocation-free reduction (one face per thread).
+constexpr int kTaylorThreads = 128;
 // record = false: results to p.out; record = true: to the next ring slot.
 void launch_taylor(int prec, const MeshDev &m, const TaylorPlan &p, bool record, cudaStream_t s);
 // The same for n_snap (<= kTaylorBatch) position snapshots in one launch:

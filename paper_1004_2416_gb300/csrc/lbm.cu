@@ -10,6 +10,7 @@
 // cell; only tiles flagged by the spreading kernel hold non-zero force, so
 // the collide kernel reads it only there and zeroes the previous step's
 // tiles as it passes.
+#include <algorithm>
 #include <type_traits>
 
 #include "device_common.cuh"
@@ -304,62 +305,21 @@ __host__ __device__ constexpr int rows_per_block() {
     return LR <= 32 ? 8 * (32 / LR) : 8 / (LR / 32);
 }
 
-// WM: also write the moments of f(t), float4 (j, rho - 1) per cell.
-// LIN: the linearised equilibrium (as collide_cell).
-template <typename S, int LR, bool WM, bool LIN = false>
-__global__ void __launch_bounds__(256, 2)
-    k_collide_stream_x4(const S *__restrict__ src, S *__restrict__ dst,
-                        const float4 *__restrict__ fcur, const uint8_t *__restrict__ flag_cur,
-                        float4 *__restrict__ fold, uint8_t *__restrict__ flag_old, int ny, int nz,
-                        int ncell, float omega, float u_wall, int *status, float4 *__restrict__ moments) {
+// Collision and streaming of one thread's quad (4 consecutive cells of a row)
+// from its 19 populations g (pairs (0,1) and (2,3), storage units), shared by
+// the kernel that loads them from global memory and the one that loads them
+// from a tile staged in shared memory.  Every lane of the block calls it (the
+// inactive ones too: they join the shuffles and, for rows spanning several
+// warps, the block barrier of the warp-edge rewrite; `edge` holds one row of
+// ten values per warp).
+template <typename S, int LR, bool WM, bool LIN>
+__device__ __forceinline__ void collide_quad(const float2 (&g)[19][2], S *__restrict__ dst,
+                                             const float4 *__restrict__ fcur, bool has_cur, bool active, int row,
+                                             int y, int z, int x0, int cell0, int lane, int warp, int ny, int nz,
+                                             int ncell, float omega, float u_wall, int *status,
+                                             float4 *__restrict__ moments, float (*edge)[10]) {
     constexpr int NX = 4 * LR;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nrows = ny * nz;
-    int row_raw, lx;
-    if constexpr (LR <= 32) {
-        row_raw = blockIdx.x * rows_per_block<LR>() + warp * (32 / LR) + lane / LR;
-        lx = lane & (LR - 1);
-    } else {
-        constexpr int WPR = LR / 32;
-        row_raw = blockIdx.x * rows_per_block<LR>() + warp / WPR;
-        lx = (warp % WPR) * 32 + lane;
-    }
-    const bool active = row_raw < nrows;
-    const int row = active ? row_raw : nrows - 1;  // inactive lanes still join the exchanges
-    const int y = row % ny, z = row / ny;
-    const int x0 = 4 * lx;
-    const int cell0 = x0 + NX * row;
-    __shared__ float edge[8][10];  // rows spanning several warps: crossing values by warp and direction
-
-    // the force flags and density come from the spreading kernel before this
-    // one (reading the populations before waiting for it puts the flags'
-    // round trip after the loads: slower)
-    prior_grid_wait();
-    allow_dependents();
-
-    // force flags per 32-cell segment of a row (the whole row if nx < 32); the
-    // lanes of one segment are consecutive lanes of one warp
-    constexpr int FTX = NX < 32 ? NX : 32;
-    const int fidx = row * (NX / FTX) + x0 / FTX;
-    const bool has_old = flag_old[fidx] != 0;
-    const bool has_cur = flag_cur[fidx] != 0;
-    if (has_old && active) {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) fold[cell0 + k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    __syncwarp();  // every lane of the segment has read its flag
-    if (has_old && active && x0 % FTX == 0) flag_old[fidx] = 0;
-
-    // Arithmetic on cell pairs (0,1) and (2,3) with the paired FP32
-    // instructions of sm_100+, in storage units: G = kScale g, so binary16
-    // values are used as loaded (exact power-of-two scale folded into the
-    // per-cell quantities).
     constexpr float SC = Quad<S>::kScale, ISC = 1.f / Quad<S>::kScale;
-    float2 g[19][2];
-#pragma unroll
-    for (int i = 0; i < 19; ++i) Quad<S>::load_raw(src + (size_t)i * ncell + cell0, g[i][0], g[i][1]);
-
-
     // per cell: moments, velocity with the half force, and the pair vectors
     // of the per-direction arithmetic.  A = D + kScale rho (-3/2 u.u) is the
     // part of the equilibrium (minus the weight) common to all directions
@@ -525,6 +485,63 @@ __global__ void __launch_bounds__(256, 2)
             }
         }
     }
+}
+
+// WM: also write the moments of f(t), float4 (j, rho - 1) per cell.
+// LIN: the linearised equilibrium (as collide_cell).
+template <typename S, int LR, bool WM, bool LIN = false>
+__global__ void __launch_bounds__(256, 2)
+    k_collide_stream_x4(const S *__restrict__ src, S *__restrict__ dst,
+                        const float4 *__restrict__ fcur, const uint8_t *__restrict__ flag_cur,
+                        float4 *__restrict__ fold, uint8_t *__restrict__ flag_old, int ny, int nz,
+                        int ncell, float omega, float u_wall, int *status, float4 *__restrict__ moments) {
+    constexpr int NX = 4 * LR;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nrows = ny * nz;
+    int row_raw, lx;
+    if constexpr (LR <= 32) {
+        row_raw = blockIdx.x * rows_per_block<LR>() + warp * (32 / LR) + lane / LR;
+        lx = lane & (LR - 1);
+    } else {
+        constexpr int WPR = LR / 32;
+        row_raw = blockIdx.x * rows_per_block<LR>() + warp / WPR;
+        lx = (warp % WPR) * 32 + lane;
+    }
+    const bool active = row_raw < nrows;
+    const int row = active ? row_raw : nrows - 1;  // inactive lanes still join the exchanges
+    const int y = row % ny, z = row / ny;
+    const int x0 = 4 * lx;
+    const int cell0 = x0 + NX * row;
+    __shared__ float edge[8][10];  // rows spanning several warps: crossing values by warp and direction
+
+    // the force flags and density come from the spreading kernel before this
+    // one (reading the populations before waiting for it puts the flags'
+    // round trip after the loads: slower)
+    prior_grid_wait();
+    allow_dependents();
+
+    // force flags per 32-cell segment of a row (the whole row if nx < 32); the
+    // lanes of one segment are consecutive lanes of one warp
+    constexpr int FTX = NX < 32 ? NX : 32;
+    const int fidx = row * (NX / FTX) + x0 / FTX;
+    const bool has_old = flag_old[fidx] != 0;
+    const bool has_cur = flag_cur[fidx] != 0;
+    if (has_old && active) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) fold[cell0 + k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncwarp();  // every lane of the segment has read its flag
+    if (has_old && active && x0 % FTX == 0) flag_old[fidx] = 0;
+
+    // Arithmetic on cell pairs (0,1) and (2,3) with the paired FP32
+    // instructions of sm_100+, in storage units: G = kScale g, so binary16
+    // values are used as loaded (exact power-of-two scale folded into the
+    // per-cell quantities).
+    float2 g[19][2];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) Quad<S>::load_raw(src + (size_t)i * ncell + cell0, g[i][0], g[i][1]);
+    collide_quad<S, LR, WM, LIN>(g, dst, fcur, has_cur, active, row, y, z, x0, cell0, lane, warp, ny, nz, ncell,
+                                 omega, u_wall, status, moments, edge);
 }
 
 // ---- two cells per thread (rows of even length, float arithmetic) ------------------
@@ -886,6 +903,67 @@ void launch_collide_batch(int prec, const BatchArgs &b, const CollideArgs &a, cu
     if (prec == kF64) collide_batch_impl<double, double>(b, a, s, overlap);
     else if (prec == kF32) collide_batch_impl<float, float>(b, a, s, overlap);
     else collide_batch_impl<__half, float>(b, a, s, overlap);
+}
+
+// ---- checkpoint section checksum ------------------------------------------------------
+// Sum modulo 2^64 of mix(w_k + k * 0x9e3779b97f4a7c15) over the 64-bit words
+// w_k of a byte range (the last word zero-padded), mix being the SplitMix64
+// finaliser (a bijection).  Addition modulo 2^64 does not depend on order, so
+// the device's atomic sum and the host loop of capi.cpp give the same value,
+// and a change of any single byte changes exactly one term.
+__device__ __forceinline__ unsigned long long ck_mix(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_checksum(const unsigned char *__restrict__ p, unsigned long long n_bytes,
+                           unsigned long long *__restrict__ out) {
+    const unsigned long long n_words = (n_bytes + 7) / 8;
+    unsigned long long acc = 0;
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < n_words;
+         k += (unsigned long long)gridDim.x * blockDim.x) {
+        unsigned long long w = 0;
+        if (8 * k + 8 <= n_bytes) {
+            w = ((const unsigned long long *)p)[k];  // sections start 256-byte aligned
+        } else {
+            for (unsigned long long b = 8 * k; b < n_bytes; ++b) w |= (unsigned long long)p[b] << (8 * (b - 8 * k));
+        }
+        acc += ck_mix(w + k * 0x9e3779b97f4a7c15ull);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
+void launch_checksum(const void *p, size_t n_bytes, unsigned long long *out, cudaStream_t s) {
+    const size_t words = (n_bytes + 7) / 8;
+    const unsigned blocks = (unsigned)std::min<size_t>((words + 255) / 256, 152 * 8);
+    if (blocks) k_checksum<<<blocks, 256, 0, s>>>((const unsigned char *)p, n_bytes, out);
+}
+
+const char *collide_kernel_name(int prec, const Lattice &L) {
+    static const char *const x4_f32[9] = {
+        "k_collide_stream_x4<float,1>",  "k_collide_stream_x4<float,2>",  "k_collide_stream_x4<float,4>",
+        "k_collide_stream_x4<float,8>",  "k_collide_stream_x4<float,16>", "k_collide_stream_x4<float,32>",
+        "k_collide_stream_x4<float,64>", "k_collide_stream_x4<float,128>", "k_collide_stream_x4<float,256>"};
+    static const char *const x4_f16[9] = {
+        "k_collide_stream_x4<__half,1>",  "k_collide_stream_x4<__half,2>",  "k_collide_stream_x4<__half,4>",
+        "k_collide_stream_x4<__half,8>",  "k_collide_stream_x4<__half,16>", "k_collide_stream_x4<__half,32>",
+        "k_collide_stream_x4<__half,64>", "k_collide_stream_x4<__half,128>", "k_collide_stream_x4<__half,256>"};
+    if (prec == kF64) return "k_collide_stream<double,double>";
+    if (L.lanes_row) {
+        int k = 0;
+        while ((1 << k) < L.lanes_row) ++k;
+        return prec == kF32 ? x4_f32[k] : x4_f16[k];
+    }
+    if (L.nx % 2 == 0) return prec == kF32 ? "k_collide_pair<float>" : "k_collide_pair<__half>";
+    return prec == kF32 ? "k_collide_stream<float,float>" : "k_collide_stream<__half,float>";
+}
+
+const char *collide_batch_kernel_name(int prec, bool pairs) {
+    if (prec == kF64) return "k_collide_batch<double,double>";
+    if (pairs) return prec == kF32 ? "k_collide_pair_batch<float>" : "k_collide_pair_batch<__half>";
+    return prec == kF32 ? "k_collide_batch<float,float>" : "k_collide_batch<__half,float>";
 }
 
 int collide_batch_blocks_per_sm(int prec, bool pairs) {

@@ -3,22 +3,21 @@
 // tensor I_ab = 1/5 sum_faces A_i (r_i^2 delta_ab r_g - r_ia r_ib r_ig) n_ig
 // about the centroid.
 //
-// Recorded reductions take several position snapshots per launch (grid y),
-// so the cost of the launches is shared by consecutive records.
+// One launch per reduction: one thread-block cluster per capsule (and per
+// position snapshot, grid y, so that consecutive records share a launch)
+// makes two passes over the capsule's faces, each ending in a fixed-order sum
+// over the cluster (block sums exchanged through distributed shared memory),
+// so results are bitwise reproducible:
+//   1. V = 1/3 sum r.(A n), A = sum |A n|, m = sum (r.(A n)) r with r the face
+//      centroid minus the capsule's origin (its reference centre), and the
+//      centroid c = origin + m / (4 V);
+//   2. the inertia terms of the faces about c.
+// In the float builds the per-face terms are formed in float from the
+// positions relative to the origin and only the sums are carried in double.
 //
-// The faces of a capsule are split over several blocks (FP64 arithmetic is
-// scarce per SM, so a capsule is spread over many SMs; in the float builds the
-// per-face terms are formed in float and only the sums are in double).  Three launches, each
-// a fixed-order reduction, so results are bitwise reproducible:
-//   1. per block: V = 1/3 sum r.(A n), A = sum |A n|, m = sum (r.(A n)) r with
-//      r the face centroid minus the capsule's origin (its reference centre);
-//   2. per block: the block first totals the stage-1 partials of its capsule,
-//      forms the centroid c = origin + m / (4 V), then sums the inertia terms
-//      of its faces about c;
-//   3. per capsule: totals of both stages -> {V, A, c, I} in the output.
-// A block of 128 threads takes 128 to 1024 faces (chosen by the host).  Per-block
-// partials live in a scratch array [blocks][16] (stage 1 in entries 0..4,
-// stage 2 in entries 8..13).
+// The allocation-free entry point at the end keeps a three-launch form whose
+// per-block partial sums live in a fixed device array.
+#include <cooperative_groups.h>
 #include <mutex>
 #include <string>
 
@@ -205,114 +204,162 @@ struct FaceMath<NodeRead<float>> {
     }
 };
 
-template <typename R>
-__global__ void __launch_bounds__(kTB) k_taylor_stage1(R nodes0, const int4 *__restrict__ tri, TaylorPlan p,
-                                                       SnapSet ss) {
-    __shared__ double sh[kTB / 32][5];
-    const R nodes = nodes0.at(ss.slot(blockIdx.y), ss.stride);
-    const int b = blockIdx.x;
-    const int cap = p.blk_cap[b];
-    double *partial = p.partial + (size_t)blockIdx.y * p.total_blocks * 16;
-    double v[5] = {0, 0, 0, 0, 0};
-    for (int j = threadIdx.x; j < p.blk_nface[b]; j += kTB) {
-        const int4 t = tri[p.blk_face0[b] + j];
-        double w[5];
-        FaceMath<R>::stage1(nodes, t, p.origin + 3 * cap, w);
-        for (int k = 0; k < 5; ++k) v[k] += w[k];
-    }
-    block_sum<5>(v, sh);
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 5; ++k) partial[16 * b + k] = v[k];
-}
-
-// Totals of K partial entries (from entry `first`) over the blocks of one
-// capsule, by one full warp: lane l sums blocks l, l+32, ... in order, then a
-// fixed butterfly; every lane returns the same totals.
+// Fixed-order sum over the block (blockDim.x a multiple of 32, at most 1024)
+// of K doubles per thread: a butterfly within each warp, then the warps' sums
+// in warp order by thread 0, which alone holds the result.  `sh` may be reused
+// right after a call (it begins with a barrier).
 template <int K>
-__device__ __forceinline__ void capsule_totals(const TaylorPlan &p, const double *partial, int cap, int first,
-                                               double tot[K]) {
-    const int lane = threadIdx.x & 31;
-    for (int k = 0; k < K; ++k) tot[k] = 0.0;
-    for (int b = p.cap_blk0[cap] + lane; b < p.cap_blk0[cap + 1]; b += 32)
-        for (int k = 0; k < K; ++k) tot[k] += partial[16 * b + first + k];
+__device__ __forceinline__ void block_sum_any(double v[K], double (*sh)[K]) {
+#pragma unroll
     for (int k = 0; k < K; ++k)
-        for (int o = 16; o > 0; o >>= 1) tot[k] += __shfl_xor_sync(0xffffffffu, tot[k], o);
-}
-
-template <typename R>
-__global__ void __launch_bounds__(kTB) k_taylor_stage2(R nodes0, const int4 *__restrict__ tri, TaylorPlan p,
-                                                       SnapSet ss) {
-    __shared__ double sh[kTB / 32][6];
-    __shared__ double cen_sh[3];
-    const R nodes = nodes0.at(ss.slot(blockIdx.y), ss.stride);
-    const int b = blockIdx.x;
-    const int cap = p.blk_cap[b];
-    double *partial = p.partial + (size_t)blockIdx.y * p.total_blocks * 16;
-    if (threadIdx.x < 32) {
-        double tot[5];
-        capsule_totals<5>(p, partial, cap, 0, tot);
-        if (threadIdx.x == 0)
-            for (int k = 0; k < 3; ++k) cen_sh[k] = p.origin[3 * cap + k] + tot[2 + k] / (4.0 * tot[0]);
-    }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __syncthreads();
-    double v[6] = {0, 0, 0, 0, 0, 0};
-    for (int j = threadIdx.x; j < p.blk_nface[b]; j += kTB) {
-        const int4 t = tri[p.blk_face0[b] + j];
-        double w[6];
-        FaceMath<R>::stage2(nodes, t, p.origin + 3 * cap, cen_sh, w);
-        for (int k = 0; k < 6; ++k) v[k] += w[k];
-    }
-    block_sum<6>(v, sh);
-    if (threadIdx.x == 0)
-        for (int k = 0; k < 6; ++k) partial[16 * b + 8 + k] = v[k];
-}
-
-// One warp per capsule, 8 capsules per block, as many blocks as needed (the
-// FP64 work is spread over the SMs), grid y over the snapshots.  In recording
-// mode snapshot k goes to ring record count + k, and the last block to finish
-// advances the record counter by the number of snapshots.
-__global__ void __launch_bounds__(256) k_taylor_stage3(TaylorPlan p, int record, SnapSet ss) {
-    double *base = p.out;
-    unsigned long long count = 0;
-    if (record) {
-        count = *p.ring_count;
-        base = p.ring + (size_t)((count + blockIdx.y) % (unsigned long long)p.ring_len) * p.n_caps * 12;
-    }
-    const double *partial = p.partial + (size_t)blockIdx.y * p.total_blocks * 16;
-    const int lane = threadIdx.x & 31;
-    const int cap = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (cap < p.n_caps) {
-        double tot[5], I[6];
-        capsule_totals<5>(p, partial, cap, 0, tot);
-        capsule_totals<6>(p, partial, cap, 8, I);
-        if (lane == 0) {
-            double *o = base + 12 * cap;
-            o[0] = tot[0];
-            o[1] = tot[1];
-            for (int k = 0; k < 3; ++k) o[2 + k] = p.origin[3 * cap + k] + tot[2 + k] / (4.0 * tot[0]);
-            for (int k = 0; k < 6; ++k) o[5 + k] = I[k];
-            o[11] = 0.0;
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < K; ++k) sh[warp][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        for (int k = 0; k < K; ++k) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += sh[w][k];
+            v[k] = t;
         }
     }
-    if (record) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
+}
+
+// One thread-block cluster of CS blocks per capsule and snapshot (grid x:
+// capsules times CS, grid y: snapshots); FP64 arithmetic is scarce per SM on
+// this GPU, so a large capsule spreads its faces over the CS SMs of the
+// cluster, whose blocks exchange partial sums through distributed shared
+// memory within the one launch.  Block `rank` takes the faces
+// f0 + rank * blockDim.x + threadIdx.x + k * CS * blockDim.x in order.
+// Pass 1 gives each block's V, A and first-moment sums; after a cluster
+// barrier every block adds the CS partials in rank order (the same bits in
+// every block) and forms the centroid c = origin + m / (4 V); pass 2 sums the
+// inertia terms about c, and block 0 adds those partials in rank order.  In
+// recording mode snapshot k goes to ring record count + k and the last
+// cluster to finish advances the record counter by the number of snapshots.
+template <typename R>
+__global__ void __launch_bounds__(kTaylorClusterThreads) k_taylor_cluster(R nodes0, const int4 *__restrict__ tri,
+                                                                          TaylorPlan p, SnapSet ss, int record) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    __shared__ double sh[kTaylorClusterThreads / 32][6];
+    __shared__ double part1[6], part2[6];  // this block's sums of pass 1 and 2 (read by the cluster)
+    __shared__ double cen_sh[5];           // V, A, centroid
+    const int CS = (int)cluster.num_blocks();
+    const int rank = (int)cluster.block_rank();
+    const R nodes = nodes0.at(ss.slot(blockIdx.y), ss.stride);
+    const int cap = blockIdx.x / CS;
+    const int f0 = p.cap_face0[cap], f1 = p.cap_face0[cap + 1];
+    const double o[3] = {p.origin[3 * cap], p.origin[3 * cap + 1], p.origin[3 * cap + 2]};
+    const int stride = CS * blockDim.x;
+    double v[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll 4
+    for (int f = f0 + rank * blockDim.x + threadIdx.x; f < f1; f += stride) {
+        double w[5];
+        FaceMath<R>::stage1(nodes, tri[f], o, w);
+        for (int k = 0; k < 5; ++k) v[k] += w[k];
+    }
+    block_sum_any<6>(v, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 5; ++k) part1[k] = v[k];
+    cluster.sync();
+    if (threadIdx.x == 0) {
+        double t[5] = {0, 0, 0, 0, 0};
+        for (int r = 0; r < CS; ++r) {
+            const double *q = cluster.map_shared_rank(part1, r);
+            for (int k = 0; k < 5; ++k) t[k] += q[k];
+        }
+        cen_sh[0] = t[0];
+        cen_sh[1] = t[1];
+        for (int k = 0; k < 3; ++k) cen_sh[2 + k] = o[k] + t[2 + k] / (4.0 * t[0]);
+    }
+    __syncthreads();
+    const double c[3] = {cen_sh[2], cen_sh[3], cen_sh[4]};
+    double I[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll 4
+    for (int f = f0 + rank * blockDim.x + threadIdx.x; f < f1; f += stride) {
+        double w[6];
+        FaceMath<R>::stage2(nodes, tri[f], o, c, w);
+        for (int k = 0; k < 6; ++k) I[k] += w[k];
+    }
+    block_sum_any<6>(I, sh);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 6; ++k) part2[k] = I[k];
+    cluster.sync();
+    if (rank == 0 && threadIdx.x == 0) {
+        double t[6] = {0, 0, 0, 0, 0, 0};
+        for (int r = 0; r < CS; ++r) {
+            const double *q = cluster.map_shared_rank(part2, r);
+            for (int k = 0; k < 6; ++k) t[k] += q[k];
+        }
+        // every cluster reads the record counter before its ticket, so before
+        // the last one advances it
+        const unsigned long long count = record ? *p.ring_count : 0ull;
+        double *out = record ? p.ring + (size_t)((count + blockIdx.y) % (unsigned long long)p.ring_len) * p.n_caps * 12
+                             : p.out;
+        double *r = out + 12 * cap;
+        for (int k = 0; k < 5; ++k) r[k] = cen_sh[k];
+        for (int k = 0; k < 6; ++k) r[5 + k] = t[k];
+        r[11] = 0.0;
+        if (record) {
             __threadfence();
-            if (atomicAdd(p.ticket, 1u) == gridDim.x * gridDim.y - 1) {
+            if (atomicAdd(p.ticket, 1u) == (gridDim.x / CS) * gridDim.y - 1) {
                 *p.ticket = 0u;
                 *p.ring_count = count + gridDim.y;
             }
         }
     }
+    cluster.sync();  // the other blocks' shared memory stays until block 0 has read it
 }
 
 template <typename R>
 static void taylor_impl(R nodes, const MeshDev &m, const TaylorPlan &p, bool record, SnapSet ss,
                         cudaStream_t s) {
-    const dim3 g12(p.total_blocks, ss.n_snap), g3((p.n_caps + 7) / 8, ss.n_snap);
-    k_taylor_stage1<R><<<g12, kTB, 0, s>>>(nodes, (const int4 *)m.tri, p, ss);
-    k_taylor_stage2<R><<<g12, kTB, 0, s>>>(nodes, (const int4 *)m.tri, p, ss);
-    k_taylor_stage3<<<g3, 256, 0, s>>>(p, record ? 1 : 0, ss);
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = p.cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t c = {};
+    c.gridDim = dim3(p.n_caps * p.cluster, ss.n_snap);
+    c.blockDim = dim3(kTaylorClusterThreads);
+    c.dynamicSmemBytes = 0;
+    c.stream = s;
+    c.attrs = at;
+    c.numAttrs = 1;
+    cudaLaunchKernelEx(&c, k_taylor_cluster<R>, nodes, (const int4 *)m.tri, p, ss, record ? 1 : 0);
+}
+
+int taylor_max_cluster() {
+    static int best = 0;
+    if (best) return best;
+    // 16 blocks per cluster where the GPU allows it (non-portable size), else 8
+    int b = 8;
+    if (cudaFuncSetAttribute(k_taylor_cluster<NodeRead<float>>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+            cudaSuccess &&
+        cudaFuncSetAttribute(k_taylor_cluster<NodeRead<double>>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ==
+            cudaSuccess) {
+        cudaLaunchConfig_t c = {};
+        c.gridDim = dim3(16);
+        c.blockDim = dim3(kTaylorClusterThreads);
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 16;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        c.attrs = at;
+        c.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, k_taylor_cluster<NodeRead<float>>, &c) == cudaSuccess && n > 0) b = 16;
+    }
+    cudaGetLastError();
+    best = b;
+    return best;
 }
 
 void launch_taylor(int prec, const MeshDev &m, const TaylorPlan &p, bool record, cudaStream_t s) {
@@ -332,9 +379,10 @@ void launch_taylor_snapshots(int prec, const MeshDev &m, const TaylorPlan &p, bo
 
 // ---- allocation-free variant ---------------------------------------------------------
 // Some callers cannot allocate device memory when they need these reductions:
-// code that runs while a framework captures its stream into a CUDA graph, code
-// whose whole device budget is handed to another allocator, or a tight loop in
-// which an allocation would synchronise the device.  For them the per-block
+// code whose whole device budget is handed to another allocator (a framework's
+// caching allocator or a fixed arena), plug-ins called back from such a
+// framework, or a tight loop in which an allocation would synchronise the
+// device.  For them the per-block
 // partial sums of the three stages live in this fixed array, which every GPU
 // that loads the library holds until the process exits.
 constexpr int kNoAllocMaxBlocks = 1024;  // 1024 blocks x 128 faces = 131072 faces
@@ -453,7 +501,9 @@ __global__ void k_noalloc_stage3(const double *__restrict__ partial, int nb, dou
 }  // namespace iblbm
 
 namespace {
-// Device address of g_noalloc_partial, looked up once per device.
+// Device address of g_noalloc_partial, looked up once per device and kept for
+// the life of the process (a device reset would invalidate it; the header
+// says so).
 std::mutex g_noalloc_mu;
 double *g_noalloc_ptr[256] = {nullptr};
 }  // namespace

@@ -33,7 +33,6 @@ IBLBM_ERR_OOM = -2
 IBLBM_ERR_CUDA = -3
 IBLBM_ERR_UNSTABLE = -4
 IBLBM_ERR_STENCIL = -5
-IBLBM_ERR_TIMEOUT = -6
 IBLBM_ERR_STATE = -7
 
 IBLBM_FP64 = 0
@@ -80,6 +79,10 @@ _SIGS = {
     "iblbm_set_skalak": (_int, [_vp, _int, _dbl, _dbl]),
     "iblbm_init_fluid": (_int, [_vp, _int]),
     "iblbm_step": (_int, [_vp, ctypes.c_int64]),
+    "iblbm_prepare_steps": (_int, [_vp, ctypes.c_int64]),
+    "iblbm_set_kernel_timing": (_int, [_vp, _int]),
+    "iblbm_get_kernel_times": (_int, [_vp, _dp, ctypes.POINTER(ctypes.c_int64)]),
+    "iblbm_collide_kernel": (ctypes.c_char_p, [_vp]),
     "iblbm_sync": (_int, [_vp]),
     "iblbm_get_velocity": (_int, [_vp, _dp]),
     "iblbm_get_density": (_int, [_vp, _dp]),
@@ -112,7 +115,7 @@ _SIGS = {
     "iblbm_mesh_quality": (_int, [_vp, _int, _dp]),
     "iblbm_set_equilibrium": (_int, [_vp, _int]),
     "iblbm_checkpoint_save": (_int, [_vp, _vp, _int]),
-    "iblbm_checkpoint_restore": (_int, [_vp, _vp, _int]),
+    "iblbm_checkpoint_restore": (_int, [_vp, _vp, ctypes.c_size_t, _int]),
     "iblbm_batch_create": (_int, [ctypes.POINTER(_vp), ctypes.POINTER(iblbm_run_spec), _int, _int, _int,
                                   _vp, ctypes.POINTER(iblbm_allocator)]),
     "iblbm_add_capsule_icosphere_in_run": (_int, [_vp, _int, _dbl, _dbl, _dbl, _dbl, _int, _ip]),
@@ -420,6 +423,24 @@ class Sim:
         _check(iblbm_profile_kernels(self._h, int(n_steps), _d(ms)), self._h)
         return dict(zip(("force_spread", "collide_stream", "interp_advect", "taylor"), ms.tolist()))
 
+    def prepare_steps(self, n: int):
+        """Captures the graphs a following step(n) replays (runs nothing)."""
+        _check(iblbm_prepare_steps(self._h, int(n)), self._h)
+
+    def set_kernel_timing(self, on: bool = True):
+        _check(iblbm_set_kernel_timing(self._h, 1 if on else 0), self._h)
+
+    def kernel_times(self) -> dict:
+        """Mean device ms per step of the kernel groups of the last replay of
+        every step graph replayed since the previous call (kernel timing on)."""
+        ms = np.zeros(3)
+        n = ctypes.c_int64(0)
+        _check(iblbm_get_kernel_times(self._h, _d(ms), ctypes.byref(n)), self._h)
+        return {"force_spread": ms[0], "collide_stream": ms[1], "interp_advect": ms[2], "steps": int(n.value)}
+
+    def collide_kernel(self) -> str:
+        return iblbm_collide_kernel(self._h).decode()
+
     def adjoint_forward(self, n_steps: int, checkpoint_every: int):
         _check(iblbm_adjoint_forward(self._h, int(n_steps), int(checkpoint_every)), self._h)
 
@@ -483,8 +504,11 @@ class Sim:
         return buf
 
     def checkpoint_restore(self, buf):
-        ptr, dev = _buffer(buf, self.checkpoint_size())
-        _check(iblbm_checkpoint_restore(self._h, ptr, dev), self._h)
+        """Restores from buf (as checkpoint_save writes it); the library checks
+        the header, the length and the sections' checksums first."""
+        ptr, dev = _buffer(buf, 0)
+        nbytes = buf.nbytes if isinstance(buf, np.ndarray) else buf.numel() * buf.element_size()
+        _check(iblbm_checkpoint_restore(self._h, ptr, nbytes, dev), self._h)
 
     def taylor(self, capsule_id: int = 0) -> dict:
         out = np.empty(16, np.float64)

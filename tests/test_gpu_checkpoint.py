@@ -2,8 +2,9 @@
 checkpoint matches the uninterrupted run (bit for bit without membranes,
 where nothing depends on the order of atomic additions; to rounding of the
 spreading's atomics with them), in every storage precision, with host and
-device buffers, into the same object and into a fresh one; mismatched or
-corrupt checkpoints are rejected before anything is written."""
+device buffers, into the same object and into a fresh one; mismatched,
+truncated or corrupt checkpoints (a byte flipped in a section fails that
+section's checksum) are rejected before anything is written."""
 import numpy as np
 import pytest
 
@@ -90,6 +91,27 @@ def test_checkpoint_rejects_mismatch_and_corruption():
         g.checkpoint_restore(bad)
     assert e.value.code == B.IBLBM_ERR_ARG
     assert np.array_equal(g.get_populations(), before)  # nothing was written
+    # one byte flipped inside a section: the section's checksum no longer
+    # matches, in a host buffer and in a device buffer; a truncated buffer is
+    # refused by its length
+    import torch
+
+    size = g.checkpoint_size()
+    for off, section in ((256 + 1234, "populations"), (size - 300, "node velocities")):
+        bad = buf.copy()
+        bad[off] ^= 0x04
+        for b in (bad, torch.from_numpy(bad).cuda()):
+            with pytest.raises(B.IblbmError) as e:
+                g.checkpoint_restore(b)
+            assert e.value.code == B.IBLBM_ERR_ARG and "checksum" in str(e.value), str(e.value)
+            assert section in str(e.value)
+    for n in (100, size - 1):
+        with pytest.raises(B.IblbmError) as e:
+            g.checkpoint_restore(buf[:n].copy())
+        assert e.value.code == B.IBLBM_ERR_ARG
+    assert np.array_equal(g.get_populations(), before)
+    g.checkpoint_restore(torch.from_numpy(buf).cuda())  # the intact copy on the device
+    assert np.array_equal(g.get_populations(), before)
     # a host buffer declared as device memory is refused
     ptr = B.ctypes.c_void_p(buf.ctypes.data)
     assert B.iblbm_checkpoint_save(g._h, ptr, 1) == B.IBLBM_ERR_ARG
