@@ -25,27 +25,37 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_CS_LIB_PATH = os.path.join(_BUILD, "liboracle_cs.so")
 _SOURCES = ["lattice.c", "ibm.c", "membrane.c", "mesh.c", "taylor.c", "diag.c", "sim.c"]
+# the complex-step build: the method's sources with real = double _Complex
+_CS_SOURCES = ["lattice.c", "ibm.c", "membrane.c", "taylor.c", "sim.c", "tangent.c"]
 _lock = threading.Lock()
 _lib = None
 
 ERR_STENCIL = -5
 
 
-def build(force: bool = False) -> str:
-    """Compile ``liboracle.so`` (gcc, FP64, no FMA contraction)."""
-    srcs = [os.path.join(_HERE, s) for s in _SOURCES] + [os.path.join(_HERE, "oracle.h")]
-    if not force and os.path.exists(_LIB_PATH):
-        t_lib = os.path.getmtime(_LIB_PATH)
+def _compile(path: str, sources, defines, force: bool) -> str:
+    srcs = [os.path.join(_HERE, s) for s in sources] + [os.path.join(_HERE, "oracle.h")]
+    if not force and os.path.exists(path):
+        t_lib = os.path.getmtime(path)
         if all(os.path.getmtime(s) <= t_lib for s in srcs):
-            return _LIB_PATH
+            return path
     os.makedirs(_BUILD, exist_ok=True)
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp",
-           "-o", tmp] + [os.path.join(_HERE, s) for s in _SOURCES] + ["-lm"]
+    tmp = path + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp", *defines,
+           "-o", tmp] + [os.path.join(_HERE, s) for s in sources] + ["-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, path)
+    return path
+
+
+def build(force: bool = False) -> str:
+    """Compile ``liboracle.so`` (gcc, FP64, no FMA contraction) and its
+    complex-step twin ``liboracle_cs.so`` (the same sources with
+    real = double _Complex, for tangent derivatives)."""
+    _compile(_CS_LIB_PATH, _CS_SOURCES, ["-DORC_COMPLEX_STEP"], force)
+    return _compile(_LIB_PATH, _SOURCES, [], force)
 
 
 def lib() -> ctypes.CDLL:
@@ -108,6 +118,45 @@ def _declare(L):
     for name in ("get_f", "set_f", "get_nodes", "set_nodes", "get_force_field",
                  "get_node_forces", "get_node_velocities", "get_density", "get_velocity"):
         getattr(L, "orc_sim_" + name).argtypes = [c_void_p, _dp]
+
+
+_cs_lib = None
+
+
+def cs_lib() -> ctypes.CDLL:
+    """The complex-step build (real = double _Complex) of the oracle."""
+    global _cs_lib
+    with _lock:
+        if _cs_lib is None:
+            build()
+            L = ctypes.CDLL(_CS_LIB_PATH)
+            L.orc_tangent_taylor_D.argtypes = [
+                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double,
+                ctypes.c_double, ctypes.c_int, _dp, _dp, ctypes.c_int, _ip, ctypes.c_double, ctypes.c_double,
+                ctypes.c_double, ctypes.c_int, ctypes.c_double, _dp]
+            L.orc_set_threads.argtypes = [ctypes.c_int]
+            _cs_lib = L
+    return _cs_lib
+
+
+def tangent_taylor_D(shape, tau: float, delta_n: int, u_wall: float, X0, tri, ks: float, C: float,
+                     n_steps: int, du_wall: float = 0.0, dX0=None, dks: float = 0.0, h: float = 1e-30,
+                     threads: int = 1):
+    """(D, dD): the Taylor deformation of the final shape after n_steps of the
+    coupled step (one capsule starting in its reference shape X0, Couette start)
+    and its derivative along (du_wall, dX0, dks) at fixed C = k_alpha / k_s, by
+    the complex-step method on the whole oracle."""
+    L = cs_lib()
+    L.orc_set_threads(int(threads))
+    X0, tri = _f64(X0), _i32(tri)
+    dX = np.zeros_like(X0) if dX0 is None else _f64(dX0)
+    out = np.zeros(2)
+    nx, ny, nz = shape
+    rc = L.orc_tangent_taylor_D(nx, ny, nz, tau, delta_n, u_wall, du_wall, X0.shape[0], _d(X0), _d(dX),
+                                tri.shape[0], _i(tri), ks, dks, C, int(n_steps), h, _d(out))
+    if rc:
+        raise ValueError(f"orc_tangent_taylor_D returned {rc}")
+    return float(out[0]), float(out[1])
 
 
 def set_threads(n: int) -> None:

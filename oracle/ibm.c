@@ -27,37 +27,37 @@
 #include "oracle.h"
 
 /* Eqs. (2point), (3point), (4point). */
-double orc_phi(int n, double r) {
-    double a = fabs(r);
+real orc_phi(int n, real r) {
+    real a = r_abs(r);
     if (n == 2) {
-        return a <= 1.0 ? 1.0 - a : 0.0;
+        return RE(a) <= 1.0 ? 1.0 - a : 0.0;
     }
     if (n == 3) {
-        if (a <= 0.5) return (1.0 + sqrt(1.0 - 3.0 * r * r)) / 3.0;
-        if (a <= 1.5) return (5.0 - 3.0 * a - sqrt(-2.0 + 6.0 * a - 3.0 * r * r)) / 6.0;
+        if (RE(a) <= 0.5) return (1.0 + r_sqrt(1.0 - 3.0 * r * r)) / 3.0;
+        if (RE(a) <= 1.5) return (5.0 - 3.0 * a - r_sqrt(-2.0 + 6.0 * a - 3.0 * r * r)) / 6.0;
         return 0.0;
     }
     if (n == 4) {
-        if (a <= 1.0) return (3.0 - 2.0 * a + sqrt(1.0 + 4.0 * a - 4.0 * r * r)) / 8.0;
-        if (a <= 2.0) return (5.0 - 2.0 * a - sqrt(-7.0 + 12.0 * a - 4.0 * r * r)) / 8.0;
+        if (RE(a) <= 1.0) return (3.0 - 2.0 * a + r_sqrt(1.0 + 4.0 * a - 4.0 * r * r)) / 8.0;
+        if (RE(a) <= 2.0) return (5.0 - 2.0 * a - r_sqrt(-7.0 + 12.0 * a - 4.0 * r * r)) / 8.0;
         return 0.0;
     }
     return 0.0;
 }
 
-int orc_stencil_base(int n, double x) { return (int)floor(x - 0.5 * n) + 1; }
+int orc_stencil_base(int n, real x) { return (int)floor(RE(x) - 0.5 * n) + 1; }
 
 static int wrap(int a, int n) { return ((a % n) + n) % n; }
 
 /* Eq. (forcespreading), delta(r) = phi(x) phi(y) phi(z).  Nodes in order,
  * stencil nodes in (z, y, x) lexicographic order. */
-int orc_spread(int nx, int ny, int nz, int n, int n_nodes, const double *x,
-               const double *F, double *force_out) {
+int orc_spread(int nx, int ny, int nz, int n, int n_nodes, const real *x,
+               const real *F, real *force_out) {
     if (n < 2 || n > 4) return -1;
     const size_t N = (size_t)nx * ny * nz;
-    memset(force_out, 0, 3 * N * sizeof(double));
+    memset(force_out, 0, 3 * N * sizeof(real));
     for (int i = 0; i < n_nodes; ++i) {
-        const double *xi = x + 3 * i;
+        const real *xi = x + 3 * i;
         int b[3];
         for (int a = 0; a < 3; ++a) b[a] = orc_stencil_base(n, xi[a]);
         for (int kz = 0; kz < n; ++kz) {
@@ -67,7 +67,7 @@ int orc_spread(int nx, int ny, int nz, int n, int n_nodes, const double *x,
                 int Y = b[1] + ky;
                 for (int kx = 0; kx < n; ++kx) {
                     int X = b[0] + kx;
-                    double d = orc_phi(n, X - xi[0]) * orc_phi(n, Y - xi[1]) *
+                    real d = orc_phi(n, X - xi[0]) * orc_phi(n, Y - xi[1]) *
                                orc_phi(n, Z - xi[2]);
                     size_t cell = (size_t)wrap(X, nx) +
                                   (size_t)nx * (wrap(Y, ny) + (size_t)ny * Z);
@@ -81,12 +81,12 @@ int orc_spread(int nx, int ny, int nz, int n, int n_nodes, const double *x,
 
 /* Eq. (velocityinterpolation). */
 int orc_interpolate(int nx, int ny, int nz, int n, int n_nodes,
-                    const double *x, const double *u_field, double *u_out) {
+                    const real *x, const real *u_field, real *u_out) {
     if (n < 2 || n > 4) return -1;
     const size_t N = (size_t)nx * ny * nz;
     for (int i = 0; i < n_nodes; ++i) {
-        const double *xi = x + 3 * i;
-        double acc[3] = {0.0, 0.0, 0.0};
+        const real *xi = x + 3 * i;
+        real acc[3] = {0.0, 0.0, 0.0};
         int b[3];
         for (int a = 0; a < 3; ++a) b[a] = orc_stencil_base(n, xi[a]);
         for (int kz = 0; kz < n; ++kz) {
@@ -96,7 +96,7 @@ int orc_interpolate(int nx, int ny, int nz, int n, int n_nodes,
                 int Y = b[1] + ky;
                 for (int kx = 0; kx < n; ++kx) {
                     int X = b[0] + kx;
-                    double d = orc_phi(n, X - xi[0]) * orc_phi(n, Y - xi[1]) *
+                    real d = orc_phi(n, X - xi[0]) * orc_phi(n, Y - xi[1]) *
                                orc_phi(n, Z - xi[2]);
                     size_t cell = (size_t)wrap(X, nx) +
                                   (size_t)nx * (wrap(Y, ny) + (size_t)ny * Z);

@@ -59,42 +59,42 @@ void orc_d3q19(int c[19][3], double w[19], int opp[19]) {
 }
 
 /* Eq. (equilibrium). */
-double orc_feq(int i, double rho, const double u[3]) {
-    double cu = C[i][0] * u[0] + C[i][1] * u[1] + C[i][2] * u[2];
-    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+real orc_feq(int i, real rho, const real u[3]) {
+    real cu = C[i][0] * u[0] + C[i][1] * u[1] + C[i][2] * u[2];
+    real uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     return weight(i) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
 }
 
 /* The linearised equilibrium of Sec. IV.A, f_i^eq = w_i rho (1 + 3 c_i.u):
  * the second-order terms of Eq. (equilibrium) dropped. */
-double orc_feq_linear(int i, double rho, const double u[3]) {
-    double cu = C[i][0] * u[0] + C[i][1] * u[1] + C[i][2] * u[2];
+real orc_feq_linear(int i, real rho, const real u[3]) {
+    real cu = C[i][0] * u[0] + C[i][1] * u[1] + C[i][2] * u[2];
     return weight(i) * rho * (1.0 + 3.0 * cu);
 }
 
 /* Eq. (latticeforce) with c_s^2 = 1/3:
  * F_i = (1 - 1/(2 tau)) w_i [ (c_i - u)/c_s^2 + (c_i.u) c_i / c_s^4 ] . f */
-double orc_guo(int i, double tau, const double u[3], const double f[3]) {
+real orc_guo(int i, double tau, const real u[3], const real f[3]) {
     const double cs2 = 1.0 / 3.0;
-    double cu = C[i][0] * u[0] + C[i][1] * u[1] + C[i][2] * u[2];
-    double s = 0.0;
+    real cu = C[i][0] * u[0] + C[i][1] * u[1] + C[i][2] * u[2];
+    real s = 0.0;
     for (int a = 0; a < 3; ++a) {
-        double term = (C[i][a] - u[a]) / cs2 + cu * C[i][a] / (cs2 * cs2);
+        real term = (C[i][a] - u[a]) / cs2 + cu * C[i][a] / (cs2 * cs2);
         s += term * f[a];
     }
     return (1.0 - 1.0 / (2.0 * tau)) * weight(i) * s;
 }
 
 /* Eqs. (lbmmomenta0) and (lbmmomenta1). */
-void orc_moments(const double fi[19], const double force[3], double *rho,
-                 double u[3]) {
-    double r = 0.0, j[3] = {0.0, 0.0, 0.0};
+void orc_moments(const real fi[19], const real force[3], real *rho,
+                 real u[3]) {
+    real r = 0.0, j[3] = {0.0, 0.0, 0.0};
     for (int i = 0; i < 19; ++i) {
         r += fi[i];
         for (int a = 0; a < 3; ++a) j[a] += C[i][a] * fi[i];
     }
     for (int a = 0; a < 3; ++a) {
-        double fa = force ? force[a] : 0.0;
+        real fa = force ? force[a] : 0.0;
         u[a] = (j[a] + 0.5 * fa) / r;
     }
     *rho = r;
@@ -110,16 +110,16 @@ static int wrap(int a, int n) { return ((a % n) + n) % n; }
  *     f_opp(i)(x, t+1) = f_i*(x, t) - 2 w_i rho0 (c_i . u_wall) / c_s^2
  * with rho0 = 1 and u_wall = (+u_wall, 0, 0) at the top plane z = nz - 1/2,
  * (-u_wall, 0, 0) at the bottom plane z = -1/2. */
-int orc_lbm_step(int nx, int ny, int nz, double tau, double u_wall,
-                 const double *f, const double *force, double *f_out) {
+int orc_lbm_step(int nx, int ny, int nz, double tau, real u_wall,
+                 const real *f, const real *force, real *f_out) {
     return orc_lbm_step_eq(nx, ny, nz, tau, u_wall, f, force, f_out, 2);
 }
 
 /* The same step with the equilibrium of the given order: 2 for Eq.
  * (equilibrium), 1 for the linearised one of Sec. IV.A (the forcing term is
  * Eq. (latticeforce) in both; the paper changes only the equilibrium). */
-int orc_lbm_step_eq(int nx, int ny, int nz, double tau, double u_wall,
-                    const double *f, const double *force, double *f_out, int order) {
+int orc_lbm_step_eq(int nx, int ny, int nz, double tau, real u_wall,
+                    const real *f, const real *force, real *f_out, int order) {
     if (nx < 1 || ny < 1 || nz < 1 || !(tau > 0.5) || (order != 1 && order != 2)) return -1;
     const size_t N = (size_t)nx * ny * nz;
     const double cs2 = 1.0 / 3.0;
@@ -131,18 +131,18 @@ int orc_lbm_step_eq(int nx, int ny, int nz, double tau, double u_wall,
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 size_t cell = (size_t)x + (size_t)nx * (y + (size_t)ny * z);
-                double fi[19], fc[3] = {0.0, 0.0, 0.0}, rho, u[3];
+                real fi[19], fc[3] = {0.0, 0.0, 0.0}, rho, u[3];
                 for (int i = 0; i < 19; ++i) fi[i] = f[i * N + cell];
                 if (force)
                     for (int a = 0; a < 3; ++a) fc[a] = force[a * N + cell];
                 orc_moments(fi, fc, &rho, u);
                 for (int i = 0; i < 19; ++i) {
-                    double eq = order == 2 ? orc_feq(i, rho, u) : orc_feq_linear(i, rho, u);
-                    double post = fi[i] - (fi[i] - eq) / tau + orc_guo(i, tau, u, fc);
+                    real eq = order == 2 ? orc_feq(i, rho, u) : orc_feq_linear(i, rho, u);
+                    real post = fi[i] - (fi[i] - eq) / tau + orc_guo(i, tau, u, fc);
                     int zt = z + C[i][2];
                     if (zt < 0 || zt >= nz) {
-                        double uw = (zt >= nz) ? u_wall : -u_wall;
-                        double cuw = C[i][0] * uw;
+                        real uw = (zt >= nz) ? u_wall : -u_wall;
+                        real cuw = C[i][0] * uw;
                         f_out[opp[i] * N + cell] =
                             post - 2.0 * weight(i) * 1.0 * cuw / cs2;
                     } else {
@@ -159,14 +159,14 @@ int orc_lbm_step_eq(int nx, int ny, int nz, double tau, double u_wall,
 /* Initial state (reading: the paper does not state one): equilibrium at
  * rho = 1 with the linear Couette profile between the moving walls,
  * shear rate 2 u_wall / H with H = nz. */
-void orc_init_couette(int nx, int ny, int nz, double u_wall, double *f) {
+void orc_init_couette(int nx, int ny, int nz, real u_wall, real *f) {
     const size_t N = (size_t)nx * ny * nz;
-    const double gamma = 2.0 * u_wall / nz;
+    const real gamma = 2.0 * u_wall / nz;
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
                 size_t cell = (size_t)x + (size_t)nx * (y + (size_t)ny * z);
-                double u[3] = {gamma * (z - 0.5 * (nz - 1)), 0.0, 0.0};
+                real u[3] = {gamma * (z - 0.5 * (nz - 1)), 0.0, 0.0};
                 for (int i = 0; i < 19; ++i) f[i * N + cell] = orc_feq(i, 1.0, u);
             }
 }

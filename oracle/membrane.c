@@ -28,11 +28,11 @@
 
 #define ND 9
 typedef struct {
-    double v;
-    double d[ND];
+    real v;
+    real d[ND];
 } dual;
 
-static dual d_const(double v) {
+static dual d_const(real v) {
     dual r;
     r.v = v;
     for (int k = 0; k < ND; ++k) r.d[k] = 0.0;
@@ -64,11 +64,11 @@ static dual d_div(dual a, dual b) {
 }
 static dual d_sqrt(dual a) {
     dual r;
-    r.v = sqrt(a.v);
+    r.v = r_sqrt(a.v);
     for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] / (2.0 * r.v);
     return r;
 }
-static dual d_scale(dual a, double s) {
+static dual d_scale(dual a, real s) {
     dual r;
     r.v = a.v * s;
     for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] * s;
@@ -77,9 +77,9 @@ static dual d_scale(dual a, double s) {
 
 /* Reference geometry of a face: l0 = |X3 - X1|, l0' = |X2 - X1|, phi0 the
  * angle at corner 1, and the reference area A0 = l0 l0' sin(phi0) / 2. */
-static void reference(const double X0[9], double *l0, double *lp0,
-                      double *cos0, double *sin0, double *A0) {
-    double e[3], ep[3], cr[3];
+static void reference(const real X0[9], real *l0, real *lp0,
+                      real *cos0, real *sin0, real *A0) {
+    real e[3], ep[3], cr[3];
     for (int a = 0; a < 3; ++a) {
         e[a] = X0[6 + a] - X0[a];
         ep[a] = X0[3 + a] - X0[a];
@@ -87,17 +87,17 @@ static void reference(const double X0[9], double *l0, double *lp0,
     cr[0] = e[1] * ep[2] - e[2] * ep[1];
     cr[1] = e[2] * ep[0] - e[0] * ep[2];
     cr[2] = e[0] * ep[1] - e[1] * ep[0];
-    *l0 = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
-    *lp0 = sqrt(ep[0] * ep[0] + ep[1] * ep[1] + ep[2] * ep[2]);
+    *l0 = r_sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    *lp0 = r_sqrt(ep[0] * ep[0] + ep[1] * ep[1] + ep[2] * ep[2]);
     *cos0 = (e[0] * ep[0] + e[1] * ep[1] + e[2] * ep[2]) / (*l0 * *lp0);
-    *sin0 = sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]) / (*l0 * *lp0);
+    *sin0 = r_sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]) / (*l0 * *lp0);
     *A0 = 0.5 * *l0 * *lp0 * *sin0;
 }
 
 /* a, b, c of Eq. (c) and the invariants of Eq. (lambda1), on dual numbers. */
-static void invariants(const double X0[9], const dual x[9], dual *I1, dual *I2,
-                       double *A0) {
-    double l0, lp0, cos0, sin0;
+static void invariants(const real X0[9], const dual x[9], dual *I1, dual *I2,
+                       real *A0) {
+    real l0, lp0, cos0, sin0;
     reference(X0, &l0, &lp0, &cos0, &sin0, A0);
     dual e[3], ep[3];
     for (int a = 0; a < 3; ++a) {
@@ -129,34 +129,34 @@ static void invariants(const double X0[9], const dual x[9], dual *I1, dual *I2,
 }
 
 /* Eq. (constitutivelaw) times the reference area. */
-static dual face_energy(const double X0[9], const dual x[9], double ks,
-                        double ka) {
+static dual face_energy(const real X0[9], const dual x[9], real ks,
+                        real ka) {
     dual I1, I2;
-    double A0;
+    real A0;
     invariants(X0, x, &I1, &I2, &A0);
     dual t1 = d_sub(d_add(d_mul(I1, I1), d_scale(I1, 2.0)), d_scale(I2, 2.0));
     dual w = d_add(d_scale(t1, ks / 12.0), d_scale(d_mul(I2, I2), ka / 12.0));
     return d_scale(w, A0);
 }
 
-static void seed(const double x[9], dual xd[9]) {
+static void seed(const real x[9], dual xd[9]) {
     for (int k = 0; k < 9; ++k) {
         xd[k] = d_const(x[k]);
         xd[k].d[k] = 1.0;
     }
 }
 
-double orc_face_energy(const double X0[9], const double x[9], double ks,
-                       double ka) {
+real orc_face_energy(const real X0[9], const real x[9], real ks,
+                       real ka) {
     dual xd[9];
     for (int k = 0; k < 9; ++k) xd[k] = d_const(x[k]);
     return face_energy(X0, xd, ks, ka).v;
 }
 
-void orc_face_invariants(const double X0[9], const double x[9], double *I1,
-                         double *I2) {
+void orc_face_invariants(const real X0[9], const real x[9], real *I1,
+                         real *I2) {
     dual xd[9], i1, i2;
-    double A0;
+    real A0;
     for (int k = 0; k < 9; ++k) xd[k] = d_const(x[k]);
     invariants(X0, xd, &i1, &i2, &A0);
     *I1 = i1.v;
@@ -164,8 +164,8 @@ void orc_face_invariants(const double X0[9], const double x[9], double *I1,
 }
 
 /* Eq. (forcefromenergy) for one face. */
-double orc_face_forces(const double X0[9], const double x[9], double ks,
-                       double ka, double F[9]) {
+real orc_face_forces(const real X0[9], const real x[9], real ks,
+                       real ka, real F[9]) {
     dual xd[9];
     seed(x, xd);
     dual W = face_energy(X0, xd, ks, ka);
@@ -175,13 +175,13 @@ double orc_face_forces(const double X0[9], const double x[9], double ks,
 
 /* W = sum over faces of A0_j w_j; node force = sum of the corner forces of
  * its faces, faces visited in ascending order. */
-double orc_membrane_forces(int n_nodes, const double *X0, const double *x,
-                           int n_tri, const int *tri, double ks, double ka,
-                           double *F) {
-    memset(F, 0, 3 * (size_t)n_nodes * sizeof(double));
-    double W = 0.0;
+real orc_membrane_forces(int n_nodes, const real *X0, const real *x,
+                           int n_tri, const int *tri, real ks, real ka,
+                           real *F) {
+    memset(F, 0, 3 * (size_t)n_nodes * sizeof(real));
+    real W = 0.0;
     for (int f = 0; f < n_tri; ++f) {
-        double X0f[9], xf[9], Ff[9];
+        real X0f[9], xf[9], Ff[9];
         for (int k = 0; k < 3; ++k)
             for (int a = 0; a < 3; ++a) {
                 X0f[3 * k + a] = X0[3 * tri[3 * f + k] + a];

@@ -36,19 +36,20 @@
 
 struct orc_sim {
     int nx, ny, nz, n;
-    double tau, u_wall;
+    double tau;
+    real u_wall;
     size_t N;
-    double *f, *f_new, *force;
+    real *f, *f_new, *force;
     int n_caps, n_nodes, n_tri;
     int cap_node0[1024], cap_nn[1024], cap_tri0[1024], cap_nt[1024];
-    double cap_ks[1024], cap_ka[1024];
-    double *X0, *x, *F, *u, *u_prev;
+    real cap_ks[1024], cap_ka[1024];
+    real *X0, *x, *F, *u, *u_prev;
     int *tri;
     int integrator, eq_order, have_prev;
 };
 
 orc_sim *orc_sim_create(int nx, int ny, int nz, double tau, int delta_n,
-                        double u_wall) {
+                        real u_wall) {
     if (nx < 1 || ny < 1 || nz < 1 || delta_n < 2 || delta_n > 4 || !(tau > 0.5))
         return NULL;
     orc_sim *s = (orc_sim *)calloc(1, sizeof(orc_sim));
@@ -57,9 +58,9 @@ orc_sim *orc_sim_create(int nx, int ny, int nz, double tau, int delta_n,
     s->tau = tau; s->u_wall = u_wall;
     s->eq_order = 2;
     s->N = (size_t)nx * ny * nz;
-    s->f = (double *)calloc(19 * s->N, sizeof(double));
-    s->f_new = (double *)calloc(19 * s->N, sizeof(double));
-    s->force = (double *)calloc(3 * s->N, sizeof(double));
+    s->f = (real *)calloc(19 * s->N, sizeof(real));
+    s->f_new = (real *)calloc(19 * s->N, sizeof(real));
+    s->force = (real *)calloc(3 * s->N, sizeof(real));
     if (!s->f || !s->f_new || !s->force) {
         orc_sim_destroy(s);
         return NULL;
@@ -75,19 +76,19 @@ void orc_sim_destroy(orc_sim *s) {
     free(s);
 }
 
-int orc_sim_add_capsule(orc_sim *s, int n_nodes, const double *X0, int n_tri,
-                        const int *tri, double ks, double ka) {
+int orc_sim_add_capsule(orc_sim *s, int n_nodes, const real *X0, int n_tri,
+                        const int *tri, real ks, real ka) {
     if (s->n_caps >= 1024 || n_nodes < 4 || n_tri < 4) return -1;
     int nn = s->n_nodes + n_nodes, nt = s->n_tri + n_tri;
-    double *X0n = (double *)realloc(s->X0, sizeof(double) * 3 * nn);
+    real *X0n = (real *)realloc(s->X0, sizeof(real) * 3 * nn);
     if (X0n) s->X0 = X0n;
-    double *xn = (double *)realloc(s->x, sizeof(double) * 3 * nn);
+    real *xn = (real *)realloc(s->x, sizeof(real) * 3 * nn);
     if (xn) s->x = xn;
-    double *Fn = (double *)realloc(s->F, sizeof(double) * 3 * nn);
+    real *Fn = (real *)realloc(s->F, sizeof(real) * 3 * nn);
     if (Fn) s->F = Fn;
-    double *un = (double *)realloc(s->u, sizeof(double) * 3 * nn);
+    real *un = (real *)realloc(s->u, sizeof(real) * 3 * nn);
     if (un) s->u = un;
-    double *upn = (double *)realloc(s->u_prev, sizeof(double) * 3 * nn);
+    real *upn = (real *)realloc(s->u_prev, sizeof(real) * 3 * nn);
     if (upn) s->u_prev = upn;
     int *tn = (int *)realloc(s->tri, sizeof(int) * 3 * nt);
     if (tn) s->tri = tn;
@@ -96,10 +97,10 @@ int orc_sim_add_capsule(orc_sim *s, int n_nodes, const double *X0, int n_tri,
         if (tri[t] < 0 || tri[t] >= n_nodes) return -1;
         s->tri[3 * s->n_tri + t] = tri[t];
     }
-    memcpy(s->X0 + 3 * s->n_nodes, X0, sizeof(double) * 3 * n_nodes);
-    memcpy(s->x + 3 * s->n_nodes, X0, sizeof(double) * 3 * n_nodes);
-    memset(s->F + 3 * s->n_nodes, 0, sizeof(double) * 3 * n_nodes);
-    memset(s->u + 3 * s->n_nodes, 0, sizeof(double) * 3 * n_nodes);
+    memcpy(s->X0 + 3 * s->n_nodes, X0, sizeof(real) * 3 * n_nodes);
+    memcpy(s->x + 3 * s->n_nodes, X0, sizeof(real) * 3 * n_nodes);
+    memset(s->F + 3 * s->n_nodes, 0, sizeof(real) * 3 * n_nodes);
+    memset(s->u + 3 * s->n_nodes, 0, sizeof(real) * 3 * n_nodes);
     int id = s->n_caps++;
     s->cap_node0[id] = s->n_nodes;
     s->cap_nn[id] = n_nodes;
@@ -130,16 +131,16 @@ int orc_sim_n_nodes(const orc_sim *s) { return s->n_nodes; }
 
 void orc_sim_init_couette(orc_sim *s) {
     orc_init_couette(s->nx, s->ny, s->nz, s->u_wall, s->f);
-    memset(s->force, 0, sizeof(double) * 3 * s->N);
+    memset(s->force, 0, sizeof(real) * 3 * s->N);
 }
 
 /* Lattice velocity of Eq. (lbmmomenta1) with the last spread force. */
-static void velocity_field(const orc_sim *s, double *ufield, double *rho_out) {
+static void velocity_field(const orc_sim *s, real *ufield, real *rho_out) {
     const int nthreads = orc_get_threads();
     const long long N = (long long)s->N;
 #pragma omp parallel for schedule(static) num_threads(nthreads) if (nthreads > 1)
     for (long long cell = 0; cell < N; ++cell) {
-        double fi[19], fc[3], rho, u[3];
+        real fi[19], fc[3], rho, u[3];
         for (int i = 0; i < 19; ++i) fi[i] = s->f[i * s->N + cell];
         for (int a = 0; a < 3; ++a) fc[a] = s->force[a * s->N + cell];
         orc_moments(fi, fc, &rho, u);
@@ -150,7 +151,7 @@ static void velocity_field(const orc_sim *s, double *ufield, double *rho_out) {
 }
 
 int orc_sim_step(orc_sim *s, int n_steps) {
-    double *ufield = (double *)malloc(sizeof(double) * 3 * s->N);
+    real *ufield = (real *)malloc(sizeof(real) * 3 * s->N);
     if (!ufield) return -2;
     int rc = 0;
     for (int step = 0; step < n_steps && rc == 0; ++step) {
@@ -167,11 +168,11 @@ int orc_sim_step(orc_sim *s, int n_steps) {
         /* 3. lattice Boltzmann step with f(X, t) */
         rc = orc_lbm_step_eq(s->nx, s->ny, s->nz, s->tau, s->u_wall, s->f, s->force, s->f_new, s->eq_order);
         if (rc) break;
-        double *tmp = s->f;
+        real *tmp = s->f;
         s->f = s->f_new;
         s->f_new = tmp;
         /* 4. interpolation of u(X, t+1) at x_i(t); u_i(t) kept */
-        memcpy(s->u_prev, s->u, sizeof(double) * 3 * s->n_nodes);
+        memcpy(s->u_prev, s->u, sizeof(real) * 3 * s->n_nodes);
         velocity_field(s, ufield, NULL);
         rc = orc_interpolate(s->nx, s->ny, s->nz, s->n, s->n_nodes, s->x, ufield, s->u);
         if (rc) break;
@@ -186,27 +187,27 @@ int orc_sim_step(orc_sim *s, int n_steps) {
     return rc;
 }
 
-void orc_sim_get_f(const orc_sim *s, double *f) {
-    memcpy(f, s->f, sizeof(double) * 19 * s->N);
+void orc_sim_get_f(const orc_sim *s, real *f) {
+    memcpy(f, s->f, sizeof(real) * 19 * s->N);
 }
-void orc_sim_set_f(orc_sim *s, const double *f) {
-    memcpy(s->f, f, sizeof(double) * 19 * s->N);
+void orc_sim_set_f(orc_sim *s, const real *f) {
+    memcpy(s->f, f, sizeof(real) * 19 * s->N);
 }
-void orc_sim_get_nodes(const orc_sim *s, double *x) {
-    memcpy(x, s->x, sizeof(double) * 3 * s->n_nodes);
+void orc_sim_get_nodes(const orc_sim *s, real *x) {
+    memcpy(x, s->x, sizeof(real) * 3 * s->n_nodes);
 }
-void orc_sim_set_nodes(orc_sim *s, const double *x) {
-    memcpy(s->x, x, sizeof(double) * 3 * s->n_nodes);
+void orc_sim_set_nodes(orc_sim *s, const real *x) {
+    memcpy(s->x, x, sizeof(real) * 3 * s->n_nodes);
     s->have_prev = 0;
 }
-void orc_sim_get_force_field(const orc_sim *s, double *force) {
-    memcpy(force, s->force, sizeof(double) * 3 * s->N);
+void orc_sim_get_force_field(const orc_sim *s, real *force) {
+    memcpy(force, s->force, sizeof(real) * 3 * s->N);
 }
-void orc_sim_get_node_forces(const orc_sim *s, double *F) {
-    memcpy(F, s->F, sizeof(double) * 3 * s->n_nodes);
+void orc_sim_get_node_forces(const orc_sim *s, real *F) {
+    memcpy(F, s->F, sizeof(real) * 3 * s->n_nodes);
 }
-void orc_sim_get_node_velocities(const orc_sim *s, double *u) {
-    memcpy(u, s->u, sizeof(double) * 3 * s->n_nodes);
+void orc_sim_get_node_velocities(const orc_sim *s, real *u) {
+    memcpy(u, s->u, sizeof(real) * 3 * s->n_nodes);
 }
-void orc_sim_get_density(const orc_sim *s, double *rho) { velocity_field(s, NULL, rho); }
-void orc_sim_get_velocity(const orc_sim *s, double *u) { velocity_field(s, u, NULL); }
+void orc_sim_get_density(const orc_sim *s, real *rho) { velocity_field(s, NULL, rho); }
+void orc_sim_get_velocity(const orc_sim *s, real *u) { velocity_field(s, u, NULL); }
