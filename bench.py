@@ -64,6 +64,8 @@ def _args():
                    help="interpolation: -1 automatic, 0 gather at the stencil cells, 1 cell velocities first")
     p.add_argument("--launch-overlap", type=int, default=-1, choices=[-1, 0, 1],
                    help="step kernels with programmatic dependent launch: 1 on, 0 off, -1 automatic")
+    p.add_argument("--collide-staging", type=int, default=-1, choices=[-1, 0, 1],
+                   help="collide populations staged in shared memory by bulk copies: 1 on, 0 off, -1 automatic")
     p.add_argument("--adjoint-only", action="store_true",
                    help="only the config-5 adjoint timing, printed as {\"adjoint\": ...}")
     p.add_argument("--adjoint-steps", type=int, default=None,
@@ -476,10 +478,13 @@ def run_ours(a):
             print(json.dumps({"adjoint": out}), flush=True)
         return
     case = _workload(a)
+    batch = isinstance(case, Batch)
     stream = torch.cuda.Stream()
     sim = _make_sim(case, stream)
     sim.set_interp_mode(a.interp_mode)
     sim.set_launch_overlap(a.launch_overlap)
+    if not batch:
+        sim.set_collide_staging(a.collide_staging)
     sim.set_equilibrium(a.equilibrium)
     sim.set_integrator(a.integrator)
     batch = isinstance(case, Batch)

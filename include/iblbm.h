@@ -47,7 +47,7 @@ typedef enum {
     IBLBM_ERR_CUDA = -3,     /* a CUDA runtime call failed */
     IBLBM_ERR_UNSTABLE = -4, /* density left (0.5, 2) or became NaN */
     IBLBM_ERR_STENCIL = -5,  /* an IBM stencil cell lies beyond a wall */
-    /* -6 is not used: no kernel of the library waits on another */
+    IBLBM_ERR_TIMEOUT = -6,  /* a bounded device wait for staged data gave up */
     IBLBM_ERR_STATE = -7     /* call not valid in the current state */
 } iblbm_status;
 
@@ -115,6 +115,73 @@ int iblbm_create(iblbm_sim **out, int nx, int ny, int nz, double tau,
 int iblbm_batch_create(iblbm_sim **out, const iblbm_run_spec *runs, int n_runs,
                        int precision, int delta_points, void *stream,
                        const iblbm_allocator *alloc);
+
+/* x-slab decomposition of one lattice (the natural split along the flow
+ * direction x; it keeps the walls local).  Creates a group of n_slabs lattice
+ * objects, slab k holding nx/n_slabs (+1 for the first nx mod n_slabs) global
+ * columns starting at x0_k, all on the current device and the given stream,
+ * driven as one lattice of nx*ny*nz cells.  Per time step every slab spreads
+ * the forces of the membranes (which every slab holds, replicated) into its
+ * own cells and collides and streams with its own periodic wrap in x; then
+ * each slab takes the ten boundary columns of the populations with c_x = +1
+ * (at x = 0) from its left neighbour and those with c_x = -1 (at x = w - 1)
+ * from its right one, which turns the wraps into the global streaming of
+ * Eq. (lbequation) (entries the moving-wall bounce-back filled are kept); each
+ * slab interpolates the new velocity over its own cells (a partial sum per
+ * node, Eq. velocityinterpolation) and every slab advances its copy of the
+ * nodes by the sum of the partials taken in slab order (Eq. positionupdate),
+ * so the copies stay identical.  Per step and slab boundary the slabs
+ * exchange 10 ny nz populations, plus 3 numbers per node.  The group takes
+ * the calls of a single lattice for configuration (walls, capsules, moduli,
+ * fluid start, equilibrium order, Euler advection), stepping, iblbm_sync, the
+ * whole-lattice field getters and setter (assembled from the slabs), node
+ * getters and setter, meshes, Taylor deformation and mesh quality; the other
+ * calls return IBLBM_ERR_STATE.  Limits: 1 <= n_slabs <= 64, at least four
+ * columns per slab, otherwise as iblbm_create.  iblbm_get_slab gives the
+ * first global column and the width of slab k. */
+int iblbm_create_slabs(iblbm_sim **out, int nx, int ny, int nz, double tau,
+                       int precision, int delta_points, int n_slabs,
+                       void *stream, const iblbm_allocator *alloc);
+int iblbm_get_slab(const iblbm_sim *sim, int slab, int *x0, int *width);
+
+/* The x-slab step of a group, in the calls a process holding one slab of a
+ * lattice makes between its exchanges with the other processes (over the
+ * host, NCCL or peer copies), for a single lattice object of w columns:
+ *   iblbm_slab_configure  makes it the global columns x0 .. x0 + w - 1 of a
+ *                         periodic lattice of nx_global columns (its IB
+ *                         kernels then take only these columns of each
+ *                         stencil, wrapping with nx_global); before stepping;
+ *   iblbm_slab_step_begin forces, spreading into the slab, collide-and-stream
+ *                         with the slab's own wrap (asynchronous);
+ *   iblbm_slab_get_columns / iblbm_slab_set_columns
+ *                         the ten boundary columns (iblbm_slab_columns_size
+ *                         bytes: the five c_x = +1 populations at x = 0, then
+ *                         the five c_x = -1 at x = w - 1, each [nz][ny], in the
+ *                         storage format) out, and in from the left and right
+ *                         neighbours' outputs;
+ *   iblbm_slab_get_partials
+ *                         this slab's partial node velocities
+ *                         (iblbm_slab_partials_size bytes, a 4-vector of the
+ *                         storage's float type per node);
+ *   iblbm_slab_step_end   the partials of all n_parts slabs, consecutive, in
+ *                         slab order: their sum moves the nodes (Euler) and the
+ *                         step completes.
+ * Buffers are host memory (on_device = 0) or device memory of the object's
+ * device (on_device = 1), owned by the caller.  A group of processes that
+ * calls these in this order with the right neighbours computes what
+ * iblbm_create_slabs computes, bit for bit.  Euler advection and no Taylor
+ * recording (IBLBM_ERR_STATE otherwise); the column and partial calls
+ * synchronise. */
+int iblbm_slab_configure(iblbm_sim *sim, int x0, int nx_global);
+int iblbm_slab_step_begin(iblbm_sim *sim);
+int iblbm_slab_columns_size(iblbm_sim *sim, size_t *bytes);
+int iblbm_slab_get_columns(iblbm_sim *sim, void *out, int on_device);
+int iblbm_slab_set_columns(iblbm_sim *sim, const void *left, const void *right,
+                           int on_device);
+int iblbm_slab_partials_size(iblbm_sim *sim, size_t *bytes);
+int iblbm_slab_get_partials(iblbm_sim *sim, void *out, int on_device);
+int iblbm_slab_step_end(iblbm_sim *sim, const void *parts, int n_parts,
+                        int on_device);
 
 /* Frees all device and host memory of the object (NULL is accepted). */
 int iblbm_destroy(iblbm_sim *sim);
@@ -224,6 +291,29 @@ int iblbm_get_kernel_times(iblbm_sim *sim, double ms_out[3], int64_t *n_steps);
 /* Static name of the collide-and-stream kernel the steps of this object
  * launch (template arguments included), "" for NULL. */
 const char *iblbm_collide_kernel(const iblbm_sim *sim);
+
+/* How the collide-and-stream kernel of a single float or half lattice whose
+ * rows take the vectorised kernel (nx/4 a power of two <= 256, nx times the
+ * element size a multiple of 16 bytes, nx <= 512 for float, <= 1024 for
+ * half) reads its populations (Eq. lbequation
+ * in both): mode 0, every thread loads its 19 populations from global
+ * memory; mode 1, a persistent kernel has the bulk-copy engine stage tiles of
+ * whole rows of all 19 populations in shared memory, the next tile arriving
+ * while the block computes the current one; -1 (default) is mode 0, which
+ * measured faster on GB300 for float and half storage.  The results are the
+ * same bit for bit.  IBLBM_ERR_ARG for another
+ * mode, IBLBM_ERR_STATE for mode 1 on a lattice that cannot take it.
+ * Synchronising. */
+int iblbm_set_collide_staging(iblbm_sim *sim, int mode);
+
+/* Longest time in nanoseconds a kernel waits for data it has staged before it
+ * gives up (default 1e9): the kernel then records IBLBM_ERR_TIMEOUT, waits
+ * (again bounded) for its copies in flight and returns, leaving that step's
+ * populations incomplete; the next synchronising call returns the error.
+ * 0 gives up at the first wait, without polling (to exercise the path).
+ * Only the staged collide waits.  IBLBM_ERR_ARG for a negative limit.
+ * Synchronising. */
+int iblbm_set_device_wait_limit(iblbm_sim *sim, int64_t ns);
 
 /* Sub-step 6 of the step list of Sec. II.C, kept on the device: after every
  * `every`-th step (counted from iblbm_init_fluid; every = 0 switches it off)

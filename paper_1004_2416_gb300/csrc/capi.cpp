@@ -76,6 +76,8 @@ struct iblbm_sim {
     uint8_t *flags[2] = {nullptr, nullptr};
     void *uvel = nullptr;  // velocity of the cells of the flagged tiles (Vec4 per cell)
     int interp_mode = -1;  // -1 automatic, 0 gather at the stencil cells, 1 cell velocities first
+    int staging = -1;      // collide populations staged by bulk copies: -1 automatic, 0 off, 1 on
+    unsigned long long wait_ns = 1000000000ull;  // longest device wait for staged data
     int overlap = -1;      // step kernels overlapping their predecessor: -1 automatic, 0 off, 1 on
     // Method variants: node advection 0 = Euler (Eq. positionupdate), 1 =
     // Adams-Bashforth (Sec. II.C), which needs the node velocities of the step
@@ -172,6 +174,17 @@ struct iblbm_sim {
     bool kernel_timing = false;  // graphs carry event nodes around the kernel groups
     int64_t launches = 0;               // kernels launched for time steps
     int graph_len = 0;
+    // x-slab group (iblbm_create_slabs): the slabs, each a lattice object of
+    // its own holding the global columns L.x0 .. L.x0 + L.nx - 1, with the
+    // membranes replicated on every slab; the group object itself holds no
+    // lattice buffers.
+    std::vector<iblbm_sim *> slabs;
+    void *slab_planes = nullptr;       // packed boundary columns, one block per slab
+    size_t slab_plane_bytes = 0;       // one slab's block
+    void *slab_parts = nullptr;        // node-velocity partials, one Vec4 array per slab
+    void **slab_part_ptrs = nullptr;   // device array of the partials' addresses
+    int slab_parts_nodes = -1;
+    size_t slab_parts_bytes = 0;       // held by slab_parts (per-process slab phases)
     int64_t steps = 0;
     std::string err;
 };
@@ -179,6 +192,10 @@ struct iblbm_sim {
 namespace {
 
 void adj_free(iblbm_sim *s);
+bool is_group(const iblbm_sim *s);
+int group_unsupported(iblbm_sim *s);
+int group_step(iblbm_sim *s, int64_t n_steps);
+int group_field(iblbm_sim *s, int what, double *host, bool set);
 
 int fail(iblbm_sim *s, int code, const std::string &msg) {
     if (s) s->err = msg;
@@ -487,6 +504,17 @@ bool launch_overlap(const iblbm_sim *s) {
     return s->mesh.n_nodes >= 152 * 32;
 }
 
+// Whether the single-lattice collide stages its populations in shared memory
+// by bulk copies: only on request (mode 1).  Measured on the 256x128x128
+// FP16 and 128^3 FP32 lattices the staged kernel is slower than direct loads
+// (86.7 vs 72.1 us and 54.0 vs 46.6 us per launch): with every warp of a block
+// computing the same tile and meeting at its barriers, the issue slots idle
+// that the direct kernel's independent blocks fill.
+bool collide_staged(const iblbm_sim *s) {
+    if (s->batch || !collide_staging_supported(s->prec, s->L)) return false;
+    return s->staging == 1;
+}
+
 bool cell_velocity_first(const iblbm_sim *s) {
     if (s->interp_mode >= 0) return s->interp_mode == 1;
     const double touches = (double)s->mesh.n_nodes * s->delta * s->delta * s->delta;
@@ -533,6 +561,8 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr, 
     a.u_wall = s->u_wall;
     a.status = s->d_status;
     a.eq_order = s->eq_order;
+    a.staged = collide_staged(s);
+    a.wait_ns = s->wait_ns;
     if (s->batch) {
         BatchArgs b{s->d_runs, s->d_items, s->n_items, s->batch_grid, s->batch_pairs};
         launch_collide_batch(s->prec, b, a, s->stream, ov);
@@ -614,7 +644,16 @@ int check_sim(const iblbm_sim *s) { return s ? IBLBM_OK : IBLBM_ERR_ARG; }
 int status_from_bits(int bits) {
     if (bits & 1) return IBLBM_ERR_UNSTABLE;
     if (bits & 2) return IBLBM_ERR_STENCIL;
+    if (bits & 4) return IBLBM_ERR_TIMEOUT;
     return IBLBM_OK;
+}
+
+const char *status_message(int rc) {
+    switch (rc) {
+        case IBLBM_ERR_UNSTABLE: return "density left (0.5, 2) or became non-finite";
+        case IBLBM_ERR_STENCIL: return "an IBM stencil cell lies beyond a wall (z < 0 or z >= nz)";
+        default: return "a device wait for staged populations gave up (results of that step are incomplete)";
+    }
 }
 
 int sync_status(iblbm_sim *s) {
@@ -626,9 +665,7 @@ int sync_status(iblbm_sim *s) {
     if (bits) {
         CK(cudaMemset(s->d_status, 0, sizeof(int)));
         int rc = status_from_bits(bits);
-        return fail(s, rc, rc == IBLBM_ERR_UNSTABLE
-                               ? "density left (0.5, 2) or became non-finite"
-                               : "an IBM stencil cell lies beyond a wall (z < 0 or z >= nz)");
+        return fail(s, rc, status_message(rc));
     }
     return IBLBM_OK;
 }
@@ -686,6 +723,7 @@ const char *iblbm_status_string(int status) {
         case IBLBM_ERR_CUDA: return "IBLBM_ERR_CUDA";
         case IBLBM_ERR_UNSTABLE: return "IBLBM_ERR_UNSTABLE";
         case IBLBM_ERR_STENCIL: return "IBLBM_ERR_STENCIL";
+        case IBLBM_ERR_TIMEOUT: return "IBLBM_ERR_TIMEOUT";
         case IBLBM_ERR_STATE: return "IBLBM_ERR_STATE";
         default: return "IBLBM_ERR_UNKNOWN";
     }
@@ -940,6 +978,16 @@ int iblbm_batch_create(iblbm_sim **out, const iblbm_run_spec *specs, int n_runs,
 }
 
 int iblbm_destroy(iblbm_sim *s) {
+    if (is_group(s)) {
+        cudaStreamSynchronize(s->stream);
+        for (iblbm_sim *p : s->slabs) iblbm_destroy(p);
+        dev_free(s, s->slab_planes);
+        dev_free(s, s->slab_parts);
+        dev_free(s, s->slab_part_ptrs);
+        if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+        delete s;
+        return IBLBM_OK;
+    }
     if (!s) return IBLBM_OK;
     cudaSetDevice(s->device);
     if (s->stream) cudaStreamSynchronize(s->stream);
@@ -955,6 +1003,9 @@ int iblbm_destroy(iblbm_sim *s) {
     dev_free(s, s->d_readback);
     dev_free(s, s->d_scratch);
     dev_free(s, s->d_cksum);
+    dev_free(s, s->slab_planes);
+    dev_free(s, s->slab_parts);
+    dev_free(s, s->slab_part_ptrs);
     dev_free(s, s->d_runs);
     dev_free(s, s->d_items);
     adj_free(s);
@@ -980,6 +1031,15 @@ int iblbm_destroy(iblbm_sim *s) {
 
 int iblbm_get_info(const iblbm_sim *s, iblbm_info *out) {
     if (!s || !out) return IBLBM_ERR_ARG;
+    if (is_group(s)) {
+        int rc = iblbm_get_info(s->slabs[0], out);
+        out->nx = s->L.nx;
+        out->step = s->steps;
+        int64_t launches = 0;
+        for (const iblbm_sim *p : s->slabs) launches += p->launches;
+        out->kernel_launches = launches;
+        return rc;
+    }
     out->nx = s->L.nx;
     out->ny = s->L.ny;
     out->nz = s->L.nz;
@@ -998,6 +1058,14 @@ int iblbm_get_info(const iblbm_sim *s, iblbm_info *out) {
 
 int iblbm_set_shear_walls(iblbm_sim *s, double u_wall) {
     if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s)) {
+        for (iblbm_sim *p : s->slabs) {
+            int rc = iblbm_set_shear_walls(p, u_wall);
+            if (rc) return fail(s, rc, p->err);
+        }
+        s->u_wall = u_wall;
+        return IBLBM_OK;
+    }
     if (!std::isfinite(u_wall) || std::fabs(u_wall) > 0.3)
         return fail(s, IBLBM_ERR_ARG, "wall speed must be finite and |u_wall| <= 0.3");
     s->u_wall = u_wall;
@@ -1015,6 +1083,13 @@ int iblbm_set_shear_walls(iblbm_sim *s, double u_wall) {
 int iblbm_add_capsule_icosphere(iblbm_sim *s, double cx, double cy, double cz, double radius,
                                 int subdivisions, int *capsule_id) {
     if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s)) {  // the membranes are replicated on every slab
+        for (iblbm_sim *p : s->slabs) {
+            int rc = iblbm_add_capsule_icosphere(p, cx, cy, cz, radius, subdivisions, capsule_id);
+            if (rc) return fail(s, rc, p->err);
+        }
+        return IBLBM_OK;
+    }
     if (subdivisions < 0 || subdivisions > 7 || !(radius > 0.0) || !std::isfinite(radius))
         return fail(s, IBLBM_ERR_ARG, "subdivisions must be 0..7 and radius positive");
     std::vector<double> nodes;
@@ -1050,11 +1125,25 @@ int iblbm_taylor_gradient(const double *nodes, int n_nodes, const int32_t *tri, 
 int iblbm_add_capsule_mesh(iblbm_sim *s, const double *ref_xyz, int n_nodes, const int32_t *tri,
                            int n_tri, int *capsule_id) {
     if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s)) {
+        for (iblbm_sim *p : s->slabs) {
+            int rc = iblbm_add_capsule_mesh(p, ref_xyz, n_nodes, tri, n_tri, capsule_id);
+            if (rc) return fail(s, rc, p->err);
+        }
+        return IBLBM_OK;
+    }
     return add_capsule(s, 0, ref_xyz, n_nodes, (const int *)tri, n_tri, capsule_id);
 }
 
 int iblbm_set_skalak(iblbm_sim *s, int capsule_id, double k_s, double C) {
     if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s)) {
+        for (iblbm_sim *p : s->slabs) {
+            int rc = iblbm_set_skalak(p, capsule_id, k_s, C);
+            if (rc) return fail(s, rc, p->err);
+        }
+        return IBLBM_OK;
+    }
     if (!(k_s >= 0.0) || !(C >= 0.0) || !std::isfinite(k_s) || !std::isfinite(C))
         return fail(s, IBLBM_ERR_ARG, "moduli must be finite and non-negative");
     if (capsule_id < -1 || capsule_id >= (int)s->caps.size())
@@ -1089,6 +1178,14 @@ int iblbm_set_skalak(iblbm_sim *s, int capsule_id, double k_s, double C) {
 
 int iblbm_init_fluid(iblbm_sim *s, int mode) {
     if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s)) {
+        for (iblbm_sim *p : s->slabs) {
+            int rc = iblbm_init_fluid(p, mode);
+            if (rc) return fail(s, rc, p->err);
+        }
+        s->steps = 0;
+        return IBLBM_OK;
+    }
     if (mode != 0 && mode != 1) return fail(s, IBLBM_ERR_ARG, "mode must be 0 or 1");
     CK(cudaSetDevice(s->device));
     join_side(s);
@@ -1286,18 +1383,24 @@ extern "C" {
 
 int iblbm_step(iblbm_sim *s, int64_t n_steps) {
     if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s)) {
+        if (n_steps < 0) return fail(s, IBLBM_ERR_ARG, "negative step count");
+        return group_step(s, n_steps);
+    }
     int rc = step_prologue(s, n_steps);
     return rc ? rc : run_steps(s, n_steps, true);
 }
 
 int iblbm_prepare_steps(iblbm_sim *s, int64_t n_steps) {
     if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s)) return group_unsupported(s);
     int rc = step_prologue(s, n_steps);
     return rc ? rc : run_steps(s, n_steps, false);
 }
 
 int iblbm_set_kernel_timing(iblbm_sim *s, int on) {
     if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s)) return group_unsupported(s);
     if (on != 0 && on != 1) return fail(s, IBLBM_ERR_ARG, "on must be 0 or 1");
     CK(cudaSetDevice(s->device));
     join_side(s);
@@ -1309,6 +1412,7 @@ int iblbm_set_kernel_timing(iblbm_sim *s, int on) {
 
 int iblbm_get_kernel_times(iblbm_sim *s, double ms_out[3], int64_t *n_steps) {
     if (!s || !ms_out) return IBLBM_ERR_ARG;
+    if (is_group(s)) return group_unsupported(s);
     int rc = sync_status(s);
     if (rc) return rc;
     double acc[3] = {0, 0, 0};
@@ -1331,8 +1435,37 @@ int iblbm_get_kernel_times(iblbm_sim *s, double ms_out[3], int64_t *n_steps) {
 
 const char *iblbm_collide_kernel(const iblbm_sim *s) {
     if (!s) return "";
+    if (is_group(s)) return iblbm_collide_kernel(s->slabs[0]);
     if (s->batch) return collide_batch_kernel_name(s->prec, s->batch_pairs);
-    return collide_kernel_name(s->prec, s->L);
+    return collide_kernel_name(s->prec, s->L, collide_staged(s));
+}
+
+int iblbm_set_collide_staging(iblbm_sim *s, int mode) {
+    if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s)) return group_unsupported(s);
+    if (mode < -1 || mode > 1) return fail(s, IBLBM_ERR_ARG, "mode must be -1, 0 or 1");
+    if (mode == 1 && (s->batch || !collide_staging_supported(s->prec, s->L)))
+        return fail(s, IBLBM_ERR_STATE,
+                    "staged collide needs a single float or half lattice with nx/4 a power of two <= 256 and "
+                    "nx times the element size a multiple of 16 bytes");
+    CK(cudaSetDevice(s->device));
+    join_side(s);
+    CK(cudaStreamSynchronize(s->stream));
+    drop_graphs(s);
+    s->staging = mode;
+    return IBLBM_OK;
+}
+
+int iblbm_set_device_wait_limit(iblbm_sim *s, int64_t ns) {
+    if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s)) return group_unsupported(s);
+    if (ns < 0) return fail(s, IBLBM_ERR_ARG, "the limit must be >= 0 ns");
+    CK(cudaSetDevice(s->device));
+    join_side(s);
+    CK(cudaStreamSynchronize(s->stream));
+    drop_graphs(s);
+    s->wait_ns = (unsigned long long)ns;
+    return IBLBM_OK;
 }
 
 }  // extern "C"
@@ -1410,6 +1543,7 @@ extern "C" {
 
 int iblbm_adjoint_forward(iblbm_sim *s, int64_t n_steps, int checkpoint_every) {
     if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s)) return group_unsupported(s);
     if (s->batch) return fail(s, IBLBM_ERR_STATE, "the adjoint works on a single lattice");
     if (s->caps.size() != 1) return fail(s, IBLBM_ERR_STATE, "the adjoint needs exactly one capsule");
     if (s->integrator != 0 || s->eq_order != 2)
@@ -1455,6 +1589,7 @@ int iblbm_adjoint_forward(iblbm_sim *s, int64_t n_steps, int checkpoint_every) {
 int iblbm_adjoint_backward(iblbm_sim *s, int capsule_id, double *D_out, double *dD_dks, double *dD_duw,
                            double *dD_dX0, double *dD_dx0) {
     if (!s || !D_out) return IBLBM_ERR_ARG;
+    if (is_group(s)) return group_unsupported(s);
     iblbm_sim::Adjoint &A = s->adj;
     if (!A.ready || s->steps != A.t_start + A.n || s->mesh_dirty)
         return fail(s, IBLBM_ERR_STATE, "run iblbm_adjoint_forward first, with no step since");
@@ -1726,6 +1861,7 @@ int iblbm_adjoint_backward(iblbm_sim *s, int capsule_id, double *D_out, double *
 
 int iblbm_set_taylor_recording(iblbm_sim *s, int every, int ring) {
     if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s)) return group_unsupported(s);
     if (every < 0 || (every > 0 && (ring < 1 || ring > (1 << 24))))
         return fail(s, IBLBM_ERR_ARG, "every must be >= 0 and ring in 1..2^24");
     CK(cudaSetDevice(s->device));
@@ -1743,6 +1879,7 @@ static void taylor_from_sums(const double r[12], double out[16]);
 int iblbm_get_taylor_records(iblbm_sim *s, int capsule_id, int max_records, double *out,
                              int64_t *steps_out, int *n_out) {
     if (!s || !n_out || max_records < 0) return IBLBM_ERR_ARG;
+    if (is_group(s)) return group_unsupported(s);
     if (capsule_id < 0 || capsule_id >= (int)s->caps.size()) return fail(s, IBLBM_ERR_ARG, "no such capsule");
     int rc = sync_status(s);
     if (rc) return rc;
@@ -1767,6 +1904,7 @@ int iblbm_get_taylor_records(iblbm_sim *s, int capsule_id, int max_records, doub
 
 int iblbm_profile_kernels(iblbm_sim *s, int n_steps, double ms_out[4]) {
     if (!s || !ms_out || n_steps < 1 || n_steps > 100000) return IBLBM_ERR_ARG;
+    if (is_group(s)) return group_unsupported(s);
     CK(cudaSetDevice(s->device));
     int rc = ensure_mesh(s);
     if (rc) return rc;
@@ -1797,6 +1935,14 @@ int iblbm_profile_kernels(iblbm_sim *s, int n_steps, double ms_out[4]) {
 
 int iblbm_sync(iblbm_sim *s) {
     if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s)) {
+        int first = IBLBM_OK;
+        for (iblbm_sim *p : s->slabs) {
+            int rc = sync_status(p);
+            if (rc && !first) first = fail(s, rc, p->err);
+        }
+        return first;
+    }
     return sync_status(s);
 }
 
@@ -1825,6 +1971,7 @@ int iblbm_ellipsoid_fit(const double *nodes, int n_nodes, const double center[3]
 
 int iblbm_mesh_quality(iblbm_sim *s, int capsule_id, double out[4]) {
     if (!s || !out) return IBLBM_ERR_ARG;
+    if (is_group(s)) return iblbm_mesh_quality(s->slabs[0], capsule_id, out);
     if (capsule_id < 0 || capsule_id >= (int)s->caps.size()) return fail(s, IBLBM_ERR_ARG, "no such capsule");
     const Capsule &c = s->caps[capsule_id];
     std::vector<double> x(3 * (size_t)c.n_nodes);
@@ -1841,6 +1988,10 @@ int iblbm_mesh_quality(iblbm_sim *s, int capsule_id, double out[4]) {
 
 int iblbm_set_integrator(iblbm_sim *s, int mode) {
     if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s)) {
+        if (mode != 0) return fail(s, IBLBM_ERR_STATE, "a slab group advects by Euler's rule only");
+        return IBLBM_OK;
+    }
     if (mode != 0 && mode != 1) return fail(s, IBLBM_ERR_ARG, "integrator must be 0 (Euler) or 1 (Adams-Bashforth)");
     join_side(s);
     CK(cudaStreamSynchronize(s->stream));
@@ -1853,6 +2004,13 @@ int iblbm_set_integrator(iblbm_sim *s, int mode) {
 
 int iblbm_set_equilibrium(iblbm_sim *s, int order) {
     if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s)) {
+        for (iblbm_sim *p : s->slabs) {
+            int rc = iblbm_set_equilibrium(p, order);
+            if (rc) return fail(s, rc, p->err);
+        }
+        return IBLBM_OK;
+    }
     if (order != 1 && order != 2) return fail(s, IBLBM_ERR_ARG, "equilibrium order must be 1 or 2");
     join_side(s);
     CK(cudaStreamSynchronize(s->stream));
@@ -1864,6 +2022,7 @@ int iblbm_set_equilibrium(iblbm_sim *s, int order) {
 
 int iblbm_set_interp_mode(iblbm_sim *s, int mode) {
     if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s)) return group_unsupported(s);
     if (mode < -1 || mode > 1) return fail(s, IBLBM_ERR_ARG, "mode must be -1, 0 or 1");
     join_side(s);
     CK(cudaStreamSynchronize(s->stream));
@@ -1874,6 +2033,7 @@ int iblbm_set_interp_mode(iblbm_sim *s, int mode) {
 
 int iblbm_set_launch_overlap(iblbm_sim *s, int mode) {
     if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s)) return group_unsupported(s);
     if (mode < -1 || mode > 1) return fail(s, IBLBM_ERR_ARG, "mode must be -1, 0 or 1");
     join_side(s);
     CK(cudaStreamSynchronize(s->stream));
@@ -1895,6 +2055,7 @@ int check_run(iblbm_sim *s, int run) {
 // 3 force density [3][cells]
 int lattice_get(iblbm_sim *s, int run, int what, double *host_out) {
     if (!s || !host_out) return IBLBM_ERR_ARG;
+    if (is_group(s)) return group_unsupported(s);
     int rc = check_run(s, run);
     if (rc) return rc;
     rc = sync_status(s);
@@ -1919,6 +2080,7 @@ int lattice_get(iblbm_sim *s, int run, int what, double *host_out) {
 
 int lattice_set_populations(iblbm_sim *s, int run, const double *host_in) {
     if (!s || !host_in) return IBLBM_ERR_ARG;
+    if (is_group(s)) return group_unsupported(s);
     int rc = check_run(s, run);
     if (rc) return rc;
     rc = sync_status(s);
@@ -1948,22 +2110,27 @@ int whole_lattice_only(iblbm_sim *s) {
 extern "C" {
 
 int iblbm_get_velocity(iblbm_sim *s, double *out) {
+    if (is_group(s)) return out ? group_field(s, 0, out, false) : IBLBM_ERR_ARG;
     int rc = whole_lattice_only(s);
     return rc ? rc : lattice_get(s, 0, 0, out);
 }
 int iblbm_get_density(iblbm_sim *s, double *out) {
+    if (is_group(s)) return out ? group_field(s, 1, out, false) : IBLBM_ERR_ARG;
     int rc = whole_lattice_only(s);
     return rc ? rc : lattice_get(s, 0, 1, out);
 }
 int iblbm_get_populations(iblbm_sim *s, double *out) {
+    if (is_group(s)) return out ? group_field(s, 2, out, false) : IBLBM_ERR_ARG;
     int rc = whole_lattice_only(s);
     return rc ? rc : lattice_get(s, 0, 2, out);
 }
 int iblbm_get_force_field(iblbm_sim *s, double *out) {
+    if (is_group(s)) return out ? group_field(s, 3, out, false) : IBLBM_ERR_ARG;
     int rc = whole_lattice_only(s);
     return rc ? rc : lattice_get(s, 0, 3, out);
 }
 int iblbm_set_populations(iblbm_sim *s, const double *in) {
+    if (is_group(s)) return in ? group_field(s, 2, const_cast<double *>(in), true) : IBLBM_ERR_ARG;
     int rc = whole_lattice_only(s);
     return rc ? rc : lattice_set_populations(s, 0, in);
 }
@@ -1976,6 +2143,7 @@ int iblbm_set_run_populations(iblbm_sim *s, int run, const double *in) {
 int iblbm_add_capsule_icosphere_in_run(iblbm_sim *s, int run, double cx, double cy, double cz,
                                        double radius, int subdivisions, int *capsule_id) {
     if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s)) return group_unsupported(s);
     if (subdivisions < 0 || subdivisions > 7 || !(radius > 0.0) || !std::isfinite(radius))
         return fail(s, IBLBM_ERR_ARG, "subdivisions must be 0..7 and radius positive");
     std::vector<double> nodes;
@@ -2001,6 +2169,7 @@ int iblbm_get_run_tile(const iblbm_sim *s, int run, int *tx, int *ty) {
 
 int iblbm_autotune_tiles(iblbm_sim *s, int repeats) {
     if (!s || repeats < 1 || repeats > 1000) return IBLBM_ERR_ARG;
+    if (is_group(s)) return group_unsupported(s);
     if (!s->batch) return IBLBM_OK;  // a single lattice has fixed kernels
     if (s->steps != 0) return fail(s, IBLBM_ERR_STATE, "tile autotuning must precede the first step");
     CK(cudaSetDevice(s->device));
@@ -2076,6 +2245,7 @@ int iblbm_autotune_tiles(iblbm_sim *s, int repeats) {
 
 static int node_get(iblbm_sim *s, int id, int which, double *host_out) {
     if (!s || !host_out) return IBLBM_ERR_ARG;
+    if (is_group(s)) return node_get(s->slabs[0], id, which, host_out);
     int rc = sync_status(s);
     if (rc) return rc;
     int first, count;
@@ -2099,6 +2269,13 @@ int iblbm_get_node_velocities(iblbm_sim *s, int id, double *out) { return node_g
 
 int iblbm_set_nodes(iblbm_sim *s, int id, const double *host_in) {
     if (!s || !host_in) return IBLBM_ERR_ARG;
+    if (is_group(s)) {
+        for (iblbm_sim *p : s->slabs) {
+            int rc = iblbm_set_nodes(p, id, host_in);
+            if (rc) return fail(s, rc, p->err);
+        }
+        return IBLBM_OK;
+    }
     int rc = sync_status(s);
     if (rc) return rc;
     int first, count;
@@ -2121,6 +2298,7 @@ int iblbm_set_nodes(iblbm_sim *s, int id, const double *host_in) {
 
 int iblbm_get_mesh(iblbm_sim *s, int id, int *n_nodes, int *n_tri, int32_t *tri_out) {
     if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s)) return iblbm_get_mesh(s->slabs[0], id, n_nodes, n_tri, tri_out);
     if (id < 0 || id >= (int)s->caps.size()) return fail(s, IBLBM_ERR_ARG, "no such capsule");
     const Capsule &c = s->caps[id];
     if (n_nodes) *n_nodes = c.n_nodes;
@@ -2132,6 +2310,7 @@ int iblbm_get_mesh(iblbm_sim *s, int id, int *n_nodes, int *n_tri, int32_t *tri_
 
 int iblbm_get_taylor(iblbm_sim *s, int id, double out[16]) {
     if (!s || !out) return IBLBM_ERR_ARG;
+    if (is_group(s)) return iblbm_get_taylor(s->slabs[0], id, out);
     if (id < 0 || id >= (int)s->caps.size()) return fail(s, IBLBM_ERR_ARG, "no such capsule");
     int rc = sync_status(s);
     if (rc) return rc;
@@ -2148,6 +2327,7 @@ int iblbm_get_taylor(iblbm_sim *s, int id, double out[16]) {
 
 int iblbm_read_async(iblbm_sim *s, double *host_nodes, double *host_sums) {
     if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s)) return group_unsupported(s);
     CK(cudaSetDevice(s->device));
     int rc = ensure_mesh(s);
     if (rc) return rc;
@@ -2188,6 +2368,7 @@ int iblbm_taylor_from_sums(const double sums[12], double out[16]) {
 int iblbm_adjoint_taylor(iblbm_sim *s, int capsule_id, int64_t n_steps, int checkpoint_every, double *dD_dks,
                          double *dD_dCa, double *dD_dX0, double *D) {
     if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s)) return group_unsupported(s);
     if (capsule_id != 0 || s->caps.size() != 1) return fail(s, IBLBM_ERR_ARG, "no such capsule");
     int rc = iblbm_adjoint_forward(s, n_steps, checkpoint_every);
     if (rc) return rc;
@@ -2341,6 +2522,7 @@ extern "C" {
 
 int iblbm_checkpoint_size(iblbm_sim *s, size_t *bytes) {
     if (!s || !bytes) return IBLBM_ERR_ARG;
+    if (is_group(s)) return group_unsupported(s);
     CK(cudaSetDevice(s->device));
     int rc = ensure_mesh(s);
     if (rc) return rc;
@@ -2350,6 +2532,7 @@ int iblbm_checkpoint_size(iblbm_sim *s, size_t *bytes) {
 
 int iblbm_checkpoint_save(iblbm_sim *s, void *buf, int on_device) {
     if (!s || !buf) return IBLBM_ERR_ARG;
+    if (is_group(s)) return group_unsupported(s);
     int rc = sync_status(s);
     if (rc) return rc;
     rc = ensure_mesh(s);
@@ -2386,6 +2569,7 @@ int iblbm_checkpoint_save(iblbm_sim *s, void *buf, int on_device) {
 
 int iblbm_checkpoint_restore(iblbm_sim *s, const void *buf, size_t buf_bytes, int on_device) {
     if (!s || !buf) return IBLBM_ERR_ARG;
+    if (is_group(s)) return group_unsupported(s);
     int rc = sync_status(s);
     if (rc) return rc;
     rc = ensure_mesh(s);
@@ -2473,3 +2657,386 @@ static void taylor_from_sums(const double r[12], double out[16]) {
     out[9] = r[4];
     for (int k = 0; k < 6; ++k) out[10 + k] = r[5 + k];
 }
+
+// ---- x-slab decomposition -------------------------------------------------------------
+//
+// A group of P slab objects covers one periodic lattice of nx columns: slab p
+// holds the global columns x0_p .. x0_p + w_p - 1.  Per time step (the
+// sub-step list of Sec. II.C), on the group's stream:
+//   1. every slab: membrane forces of the replicated membranes and spreading
+//      into its own cells (Eq. forcespreading), then collide and stream with
+//      its own periodic wrap in x (Eq. lbequation);
+//   2. the ten boundary columns of every slab are packed, and every slab takes
+//      its c_x = +1 column x = 0 from its left neighbour and its c_x = -1 column
+//      x = w_p - 1 from its right one: the wraps become the global streaming;
+//   3. every slab interpolates the new lattice velocity over its own cells
+//      (Eq. velocityinterpolation, a partial sum per node);
+//   4. every slab adds the P partials in slab order and advances its copy of
+//      the nodes (Eq. positionupdate), so all copies stay identical.
+// The exchange is 10 ny nz populations per slab boundary plus 3 numbers per
+// node, the data the slabs of several GPUs would send each other.
+namespace {
+
+bool is_group(const iblbm_sim *s) { return s && !s->slabs.empty(); }
+
+int group_unsupported(iblbm_sim *s) {
+    return fail(s, IBLBM_ERR_STATE, "not available on a slab group (x-slab decomposition)");
+}
+
+int group_each(iblbm_sim *s, int (*fn)(iblbm_sim *, void *), void *arg) {
+    for (iblbm_sim *p : s->slabs) {
+        int rc = fn(p, arg);
+        if (rc) return fail(s, rc, std::string("slab: ") + p->err);
+    }
+    return IBLBM_OK;
+}
+
+int group_ensure_buffers(iblbm_sim *s) {
+    iblbm_sim *p0 = s->slabs[0];
+    const int P = (int)s->slabs.size();
+    if (!s->slab_planes) {
+        const size_t el = s->prec == kF64 ? 8 : (s->prec == kF32 ? 4 : 2);
+        s->slab_plane_bytes = (10 * el * (size_t)s->L.ny * s->L.nz + 255) & ~(size_t)255;
+        s->slab_planes = dev_alloc(s, s->slab_plane_bytes * P);
+        if (!s->slab_planes) return fail(s, IBLBM_ERR_OOM, "slab exchange buffer allocation failed");
+    }
+    const int nn = p0->mesh.n_nodes;
+    if (s->slab_parts_nodes != nn) {
+        dev_free(s, s->slab_parts);
+        dev_free(s, s->slab_part_ptrs);
+        const size_t v4 = (4 * real_bytes(p0) * (size_t)std::max(nn, 1) + 255) & ~(size_t)255;
+        s->slab_parts = dev_alloc(s, v4 * P);
+        s->slab_part_ptrs = (void **)dev_alloc(s, sizeof(void *) * P);
+        if (!s->slab_parts || !s->slab_part_ptrs) return fail(s, IBLBM_ERR_OOM, "slab partials allocation failed");
+        std::vector<void *> ptrs(P);
+        for (int k = 0; k < P; ++k) ptrs[k] = (char *)s->slab_parts + k * v4;
+        CK(cudaMemcpyAsync(s->slab_part_ptrs, ptrs.data(), sizeof(void *) * P, cudaMemcpyHostToDevice, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+        s->slab_parts_nodes = nn;
+    }
+    return IBLBM_OK;
+}
+
+int group_step(iblbm_sim *s, int64_t n_steps) {
+    const int P = (int)s->slabs.size();
+    for (iblbm_sim *p : s->slabs) {
+        CK(cudaSetDevice(p->device));
+        int rc = ensure_mesh(p);
+        if (rc) return fail(s, rc, std::string("slab: ") + p->err);
+    }
+    int rc = group_ensure_buffers(s);
+    if (rc) return rc;
+    iblbm_sim *p0 = s->slabs[0];
+    const size_t v4 = (4 * real_bytes(p0) * (size_t)std::max(p0->mesh.n_nodes, 1) + 255) & ~(size_t)255;
+    cudaGetLastError();
+    for (int64_t t = 0; t < n_steps; ++t) {
+        for (iblbm_sim *p : s->slabs) {
+            const int c = p->cur, n = 1 - p->cur;
+            launch_force_spread_slab(p->prec, p->delta, p->L, p->mesh, p->force[n], p->flags[n], p->d_status,
+                                     p->stream);
+            CollideArgs a;
+            a.src = p->pop[c];
+            a.dst = p->pop[n];
+            a.fcur = p->force[n];
+            a.flag_cur = p->flags[n];
+            a.fold = p->force[c];
+            a.flag_old = p->flags[c];
+            a.tau = p->tau;
+            a.u_wall = p->u_wall;
+            a.status = p->d_status;
+            a.eq_order = p->eq_order;
+            launch_collide_stream(p->prec, p->L, a, p->stream, false);
+        }
+        for (int k = 0; k < P; ++k) {
+            iblbm_sim *p = s->slabs[k];
+            launch_plane_pack(p->prec, p->L, p->pop[1 - p->cur], (char *)s->slab_planes + k * s->slab_plane_bytes,
+                              p->stream);
+        }
+        for (int k = 0; k < P; ++k) {
+            iblbm_sim *p = s->slabs[k];
+            const char *base = (const char *)s->slab_planes;
+            launch_plane_unpack(p->prec, p->L, p->pop[1 - p->cur], base + ((k + P - 1) % P) * s->slab_plane_bytes,
+                                base + ((k + 1) % P) * s->slab_plane_bytes, p->stream);
+        }
+        for (int k = 0; k < P; ++k) {
+            iblbm_sim *p = s->slabs[k];
+            const int n = 1 - p->cur;
+            launch_interp_partial_slab(p->prec, p->delta, p->L, p->mesh, p->pop[n], p->force[n],
+                                       (char *)s->slab_parts + k * v4, p->stream);
+        }
+        for (iblbm_sim *p : s->slabs) {
+            launch_slab_advect(p->prec, p->mesh, (const void *const *)s->slab_part_ptrs, P, p->stream);
+            p->cur = 1 - p->cur;
+            p->steps++;
+            p->ab2_ready = true;
+            p->launches += 5;
+        }
+        s->steps++;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(s, e, "slab step launch");
+    }
+    return IBLBM_OK;
+}
+
+// A global field [comp][nz][ny][nx] from (get) or to (set) the slabs' own
+// [comp][nz][ny][w] fields.
+int group_field(iblbm_sim *s, int what, double *host, bool set) {
+    const int nx = s->L.nx, ny = s->L.ny, nz = s->L.nz;
+    const int comps = what == 1 ? 1 : (what == 2 ? 19 : 3);
+    const size_t rows = (size_t)comps * nz * ny;
+    for (iblbm_sim *p : s->slabs) {
+        const int w = p->L.nx, x0 = p->L.x0;
+        std::vector<double> part(rows * w);
+        if (set)
+            for (size_t r = 0; r < rows; ++r) std::memcpy(&part[r * w], host + r * nx + x0, sizeof(double) * w);
+        const int rc = set ? lattice_set_populations(p, 0, part.data()) : lattice_get(p, 0, what, part.data());
+        if (rc) return fail(s, rc, std::string("slab: ") + p->err);
+        if (!set)
+            for (size_t r = 0; r < rows; ++r) std::memcpy(host + r * nx + x0, &part[r * w], sizeof(double) * w);
+    }
+    return IBLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int iblbm_create_slabs(iblbm_sim **out, int nx, int ny, int nz, double tau, int precision, int delta_points,
+                       int n_slabs, void *stream, const iblbm_allocator *alloc) {
+    if (!out) return IBLBM_ERR_ARG;
+    *out = nullptr;
+    g_create_error.clear();
+    if (n_slabs < 1 || n_slabs > 64 || nx < 4 * n_slabs) {
+        g_create_error = "need 1 <= n_slabs <= 64 and at least 4 columns per slab";
+        return IBLBM_ERR_ARG;
+    }
+    if (ny < 1 || nz < 1 || (long long)nx * ny * nz > 2147483647LL || !(tau > 0.5) || !std::isfinite(tau) ||
+        precision < 0 || precision > 2 || delta_points < 2 || delta_points > 4 ||
+        (alloc && (!alloc->alloc || !alloc->free))) {
+        g_create_error = "lattice, tau, precision, stencil or allocator out of range (as iblbm_create)";
+        return IBLBM_ERR_ARG;
+    }
+    int rc = IBLBM_OK;
+    iblbm_sim *s = new (std::nothrow) iblbm_sim();
+    if (!s) return IBLBM_ERR_OOM;
+    s->L = make_lattice(nx, ny, nz, precision != kF64);
+    s->prec = precision;
+    s->delta = delta_points;
+    s->tau = tau;
+    cudaGetDevice(&s->device);
+    if (alloc) {
+        s->alloc = *alloc;
+        s->has_alloc = true;
+    }
+    if (stream) {
+        s->stream = (cudaStream_t)stream;
+    } else if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        g_create_error = "cudaStreamCreate failed";
+        return IBLBM_ERR_CUDA;
+    } else {
+        s->own_stream = true;
+    }
+    int x0 = 0;
+    for (int k = 0; k < n_slabs; ++k) {
+        const int w = nx / n_slabs + (k < nx % n_slabs ? 1 : 0);
+        iblbm_sim *p = nullptr;
+        rc = iblbm_create(&p, w, ny, nz, tau, precision, delta_points, (void *)s->stream, alloc);
+        if (rc) {
+            iblbm_destroy(s);
+            return rc;
+        }
+        p->L.x0 = x0;
+        p->L.gnx = nx;
+        s->slabs.push_back(p);
+        x0 += w;
+    }
+    *out = s;
+    return IBLBM_OK;
+}
+
+int iblbm_get_slab(const iblbm_sim *s, int slab, int *x0, int *width) {
+    if (!s || !is_group(s) || slab < 0 || slab >= (int)s->slabs.size()) return IBLBM_ERR_ARG;
+    if (x0) *x0 = s->slabs[slab]->L.x0;
+    if (width) *width = s->slabs[slab]->L.nx;
+    return IBLBM_OK;
+}
+
+}  // extern "C"
+
+// ---- x-slab phases for drivers that hold one slab per process ------------------------------
+// The group step above, split into the calls a process holding one slab of a
+// lattice makes between its exchanges with the other processes (over the
+// host, NCCL or peer copies): begin (forces, spreading, collide-and-stream),
+// the boundary columns out and the neighbours' in, the partial node
+// velocities out, and the end of the step with every slab's partials.
+namespace {
+
+int slab_phase_check(iblbm_sim *s) {
+    if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s) || s->batch) return fail(s, IBLBM_ERR_STATE, "slab phases take a single lattice object");
+    return IBLBM_OK;
+}
+
+size_t slab_column_bytes(const iblbm_sim *s) {
+    const size_t el = s->prec == kF64 ? 8 : (s->prec == kF32 ? 4 : 2);
+    return 10 * el * (size_t)s->L.ny * s->L.nz;
+}
+
+size_t slab_part_bytes(const iblbm_sim *s) { return 4 * real_bytes(s) * (size_t)s->mesh.n_nodes; }
+
+int slab_buffers(iblbm_sim *s, size_t parts_bytes) {
+    if (!s->slab_planes) {
+        s->slab_plane_bytes = (slab_column_bytes(s) + 255) & ~(size_t)255;
+        s->slab_planes = dev_alloc(s, 3 * s->slab_plane_bytes);  // own, left, right
+        if (!s->slab_planes) return fail(s, IBLBM_ERR_OOM, "slab column buffer allocation failed");
+    }
+    const size_t pb = std::max<size_t>(parts_bytes, 16);
+    if (s->slab_parts_bytes < pb) {
+        CK(cudaStreamSynchronize(s->stream));  // a pending step may still read the old buffer
+        dev_free(s, s->slab_parts);
+        s->slab_parts = dev_alloc(s, pb);
+        s->slab_parts_bytes = s->slab_parts ? pb : 0;
+        if (!s->slab_parts) return fail(s, IBLBM_ERR_OOM, "slab partials allocation failed");
+    }
+    if (!s->slab_part_ptrs) {
+        s->slab_part_ptrs = (void **)dev_alloc(s, sizeof(void *) * 64);
+        if (!s->slab_part_ptrs) return fail(s, IBLBM_ERR_OOM, "slab pointer table allocation failed");
+    }
+    return IBLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int iblbm_slab_configure(iblbm_sim *s, int x0, int nx_global) {
+    if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s) || s->batch) return fail(s, IBLBM_ERR_STATE, "a slab is a single lattice object");
+    if (x0 < 0 || nx_global < s->L.nx || x0 + s->L.nx > nx_global || s->L.nx < 4)
+        return fail(s, IBLBM_ERR_ARG, "need 0 <= x0, x0 + nx <= nx_global and nx >= 4");
+    CK(cudaSetDevice(s->device));
+    join_side(s);
+    CK(cudaStreamSynchronize(s->stream));
+    drop_graphs(s);
+    s->L.x0 = x0;
+    s->L.gnx = nx_global;
+    return IBLBM_OK;
+}
+
+int iblbm_slab_step_begin(iblbm_sim *s) {
+    int rc = slab_phase_check(s);
+    if (rc) return rc;
+    if (s->rec_every > 0 || s->integrator != 0)
+        return fail(s, IBLBM_ERR_STATE, "slab phases take Euler advection and no Taylor recording");
+    CK(cudaSetDevice(s->device));
+    rc = ensure_mesh(s);
+    if (rc) return rc;
+    const int c = s->cur, n = 1 - s->cur;
+    launch_force_spread_slab(s->prec, s->delta, s->L, s->mesh, s->force[n], s->flags[n], s->d_status, s->stream);
+    CollideArgs a;
+    a.src = s->pop[c];
+    a.dst = s->pop[n];
+    a.fcur = s->force[n];
+    a.flag_cur = s->flags[n];
+    a.fold = s->force[c];
+    a.flag_old = s->flags[c];
+    a.tau = s->tau;
+    a.u_wall = s->u_wall;
+    a.status = s->d_status;
+    a.eq_order = s->eq_order;
+    launch_collide_stream(s->prec, s->L, a, s->stream, false);
+    CK(cudaGetLastError());
+    return IBLBM_OK;
+}
+
+int iblbm_slab_columns_size(iblbm_sim *s, size_t *bytes) {
+    if (!s || !bytes) return IBLBM_ERR_ARG;
+    *bytes = slab_column_bytes(s);
+    return IBLBM_OK;
+}
+
+int iblbm_slab_get_columns(iblbm_sim *s, void *out, int on_device) {
+    int rc = slab_phase_check(s);
+    if (rc) return rc;
+    if (!out) return IBLBM_ERR_ARG;
+    rc = slab_buffers(s, 0);
+    if (rc) return rc;
+    launch_plane_pack(s->prec, s->L, s->pop[1 - s->cur], s->slab_planes, s->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, s->slab_planes, slab_column_bytes(s),
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return IBLBM_OK;
+}
+
+int iblbm_slab_set_columns(iblbm_sim *s, const void *left, const void *right, int on_device) {
+    int rc = slab_phase_check(s);
+    if (rc) return rc;
+    if (!left || !right) return IBLBM_ERR_ARG;
+    rc = slab_buffers(s, 0);
+    if (rc) return rc;
+    const size_t b = slab_column_bytes(s);
+    char *l = (char *)s->slab_planes + s->slab_plane_bytes, *r = l + s->slab_plane_bytes;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(l, left, b, k, s->stream));
+    CK(cudaMemcpyAsync(r, right, b, k, s->stream));
+    launch_plane_unpack(s->prec, s->L, s->pop[1 - s->cur], l, r, s->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s->stream));
+    return IBLBM_OK;
+}
+
+int iblbm_slab_partials_size(iblbm_sim *s, size_t *bytes) {
+    if (!s || !bytes) return IBLBM_ERR_ARG;
+    int rc = ensure_mesh(s);
+    if (rc) return rc;
+    *bytes = slab_part_bytes(s);
+    return IBLBM_OK;
+}
+
+int iblbm_slab_get_partials(iblbm_sim *s, void *out, int on_device) {
+    int rc = slab_phase_check(s);
+    if (rc) return rc;
+    if (!out) return IBLBM_ERR_ARG;
+    const size_t pb = slab_part_bytes(s);
+    rc = slab_buffers(s, pb);
+    if (rc) return rc;
+    const int n = 1 - s->cur;
+    launch_interp_partial_slab(s->prec, s->delta, s->L, s->mesh, s->pop[n], s->force[n], s->slab_parts, s->stream);
+    CK(cudaGetLastError());
+    if (pb)
+        CK(cudaMemcpyAsync(out, s->slab_parts, pb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return IBLBM_OK;
+}
+
+int iblbm_slab_step_end(iblbm_sim *s, const void *parts, int n_parts, int on_device) {
+    int rc = slab_phase_check(s);
+    if (rc) return rc;
+    if (!parts || n_parts < 1 || n_parts > 64) return fail(s, IBLBM_ERR_ARG, "need 1..64 partial arrays");
+    const size_t pb = slab_part_bytes(s);
+    rc = slab_buffers(s, pb * (n_parts + 1));
+    if (rc) return rc;
+    // the partials after this slab's own, then their addresses
+    char *base = (char *)s->slab_parts + pb;
+    CK(cudaMemcpyAsync(base, parts, pb * n_parts, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       s->stream));
+    std::vector<void *> ptrs(n_parts);
+    for (int k = 0; k < n_parts; ++k) ptrs[k] = base + k * pb;
+    CK(cudaMemcpyAsync(s->slab_part_ptrs, ptrs.data(), sizeof(void *) * n_parts, cudaMemcpyHostToDevice,
+                       s->stream));
+    launch_slab_advect(s->prec, s->mesh, (const void *const *)s->slab_part_ptrs, n_parts, s->stream);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // the pointer table is host memory's copy
+    if (e != cudaSuccess) return cuda_fail(s, e, "slab advection");
+    s->cur = 1 - s->cur;
+    s->steps++;
+    s->ab2_ready = true;
+    s->launches += 5;
+    return IBLBM_OK;
+}
+
+}  // extern "C"

@@ -181,6 +181,9 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)
 __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
+// Makes mbarrier initialisations visible to the other threads and to the
+// bulk-copy engine (followed by a block barrier).
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 // Orders this thread's generic-proxy shared-memory accesses (an mbarrier
 // init, reads of a buffer about to be refilled) before later bulk copies.
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -211,10 +214,11 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 // Waits for phase `parity` of `bar`, giving up after limit_ns nanoseconds
-// (0: one try only).  Returns whether the phase completed.
+// (0: gives up at once, without polling, so that the failure path can be
+// exercised deterministically).  Returns whether the phase completed.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, unsigned parity, unsigned long long limit_ns) {
-    if (mbar_try_wait(bar, parity)) return true;
     if (limit_ns == 0) return false;
+    if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(bar, parity))
         if (global_ns() - t0 > limit_ns) return false;

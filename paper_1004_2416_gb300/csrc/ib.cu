@@ -56,7 +56,7 @@ namespace iblbm {
 // node's n^2 stencil rows.  Four nodes per warp waste fewer lanes on the faces
 // (a node has five or six) when there are enough nodes to fill the GPU; one
 // node per warp keeps more warps in flight otherwise.
-template <int N, typename T, int NPW>
+template <int N, typename T, int NPW, bool SLAB = false>
 __global__ void __launch_bounds__(256)
     k_force_spread(int n_nodes, PosView<T> pos, const int *__restrict__ adj_off,
                    const int4 *__restrict__ adj4, const int *__restrict__ node_cap,
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256)
     const int bx = stencil_first<N>(pc[0]), by = stencil_first<N>(pc[1]), bz = stencil_first<N>(pc[2]);
     const RunDesc R = runs ? runs[node_run[node]] : single;
     const int sx = __ffs(R.tx) - 1, sy = __ffs(R.ty) - 1;
-    const int xw0 = wrap_index(bx, R.nx);
+    const int xw0 = wrap_index(bx, SLAB ? R.gnx : R.nx);
     T wrow[CX == N ? N : 1];
     if constexpr (CX == N) {
 #pragma unroll
@@ -180,7 +180,13 @@ __global__ void __launch_bounds__(256)
             const T w = wxv * wy * wz;
             if (w == T(0)) continue;
             const int xa = xw0 + kx0 + c;
-            const int xw = xa < R.nx ? xa : wrap_index(xa, R.nx);
+            int xw;
+            if constexpr (SLAB) {  // the slab's own columns only
+                xw = (xa < R.gnx ? xa : xa - R.gnx) - R.x0;
+                if (xw < 0 || xw >= R.nx) continue;
+            } else {
+                xw = xa < R.nx ? xa : wrap_index(xa, R.nx);
+            }
             add_force(&fr[rc + xw], w * fx, w * fy, w * fz);
             const int xt = xw >> sx;
             if (xt != last) {
@@ -320,7 +326,7 @@ __global__ void __launch_bounds__(256, sizeof(S) == 2 ? 4 : 3)
 // depend only on the cell index and are issued before the weights are used
 // (cells of zero weight are read and not used).  Groups past the last node
 // repeat its work and write nothing.
-template <int N, typename S, typename T, bool PRE, int NPW>
+template <int N, typename S, typename T, bool PRE, int NPW, bool SLAB = false>
 __global__ void __launch_bounds__(256)
     k_interp_advect(int n_nodes, PosView<T> pos, const typename Vec4<T>::type *__restrict__ uvel,
                     const S *__restrict__ pop, const typename Vec4<T>::type *__restrict__ force,
@@ -353,7 +359,7 @@ __global__ void __launch_bounds__(256)
         pc[0] = p[0]; pc[1] = p[1]; pc[2] = p[2];
     }
     const int bx = stencil_first<N>(pc[0]), by = stencil_first<N>(pc[1]), bz = stencil_first<N>(pc[2]);
-    const int xw0 = wrap_index(bx, nx);
+    const int xw0 = wrap_index(bx, SLAB ? R.gnx : nx);
     // this lane's pieces; a stencil beyond a wall is reported by the spreading
     bool in[RPL];
     long long rc[RPL];
@@ -369,7 +375,12 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int c = 0; c < CX; ++c) {
             const int xa = xw0 + KX[j] + c;
-            XW[j][c] = xa < nx ? xa : wrap_index(xa, nx);
+            if constexpr (SLAB) {  // the slab's own columns; -1 elsewhere
+                const int xl = (xa < R.gnx ? xa : xa - R.gnx) - R.x0;
+                XW[j][c] = (xl >= 0 && xl < nx) ? xl : -1;
+            } else {
+                XW[j][c] = xa < nx ? xa : wrap_index(xa, nx);
+            }
         }
     }
     // x factors: once per lane for whole rows, else per cell
@@ -430,9 +441,10 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
             for (int c = 0; c < CX; ++c) {
 #pragma unroll
+                const bool own = in[j] && (!SLAB || XW[j][c] >= 0);
                 for (int i = 0; i < 19; ++i)
-                    g[slot][c][i] = in[j] ? Store<S, T>::load(pr + i * R.ncell + rc[j] + XW[j][c]) : T(0);
-                f[slot][c] = in[j] ? fr[rc[j] + XW[j][c]] : V4{};
+                    g[slot][c][i] = own ? Store<S, T>::load(pr + i * R.ncell + rc[j] + XW[j][c]) : T(0);
+                f[slot][c] = own ? fr[rc[j] + XW[j][c]] : V4{};
             }
         };
         if constexpr (ALL) {
@@ -449,6 +461,7 @@ __global__ void __launch_bounds__(256)
             const T wy = delta_phi<N>(d[1]), wz = delta_phi<N>(d[2]);
 #pragma unroll
             for (int c = 0; c < CX; ++c) {
+                if (SLAB && XW[j][c] < 0) continue;
                 const T w = weight(j, c, wy, wz);
                 if (w == T(0)) continue;
                 const V4 u = velocity_from<T>(g[slot][c], f[slot][c]);
@@ -463,6 +476,10 @@ __global__ void __launch_bounds__(256)
         ax += __shfl_xor_sync(0xffffffffu, ax, o);
         ay += __shfl_xor_sync(0xffffffffu, ay, o);
         az += __shfl_xor_sync(0xffffffffu, az, o);
+    }
+    if constexpr (SLAB) {  // the slab's partial sum; the nodes move once all slabs are summed
+        if (valid && gl == 0) nodeU[node] = V4{ax, ay, az, T(0)};
+        return;
     }
     if (valid && gl == 0) {
         if (ab2) {  // Sec. II.C: x += 3/2 u_i(t+1) - 1/2 u_i(t)
@@ -653,6 +670,97 @@ void launch_interp_advect(int prec, int delta, const Lattice &L, const MeshDev &
         else if (delta == 3) interp_impl<3, __half, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2, overlap);
         else interp_impl<4, __half, float>(L, m, uvel, pop, force, runs, node_run, s, snap_x, snap_lo, ab2, overlap);
     }
+}
+
+// ---- x-slabs ---------------------------------------------------------------------
+static RunDesc slab_run(const Lattice &L) {
+    RunDesc R = single_run(L);
+    R.x0 = L.x0;
+    R.gnx = L.gnx;
+    return R;
+}
+
+template <int N, typename T>
+static void force_spread_slab_impl(const Lattice &L, const MeshDev &m, void *force, uint8_t *flags, int *status,
+                                   cudaStream_t s) {
+    using V4 = typename Vec4<T>::type;
+    const unsigned nb = (unsigned)((m.n_nodes + kNodesPerBlock - 1) / kNodesPerBlock);
+    k_force_spread<N, T, 1, true><<<nb, 32 * kNodesPerBlock, 0, s>>>(
+        m.n_nodes, view<T>(m), m.adj_off, (const int4 *)m.adj4, m.node_cap, (const V4 *)m.fconst,
+        (const V4 *)m.capmod, (V4 *)m.F, (V4 *)force, flags, slab_run(L), nullptr, nullptr, status);
+}
+
+template <int N, typename S, typename T>
+static void interp_partial_slab_impl(const Lattice &L, const MeshDev &m, const void *pop, const void *force,
+                                     void *part, cudaStream_t s) {
+    using V4 = typename Vec4<T>::type;
+    const unsigned nb = (unsigned)((m.n_nodes + kNodesPerBlock - 1) / kNodesPerBlock);
+    MeshDev none{};
+    k_interp_advect<N, S, T, false, 1, true><<<nb, 32 * kNodesPerBlock, 0, s>>>(
+        m.n_nodes, view<T>(m), nullptr, (const S *)pop, (const V4 *)force, (V4 *)part, slab_run(L), nullptr,
+        nullptr, view<T>(none), 0);
+}
+
+// u = sum of the slabs' partials in slab order; x += u (Eq. positionupdate).
+template <typename T>
+__global__ void k_slab_advect(int n_nodes, PosView<T> pos, typename Vec4<T>::type *__restrict__ nodeU,
+                              const typename Vec4<T>::type *const *__restrict__ parts, int n_parts) {
+    using V4 = typename Vec4<T>::type;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_nodes) return;
+    T ux = T(0), uy = T(0), uz = T(0);
+    for (int p = 0; p < n_parts; ++p) {
+        const V4 q = parts[p][i];
+        ux += q.x;
+        uy += q.y;
+        uz += q.z;
+    }
+    PosView<T> none{};
+    pos.advance(i, ux, uy, uz, none);
+    nodeU[i] = V4{ux, uy, uz, T(0)};
+}
+
+void launch_force_spread_slab(int prec, int delta, const Lattice &L, const MeshDev &m, void *force,
+                              uint8_t *flags, int *status, cudaStream_t s) {
+    if (m.n_nodes == 0) return;
+    if (prec == kF64) {
+        if (delta == 2) force_spread_slab_impl<2, double>(L, m, force, flags, status, s);
+        else if (delta == 3) force_spread_slab_impl<3, double>(L, m, force, flags, status, s);
+        else force_spread_slab_impl<4, double>(L, m, force, flags, status, s);
+    } else {
+        if (delta == 2) force_spread_slab_impl<2, float>(L, m, force, flags, status, s);
+        else if (delta == 3) force_spread_slab_impl<3, float>(L, m, force, flags, status, s);
+        else force_spread_slab_impl<4, float>(L, m, force, flags, status, s);
+    }
+}
+
+void launch_interp_partial_slab(int prec, int delta, const Lattice &L, const MeshDev &m, const void *pop,
+                                const void *force, void *part, cudaStream_t s) {
+    if (m.n_nodes == 0) return;
+    if (prec == kF64) {
+        if (delta == 2) interp_partial_slab_impl<2, double, double>(L, m, pop, force, part, s);
+        else if (delta == 3) interp_partial_slab_impl<3, double, double>(L, m, pop, force, part, s);
+        else interp_partial_slab_impl<4, double, double>(L, m, pop, force, part, s);
+    } else if (prec == kF32) {
+        if (delta == 2) interp_partial_slab_impl<2, float, float>(L, m, pop, force, part, s);
+        else if (delta == 3) interp_partial_slab_impl<3, float, float>(L, m, pop, force, part, s);
+        else interp_partial_slab_impl<4, float, float>(L, m, pop, force, part, s);
+    } else {
+        if (delta == 2) interp_partial_slab_impl<2, __half, float>(L, m, pop, force, part, s);
+        else if (delta == 3) interp_partial_slab_impl<3, __half, float>(L, m, pop, force, part, s);
+        else interp_partial_slab_impl<4, __half, float>(L, m, pop, force, part, s);
+    }
+}
+
+void launch_slab_advect(int prec, const MeshDev &m, const void *const *parts, int n_parts, cudaStream_t s) {
+    if (m.n_nodes == 0) return;
+    const unsigned nb = (unsigned)((m.n_nodes + 127) / 128);
+    if (prec == kF64)
+        k_slab_advect<double><<<nb, 128, 0, s>>>(m.n_nodes, view<double>(m), (dvec4 *)m.u,
+                                                 (const dvec4 *const *)parts, n_parts);
+    else
+        k_slab_advect<float><<<nb, 128, 0, s>>>(m.n_nodes, view<float>(m), (float4 *)m.u,
+                                                (const float4 *const *)parts, n_parts);
 }
 
 void launch_nodes_to_f64(int prec, const MeshDev &m, int which, int first, int count, double *out,

@@ -22,6 +22,9 @@ constexpr int kTileY = 8;
 
 struct Lattice {
     int nx, ny, nz;
+    // x-slab of a larger periodic lattice: this lattice holds the global
+    // columns x0 .. x0 + nx - 1 of gnx (x0 = 0, gnx = nx for a whole lattice)
+    int x0 = 0, gnx = 0;
     int ntx, nty;   // scalar-kernel tiles along x and y
     int lanes_row;  // vectorised kernel: nx / 4 lanes per row; 0 = scalar kernel
     int ftx, fty;   // cells per force flag along x and y
@@ -47,6 +50,8 @@ inline Lattice make_lattice(int nx, int ny, int nz, bool vec) {
     L.nfy = (ny + L.fty - 1) / L.fty;
     L.ncell = (long long)nx * ny * nz;
     L.ntiles = (long long)L.nfx * L.nfy * nz;
+    L.x0 = 0;
+    L.gnx = nx;
     return L;
 }
 
@@ -61,6 +66,7 @@ struct RunDesc {
     int nx, ny, nz;
     int tx, ty;    // tile shape
     int ntx, nty;  // tiles along x and y
+    int x0, gnx;   // x-slab: global origin and global width (0, nx otherwise)
     int pad;
     long long cell_off, tile_off, ncell;
     double omega, u_wall;
@@ -109,7 +115,15 @@ struct CollideArgs {
     // adjoint's recomputation keeps them); null in a plain step
     void *moments = nullptr;
     int eq_order = 2;  // 2: Eq. (equilibrium); 1: the linearised form of Sec. IV.A
+    // vectorised kernel: stage the populations in shared memory by bulk copies
+    // (where collide_staging_supported), giving up a wait after wait_ns
+    bool staged = false;
+    unsigned long long wait_ns = 1000000000ull;
 };
+// Whether the vectorised lattice can take the staged (bulk-copy) collide:
+// float or half storage, rows of nx = 4 * lanes_row cells with nx * element
+// size a multiple of 16 bytes.
+bool collide_staging_supported(int prec, const Lattice &L);
 // Launchers of the time-step kernels take `overlap`: launch with programmatic
 // stream serialization, so that the kernel may start while the previous kernel
 // of the stream still runs (the kernels wait for it where they must; see
@@ -134,12 +148,21 @@ void launch_collide_stream(int prec, const Lattice &L, const CollideArgs &a, cud
 void launch_collide_batch(int prec, const BatchArgs &b, const CollideArgs &a, cudaStream_t s,
                           bool overlap = false);
 int collide_batch_blocks_per_sm(int prec, bool pairs);
+// x-slabs: the ten boundary columns of a slab's populations (c_x = +1 at
+// x = 0, c_x = -1 at x = nx - 1, each [nz][ny]) to and from a packed buffer
+// of 10 * ny * nz elements; unpack takes the c_x = +1 columns from `left`
+// (the left neighbour's packed buffer) and the c_x = -1 ones from `right`,
+// skipping the rows the wall bounce-back filled.
+void launch_plane_pack(int prec, const Lattice &L, const void *pop, void *out, cudaStream_t s);
+void launch_plane_unpack(int prec, const Lattice &L, void *pop, const void *left, const void *right,
+                         cudaStream_t s);
 // Checksum of a device byte range (added into *out, which the caller zeroes):
 // the sum modulo 2^64 of the SplitMix64 finaliser of each 64-bit word plus
 // its index times 0x9e3779b97f4a7c15 (last word zero-padded).
 void launch_checksum(const void *p, size_t n_bytes, unsigned long long *out, cudaStream_t s);
 // Name of the collide-and-stream kernel a plain step launches (static string).
 const char *collide_kernel_name(int prec, const Lattice &L);
+const char *collide_kernel_name(int prec, const Lattice &L, bool staged);
 const char *collide_batch_kernel_name(int prec, bool pairs);
 // mode 0: rest; mode 1: linear Couette equilibrium
 void launch_init_fluid(int prec, const Lattice &L, void *pop, int mode, double u_wall, cudaStream_t s);
@@ -172,6 +195,18 @@ void launch_interp_advect(int prec, int delta, const Lattice &L, const MeshDev &
                           const void *pop, const void *force, const RunDesc *runs, const int *node_run,
                           cudaStream_t s, void *snap_x = nullptr, void *snap_lo = nullptr, int ab2 = 0,
                           bool overlap = false);
+// x-slab of a lattice (L.gnx > L.nx): the spreading and the interpolation
+// take only the slab's own cells of every node's stencil (x indices wrap
+// with the global width); the interpolation writes the partial node
+// velocities to m.u without moving the nodes, and launch_slab_advect adds the
+// partials of all slabs, in slab order, and advances the nodes (Euler).
+void launch_force_spread_slab(int prec, int delta, const Lattice &L, const MeshDev &m, void *force,
+                              uint8_t *flags, int *status, cudaStream_t s);
+void launch_interp_partial_slab(int prec, int delta, const Lattice &L, const MeshDev &m, const void *pop,
+                                const void *force, void *part, cudaStream_t s);
+// parts: device array of n_parts pointers to the slabs' partial velocities
+// (Vec4 per node); the sum goes to m.u and the nodes move by it
+void launch_slab_advect(int prec, const MeshDev &m, const void *const *parts, int n_parts, cudaStream_t s);
 // node data <-> host doubles [n][3]
 void launch_nodes_to_f64(int prec, const MeshDev &m, int which, int first, int count, double *out,
                          cudaStream_t s);
@@ -222,7 +257,9 @@ struct TaylorPlan {
     unsigned *ticket;       // blocks of a recording launch done (returns to 0)
 };
 // Blocks of kTaylorClusterThreads threads per capsule: about four faces per
-// thread, at most max_cluster (taylor_max_cluster()).
+// thread, at most max_cluster (taylor_max_cluster()).  (Two faces per thread
+// in blocks of 256 measured slower: 30 vs 27.5 us for eight records of one
+// 5120-face capsule, 72 vs 46 us for one record of 200 1280-face capsules.)
 constexpr int kTaylorClusterThreads = 128;
 inline int taylor_cluster_size(int max_faces_per_capsule, int max_cluster) {
     int c = (max_faces_per_capsule + 4 * kTaylorClusterThreads - 1) / (4 * kTaylorClusterThreads);

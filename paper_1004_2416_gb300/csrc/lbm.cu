@@ -252,6 +252,26 @@ struct Quad<__half> {
     }
 };
 
+// The same quad loads from shared memory (a staged tile), in storage units.
+template <typename S>
+struct QuadSmem;
+template <>
+struct QuadSmem<float> {
+    static __device__ __forceinline__ void load(const float *p, float2 &a, float2 &b) {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        a = make_float2(q.x, q.y);
+        b = make_float2(q.z, q.w);
+    }
+};
+template <>
+struct QuadSmem<__half> {
+    static __device__ __forceinline__ void load(const __half *p, float2 &a, float2 &b) {
+        const uint2 q = *reinterpret_cast<const uint2 *>(p);
+        a = __half22float2(*reinterpret_cast<const __half2 *>(&q.x));
+        b = __half22float2(*reinterpret_cast<const __half2 *>(&q.y));
+    }
+};
+
 // Vectorised collide-and-stream for nx = 4 * LR, LR a power of two <= 256:
 // each thread owns 4 consecutive cells of one x-row and LR lanes cover the
 // row.  With LR <= 32 a warp covers 32 / LR rows; with LR > 32 a row spans
@@ -544,6 +564,118 @@ __global__ void __launch_bounds__(256, 2)
                                  omega, u_wall, status, moments, edge);
 }
 
+// ---- the same on tiles staged in shared memory by the bulk-copy engine ---------------
+// Persistent variant of k_collide_stream_x4: each block walks tiles of TR =
+// THREADS * 4 / nx consecutive rows.  For every tile one thread issues 19
+// bulk copies (one per direction, the tile's rows being contiguous in each
+// direction's array) into one of two shared-memory buffers; the copies of the
+// next tile run while the block computes the current one, so the warps never
+// wait on global loads and their issue slots go to the arithmetic and the
+// stores.  A wait that runs past wait_ns nanoseconds records kStatusTimeout,
+// waits (bounded) for the copies still in flight and leaves the block.
+template <typename S, int LR, bool LIN, int THREADS>
+__global__ void __launch_bounds__(THREADS, 2)
+    k_collide_stream_tma(const S *__restrict__ src, S *__restrict__ dst, const float4 *__restrict__ fcur,
+                         const uint8_t *__restrict__ flag_cur, float4 *__restrict__ fold,
+                         uint8_t *__restrict__ flag_old, int ny, int nz, int ncell, float omega, float u_wall,
+                         int *status, int n_tiles, unsigned long long wait_ns) {
+    constexpr int NX = 4 * LR;
+    constexpr int TR = THREADS * 4 / NX;  // rows per tile
+    constexpr int TILE = TR * NX;         // cells per tile
+    constexpr int NW = THREADS / 32;
+    static_assert(TR >= 1 && TR * NX == THREADS * 4, "a tile is a whole number of rows");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    S *stage = reinterpret_cast<S *>(smem_raw);  // [2][19][TILE]
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ float edge[NW][10];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int lr, lx;  // row within the tile, lane within the row
+    if constexpr (LR <= 32) {
+        lr = warp * (32 / LR) + lane / LR;
+        lx = lane & (LR - 1);
+    } else {
+        constexpr int WPR = LR / 32;
+        lr = warp / WPR;
+        lx = (warp % WPR) * 32 + lane;
+    }
+    const int nrows = ny * nz;
+    const int x0 = 4 * lx;
+
+    prior_grid_wait();
+    allow_dependents();
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        fence_async_smem();
+    }
+    __syncthreads();
+    // thread 0: copies of tile t into buffer b
+    auto issue = [&](int t, int b) {
+        const int r0 = t * TR;
+        const int nr = min(TR, nrows - r0);
+        const unsigned bytes = (unsigned)(nr * NX * (int)sizeof(S));
+        mbar_expect_bytes(&bar[b], 19u * bytes);
+#pragma unroll 1
+        for (int i = 0; i < 19; ++i)
+            bulk_copy_to_smem(stage + ((size_t)b * 19 + i) * TILE, src + (size_t)i * ncell + (size_t)r0 * NX, bytes,
+                              &bar[b]);
+    };
+    int pending[2] = {0, 0};  // thread 0: copies issued and not yet waited for, per buffer
+    if (threadIdx.x == 0) {
+        if ((int)blockIdx.x < n_tiles) { issue(blockIdx.x, 0); pending[0] = 1; }
+        if ((int)(blockIdx.x + gridDim.x) < n_tiles) { issue(blockIdx.x + gridDim.x, 1); pending[1] = 1; }
+    }
+    constexpr int FTX = NX < 32 ? NX : 32;
+    int k = 0;
+    bool gave_up = false;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++k) {
+        const int b = k & 1;
+        const unsigned parity = (unsigned)((k >> 1) & 1);
+        const bool ok = mbar_wait_bounded(&bar[b], parity, wait_ns);
+        if (__syncthreads_or(!ok)) {
+            gave_up = true;
+            break;
+        }
+        if (threadIdx.x == 0) pending[b] = 0;
+        const int row_raw = t * TR + lr;
+        const bool active = row_raw < nrows;
+        const int row = active ? row_raw : nrows - 1;  // inactive lanes still join the exchanges
+        const int y = row % ny, z = row / ny;
+        const int cell0 = x0 + NX * row;
+        const int fidx = row * (NX / FTX) + x0 / FTX;
+        const bool has_old = flag_old[fidx] != 0;
+        const bool has_cur = flag_cur[fidx] != 0;
+        if (has_old && active) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) fold[cell0 + q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncwarp();  // every lane of the segment has read its flag
+        if (has_old && active && x0 % FTX == 0) flag_old[fidx] = 0;
+        // this thread's quad from the staged tile (an inactive lane reads row 0 of the tile)
+        const S *tile = stage + (size_t)b * 19 * TILE + (active ? lr : 0) * NX + x0;
+        float2 g[19][2];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) QuadSmem<S>::load(tile + (size_t)i * TILE, g[i][0], g[i][1]);
+        collide_quad<S, LR, false, LIN>(g, dst, fcur, has_cur, active, row, y, z, x0, cell0, lane, warp, ny, nz,
+                                        ncell, omega, u_wall, status, nullptr, edge);
+        __syncthreads();  // buffer b is read: it may be refilled
+        if (threadIdx.x == 0 && t + 2 * (int)gridDim.x < n_tiles) {
+            fence_async_smem();
+            issue(t + 2 * gridDim.x, b);
+            pending[b] = 1;
+        }
+    }
+    if (gave_up && threadIdx.x == 0) {
+        set_status(status, kStatusTimeout);
+        // no copy may still write into the block's shared memory when it leaves
+        for (int b = 0; b < 2; ++b) {
+            const int kb = (k & 1) == b ? k : k + 1;  // next use of buffer b
+            if (pending[b]) mbar_wait_bounded(&bar[b], (unsigned)((kb >> 1) & 1), 2000000000ull);
+        }
+    }
+}
+
 // ---- two cells per thread (rows of even length, float arithmetic) ------------------
 // Cells (x, x + 1), x even, of a row of even length: one 8-byte (float) or
 // 4-byte (binary16) load per direction, arithmetic on the pair with the
@@ -811,10 +943,76 @@ __global__ void k_force_to_f64(const typename Vec4<T>::type *force, long long nc
 
 static inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+static int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                      cudaSuccess || n < 1) {
+            cudaGetLastError();
+            n = 152;
+        }
+    }
+    return n;
+}
+
+// Threads per block of the staged kernel: a tile of THREADS * 4 cells is
+// 19 * 1024 * 2 = 38 912 bytes per buffer in half storage (256 threads) and
+// 19 * 512 * 4 = 38 912 bytes in float storage (128 threads); two buffers per
+// block and two blocks per SM, so that one block computes while the other's
+// copies arrive.
+template <typename S>
+constexpr int staged_threads() { return sizeof(S) == 2 ? 256 : 128; }
+
+bool collide_staging_supported(int prec, const Lattice &L) {
+    if (prec == kF64 || !L.lanes_row) return false;
+    const int nx = 4 * L.lanes_row;
+    const int threads = prec == kF32 ? staged_threads<float>() : staged_threads<__half>();
+    return (nx * (prec == kF32 ? 4 : 2)) % 16 == 0 && nx <= 4 * threads;
+}
+
+
+template <typename S, int LR, bool LIN>
+static void collide_staged(const Lattice &L, const CollideArgs &a, cudaStream_t s, bool ov) {
+    constexpr int T = staged_threads<S>();
+    constexpr int NX = 4 * LR;
+    constexpr int TR = T * 4 / NX;
+    const size_t smem = 2 * 19 * (size_t)T * 4 * sizeof(S);
+    auto kern = k_collide_stream_tma<S, LR, LIN, T>;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    const int nrows = L.ny * L.nz;
+    const int n_tiles = (nrows + TR - 1) / TR;
+    const int grid = std::min(n_tiles, 2 * sm_count());
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t c = {};
+    c.gridDim = dim3(grid);
+    c.blockDim = dim3(T);
+    c.dynamicSmemBytes = smem;
+    c.stream = s;
+    c.attrs = at;
+    c.numAttrs = ov ? 1 : 0;
+    cudaLaunchKernelEx(&c, kern, (const S *)a.src, (S *)a.dst, (const float4 *)a.fcur, a.flag_cur,
+                       (float4 *)a.fold, a.flag_old, L.ny, L.nz, (int)L.ncell, (float)(1.0 / a.tau),
+                       (float)a.u_wall, a.status, n_tiles, a.wait_ns);
+}
+
 template <typename S, int LR>
 static void collide_x4(const Lattice &L, const CollideArgs &a, cudaStream_t s, bool ov) {
     constexpr int rpb = rows_per_block<LR>();
     const int nrows = L.ny * L.nz;
+    if constexpr ((4 * LR * sizeof(S)) % 16 == 0 && LR <= staged_threads<S>()) {
+        if (a.staged && !a.moments) {
+            if (a.eq_order == 1) collide_staged<S, LR, true>(L, a, s, ov);
+            else collide_staged<S, LR, false>(L, a, s, ov);
+            return;
+        }
+    }
     const unsigned nb = (unsigned)((nrows + rpb - 1) / rpb);
     // the moments are kept only by the adjoint's recomputation, which runs
     // with the full equilibrium
@@ -905,6 +1103,65 @@ void launch_collide_batch(int prec, const BatchArgs &b, const CollideArgs &a, cu
     else collide_batch_impl<__half, float>(b, a, s, overlap);
 }
 
+// ---- x-slab boundary planes -------------------------------------------------------------
+// A slab streams with its own periodic wrap in x, so after its collide the
+// populations with c_x = +1 that crossed its right edge sit in its column
+// x = 0, and those with c_x = -1 that crossed its left edge in its column
+// x = nx - 1.  Packing these ten columns and writing each slab's from its
+// neighbour's (left neighbour for c_x = +1, right for c_x = -1) turns the
+// wraps into the global periodic streaming of Eq. (lbequation).  Entries of a
+// column that the moving-wall bounce-back filled (the rows whose stream
+// source lies beyond a wall) are the cell's own and are kept.
+__host__ __device__ constexpr int plane_dir(int k) {
+    // c_x = +1: 1, 7, 10, 12, 13; c_x = -1: 2, 8, 9, 11, 14 (Fig. d3q19)
+    constexpr int t[10] = {1, 7, 10, 12, 13, 2, 8, 9, 11, 14};
+    return t[k];
+}
+
+template <typename E>
+__global__ void k_plane_pack(const E *__restrict__ pop, int nx, int ny, int nz, long long ncell,
+                             E *__restrict__ out) {
+    const long long per = (long long)ny * nz;
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= 10 * per) return;
+    const int k = (int)(idx / per);
+    const long long yz = idx % per;
+    const int xcol = k < 5 ? 0 : nx - 1;
+    out[idx] = pop[plane_dir(k) * ncell + yz * nx + xcol];
+}
+
+template <typename E>
+__global__ void k_plane_unpack(E *__restrict__ pop, int nx, int ny, int nz, long long ncell,
+                               const E *__restrict__ left, const E *__restrict__ right) {
+    const long long per = (long long)ny * nz;
+    const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (idx >= 10 * per) return;
+    const int k = (int)(idx / per);
+    const long long yz = idx % per;
+    const int z = (int)(yz / ny);
+    const int i = plane_dir(k), cz = q_cz(i);
+    if (z - cz < 0 || z - cz >= nz) return;  // filled by the wall's bounce-back
+    const int xcol = k < 5 ? 0 : nx - 1;
+    pop[i * ncell + yz * nx + xcol] = (k < 5 ? left : right)[idx];
+}
+
+void launch_plane_pack(int prec, const Lattice &L, const void *pop, void *out, cudaStream_t s) {
+    const long long n = 10LL * L.ny * L.nz;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    if (prec == kF64) k_plane_pack<unsigned long long><<<nb, 256, 0, s>>>((const unsigned long long *)pop, L.nx, L.ny, L.nz, L.ncell, (unsigned long long *)out);
+    else if (prec == kF32) k_plane_pack<unsigned><<<nb, 256, 0, s>>>((const unsigned *)pop, L.nx, L.ny, L.nz, L.ncell, (unsigned *)out);
+    else k_plane_pack<unsigned short><<<nb, 256, 0, s>>>((const unsigned short *)pop, L.nx, L.ny, L.nz, L.ncell, (unsigned short *)out);
+}
+
+void launch_plane_unpack(int prec, const Lattice &L, void *pop, const void *left, const void *right,
+                         cudaStream_t s) {
+    const long long n = 10LL * L.ny * L.nz;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    if (prec == kF64) k_plane_unpack<unsigned long long><<<nb, 256, 0, s>>>((unsigned long long *)pop, L.nx, L.ny, L.nz, L.ncell, (const unsigned long long *)left, (const unsigned long long *)right);
+    else if (prec == kF32) k_plane_unpack<unsigned><<<nb, 256, 0, s>>>((unsigned *)pop, L.nx, L.ny, L.nz, L.ncell, (const unsigned *)left, (const unsigned *)right);
+    else k_plane_unpack<unsigned short><<<nb, 256, 0, s>>>((unsigned short *)pop, L.nx, L.ny, L.nz, L.ncell, (const unsigned short *)left, (const unsigned short *)right);
+}
+
 // ---- checkpoint section checksum ------------------------------------------------------
 // Sum modulo 2^64 of mix(w_k + k * 0x9e3779b97f4a7c15) over the 64-bit words
 // w_k of a byte range (the last word zero-padded), mix being the SplitMix64
@@ -939,6 +1196,23 @@ void launch_checksum(const void *p, size_t n_bytes, unsigned long long *out, cud
     const size_t words = (n_bytes + 7) / 8;
     const unsigned blocks = (unsigned)std::min<size_t>((words + 255) / 256, 152 * 8);
     if (blocks) k_checksum<<<blocks, 256, 0, s>>>((const unsigned char *)p, n_bytes, out);
+}
+
+const char *collide_kernel_name(int prec, const Lattice &L, bool staged) {
+    static const char *const tma_f32[9] = {
+        "k_collide_stream_tma<float,1>",  "k_collide_stream_tma<float,2>",  "k_collide_stream_tma<float,4>",
+        "k_collide_stream_tma<float,8>",  "k_collide_stream_tma<float,16>", "k_collide_stream_tma<float,32>",
+        "k_collide_stream_tma<float,64>", "k_collide_stream_tma<float,128>", "k_collide_stream_tma<float,256>"};
+    static const char *const tma_f16[9] = {
+        "k_collide_stream_tma<__half,1>",  "k_collide_stream_tma<__half,2>",  "k_collide_stream_tma<__half,4>",
+        "k_collide_stream_tma<__half,8>",  "k_collide_stream_tma<__half,16>", "k_collide_stream_tma<__half,32>",
+        "k_collide_stream_tma<__half,64>", "k_collide_stream_tma<__half,128>", "k_collide_stream_tma<__half,256>"};
+    if (staged && collide_staging_supported(prec, L)) {
+        int k = 0;
+        while ((1 << k) < L.lanes_row) ++k;
+        return prec == kF32 ? tma_f32[k] : tma_f16[k];
+    }
+    return collide_kernel_name(prec, L);
 }
 
 const char *collide_kernel_name(int prec, const Lattice &L) {

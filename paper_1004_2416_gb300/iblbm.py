@@ -33,6 +33,7 @@ IBLBM_ERR_OOM = -2
 IBLBM_ERR_CUDA = -3
 IBLBM_ERR_UNSTABLE = -4
 IBLBM_ERR_STENCIL = -5
+IBLBM_ERR_TIMEOUT = -6
 IBLBM_ERR_STATE = -7
 
 IBLBM_FP64 = 0
@@ -83,6 +84,8 @@ _SIGS = {
     "iblbm_set_kernel_timing": (_int, [_vp, _int]),
     "iblbm_get_kernel_times": (_int, [_vp, _dp, ctypes.POINTER(ctypes.c_int64)]),
     "iblbm_collide_kernel": (ctypes.c_char_p, [_vp]),
+    "iblbm_set_collide_staging": (_int, [_vp, _int]),
+    "iblbm_set_device_wait_limit": (_int, [_vp, ctypes.c_int64]),
     "iblbm_sync": (_int, [_vp]),
     "iblbm_get_velocity": (_int, [_vp, _dp]),
     "iblbm_get_density": (_int, [_vp, _dp]),
@@ -118,6 +121,17 @@ _SIGS = {
     "iblbm_checkpoint_restore": (_int, [_vp, _vp, ctypes.c_size_t, _int]),
     "iblbm_batch_create": (_int, [ctypes.POINTER(_vp), ctypes.POINTER(iblbm_run_spec), _int, _int, _int,
                                   _vp, ctypes.POINTER(iblbm_allocator)]),
+    "iblbm_create_slabs": (_int, [ctypes.POINTER(_vp), _int, _int, _int, _dbl, _int, _int, _int, _vp,
+                                  ctypes.POINTER(iblbm_allocator)]),
+    "iblbm_get_slab": (_int, [_vp, _int, _ip, _ip]),
+    "iblbm_slab_configure": (_int, [_vp, _int, _int]),
+    "iblbm_slab_step_begin": (_int, [_vp]),
+    "iblbm_slab_columns_size": (_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "iblbm_slab_get_columns": (_int, [_vp, _vp, _int]),
+    "iblbm_slab_set_columns": (_int, [_vp, _vp, _vp, _int]),
+    "iblbm_slab_partials_size": (_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "iblbm_slab_get_partials": (_int, [_vp, _vp, _int]),
+    "iblbm_slab_step_end": (_int, [_vp, _vp, _int, _int]),
     "iblbm_add_capsule_icosphere_in_run": (_int, [_vp, _int, _dbl, _dbl, _dbl, _dbl, _int, _ip]),
     "iblbm_autotune_tiles": (_int, [_vp, _int]),
     "iblbm_get_run_tile": (_int, [_vp, _int, _ip, _ip]),
@@ -254,6 +268,61 @@ class Sim:
         self.ncell = sum(a * b * c for a, b, c in self.runs)
         self._ncaps = 0
         return self
+
+    @classmethod
+    def slabs(cls, nx: int, ny: int, nz: int, n_slabs: int, tau: float = 1.0, precision="fp32",
+              delta_points: int = 3, stream=None):
+        """One nx*ny*nz lattice decomposed into n_slabs x-slabs (iblbm_create_slabs)."""
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        h = _vp()
+        rc = iblbm_create_slabs(ctypes.byref(h), nx, ny, nz, tau, prec, delta_points, n_slabs,
+                                _stream_handle(stream), None)
+        if rc != IBLBM_OK:
+            raise IblbmError(rc, iblbm_last_error(None).decode(errors="replace"))
+        self = cls.__new__(cls)
+        self._keep = None
+        self._h = h
+        self.shape = (nx, ny, nz)
+        self.ncell = nx * ny * nz
+        self.runs = [self.shape]
+        self._ncaps = 0
+        return self
+
+    # x-slab phases of one slab held by this process (iblbm_slab_*); buffers are
+    # host numpy arrays of bytes
+    def slab_configure(self, x0: int, nx_global: int):
+        _check(iblbm_slab_configure(self._h, int(x0), int(nx_global)), self._h)
+
+    def slab_step_begin(self):
+        _check(iblbm_slab_step_begin(self._h), self._h)
+
+    def slab_columns(self) -> np.ndarray:
+        n = ctypes.c_size_t()
+        _check(iblbm_slab_columns_size(self._h, ctypes.byref(n)), self._h)
+        out = np.empty(n.value, np.uint8)
+        _check(iblbm_slab_get_columns(self._h, out.ctypes.data_as(_vp), 0), self._h)
+        return out
+
+    def slab_set_columns(self, left: np.ndarray, right: np.ndarray):
+        left, right = np.ascontiguousarray(left, np.uint8), np.ascontiguousarray(right, np.uint8)
+        _check(iblbm_slab_set_columns(self._h, left.ctypes.data_as(_vp), right.ctypes.data_as(_vp), 0), self._h)
+
+    def slab_partials(self) -> np.ndarray:
+        n = ctypes.c_size_t()
+        _check(iblbm_slab_partials_size(self._h, ctypes.byref(n)), self._h)
+        out = np.empty(max(n.value, 1), np.uint8)
+        _check(iblbm_slab_get_partials(self._h, out.ctypes.data_as(_vp), 0), self._h)
+        return out[:n.value]
+
+    def slab_step_end(self, parts: np.ndarray, n_parts: int):
+        parts = np.ascontiguousarray(parts, np.uint8)
+        _check(iblbm_slab_step_end(self._h, parts.ctypes.data_as(_vp), int(n_parts), 0), self._h)
+
+    def slab(self, k: int):
+        """(first global column, width) of slab k of a slab group."""
+        x0, w = _int(), _int()
+        _check(iblbm_get_slab(self._h, k, ctypes.byref(x0), ctypes.byref(w)), self._h)
+        return x0.value, w.value
 
     def add_capsule_icosphere_in_run(self, run: int, center, radius: float, subdivisions: int) -> int:
         cid = _int()
@@ -440,6 +509,13 @@ class Sim:
 
     def collide_kernel(self) -> str:
         return iblbm_collide_kernel(self._h).decode()
+
+    def set_collide_staging(self, mode: int):
+        """-1 automatic, 0 direct loads, 1 populations staged by bulk copies."""
+        _check(iblbm_set_collide_staging(self._h, int(mode)), self._h)
+
+    def set_device_wait_limit(self, ns: int):
+        _check(iblbm_set_device_wait_limit(self._h, int(ns)), self._h)
 
     def adjoint_forward(self, n_steps: int, checkpoint_every: int):
         _check(iblbm_adjoint_forward(self._h, int(n_steps), int(checkpoint_every)), self._h)

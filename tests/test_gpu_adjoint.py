@@ -2,7 +2,11 @@
 to the shear modulus, the wall speed (capillary number) and the reference node
 positions, from the hand-written reverse sweep, against central finite
 differences of the FP64 oracle (tests/golden/adjoint_fd_*.json, written by
-tests/golden/make_adjoint_fd.py, which calls only the oracle)."""
+tests/golden/make_adjoint_fd.py) and against the oracle's own reference
+gradient, its complex-step tangent (tests/golden/adjoint_tangent_*.json,
+written by tests/golden/make_adjoint_tangent.py); both scripts call only the
+oracle.  The tangent carries no truncation error, so the FP64 build is held to
+it at 1e-8 (the rounding of two different evaluation orders over the run)."""
 import importlib.util
 import json
 import os
@@ -23,6 +27,27 @@ _spec.loader.exec_module(FDMOD)
 def _fd(name):
     with open(os.path.join(GOLDEN, f"adjoint_fd_{name}.json")) as fh:
         return json.load(fh)
+
+
+def _tangent(name):
+    path = os.path.join(GOLDEN, f"adjoint_tangent_{name}.json")
+    if not os.path.exists(path):
+        pytest.skip(f"{path} not written")
+    with open(path) as fh:
+        return json.load(fh)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-8), ("fp32", 1e-3)])
+def test_adjoint_small_against_oracle_tangent(prec, tol, capsys):
+    case, _, _ = FDMOD.case("small")
+    t = _tangent("small")
+    g = gpu_sim(case, precision=prec)
+    g.adjoint_forward(case.steps, 50)
+    n = len(g.get_nodes())
+    r = g.adjoint_backward(0)
+    assert r["D"] == pytest.approx(t["D"], rel=1e-9 if prec == "fp64" else 1e-4)
+    _check(r, t, n, tol, capsys, f"adjoint {prec} vs tangent")
+    g.close()
 
 
 def _check(r, fd, n_nodes, tol, capsys, label):
@@ -112,6 +137,10 @@ def test_adjoint_config5_against_oracle_fd(capsys):
     r = g.adjoint_backward(0)
     assert r["D"] == pytest.approx(fd["D"], rel=1e-4)
     _check(r, fd, len(r["dD_dX0"]), 1e-3, capsys, "adjoint config5 fp32")
+    # and against the oracle's complex-step tangent along the same directions
+    t = _tangent("config5")
+    _check(r, t, len(r["dD_dX0"]), 1e-3, capsys, "adjoint config5 fp32 vs tangent")
+    g.close()
 
 
 def test_adjoint_taylor_one_call(capsys):

@@ -78,3 +78,20 @@ def test_no_deformation_no_derivative():
     c, cap, X0, tri, _ = _small()
     D, dks0 = O.tangent_taylor_D(c.shape, c.tau, c.delta, 0.0, X0, tri, cap.k_s, cap.C, 30, dks=1.0)
     assert abs(D) < 1e-12 and abs(dks0) < 1e-9
+
+
+@pytest.mark.parametrize("name", ["small", "config5"])
+def test_stored_tangents_agree_with_stored_differences(name):
+    """The committed reference gradients (complex step) and the committed
+    central differences, both from the oracle, agree to the differences' error
+    (1e-6 relative; 1e-6 of the largest for the X0 directions)."""
+    with open(os.path.join(GOLDEN, f"adjoint_fd_{name}.json")) as fh:
+        fd = json.load(fh)
+    with open(os.path.join(GOLDEN, f"adjoint_tangent_{name}.json")) as fh:
+        tg = json.load(fh)
+    assert tg["D"] == pytest.approx(fd["D"], rel=1e-12)
+    assert tg["dD_dks"] == pytest.approx(fd["dD_dks"], rel=1e-6)
+    assert tg["dD_duw"] == pytest.approx(fd["dD_duw"], rel=1e-6)
+    scale = max(abs(v) for v in fd["dD_dX0_along"])
+    for a, b in zip(tg["dD_dX0_along"], fd["dD_dX0_along"]):
+        assert abs(a - b) <= 1e-6 * scale
