@@ -16,7 +16,9 @@ namespace iblbm {
 // kTileX x kTileY x 1 cells; the vectorised one on whole x-rows (4 cells per
 // thread, nx/4 lanes per row, nx/4 a power of two <= 256).  The sparse
 // force-density flags have the granularity of the kernel in use:
-// ftx x fty x 1 cells per flag (32 x 8 tiles, or 32-cell segments of a row).
+// ftx x fty x 1 cells per flag (32 x 8 tiles, or the 4-cell quad of one
+// thread of the vectorised kernel, so that its collide reads the force, and
+// the velocity pass of a dense suspension forms u, only where stencils touch).
 constexpr int kTileX = 32;
 constexpr int kTileY = 8;
 
@@ -44,7 +46,7 @@ inline Lattice make_lattice(int nx, int ny, int nz, bool vec) {
     L.ntx = (nx + kTileX - 1) / kTileX;
     L.nty = (ny + kTileY - 1) / kTileY;
     L.lanes_row = (vec && nx % 4 == 0 && is_pow2(nx / 4) && nx / 4 <= 256) ? nx / 4 : 0;
-    L.ftx = L.lanes_row ? (nx < 32 ? nx : 32) : kTileX;  // vector kernel: 32-cell row segments
+    L.ftx = L.lanes_row ? 4 : kTileX;  // vector kernel: one flag per thread's 4-cell quad
     L.fty = L.lanes_row ? 1 : kTileY;
     L.nfx = (nx + L.ftx - 1) / L.ftx;
     L.nfy = (ny + L.fty - 1) / L.fty;

@@ -284,7 +284,7 @@ struct QuadSmem<__half> {
 // the edge lane that got the wrong crossing value (the shuffle wraps within
 // its own warp) rewrites that one cell after a block barrier with the value
 // the neighbouring warp's edge lane left in shared memory.  One force flag
-// per 32-cell segment of a row.
+// per thread's quad.
 // Paired FP32 arithmetic (two cells per instruction).
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
@@ -540,9 +540,8 @@ __global__ void __launch_bounds__(256, 2)
     prior_grid_wait();
     allow_dependents();
 
-    // force flags per 32-cell segment of a row (the whole row if nx < 32); the
-    // lanes of one segment are consecutive lanes of one warp
-    constexpr int FTX = NX < 32 ? NX : 32;
+    // one force flag per quad: this thread's own
+    constexpr int FTX = 4;  // one force flag per quad (Lattice::ftx)
     const int fidx = row * (NX / FTX) + x0 / FTX;
     const bool has_old = flag_old[fidx] != 0;
     const bool has_cur = flag_cur[fidx] != 0;
@@ -550,8 +549,7 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
         for (int k = 0; k < 4; ++k) fold[cell0 + k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    __syncwarp();  // every lane of the segment has read its flag
-    if (has_old && active && x0 % FTX == 0) flag_old[fidx] = 0;
+    if (has_old && active) flag_old[fidx] = 0;
 
     // Arithmetic on cell pairs (0,1) and (2,3) with the paired FP32
     // instructions of sm_100+, in storage units: G = kScale g, so binary16
@@ -626,7 +624,7 @@ __global__ void __launch_bounds__(THREADS, 2)
         if ((int)blockIdx.x < n_tiles) { issue(blockIdx.x, 0); pending[0] = 1; }
         if ((int)(blockIdx.x + gridDim.x) < n_tiles) { issue(blockIdx.x + gridDim.x, 1); pending[1] = 1; }
     }
-    constexpr int FTX = NX < 32 ? NX : 32;
+    constexpr int FTX = 4;  // one force flag per quad (Lattice::ftx)
     int k = 0;
     bool gave_up = false;
     for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++k) {
@@ -650,8 +648,7 @@ __global__ void __launch_bounds__(THREADS, 2)
 #pragma unroll
             for (int q = 0; q < 4; ++q) fold[cell0 + q] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        __syncwarp();  // every lane of the segment has read its flag
-        if (has_old && active && x0 % FTX == 0) flag_old[fidx] = 0;
+        if (has_old && active) flag_old[fidx] = 0;
         // this thread's quad from the staged tile (an inactive lane reads row 0 of the tile)
         const S *tile = stage + (size_t)b * 19 * TILE + (active ? lr : 0) * NX + x0;
         float2 g[19][2];

@@ -13,11 +13,14 @@
 //      centroid c = origin + m / (4 V);
 //   2. the inertia terms of the faces about c.
 // In the float builds the per-face terms are formed in float from the
-// positions relative to the origin and only the sums are carried in double.
+// positions relative to the origin, each thread adds its few faces (about
+// four) in float, and the sums over threads, blocks and the cluster are
+// carried in double.
 //
 // The allocation-free entry point at the end keeps a three-launch form whose
 // per-block partial sums live in a fixed device array.
 #include <cooperative_groups.h>
+#include <type_traits>
 #include <mutex>
 #include <string>
 
@@ -176,6 +179,34 @@ struct FaceMath<NodeRead<float>> {
         An[1] = 0.5f * (e1[2] * e2[0] - e1[0] * e2[2]);
         An[2] = 0.5f * (e1[0] * e2[1] - e1[1] * e2[0]);
     }
+    // the same terms in float (a thread adds its few faces in float and the
+    // sums over threads and blocks are carried in double)
+    static __device__ __forceinline__ void stage1f(const NodeRead<float> &nodes, int4 t, const double o[3],
+                                                   float v[5]) {
+        float r[3], An[3];
+        geom(nodes, t, o, r, An);
+        const float rn = r[0] * An[0] + r[1] * An[1] + r[2] * An[2];
+        v[0] = rn * (1.0f / 3.0f);
+        v[1] = sqrtf(An[0] * An[0] + An[1] * An[1] + An[2] * An[2]);
+        v[2] = rn * r[0];
+        v[3] = rn * r[1];
+        v[4] = rn * r[2];
+    }
+    static __device__ __forceinline__ void stage2f(const NodeRead<float> &nodes, int4 t, const double o[3],
+                                                   const double c[3], float v[6]) {
+        float cen[3], An[3];
+        geom(nodes, t, o, cen, An);
+        float r[3];
+        for (int k = 0; k < 3; ++k) r[k] = cen[k] - (float)(c[k] - o[k]);
+        const float rn = (r[0] * An[0] + r[1] * An[1] + r[2] * An[2]) * 0.2f;
+        const float r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+        v[0] = (r2 - r[0] * r[0]) * rn;
+        v[1] = (r2 - r[1] * r[1]) * rn;
+        v[2] = (r2 - r[2] * r[2]) * rn;
+        v[3] = -r[0] * r[1] * rn;
+        v[4] = -r[0] * r[2] * rn;
+        v[5] = -r[1] * r[2] * rn;
+    }
     static __device__ __forceinline__ void stage1(const NodeRead<float> &nodes, int4 t,
                                                   const double o[3], double v[5]) {
         float r[3], An[3];
@@ -258,11 +289,22 @@ __global__ void __launch_bounds__(kTaylorClusterThreads) k_taylor_cluster(R node
     const double o[3] = {p.origin[3 * cap], p.origin[3 * cap + 1], p.origin[3 * cap + 2]};
     const int stride = CS * blockDim.x;
     double v[6] = {0, 0, 0, 0, 0, 0};
+    if constexpr (std::is_same<R, NodeRead<float>>::value) {
+        float vf[5] = {0, 0, 0, 0, 0};
 #pragma unroll 4
-    for (int f = f0 + rank * blockDim.x + threadIdx.x; f < f1; f += stride) {
-        double w[5];
-        FaceMath<R>::stage1(nodes, tri[f], o, w);
-        for (int k = 0; k < 5; ++k) v[k] += w[k];
+        for (int f = f0 + rank * blockDim.x + threadIdx.x; f < f1; f += stride) {
+            float w[5];
+            FaceMath<R>::stage1f(nodes, tri[f], o, w);
+            for (int k = 0; k < 5; ++k) vf[k] += w[k];
+        }
+        for (int k = 0; k < 5; ++k) v[k] = (double)vf[k];
+    } else {
+#pragma unroll 4
+        for (int f = f0 + rank * blockDim.x + threadIdx.x; f < f1; f += stride) {
+            double w[5];
+            FaceMath<R>::stage1(nodes, tri[f], o, w);
+            for (int k = 0; k < 5; ++k) v[k] += w[k];
+        }
     }
     block_sum_any<6>(v, sh);
     if (threadIdx.x == 0)
@@ -281,11 +323,22 @@ __global__ void __launch_bounds__(kTaylorClusterThreads) k_taylor_cluster(R node
     __syncthreads();
     const double c[3] = {cen_sh[2], cen_sh[3], cen_sh[4]};
     double I[6] = {0, 0, 0, 0, 0, 0};
+    if constexpr (std::is_same<R, NodeRead<float>>::value) {
+        float If[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll 4
-    for (int f = f0 + rank * blockDim.x + threadIdx.x; f < f1; f += stride) {
-        double w[6];
-        FaceMath<R>::stage2(nodes, tri[f], o, c, w);
-        for (int k = 0; k < 6; ++k) I[k] += w[k];
+        for (int f = f0 + rank * blockDim.x + threadIdx.x; f < f1; f += stride) {
+            float w[6];
+            FaceMath<R>::stage2f(nodes, tri[f], o, c, w);
+            for (int k = 0; k < 6; ++k) If[k] += w[k];
+        }
+        for (int k = 0; k < 6; ++k) I[k] = (double)If[k];
+    } else {
+#pragma unroll 4
+        for (int f = f0 + rank * blockDim.x + threadIdx.x; f < f1; f += stride) {
+            double w[6];
+            FaceMath<R>::stage2(nodes, tri[f], o, c, w);
+            for (int k = 0; k < 6; ++k) I[k] += w[k];
+        }
     }
     block_sum_any<6>(I, sh);
     if (threadIdx.x == 0)
