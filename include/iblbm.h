@@ -493,7 +493,9 @@ int iblbm_get_velocity(iblbm_sim *sim, double *host_out);
 int iblbm_get_density(iblbm_sim *sim, double *host_out);
 
 /* Full populations f_i (not deviations), [19][nz][ny][nx], velocity i as in
- * Fig. d3q19. */
+ * Fig. d3q19.  The setter uploads host_in (pinned memory copies fastest),
+ * checks it on the device and returns IBLBM_ERR_ARG, leaving the lattice as
+ * it was, if any value is not finite. */
 int iblbm_get_populations(iblbm_sim *sim, double *host_out);
 int iblbm_set_populations(iblbm_sim *sim, const double *host_in);
 

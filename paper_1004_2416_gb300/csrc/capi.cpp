@@ -2088,14 +2088,20 @@ int lattice_set_populations(iblbm_sim *s, int run, const double *host_in) {
     size_t po, vo;
     const Lattice Lr = run_lattice(s, run, &po, &vo);
     const size_t n = 19 * (size_t)Lr.ncell;
-    for (size_t k = 0; k < n; ++k)
-        if (!std::isfinite(host_in[k])) return fail(s, IBLBM_ERR_ARG, "non-finite population");
-    rc = ensure_scratch(s, sizeof(double) * n);
+    // the finiteness check runs on the device, on the uploaded copy: a word
+    // after the n values records a non-finite one and the conversion then
+    // leaves the lattice untouched
+    rc = ensure_scratch(s, sizeof(double) * (n + 1));
     if (rc) return rc;
+    int *bad = (int *)(s->d_scratch + n);
+    CK(cudaMemsetAsync(bad, 0, sizeof(int), s->stream));
     CK(cudaMemcpyAsync(s->d_scratch, host_in, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
-    launch_f64_to_pop(s->prec, Lr, s->d_scratch, (char *)s->pop[s->cur] + po, s->stream);
+    launch_f64_to_pop(s->prec, Lr, s->d_scratch, (char *)s->pop[s->cur] + po, bad, s->stream);
     CK(cudaGetLastError());
+    int bad_host = 0;
+    CK(cudaMemcpyAsync(&bad_host, bad, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
+    if (bad_host) return fail(s, IBLBM_ERR_ARG, "non-finite population");
     return IBLBM_OK;
 }
 

@@ -172,7 +172,9 @@ void launch_init_fluid(int prec, const Lattice &L, void *pop, int mode, double u
 void launch_moments(int prec, const Lattice &L, const void *pop, const void *force, double *rho,
                     double *u, cudaStream_t s);
 void launch_pop_to_f64(int prec, const Lattice &L, const void *pop, double *out, cudaStream_t s);
-void launch_f64_to_pop(int prec, const Lattice &L, const double *in, void *pop, cudaStream_t s);
+// Checks the n = 19 ncell uploaded values on the device (*bad = 1 on a
+// non-finite one; *bad must be 0 before) and converts them unless one was.
+void launch_f64_to_pop(int prec, const Lattice &L, const double *in, void *pop, int *bad, cudaStream_t s);
 void launch_force_to_f64(int prec, const Lattice &L, const void *force, double *out, cudaStream_t s);
 
 // ---- ib.cu ----------------------------------------------------------------------

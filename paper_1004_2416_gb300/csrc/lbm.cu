@@ -920,8 +920,20 @@ __global__ void k_pop_to_f64(const S *pop, long long ncell, double *out) {
     out[k] = (double)Store<S, T>::load(pop + k) + q_w<double>(i);
 }
 
+// Sets *bad when any of the n uploaded values is not finite.
+__global__ void k_flag_nonfinite(const double *in, long long n, int *bad) {
+    bool any = false;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x)
+        any |= !isfinite(in[k]);
+    if (__syncthreads_or(any) && threadIdx.x == 0) *bad = 1;
+}
+
+// Converts uploaded FP64 populations to the storage format, unless the check
+// before it found a non-finite value (the lattice then stays as it was).
 template <typename S, typename T>
-__global__ void k_f64_to_pop(const double *in, long long ncell, S *pop) {
+__global__ void k_f64_to_pop(const double *in, long long ncell, S *pop, const int *bad) {
+    if (*bad) return;
     long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (k >= 19 * ncell) return;
     int i = (int)(k / ncell);
@@ -1280,11 +1292,14 @@ void launch_pop_to_f64(int prec, const Lattice &L, const void *pop, double *out,
     else k_pop_to_f64<__half, float><<<nb, 256, 0, s>>>((const __half *)pop, L.ncell, out);
 }
 
-void launch_f64_to_pop(int prec, const Lattice &L, const double *in, void *pop, cudaStream_t s) {
-    unsigned nb = blocks_for(19 * L.ncell, 256);
-    if (prec == kF64) k_f64_to_pop<double, double><<<nb, 256, 0, s>>>(in, L.ncell, (double *)pop);
-    else if (prec == kF32) k_f64_to_pop<float, float><<<nb, 256, 0, s>>>(in, L.ncell, (float *)pop);
-    else k_f64_to_pop<__half, float><<<nb, 256, 0, s>>>(in, L.ncell, (__half *)pop);
+void launch_f64_to_pop(int prec, const Lattice &L, const double *in, void *pop, int *bad, cudaStream_t s) {
+    const long long n = 19 * L.ncell;
+    unsigned nc = (unsigned)std::min<long long>(blocks_for(n, 256), 8LL * sm_count());
+    k_flag_nonfinite<<<nc, 256, 0, s>>>(in, n, bad);
+    unsigned nb = blocks_for(n, 256);
+    if (prec == kF64) k_f64_to_pop<double, double><<<nb, 256, 0, s>>>(in, L.ncell, (double *)pop, bad);
+    else if (prec == kF32) k_f64_to_pop<float, float><<<nb, 256, 0, s>>>(in, L.ncell, (float *)pop, bad);
+    else k_f64_to_pop<__half, float><<<nb, 256, 0, s>>>(in, L.ncell, (__half *)pop, bad);
 }
 
 void launch_force_to_f64(int prec, const Lattice &L, const void *force, double *out, cudaStream_t s) {

@@ -111,11 +111,21 @@ def test_upload_refuses_nan(prec):
     from paper_1004_2416_gb300 import Sim
 
     s = Sim(20, 6, 7, tau=1.0, precision=prec, delta_points=3)
+    before = s.get_populations()
     f = O.init_couette(20, 6, 7, 0.02)
-    f[3, 2, 1, 4] = np.nan
-    with pytest.raises(B.IblbmError) as e:
-        s.set_populations(f)
-    assert e.value.code == B.IBLBM_ERR_ARG and "non-finite" in str(e.value)
+    for bad in (np.nan, np.inf, -np.inf):
+        g = f.copy()
+        g[3, 2, 1, 4] = bad
+        with pytest.raises(B.IblbmError) as e:
+            s.set_populations(g)
+        assert e.value.code == B.IBLBM_ERR_ARG and "non-finite" in str(e.value)
+        assert np.array_equal(s.get_populations(), before)  # the lattice is left as it was
+    g = f.copy()
+    g[18, 6, 5, 19] = np.nan  # the last value
+    with pytest.raises(B.IblbmError):
+        s.set_populations(g)
+    s.set_populations(f)  # a clean upload after refused ones
+    assert np.abs(s.get_populations() - f).max() < {"fp64": 1e-15, "fp32": 1e-7, "fp16": 1e-4}[prec]
     s.step(1)
     s.sync()
     s.close()
