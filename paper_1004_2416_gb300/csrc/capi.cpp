@@ -1293,6 +1293,12 @@ int step_graph(iblbm_sim *s, int len, int cur, int first_rec, iblbm_sim::StepGra
     if (e == cudaSuccess)
         // kernel nodes keep the priority of the stream they were captured on
         e = cudaGraphInstantiate(&g.exec, graph, cudaGraphInstantiateFlagUseNodePriority);
+    // the device copy of the graph is made now, not at its first launch (a
+    // prepared call's first replay then costs what the others do)
+    if (e == cudaSuccess) {
+        e = cudaGraphUpload(g.exec, s->stream);
+        if (e != cudaSuccess) cudaGraphExecDestroy(g.exec);
+    }
     if (graph) cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
         g.exec = nullptr;

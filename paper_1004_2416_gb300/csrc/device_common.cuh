@@ -160,6 +160,14 @@ __device__ __forceinline__ int wrap_index(int a, int n) {
     int r = a % n;
     return r < 0 ? r + n : r;
 }
+// wrap_index(w0 + k, n) for w0 already in [0, n) and 0 <= k < N: one
+// subtraction when n >= N (no division), else the general form.
+template <int N>
+__device__ __forceinline__ int wrap_next(int w0, int k, int n) {
+    const int a = w0 + k;
+    if (a < n) return a;
+    return n >= N ? a - n : wrap_index(a, n);
+}
 
 __device__ __forceinline__ void set_status(int *status, int bit) { atomicOr(status, bit); }
 

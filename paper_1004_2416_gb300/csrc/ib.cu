@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256)
     const int bx = stencil_first<N>(pc[0]), by = stencil_first<N>(pc[1]), bz = stencil_first<N>(pc[2]);
     const RunDesc R = runs ? runs[node_run[node]] : single;
     const int sx = __ffs(R.tx) - 1, sy = __ffs(R.ty) - 1;
-    const int xw0 = wrap_index(bx, SLAB ? R.gnx : R.nx);
+    const int xw0 = wrap_index(bx, SLAB ? R.gnx : R.nx), yw0 = wrap_index(by, R.ny);
     T wrow[CX == N ? N : 1];
     if constexpr (CX == N) {
 #pragma unroll
@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(256)
         T d[3];
         pos.rel(p, bx, Y, Z, d);
         const T wy = delta_phi<N>(d[1]), wz = delta_phi<N>(d[2]);
-        const int yw = wrap_index(Y, R.ny);
+        const int yw = wrap_next<N>(yw0, r % N, R.ny);
         const long long rc = (long long)R.nx * (yw + (long long)R.ny * Z);
         const long long rt = ((long long)Z * R.nty + (yw >> sy)) * R.ntx;
         int last = -1;
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(256)
         pc[0] = p[0]; pc[1] = p[1]; pc[2] = p[2];
     }
     const int bx = stencil_first<N>(pc[0]), by = stencil_first<N>(pc[1]), bz = stencil_first<N>(pc[2]);
-    const int xw0 = wrap_index(bx, SLAB ? R.gnx : nx);
+    const int xw0 = wrap_index(bx, SLAB ? R.gnx : nx), yw0 = wrap_index(by, ny);
     // this lane's pieces; a stencil beyond a wall is reported by the spreading
     bool in[RPL];
     long long rc[RPL];
@@ -371,7 +371,7 @@ __global__ void __launch_bounds__(256)
         Y[j] = by + r % N;
         Z[j] = bz + r / N;
         in[j] = sl < NS && Z[j] >= 0 && Z[j] < nz;
-        rc[j] = in[j] ? (long long)nx * (wrap_index(Y[j], ny) + (long long)ny * Z[j]) : 0;
+        rc[j] = in[j] ? (long long)nx * (wrap_next<N>(yw0, r % N, ny) + (long long)ny * Z[j]) : 0;
 #pragma unroll
         for (int c = 0; c < CX; ++c) {
             const int xa = xw0 + KX[j] + c;
