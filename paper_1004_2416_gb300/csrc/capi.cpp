@@ -437,7 +437,7 @@ int ensure_mesh(iblbm_sim *s) {
         };
         TaylorPlan p{};
         p.n_caps = nc;
-        p.cluster = taylor_cluster_size(maxf, taylor_max_cluster());
+        p.cluster = taylor_cluster_size(maxf, taylor_max_cluster(), nc);
         p.cap_face0 = (const int *)P(sizeof(int) * (nc + 1));
         p.origin = (const double *)P(sizeof(double) * 3 * nc);
         p.out = (double *)P(sizeof(double) * 12 * nc);

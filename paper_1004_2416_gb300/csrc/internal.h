@@ -261,12 +261,18 @@ struct TaylorPlan {
     unsigned *ticket;       // blocks of a recording launch done (returns to 0)
 };
 // Blocks of kTaylorClusterThreads threads per capsule: about four faces per
-// thread, at most max_cluster (taylor_max_cluster()).  (Two faces per thread
-// in blocks of 256 measured slower: 30 vs 27.5 us for eight records of one
-// 5120-face capsule, 72 vs 46 us for one record of 200 1280-face capsules.)
+// thread, at most max_cluster (taylor_max_cluster()), and no more than keep
+// all capsules' blocks within one per SM of 152: a suspension has blocks
+// enough, and the record runs beside the steps, whose kernels lose the SMs
+// it holds.  (Two faces per thread in blocks of 256 measured slower: 30 vs
+// 27.5 us for eight records of one 5120-face capsule, 72 vs 46 us for one
+// record of 200 1280-face capsules; for those 200 capsules one block each
+// instead of three: step 176.0 -> 167.7 us with a record every step.)
 constexpr int kTaylorClusterThreads = 128;
-inline int taylor_cluster_size(int max_faces_per_capsule, int max_cluster) {
+inline int taylor_cluster_size(int max_faces_per_capsule, int max_cluster, int n_caps) {
     int c = (max_faces_per_capsule + 4 * kTaylorClusterThreads - 1) / (4 * kTaylorClusterThreads);
+    const int fill = n_caps > 0 ? 152 / n_caps : 152;
+    if (c > fill) c = fill;
     return c < 1 ? 1 : (c > max_cluster ? max_cluster : c);
 }
 // Largest cluster the reduction kernel may use on this GPU (16 where allowed, else 8).
