@@ -20,9 +20,10 @@ def test_mesh_quality_and_fit(prec):
     q0 = g.mesh_quality(0)
     # at the start the nodes are the reference (float builds keep ~48 bits of them)
     assert abs(q0["dA_mean"]) < 1e-12 and q0["dA_std"] < 1e-12 and abs(q0["dV"]) < 1e-12
+    g.step(case.steps - 20)
     x_then = g.get_nodes()
     c_then = np.array([g.taylor(0)[k] for k in ("c_x", "c_y", "c_z")])
-    g.step(case.steps)
+    g.step(20)
     x = g.get_nodes()
     X0, tri = O.icosphere(c.subdivisions, c.radius, c.center)
     q = g.mesh_quality(0)
@@ -43,13 +44,16 @@ def test_mesh_quality_and_fit(prec):
     for k in O.FIT_KEYS:
         assert fit[k] == pytest.approx(ofit[k], rel=1e-9, abs=1e-12), k
     assert fit["D"] == pytest.approx(T["D"], rel=0.1)
-    om, mean = B.tank_treading(x_then, x, c_then, cen, float(case.steps))
-    om_o, mean_o = O.tank_treading(x_then, x, c_then, cen, float(case.steps))
-    # per node to 1e-9 of the largest rate: a node close to the rotation axis
-    # has an ill-conditioned angle, which the two routes round differently
-    assert np.abs(om - om_o).max() <= 1e-9 * np.abs(om_o).max()
-    assert mean == pytest.approx(mean_o, rel=1e-9)
+    # rotation rates over the last 20 steps (angles well below pi, so both
+    # routes take the same branch), library against oracle on the nodes away
+    # from the rotation axis, whose angles are well conditioned
+    om, mean = B.tank_treading(x_then, x, c_then, cen, 20.0)
+    om_o, mean_o = O.tank_treading(x_then, x, c_then, cen, 20.0)
+    far = np.hypot(x[:, 0] - cen[0], x[:, 2] - cen[2]) > 0.3 * c.radius
+    assert far.sum() > len(x) // 2
+    assert np.abs(om - om_o)[far].max() <= 1e-9 * np.abs(om_o[far]).max()
+    assert mean == pytest.approx(mean_o, rel=1e-6)
     # the membrane turns with the shear (shear rate 2 u_w / nz; a rigid
     # sphere would turn at half of it, a deforming one at no more than that)
     rate = 2 * case.u_wall / case.shape[2]
-    assert 0.05 * rate < mean < 0.6 * rate
+    assert 0.05 * rate < np.median(om[far]) < 0.6 * rate
