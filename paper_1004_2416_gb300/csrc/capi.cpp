@@ -244,6 +244,9 @@ void drop_graphs(iblbm_sim *s) {
 
 int ensure_scratch(iblbm_sim *s, size_t bytes) {
     if (s->scratch_bytes >= bytes) return IBLBM_OK;
+    // whole MiB, so that requests a few words apart (a field read back, then
+    // the same field uploaded with its status word) share one allocation
+    bytes = (bytes + (1u << 20) - 1) & ~(size_t)((1u << 20) - 1);
     dev_free(s, s->d_scratch);
     s->d_scratch = (double *)dev_alloc(s, bytes);
     s->scratch_bytes = s->d_scratch ? bytes : 0;
