@@ -608,7 +608,7 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr, 
         mark("Taylor record");
     }
     if (ev) cudaEventRecord(ev[4], s->stream);
-    s->launches += 3 + (pre ? 1 : 0) + (record && ev ? 3 : 0);
+    s->launches += 3 + (pre ? 1 : 0) + (record && ev ? 1 : 0);
     s->cur = n;
 }
 
@@ -621,7 +621,7 @@ void reduce_snapshots(iblbm_sim *s) {
         cudaStreamWaitEvent(s->side, s->ev_fork, 0);
         launch_taylor_snapshots(s->prec, s->mesh, s->plan, true, s->snap_x, s->snap_lo, h * s->rec_batch,
                                 2 * s->rec_batch, s->rec_fill, s->side);
-        s->launches += 3;
+        s->launches += 1;
         cudaEventRecord(s->ev_join[h], s->side);
         s->side_pending[h] = true;
         cudaError_t e = cudaGetLastError();
