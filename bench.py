@@ -64,6 +64,8 @@ def _args():
                    help="interpolation: -1 automatic, 0 gather at the stencil cells, 1 cell velocities first")
     p.add_argument("--launch-overlap", type=int, default=-1, choices=[-1, 0, 1],
                    help="step kernels with programmatic dependent launch: 1 on, 0 off, -1 automatic")
+    p.add_argument("--deterministic-spreading", action="store_true",
+                   help="force density summed in 64-bit fixed point (bit-reproducible steps)")
     p.add_argument("--collide-staging", type=int, default=-1, choices=[-1, 0, 1],
                    help="collide populations staged in shared memory by bulk copies: 1 on, 0 off, -1 automatic")
     p.add_argument("--adjoint-only", action="store_true",
@@ -169,6 +171,7 @@ def _config(case, a):
         "record_every": a.record_every,
         "equilibrium": "second order, Eq. (equilibrium)" if a.equilibrium == 2 else "linearised, Sec. IV.A",
         "advection": "Euler" if a.integrator == 0 else "Adams-Bashforth",
+        "spreading": "64-bit fixed point (deterministic)" if a.deterministic_spreading else "float atomics",
         "l2": f"inputs larger than L2: two population buffers of {19 * case.ncell * BYTES_PER_CELL[case.precision] // 38 / 1e6:.0f} MB each",
         "parallelism": "replicas (one independent simulation per rank)",
     }
@@ -485,6 +488,8 @@ def run_ours(a):
     sim.set_launch_overlap(a.launch_overlap)
     if not batch:
         sim.set_collide_staging(a.collide_staging)
+        if a.deterministic_spreading:
+            sim.set_deterministic_spreading(True)
     sim.set_equilibrium(a.equilibrium)
     sim.set_integrator(a.integrator)
     batch = isinstance(case, Batch)

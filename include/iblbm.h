@@ -354,6 +354,22 @@ int iblbm_set_equilibrium(iblbm_sim *sim, int order);
  * Synchronising. */
 int iblbm_set_interp_mode(iblbm_sim *sim, int mode);
 
+/* Deterministic spreading (on = 1; off = 0, the default): the force density
+ * of Eq. (forcespreading) is summed in 64-bit fixed point, whose integer
+ * additions give the same bits in any order, then converted to the storage
+ * type for the collide.  With it every time step is bit-reproducible (float
+ * atomics otherwise add in an order that varies between runs), so a restart
+ * from a checkpoint continues the same trajectory bit for bit with membranes
+ * too.  Resolution 2^-40 (float and half storage) or 2^-52 (FP64 build) per
+ * contribution; a contribution of magnitude 2^22 (float) or 2^10 (FP64) or
+ * more is not added and the next synchronising call returns
+ * IBLBM_ERR_UNSTABLE.  Costs three 64-bit integer atomics per stencil cell
+ * instead of one vector atomic, a conversion pass over the force tiles and
+ * 24 bytes per cell of device memory.  A single lattice only
+ * (IBLBM_ERR_STATE for a batch or a slab group); IBLBM_ERR_ARG for another
+ * value.  Synchronising. */
+int iblbm_set_deterministic_spreading(iblbm_sim *sim, int on);
+
 /* Whether the kernels of a time step are launched with programmatic
  * dependent launch: each kernel may start while the one before it in the
  * step finishes, does what needs nothing of that kernel (the interpolation

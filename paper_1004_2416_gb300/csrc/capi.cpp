@@ -79,6 +79,9 @@ struct iblbm_sim {
     int staging = -1;      // collide populations staged by bulk copies: -1 automatic, 0 off, 1 on
     unsigned long long wait_ns = 1000000000ull;  // longest device wait for staged data
     int overlap = -1;      // step kernels overlapping their predecessor: -1 automatic, 0 off, 1 on
+    // deterministic spreading: the force density summed in 64-bit fixed point
+    // ([ncell][3], zero between steps), then converted (iblbm_set_deterministic_spreading)
+    unsigned long long *d_fix = nullptr;
     // Method variants: node advection 0 = Euler (Eq. positionupdate), 1 =
     // Adams-Bashforth (Sec. II.C), which needs the node velocities of the step
     // before (ab2_ready); equilibrium order 2 = Eq. (equilibrium), 1 = the
@@ -535,6 +538,7 @@ bool cell_velocity_first(const iblbm_sim *s) {
 // place on the side stream.
 void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr, cudaEvent_t *graph_ev = nullptr) {
     const int c = s->cur, n = 1 - s->cur;
+    const bool det = s->d_fix != nullptr && !s->batch;
     auto mark = [s](const char *what) {
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess && !s->launch_fail) s->launch_fail = what;
@@ -549,7 +553,9 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr, 
     if (ev) cudaEventRecord(ev[0], s->stream);
     gmark(0);
     launch_force_spread(s->prec, s->delta, s->L, s->mesh, s->force[n], s->flags[n], s->d_status,
-                        s->batch ? s->d_runs : nullptr, s->d_node_run, s->stream, ov);
+                        s->batch ? s->d_runs : nullptr, s->d_node_run, s->stream, ov, det ? s->d_fix : nullptr);
+    if (det && s->mesh.n_nodes > 0)
+        launch_fix_to_force(s->prec, s->L, s->d_fix, s->force[n], s->flags[n], s->stream, ov);
     mark("membrane force + spreading");
     if (ev) cudaEventRecord(ev[1], s->stream);
     gmark(1);
@@ -608,7 +614,7 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr, 
         mark("Taylor record");
     }
     if (ev) cudaEventRecord(ev[4], s->stream);
-    s->launches += 3 + (pre ? 1 : 0) + (record && ev ? 1 : 0);
+    s->launches += 3 + (det && s->mesh.n_nodes > 0 ? 1 : 0) + (pre ? 1 : 0) + (record && ev ? 1 : 0);
     s->cur = n;
 }
 
@@ -645,7 +651,7 @@ void join_side(iblbm_sim *s) {
 int check_sim(const iblbm_sim *s) { return s ? IBLBM_OK : IBLBM_ERR_ARG; }
 
 int status_from_bits(int bits) {
-    if (bits & 1) return IBLBM_ERR_UNSTABLE;
+    if (bits & 9) return IBLBM_ERR_UNSTABLE;
     if (bits & 2) return IBLBM_ERR_STENCIL;
     if (bits & 4) return IBLBM_ERR_TIMEOUT;
     return IBLBM_OK;
@@ -668,6 +674,8 @@ int sync_status(iblbm_sim *s) {
     if (bits) {
         CK(cudaMemset(s->d_status, 0, sizeof(int)));
         int rc = status_from_bits(bits);
+        if (!(bits & 1) && (bits & 8))
+            return fail(s, rc, "a spread force contribution left the fixed-point range of the deterministic spreading");
         return fail(s, rc, status_message(rc));
     }
     return IBLBM_OK;
@@ -1002,6 +1010,7 @@ int iblbm_destroy(iblbm_sim *s) {
         dev_free(s, s->flags[k]);
     }
     dev_free(s, s->d_status);
+    dev_free(s, s->d_fix);
     dev_free(s, s->uvel);
     dev_free(s, s->d_readback);
     dev_free(s, s->d_scratch);
@@ -2037,6 +2046,28 @@ int iblbm_set_interp_mode(iblbm_sim *s, int mode) {
     CK(cudaStreamSynchronize(s->stream));
     drop_graphs(s);
     s->interp_mode = mode;
+    return IBLBM_OK;
+}
+
+int iblbm_set_deterministic_spreading(iblbm_sim *s, int on) {
+    if (!s) return IBLBM_ERR_ARG;
+    if (is_group(s) || s->batch)
+        return fail(s, IBLBM_ERR_STATE, "deterministic spreading is for a single lattice");
+    if (on != 0 && on != 1) return fail(s, IBLBM_ERR_ARG, "on must be 0 or 1");
+    CK(cudaSetDevice(s->device));
+    join_side(s);
+    CK(cudaStreamSynchronize(s->stream));
+    drop_graphs(s);
+    if (on && !s->d_fix) {
+        const size_t bytes = sizeof(unsigned long long) * 3 * (size_t)s->L.ncell;
+        s->d_fix = (unsigned long long *)dev_alloc(s, bytes);
+        if (!s->d_fix) return fail(s, IBLBM_ERR_OOM, "fixed-point accumulator allocation failed");
+        CK(cudaMemsetAsync(s->d_fix, 0, bytes, s->stream));
+        CK(cudaStreamSynchronize(s->stream));
+    } else if (!on && s->d_fix) {
+        dev_free(s, s->d_fix);
+        s->d_fix = nullptr;
+    }
     return IBLBM_OK;
 }
 

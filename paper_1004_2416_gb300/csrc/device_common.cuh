@@ -14,6 +14,7 @@ enum : int {
     kStatusUnstable = 1,  // density out of (0.5, 2) or NaN
     kStatusStencil = 2,   // an IBM stencil cell beyond a wall
     kStatusTimeout = 4,   // a bounded wait for staged data gave up
+    kStatusForceRange = 8,  // a force contribution beyond the deterministic spreading's fixed-point range
 };
 
 // D3Q19 velocity set numbered as in Fig. d3q19 of the paper (the arrow i

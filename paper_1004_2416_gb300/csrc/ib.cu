@@ -56,7 +56,9 @@ namespace iblbm {
 // node's n^2 stencil rows.  Four nodes per warp waste fewer lanes on the faces
 // (a node has five or six) when there are enough nodes to fill the GPU; one
 // node per warp keeps more warps in flight otherwise.
-template <int N, typename T, int NPW, bool SLAB = false>
+// FIX: add into the 64-bit fixed-point accumulator `fix` (three per cell)
+// instead of the float force density (deterministic spreading).
+template <int N, typename T, int NPW, bool SLAB = false, bool FIX = false>
 __global__ void __launch_bounds__(256)
     k_force_spread(int n_nodes, PosView<T> pos, const int *__restrict__ adj_off,
                    const int4 *__restrict__ adj4, const int *__restrict__ node_cap,
@@ -65,7 +67,7 @@ __global__ void __launch_bounds__(256)
                    typename Vec4<T>::type *__restrict__ nodeF,
                    typename Vec4<T>::type *__restrict__ force, uint8_t *__restrict__ flags,
                    RunDesc single, const RunDesc *__restrict__ runs,
-                   const int *__restrict__ node_run, int *status) {
+                   const int *__restrict__ node_run, int *status, unsigned long long *__restrict__ fix) {
     using V4 = typename Vec4<T>::type;
     prior_grid_wait();  // the node positions come from the previous interpolation
     allow_dependents();
@@ -187,7 +189,10 @@ __global__ void __launch_bounds__(256)
             } else {
                 xw = xa < R.nx ? xa : wrap_index(xa, R.nx);
             }
-            add_force(&fr[rc + xw], w * fx, w * fy, w * fz);
+            if constexpr (FIX)
+                add_force_fix(fix + 3 * (R.cell_off + rc + xw), w * fx, w * fy, w * fz, status);
+            else
+                add_force(&fr[rc + xw], w * fx, w * fy, w * fz);
             const int xt = xw >> sx;
             if (xt != last) {
                 flr[rt + xt] = 1;
@@ -572,18 +577,42 @@ static RunDesc single_run(const Lattice &L) {
 template <int N, typename T>
 static void force_spread_impl(const Lattice &L, const MeshDev &m, void *force, uint8_t *flags,
                               int *status, const RunDesc *runs, const int *node_run,
-                              cudaStream_t s, bool ov) {
+                              cudaStream_t s, bool ov, unsigned long long *fix) {
     using V4 = typename Vec4<T>::type;
     // four nodes per warp once one-node warps would exceed 32 per SM
     const bool four = m.n_nodes >= 152 * 32;
     const long long warps = four ? (m.n_nodes + 3) / 4 : m.n_nodes;
     const int wpb = warps >= 152 * 16 ? 4 : 2;
     const unsigned nb = (unsigned)((warps + wpb - 1) / wpb);
-    auto kern = four ? k_force_spread<N, T, 4> : k_force_spread<N, T, 1>;
+    auto kern = fix ? (four ? k_force_spread<N, T, 4, false, true> : k_force_spread<N, T, 1, false, true>)
+                    : (four ? k_force_spread<N, T, 4> : k_force_spread<N, T, 1>);
     launch_maybe_overlapped(kern, dim3(nb), dim3(32 * wpb), s, ov,
         m.n_nodes, view<T>(m), m.adj_off, (const int4 *)m.adj4, m.node_cap, (const V4 *)m.fconst,
         (const V4 *)m.capmod, (V4 *)m.F, (V4 *)force, flags, single_run(L), runs, node_run,
-        status);
+        status, fix);
+}
+
+// The fixed-point sums of the cells of the flagged tiles to the force
+// density (one thread per cell), zeroing the accumulators for the next step.
+template <typename T>
+__global__ void __launch_bounds__(256)
+    k_fix_to_force(RunDesc R, unsigned long long *__restrict__ fix, typename Vec4<T>::type *__restrict__ force,
+                   const uint8_t *__restrict__ flags) {
+    using V4 = typename Vec4<T>::type;
+    prior_grid_wait();  // the sums come from the spreading
+    allow_dependents();
+    const long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (cell >= R.ncell) return;
+    const int x = (int)(cell % R.nx);
+    const long long rest = cell / R.nx;
+    const int y = (int)(rest % R.ny), z = (int)(rest / R.ny);
+    if (!flags[((long long)z * R.nty + y / R.ty) * R.ntx + x / R.tx]) return;
+    unsigned long long *q = fix + 3 * cell;
+    const T inv = T(1) / T(1ll << kFixBits<T>);
+    force[cell] = V4{(T)(long long)q[0] * inv, (T)(long long)q[1] * inv, (T)(long long)q[2] * inv, T(0)};
+    q[0] = 0ull;
+    q[1] = 0ull;
+    q[2] = 0ull;
 }
 
 template <int N, typename S, typename T>
@@ -632,17 +661,28 @@ static void flag_velocity_impl(const Lattice &L, const void *pop, const void *fo
 
 void launch_force_spread(int prec, int delta, const Lattice &L, const MeshDev &m, void *force,
                          uint8_t *flags, int *status, const RunDesc *runs, const int *node_run,
-                         cudaStream_t s, bool overlap) {
+                         cudaStream_t s, bool overlap, unsigned long long *fix) {
     if (m.n_nodes == 0) return;
     if (prec == kF64) {
-        if (delta == 2) force_spread_impl<2, double>(L, m, force, flags, status, runs, node_run, s, overlap);
-        else if (delta == 3) force_spread_impl<3, double>(L, m, force, flags, status, runs, node_run, s, overlap);
-        else force_spread_impl<4, double>(L, m, force, flags, status, runs, node_run, s, overlap);
+        if (delta == 2) force_spread_impl<2, double>(L, m, force, flags, status, runs, node_run, s, overlap, fix);
+        else if (delta == 3) force_spread_impl<3, double>(L, m, force, flags, status, runs, node_run, s, overlap, fix);
+        else force_spread_impl<4, double>(L, m, force, flags, status, runs, node_run, s, overlap, fix);
     } else {
-        if (delta == 2) force_spread_impl<2, float>(L, m, force, flags, status, runs, node_run, s, overlap);
-        else if (delta == 3) force_spread_impl<3, float>(L, m, force, flags, status, runs, node_run, s, overlap);
-        else force_spread_impl<4, float>(L, m, force, flags, status, runs, node_run, s, overlap);
+        if (delta == 2) force_spread_impl<2, float>(L, m, force, flags, status, runs, node_run, s, overlap, fix);
+        else if (delta == 3) force_spread_impl<3, float>(L, m, force, flags, status, runs, node_run, s, overlap, fix);
+        else force_spread_impl<4, float>(L, m, force, flags, status, runs, node_run, s, overlap, fix);
     }
+}
+
+void launch_fix_to_force(int prec, const Lattice &L, unsigned long long *fix, void *force, const uint8_t *flags,
+                         cudaStream_t s, bool overlap) {
+    const unsigned nb = (unsigned)((L.ncell + 255) / 256);
+    if (prec == kF64)
+        launch_maybe_overlapped(k_fix_to_force<double>, dim3(nb), dim3(256), s, overlap, single_run(L), fix,
+                                (dvec4 *)force, flags);
+    else
+        launch_maybe_overlapped(k_fix_to_force<float>, dim3(nb), dim3(256), s, overlap, single_run(L), fix,
+                                (float4 *)force, flags);
 }
 
 void launch_flag_velocity(int prec, const Lattice &L, const void *pop, const void *force, const uint8_t *flags,
@@ -687,7 +727,7 @@ static void force_spread_slab_impl(const Lattice &L, const MeshDev &m, void *for
     const unsigned nb = (unsigned)((m.n_nodes + kNodesPerBlock - 1) / kNodesPerBlock);
     k_force_spread<N, T, 1, true><<<nb, 32 * kNodesPerBlock, 0, s>>>(
         m.n_nodes, view<T>(m), m.adj_off, (const int4 *)m.adj4, m.node_cap, (const V4 *)m.fconst,
-        (const V4 *)m.capmod, (V4 *)m.F, (V4 *)force, flags, slab_run(L), nullptr, nullptr, status);
+        (const V4 *)m.capmod, (V4 *)m.F, (V4 *)force, flags, slab_run(L), nullptr, nullptr, status, nullptr);
 }
 
 template <int N, typename S, typename T>

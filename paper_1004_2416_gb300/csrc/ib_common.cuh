@@ -120,6 +120,36 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// Deterministic spreading: the force density accumulates in 64-bit fixed
+// point (integer additions are associative, so the sum does not depend on
+// the order of the atomics), kFixBits fractional bits: 2^-40 (about 1e-12)
+// in the float builds, 2^-52 in the FP64 build; a contribution of magnitude
+// 2^22 (float) or 2^10 (FP64) or more is refused with kStatusForceRange.
+template <typename T>
+constexpr int kFixBits = 40;
+template <>
+constexpr int kFixBits<double> = 52;
+__device__ __forceinline__ void add_force_fix(unsigned long long *f, float x, float y, float z, int *status) {
+    constexpr float S = 1099511627776.0f;  // 2^40
+    const float v[3] = {x * S, y * S, z * S};
+    if (!(fabsf(v[0]) < 4.6e18f && fabsf(v[1]) < 4.6e18f && fabsf(v[2]) < 4.6e18f)) {
+        set_status(status, kStatusForceRange);
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) atomicAdd(f + k, (unsigned long long)__float2ll_rn(v[k]));
+}
+__device__ __forceinline__ void add_force_fix(unsigned long long *f, double x, double y, double z, int *status) {
+    constexpr double S = 4503599627370496.0;  // 2^52
+    const double v[3] = {x * S, y * S, z * S};
+    if (!(fabs(v[0]) < 4.6e18 && fabs(v[1]) < 4.6e18 && fabs(v[2]) < 4.6e18)) {
+        set_status(status, kStatusForceRange);
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) atomicAdd(f + k, (unsigned long long)__double2ll_rn(v[k]));
+}
+
 __device__ __forceinline__ void add_force(float4 *f, float x, float y, float z) {
     atomicAdd(f, make_float4(x, y, z, 0.0f));
 }

@@ -180,8 +180,13 @@ void launch_force_to_f64(int prec, const Lattice &L, const void *force, double *
 // ---- ib.cu ----------------------------------------------------------------------
 // runs / node_run: device run table and per-node run index of a batch, or
 // null for a single lattice described by L.
+// fix (may be null): deterministic spreading, the sums in 64-bit fixed
+// point in fix [ncell][3] (zero on entry), turned into the force density of
+// the flagged tiles by launch_fix_to_force, which zeroes them again.
 void launch_force_spread(int prec, int delta, const Lattice &L, const MeshDev &m, void *force,
                          uint8_t *flags, int *status, const RunDesc *runs, const int *node_run,
+                         cudaStream_t s, bool overlap = false, unsigned long long *fix = nullptr);
+void launch_fix_to_force(int prec, const Lattice &L, unsigned long long *fix, void *force, const uint8_t *flags,
                          cudaStream_t s, bool overlap = false);
 // velocity (Vec4) of every cell of the force-flagged tiles from the
 // populations after the step and the step's force density; items / n_items:

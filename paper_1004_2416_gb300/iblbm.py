@@ -110,6 +110,7 @@ _SIGS = {
     "iblbm_checkpoint_size": (_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "iblbm_set_interp_mode": (_int, [_vp, _int]),
     "iblbm_set_launch_overlap": (_int, [_vp, _int]),
+    "iblbm_set_deterministic_spreading": (_int, [_vp, _int]),
     "iblbm_read_async": (_int, [_vp, _vp, _vp]),
     "iblbm_taylor_from_sums": (_int, [_vp, _vp]),
     "iblbm_set_integrator": (_int, [_vp, _int]),
@@ -557,6 +558,10 @@ class Sim:
     def set_interp_mode(self, mode: int):
         """-1 automatic (default), 0 gather at the stencil cells, 1 cell velocities first."""
         _check(iblbm_set_interp_mode(self._h, int(mode)), self._h)
+
+    def set_deterministic_spreading(self, on: bool):
+        """Force density summed in 64-bit fixed point: bit-reproducible steps."""
+        _check(iblbm_set_deterministic_spreading(self._h, 1 if on else 0), self._h)
 
     def set_launch_overlap(self, mode):
         """Programmatic dependent launch of the step kernels: True/1 on,
