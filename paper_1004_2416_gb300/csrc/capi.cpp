@@ -93,6 +93,9 @@ struct iblbm_sim {
 
     std::vector<Capsule> caps;
     std::vector<double> X0;  // reference nodes [n][3]
+    // current positions of the nodes of a mesh whose rebuild failed (its device
+    // tables are gone; the next ensure_mesh starts from these)
+    std::vector<double> x_pending;
     std::vector<int> tri;    // faces [f][3], global node indices
     bool mesh_dirty = false;
     int dev_nodes = 0;  // nodes present in the device arrays
@@ -278,13 +281,22 @@ int ensure_mesh(iblbm_sim *s) {
         CK(cudaMemcpyAsync(xcur.data(), s->d_scratch, sizeof(double) * 3 * s->dev_nodes,
                            cudaMemcpyDeviceToHost, s->stream));
         CK(cudaStreamSynchronize(s->stream));
+        s->x_pending.assign(xcur.begin(), xcur.begin() + 3 * (size_t)s->dev_nodes);
+    } else {
+        std::copy(s->x_pending.begin(), s->x_pending.begin() + std::min(s->x_pending.size(), xcur.size()),
+                  xcur.begin());
     }
+    // from here on the old tables are gone: a failure below leaves no device
+    // pointer to them, and a later call rebuilds from x_pending
+    drop_graphs(s);
+    free_ring(s);
     for (void *p : s->mesh_allocs) dev_free(s, p);
     s->mesh_allocs.clear();
     for (void *p : s->plan_allocs) dev_free(s, p);
     s->plan_allocs.clear();
-    drop_graphs(s);
-    free_ring(s);
+    s->mesh = MeshDev{};
+    s->plan = TaylorPlan{};
+    s->dev_nodes = 0;
 
     const size_t rb = real_bytes(s);
     const size_t v4 = 4 * rb;
@@ -458,6 +470,7 @@ int ensure_mesh(iblbm_sim *s) {
     }
     CK(cudaStreamSynchronize(s->stream));
     s->dev_nodes = nn;
+    s->x_pending.clear();
     s->mesh_dirty = false;
     s->ab2_ready = false;
     return IBLBM_OK;
@@ -479,7 +492,13 @@ int ensure_ring(iblbm_sim *s) {
     if (s->rec_every <= 0 || s->d_ring || s->caps.empty()) return IBLBM_OK;
     s->d_ring = (double *)dev_alloc(s, sizeof(double) * 12 * s->caps.size() * (size_t)s->rec_ring);
     s->d_ring_count = (unsigned long long *)dev_alloc(s, sizeof(unsigned long long));
-    if (!s->d_ring || !s->d_ring_count) return fail(s, IBLBM_ERR_OOM, "record ring allocation failed");
+    if (!s->d_ring || !s->d_ring_count) {
+        dev_free(s, s->d_ring);
+        dev_free(s, s->d_ring_count);
+        s->d_ring = nullptr;
+        s->d_ring_count = nullptr;
+        return fail(s, IBLBM_ERR_OOM, "record ring allocation failed");
+    }
     CK(cudaMemsetAsync(s->d_ring_count, 0, sizeof(unsigned long long), s->stream));
     s->rec_steps.clear();
     s->plan.ring = s->d_ring;
@@ -856,7 +875,15 @@ int upload_batch_tables(iblbm_sim *s) {
     dev_free(s, s->d_items);
     s->d_runs = (RunDesc *)dev_alloc(s, sizeof(RunDesc) * s->runs.size());
     s->d_items = (int2 *)dev_alloc(s, sizeof(int2) * items.size());
-    if (!s->d_runs || !s->d_items) return fail(s, IBLBM_ERR_OOM, "run table allocation failed");
+    if (!s->d_runs || !s->d_items) {
+        // no tables at all rather than half of them: the steps refuse to run
+        dev_free(s, s->d_runs);
+        dev_free(s, s->d_items);
+        s->d_runs = nullptr;
+        s->d_items = nullptr;
+        s->n_items = 0;
+        return fail(s, IBLBM_ERR_OOM, "run table allocation failed");
+    }
     CK(cudaMemcpyAsync(s->d_runs, s->runs.data(), sizeof(RunDesc) * s->runs.size(),
                        cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(s->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice,
@@ -1383,11 +1410,20 @@ int run_steps(iblbm_sim *s, int64_t n_steps, bool run) {
     return IBLBM_OK;
 }
 
+// A batch whose run tables could not be (re)allocated has none: no step may run.
+int batch_tables_ok(iblbm_sim *s) {
+    if (s->batch && (!s->d_runs || !s->d_items))
+        return fail(s, IBLBM_ERR_OOM, "the batch's run tables are missing (an allocation failed)");
+    return IBLBM_OK;
+}
+
 int step_prologue(iblbm_sim *s, int64_t n_steps) {
     if (n_steps < 0) return fail(s, IBLBM_ERR_ARG, "negative step count");
     CK(cudaSetDevice(s->device));
     cudaGetLastError();  // an error left by some earlier, unrelated call is not ours
-    int rc = ensure_mesh(s);
+    int rc = batch_tables_ok(s);
+    if (rc) return rc;
+    rc = ensure_mesh(s);
     if (rc) return rc;
     rc = ensure_ring(s);
     if (rc) return rc;
@@ -1924,7 +1960,9 @@ int iblbm_profile_kernels(iblbm_sim *s, int n_steps, double ms_out[4]) {
     if (!s || !ms_out || n_steps < 1 || n_steps > 100000) return IBLBM_ERR_ARG;
     if (is_group(s)) return group_unsupported(s);
     CK(cudaSetDevice(s->device));
-    int rc = ensure_mesh(s);
+    int rc = batch_tables_ok(s);
+    if (rc) return rc;
+    rc = ensure_mesh(s);
     if (rc) return rc;
     rc = ensure_ring(s);
     if (rc) return rc;

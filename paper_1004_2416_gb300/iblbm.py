@@ -8,7 +8,7 @@ built (there is no fallback path).  Functions keep the C names
 Streams and device memory can come from PyTorch: pass
 ``stream=torch.cuda.current_stream()`` to :class:`Sim`, or
 ``allocator="torch"`` to let the library allocate through PyTorch's caching
-allocator.
+allocator (or an ``iblbm_allocator`` of one's own, kept alive by the caller).
 """
 from __future__ import annotations
 
@@ -240,6 +240,9 @@ class Sim:
             a, live = _torch_allocator()
             self._keep = (a, live)
             alloc_p = ctypes.pointer(a)
+        elif isinstance(allocator, iblbm_allocator):  # the caller keeps its callbacks alive
+            self._keep = allocator
+            alloc_p = ctypes.pointer(allocator)
         h = _vp()
         rc = iblbm_create(ctypes.byref(h), nx, ny, nz, tau, prec, delta_points,
                           _stream_handle(stream), alloc_p)
