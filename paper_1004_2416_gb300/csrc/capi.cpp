@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "iblbm.h"
 #include "internal.h"
 
@@ -33,6 +35,16 @@ constexpr int kGraphSteps = 32;  // steps per captured graph (even)
 constexpr int kMaxStepGraphs = 16;  // captured step sequences kept per object
 
 thread_local std::string g_create_error;
+
+// A named range on the host timeline of a profiler (NVTX; a few nanoseconds
+// when no tool is attached): the API calls below and, inside a step, each
+// kernel group as it is enqueued or captured.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 }  // namespace
 
@@ -571,13 +583,16 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr, 
     const bool ov = launch_overlap(s);
     if (ev) cudaEventRecord(ev[0], s->stream);
     gmark(0);
+    nvtxRangePushA("membrane force + spreading");
     launch_force_spread(s->prec, s->delta, s->L, s->mesh, s->force[n], s->flags[n], s->d_status,
                         s->batch ? s->d_runs : nullptr, s->d_node_run, s->stream, ov, det ? s->d_fix : nullptr);
     if (det && s->mesh.n_nodes > 0)
         launch_fix_to_force(s->prec, s->L, s->d_fix, s->force[n], s->flags[n], s->stream, ov);
     mark("membrane force + spreading");
+    nvtxRangePop();
     if (ev) cudaEventRecord(ev[1], s->stream);
     gmark(1);
+    nvtxRangePushA("collide-stream");
     CollideArgs a;
     a.src = s->pop[c];
     a.dst = s->pop[n];
@@ -598,8 +613,10 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr, 
         launch_collide_stream(s->prec, s->L, a, s->stream, ov);
     }
     mark("collide-stream");
+    nvtxRangePop();
     if (ev) cudaEventRecord(ev[2], s->stream);
     gmark(2);
+    nvtxRangePushA("interpolation + advection");
     const bool pre = cell_velocity_first(s);
     if (pre) {
         launch_flag_velocity(s->prec, s->L, s->pop[n], s->force[n], s->flags[n], s->uvel,
@@ -622,6 +639,7 @@ void enqueue_step(iblbm_sim *s, bool record = false, cudaEvent_t *ev = nullptr, 
                          s->integrator == 1 && s->ab2_ready ? 1 : 0, ov);
     s->ab2_ready = true;  // m.u now holds u_i(t+1)
     mark("interpolation + advection");
+    nvtxRangePop();
     if (ev) cudaEventRecord(ev[3], s->stream);
     gmark(3);
     if (record) {
@@ -1436,6 +1454,7 @@ int step_prologue(iblbm_sim *s, int64_t n_steps) {
 extern "C" {
 
 int iblbm_step(iblbm_sim *s, int64_t n_steps) {
+    Range range("iblbm_step");
     if (!s) return IBLBM_ERR_ARG;
     if (is_group(s)) {
         if (n_steps < 0) return fail(s, IBLBM_ERR_ARG, "negative step count");
@@ -1446,6 +1465,7 @@ int iblbm_step(iblbm_sim *s, int64_t n_steps) {
 }
 
 int iblbm_prepare_steps(iblbm_sim *s, int64_t n_steps) {
+    Range range("iblbm_prepare_steps");
     if (!s) return IBLBM_ERR_ARG;
     if (is_group(s)) return group_unsupported(s);
     int rc = step_prologue(s, n_steps);
@@ -1596,6 +1616,7 @@ cudaError_t copy_pos_in(iblbm_sim *s, const void *src, cudaStream_t st = nullptr
 extern "C" {
 
 int iblbm_adjoint_forward(iblbm_sim *s, int64_t n_steps, int checkpoint_every) {
+    Range range("iblbm_adjoint_forward");
     if (!s) return IBLBM_ERR_ARG;
     if (is_group(s)) return group_unsupported(s);
     if (s->batch) return fail(s, IBLBM_ERR_STATE, "the adjoint works on a single lattice");
@@ -1642,6 +1663,7 @@ int iblbm_adjoint_forward(iblbm_sim *s, int64_t n_steps, int checkpoint_every) {
 
 int iblbm_adjoint_backward(iblbm_sim *s, int capsule_id, double *D_out, double *dD_dks, double *dD_duw,
                            double *dD_dX0, double *dD_dx0) {
+    Range range("iblbm_adjoint_backward");
     if (!s || !D_out) return IBLBM_ERR_ARG;
     if (is_group(s)) return group_unsupported(s);
     iblbm_sim::Adjoint &A = s->adj;
@@ -1957,6 +1979,7 @@ int iblbm_get_taylor_records(iblbm_sim *s, int capsule_id, int max_records, doub
 }
 
 int iblbm_profile_kernels(iblbm_sim *s, int n_steps, double ms_out[4]) {
+    Range range("iblbm_profile_kernels");
     if (!s || !ms_out || n_steps < 1 || n_steps > 100000) return IBLBM_ERR_ARG;
     if (is_group(s)) return group_unsupported(s);
     CK(cudaSetDevice(s->device));
@@ -1990,6 +2013,7 @@ int iblbm_profile_kernels(iblbm_sim *s, int n_steps, double ms_out[4]) {
 }
 
 int iblbm_sync(iblbm_sim *s) {
+    Range range("iblbm_sync");
     if (!s) return IBLBM_ERR_ARG;
     if (is_group(s)) {
         int first = IBLBM_OK;
@@ -2410,6 +2434,7 @@ int iblbm_get_taylor(iblbm_sim *s, int id, double out[16]) {
 }
 
 int iblbm_read_async(iblbm_sim *s, double *host_nodes, double *host_sums) {
+    Range range("iblbm_read_async");
     if (!s) return IBLBM_ERR_ARG;
     if (is_group(s)) return group_unsupported(s);
     CK(cudaSetDevice(s->device));
@@ -2615,6 +2640,7 @@ int iblbm_checkpoint_size(iblbm_sim *s, size_t *bytes) {
 }
 
 int iblbm_checkpoint_save(iblbm_sim *s, void *buf, int on_device) {
+    Range range("iblbm_checkpoint_save");
     if (!s || !buf) return IBLBM_ERR_ARG;
     if (is_group(s)) return group_unsupported(s);
     int rc = sync_status(s);
@@ -2652,6 +2678,7 @@ int iblbm_checkpoint_save(iblbm_sim *s, void *buf, int on_device) {
 }
 
 int iblbm_checkpoint_restore(iblbm_sim *s, const void *buf, size_t buf_bytes, int on_device) {
+    Range range("iblbm_checkpoint_restore");
     if (!s || !buf) return IBLBM_ERR_ARG;
     if (is_group(s)) return group_unsupported(s);
     int rc = sync_status(s);
