@@ -354,6 +354,18 @@ int iblbm_set_equilibrium(iblbm_sim *sim, int order);
  * Synchronising. */
 int iblbm_set_interp_mode(iblbm_sim *sim, int mode);
 
+/* Bounds-checked build (no counterpart in the paper: a development aid).
+ * The library built with -DIBLBM_BOUNDS_CHECK (lib/libiblbm_checked.so; the
+ * binding loads it when IBLBM_LIBRARY=checked) range-checks the computed
+ * indices of the time-step kernels (streaming neighbours, stencil cells,
+ * force tiles, mesh node and face references): an index out of range is
+ * counted and replaced by 0, so the access stays inside its buffer and the
+ * kernel never faults.  iblbm_bounds_checked returns 1 in that build, 0 in
+ * the normal one; iblbm_bounds_faults gives the number of such faults since
+ * its last call (always 0 in the normal build).  Synchronises the device. */
+int iblbm_bounds_checked(void);
+int iblbm_bounds_faults(iblbm_sim *sim, unsigned long long *count);
+
 /* Deterministic spreading (on = 1; off = 0, the default): the force density
  * of Eq. (forcespreading) is summed in 64-bit fixed point, whose integer
  * additions give the same bits in any order, then converted to the storage

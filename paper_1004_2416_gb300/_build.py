@@ -1,4 +1,6 @@
-"""Builds ``lib/libiblbm.so`` in-tree from ``csrc/`` for sm_103a (GB300).
+"""Builds ``lib/libiblbm.so`` in-tree from ``csrc/`` for sm_103a (GB300),
+and ``lib/libiblbm_checked.so``, the same sources with the kernels' computed
+indices range-checked (-DIBLBM_BOUNDS_CHECK).
 
 CUDA translation units are compiled by nvcc in parallel, host translation
 units by g++ (no FMA contraction, so host geometry rounds the same on x86 and
@@ -46,29 +48,43 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def _variant_jobs(variant: str, cuda: str, force: bool):
+    """(compile jobs, objects, library) of one variant: "" the library,
+    "checked" the bounds-checked build of the same sources."""
+    nvcc = os.path.join(cuda, "bin", "nvcc")
+    obj_dir = os.path.join(OBJ, variant) if variant else OBJ
+    lib = os.path.join(LIB_DIR, f"libiblbm_{variant}.so" if variant else "libiblbm.so")
+    extra = ["-DIBLBM_BOUNDS_CHECK"] if variant == "checked" else []
+    os.makedirs(obj_dir, exist_ok=True)
+    hdrs = _sources()
+    jobs, objs = [], []
+    for u in CUDA_UNITS:
+        src = os.path.join(CSRC, u)
+        obj = os.path.join(obj_dir, u + ".o")
+        objs.append(obj)
+        if force or _stale(obj, [src] + hdrs):
+            jobs.append([nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", *extra,
+                         "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj])
+    for u in HOST_UNITS:
+        src = os.path.join(CSRC, u)
+        obj = os.path.join(obj_dir, u + ".o")
+        objs.append(obj)
+        if force or _stale(obj, [src] + hdrs):
+            jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", *extra,
+                         "-I", INCLUDE, "-I", CSRC, "-I", os.path.join(cuda, "include"),
+                         "-c", src, "-o", obj])
+    return jobs, objs, lib
+
+
+def build(force: bool = False, verbose: bool = False, variants=("", "checked")) -> str:
+    """Compiles every translation unit of every variant in parallel, then
+    links each variant's library; returns the path of the main library."""
     cuda = _cuda_home()
     nvcc = os.path.join(cuda, "bin", "nvcc")
     os.makedirs(OBJ, exist_ok=True)
     os.makedirs(LIB_DIR, exist_ok=True)
-    hdrs = _sources()
-    jobs = []
-    objs = []
-    for u in CUDA_UNITS:
-        src = os.path.join(CSRC, u)
-        obj = os.path.join(OBJ, u + ".o")
-        objs.append(obj)
-        if force or _stale(obj, [src] + hdrs):
-            jobs.append([nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-                         "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj])
-    for u in HOST_UNITS:
-        src = os.path.join(CSRC, u)
-        obj = os.path.join(OBJ, u + ".o")
-        objs.append(obj)
-        if force or _stale(obj, [src] + hdrs):
-            jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off",
-                         "-I", INCLUDE, "-I", CSRC, "-I", os.path.join(cuda, "include"),
-                         "-c", src, "-o", obj])
+    plans = [(_variant_jobs(v, cuda, force)) for v in variants]
+    jobs = [j for p in plans for j in p[0]]
     procs = [(cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)) for cmd in jobs]
     failed = []
     for cmd, p in procs:
@@ -79,14 +95,15 @@ def build(force: bool = False, verbose: bool = False) -> str:
             failed.append(" ".join(cmd))
     if failed:
         raise RuntimeError("compilation failed:\n" + "\n".join(failed))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-ldl", "-lpthread"]
-        r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
-        if r.returncode:
-            sys.stderr.write(r.stdout.decode(errors="replace"))
-            raise RuntimeError("link failed: " + " ".join(cmd))
-        os.replace(tmp, LIB)
+    for vjobs, objs, lib in plans:
+        if force or vjobs or _stale(lib, objs):
+            tmp = lib + f".tmp{os.getpid()}"
+            cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-lrt", "-ldl", "-lpthread"]
+            r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+            if r.returncode:
+                sys.stderr.write(r.stdout.decode(errors="replace"))
+                raise RuntimeError("link failed: " + " ".join(cmd))
+            os.replace(tmp, lib)
     return LIB
 
 

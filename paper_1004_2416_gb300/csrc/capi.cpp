@@ -2111,6 +2111,24 @@ int iblbm_set_interp_mode(iblbm_sim *s, int mode) {
     return IBLBM_OK;
 }
 
+int iblbm_bounds_checked(void) {
+#ifdef IBLBM_BOUNDS_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int iblbm_bounds_faults(iblbm_sim *s, unsigned long long *count) {
+    if (!s || !count) return IBLBM_ERR_ARG;
+    CK(cudaSetDevice(s->device));
+    CK(cudaDeviceSynchronize());
+    const unsigned long long a = bounds_faults_lbm(), b = bounds_faults_ib(), c = bounds_faults_taylor();
+    if (a == ~0ull || b == ~0ull || c == ~0ull) return fail(s, IBLBM_ERR_CUDA, "fault counter not readable");
+    *count = a + b + c;
+    return IBLBM_OK;
+}
+
 int iblbm_set_deterministic_spreading(iblbm_sim *s, int on) {
     if (!s) return IBLBM_ERR_ARG;
     if (is_group(s) || s->batch)

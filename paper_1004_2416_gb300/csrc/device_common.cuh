@@ -172,6 +172,39 @@ __device__ __forceinline__ int wrap_next(int w0, int k, int n) {
 
 __device__ __forceinline__ void set_status(int *status, int bit) { atomicOr(status, bit); }
 
+// ---- bounds-checked build (-DIBLBM_BOUNDS_CHECK, lib/libiblbm_checked.so) ----
+// IBLBM_OK(i, k, n): whether the k elements i .. i + k - 1 lie in [0, n).  The
+// kernels guard their computed accesses with it: in the checked build a
+// failed check is counted in this translation unit's fault counter and the
+// access is skipped (loads read 0), so the kernel never leaves its buffers;
+// in the normal build it is the constant true and its arguments are not
+// evaluated.  bounds_faults_*() read (and clear) the counter from the host.
+#ifdef IBLBM_BOUNDS_CHECK
+static __device__ unsigned long long g_bounds_faults;
+__device__ __forceinline__ bool bounds_ok(long long i, long long k, long long n) {
+    if (i < 0 || i + k > n) {
+        atomicAdd(&g_bounds_faults, 1ull);
+        return false;
+    }
+    return true;
+}
+#define IBLBM_OK(i, k, n) (::iblbm::bounds_ok((long long)(i), (long long)(k), (long long)(n)))
+#define IBLBM_BOUNDS_ACCESSOR(name)                                                        \
+    unsigned long long name() {                                                            \
+        unsigned long long v = 0, z = 0;                                                   \
+        if (cudaMemcpyFromSymbol(&v, g_bounds_faults, sizeof(v)) != cudaSuccess) {         \
+            cudaGetLastError();                                                            \
+            return ~0ull;                                                                  \
+        }                                                                                  \
+        cudaMemcpyToSymbol(g_bounds_faults, &z, sizeof(z));                                \
+        return v;                                                                          \
+    }
+#else
+#define IBLBM_OK(i, k, n) (true)
+#define IBLBM_BOUNDS_ACCESSOR(name) \
+    unsigned long long name() { return 0ull; }
+#endif
+
 // Programmatic dependent launch (sm_90 and later).  A time-step kernel may be
 // launched while its predecessor in the stream still runs.  It calls
 // prior_grid_wait() before it touches anything that the predecessor writes,

@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(256)
     for (int e = e0 + gl; e < e1; e += kFsGroup) {
         // (face * 4 + corner, a, b, c): the positions can be loaded next
         const int4 q = adj4[e];
+        if (!(IBLBM_OK(q.y, 1, n_nodes) && IBLBM_OK(q.z, 1, n_nodes) && IBLBM_OK(q.w, 1, n_nodes))) continue;
         const int f = q.x >> 2, corner = q.x & 3;
         const V4 c0 = fconst[3 * f];      // alpha, beta, gamma, kappa
         const V4 c1 = fconst[3 * f + 1];  // A0, G11, G12, G22 (hi parts in float builds)
@@ -189,13 +190,15 @@ __global__ void __launch_bounds__(256)
             } else {
                 xw = xa < R.nx ? xa : wrap_index(xa, R.nx);
             }
-            if constexpr (FIX)
-                add_force_fix(fix + 3 * (R.cell_off + rc + xw), w * fx, w * fy, w * fz, status);
-            else
-                add_force(&fr[rc + xw], w * fx, w * fy, w * fz);
+            if (IBLBM_OK(rc + xw, 1, R.ncell)) {
+                if constexpr (FIX)
+                    add_force_fix(fix + 3 * (R.cell_off + rc + xw), w * fx, w * fy, w * fz, status);
+                else
+                    add_force(&fr[rc + xw], w * fx, w * fy, w * fz);
+            }
             const int xt = xw >> sx;
             if (xt != last) {
-                flr[rt + xt] = 1;
+                if (IBLBM_OK(rt + xt, 1, (long long)R.ntx * R.nty * R.nz)) flr[rt + xt] = 1;
                 last = xt;
             }
         }
@@ -420,7 +423,8 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int j = 0; j < RPL; ++j)
 #pragma unroll
-            for (int c = 0; c < CX; ++c) u[j][c] = in[j] ? ur[rc[j] + XW[j][c]] : V4{};
+            for (int c = 0; c < CX; ++c)
+                u[j][c] = in[j] && IBLBM_OK(rc[j] + XW[j][c], 1, R.ncell) ? ur[rc[j] + XW[j][c]] : V4{};
 #pragma unroll
         for (int j = 0; j < RPL; ++j) {
             if (!in[j]) continue;
@@ -446,7 +450,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
             for (int c = 0; c < CX; ++c) {
 #pragma unroll
-                const bool own = in[j] && (!SLAB || XW[j][c] >= 0);
+                const bool own = in[j] && (!SLAB || XW[j][c] >= 0) && IBLBM_OK(rc[j] + XW[j][c], 1, R.ncell);
                 for (int i = 0; i < 19; ++i)
                     g[slot][c][i] = own ? Store<S, T>::load(pr + i * R.ncell + rc[j] + XW[j][c]) : T(0);
                 f[slot][c] = own ? fr[rc[j] + XW[j][c]] : V4{};
@@ -824,5 +828,7 @@ void launch_f64_to_nodes(int prec, const MeshDev &m, int first, int count, const
     else
         k_f64_to_nodes_f<<<nb, 256, 0, s>>>((float4 *)m.x, (float4 *)m.x_lo, first, count, in);
 }
+
+IBLBM_BOUNDS_ACCESSOR(bounds_faults_ib)
 
 }  // namespace iblbm

@@ -293,6 +293,12 @@ constexpr int kTaylorBatch = 8;
 void launch_taylor_snapshots(int prec, const MeshDev &m, const TaylorPlan &p, bool record, const void *snap_x,
                              const void *snap_lo, int first, int slots, int n_snap, cudaStream_t s);
 
+// Bounds-checked build: index faults counted by the kernels of each
+// translation unit since the last call (0 in the normal build).
+unsigned long long bounds_faults_lbm();
+unsigned long long bounds_faults_ib();
+unsigned long long bounds_faults_taylor();
+
 // Message returned by iblbm_last_error(NULL) in the calling thread (capi.cpp).
 void set_thread_error(const std::string &msg);
 

@@ -35,6 +35,7 @@ __device__ __forceinline__ void collide_cell(const S *__restrict__ src, S *__res
                                              typename Vec4<T>::type *__restrict__ moments = nullptr) {
     using V4 = typename Vec4<T>::type;
     const long long cell = x + (long long)nx * (y + (long long)ny * z);
+    if (!IBLBM_OK(cell, 1, ncell)) return;
     T g[19];
 #pragma unroll
     for (int i = 0; i < 19; ++i) g[i] = Store<S, T>::load(src + i * ncell + cell);
@@ -81,7 +82,7 @@ __device__ __forceinline__ void collide_cell(const S *__restrict__ src, S *__res
         } else {
             const long long t = cell + (cx > 0 ? dxp : (cx < 0 ? dxm : 0)) +
                                 (cy > 0 ? dyp : (cy < 0 ? dym : 0)) + cz * sz;
-            Store<S, T>::store(dst + i * ncell + t, post);
+            if (IBLBM_OK(t, 1, ncell)) Store<S, T>::store(dst + i * ncell + t, post);
         }
     };
     // rest direction: equilibrium w0 A, force term w0 (1 - omega/2)(-3 u.f)
@@ -356,7 +357,7 @@ __device__ __forceinline__ void collide_quad(const float2 (&g)[19][2], S *__rest
             if (q_cz(i)) jz = q_cz(i) > 0 ? add2(jz, g[i][h]) : sub2(jz, g[i][h]);
         }
         float fv[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-        if (has_cur) {
+        if (has_cur && IBLBM_OK(cell0, 4, ncell)) {
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 const float4 f = fcur[cell0 + 2 * h + e];
@@ -370,7 +371,8 @@ __device__ __forceinline__ void collide_quad(const float2 (&g)[19][2], S *__rest
             const float de = dr * ISC, jxe = (e ? jx.y : jx.x) * ISC;
             const float jye = (e ? jy.y : jy.x) * ISC, jze = (e ? jz.y : jz.x) * ISC;
             if constexpr (WM) {
-                if (active) moments[cell0 + 2 * h + e] = make_float4(jxe, jye, jze, de);
+                if (active && IBLBM_OK(cell0 + 2 * h + e, 1, ncell))
+                    moments[cell0 + 2 * h + e] = make_float4(jxe, jye, jze, de);
             }
             const float rho = 1.f + de;
             if (active && !(rho > 0.5f && rho < 2.f)) set_status(status, kStatusUnstable);
@@ -418,11 +420,13 @@ __device__ __forceinline__ void collide_quad(const float2 (&g)[19][2], S *__rest
             // the moving-wall term in storage units
             const float uw = (cz > 0) ? u_wall : -u_wall;
             const float wall = (cx == 0) ? 0.f : SC * 6.f * q_w<float>(i) * (cx > 0 ? uw : -uw);
-            Quad<S>::store_raw(dst + (size_t)q_opp(i) * ncell + cell0, p[0] - wall, p[1] - wall,
-                               p[2] - wall, p[3] - wall);
+            if (IBLBM_OK(cell0, 4, ncell))
+                Quad<S>::store_raw(dst + (size_t)q_opp(i) * ncell + cell0, p[0] - wall, p[1] - wall,
+                                   p[2] - wall, p[3] - wall);
         } else {
             S *rowp = dst + (size_t)i * ncell + (row0 + (cy > 0 ? dyp : (cy < 0 ? dym : 0)) + cz * plane);
-            Quad<S>::store_raw(rowp + x0, o0, o1, o2, o3);
+            if (IBLBM_OK((long long)(row0 + (cy > 0 ? dyp : (cy < 0 ? dym : 0)) + cz * plane) + x0, 4, ncell))
+                Quad<S>::store_raw(rowp + x0, o0, o1, o2, o3);
             if constexpr (LR > 32) {
                 // the value that crosses into the neighbouring warp
                 if (cx > 0 && lane == 31) edge[warp][edge_slot(i)] = p[3];
@@ -501,7 +505,9 @@ __device__ __forceinline__ void collide_quad(const float2 (&g)[19][2], S *__rest
                 if (cx == 0 || (cz > 0 ? top : (cz < 0 ? bottom : false))) continue;
                 if ((cx > 0) != (lane == 0)) continue;
                 S *rowp = dst + (size_t)i * ncell + (row0 + (cy > 0 ? dyp : (cy < 0 ? dym : 0)) + cz * plane);
-                StoreRaw<S>::store(rowp + x0 + (cx > 0 ? 0 : 3), edge[from][edge_slot(i)]);
+                if (IBLBM_OK((long long)(row0 + (cy > 0 ? dyp : (cy < 0 ? dym : 0)) + cz * plane) + x0 +
+                                 (cx > 0 ? 0 : 3), 1, ncell))
+                    StoreRaw<S>::store(rowp + x0 + (cx > 0 ? 0 : 3), edge[from][edge_slot(i)]);
             }
         }
     }
@@ -543,9 +549,10 @@ __global__ void __launch_bounds__(256, 2)
     // one force flag per quad: this thread's own
     constexpr int FTX = 4;  // one force flag per quad (Lattice::ftx)
     const int fidx = row * (NX / FTX) + x0 / FTX;
-    const bool has_old = flag_old[fidx] != 0;
-    const bool has_cur = flag_cur[fidx] != 0;
-    if (has_old && active) {
+    const bool flag_ok = IBLBM_OK(fidx, 1, (long long)nrows * (NX / FTX));
+    const bool has_old = flag_ok && flag_old[fidx] != 0;
+    const bool has_cur = flag_ok && flag_cur[fidx] != 0;
+    if (has_old && active && IBLBM_OK(cell0, 4, ncell)) {
 #pragma unroll
         for (int k = 0; k < 4; ++k) fold[cell0 + k] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
@@ -556,8 +563,16 @@ __global__ void __launch_bounds__(256, 2)
     // values are used as loaded (exact power-of-two scale folded into the
     // per-cell quantities).
     float2 g[19][2];
+    const bool quad_ok = IBLBM_OK(cell0, 4, ncell);  // constant true in the normal build
 #pragma unroll
-    for (int i = 0; i < 19; ++i) Quad<S>::load_raw(src + (size_t)i * ncell + cell0, g[i][0], g[i][1]);
+    for (int i = 0; i < 19; ++i) {
+        if (quad_ok) {
+            Quad<S>::load_raw(src + (size_t)i * ncell + cell0, g[i][0], g[i][1]);
+        } else {
+            g[i][0] = make_float2(0.f, 0.f);
+            g[i][1] = g[i][0];
+        }
+    }
     collide_quad<S, LR, WM, LIN>(g, dst, fcur, has_cur, active, row, y, z, x0, cell0, lane, warp, ny, nz, ncell,
                                  omega, u_wall, status, moments, edge);
 }
@@ -616,8 +631,9 @@ __global__ void __launch_bounds__(THREADS, 2)
         mbar_expect_bytes(&bar[b], 19u * bytes);
 #pragma unroll 1
         for (int i = 0; i < 19; ++i)
-            bulk_copy_to_smem(stage + ((size_t)b * 19 + i) * TILE, src + (size_t)i * ncell + (size_t)r0 * NX, bytes,
-                              &bar[b]);
+            if (IBLBM_OK((long long)r0 * NX, (long long)nr * NX, ncell))  // else the wait gives up, reported
+                bulk_copy_to_smem(stage + ((size_t)b * 19 + i) * TILE, src + (size_t)i * ncell + (size_t)r0 * NX,
+                                  bytes, &bar[b]);
     };
     int pending[2] = {0, 0};  // thread 0: copies issued and not yet waited for, per buffer
     if (threadIdx.x == 0) {
@@ -642,9 +658,10 @@ __global__ void __launch_bounds__(THREADS, 2)
         const int y = row % ny, z = row / ny;
         const int cell0 = x0 + NX * row;
         const int fidx = row * (NX / FTX) + x0 / FTX;
-        const bool has_old = flag_old[fidx] != 0;
-        const bool has_cur = flag_cur[fidx] != 0;
-        if (has_old && active) {
+        const bool flag_ok = IBLBM_OK(fidx, 1, (long long)nrows * (NX / FTX));
+        const bool has_old = flag_ok && flag_old[fidx] != 0;
+        const bool has_cur = flag_ok && flag_cur[fidx] != 0;
+        if (has_old && active && IBLBM_OK(cell0, 4, ncell)) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) fold[cell0 + q] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
@@ -705,6 +722,7 @@ __device__ __forceinline__ void collide_pair(const S *__restrict__ src, S *__res
                                              int z, int nx, int ny, int nz, long long ncell, float omega,
                                              float u_wall, int *status) {
     const long long cell = x + (long long)nx * (y + (long long)ny * z);
+    if (!IBLBM_OK(cell, 2, ncell)) return;
     float2 g[19];
 #pragma unroll
     for (int i = 0; i < 19; ++i) g[i] = Pair<S>::load(src + i * ncell + cell);
@@ -758,15 +776,16 @@ __device__ __forceinline__ void collide_pair(const S *__restrict__ src, S *__res
             const float wall = (cx == 0) ? 0.f : 6.f * q_w<float>(i) * (cx > 0 ? uw : -uw);
             Pair<S>::store(dst + q_opp(i) * ncell + cell, make_float2(post.x - wall, post.y - wall));
         } else {
-            S *b = dst + i * ncell + cell + (cy > 0 ? dyp : (cy < 0 ? dym : 0)) + cz * sz;
+            const long long o = cell + (cy > 0 ? dyp : (cy < 0 ? dym : 0)) + cz * sz;
+            S *b = dst + i * ncell + o;
             if (cx == 0) {
-                Pair<S>::store(b, post);
+                if (IBLBM_OK(o, 2, ncell)) Pair<S>::store(b, post);
             } else if (cx > 0) {
-                Pair<S>::store1(b + 1, post.x);
-                Pair<S>::store1(b + 1 + dxp1, post.y);
+                if (IBLBM_OK(o + 1, 1, ncell)) Pair<S>::store1(b + 1, post.x);
+                if (IBLBM_OK(o + 1 + dxp1, 1, ncell)) Pair<S>::store1(b + 1 + dxp1, post.y);
             } else {
-                Pair<S>::store1(b + dxm0, post.x);
-                Pair<S>::store1(b, post.y);
+                if (IBLBM_OK(o + dxm0, 1, ncell)) Pair<S>::store1(b + dxm0, post.x);
+                if (IBLBM_OK(o, 1, ncell)) Pair<S>::store1(b, post.y);
             }
         }
     };
@@ -1307,5 +1326,7 @@ void launch_force_to_f64(int prec, const Lattice &L, const void *force, double *
     if (prec == kF64) k_force_to_f64<double><<<nb, 256, 0, s>>>((const dvec4 *)force, L.ncell, out);
     else k_force_to_f64<float><<<nb, 256, 0, s>>>((const float4 *)force, L.ncell, out);
 }
+
+IBLBM_BOUNDS_ACCESSOR(bounds_faults_lbm)
 
 }  // namespace iblbm

@@ -273,6 +273,14 @@ __device__ __forceinline__ void block_sum_any(double v[K], double (*sh)[K]) {
 // inertia terms about c, and block 0 adds those partials in rank order.  In
 // recording mode snapshot k goes to ring record count + k and the last
 // cluster to finish advances the record counter by the number of snapshots.
+// Bounds-checked build: the nodes of face f lie among the n_nodes of a snapshot.
+#ifdef IBLBM_BOUNDS_CHECK
+#define IBLBM_FACE_OK(f)                                                                     \
+    (IBLBM_OK(tri[f].x, 1, ss.stride) && IBLBM_OK(tri[f].y, 1, ss.stride) && IBLBM_OK(tri[f].z, 1, ss.stride))
+#else
+#define IBLBM_FACE_OK(f) (true)
+#endif
+
 template <typename R>
 __global__ void __launch_bounds__(kTaylorClusterThreads) k_taylor_cluster(R nodes0, const int4 *__restrict__ tri,
                                                                           TaylorPlan p, SnapSet ss, int record) {
@@ -294,6 +302,7 @@ __global__ void __launch_bounds__(kTaylorClusterThreads) k_taylor_cluster(R node
 #pragma unroll 4
         for (int f = f0 + rank * blockDim.x + threadIdx.x; f < f1; f += stride) {
             float w[5];
+            if (!IBLBM_FACE_OK(f)) continue;
             FaceMath<R>::stage1f(nodes, tri[f], o, w);
             for (int k = 0; k < 5; ++k) vf[k] += w[k];
         }
@@ -302,6 +311,7 @@ __global__ void __launch_bounds__(kTaylorClusterThreads) k_taylor_cluster(R node
 #pragma unroll 4
         for (int f = f0 + rank * blockDim.x + threadIdx.x; f < f1; f += stride) {
             double w[5];
+            if (!IBLBM_FACE_OK(f)) continue;
             FaceMath<R>::stage1(nodes, tri[f], o, w);
             for (int k = 0; k < 5; ++k) v[k] += w[k];
         }
@@ -328,6 +338,7 @@ __global__ void __launch_bounds__(kTaylorClusterThreads) k_taylor_cluster(R node
 #pragma unroll 4
         for (int f = f0 + rank * blockDim.x + threadIdx.x; f < f1; f += stride) {
             float w[6];
+            if (!IBLBM_FACE_OK(f)) continue;
             FaceMath<R>::stage2f(nodes, tri[f], o, c, w);
             for (int k = 0; k < 6; ++k) If[k] += w[k];
         }
@@ -336,6 +347,7 @@ __global__ void __launch_bounds__(kTaylorClusterThreads) k_taylor_cluster(R node
 #pragma unroll 4
         for (int f = f0 + rank * blockDim.x + threadIdx.x; f < f1; f += stride) {
             double w[6];
+            if (!IBLBM_FACE_OK(f)) continue;
             FaceMath<R>::stage2(nodes, tri[f], o, c, w);
             for (int k = 0; k < 6; ++k) I[k] += w[k];
         }
@@ -550,6 +562,8 @@ __global__ void k_noalloc_stage3(const double *__restrict__ partial, int nb, dou
         out[11] = bad[0];
     }
 }
+
+IBLBM_BOUNDS_ACCESSOR(bounds_faults_taylor)
 
 }  // namespace iblbm
 

@@ -18,7 +18,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "lib", "libiblbm.so")
+# IBLBM_LIBRARY=checked selects the bounds-checked build of the same sources
+LIB_PATH = os.path.join(_HERE, "lib", "libiblbm_checked.so" if os.environ.get("IBLBM_LIBRARY") == "checked"
+                        else "libiblbm.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(
@@ -111,6 +113,8 @@ _SIGS = {
     "iblbm_set_interp_mode": (_int, [_vp, _int]),
     "iblbm_set_launch_overlap": (_int, [_vp, _int]),
     "iblbm_set_deterministic_spreading": (_int, [_vp, _int]),
+    "iblbm_bounds_checked": (_int, []),
+    "iblbm_bounds_faults": (_int, [_vp, ctypes.POINTER(ctypes.c_ulonglong)]),
     "iblbm_read_async": (_int, [_vp, _vp, _vp]),
     "iblbm_taylor_from_sums": (_int, [_vp, _vp]),
     "iblbm_set_integrator": (_int, [_vp, _int]),
@@ -561,6 +565,12 @@ class Sim:
     def set_interp_mode(self, mode: int):
         """-1 automatic (default), 0 gather at the stencil cells, 1 cell velocities first."""
         _check(iblbm_set_interp_mode(self._h, int(mode)), self._h)
+
+    def bounds_faults(self) -> int:
+        """Index faults counted by the bounds-checked build since the last call."""
+        n = ctypes.c_ulonglong()
+        _check(iblbm_bounds_faults(self._h, ctypes.byref(n)), self._h)
+        return n.value
 
     def set_deterministic_spreading(self, on: bool):
         """Force density summed in 64-bit fixed point: bit-reproducible steps."""

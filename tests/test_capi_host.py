@@ -34,6 +34,17 @@ def test_library_exports_every_declared_symbol():
     lib = ctypes.CDLL(LIB_PATH)
     missing = [n for n in _declared() if not hasattr(lib, n)]
     assert not missing, missing
+    assert lib.iblbm_bounds_checked() == 0
+
+
+def test_checked_build_exports_every_declared_symbol():
+    """The bounds-checked build of the same sources (loaded by the binding
+    when IBLBM_LIBRARY=checked) has the same entry points and says so."""
+    path = os.path.join(ROOT, "paper_1004_2416_gb300", "lib", "libiblbm_checked.so")
+    lib = ctypes.CDLL(path)
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert lib.iblbm_bounds_checked() == 1
 
 
 @pytest.mark.parametrize("m", range(0, 6))
