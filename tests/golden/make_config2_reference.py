@@ -1,7 +1,9 @@
-"""Writes tests/golden/config2_oracle_2000.npz: the FP64 oracle's state after
-2 000 full-size steps of the 128^3 single-capsule shear flow (r = 16, 5 120
-faces, 4-point delta, reduced shear rate G = 0.0125, shear rate 1e-3, tau = 1,
-Couette start), the sub-step list of Sec. II.C run on the host.
+"""Writes tests/golden/config2_oracle_2000.npz (and, with --steps 20000
+--every 500 --out tests/golden/config2_oracle_20000.npz, the workload's full
+20 000 steps): the FP64 oracle's state after that many full-size steps of the
+128^3 single-capsule shear flow (r = 16, 5 120 faces, 4-point delta, reduced
+shear rate G = 0.0125, shear rate 1e-3, tau = 1, Couette start), the sub-step
+list of Sec. II.C run on the host.
 
 Calls only the oracle (and the seeded workload description, which holds none
 of the method's arithmetic).  Stored:
@@ -9,12 +11,13 @@ of the method's arithmetic).  Stored:
   u_slice    [3, 64, 64] lattice velocity u(X, t) of Eq. (lbmmomenta1) on the
                          plane y = 64, every second cell in z and x
                          ([3][z/2][x/2])
-  D_steps    [20]        steps after which D was taken (every 100)
-  D, theta   [20]        Taylor deformation and inclination of Sec. III
+  D_steps    [n]         steps after which D was taken (every 100, or --every)
+  D, theta   [n]         Taylor deformation and inclination of Sec. III
   steps, G, delta        the run's parameters
 
 The oracle's whole-lattice loops run on all host cores (results do not depend
-on the thread count).  About 12 minutes on 8 cores.
+on the thread count).  About 12 minutes on 8 cores for 2 000 steps, 80 for
+20 000.
     python tests/golden/make_config2_reference.py [--steps 2000] [--threads N]
 """
 import argparse
