@@ -377,9 +377,10 @@ int iblbm_bounds_faults(iblbm_sim *sim, unsigned long long *count);
  * more is not added and the next synchronising call returns
  * IBLBM_ERR_UNSTABLE.  Costs three 64-bit integer atomics per stencil cell
  * instead of one vector atomic, a conversion pass over the force tiles and
- * 24 bytes per cell of device memory.  A single lattice only
- * (IBLBM_ERR_STATE for a batch or a slab group); IBLBM_ERR_ARG for another
- * value.  Synchronising. */
+ * 24 bytes per cell of device memory.  A single whole lattice only
+ * (IBLBM_ERR_STATE for a batch, a slab group or a lattice configured as a
+ * slab, and iblbm_slab_configure refuses a lattice that has it on);
+ * IBLBM_ERR_ARG for another value.  Synchronising. */
 int iblbm_set_deterministic_spreading(iblbm_sim *sim, int on);
 
 /* Whether the kernels of a time step are launched with programmatic

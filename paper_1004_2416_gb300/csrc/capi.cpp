@@ -2131,8 +2131,8 @@ int iblbm_bounds_faults(iblbm_sim *s, unsigned long long *count) {
 
 int iblbm_set_deterministic_spreading(iblbm_sim *s, int on) {
     if (!s) return IBLBM_ERR_ARG;
-    if (is_group(s) || s->batch)
-        return fail(s, IBLBM_ERR_STATE, "deterministic spreading is for a single lattice");
+    if (is_group(s) || s->batch || s->L.gnx != s->L.nx || s->L.x0 != 0)
+        return fail(s, IBLBM_ERR_STATE, "deterministic spreading is for a single whole lattice");
     if (on != 0 && on != 1) return fail(s, IBLBM_ERR_ARG, "on must be 0 or 1");
     CK(cudaSetDevice(s->device));
     join_side(s);
@@ -3043,6 +3043,7 @@ extern "C" {
 int iblbm_slab_configure(iblbm_sim *s, int x0, int nx_global) {
     if (!s) return IBLBM_ERR_ARG;
     if (is_group(s) || s->batch) return fail(s, IBLBM_ERR_STATE, "a slab is a single lattice object");
+    if (s->d_fix) return fail(s, IBLBM_ERR_STATE, "slab phases spread with float atomics only");
     if (x0 < 0 || nx_global < s->L.nx || x0 + s->L.nx > nx_global || s->L.nx < 4)
         return fail(s, IBLBM_ERR_ARG, "need 0 <= x0, x0 + nx <= nx_global and nx >= 4");
     CK(cudaSetDevice(s->device));

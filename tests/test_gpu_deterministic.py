@@ -117,7 +117,7 @@ def test_out_of_range_contribution_is_reported():
     o.close()
 
 
-def test_batch_refused():
+def test_batch_and_slabs_refused():
     from paper_1004_2416_gb300 import Sim
 
     b = Sim.batch([(24, 24, 24, 1.0, 0.01)], precision="fp32", delta_points=3)
@@ -125,3 +125,15 @@ def test_batch_refused():
         b.set_deterministic_spreading(True)
     assert e.value.code == B.IBLBM_ERR_STATE
     b.close()
+    s = Sim(16, 8, 8, precision="fp32")
+    s.slab_configure(16, 48)
+    with pytest.raises(B.IblbmError) as e:
+        s.set_deterministic_spreading(True)
+    assert e.value.code == B.IBLBM_ERR_STATE
+    s.close()
+    s = Sim(16, 8, 8, precision="fp32")
+    s.set_deterministic_spreading(True)
+    with pytest.raises(B.IblbmError) as e:
+        s.slab_configure(16, 48)
+    assert e.value.code == B.IBLBM_ERR_STATE
+    s.close()
