@@ -276,8 +276,9 @@ struct QuadSmem<__half> {
 // Vectorised collide-and-stream for nx = 4 * LR, LR a power of two <= 256:
 // each thread owns 4 consecutive cells of one x-row and LR lanes cover the
 // row.  With LR <= 32 a warp covers 32 / LR rows; with LR > 32 a row spans
-// LR / 32 warps.  A block has 8 warps.  All 19 loads and the stores are 16-byte
-// (float) or 8-byte (half) vectors.  Streaming along x shifts a thread's 4
+// LR / 32 warps.  A block has 8 warps, or holds one row (X4Shape).  All 19
+// loads and the stores are 16-byte (float) or 8-byte (half) vectors.
+// Streaming along x shifts a thread's 4
 // post-collision values by one cell; the value that crosses into the
 // neighbouring thread's quad comes by a warp shuffle (within the row's lane
 // segment when LR <= 32, which also closes the periodic wrap in x).  When a
@@ -321,10 +322,54 @@ __device__ __forceinline__ float from_right(float v, int lane) {
 // directions.
 __host__ __device__ constexpr int edge_slot(int i) { return i <= 2 ? i - 1 : i - 5; }
 
-template <int LR>
+// rows of a block of NWB warps
+template <int LR, int NWB = 8>
 __host__ __device__ constexpr int rows_per_block() {
-    return LR <= 32 ? 8 * (32 / LR) : 8 / (LR / 32);
+    return LR <= 32 ? NWB * (32 / LR) : NWB / (LR / 32);
 }
+
+// Launch shape of k_collide_stream_x4: blocks of eight warps, two per SM
+// (128 registers).  Binary16 rows that span several warps take one row per
+// block, so that the barrier before the warp-edge rewrite holds only the
+// warps of that row, and, for two or four warps per row, about 20 warps per
+// SM in 96 registers, the populations kept as loaded and converted where
+// used (QuadRawHalf).  Measured on the 256 x 128 x 128 FP16 lattice
+// (two warps per row): 70.6 us per collide with eight-warp blocks, 67.6 with
+// four-warp blocks, 66.6 with one-row blocks at 20 warps per SM.
+template <typename S, int LR>
+struct X4Shape {
+    static constexpr bool kRowBlocks = sizeof(S) == 2 && LR > 32;
+    static constexpr int kWarps = kRowBlocks ? LR / 32 : 8;
+    static constexpr bool kRaw = kRowBlocks && LR <= 128;
+    static constexpr int kMinBlocks = kRaw ? 20 / kWarps : 2;
+};
+
+// The 19 populations of a thread's quad as collide_quad reads them: pair h
+// (cells (0,1) or (2,3)) of direction i, in storage units, once for the
+// moments and once for the collision of its direction.  QuadRegs holds them
+// as floats; QuadRawHalf holds the binary16 words as loaded (38 registers
+// instead of 76) and converts at each use, through an opaque conversion that
+// the compiler can neither merge with the first nor hoist, so that the
+// quad's 76 floats are never live at once.  Both give the same values.
+struct QuadRegs {
+    const float2 (&g)[19][2];
+    __device__ __forceinline__ float2 moment(int i, int h) const { return g[i][h]; }
+    __device__ __forceinline__ float2 use(int i, int h) const { return g[i][h]; }
+};
+struct QuadRawHalf {
+    const uint2 (&w)[19];
+    __device__ __forceinline__ float2 moment(int i, int h) const {
+        const unsigned v = h ? w[i].y : w[i].x;
+        return __half22float2(*reinterpret_cast<const __half2 *>(&v));
+    }
+    __device__ __forceinline__ float2 use(int i, int h) const {
+        float a, b;
+        asm volatile("{\n\t.reg .b16 l, h;\n\tmov.b32 {l, h}, %2;\n\tcvt.f32.f16 %0, l;\n\tcvt.f32.f16 %1, h;\n\t}"
+                     : "=f"(a), "=f"(b)
+                     : "r"(h ? w[i].y : w[i].x));
+        return make_float2(a, b);
+    }
+};
 
 // Collision and streaming of one thread's quad (4 consecutive cells of a row)
 // from its 19 populations g (pairs (0,1) and (2,3), storage units), shared by
@@ -333,8 +378,8 @@ __host__ __device__ constexpr int rows_per_block() {
 // inactive ones too: they join the shuffles and, for rows spanning several
 // warps, the block barrier of the warp-edge rewrite; `edge` holds one row of
 // ten values per warp).
-template <typename S, int LR, bool WM, bool LIN>
-__device__ __forceinline__ void collide_quad(const float2 (&g)[19][2], S *__restrict__ dst,
+template <typename S, int LR, bool WM, bool LIN, typename Src>
+__device__ __forceinline__ void collide_quad(const Src &g, S *__restrict__ dst,
                                              const float4 *__restrict__ fcur, bool has_cur, bool active, int row,
                                              int y, int z, int x0, int cell0, int lane, int warp, int ny, int nz,
                                              int ncell, float omega, float u_wall, int *status,
@@ -351,10 +396,11 @@ __device__ __forceinline__ void collide_quad(const float2 (&g)[19][2], S *__rest
         float2 d = make_float2(0.f, 0.f), jx = d, jy = d, jz = d;
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
-            d = add2(d, g[i][h]);
-            if (q_cx(i)) jx = q_cx(i) > 0 ? add2(jx, g[i][h]) : sub2(jx, g[i][h]);
-            if (q_cy(i)) jy = q_cy(i) > 0 ? add2(jy, g[i][h]) : sub2(jy, g[i][h]);
-            if (q_cz(i)) jz = q_cz(i) > 0 ? add2(jz, g[i][h]) : sub2(jz, g[i][h]);
+            const float2 gi = g.moment(i, h);
+            d = add2(d, gi);
+            if (q_cx(i)) jx = q_cx(i) > 0 ? add2(jx, gi) : sub2(jx, gi);
+            if (q_cy(i)) jy = q_cy(i) > 0 ? add2(jy, gi) : sub2(jy, gi);
+            if (q_cz(i)) jz = q_cz(i) > 0 ? add2(jz, gi) : sub2(jz, gi);
         }
         float fv[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
         if (has_cur && IBLBM_OK(cell0, 4, ncell)) {
@@ -442,7 +488,7 @@ __device__ __forceinline__ void collide_quad(const float2 (&g)[19][2], S *__rest
         float p[4];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            float2 post = fma2(omw, A[h], mul2(keep2, g[0][h]));
+            float2 post = fma2(omw, A[h], mul2(keep2, g.use(0, h)));
             if (has_cur) post = fma2(gw, Ufm[h], post);
             p[2 * h] = post.x;
             p[2 * h + 1] = post.y;
@@ -473,8 +519,8 @@ __device__ __forceinline__ void collide_quad(const float2 (&g)[19][2], S *__rest
             const float2 e = LIN ? A[h] : fma2(mul2(r, make_float2(4.5f, 4.5f)), cu, A[h]);
             const float2 gp = fma2(r, make_float2(3.f, 3.f), e);
             const float2 gm = fma2(r, make_float2(-3.f, -3.f), e);
-            float2 postp = fma2(omw, gp, mul2(keep2, g[ip][h]));
-            float2 postm = fma2(omw, gm, mul2(keep2, g[im][h]));
+            float2 postp = fma2(omw, gp, mul2(keep2, g.use(ip, h)));
+            float2 postm = fma2(omw, gm, mul2(keep2, g.use(im, h)));
             if (has_cur) {
                 float2 cf = cx ? Fx[h] : (cy ? Fy[h] : Fz[h]);
                 if (cx && cy) cf = cy > 0 ? add2(cf, Fy[h]) : sub2(cf, Fy[h]);
@@ -516,7 +562,7 @@ __device__ __forceinline__ void collide_quad(const float2 (&g)[19][2], S *__rest
 // WM: also write the moments of f(t), float4 (j, rho - 1) per cell.
 // LIN: the linearised equilibrium (as collide_cell).
 template <typename S, int LR, bool WM, bool LIN = false>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(32 * X4Shape<S, LR>::kWarps, X4Shape<S, LR>::kMinBlocks)
     k_collide_stream_x4(const S *__restrict__ src, S *__restrict__ dst,
                         const float4 *__restrict__ fcur, const uint8_t *__restrict__ flag_cur,
                         float4 *__restrict__ fold, uint8_t *__restrict__ flag_old, int ny, int nz,
@@ -526,11 +572,11 @@ __global__ void __launch_bounds__(256, 2)
     const int nrows = ny * nz;
     int row_raw, lx;
     if constexpr (LR <= 32) {
-        row_raw = blockIdx.x * rows_per_block<LR>() + warp * (32 / LR) + lane / LR;
+        row_raw = blockIdx.x * rows_per_block<LR, X4Shape<S, LR>::kWarps>() + warp * (32 / LR) + lane / LR;
         lx = lane & (LR - 1);
     } else {
         constexpr int WPR = LR / 32;
-        row_raw = blockIdx.x * rows_per_block<LR>() + warp / WPR;
+        row_raw = blockIdx.x * rows_per_block<LR, X4Shape<S, LR>::kWarps>() + warp / WPR;
         lx = (warp % WPR) * 32 + lane;
     }
     const bool active = row_raw < nrows;
@@ -562,19 +608,29 @@ __global__ void __launch_bounds__(256, 2)
     // instructions of sm_100+, in storage units: G = kScale g, so binary16
     // values are used as loaded (exact power-of-two scale folded into the
     // per-cell quantities).
-    float2 g[19][2];
     const bool quad_ok = IBLBM_OK(cell0, 4, ncell);  // constant true in the normal build
+    if constexpr (X4Shape<S, LR>::kRaw) {
+        uint2 raw[19];
 #pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        if (quad_ok) {
-            Quad<S>::load_raw(src + (size_t)i * ncell + cell0, g[i][0], g[i][1]);
-        } else {
-            g[i][0] = make_float2(0.f, 0.f);
-            g[i][1] = g[i][0];
+        for (int i = 0; i < 19; ++i)
+            raw[i] = quad_ok ? __ldg(reinterpret_cast<const uint2 *>(src + (size_t)i * ncell + cell0))
+                             : make_uint2(0u, 0u);
+        collide_quad<S, LR, WM, LIN>(QuadRawHalf{raw}, dst, fcur, has_cur, active, row, y, z, x0, cell0, lane,
+                                     warp, ny, nz, ncell, omega, u_wall, status, moments, edge);
+    } else {
+        float2 g[19][2];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) {
+            if (quad_ok) {
+                Quad<S>::load_raw(src + (size_t)i * ncell + cell0, g[i][0], g[i][1]);
+            } else {
+                g[i][0] = make_float2(0.f, 0.f);
+                g[i][1] = g[i][0];
+            }
         }
+        collide_quad<S, LR, WM, LIN>(QuadRegs{g}, dst, fcur, has_cur, active, row, y, z, x0, cell0, lane, warp,
+                                     ny, nz, ncell, omega, u_wall, status, moments, edge);
     }
-    collide_quad<S, LR, WM, LIN>(g, dst, fcur, has_cur, active, row, y, z, x0, cell0, lane, warp, ny, nz, ncell,
-                                 omega, u_wall, status, moments, edge);
 }
 
 // ---- the same on tiles staged in shared memory by the bulk-copy engine ---------------
@@ -671,8 +727,8 @@ __global__ void __launch_bounds__(THREADS, 2)
         float2 g[19][2];
 #pragma unroll
         for (int i = 0; i < 19; ++i) QuadSmem<S>::load(tile + (size_t)i * TILE, g[i][0], g[i][1]);
-        collide_quad<S, LR, false, LIN>(g, dst, fcur, has_cur, active, row, y, z, x0, cell0, lane, warp, ny, nz,
-                                        ncell, omega, u_wall, status, nullptr, edge);
+        collide_quad<S, LR, false, LIN>(QuadRegs{g}, dst, fcur, has_cur, active, row, y, z, x0, cell0, lane,
+                                        warp, ny, nz, ncell, omega, u_wall, status, nullptr, edge);
         __syncthreads();  // buffer b is read: it may be refilled
         if (threadIdx.x == 0 && t + 2 * (int)gridDim.x < n_tiles) {
             fence_async_smem();
@@ -1032,7 +1088,9 @@ static void collide_staged(const Lattice &L, const CollideArgs &a, cudaStream_t 
 
 template <typename S, int LR>
 static void collide_x4(const Lattice &L, const CollideArgs &a, cudaStream_t s, bool ov) {
-    constexpr int rpb = rows_per_block<LR>();
+    using Sh = X4Shape<S, LR>;
+    constexpr int rpb = rows_per_block<LR, Sh::kWarps>();
+    constexpr unsigned threads = 32 * Sh::kWarps;
     const int nrows = L.ny * L.nz;
     if constexpr ((4 * LR * sizeof(S)) % 16 == 0 && LR <= staged_threads<S>()) {
         if (a.staged && !a.moments) {
@@ -1045,17 +1103,17 @@ static void collide_x4(const Lattice &L, const CollideArgs &a, cudaStream_t s, b
     // the moments are kept only by the adjoint's recomputation, which runs
     // with the full equilibrium
     if (a.moments)
-        launch_maybe_overlapped(k_collide_stream_x4<S, LR, true>, dim3(nb), dim3(256), s, ov,
+        launch_maybe_overlapped(k_collide_stream_x4<S, LR, true>, dim3(nb), dim3(threads), s, ov,
             (const S *)a.src, (S *)a.dst, (const float4 *)a.fcur, a.flag_cur, (float4 *)a.fold,
             a.flag_old, L.ny, L.nz, (int)L.ncell, (float)(1.0 / a.tau), (float)a.u_wall, a.status,
             (float4 *)a.moments);
     else if (a.eq_order == 1)
-        launch_maybe_overlapped(k_collide_stream_x4<S, LR, false, true>, dim3(nb), dim3(256), s, ov,
+        launch_maybe_overlapped(k_collide_stream_x4<S, LR, false, true>, dim3(nb), dim3(threads), s, ov,
             (const S *)a.src, (S *)a.dst, (const float4 *)a.fcur, a.flag_cur, (float4 *)a.fold,
             a.flag_old, L.ny, L.nz, (int)L.ncell, (float)(1.0 / a.tau), (float)a.u_wall, a.status,
             nullptr);
     else
-        launch_maybe_overlapped(k_collide_stream_x4<S, LR, false>, dim3(nb), dim3(256), s, ov,
+        launch_maybe_overlapped(k_collide_stream_x4<S, LR, false>, dim3(nb), dim3(threads), s, ov,
             (const S *)a.src, (S *)a.dst, (const float4 *)a.fcur, a.flag_cur, (float4 *)a.fold,
             a.flag_old, L.ny, L.nz, (int)L.ncell, (float)(1.0 / a.tau), (float)a.u_wall, a.status,
             nullptr);
