@@ -123,8 +123,6 @@ __global__ void __launch_bounds__(256)
     }
     if (valid && gl == 0) nodeF[node] = V4{fx, fy, fz, T(0)};
 
-    if (!valid) return;  // no shuffles below
-
     // Stencil phase: lane gl of the node's group takes the stencil pieces
     // gl, gl + 32 / NPW, ... of its node (CX cells along x of one row
     // (ky, kz)); a piece's y and z weights and its wrapped row base are formed
@@ -133,8 +131,15 @@ __global__ void __launch_bounds__(256)
     // pieces: whole rows with four nodes per warp; with one node per warp
     // pieces that spread the n^3 cells over most of the 32 lanes
     constexpr int CX = NPW == 1 ? (N == 4 ? 2 : 1) : N, SPR = N / CX, NS = N * N * SPR;
+    // whole rows: the group shares the node's delta factors by shuffles
+    // (below), so every lane stays until they are formed; a group past the
+    // last node forms those of the last node and leaves before writing
+    if constexpr (CX != N) {
+        if (!valid) return;  // no shuffles below
+    }
+    const int nd = valid ? node : n_nodes - 1;
     T p[kPosLen<T>];
-    pos.approx(node, p);
+    pos.approx(nd, p);
     T pc[3];
     if constexpr (kPosLen<T> == 6) {
         pc[0] = p[0] + p[3]; pc[1] = p[1] + p[4]; pc[2] = p[2] + p[5];
@@ -142,17 +147,46 @@ __global__ void __launch_bounds__(256)
         pc[0] = p[0]; pc[1] = p[1]; pc[2] = p[2];
     }
     const int bx = stencil_first<N>(pc[0]), by = stencil_first<N>(pc[1]), bz = stencil_first<N>(pc[2]);
-    const RunDesc R = runs ? runs[node_run[node]] : single;
+    const RunDesc R = runs ? runs[node_run[nd]] : single;
     const int sx = __ffs(R.tx) - 1, sy = __ffs(R.ty) - 1;
     const int xw0 = wrap_index(bx, SLAB ? R.gnx : R.nx), yw0 = wrap_index(by, R.ny);
-    T wrow[CX == N ? N : 1];
+    // whole rows: the x factors of the node and the y and z factors of the
+    // lane's rows gl and gl + G.  The node has 3N factors, delta_phi of axis
+    // k / N at stencil offset k % N (the same arguments as formed cell by
+    // cell, so the same values); lane gl of the group forms factor gl and,
+    // where 3N > G, factor gl + G, and the group exchanges them.
+    T wrow[CX == N ? N : 1], wy2[2] = {T(0), T(0)}, wz2[2] = {T(0), T(0)};
     if constexpr (CX == N) {
-#pragma unroll
-        for (int kx = 0; kx < N; ++kx) {
+        constexpr int G = kFsGroup, NF = 3 * N;
+        static_assert(N * N <= 2 * G && NF <= 2 * G, "two rows and two factors per lane at most");
+        auto factor = [&](int k) {
+            const int ax = k / N, j = k % N;
             T d[3];
-            pos.rel(p, bx + kx, by, bz, d);
-            wrow[kx] = delta_phi<N>(d[0]);
+            pos.rel(p, bx + j, by + j, bz + j, d);
+            return delta_phi<N>(ax == 0 ? d[0] : (ax == 1 ? d[1] : d[2]));
+        };
+        const T fa = factor(gl < NF ? gl : 0);
+        T fb = T(0);
+        if constexpr (NF > G) {
+            if (gl + G < NF) fb = factor(gl + G);
         }
+        auto share = [&](int k) {  // factor k of the group (every lane takes part)
+            T v = __shfl_sync(0xffffffffu, fa, k < G ? k : 0, G);
+            if constexpr (NF > G) {
+                const T b = __shfl_sync(0xffffffffu, fb, k >= G ? k - G : 0, G);
+                if (k >= G) v = b;
+            }
+            return v;
+        };
+#pragma unroll
+        for (int kx = 0; kx < N; ++kx) wrow[kx] = share(kx);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = (gl + h * G) % (N * N);  // rows past the last are not used
+            wy2[h] = share(N + r % N);
+            wz2[h] = share(2 * N + r / N);
+        }
+        if (!valid) return;
     }
     V4 *fr = force + R.cell_off;
     uint8_t *flr = flags + R.tile_off;
@@ -163,9 +197,16 @@ __global__ void __launch_bounds__(256)
             set_status(status, kStatusStencil);
             continue;
         }
-        T d[3];
-        pos.rel(p, bx, Y, Z, d);
-        const T wy = delta_phi<N>(d[1]), wz = delta_phi<N>(d[2]);
+        T wy, wz;
+        if constexpr (CX == N) {
+            wy = sl < kFsGroup ? wy2[0] : wy2[1];
+            wz = sl < kFsGroup ? wz2[0] : wz2[1];
+        } else {
+            T d[3];
+            pos.rel(p, bx, Y, Z, d);
+            wy = delta_phi<N>(d[1]);
+            wz = delta_phi<N>(d[2]);
+        }
         const int yw = wrap_next<N>(yw0, r % N, R.ny);
         const long long rc = (long long)R.nx * (yw + (long long)R.ny * Z);
         const long long rt = ((long long)Z * R.nty + (yw >> sy)) * R.ntx;
@@ -288,16 +329,37 @@ __device__ __forceinline__ void load_quad<__half>(const __half *p, float v[4]) {
 // k_flag_velocity for a lattice flagged per ftx-cell segment of an x-row
 // (ftx a multiple of 4 dividing nx, so flag index = cell / ftx): one thread
 // takes four consecutive cells of a segment with vector loads (the same
-// arithmetic per cell).
+// arithmetic per cell).  A block covers 256 consecutive quads and first
+// packs its flagged ones onto its first threads (a ballot per warp and the
+// warps' counts in shared memory), so that a flagged quad does not hold a
+// warp of mostly idle lanes: in a dense suspension about one quad in eight
+// is flagged, in short runs along x.
 template <typename S>
 __global__ void __launch_bounds__(256, sizeof(S) == 2 ? 4 : 3)
     k_flag_velocity_x4(const S *__restrict__ pop, const float4 *__restrict__ force,
                        const uint8_t *__restrict__ flags, float4 *__restrict__ uvel, long long ncell,
                        int ftx) {
+    __shared__ int warp_count[8];
+    __shared__ unsigned char packed[256];  // the block's flagged quads, in order
     prior_grid_wait();
     allow_dependents();
-    const long long cell0 = 4 * (blockIdx.x * (long long)blockDim.x + threadIdx.x);
-    if (cell0 >= ncell || !flags[cell0 / ftx]) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long q0 = 256 * (long long)blockIdx.x;  // first quad of the block
+    const long long own = 4 * (q0 + tid);
+    const bool flagged = own < ncell && flags[own / ftx];
+    const unsigned ballot = __ballot_sync(0xffffffffu, flagged);
+    if (lane == 0) warp_count[warp] = __popc(ballot);
+    __syncthreads();
+    int before = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        before += w < warp ? warp_count[w] : 0;
+        total += warp_count[w];
+    }
+    if (flagged) packed[before + __popc(ballot & ((1u << lane) - 1u))] = (unsigned char)tid;
+    __syncthreads();
+    if (tid >= total) return;
+    const long long cell0 = 4 * (q0 + packed[tid]);
     // velocity_from's sums, in its order, as the loads arrive
     float drho[4] = {0.f, 0.f, 0.f, 0.f}, jx[4] = {0.f, 0.f, 0.f, 0.f};
     float jy[4] = {0.f, 0.f, 0.f, 0.f}, jz[4] = {0.f, 0.f, 0.f, 0.f};
