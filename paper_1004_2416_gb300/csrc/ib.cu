@@ -49,6 +49,41 @@
 
 namespace iblbm {
 
+// The 3N separable delta factors of a node's N^3 stencil, formed once by the
+// G lanes of the node's group and exchanged by shuffles: factor k is
+// delta_phi<N> along axis k / N at stencil offset k % N, from the same
+// difference (cell coordinate - node position) as a factor formed cell by
+// cell, so the same value; lane gl forms factors gl and, where 3N > G,
+// gl + G.  share() is called by every lane of the warp together.
+template <int N, typename T, int G>
+struct GroupFactors {
+    static constexpr int NF = 3 * N;
+    static_assert(NF <= 2 * G, "two factors per lane at most");
+    T fa, fb;
+    template <typename P>
+    __device__ __forceinline__ GroupFactors(const P &pos, const T *p, int bx, int by, int bz, int gl) {
+        auto factor = [&](int k) {
+            const int ax = k / N, j = k % N;
+            T d[3];
+            pos.rel(p, bx + j, by + j, bz + j, d);
+            return delta_phi<N>(ax == 0 ? d[0] : (ax == 1 ? d[1] : d[2]));
+        };
+        fa = factor(gl < NF ? gl : 0);
+        fb = T(0);
+        if constexpr (NF > G) {
+            if (gl + G < NF) fb = factor(gl + G);
+        }
+    }
+    __device__ __forceinline__ T share(int k) const {
+        T v = __shfl_sync(0xffffffffu, fa, k < G ? k : 0, G);
+        if constexpr (NF > G) {
+            const T b = __shfl_sync(0xffffffffu, fb, k >= G ? k - G : 0, G);
+            if (k >= G) v = b;
+        }
+        return v;
+    }
+};
+
 // One warp takes NPW nodes (1 or 4).  Face phase: a group of 32 / NPW lanes
 // per node, one adjacent face per lane (a loop for higher valences), a
 // fixed-order butterfly reduction within the group that leaves the node force
@@ -151,40 +186,19 @@ __global__ void __launch_bounds__(256)
     const int sx = __ffs(R.tx) - 1, sy = __ffs(R.ty) - 1;
     const int xw0 = wrap_index(bx, SLAB ? R.gnx : R.nx), yw0 = wrap_index(by, R.ny);
     // whole rows: the x factors of the node and the y and z factors of the
-    // lane's rows gl and gl + G.  The node has 3N factors, delta_phi of axis
-    // k / N at stencil offset k % N (the same arguments as formed cell by
-    // cell, so the same values); lane gl of the group forms factor gl and,
-    // where 3N > G, factor gl + G, and the group exchanges them.
+    // lane's rows gl and gl + G, from the group's shared factors
     T wrow[CX == N ? N : 1], wy2[2] = {T(0), T(0)}, wz2[2] = {T(0), T(0)};
     if constexpr (CX == N) {
-        constexpr int G = kFsGroup, NF = 3 * N;
-        static_assert(N * N <= 2 * G && NF <= 2 * G, "two rows and two factors per lane at most");
-        auto factor = [&](int k) {
-            const int ax = k / N, j = k % N;
-            T d[3];
-            pos.rel(p, bx + j, by + j, bz + j, d);
-            return delta_phi<N>(ax == 0 ? d[0] : (ax == 1 ? d[1] : d[2]));
-        };
-        const T fa = factor(gl < NF ? gl : 0);
-        T fb = T(0);
-        if constexpr (NF > G) {
-            if (gl + G < NF) fb = factor(gl + G);
-        }
-        auto share = [&](int k) {  // factor k of the group (every lane takes part)
-            T v = __shfl_sync(0xffffffffu, fa, k < G ? k : 0, G);
-            if constexpr (NF > G) {
-                const T b = __shfl_sync(0xffffffffu, fb, k >= G ? k - G : 0, G);
-                if (k >= G) v = b;
-            }
-            return v;
-        };
+        constexpr int G = kFsGroup;
+        static_assert(N * N <= 2 * G, "two rows per lane at most");
+        const GroupFactors<N, T, G> gf(pos, p, bx, by, bz, gl);
 #pragma unroll
-        for (int kx = 0; kx < N; ++kx) wrow[kx] = share(kx);
+        for (int kx = 0; kx < N; ++kx) wrow[kx] = gf.share(kx);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int r = (gl + h * G) % (N * N);  // rows past the last are not used
-            wy2[h] = share(N + r % N);
-            wz2[h] = share(2 * N + r / N);
+            wy2[h] = gf.share(N + r % N);
+            wz2[h] = gf.share(2 * N + r / N);
         }
         if (!valid) return;
     }
@@ -453,14 +467,20 @@ __global__ void __launch_bounds__(256)
             }
         }
     }
-    // x factors: once per lane for whole rows, else per cell
-    T wrow[CX == N ? N : 1];
+    // whole rows: the x factors of the node and the y and z factors of the
+    // lane's rows from the group's shared factors (every lane of the warp
+    // takes part: a group past the last node works on the last node);
+    // otherwise x factors per cell, y and z per piece
+    T wrow[CX == N ? N : 1], WY[RPL], WZ[RPL];
     if constexpr (CX == N) {
+        const GroupFactors<N, T, G> gf(pos, p, bx, by, bz, gl);
 #pragma unroll
-        for (int kx = 0; kx < N; ++kx) {
-            T d[3];
-            pos.rel(p, bx + kx, by, bz, d);
-            wrow[kx] = delta_phi<N>(d[0]);
+        for (int kx = 0; kx < N; ++kx) wrow[kx] = gf.share(kx);
+#pragma unroll
+        for (int j = 0; j < RPL; ++j) {
+            const int r = (gl + G * j) % NS;  // pieces past the last are not used
+            WY[j] = gf.share(N + r % N);
+            WZ[j] = gf.share(2 * N + r / N);
         }
     }
     auto weight = [&](int j, int c, T wyz_y, T wyz_z) -> T {
@@ -490,9 +510,16 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int j = 0; j < RPL; ++j) {
             if (!in[j]) continue;
-            T d[3];
-            pos.rel(p, bx, Y[j], Z[j], d);
-            const T wy = delta_phi<N>(d[1]), wz = delta_phi<N>(d[2]);
+            T wy, wz;
+            if constexpr (CX == N) {
+                wy = WY[j];
+                wz = WZ[j];
+            } else {
+                T d[3];
+                pos.rel(p, bx, Y[j], Z[j], d);
+                wy = delta_phi<N>(d[1]);
+                wz = delta_phi<N>(d[2]);
+            }
 #pragma unroll
             for (int c = 0; c < CX; ++c) {
                 const T w = weight(j, c, wy, wz);
@@ -511,8 +538,8 @@ __global__ void __launch_bounds__(256)
         auto load = [&](int j, int slot) {
 #pragma unroll
             for (int c = 0; c < CX; ++c) {
-#pragma unroll
                 const bool own = in[j] && (!SLAB || XW[j][c] >= 0) && IBLBM_OK(rc[j] + XW[j][c], 1, R.ncell);
+#pragma unroll
                 for (int i = 0; i < 19; ++i)
                     g[slot][c][i] = own ? Store<S, T>::load(pr + i * R.ncell + rc[j] + XW[j][c]) : T(0);
                 f[slot][c] = own ? fr[rc[j] + XW[j][c]] : V4{};
