@@ -158,13 +158,16 @@ struct FaceMath<NodeRead<float>> {
         r[1] = (h.y - oh[1]) + (l.y - ol[1]);
         r[2] = (h.z - oh[2]) + (l.z - ol[2]);
     }
-    static __device__ __forceinline__ void geom(const NodeRead<float> &nodes, int4 t, const double o[3],
-                                                float cen[3], float An[3]) {
-        float oh[3], ol[3];
+    // the capsule origin as a float pair (hi, lo): formed once per thread,
+    // not per face (double arithmetic is scarce on this GPU)
+    static __device__ __forceinline__ void split(const double o[3], float oh[3], float ol[3]) {
         for (int k = 0; k < 3; ++k) {
             oh[k] = (float)o[k];
             ol[k] = (float)(o[k] - (double)oh[k]);
         }
+    }
+    static __device__ __forceinline__ void geom(const NodeRead<float> &nodes, int4 t, const float oh[3],
+                                                const float ol[3], float cen[3], float An[3]) {
         float a[3], b[3], c[3];
         rel(nodes, t.x, oh, ol, a);
         rel(nodes, t.y, oh, ol, b);
@@ -179,12 +182,10 @@ struct FaceMath<NodeRead<float>> {
         An[1] = 0.5f * (e1[2] * e2[0] - e1[0] * e2[2]);
         An[2] = 0.5f * (e1[0] * e2[1] - e1[1] * e2[0]);
     }
-    // the same terms in float (a thread adds its few faces in float and the
-    // sums over threads and blocks are carried in double)
-    static __device__ __forceinline__ void stage1f(const NodeRead<float> &nodes, int4 t, const double o[3],
-                                                   float v[5]) {
-        float r[3], An[3];
-        geom(nodes, t, o, r, An);
+    // the terms in float (a thread adds its few faces in float and the sums
+    // over threads and blocks are carried in double), from the face centroid
+    // relative to the origin r and the area vector An
+    static __device__ __forceinline__ void terms1(const float r[3], const float An[3], float v[5]) {
         const float rn = r[0] * An[0] + r[1] * An[1] + r[2] * An[2];
         v[0] = rn * (1.0f / 3.0f);
         v[1] = sqrtf(An[0] * An[0] + An[1] * An[1] + An[2] * An[2]);
@@ -192,12 +193,11 @@ struct FaceMath<NodeRead<float>> {
         v[3] = rn * r[1];
         v[4] = rn * r[2];
     }
-    static __device__ __forceinline__ void stage2f(const NodeRead<float> &nodes, int4 t, const double o[3],
-                                                   const double c[3], float v[6]) {
-        float cen[3], An[3];
-        geom(nodes, t, o, cen, An);
+    // co = capsule centroid - origin in float, formed once per thread
+    static __device__ __forceinline__ void terms2(const float cen[3], const float An[3], const float co[3],
+                                                  float v[6]) {
         float r[3];
-        for (int k = 0; k < 3; ++k) r[k] = cen[k] - (float)(c[k] - o[k]);
+        for (int k = 0; k < 3; ++k) r[k] = cen[k] - co[k];
         const float rn = (r[0] * An[0] + r[1] * An[1] + r[2] * An[2]) * 0.2f;
         const float r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
         v[0] = (r2 - r[0] * r[0]) * rn;
@@ -206,32 +206,6 @@ struct FaceMath<NodeRead<float>> {
         v[3] = -r[0] * r[1] * rn;
         v[4] = -r[0] * r[2] * rn;
         v[5] = -r[1] * r[2] * rn;
-    }
-    static __device__ __forceinline__ void stage1(const NodeRead<float> &nodes, int4 t,
-                                                  const double o[3], double v[5]) {
-        float r[3], An[3];
-        geom(nodes, t, o, r, An);
-        const float rn = r[0] * An[0] + r[1] * An[1] + r[2] * An[2];
-        v[0] = (double)rn * (1.0 / 3.0);
-        v[1] = (double)sqrtf(An[0] * An[0] + An[1] * An[1] + An[2] * An[2]);
-        v[2] = (double)(rn * r[0]);
-        v[3] = (double)(rn * r[1]);
-        v[4] = (double)(rn * r[2]);
-    }
-    static __device__ __forceinline__ void stage2(const NodeRead<float> &nodes, int4 t,
-                                                  const double o[3], const double c[3], double v[6]) {
-        float cen[3], An[3];
-        geom(nodes, t, o, cen, An);
-        float r[3];
-        for (int k = 0; k < 3; ++k) r[k] = cen[k] - (float)(c[k] - o[k]);
-        const float rn = (r[0] * An[0] + r[1] * An[1] + r[2] * An[2]) * 0.2f;
-        const float r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-        v[0] = (double)((r2 - r[0] * r[0]) * rn);
-        v[1] = (double)((r2 - r[1] * r[1]) * rn);
-        v[2] = (double)((r2 - r[2] * r[2]) * rn);
-        v[3] = (double)(-r[0] * r[1] * rn);
-        v[4] = (double)(-r[0] * r[2] * rn);
-        v[5] = (double)(-r[1] * r[2] * rn);
     }
 };
 
@@ -297,13 +271,16 @@ __global__ void __launch_bounds__(kTaylorClusterThreads) k_taylor_cluster(R node
     const double o[3] = {p.origin[3 * cap], p.origin[3 * cap + 1], p.origin[3 * cap + 2]};
     const int stride = CS * blockDim.x;
     double v[6] = {0, 0, 0, 0, 0, 0};
+    float oh[3], ol[3];  // float builds: the origin as a float pair
+    if constexpr (std::is_same<R, NodeRead<float>>::value) FaceMath<R>::split(o, oh, ol);
     if constexpr (std::is_same<R, NodeRead<float>>::value) {
         float vf[5] = {0, 0, 0, 0, 0};
 #pragma unroll 4
         for (int f = f0 + rank * blockDim.x + threadIdx.x; f < f1; f += stride) {
-            float w[5];
             if (!IBLBM_FACE_OK(f)) continue;
-            FaceMath<R>::stage1f(nodes, tri[f], o, w);
+            float r[3], An[3], w[5];
+            FaceMath<R>::geom(nodes, tri[f], oh, ol, r, An);
+            FaceMath<R>::terms1(r, An, w);
             for (int k = 0; k < 5; ++k) vf[k] += w[k];
         }
         for (int k = 0; k < 5; ++k) v[k] = (double)vf[k];
@@ -335,11 +312,14 @@ __global__ void __launch_bounds__(kTaylorClusterThreads) k_taylor_cluster(R node
     double I[6] = {0, 0, 0, 0, 0, 0};
     if constexpr (std::is_same<R, NodeRead<float>>::value) {
         float If[6] = {0, 0, 0, 0, 0, 0};
+        float co[3];
+        for (int k = 0; k < 3; ++k) co[k] = (float)(c[k] - o[k]);
 #pragma unroll 4
         for (int f = f0 + rank * blockDim.x + threadIdx.x; f < f1; f += stride) {
-            float w[6];
             if (!IBLBM_FACE_OK(f)) continue;
-            FaceMath<R>::stage2f(nodes, tri[f], o, c, w);
+            float cen[3], An[3], w[6];
+            FaceMath<R>::geom(nodes, tri[f], oh, ol, cen, An);
+            FaceMath<R>::terms2(cen, An, co, w);
             for (int k = 0; k < 6; ++k) If[k] += w[k];
         }
         for (int k = 0; k < 6; ++k) I[k] = (double)If[k];
