@@ -160,18 +160,15 @@ __global__ void __launch_bounds__(256)
 
     // Stencil phase: lane gl of the node's group takes the stencil pieces
     // gl, gl + 32 / NPW, ... of its node (CX cells along x of one row
-    // (ky, kz)); a piece's y and z weights and its wrapped row base are formed
-    // once, the x weights once per lane when the pieces are whole rows.
-    // Force flag tiles are powers of two.
+    // (ky, kz)); a piece's wrapped row base is formed once, its delta
+    // weights come from the node's 3N separable factors, formed once across
+    // the group and shared by shuffles (GroupFactors), so every lane stays
+    // until they are formed; a group past the last node forms those of the
+    // last node and leaves before writing.  Force flag tiles are powers of two.
     // pieces: whole rows with four nodes per warp; with one node per warp
     // pieces that spread the n^3 cells over most of the 32 lanes
     constexpr int CX = NPW == 1 ? (N == 4 ? 2 : 1) : N, SPR = N / CX, NS = N * N * SPR;
-    // whole rows: the group shares the node's delta factors by shuffles
-    // (below), so every lane stays until they are formed; a group past the
-    // last node forms those of the last node and leaves before writing
-    if constexpr (CX != N) {
-        if (!valid) return;  // no shuffles below
-    }
+    constexpr int G = kFsGroup, RPL = (NS + G - 1) / G;  // pieces per lane, at most
     const int nd = valid ? node : n_nodes - 1;
     T p[kPosLen<T>];
     pos.approx(nd, p);
@@ -185,57 +182,41 @@ __global__ void __launch_bounds__(256)
     const RunDesc R = runs ? runs[node_run[nd]] : single;
     const int sx = __ffs(R.tx) - 1, sy = __ffs(R.ty) - 1;
     const int xw0 = wrap_index(bx, SLAB ? R.gnx : R.nx), yw0 = wrap_index(by, R.ny);
-    // whole rows: the x factors of the node and the y and z factors of the
-    // lane's rows gl and gl + G, from the group's shared factors
-    T wrow[CX == N ? N : 1], wy2[2] = {T(0), T(0)}, wz2[2] = {T(0), T(0)};
-    if constexpr (CX == N) {
-        constexpr int G = kFsGroup;
-        static_assert(N * N <= 2 * G, "two rows per lane at most");
+    // the x, y and z factors of the lane's pieces
+    T WX[RPL][CX], WY[RPL], WZ[RPL];
+    {
         const GroupFactors<N, T, G> gf(pos, p, bx, by, bz, gl);
 #pragma unroll
-        for (int kx = 0; kx < N; ++kx) wrow[kx] = gf.share(kx);
+        for (int j = 0; j < RPL; ++j) {
+            const int sl = (gl + G * j) % NS;  // pieces past the last are not used
+            const int r = sl / SPR, kx0 = (sl % SPR) * CX;
+            WY[j] = gf.share(N + r % N);
+            WZ[j] = gf.share(2 * N + r / N);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int r = (gl + h * G) % (N * N);  // rows past the last are not used
-            wy2[h] = gf.share(N + r % N);
-            wz2[h] = gf.share(2 * N + r / N);
+            for (int c = 0; c < CX; ++c) WX[j][c] = gf.share(kx0 + c);
         }
-        if (!valid) return;
     }
+    if (!valid) return;
     V4 *fr = force + R.cell_off;
     uint8_t *flr = flags + R.tile_off;
-    for (int sl = gl; sl < NS; sl += kFsGroup) {
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) {
+        const int sl = gl + G * j;
+        if (sl >= NS) break;
         const int r = sl / SPR, kx0 = (sl % SPR) * CX;
-        const int Y = by + r % N, Z = bz + r / N;
+        const int Z = bz + r / N;
         if (Z < 0 || Z >= R.nz) {
             set_status(status, kStatusStencil);
             continue;
         }
-        T wy, wz;
-        if constexpr (CX == N) {
-            wy = sl < kFsGroup ? wy2[0] : wy2[1];
-            wz = sl < kFsGroup ? wz2[0] : wz2[1];
-        } else {
-            T d[3];
-            pos.rel(p, bx, Y, Z, d);
-            wy = delta_phi<N>(d[1]);
-            wz = delta_phi<N>(d[2]);
-        }
+        const T wy = WY[j], wz = WZ[j];
         const int yw = wrap_next<N>(yw0, r % N, R.ny);
         const long long rc = (long long)R.nx * (yw + (long long)R.ny * Z);
         const long long rt = ((long long)Z * R.nty + (yw >> sy)) * R.ntx;
         int last = -1;
 #pragma unroll
         for (int c = 0; c < CX; ++c) {
-            T wxv;
-            if constexpr (CX == N) {
-                wxv = wrow[c];
-            } else {
-                T dx[3];
-                pos.rel(p, bx + kx0 + c, by, bz, dx);
-                wxv = delta_phi<N>(dx[0]);
-            }
-            const T w = wxv * wy * wz;
+            const T w = WX[j][c] * wy * wz;
             if (w == T(0)) continue;
             const int xa = xw0 + kx0 + c;
             int xw;
@@ -447,12 +428,11 @@ __global__ void __launch_bounds__(256)
     // this lane's pieces; a stencil beyond a wall is reported by the spreading
     bool in[RPL];
     long long rc[RPL];
-    int Y[RPL], Z[RPL], KX[RPL], XW[RPL][CX];
+    int Z[RPL], KX[RPL], XW[RPL][CX];
 #pragma unroll
     for (int j = 0; j < RPL; ++j) {
         const int sl = gl + G * j, r = sl / SPR;
         KX[j] = (sl % SPR) * CX;
-        Y[j] = by + r % N;
         Z[j] = bz + r / N;
         in[j] = sl < NS && Z[j] >= 0 && Z[j] < nz;
         rc[j] = in[j] ? (long long)nx * (wrap_next<N>(yw0, r % N, ny) + (long long)ny * Z[j]) : 0;
@@ -467,33 +447,22 @@ __global__ void __launch_bounds__(256)
             }
         }
     }
-    // whole rows: the x factors of the node and the y and z factors of the
-    // lane's rows from the group's shared factors (every lane of the warp
-    // takes part: a group past the last node works on the last node);
-    // otherwise x factors per cell, y and z per piece
-    T wrow[CX == N ? N : 1], WY[RPL], WZ[RPL];
-    if constexpr (CX == N) {
+    // the x, y and z delta factors of the lane's pieces, from the node's 3N
+    // factors formed once across the group and shared (every lane of the
+    // warp takes part: a group past the last node works on the last node)
+    T WX[RPL][CX], WY[RPL], WZ[RPL];
+    {
         const GroupFactors<N, T, G> gf(pos, p, bx, by, bz, gl);
 #pragma unroll
-        for (int kx = 0; kx < N; ++kx) wrow[kx] = gf.share(kx);
-#pragma unroll
         for (int j = 0; j < RPL; ++j) {
-            const int r = (gl + G * j) % NS;  // pieces past the last are not used
+            const int sl = (gl + G * j) % NS;  // pieces past the last are not used
+            const int r = sl / SPR, kx0 = (sl % SPR) * CX;
             WY[j] = gf.share(N + r % N);
             WZ[j] = gf.share(2 * N + r / N);
+#pragma unroll
+            for (int c = 0; c < CX; ++c) WX[j][c] = gf.share(kx0 + c);
         }
     }
-    auto weight = [&](int j, int c, T wyz_y, T wyz_z) -> T {
-        T wxv;
-        if constexpr (CX == N) {
-            wxv = wrow[c];
-        } else {
-            T d[3];
-            pos.rel(p, bx + KX[j] + c, by, bz, d);
-            wxv = delta_phi<N>(d[0]);
-        }
-        return wxv * wyz_y * wyz_z;
-    };
     // positions, stencil indices and x factors need nothing of the collide
     // or velocity kernel before this one; the velocities do
     prior_grid_wait();
@@ -510,19 +479,9 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int j = 0; j < RPL; ++j) {
             if (!in[j]) continue;
-            T wy, wz;
-            if constexpr (CX == N) {
-                wy = WY[j];
-                wz = WZ[j];
-            } else {
-                T d[3];
-                pos.rel(p, bx, Y[j], Z[j], d);
-                wy = delta_phi<N>(d[1]);
-                wz = delta_phi<N>(d[2]);
-            }
 #pragma unroll
             for (int c = 0; c < CX; ++c) {
-                const T w = weight(j, c, wy, wz);
+                const T w = WX[j][c] * WY[j] * WZ[j];
                 if (w == T(0)) continue;
                 ax += w * u[j][c].x;
                 ay += w * u[j][c].y;
@@ -554,13 +513,10 @@ __global__ void __launch_bounds__(256)
             if (!in[j]) continue;
             const int slot = ALL ? j : 0;
             if constexpr (!ALL) load(j, 0);
-            T d[3];
-            pos.rel(p, bx, Y[j], Z[j], d);
-            const T wy = delta_phi<N>(d[1]), wz = delta_phi<N>(d[2]);
 #pragma unroll
             for (int c = 0; c < CX; ++c) {
                 if (SLAB && XW[j][c] < 0) continue;
-                const T w = weight(j, c, wy, wz);
+                const T w = WX[j][c] * WY[j] * WZ[j];
                 if (w == T(0)) continue;
                 const V4 u = velocity_from<T>(g[slot][c], f[slot][c]);
                 ax += w * u.x;
