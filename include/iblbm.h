@@ -564,23 +564,26 @@ int iblbm_get_taylor(iblbm_sim *sim, int capsule_id, double out[16]);
 
 /* ---- asynchronous read-back -------------------------------------------------------
  *
- * Enqueues on the object's stream, after the work already enqueued, and
- * returns without synchronising:
+ * Copies the node positions into a snapshot on the object's stream, after
+ * the work already enqueued, and returns without synchronising; the rest runs
+ * from the snapshot on a read-back stream of the object, so that the steps
+ * enqueued after this call do not wait for it:
  *   host_nodes  (may be NULL) the positions of all nodes, [n_nodes][3]
  *               doubles, capsules in order (as iblbm_get_nodes(sim, -1, ..));
  *   host_sums   (may be NULL) the device reductions of every capsule,
  *               [n_capsules][12] doubles {V, A, c_x, c_y, c_z, I_xx, I_yy,
  *               I_zz, I_xy, I_xz, I_yz, 0} (as behind iblbm_get_taylor;
  *               iblbm_taylor_from_sums turns one into the 16 shape values).
- * The host buffers belong to the caller and are written when the stream
- * reaches the copies: read them after the next synchronising call (e.g.
- * iblbm_sync), and leave them alone until then.  Page-locked buffers
- * (cudaHostAlloc, cudaHostRegister, torch pin_memory) let the copies run
- * while the host enqueues further steps; pageable buffers make the copies
- * synchronous.  The device conversions use buffers of the object, so a later
- * read-back may be enqueued at once (the stream orders them).  Device errors
- * come back from the next synchronising call.  IBLBM_ERR_ARG for a null
- * object. */
+ * The host buffers belong to the caller and are written by the read-back
+ * stream: read them after the next iblbm_sync (which waits for that stream
+ * too), and leave them alone until then.  Page-locked buffers (cudaHostAlloc,
+ * cudaHostRegister, torch pin_memory) let the copies run while the host
+ * enqueues further steps; pageable buffers make the copies synchronous.  The
+ * snapshots and device conversions use two sets of buffers of the object,
+ * taken in turn, so later read-backs may be enqueued at once (a set is
+ * reused after the read-back stream is done with it).  Device errors come
+ * back from the next iblbm_sync.  IBLBM_ERR_ARG for a null object,
+ * IBLBM_ERR_OOM when the buffers cannot be allocated (none is kept). */
 int iblbm_read_async(iblbm_sim *sim, double *host_nodes, double *host_sums);
 
 /* The 16 shape values of iblbm_get_taylor from one capsule's 12 reduced sums

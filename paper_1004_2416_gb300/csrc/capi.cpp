@@ -118,8 +118,19 @@ struct iblbm_sim {
 
     double *d_scratch = nullptr;
     unsigned long long *d_cksum = nullptr;  // checkpoint section checksums
-    double *d_readback = nullptr;  // iblbm_read_async's node conversion
-    size_t readback_bytes = 0;
+    // iblbm_read_async: the positions are copied into a snapshot on the main
+    // stream; their conversion to doubles, the capsule reductions and the
+    // copies to the host run from it on the read-back stream, so the steps
+    // enqueued after a read-back do not wait for it.  Two sets of buffers,
+    // alternating; a set is written again once the read-back stream is done
+    // with it (ev_rdone).
+    cudaStream_t rstream = nullptr;
+    cudaEvent_t ev_rsnap[2] = {nullptr, nullptr}, ev_rdone[2] = {nullptr, nullptr};
+    bool rb_used[2] = {false, false};
+    int rb_next = 0;
+    void *rb_x[2] = {nullptr, nullptr}, *rb_lo[2] = {nullptr, nullptr};  // layout of mesh.x / x_lo
+    double *rb_nodes[2] = {nullptr, nullptr}, *rb_sums[2] = {nullptr, nullptr};
+    int rb_nodes_cap = 0, rb_caps_cap = 0;  // nodes and capsules the buffers hold
     size_t scratch_bytes = 0;
 
     // Taylor recording: after every `rec_every`-th step (0 = off) the device
@@ -278,12 +289,52 @@ void free_ring(iblbm_sim *s);
 void join_side(iblbm_sim *s);
 void reduce_snapshots(iblbm_sim *s);
 
+// iblbm_read_async's buffers: released once the read-back stream is done
+// with them.
+void free_readback(iblbm_sim *s) {
+    if (s->rstream) cudaStreamSynchronize(s->rstream);
+    for (int b = 0; b < 2; ++b) {
+        dev_free(s, s->rb_x[b]);
+        dev_free(s, s->rb_lo[b]);
+        dev_free(s, s->rb_nodes[b]);
+        dev_free(s, s->rb_sums[b]);
+        s->rb_x[b] = s->rb_lo[b] = nullptr;
+        s->rb_nodes[b] = s->rb_sums[b] = nullptr;
+        s->rb_used[b] = false;
+    }
+    s->rb_nodes_cap = s->rb_caps_cap = 0;
+}
+
+// Both sets of read-back buffers for n nodes and nc capsules; on a refused
+// block none is kept.
+int ensure_readback(iblbm_sim *s, int n, int nc) {
+    if (s->rb_nodes_cap >= n && s->rb_caps_cap >= nc && s->rb_x[0]) return IBLBM_OK;
+    free_readback(s);
+    const size_t v4 = 4 * real_bytes(s) * (size_t)n;
+    bool ok = true;
+    for (int b = 0; b < 2 && ok; ++b) {
+        s->rb_x[b] = dev_alloc(s, v4);
+        s->rb_lo[b] = s->prec == kF64 ? nullptr : dev_alloc(s, (size_t)16 * n);
+        s->rb_nodes[b] = (double *)dev_alloc(s, sizeof(double) * 3 * (size_t)n);
+        s->rb_sums[b] = (double *)dev_alloc(s, sizeof(double) * 12 * (size_t)(nc > 0 ? nc : 1));
+        ok = s->rb_x[b] && (s->prec == kF64 || s->rb_lo[b]) && s->rb_nodes[b] && s->rb_sums[b];
+    }
+    if (!ok) {
+        free_readback(s);
+        return fail(s, IBLBM_ERR_OOM, "read-back buffer allocation failed");
+    }
+    s->rb_nodes_cap = n;
+    s->rb_caps_cap = nc;
+    return IBLBM_OK;
+}
+
 // (Re)builds the device membrane tables after capsules were added.  Current
 // node positions of existing capsules are kept.
 int ensure_mesh(iblbm_sim *s) {
     if (!s->mesh_dirty) return IBLBM_OK;
     join_side(s);  // nothing may still read the tables that are rebuilt below
     CK(cudaStreamSynchronize(s->stream));
+    if (s->rstream) CK(cudaStreamSynchronize(s->rstream));  // nor a read-back
     const int nn = (int)(s->X0.size() / 3), nf = (int)(s->tri.size() / 3), nc = (int)s->caps.size();
     std::vector<double> xcur(s->X0);
     if (s->dev_nodes > 0) {
@@ -706,6 +757,7 @@ int sync_status(iblbm_sim *s) {
     CK(cudaSetDevice(s->device));
     join_side(s);
     CK(cudaStreamSynchronize(s->stream));
+    if (s->rstream) CK(cudaStreamSynchronize(s->rstream));  // iblbm_read_async's copies
     int bits = 0;
     CK(cudaMemcpy(&bits, s->d_status, sizeof(int), cudaMemcpyDeviceToHost));
     if (bits) {
@@ -818,7 +870,12 @@ int setup_object(iblbm_sim *s, void *stream, const iblbm_allocator *alloc, long 
         cudaEventCreateWithFlags(&s->ev_join[0], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->ev_join[1], cudaEventDisableTiming) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->tstream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&s->ev_tfork, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&s->ev_tfork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&s->rstream, cudaStreamNonBlocking, least_prio) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_rsnap[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_rsnap[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_rdone[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev_rdone[1], cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         g_create_error = "stream or event creation failed";
         return IBLBM_ERR_CUDA;
@@ -1048,6 +1105,7 @@ int iblbm_destroy(iblbm_sim *s) {
     cudaSetDevice(s->device);
     if (s->stream) cudaStreamSynchronize(s->stream);
     if (s->side) cudaStreamSynchronize(s->side);
+    if (s->rstream) cudaStreamSynchronize(s->rstream);
     drop_graphs(s);
     for (int k = 0; k < 2; ++k) {
         dev_free(s, s->pop[k]);
@@ -1057,7 +1115,7 @@ int iblbm_destroy(iblbm_sim *s) {
     dev_free(s, s->d_status);
     dev_free(s, s->d_fix);
     dev_free(s, s->uvel);
-    dev_free(s, s->d_readback);
+    free_readback(s);
     dev_free(s, s->d_scratch);
     dev_free(s, s->d_cksum);
     dev_free(s, s->slab_planes);
@@ -1076,6 +1134,11 @@ int iblbm_destroy(iblbm_sim *s) {
     if (s->tstream) {
         cudaStreamSynchronize(s->tstream);
         cudaStreamDestroy(s->tstream);
+    }
+    if (s->rstream) cudaStreamDestroy(s->rstream);
+    for (int k = 0; k < 2; ++k) {
+        if (s->ev_rsnap[k]) cudaEventDestroy(s->ev_rsnap[k]);
+        if (s->ev_rdone[k]) cudaEventDestroy(s->ev_rdone[k]);
     }
     if (s->ev_tfork) cudaEventDestroy(s->ev_tfork);
     if (s->ev_fork) cudaEventDestroy(s->ev_fork);
@@ -2459,28 +2522,39 @@ int iblbm_read_async(iblbm_sim *s, double *host_nodes, double *host_sums) {
     int rc = ensure_mesh(s);
     if (rc) return rc;
     const int n = s->mesh.n_nodes, nc = (int)s->caps.size();
-    if (host_nodes && n > 0) {
-        const size_t bytes = sizeof(double) * 3 * (size_t)n;
-        if (s->readback_bytes < bytes) {
-            CK(cudaStreamSynchronize(s->stream));  // a pending copy may still read the old buffer
-            dev_free(s, s->d_readback);
-            s->d_readback = (double *)dev_alloc(s, bytes);
-            s->readback_bytes = s->d_readback ? bytes : 0;
-            if (!s->d_readback) return fail(s, IBLBM_ERR_OOM, "read-back buffer allocation failed");
-        }
-        launch_nodes_to_f64(s->prec, s->mesh, 0, 0, n, s->d_readback, s->stream);
+    const bool want_nodes = host_nodes && n > 0, want_sums = host_sums && nc > 0;
+    if (!want_nodes && !want_sums) return IBLBM_OK;
+    rc = ensure_readback(s, n, nc);
+    if (rc) return rc;
+    const int b = s->rb_next;
+    s->rb_next = 1 - b;
+    // the snapshot: set b once the read-back stream is done with its last use
+    if (s->rb_used[b]) CK(cudaStreamWaitEvent(s->stream, s->ev_rdone[b], 0));
+    CK(cudaMemcpyAsync(s->rb_x[b], s->mesh.x, 4 * real_bytes(s) * (size_t)n, cudaMemcpyDeviceToDevice,
+                       s->stream));
+    if (s->mesh.x_lo)
+        CK(cudaMemcpyAsync(s->rb_lo[b], s->mesh.x_lo, (size_t)16 * n, cudaMemcpyDeviceToDevice, s->stream));
+    CK(cudaEventRecord(s->ev_rsnap[b], s->stream));
+    CK(cudaStreamWaitEvent(s->rstream, s->ev_rsnap[b], 0));
+    MeshDev m = s->mesh;  // the same tables, positions from the snapshot
+    m.x = s->rb_x[b];
+    m.x_lo = s->rb_lo[b];
+    if (want_nodes) {
+        launch_nodes_to_f64(s->prec, m, 0, 0, n, s->rb_nodes[b], s->rstream);
         CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(host_nodes, s->d_readback, bytes, cudaMemcpyDeviceToHost, s->stream));
+        CK(cudaMemcpyAsync(host_nodes, s->rb_nodes[b], sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToHost,
+                           s->rstream));
     }
-    if (host_sums && nc > 0) {
-        // the recorded reductions on the side stream share the partial sums:
-        // the stream waits for them (events only, no host synchronisation)
-        join_side(s);
-        launch_taylor(s->prec, s->mesh, s->plan, false, s->stream);
+    if (want_sums) {
+        TaylorPlan p = s->plan;  // an immediate reduction into this set's output
+        p.out = s->rb_sums[b];
+        launch_taylor(s->prec, m, p, false, s->rstream);
         CK(cudaGetLastError());
-        CK(cudaMemcpyAsync(host_sums, s->plan.out, sizeof(double) * 12 * (size_t)nc, cudaMemcpyDeviceToHost,
-                           s->stream));
+        CK(cudaMemcpyAsync(host_sums, s->rb_sums[b], sizeof(double) * 12 * (size_t)nc, cudaMemcpyDeviceToHost,
+                           s->rstream));
     }
+    CK(cudaEventRecord(s->ev_rdone[b], s->rstream));
+    s->rb_used[b] = true;
     return IBLBM_OK;
 }
 

@@ -1,6 +1,8 @@
-"""Asynchronous read-back: iblbm_read_async enqueues copies of the node
-positions and the capsule reductions behind the steps already enqueued; after
-a synchronising call they equal what the synchronising getters return."""
+"""Asynchronous read-back: iblbm_read_async snapshots the node positions
+behind the steps already enqueued and copies them and the capsule reductions
+to the host from a read-back stream; after iblbm_sync they equal what the
+synchronising getters return at the same step, also when further steps ran
+while the read-backs were in flight."""
 import numpy as np
 import pytest
 import torch
@@ -47,6 +49,35 @@ def test_read_async_matches_getters(prec, pinned):
         for key in ("D", "theta", "V", "A", "c_x", "I_xx", "I_xz"):
             assert got[key] == ref[key], (k, key)
     g.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
+def test_read_async_per_step_while_stepping(prec):
+    """A read-back after each of eight steps, all in flight while the next
+    steps run, against the getters of a twin run after the same steps
+    (deterministic spreading: both runs have the same bits)."""
+    case = _case(prec)
+    runs = [gpu_sim(case), gpu_sim(case)]
+    for g in runs:
+        g.set_deterministic_spreading(True)
+    a, twin = runs
+    n, nc, k_steps = a.info().n_nodes, len(case.capsules), 8
+    nodes = [torch.empty(n * 3, dtype=torch.float64, pin_memory=True).numpy() for _ in range(k_steps)]
+    sums = [torch.empty(nc * 12, dtype=torch.float64, pin_memory=True).numpy() for _ in range(k_steps)]
+    for k in range(k_steps):
+        a.step(1)
+        a.read_async(nodes[k], sums[k])
+    a.sync()
+    for k in range(k_steps):
+        twin.step(1)
+        assert np.array_equal(nodes[k].reshape(-1, 3), twin.get_nodes()), k
+        for c in range(nc):
+            got = B.taylor_from_sums(sums[k][12 * c:12 * (c + 1)])
+            ref = twin.taylor(c)
+            for key in ("D", "theta", "V", "A", "c_x", "I_xx", "I_xz"):
+                assert got[key] == ref[key], (k, c, key)
+    for g in runs:
+        g.close()
 
 
 def test_read_async_arguments():
