@@ -328,6 +328,31 @@ __host__ __device__ constexpr int rows_per_block() {
     return LR <= 32 ? NWB * (32 / LR) : NWB / (LR / 32);
 }
 
+// The 19 direction arrays of a population buffer as the vectorised kernel
+// addresses them: DirPtrs passes the 19 base pointers as kernel parameters (an
+// address is a base pointer from the parameter bank plus the cell offset),
+// DirStride one base pointer and the direction stride.
+template <typename P>
+struct DirPtrs {
+    P *p[19];
+    __device__ __forceinline__ P *operator()(int i, int) const { return p[i]; }
+};
+template <typename P>
+struct DirStride {
+    P *base;
+    __device__ __forceinline__ P *operator()(int i, int ncell) const { return base + (size_t)i * ncell; }
+};
+template <typename D, typename P>
+D make_dirs(P *base, int ncell) {
+    D d{};
+    if constexpr (std::is_same<D, DirStride<P>>::value) {
+        d.base = base;
+    } else {
+        for (int i = 0; i < 19; ++i) d.p[i] = base + (size_t)i * ncell;
+    }
+    return d;
+}
+
 // Launch shape of k_collide_stream_x4: blocks of eight warps, two per SM
 // (128 registers).  Binary16 rows that span several warps take one row per
 // block, so that the barrier before the warp-edge rewrite holds only the
@@ -342,6 +367,12 @@ struct X4Shape {
     static constexpr int kWarps = kRowBlocks ? LR / 32 : 8;
     static constexpr bool kRaw = kRowBlocks && LR <= 128;
     static constexpr int kMinBlocks = kRaw ? 20 / kWarps : 2;
+    // binary16: the direction base pointers as parameters (config 4's collide
+    // 66.5 -> 64.7 us); float storage keeps one base and the stride (the table
+    // took 9 % of the FP32 kernel's instructions away but none of its time,
+    // which the HBM sets)
+    using Src = std::conditional_t<sizeof(S) == 2, DirPtrs<const S>, DirStride<const S>>;
+    using Dst = std::conditional_t<sizeof(S) == 2, DirPtrs<S>, DirStride<S>>;
 };
 
 // The 19 populations of a thread's quad as collide_quad reads them: pair h
@@ -378,8 +409,8 @@ struct QuadRawHalf {
 // inactive ones too: they join the shuffles and, for rows spanning several
 // warps, the block barrier of the warp-edge rewrite; `edge` holds one row of
 // ten values per warp).
-template <typename S, int LR, bool WM, bool LIN, typename Src>
-__device__ __forceinline__ void collide_quad(const Src &g, S *__restrict__ dst,
+template <typename S, int LR, bool WM, bool LIN, typename Src, typename Dst>
+__device__ __forceinline__ void collide_quad(const Src &g, const Dst &dst,
                                              const float4 *__restrict__ fcur, bool has_cur, bool active, int row,
                                              int y, int z, int x0, int cell0, int lane, int warp, int ny, int nz,
                                              int ncell, float omega, float u_wall, int *status,
@@ -467,10 +498,10 @@ __device__ __forceinline__ void collide_quad(const Src &g, S *__restrict__ dst,
             const float uw = (cz > 0) ? u_wall : -u_wall;
             const float wall = (cx == 0) ? 0.f : SC * 6.f * q_w<float>(i) * (cx > 0 ? uw : -uw);
             if (IBLBM_OK(cell0, 4, ncell))
-                Quad<S>::store_raw(dst + (size_t)q_opp(i) * ncell + cell0, p[0] - wall, p[1] - wall,
+                Quad<S>::store_raw(dst(q_opp(i), ncell) + cell0, p[0] - wall, p[1] - wall,
                                    p[2] - wall, p[3] - wall);
         } else {
-            S *rowp = dst + (size_t)i * ncell + (row0 + (cy > 0 ? dyp : (cy < 0 ? dym : 0)) + cz * plane);
+            S *rowp = dst(i, ncell) + (row0 + (cy > 0 ? dyp : (cy < 0 ? dym : 0)) + cz * plane);
             if (IBLBM_OK((long long)(row0 + (cy > 0 ? dyp : (cy < 0 ? dym : 0)) + cz * plane) + x0, 4, ncell))
                 Quad<S>::store_raw(rowp + x0, o0, o1, o2, o3);
             if constexpr (LR > 32) {
@@ -550,7 +581,7 @@ __device__ __forceinline__ void collide_quad(const Src &g, S *__restrict__ dst,
                 const int cx = q_cx(i), cy = q_cy(i), cz = q_cz(i);
                 if (cx == 0 || (cz > 0 ? top : (cz < 0 ? bottom : false))) continue;
                 if ((cx > 0) != (lane == 0)) continue;
-                S *rowp = dst + (size_t)i * ncell + (row0 + (cy > 0 ? dyp : (cy < 0 ? dym : 0)) + cz * plane);
+                S *rowp = dst(i, ncell) + (row0 + (cy > 0 ? dyp : (cy < 0 ? dym : 0)) + cz * plane);
                 if (IBLBM_OK((long long)(row0 + (cy > 0 ? dyp : (cy < 0 ? dym : 0)) + cz * plane) + x0 +
                                  (cx > 0 ? 0 : 3), 1, ncell))
                     StoreRaw<S>::store(rowp + x0 + (cx > 0 ? 0 : 3), edge[from][edge_slot(i)]);
@@ -563,7 +594,7 @@ __device__ __forceinline__ void collide_quad(const Src &g, S *__restrict__ dst,
 // LIN: the linearised equilibrium (as collide_cell).
 template <typename S, int LR, bool WM, bool LIN = false>
 __global__ void __launch_bounds__(32 * X4Shape<S, LR>::kWarps, X4Shape<S, LR>::kMinBlocks)
-    k_collide_stream_x4(const S *__restrict__ src, S *__restrict__ dst,
+    k_collide_stream_x4(const typename X4Shape<S, LR>::Src src, const typename X4Shape<S, LR>::Dst dst,
                         const float4 *__restrict__ fcur, const uint8_t *__restrict__ flag_cur,
                         float4 *__restrict__ fold, uint8_t *__restrict__ flag_old, int ny, int nz,
                         int ncell, float omega, float u_wall, int *status, float4 *__restrict__ moments) {
@@ -613,7 +644,7 @@ __global__ void __launch_bounds__(32 * X4Shape<S, LR>::kWarps, X4Shape<S, LR>::k
         uint2 raw[19];
 #pragma unroll
         for (int i = 0; i < 19; ++i)
-            raw[i] = quad_ok ? __ldg(reinterpret_cast<const uint2 *>(src + (size_t)i * ncell + cell0))
+            raw[i] = quad_ok ? __ldg(reinterpret_cast<const uint2 *>(src(i, ncell) + cell0))
                              : make_uint2(0u, 0u);
         collide_quad<S, LR, WM, LIN>(QuadRawHalf{raw}, dst, fcur, has_cur, active, row, y, z, x0, cell0, lane,
                                      warp, ny, nz, ncell, omega, u_wall, status, moments, edge);
@@ -622,7 +653,7 @@ __global__ void __launch_bounds__(32 * X4Shape<S, LR>::kWarps, X4Shape<S, LR>::k
 #pragma unroll
         for (int i = 0; i < 19; ++i) {
             if (quad_ok) {
-                Quad<S>::load_raw(src + (size_t)i * ncell + cell0, g[i][0], g[i][1]);
+                Quad<S>::load_raw(src(i, ncell) + cell0, g[i][0], g[i][1]);
             } else {
                 g[i][0] = make_float2(0.f, 0.f);
                 g[i][1] = g[i][0];
@@ -727,8 +758,8 @@ __global__ void __launch_bounds__(THREADS, 2)
         float2 g[19][2];
 #pragma unroll
         for (int i = 0; i < 19; ++i) QuadSmem<S>::load(tile + (size_t)i * TILE, g[i][0], g[i][1]);
-        collide_quad<S, LR, false, LIN>(QuadRegs{g}, dst, fcur, has_cur, active, row, y, z, x0, cell0, lane,
-                                        warp, ny, nz, ncell, omega, u_wall, status, nullptr, edge);
+        collide_quad<S, LR, false, LIN>(QuadRegs{g}, DirStride<S>{dst}, fcur, has_cur, active, row, y, z,
+                                        x0, cell0, lane, warp, ny, nz, ncell, omega, u_wall, status, nullptr, edge);
         __syncthreads();  // buffer b is read: it may be refilled
         if (threadIdx.x == 0 && t + 2 * (int)gridDim.x < n_tiles) {
             fence_async_smem();
@@ -1091,6 +1122,8 @@ static void collide_x4(const Lattice &L, const CollideArgs &a, cudaStream_t s, b
     using Sh = X4Shape<S, LR>;
     constexpr int rpb = rows_per_block<LR, Sh::kWarps>();
     constexpr unsigned threads = 32 * Sh::kWarps;
+    const auto sp = make_dirs<typename Sh::Src>((const S *)a.src, (int)L.ncell);
+    const auto dp = make_dirs<typename Sh::Dst>((S *)a.dst, (int)L.ncell);
     const int nrows = L.ny * L.nz;
     if constexpr ((4 * LR * sizeof(S)) % 16 == 0 && LR <= staged_threads<S>()) {
         if (a.staged && !a.moments) {
@@ -1104,17 +1137,17 @@ static void collide_x4(const Lattice &L, const CollideArgs &a, cudaStream_t s, b
     // with the full equilibrium
     if (a.moments)
         launch_maybe_overlapped(k_collide_stream_x4<S, LR, true>, dim3(nb), dim3(threads), s, ov,
-            (const S *)a.src, (S *)a.dst, (const float4 *)a.fcur, a.flag_cur, (float4 *)a.fold,
+            sp, dp, (const float4 *)a.fcur, a.flag_cur, (float4 *)a.fold,
             a.flag_old, L.ny, L.nz, (int)L.ncell, (float)(1.0 / a.tau), (float)a.u_wall, a.status,
             (float4 *)a.moments);
     else if (a.eq_order == 1)
         launch_maybe_overlapped(k_collide_stream_x4<S, LR, false, true>, dim3(nb), dim3(threads), s, ov,
-            (const S *)a.src, (S *)a.dst, (const float4 *)a.fcur, a.flag_cur, (float4 *)a.fold,
+            sp, dp, (const float4 *)a.fcur, a.flag_cur, (float4 *)a.fold,
             a.flag_old, L.ny, L.nz, (int)L.ncell, (float)(1.0 / a.tau), (float)a.u_wall, a.status,
             nullptr);
     else
         launch_maybe_overlapped(k_collide_stream_x4<S, LR, false>, dim3(nb), dim3(threads), s, ov,
-            (const S *)a.src, (S *)a.dst, (const float4 *)a.fcur, a.flag_cur, (float4 *)a.fold,
+            sp, dp, (const float4 *)a.fcur, a.flag_cur, (float4 *)a.fold,
             a.flag_old, L.ny, L.nz, (int)L.ncell, (float)(1.0 / a.tau), (float)a.u_wall, a.status,
             nullptr);
 }
