@@ -41,6 +41,7 @@
 // In the float builds the edges and the Gram entries are formed in
 // double-float arithmetic from the hi/lo node coordinates, so the deviations
 // d keep their relative precision even for strains of 1e-4.
+#include <algorithm>
 #include <type_traits>
 
 #include "device_common.cuh"
@@ -862,6 +863,27 @@ void launch_nodes_to_f64(int prec, const MeshDev &m, int which, int first, int c
     else
         k_nodes_to_f64<float><<<nb, 256, 0, s>>>(view<float>(m), (const float4 *)m.F,
                                                  (const float4 *)m.u, which, first, count, out);
+}
+
+// Copy of the node positions (and their low parts) into a snapshot, in one
+// launch: 16-byte words, those of x first.
+__global__ void k_copy_words(const uint4 *__restrict__ a, uint4 *__restrict__ a_out, long long na,
+                             const uint4 *__restrict__ b, uint4 *__restrict__ b_out, long long nb) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < na + nb;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (i < na) a_out[i] = a[i];
+        else b_out[i - na] = b[i - na];
+    }
+}
+
+void launch_snapshot_nodes(int prec, const MeshDev &m, int count, void *x_out, void *lo_out, cudaStream_t s) {
+    if (count <= 0) return;
+    const long long na = (long long)count * (prec == kF64 ? 2 : 1);  // dvec4: two words per node
+    const long long nb = (prec == kF64 || !m.x_lo) ? 0 : (long long)count;
+    const long long n = na + nb;
+    const unsigned blocks = (unsigned)std::min<long long>((n + 255) / 256, 4 * 152);
+    k_copy_words<<<blocks, 256, 0, s>>>((const uint4 *)m.x, (uint4 *)x_out, na, (const uint4 *)m.x_lo,
+                                        (uint4 *)lo_out, nb);
 }
 
 void launch_f64_to_nodes(int prec, const MeshDev &m, int first, int count, const double *in,

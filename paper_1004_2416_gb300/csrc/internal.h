@@ -221,6 +221,8 @@ void launch_nodes_to_f64(int prec, const MeshDev &m, int which, int first, int c
                          cudaStream_t s);
 void launch_f64_to_nodes(int prec, const MeshDev &m, int first, int count, const double *in,
                          cudaStream_t s);
+// m.x (and m.x_lo in the float builds) of `count` nodes copied to x_out (lo_out).
+void launch_snapshot_nodes(int prec, const MeshDev &m, int count, void *x_out, void *lo_out, cudaStream_t s);
 
 // ---- adjoint.cu ---------------------------------------------------------------------
 // Buffers of one reverse step (step t of a single lattice).

@@ -51,12 +51,21 @@ def test_read_async_matches_getters(prec, pinned):
     g.close()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp16"])
-def test_read_async_per_step_while_stepping(prec):
+def _case_many(prec):
+    """Four 2 562-node capsules: 10 248 nodes, above the count from which
+    the read-back snapshot is taken by a copy kernel instead of the copy
+    engine."""
+    caps = [W.Capsule((15.2 + 24.0 * k, 23.6, 19.7), 6.0, 4, W.k_s_for(0.05, 6.0)) for k in range(4)]
+    return W.Case("readback-many", (96, 48, 40), 1.0, 3, prec, 0.02, caps, 40)
+
+
+@pytest.mark.parametrize("prec,many", [("fp64", False), ("fp32", False), ("fp16", False), ("fp32", True),
+                                       ("fp64", True)])
+def test_read_async_per_step_while_stepping(prec, many):
     """A read-back after each of eight steps, all in flight while the next
     steps run, against the getters of a twin run after the same steps
     (deterministic spreading: both runs have the same bits)."""
-    case = _case(prec)
+    case = _case_many(prec) if many else _case(prec)
     runs = [gpu_sim(case), gpu_sim(case)]
     for g in runs:
         g.set_deterministic_spreading(True)
