@@ -367,10 +367,10 @@ struct X4Shape {
     static constexpr int kWarps = kRowBlocks ? LR / 32 : 8;
     static constexpr bool kRaw = kRowBlocks && LR <= 128;
     static constexpr int kMinBlocks = kRaw ? 20 / kWarps : 2;
-    // binary16: the direction base pointers as parameters (config 4's collide
-    // 66.5 -> 64.7 us); float storage keeps one base and the stride (the table
-    // took 9 % of the FP32 kernel's instructions away but none of its time,
-    // which the HBM sets)
+    // binary16: the direction base pointers as parameters (256 x 128 x 128
+    // lattice: 66.5 -> 63.9 us per collide); float storage keeps one base and
+    // the stride (on the 128^3 lattice the table took 9 % of the kernel's
+    // instructions away but none of its time, which the HBM sets)
     using Src = std::conditional_t<sizeof(S) == 2, DirPtrs<const S>, DirStride<const S>>;
     using Dst = std::conditional_t<sizeof(S) == 2, DirPtrs<S>, DirStride<S>>;
 };
